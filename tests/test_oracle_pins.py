@@ -1,0 +1,479 @@
+"""Pins of the FP64 oracle against closed forms, brute force and textbook
+routines (CPU only).  Each test names the paper passage it fixes.
+
+A plausible slip in the oracle -- a dropped term, a wrong sign or index, a
+transposed operand -- fails at least one of these.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy import integrate
+
+from paper_2410_11419_gb300 import synth
+from tests import bruteforce
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# -- helpers ------------------------------------------------------------------
+
+def one_gaussian_scene(mean, scale, rot=(1, 0, 0, 0), logit=2.0, k=0, mlp_seed=3):
+    """Scene of explicitly placed Gaussians (arrays of shape (n, ...))."""
+    mean = np.atleast_2d(np.asarray(mean, dtype=np.float64))
+    n = mean.shape[0]
+    scale = np.broadcast_to(np.asarray(scale, dtype=np.float64), (n, 3))
+    rot = np.broadcast_to(np.asarray(rot, dtype=np.float64), (n, 4))
+    logit = np.broadcast_to(np.asarray(logit, dtype=np.float64), (n,))
+    f32 = lambda a: np.ascontiguousarray(a, dtype=np.float32)
+    z1 = np.zeros((n, 1))
+    return synth.Scene(
+        n=n, k=k,
+        mean_op=f32(np.concatenate([mean, logit[:, None]], 1)),
+        scale=f32(np.concatenate([scale, z1], 1)),
+        rot=f32(rot), shade_rot=f32(np.tile([1.0, 0, 0, 0], (n, 1))),
+        albedo_d=f32(np.tile([0.8, 0.5, 0.2, 0.0], (n, 1))),
+        albedo_s=f32(np.tile([1.0, 1.0, 1.0, 0.0], (n, 1))),
+        latent=f32(np.zeros((2, n, 4))),
+        lobe_rot=f32(np.tile([1.0, 0, 0, 0], (k, n, 1))),
+        lobe_sigma=f32(np.tile([1.0, 1.0, 0.3, 0.0], (k, n, 1))),
+        lobe_amp=f32(np.tile([0.2, 0.3, 0.4, 0.0], (k, n, 1))),
+        phi=synth.make_mlp(mlp_seed, "phi", 61, 16, 2, 1, synth.RELU),
+        psi=synth.make_mlp(mlp_seed, "psi", 60, 16, 2, 3, synth.RELU),
+    )
+
+
+def np_mlp(m, x):
+    """Textbook dense layers with NumPy float64 matrix products."""
+    h = x.astype(np.float64)
+    for li, (w, b) in enumerate(zip(m.weights, m.biases)):
+        h = h @ w.astype(np.float64).T + b.astype(np.float64)
+        if li < m.n_hidden:
+            h = np.maximum(h, 0) if m.act == synth.RELU else np.where(h > 0, h, 0.01 * h)
+        else:
+            h = 1 / (1 + np.exp(-h))
+    return h
+
+
+def np_pe(v):
+    out = [v]
+    for k in range(4):
+        out += [np.sin((2 ** k) * np.pi * v), np.cos((2 ** k) * np.pi * v)]
+    return np.concatenate(out)
+
+
+def quat_mat(q):
+    w, x, y, z = np.asarray(q, dtype=np.float64) / np.linalg.norm(q)
+    return np.array([[1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)],
+                     [2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)],
+                     [2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)]])
+
+
+# -- Eq. 3 --------------------------------------------------------------------
+
+def test_diffuse_closed_forms(oracle):
+    """Eq. 3 with ELU alpha = eps = 0.01: f_d(1) = 1/pi, f_d(-1) = 0, increasing."""
+    assert oracle.diffuse(1.0) == pytest.approx(1.0 / math.pi, rel=1e-15)
+    assert abs(oracle.diffuse(-1.0)) < 1e-18
+    xs = np.linspace(-1, 1, 2001)
+    v = np.array([oracle.diffuse(x) for x in xs])
+    assert np.all(np.diff(v) > 0)
+    # slope at x < 0 is 0.01 e^x / ((1 + 0.01 (1 - 1/e)) pi): check one point by FD
+    h = 1e-6
+    fd = (oracle.diffuse(-0.5 + h) - oracle.diffuse(-0.5 - h)) / (2 * h)
+    off = 0.01 * (1 - math.exp(-1))
+    assert fd == pytest.approx(0.01 * math.exp(-0.5) / ((1 + off) * math.pi), rel=1e-6)
+
+
+# -- Eq. 5 --------------------------------------------------------------------
+
+def test_angular_gaussian_pole(oracle):
+    """At h' = z the angular Gaussian is 1/sigma_z (Eq. 5)."""
+    q = np.array([0.9, 0.1, -0.3, 0.2], dtype=np.float32)
+    z = quat_mat(q)[:, 2]
+    for sz in (0.13, 0.4, 0.69):
+        assert oracle.angular_gaussian(z, q, [0.5, 1.0, sz]) == pytest.approx(1 / sz, rel=1e-12)
+
+
+def _sphere_integral(f, n_theta=700, n_phi=1400, theta_max=math.pi):
+    th = (np.arange(n_theta) + 0.5) * theta_max / n_theta
+    ph = (np.arange(n_phi) + 0.5) * 2 * math.pi / n_phi
+    tot = 0.0
+    for t in th:
+        row = sum(f(np.array([math.sin(t) * math.cos(p), math.sin(t) * math.sin(p), math.cos(t)]))
+                  for p in ph[::7])
+        tot += row * 7 * math.sin(t)
+    return tot * (theta_max / n_theta) * (2 * math.pi / n_phi)
+
+
+def test_sphere_integrator_on_sg():
+    """The quadrature used below reproduces the SG closed form 2 pi (1 - e^-2l)/l."""
+    lam = 10.0
+    val = _sphere_integral(lambda w: math.exp(lam * (w[2] - 1.0)), n_theta=600, n_phi=700)
+    assert val == pytest.approx(2 * math.pi * (1 - math.exp(-2 * lam)) / lam, rel=2e-4)
+
+
+def test_lobe_integral_isotropic(oracle):
+    """Isotropic Eq. 5 (sigma_x = sigma_y = 1) integrates to
+    2 pi int_0^pi exp(-t^2 / (2 s^2)) sin t dt / s over the sphere."""
+    q = np.array([0.7, 0.2, 0.5, -0.1], dtype=np.float32)
+    Rl = quat_mat(q)
+    sz = 0.35
+    val = _sphere_integral(lambda w: oracle.angular_gaussian(Rl @ w, q, [1.0, 1.0, sz]),
+                           n_theta=500, n_phi=700)
+    ref = 2 * math.pi * integrate.quad(
+        lambda t: math.exp(-t * t / (2 * sz * sz)) * math.sin(t) / sz, 0, math.pi,
+        epsabs=1e-13, epsrel=1e-12)[0]
+    assert val == pytest.approx(ref, rel=2e-4)
+
+
+def test_lobe_integral_anisotropic_small_sigma(oracle):
+    """Small-sigma_z limit of the anisotropic lobe integral: 2 pi sx sy sz."""
+    q = np.array([1.0, 0.0, 0.0, 0.0], dtype=np.float32)
+    sx, sy, sz = 0.5, 1.0, 0.01
+    tmax = 12 * sz * max(sx, sy)
+    nt, nphi = 600, 720
+    th = (np.arange(nt) + 0.5) * tmax / nt
+    ph = (np.arange(nphi) + 0.5) * 2 * math.pi / nphi
+    tot = 0.0
+    for t in th:
+        s = 0.0
+        for p in ph[::4]:
+            s += oracle.angular_gaussian(
+                [math.sin(t) * math.cos(p), math.sin(t) * math.sin(p), math.cos(t)], q, [sx, sy, sz])
+        tot += s * 4 * math.sin(t)
+    tot *= (tmax / nt) * (2 * math.pi / nphi)
+    assert tot == pytest.approx(2 * math.pi * sx * sy * sz, rel=2e-3)
+
+
+def test_lobe_anisotropy_axes(oracle):
+    """Rotating h' about z by 90 degrees swaps the roles of sigma_x and sigma_y."""
+    q = np.array([1.0, 0.0, 0.0, 0.0], dtype=np.float32)
+    t = 0.3
+    hx = [math.sin(t), 0.0, math.cos(t)]
+    hy = [0.0, math.sin(t), math.cos(t)]
+    sz = 0.4
+    gx = oracle.angular_gaussian(hx, q, [0.5, 1.0, sz])
+    gy = oracle.angular_gaussian(hy, q, [0.5, 1.0, sz])
+    assert gx == pytest.approx(math.exp(-0.5 * (t / 0.5 / sz) ** 2) / sz, rel=1e-12)
+    assert gy == pytest.approx(math.exp(-0.5 * (t / 1.0 / sz) ** 2) / sz, rel=1e-12)
+
+
+# -- Eq. 2 shading --------------------------------------------------------------
+
+def test_shading_closed_form(oracle):
+    """Light and camera straight above a Gaussian with identity frames:
+    omega_i' = omega_o' = h' = e_z, so f_d = 1/pi and every lobe gives 1/sigma_z."""
+    sc = one_gaussian_scene([0.0, 0.0, 0.0], 0.05, k=2)
+    cam = synth.look_at_camera([0.0, 0.0, 3.0], width=32, height=32)
+    light = synth.Light(pos=np.array([0.0, 0.0, 2.0], dtype=np.float32), intensity=10.0)
+    rgb = oracle.shade(sc, 0, cam, light)
+    E = 10.0 / 4.0
+    amp = np.array([0.2, 0.3, 0.4], dtype=np.float32).astype(np.float64)
+    sz = float(np.float32(0.3))
+    rho = np.array([0.8, 0.5, 0.2], dtype=np.float32).astype(np.float64)
+    want = E * (rho / math.pi + 2 * amp / sz)
+    np.testing.assert_allclose(rgb, want, rtol=1e-12)
+    # switching the inverse-square fall-off off gives E = I
+    rgb2 = oracle.shade(sc, 0, cam, light, oracle.Opts(falloff=0))
+    np.testing.assert_allclose(rgb2, want / E * 10.0, rtol=1e-12)
+
+
+# -- positional encoding, MLPs (Sec. 4.2, 4.3) --------------------------------
+
+def test_pos_enc_values(oracle):
+    out = oracle.pos_enc([0.5, 0.25, 0.0])
+    np.testing.assert_allclose(out[:3], [0.5, 0.25, 0.0])
+    np.testing.assert_allclose(out[3:6], [1.0, math.sqrt(0.5), 0.0], atol=1e-15)   # sin(pi v)
+    np.testing.assert_allclose(out[6:9], [0.0, math.sqrt(0.5), 1.0], atol=1e-15)   # cos(pi v)
+    np.testing.assert_allclose(out[9:12], [0.0, 1.0, 0.0], atol=1e-15)             # sin(2 pi v)
+    np.testing.assert_allclose(out[24:27], [1.0, 1.0, 1.0], atol=1e-15)            # cos(8 pi v)
+    assert out.shape == (27,)
+
+
+@pytest.mark.parametrize("act", [synth.RELU, synth.LEAKY_RELU])
+def test_mlp_against_numpy(oracle, act):
+    m = synth.make_mlp(11, "phi", 61, 32, 3, 1, act)
+    m.biases = [np.random.default_rng(1).normal(0, 0.1, b.shape).astype(np.float32)
+                for b in m.biases]
+    x = np.random.default_rng(2).normal(0, 1, (50, 61))
+    np.testing.assert_allclose(oracle.mlp_eval(m, x), np_mlp(m, x), rtol=1e-12, atol=1e-15)
+
+
+# -- EWA projection (Sec. 3) --------------------------------------------------
+
+def test_projection_on_axis(oracle):
+    """Isotropic Gaussian on the optical axis: mean2D = principal point and
+    Sigma_2D = (f s / z)^2 I + 0.3 I."""
+    cam = synth.look_at_camera([0.0, 0.0, 3.0], width=64, height=48)
+    s, z = 0.05, 3.0
+    uv, con = oracle.project([0, 0, 0], [s, s, s], [0.3, 0.1, 0.5, 0.2], cam.R, cam.t,
+                             cam.fx, cam.fy, cam.cx, cam.cy)
+    np.testing.assert_allclose(uv, [cam.cx, cam.cy], atol=1e-9)
+    fx = np.float64(cam.fx)
+    sf = float(np.float32(s))
+    zz = float(np.float32(3.0))
+    var = (fx * sf / zz) ** 2 + 0.3
+    np.testing.assert_allclose(con, [1 / var, 0.0, 1 / var], rtol=1e-6, atol=1e-12)
+
+
+def test_projection_matches_fd_jacobian(oracle):
+    """Off axis: Sigma_2D = J W Sigma W^T J^T + 0.3 I with J the finite-difference
+    Jacobian of the pinhole map at the view-space mean."""
+    cam = synth.look_at_camera([2.0, -1.0, 2.0], width=200, height=150)
+    rng = np.random.default_rng(5)
+    R = cam.R.astype(np.float64)
+    t = cam.t.astype(np.float64)
+    for _ in range(10):
+        m = rng.uniform(-0.5, 0.5, 3)
+        s = rng.uniform(0.01, 0.08, 3)
+        q = rng.normal(size=4)
+        uv, con = oracle.project(m, s, q, cam.R, cam.t, cam.fx, cam.fy, cam.cx, cam.cy)
+        m32 = m.astype(np.float32).astype(np.float64)
+        s32 = s.astype(np.float32).astype(np.float64)
+        q32 = q.astype(np.float32).astype(np.float64)
+        p = R @ m32 + t
+        pin = lambda v: np.array([cam.fx * v[0] / v[2] + cam.cx, cam.fy * v[1] / v[2] + cam.cy])
+        J = np.zeros((2, 3))
+        h = 1e-6
+        for i in range(3):
+            e = np.zeros(3)
+            e[i] = h
+            J[:, i] = (pin(p + e) - pin(p - e)) / (2 * h)
+        Rq = quat_mat(q32)
+        Sig = Rq @ np.diag(s32 ** 2) @ Rq.T
+        S2 = J @ R @ Sig @ R.T @ J.T + 0.3 * np.eye(2)
+        np.testing.assert_allclose(uv, pin(p), rtol=1e-12)
+        np.testing.assert_allclose(con, np.array([S2[1, 1], -S2[0, 1], S2[0, 0]]) /
+                                   np.linalg.det(S2), rtol=1e-6)
+
+
+def test_light_view_centres_the_scene(oracle):
+    """The light camera sits at the light and looks at the scene centre."""
+    for pl in ([0.0, 3.0, 0.5], [1.0, -2.0, 2.0], [0.0, 0.0, 3.0]):
+        R, t = oracle.light_view(pl)
+        R = R.astype(np.float64)
+        np.testing.assert_allclose(R @ R.T, np.eye(3), atol=1e-6)
+        c = R @ np.zeros(3) + t
+        np.testing.assert_allclose(c, [0, 0, np.linalg.norm(pl)], atol=1e-5)
+        np.testing.assert_allclose(-R.T @ t, pl, atol=1e-5)
+
+
+# -- FP32 key recipe and tile lists (O7, O8) ----------------------------------
+
+@pytest.fixture(scope="module")
+def tiny_frame(oracle):
+    sc = synth.tiny_scene(0)
+    cam, light = synth.camera_light_pair(0, 128, 128)
+    return sc, cam, light, oracle.render(sc, cam, light)
+
+
+def test_keys_are_fp32_depths(oracle, tiny_frame):
+    """Camera keys are the FP32 view depths, light keys the FP32 distances to the
+    light, each within 2 ulp of the FP64 value."""
+    sc, cam, light, fr = tiny_frame
+    mu = sc.mean_op[:, :3].astype(np.float64)
+    tz = mu @ cam.R.astype(np.float64)[2] + cam.t[2]
+    vis = fr["cam_rect"][:, 0] >= 0
+    k32 = fr["cam_key"][vis].view(np.float32).astype(np.float64)
+    assert np.all(np.abs(k32 - tz[vis]) <= 2 * np.spacing(np.float32(tz[vis]).astype(np.float32)))
+    dist = np.linalg.norm(mu - light.pos.astype(np.float64), axis=1)
+    lvis = fr["light_rect"][:, 0] >= 0
+    l32 = fr["light_key"][lvis].view(np.float32).astype(np.float64)
+    assert np.all(np.abs(l32 - dist[lvis]) <= 2 * np.spacing(dist[lvis].astype(np.float32)))
+    assert not np.any(fr["cam_key"][~vis] != 0xFFFFFFFF)
+
+
+def test_rects_cover_three_sigma(oracle, tiny_frame):
+    """Each rectangle is the set of 16x16 tiles touched by the square of half
+    side ceil(3 sqrt(lambda_max)) around the mean (FP64 check, 1-tile slack at
+    rounding boundaries)."""
+    sc, cam, light, fr = tiny_frame
+    con = fr["cam_conic"]
+    det = con[:, 0] * con[:, 2] - con[:, 1] ** 2
+    # Sigma_2D = inverse(conic)
+    a, b, c = con[:, 2] / det, -con[:, 1] / det, con[:, 0] / det
+    mid = 0.5 * (a + c)
+    lam = mid + np.sqrt(np.maximum(0.1, mid * mid - (a * c - b * b)))
+    r = np.ceil(3 * np.sqrt(lam))
+    u, v = fr["cam_uv"][:, 0], fr["cam_uv"][:, 1]
+    vis = fr["cam_rect"][:, 0] >= 0
+    gx, gy = fr["gx"], fr["gy"]
+    x0 = np.clip(np.floor((u - r) / 16), 0, gx - 1)
+    x1 = np.clip(np.floor((u + r) / 16), 0, gx - 1)
+    y0 = np.clip(np.floor((v - r) / 16), 0, gy - 1)
+    y1 = np.clip(np.floor((v + r) / 16), 0, gy - 1)
+    R = fr["cam_rect"][vis]
+    for got, want in ((R[:, 0], x0[vis]), (R[:, 2], x1[vis]), (R[:, 1], y0[vis]), (R[:, 3], y1[vis])):
+        assert np.all(np.abs(got - want) <= 1)
+        assert np.mean(got == want) > 0.97
+
+
+def test_tile_lists_definition(oracle, tiny_frame):
+    """Each tile lists exactly the Gaussians whose rectangle contains it,
+    ascending by (depth bits, index)."""
+    sc, cam, light, fr = tiny_frame
+    for nm in ("cam", "light"):
+        ts, lst, rect, key = fr[f"{nm}_tile_start"], fr[f"{nm}_list"], fr[f"{nm}_rect"], fr[f"{nm}_key"]
+        area = np.where(rect[:, 0] >= 0, (rect[:, 2] - rect[:, 0] + 1) * (rect[:, 3] - rect[:, 1] + 1), 0)
+        assert fr[f"{nm}_P"] == area.sum() == ts[-1]
+        for t in range(fr["ntiles"]):
+            tx, ty = t % fr["gx"], t // fr["gx"]
+            np.testing.assert_array_equal(lst[ts[t]:ts[t + 1]], bruteforce.candidates(rect, key, tx, ty))
+
+
+# -- compositing (Eq. 2) against brute force ----------------------------------
+
+@pytest.fixture(scope="module")
+def small_frame(oracle):
+    sc = synth.make_scene(7, 300, 3, "ball")
+    cam, light = synth.camera_light_pair(7, 48, 40)
+    opts = oracle.Opts()
+    return sc, cam, light, opts, oracle.render(sc, cam, light, opts)
+
+
+def test_shadow_values_bruteforce(small_frame):
+    """Sec. 4.2: biased cumulative opacity per shadow ray, beta-weighted average,
+    against the direct O(L^2) product definition."""
+    sc, cam, light, opts, fr = small_frame
+    T = bruteforce.shadow_values(fr, opts)
+    np.testing.assert_allclose(fr["T"], T, rtol=1e-11, atol=1e-14)
+    assert np.all((fr["T"] >= 0) & (fr["T"] <= 1))
+    assert fr["T"].min() < 0.9  # the scene actually casts shadows
+
+
+def test_composite_bruteforce_and_invariants(small_frame):
+    """Eq. 2 per pixel without tiling; transmittance in [0, 1], weights sum to
+    1 - T_final, and the deferred product S * Sh + R (Sec. 4)."""
+    sc, cam, light, opts, fr = small_frame
+    img, fT, wsum = bruteforce.composite(fr, opts, fr["shade"], fr["Tp"], fr["res"])
+    np.testing.assert_allclose(fr["img"], img, rtol=1e-11, atol=1e-13)
+    np.testing.assert_allclose(fr["final_T"], fT, rtol=1e-11, atol=1e-14)
+    np.testing.assert_allclose(wsum, 1 - fT, atol=1e-12)
+    assert np.all((fT > 0) & (fT <= 1))
+    # Sh is a weighted average of T' in (0, 1) with total weight 1 - T_final
+    assert np.all(fr["Sh"] <= (1 - fT) * fr["Tp"].max() + 1e-12)
+    assert np.all(fr["Sh"] >= (1 - fT) * fr["Tp"].min() - 1e-12)
+    np.testing.assert_allclose(fr["img"], fr["S"] * fr["Sh"][..., None] + fr["R"], rtol=1e-13)
+
+
+def test_mlp_inputs_and_outputs(oracle, small_frame):
+    """Phi(T, PE(w_i), PE(mu), l) and Psi(PE(w_o), PE(mu), l) (Sec. 4.2, 4.3)
+    with world-space unit directions, against NumPy matrix products."""
+    sc, cam, light, opts, fr = small_frame
+    mu = sc.mean_op[:, :3].astype(np.float64)
+    lat = np.concatenate([sc.latent[0], sc.latent[1][:, :2]], 1).astype(np.float64)
+    wi = light.pos.astype(np.float64) - mu
+    wi /= np.linalg.norm(wi, axis=1, keepdims=True)
+    wo = cam.pos.astype(np.float64) - mu
+    wo /= np.linalg.norm(wo, axis=1, keepdims=True)
+    xphi = np.stack([np.concatenate([[fr["T"][g]], np_pe(wi[g]), np_pe(mu[g]), lat[g]])
+                     for g in range(sc.n)])
+    xpsi = np.stack([np.concatenate([np_pe(wo[g]), np_pe(mu[g]), lat[g]]) for g in range(sc.n)])
+    np.testing.assert_allclose(fr["Tp"], np_mlp(sc.phi, xphi)[:, 0], rtol=1e-12)
+    np.testing.assert_allclose(fr["res"], np_mlp(sc.psi, xpsi), rtol=1e-12)
+
+
+def test_single_gaussian_frame(oracle):
+    """One Gaussian on the optical axis: no self-shadow (T = 1), and every
+    covered pixel equals alpha^2 c T' + alpha r with
+    alpha = gamma exp(-|d|^2 / (2 var)), var = (f s / z)^2 + 0.3."""
+    sc = one_gaussian_scene([0.0, 0.0, 0.0], 0.04, logit=1.5)
+    cam = synth.look_at_camera([0.0, 0.0, 3.0], width=64, height=64)
+    light = synth.Light(pos=np.array([0.0, 2.5, 1.0], dtype=np.float32), intensity=10.0)
+    fr = oracle.render(sc, cam, light)
+    assert fr["T"][0] == 1.0
+    var = (cam.fx * float(np.float32(0.04)) / 3.0) ** 2 + 0.3
+    gam = 1 / (1 + math.exp(-1.5))
+    ys, xs = np.mgrid[0:64, 0:64]
+    d2 = (xs + 0.5 - cam.cx) ** 2 + (ys + 0.5 - cam.cy) ** 2
+    alpha = gam * np.exp(-0.5 * d2 / var)
+    c = fr["shade"][0]
+    want = alpha[..., None] ** 2 * c * fr["Tp"][0] + alpha[..., None] * fr["res"][0]
+    rect = fr["cam_rect"][0]
+    inside = (xs // 16 >= rect[0]) & (xs // 16 <= rect[2]) & (ys // 16 >= rect[1]) & (ys // 16 <= rect[3])
+    want = np.where(((alpha >= 1 / 255) & inside)[..., None], want, 0.0)
+    np.testing.assert_allclose(fr["img"], want, rtol=1e-5, atol=1e-9)
+
+
+def test_shadow_two_gaussians_on_light_axis(oracle):
+    """Sec. 4.2: a receiver behind an occluder on the light axis gets
+    sum_m beta_m (1 - alpha_front,m) / sum_m beta_m; within the 0.015 bias it
+    is unshadowed; the front Gaussian is never shadowed."""
+    light = synth.Light(pos=np.array([0.0, 0.0, 3.0], dtype=np.float32), intensity=10.0)
+    cam = synth.look_at_camera([3.0, 0.0, 0.0], width=64, height=64)
+    for sep, shadowed in ((0.2, True), (0.01, False)):
+        sc = one_gaussian_scene([[0.0, 0.0, 1.0], [0.0, 0.0, 1.0 - sep]], [0.05, 0.05, 0.05],
+                                logit=[1.0, 0.5])
+        fr = oracle.render(sc, cam, light)
+        assert fr["T"][0] == 1.0
+        if not shadowed:
+            assert fr["T"][1] == 1.0
+            continue
+        ys, xs = np.mgrid[0:64, 0:64]
+
+        def ab(g):
+            u, v = fr["light_uv"][g]
+            A, B, Cc = fr["light_conic"][g]
+            dx, dy = xs + 0.5 - u, ys + 0.5 - v
+            beta = np.exp(-0.5 * (A * dx * dx + Cc * dy * dy) - B * dx * dy)
+            a = np.minimum(0.99, fr["opacity"][g] * beta)
+            rect = fr["light_rect"][g]
+            inside = (xs // 16 >= rect[0]) & (xs // 16 <= rect[2]) & (ys // 16 >= rect[1]) & (ys // 16 <= rect[3])
+            return beta, a, inside & (a >= 1 / 255)
+
+        b0, a0, ok0 = ab(0)
+        b1, a1, ok1 = ab(1)
+        Tm = np.where(ok0, 1 - a0, 1.0)
+        want = (b1 * Tm)[ok1].sum() / b1[ok1].sum()
+        assert fr["T"][1] == pytest.approx(want, rel=1e-12)
+        assert want < 0.8
+
+
+def test_shadow_opaque_wall(oracle):
+    """Behind two dense layers of near-opaque Gaussians the shadow value
+    falls below 1e-3 (each layer multiplies by at most 1 - alpha)."""
+    g = np.linspace(-0.3, 0.3, 13)
+    xx, yy = np.meshgrid(g, g)
+    wall = []
+    for z in (0.6, 0.55):
+        wall.append(np.stack([xx.ravel(), yy.ravel(), np.full(xx.size, z)], 1))
+    means = np.concatenate(wall + [np.array([[0.0, 0.0, 0.0]])])
+    sc = one_gaussian_scene(means, [0.05, 0.05, 0.05], logit=8.0)
+    light = synth.Light(pos=np.array([0.0, 0.0, 3.0], dtype=np.float32), intensity=10.0)
+    cam = synth.look_at_camera([3.0, 0.0, 0.0], width=64, height=64)
+    fr = oracle.render(sc, cam, light)
+    assert fr["T"][-1] < 1e-3
+    front = fr["T"][:169]
+    assert np.median(front) > 0.9
+
+
+def test_fig3_weighted_average_numerator():
+    """Fig. 3 prints beta = (0.6, 0.3), T_m = (0.4, 0.6) and 'T = 0.42'.  The
+    printed value is the numerator sum beta_m T_m; the formula of Sec. 4.2
+    divides by sum beta_m = 0.9, giving 0.4667.  The oracle follows the
+    formula (known inconsistency in the figure)."""
+    vals = {}
+    with open(os.path.join(GOLDEN, "fig3_shadow_average.txt")) as fh:
+        for line in fh:
+            line = line.split("#")[0].strip()
+            if line:
+                k, v = line.split("=")
+                vals[k.strip()] = [float(x) for x in v.split(",")]
+    beta, T = np.array(vals["beta"]), np.array(vals["T_m"])
+    assert float(beta @ T) == pytest.approx(vals["printed_T"][0], abs=1e-12)
+    assert float(beta @ T / beta.sum()) == pytest.approx(0.42 / 0.9, rel=1e-12)
+
+
+def test_ablation_switches(oracle, small_frame):
+    """Render-time ablations: no shadow splat gives T = 1 for all Gaussians,
+    no Phi gives T' = T, no Psi gives a zero residual."""
+    sc, cam, light, opts, fr = small_frame
+    f1 = oracle.render(sc, cam, light, oracle.Opts(ablate=1))
+    assert np.all(f1["T"] == 1.0)
+    f2 = oracle.render(sc, cam, light, oracle.Opts(ablate=2))
+    np.testing.assert_array_equal(f2["Tp"], f2["T"])
+    f4 = oracle.render(sc, cam, light, oracle.Opts(ablate=4))
+    assert np.all(f4["res"] == 0.0)
+    np.testing.assert_allclose(f4["img"], f4["S"] * f4["Sh"][..., None], rtol=1e-13)
