@@ -1,0 +1,360 @@
+#!/usr/bin/env python
+"""Relit frames/s of the GS^3 frame render on GB300.
+
+Workload (default): 300,000-Gaussian object scene (noisy sphere shell plus
+10 % interior fluff), K = 8 lobes per Gaussian, both MLPs 3x128, 800x800
+image; one step = one full relit frame (shading, shadow splat, Phi, Psi,
+camera splat) for the next of 100 seeded camera / point-light pairs on the
+radius-3 sphere.  Inputs are synthetic and resident in HBM; L2 is flushed
+(256 MB write) between steps, outside the timed events.
+
+Prints ONE JSON line (rank 0).  Under torchrun every rank renders its own
+frames (independent replicas, no collective on the data path) and the
+reported value is all frames / the slowest rank's time.
+
+--impl reference times the FP64 CPU oracle on the host cores instead (a
+bounded window of each frame, scaled to a whole frame).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "relit frames/s at 800x800, 300k Gaussians (BF16 served vs FP32 plain); p50/p99 ms; % roofline"
+UNIT = "frames/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gs3", choices=["gs3", "reference"])
+    ap.add_argument("--n", type=int, default=300_000)
+    ap.add_argument("--res", type=int, default=800)
+    ap.add_argument("--mlp", default="fp32", choices=["fp32", "bf16"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-window", type=int, default=96, help="oracle window edge (pixels)")
+    return ap.parse_args()
+
+
+def workload_config(a, mlp):
+    return {"workload": f"object scene, {a.n} Gaussians, K=8, Phi/Psi 3x128 {mlp.upper()}, "
+                        f"{a.res}x{a.res}, point light, 100 seeded camera/light pairs",
+            "n_gaussians": a.n, "lobes": 8, "mlp": f"3x128 {mlp}", "image": [a.res, a.res],
+            "pairs": 100, "l2": "flushed between steps (256 MB write), outside the timed events",
+            "parallelism": f"replicas x{a.gpus}"}
+
+
+# ---------------------------------------------------------------------------
+# clocks
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (baseline leg and --impl reference)
+# ---------------------------------------------------------------------------
+def oracle_frame_seconds(scene, pair_seed, res, window):
+    """Oracle time for one frame: every per-Gaussian stage in full, both
+    composites over a centred window of window^2 pixels, composite time scaled
+    by the pixel ratio."""
+    from oracle import oracle as O
+    from paper_2410_11419_gb300 import synth
+    cam, light = synth.camera_light_pair(pair_seed, res, res)
+    c0 = (res - window) // 2
+    fr = O.render(scene, cam, light, O.Opts(crop=(c0, c0, c0 + window, c0 + window)))
+    t = fr["times"]
+    scale = (res * res) / float(window * window)
+    return t["prep"] + t["bin"] + t["mlp"] + scale * (t["shadow"] + t["camera"]), t
+
+
+def cpu_baseline(a, scene):
+    from oracle import oracle as O
+    O.build()
+    secs, t = oracle_frame_seconds(scene, 0, a.res, a.cpu_window)
+    return {"value": 1.0 / secs, "unit": UNIT, "cores": O.max_threads(), "kind": "oracle",
+            "sample": (f"1 frame (pair 0): FP64 oracle prep, binning and MLPs over all {a.n} "
+                       f"Gaussians; shadow and camera composites over a centred "
+                       f"{a.cpu_window}x{a.cpu_window} window, scaled x{(a.res / a.cpu_window) ** 2:.1f} "
+                       f"to the full {a.res}x{a.res} frame"),
+            "stage_s": {k: round(v, 4) for k, v in t.items()}}
+
+
+def run_reference(a):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    from paper_2410_11419_gb300 import synth
+    O.build()
+    scene = synth.object_scene(0, n=a.n)
+    times = []
+    for i in range(a.warmup + a.steps):
+        s, _ = oracle_frame_seconds(scene, i % 100, a.res, a.cpu_window)
+        if i >= a.warmup:
+            times.append(s)
+    tot = sum(times)
+    v = a.steps / tot
+    sample = (f"per step one frame: FP64 oracle over all {a.n} Gaussians, composites over a "
+              f"{a.cpu_window}x{a.cpu_window} window scaled to {a.res}x{a.res}")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": a.gpus,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * tot / a.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": workload_config(a, "fp64"),
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": O.max_threads(), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def main():
+    a = parse()
+    if a.impl == "reference":
+        return run_reference(a)
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    import __graft_entry__ as ge
+    ge.build()
+    from paper_2410_11419_gb300 import _native as N, render as R, synth
+
+    scene = synth.object_scene(0, n=a.n)
+    pairs = [synth.camera_light_pair(i, a.res, a.res) for i in range(100)]
+    mlp_dtype = N.GS3_MLP_BF16 if a.mlp == "bf16" else N.GS3_MLP_FP32
+    ds = R.DeviceScene(scene, device=dev, mlp_dtype=mlp_dtype)
+    cap = 40_000_000 if a.n <= 300_000 else int(a.n * 140)
+    rd = R.Renderer(ds, a.res, a.res, cap, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    groups = [("prep", N.GS3_STAGE_PREP), ("camera_bin", N.GS3_STAGE_CAMERA_BIN),
+              ("light_bin", N.GS3_STAGE_LIGHT_BIN), ("shadow_composite", N.GS3_STAGE_SHADOW_COMPOSITE),
+              ("shadow_reduce", N.GS3_STAGE_SHADOW_REDUCE), ("mlp", N.GS3_STAGE_MLP),
+              ("camera_composite", N.GS3_STAGE_CAMERA)]
+    opts = R.opts_struct()
+    ntiles = ((a.res + 15) // 16) ** 2
+
+    def frame(i, evs=None):
+        cam, light = pairs[i % 100]
+        if evs is None:
+            rd.render(cam, light, opts)
+            return
+        evs[0].record(stream)
+        for j, (_, st) in enumerate(groups):
+            rd.render_stages(cam, light, st, opts)
+            evs[j + 1].record(stream)
+
+    # warm-up (also checks the workspace capacity)
+    for i in range(max(a.warmup, 3)):
+        frame(i)
+    torch.cuda.synchronize()
+    rd.check()
+
+    K = a.steps
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(len(groups) + 1)] for _ in range(K)]
+    ts_host = torch.empty((K, 2, ntiles + 1), dtype=torch.int32, pin_memory=True)
+    nc_host = torch.empty((K, a.res * a.res), dtype=torch.int32, pin_memory=True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    launches0 = N.gs3_kernel_launches()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for s in range(K):
+        flush.zero_()
+        frame(a.warmup + s, evs[s])
+        ts_host[s, 0].copy_(rd.stage("tile_start", 0), non_blocking=True)
+        ts_host[s, 1].copy_(rd.stage("tile_start", 1), non_blocking=True)
+        nc_host[s].copy_(rd.stage("n_contrib").view(-1), non_blocking=True)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    if world > 1:
+        dist.barrier()
+    launches = N.gs3_kernel_launches() - launches0
+    clk = clocks.stop()
+    rd.check()
+
+    step_ms = np.array([evs[s][0].elapsed_time(evs[s][-1]) for s in range(K)])
+    stage_ms = {nm: float(np.mean([evs[s][j].elapsed_time(evs[s][j + 1]) for s in range(K)]))
+                for j, (nm, _) in enumerate(groups)}
+    total_ms = float(step_ms.sum())
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * K / (total_ms / 1e3)
+
+    # ---- end to end through the public API with host buffers ----
+    host_img = torch.empty((a.res, a.res, 3), dtype=torch.float32, pin_memory=True)
+    cam_b = len(bytes(R.camera_struct(pairs[0][0]))) + len(bytes(R.light_struct(pairs[0][1])))
+    torch.cuda.synchronize()
+    e0 = time.perf_counter()
+    for s in range(K):
+        img = rd.render(*pairs[(a.warmup + s) % 100], opts)
+        host_img.copy_(img, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+    e2e_s = time.perf_counter() - e0
+    e2e_val = world * K / e2e_s if world == 1 else None
+    if world > 1:
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_val = world * K / float(t.item())
+
+    # ---- roofline of the dominant kernel ----
+    ts = ts_host.numpy().astype(np.int64)
+    gx = (a.res + 15) // 16
+    tile_pix = np.full(ntiles, 256, dtype=np.int64)  # 800 = 50 x 16: full tiles
+    if a.res % 16:
+        tx = np.arange(ntiles) % gx
+        ty = np.arange(ntiles) // gx
+        wpx = np.minimum(16, a.res - 16 * tx)
+        wpy = np.minimum(16, a.res - 16 * ty)
+        tile_pix = wpx * wpy
+    light_pairs_evals = [(np.diff(ts[s, 1]) * tile_pix).sum() for s in range(K)]
+    cam_evals = [int(nc_host[s].numpy().astype(np.int64).sum()) for s in range(K)]
+    per_step_light_P = [int(ts[s, 1, -1]) for s in range(K)]
+    per_step_cam_P = [int(ts[s, 0, -1]) for s in range(K)]
+    dominant = max(stage_ms, key=stage_ms.get)
+    sm_max = clk.get("sm_max_mhz") or 2070.0
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    fp32_peak_tflops = n_sm * 128 * 2 * sm_max * 1e6 / 1e12
+    FLOP_PER_EVAL = 12.0
+    roof = None
+    if dominant == "shadow_composite":
+        achieved = FLOP_PER_EVAL * float(np.mean(light_pairs_evals)) / (stage_ms[dominant] / 1e3) / 1e12
+        roof = {"kernel": "k_shadow", "bound": "alu", "achieved": achieved, "peak": fp32_peak_tflops,
+                "unit": "TFLOP/s", "frac": achieved / fp32_peak_tflops, "traffic": None,
+                "work": f"{FLOP_PER_EVAL:.0f} FLOP x (light pixel, list entry) pairs "
+                        f"({float(np.mean(light_pairs_evals)):.3e} per frame)",
+                "peak_source": f"derived: {n_sm} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz"}
+    elif dominant == "camera_composite":
+        achieved = 20.0 * float(np.mean(cam_evals)) / (stage_ms[dominant] / 1e3) / 1e12
+        roof = {"kernel": "k_camera", "bound": "alu", "achieved": achieved, "peak": fp32_peak_tflops,
+                "unit": "TFLOP/s", "frac": achieved / fp32_peak_tflops, "traffic": None,
+                "work": "20 FLOP x entries consumed per pixel",
+                "peak_source": f"derived: {n_sm} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz"}
+    elif dominant == "mlp":
+        flops = 2.0 * a.n * (61 * 128 + 2 * 128 * 128 + 128 + 60 * 128 + 2 * 128 * 128 + 3 * 128)
+        achieved = flops / (stage_ms[dominant] / 1e3) / 1e12
+        roof = {"kernel": "k_mlp", "bound": "alu", "achieved": achieved, "peak": fp32_peak_tflops,
+                "unit": "TFLOP/s", "frac": achieved / fp32_peak_tflops, "traffic": None,
+                "work": "2 x N x sum(in x out) of both MLPs",
+                "peak_source": f"derived: {n_sm} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz"}
+    else:
+        P = float(np.mean(per_step_light_P if dominant == "light_bin" else per_step_cam_P))
+        byts = P * 8 * 2 + a.n * 48 * 2
+        achieved = byts / (stage_ms[dominant] / 1e3) / 1e9
+        peak = 6796.5
+        try:
+            peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]
+        except Exception:
+            pass
+        roof = {"kernel": dominant, "bound": "hbm", "achieved": achieved, "peak": peak,
+                "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                "work": "pairs written + read once (8 B each) + records"}
+
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+        "warmup": a.warmup, "ms_per_step": total_ms / K, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if a.mlp == "fp32" else "bf16+f32",
+        "data": "synthetic (seeded object scene, random-init MLPs)",
+        "config": workload_config(a, a.mlp),
+        "p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99)),
+        "stages_ms": {k: round(v, 4) for k, v in stage_ms.items()},
+        "pairs_per_frame": {"camera": float(np.mean(per_step_cam_P)),
+                            "light": float(np.mean(per_step_light_P))},
+        "roofline": roof,
+        "clocks": clk,
+        "gpu_launches": int(launches),
+        "wall_s_timed_region": wall,
+        "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": cam_b,
+                "d2h_bytes_per_step": a.res * a.res * 3 * 4,
+                "note": "gs3_render through the C ABI, camera/light host structs in, image copied "
+                        "to pinned host memory and synchronised every step"},
+    }
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(a, scene)
+    if rank == 0:
+        print(json.dumps(out))
+    ds.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,218 @@
+/*
+ * gs3.h -- C ABI of the GB300 (sm_103a) GS^3 triple-splatting renderer.
+ *
+ * GS^3 (Bi et al., SIGGRAPH Asia 2024) renders a relit image of a set of
+ * spatial Gaussians for one camera and one point light (Sec. 4, Sec. 4.5):
+ *   1. colour every Gaussian with a Lambertian plus a mixture of angular
+ *      Gaussian lobes (Sec. 4.1, Eq. 2-5);
+ *   2. splat all Gaussians toward the light and alpha-composite every shadow
+ *      ray front to back to get one shadow value per Gaussian (Sec. 4.2,
+ *      Fig. 3), refined by the MLP Phi;
+ *   3. colour every Gaussian with the residual MLP Psi (Sec. 4.3);
+ *   4. splat shading, shadow and residual toward the camera (Sec. 3, Eq. 2)
+ *      and combine them per pixel: shading * shadow + residual (Sec. 4).
+ *
+ * Conventions for every entry point:
+ *   - Pointers documented as "device" are CUDA device pointers on the current
+ *     device; "host" pointers are ordinary CPU memory.
+ *   - The library never frees caller memory and never keeps a caller pointer
+ *     beyond the call, except the scene parameter pointers captured by
+ *     gs3_create_scene, which must stay valid until gs3_destroy_scene.
+ *   - Work is enqueued on the caller's CUDA stream (`stream`, a cudaStream_t
+ *     passed as void*; NULL is the legacy default stream) and is asynchronous
+ *     unless stated otherwise.
+ *   - Errors are returned as gs3_status; no exception or abort crosses the
+ *     ABI.  gs3_last_error() gives a thread-local message for the last error.
+ *   - Errors found on the device (key capacity exceeded, a bounded wait that
+ *     ran out) are written to a status word in the workspace and read back by
+ *     gs3_workspace_read_header after the stream has been synchronised.
+ */
+#ifndef GS3_H
+#define GS3_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    GS3_OK = 0,
+    GS3_ERR_INVALID_ARG = 1, /* a size, pointer or option is out of range */
+    GS3_ERR_OOM = 2,         /* a scene-owned allocation failed */
+    GS3_ERR_CAPACITY = 3,    /* more (tile, Gaussian) pairs than key_capacity */
+    GS3_ERR_CUDA = 4,        /* a CUDA runtime call failed (message in gs3_last_error) */
+    GS3_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up */
+    GS3_ERR_UNSUPPORTED = 6  /* valid request the library does not implement */
+} gs3_status;
+
+enum { GS3_ACT_RELU = 0, GS3_ACT_LEAKY_RELU = 1 };         /* hidden-layer activation */
+enum { GS3_MLP_FP32 = 0, GS3_MLP_BF16 = 1 };               /* MLP operand precision */
+enum { GS3_ABLATE_SHADOW_SPLAT = 1, GS3_ABLATE_PHI = 2, GS3_ABLATE_PSI = 4 };
+
+/* Fully connected network in_dim -> [width] x n_hidden -> out_dim with a
+ * sigmoid output (Sec. 4.2: Phi, Sec. 4.3: Psi).
+ *   w: device, float32, every layer's (out, in) row-major matrix, concatenated
+ *   b: device, float32, every layer's bias, concatenated
+ * Supported: in_dim = 61 (Phi) / 60 (Psi), out_dim = 1 (Phi) / 3 (Psi),
+ * 1 <= n_hidden <= 4, width in {16, 32, 64, 128}. */
+typedef struct {
+    int32_t in_dim, width, n_hidden, out_dim, act;
+    const float *w;
+    const float *b;
+} gs3_mlp_desc;
+
+/* Scene parameters: structure of arrays, every array float4-padded, device,
+ * float32, borrowed (the caller keeps them alive until gs3_destroy_scene).
+ *   mean_op[N]    (x, y, z, opacity logit); opacity = sigmoid(logit)   Eq. 1-2
+ *   scale[N]      (sx, sy, sz, -) positive; Sigma = R S S^T R^T        Eq. 1
+ *   rot[N]        (w, x, y, z) quaternion of R (normalised inside)     Eq. 1
+ *   shade_rot[N]  (w, x, y, z) world -> shading frame [t, b, n]; the normal
+ *                 n' is the frame's z axis                             Sec. 4.1
+ *   albedo_d[N], albedo_s[N]  (rgb, -) rho_d, rho_s                    Eq. 2
+ *   latent[2N]    latent[g] = (l0..l3), latent[N+g] = (l4, l5, -, -)   Sec. 4.2
+ *   lobe_rot[K*N]   (w, x, y, z) lobe frame [x, y, z] in the shading frame,
+ *                   lobe-major: lobe j of Gaussian g at j*N + g          Eq. 5
+ *   lobe_sigma[K*N] (sigma_x, sigma_y, sigma_z, -)                       Eq. 5
+ *   lobe_amp[K*N]   (alpha_j rgb, -) lobe weights                        Eq. 4
+ * 1 <= N, 0 <= K <= 16. */
+typedef struct {
+    int32_t n, k;
+    const float *mean_op, *scale, *rot, *shade_rot, *albedo_d, *albedo_s, *latent;
+    const float *lobe_rot, *lobe_sigma, *lobe_amp;
+    gs3_mlp_desc phi, psi;
+    int32_t mlp_dtype; /* GS3_MLP_FP32 or GS3_MLP_BF16 (tensor cores, FP32 accumulate) */
+} gs3_scene_desc;
+
+/* Pinhole camera, host struct.  R: world -> camera rotation rows (x right,
+ * y down, z forward); t: translation (p_cam = R p + t); pos: camera centre
+ * in world space; fx, fy, cx, cy in pixels; pixel (x, y) has its centre at
+ * (x + 0.5, y + 0.5).  The shadow splat's light camera uses the same
+ * intrinsics and resolution (Sec. 4.2). */
+typedef struct {
+    float R[9], t[3], pos[3];
+    float fx, fy, cx, cy;
+    int32_t width, height;
+} gs3_camera;
+
+/* Point light (Sec. 4.2), host struct. */
+typedef struct {
+    float pos[3];
+    float intensity;
+} gs3_light;
+
+/* Render options, host struct; gs3_default_opts fills the paper's values:
+ *   shadow_bias 0.015 (Sec. 4.2), alpha_min 1/255, alpha_max 0.99,
+ *   t_stop 1e-4, near_z 0.2, lowpass 0.3 px^2, frustum 1.3, tile 16,
+ *   target (0,0,0) = point the light camera looks at, falloff 1 (irradiance
+ *   I / d^2), ablate 0 (bits GS3_ABLATE_*). */
+typedef struct {
+    float near_z, lowpass, frustum, shadow_bias, alpha_min, alpha_max, t_stop;
+    float target[3];
+    int32_t falloff, tile, ablate;
+} gs3_render_opts;
+
+typedef struct gs3_scene gs3_scene;
+
+/* Device status word and pair counts at the start of every workspace. */
+typedef struct {
+    uint32_t status;      /* GS3_OK, or the first device-side error */
+    uint32_t pairs_cam;   /* (tile, Gaussian) pairs of the camera splat */
+    uint32_t pairs_light; /* (tile, Gaussian) pairs of the shadow splat */
+    uint32_t pairs_cam_needed, pairs_light_needed; /* before clamping to the capacity */
+    uint32_t reserved[3];
+    float light_R[9], light_t[3]; /* light camera used by the shadow splat */
+} gs3_ws_header;
+
+/* Byte offsets of the named intermediate buffers inside a workspace (for
+ * inspection and tests).  Per-splat arrays are indexed [0] camera, [1] light. */
+typedef struct {
+    size_t total;
+    size_t header;
+    size_t key[2];        /* uint32[N] FP32 depth / light-distance bits by Gaussian */
+    size_t order[2];      /* uint32[N] Gaussian index of depth rank r */
+    size_t tile_start[2]; /* uint32[tiles + 1] per-tile range into the sorted list */
+    size_t list[2];       /* uint32[capacity] sorted list: depth rank per entry */
+    size_t rect[2];       /* int4[N] tile rectangle x0, y0, x1, y1 by Gaussian (x0 < 0: culled) */
+    size_t shade;         /* float4[N] shading colour rgb by Gaussian */
+    size_t shadow;        /* float[N] shadow value T by Gaussian */
+    size_t shadow_refined;/* float[N] T' = Phi(...) by Gaussian */
+    size_t residual;      /* float4[N] Psi(...) rgb by Gaussian */
+    size_t final_t;       /* float[H*W] transmittance left after the camera ray */
+    size_t n_contrib;     /* uint32[H*W] list entries consumed by the camera ray */
+} gs3_ws_layout;
+
+/* Fill `o` with the paper's defaults (see gs3_render_opts). */
+void gs3_default_opts(gs3_render_opts *o);
+
+/* Validate `desc` and create a scene.  The scene borrows the parameter and
+ * weight pointers and owns derived buffers (packed / BF16 MLP weights).
+ * Errors: INVALID_ARG (sizes, NULL pointers, unsupported MLP shape), OOM. */
+gs3_status gs3_create_scene(const gs3_scene_desc *desc, gs3_scene **out);
+
+/* Release a scene; waits for nothing (the caller synchronises first). */
+gs3_status gs3_destroy_scene(gs3_scene *scene);
+
+/* Bytes of workspace one render of an n-Gaussian scene at width x height
+ * needs when at most key_capacity (tile, Gaussian) pairs per splat fit. */
+size_t gs3_workspace_size(int32_t n, int32_t width, int32_t height, size_t key_capacity);
+
+/* Offsets of the workspace buffers for the same arguments. */
+gs3_status gs3_workspace_layout(int32_t n, int32_t width, int32_t height, size_t key_capacity,
+                                gs3_ws_layout *out);
+
+/* Render one relit frame (Sec. 4, Sec. 4.5): shading, shadow splat, Phi, Psi,
+ * camera splat and the per-pixel combination.
+ *   out_rgb:   device, float32 [height][width][3], caller-owned, overwritten
+ *   workspace: device, >= gs3_workspace_size(n, w, h, key_capacity) bytes,
+ *              256-byte aligned, caller-owned; holds every intermediate and
+ *              the status header.  Calls that overlap on the GPU must use
+ *              different workspaces.
+ *   stream:    cudaStream_t (void*)
+ * Asynchronous.  Host-detectable errors (INVALID_ARG, CUDA launch errors) are
+ * returned; a capacity overflow is reported in the workspace header (status
+ * GS3_ERR_CAPACITY, the image is then undefined) and is read with
+ * gs3_workspace_read_header after the work completes. */
+gs3_status gs3_render(gs3_scene *scene, const gs3_camera *camera, const gs3_light *light,
+                      const gs3_render_opts *opts, float *out_rgb, void *workspace,
+                      size_t workspace_bytes, size_t key_capacity, void *stream);
+
+/* Stage bits of gs3_render_stages (in pipeline order). */
+enum {
+    GS3_STAGE_PREP = 1,             /* K1: shading colour, both projections, keys */
+    GS3_STAGE_CAMERA_BIN = 2,       /* camera splat: depth sort, pairs, tile sort, ranges */
+    GS3_STAGE_LIGHT_BIN = 4,        /* light splat: the same toward the light */
+    GS3_STAGE_SHADOW_COMPOSITE = 8, /* shadow rays: biased transmittance, partial sums (Sec. 4.2) */
+    GS3_STAGE_SHADOW_REDUCE = 16,   /* per-Gaussian beta-weighted average (Sec. 4.2) */
+    GS3_STAGE_MLP = 32,             /* Phi and Psi (Sec. 4.2, 4.3) */
+    GS3_STAGE_CAMERA = 64,          /* camera composite and combination (Eq. 2, Sec. 4) */
+    GS3_STAGE_ALL = 127
+};
+
+/* Run only the selected stages of gs3_render on `workspace`, in pipeline
+ * order.  Each stage reads what the earlier stages left in the same
+ * workspace, so a frame split into several calls (same scene, camera, light,
+ * options and workspace, stages in order, header reset by the call that
+ * includes GS3_STAGE_PREP) equals one gs3_render.  Used to time stages with
+ * events recorded on `stream` between the calls.  Errors as gs3_render. */
+gs3_status gs3_render_stages(gs3_scene *scene, const gs3_camera *camera, const gs3_light *light,
+                             const gs3_render_opts *opts, float *out_rgb, void *workspace,
+                             size_t workspace_bytes, size_t key_capacity, uint32_t stages,
+                             void *stream);
+
+/* Copy the workspace header to `out` (host) and synchronise `stream`. */
+gs3_status gs3_workspace_read_header(const void *workspace, gs3_ws_header *out, void *stream);
+
+/* Number of CUDA kernels this library has launched in this process (all
+ * threads, all devices); a host-side counter for launch accounting. */
+uint64_t gs3_kernel_launches(void);
+
+/* Message of the last error on the calling thread ("" if none). */
+const char *gs3_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GS3_H */

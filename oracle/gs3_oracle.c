@@ -56,7 +56,16 @@
 #include <omp.h>
 #endif
 
+#include <time.h>
+
 #define GO_PI 3.14159265358979323846
+
+static double now_s(void)
+{
+    struct timespec ts;
+    clock_gettime(CLOCK_MONOTONIC, &ts);
+    return ts.tv_sec + 1e-9 * ts.tv_nsec;
+}
 
 /* ------------------------------------------------------------------------ */
 /* Public structures (mirrored by oracle.py through ctypes).                 */
@@ -91,6 +100,7 @@ typedef struct {
     int falloff, tile, ablate; /* ablate bits: 1 no shadow splat, 2 no Phi, 4 no Psi */
     int threads;
     double margin_alpha, margin_tstop;
+    int crop[4]; /* x0, y0, x1, y1 (exclusive) pixel window of both composites; all 0 = full */
 } go_opts;
 
 typedef struct {
@@ -119,7 +129,20 @@ typedef struct {
     double *S, *Sh, *Rimg; /* composited shading (3), shadow (1), residual (3) images */
     int64_t shadow_evals, shadow_pass, camera_evals;
     int64_t amb_shadow, amb_camera;
+    double t_prep, t_bin, t_shadow, t_mlp, t_camera; /* wall seconds per stage */
 } go_frame;
+
+/* pixel window of the composites (the whole image unless a crop is set) */
+static void window(const go_opts *o, int W, int H, int *x0, int *y0, int *x1, int *y1)
+{
+    *x0 = 0; *y0 = 0; *x1 = W; *y1 = H;
+    if (o->crop[2] > o->crop[0] && o->crop[3] > o->crop[1]) {
+        *x0 = o->crop[0] < 0 ? 0 : o->crop[0];
+        *y0 = o->crop[1] < 0 ? 0 : o->crop[1];
+        *x1 = o->crop[2] > W ? W : o->crop[2];
+        *y1 = o->crop[3] > H ? H : o->crop[3];
+    }
+}
 
 /* ------------------------------------------------------------------------ */
 /* FP32 key recipe.  Every operation below is one IEEE binary32 operation;   */
@@ -523,11 +546,13 @@ static void shadow_splat(go_frame *f, const go_opts *o)
         uint32_t *gi = malloc(sizeof(uint32_t) * cap);
         int *amb = malloc(sizeof(int) * cap);
         int *pass = malloc(sizeof(int) * cap);
+        int wx0, wy0, wx1, wy1;
+        window(o, W, H, &wx0, &wy0, &wx1, &wy1);
 #ifdef _OPENMP
 #pragma omp for schedule(dynamic, 4)
 #endif
-        for (int py = 0; py < H; ++py) {
-            for (int px = 0; px < W; ++px) {
+        for (int py = wy0; py < wy1; ++py) {
+            for (int px = wx0; px < wx1; ++px) {
                 int t = (py / ts) * f->gx + (px / ts);
                 uint32_t b = f->tile_start[1][t], e = f->tile_start[1][t + 1];
                 size_t L = e - b;
@@ -621,11 +646,20 @@ static void camera_composite(go_frame *f, const go_opts *o)
 {
     int W = f->width, H = f->height, ts = o->tile;
     int64_t evals = 0, ambs = 0;
+    int wx0, wy0, wx1, wy1;
+    window(o, W, H, &wx0, &wy0, &wx1, &wy1);
+    for (size_t p = 0; p < (size_t)W * H; ++p) { /* outside the window: empty */
+        f->final_T[p] = 1.0; f->n_contrib[p] = 0; f->Sh[p] = 0.0;
+        for (int c = 0; c < 3; ++c) {
+            f->S[3 * p + c] = 0.0; f->Rimg[3 * p + c] = 0.0; f->img[3 * p + c] = 0.0;
+            f->img_bound[3 * p + c] = 0.0;
+        }
+    }
 #ifdef _OPENMP
 #pragma omp parallel for schedule(dynamic, 4) reduction(+ : evals, ambs)
 #endif
-    for (int py = 0; py < H; ++py) {
-        for (int px = 0; px < W; ++px) {
+    for (int py = wy0; py < wy1; ++py) {
+        for (int px = wx0; px < wx1; ++px) {
             int t = (py / ts) * f->gx + (px / ts);
             uint32_t b = f->tile_start[0][t], e = f->tile_start[0][t + 1];
             double cxp = px + 0.5, cyp = py + 0.5;
@@ -741,6 +775,7 @@ go_frame *go_render(const go_scene *sc, const go_camera *cam, const go_light *L,
     f->Sh = malloc(sizeof(double) * np);
     f->Rimg = malloc(sizeof(double) * 3 * np);
 
+    double t0 = now_s();
     d3 *wi = malloc(sizeof(d3) * n), *wo = malloc(sizeof(d3) * n);
 #ifdef _OPENMP
 #pragma omp parallel for schedule(static)
@@ -765,14 +800,17 @@ go_frame *go_render(const go_scene *sc, const go_camera *cam, const go_light *L,
         }
         shade_one(sc, g, cam, L, o, f->shade + 3 * g, wi + g, wo + g);
     }
+    double t1 = now_s();
     build_lists(f, 0);
     build_lists(f, 1);
+    double t2 = now_s();
 
     if (o->ablate & 1) {
         for (int g = 0; g < n; ++g) f->T[g] = 1.0;
     } else {
         shadow_splat(f, o);
     }
+    double t3 = now_s();
 
     /* Phi and Psi per Gaussian (Sec. 4.2, 4.3) */
 #ifdef _OPENMP
@@ -807,7 +845,11 @@ go_frame *go_render(const go_scene *sc, const go_camera *cam, const go_light *L,
     }
     free(wi);
     free(wo);
+    double t4 = now_s();
     camera_composite(f, o);
+    double t5 = now_s();
+    f->t_prep = t1 - t0; f->t_bin = t2 - t1; f->t_shadow = t3 - t2; f->t_mlp = t4 - t3;
+    f->t_camera = t5 - t4;
     return f;
 }
 
@@ -822,6 +864,16 @@ void go_frame_free(go_frame *f)
     free(f->Tp_bound); free(f->res); free(f->img); free(f->img_bound); free(f->final_T);
     free(f->n_contrib); free(f->S); free(f->Sh); free(f->Rimg);
     free(f);
+}
+
+/* Threads the oracle's parallel loops use. */
+int go_max_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
 }
 
 /* Shading of one Gaussian (for closed-form pins). */

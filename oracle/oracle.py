@@ -62,7 +62,8 @@ class _Opts(C.Structure):
                 ("shadow_bias", C.c_float), ("alpha_min", C.c_float), ("alpha_max", C.c_float),
                 ("t_stop", C.c_float), ("target", C.c_float * 3), ("falloff", C.c_int),
                 ("tile", C.c_int), ("ablate", C.c_int), ("threads", C.c_int),
-                ("margin_alpha", C.c_double), ("margin_tstop", C.c_double)]
+                ("margin_alpha", C.c_double), ("margin_tstop", C.c_double),
+                ("crop", C.c_int * 4)]
 
 
 _U32 = C.POINTER(C.c_uint32)
@@ -82,7 +83,8 @@ class _Frame(C.Structure):
                 ("n_contrib", _I32), ("S", _D), ("Sh", _D), ("Rimg", _D),
                 ("shadow_evals", C.c_int64), ("shadow_pass", C.c_int64),
                 ("camera_evals", C.c_int64), ("amb_shadow", C.c_int64),
-                ("amb_camera", C.c_int64)]
+                ("amb_camera", C.c_int64), ("t_prep", C.c_double), ("t_bin", C.c_double),
+                ("t_shadow", C.c_double), ("t_mlp", C.c_double), ("t_camera", C.c_double)]
 
 
 _lib = None
@@ -112,6 +114,7 @@ def lib():
         _lib.go_pos_enc.restype = C.c_int
         _lib.go_pos_enc.argtypes = [_D, _D]
         _lib.go_light_view.argtypes = [_FP, _FP, _FP, _FP]
+        _lib.go_max_threads.restype = C.c_int
     return _lib
 
 
@@ -132,6 +135,7 @@ class Opts:
     threads: int = 0
     margin_alpha: float = 1e-5
     margin_tstop: float = 1e-4
+    crop: tuple = (0, 0, 0, 0)
 
     def c(self) -> _Opts:
         o = _Opts()
@@ -139,6 +143,8 @@ class Opts:
             v = getattr(self, f)
             if f == "target":
                 o.target = (C.c_float * 3)(*v)
+            elif f == "crop":
+                o.crop = (C.c_int * 4)(*v)
             else:
                 setattr(o, f, v)
         return o
@@ -230,9 +236,15 @@ def render(scene, cam, light, opts: Opts | None = None) -> dict:
         R=_arr(f.Rimg, 3 * np_, np.float64).reshape(H, W, 3),
         shadow_evals=f.shadow_evals, shadow_pass=f.shadow_pass, camera_evals=f.camera_evals,
         amb_shadow=f.amb_shadow, amb_camera=f.amb_camera,
+        times={"prep": f.t_prep, "bin": f.t_bin, "shadow": f.t_shadow, "mlp": f.t_mlp,
+               "camera": f.t_camera},
     )
     lib().go_frame_free(fp)
     return out
+
+
+def max_threads() -> int:
+    return int(lib().go_max_threads())
 
 
 def diffuse(x: float) -> float:

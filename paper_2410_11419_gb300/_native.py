@@ -1,0 +1,190 @@
+"""ctypes binding of libgs3 (include/gs3.h): argument marshalling only.
+
+Every function here has the name of the C entry point it calls.  Device
+buffers are passed as torch CUDA tensors (their data pointers); camera,
+light and options as the ctypes structures below.  There is no CPU fallback:
+if libgs3.so is missing or a call fails, an exception is raised.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libgs3.so")
+
+GS3_OK, GS3_ERR_INVALID_ARG, GS3_ERR_OOM, GS3_ERR_CAPACITY, GS3_ERR_CUDA, GS3_ERR_TIMEOUT, \
+    GS3_ERR_UNSUPPORTED = range(7)
+GS3_ACT_RELU, GS3_ACT_LEAKY_RELU = 0, 1
+GS3_MLP_FP32, GS3_MLP_BF16 = 0, 1
+GS3_ABLATE_SHADOW_SPLAT, GS3_ABLATE_PHI, GS3_ABLATE_PSI = 1, 2, 4
+GS3_STAGE_PREP, GS3_STAGE_CAMERA_BIN, GS3_STAGE_LIGHT_BIN, GS3_STAGE_SHADOW_COMPOSITE, \
+    GS3_STAGE_SHADOW_REDUCE, GS3_STAGE_MLP, GS3_STAGE_CAMERA, GS3_STAGE_ALL = 1, 2, 4, 8, 16, 32, 64, 127
+
+STATUS_NAMES = {0: "GS3_OK", 1: "GS3_ERR_INVALID_ARG", 2: "GS3_ERR_OOM", 3: "GS3_ERR_CAPACITY",
+                4: "GS3_ERR_CUDA", 5: "GS3_ERR_TIMEOUT", 6: "GS3_ERR_UNSUPPORTED"}
+
+
+class GS3Error(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+_FP = C.POINTER(C.c_float)
+
+
+class gs3_mlp_desc(C.Structure):
+    _fields_ = [("in_dim", C.c_int32), ("width", C.c_int32), ("n_hidden", C.c_int32),
+                ("out_dim", C.c_int32), ("act", C.c_int32), ("w", C.c_void_p), ("b", C.c_void_p)]
+
+
+class gs3_scene_desc(C.Structure):
+    _fields_ = [("n", C.c_int32), ("k", C.c_int32)] + [
+        (a, C.c_void_p) for a in ("mean_op", "scale", "rot", "shade_rot", "albedo_d", "albedo_s",
+                                  "latent", "lobe_rot", "lobe_sigma", "lobe_amp")] + [
+        ("phi", gs3_mlp_desc), ("psi", gs3_mlp_desc), ("mlp_dtype", C.c_int32)]
+
+
+class gs3_camera(C.Structure):
+    _fields_ = [("R", C.c_float * 9), ("t", C.c_float * 3), ("pos", C.c_float * 3),
+                ("fx", C.c_float), ("fy", C.c_float), ("cx", C.c_float), ("cy", C.c_float),
+                ("width", C.c_int32), ("height", C.c_int32)]
+
+
+class gs3_light(C.Structure):
+    _fields_ = [("pos", C.c_float * 3), ("intensity", C.c_float)]
+
+
+class gs3_render_opts(C.Structure):
+    _fields_ = [("near_z", C.c_float), ("lowpass", C.c_float), ("frustum", C.c_float),
+                ("shadow_bias", C.c_float), ("alpha_min", C.c_float), ("alpha_max", C.c_float),
+                ("t_stop", C.c_float), ("target", C.c_float * 3), ("falloff", C.c_int32),
+                ("tile", C.c_int32), ("ablate", C.c_int32)]
+
+
+class gs3_ws_header(C.Structure):
+    _fields_ = [("status", C.c_uint32), ("pairs_cam", C.c_uint32), ("pairs_light", C.c_uint32),
+                ("pairs_cam_needed", C.c_uint32), ("pairs_light_needed", C.c_uint32),
+                ("reserved", C.c_uint32 * 3), ("light_R", C.c_float * 9), ("light_t", C.c_float * 3)]
+
+
+class gs3_ws_layout(C.Structure):
+    _fields_ = [("total", C.c_size_t), ("header", C.c_size_t), ("key", C.c_size_t * 2),
+                ("order", C.c_size_t * 2), ("tile_start", C.c_size_t * 2), ("list", C.c_size_t * 2),
+                ("rect", C.c_size_t * 2), ("shade", C.c_size_t), ("shadow", C.c_size_t),
+                ("shadow_refined", C.c_size_t), ("residual", C.c_size_t), ("final_t", C.c_size_t),
+                ("n_contrib", C.c_size_t)]
+
+
+class gs3_scene(C.Structure):
+    pass
+
+
+_SCENE_P = C.POINTER(gs3_scene)
+
+# name -> (restype, argtypes); every symbol include/gs3.h declares
+SIGNATURES = {
+    "gs3_default_opts": (None, [C.POINTER(gs3_render_opts)]),
+    "gs3_create_scene": (C.c_int, [C.POINTER(gs3_scene_desc), C.POINTER(_SCENE_P)]),
+    "gs3_destroy_scene": (C.c_int, [_SCENE_P]),
+    "gs3_workspace_size": (C.c_size_t, [C.c_int32, C.c_int32, C.c_int32, C.c_size_t]),
+    "gs3_workspace_layout": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_size_t,
+                                       C.POINTER(gs3_ws_layout)]),
+    "gs3_render": (C.c_int, [_SCENE_P, C.POINTER(gs3_camera), C.POINTER(gs3_light),
+                             C.POINTER(gs3_render_opts), C.c_void_p, C.c_void_p, C.c_size_t,
+                             C.c_size_t, C.c_void_p]),
+    "gs3_render_stages": (C.c_int, [_SCENE_P, C.POINTER(gs3_camera), C.POINTER(gs3_light),
+                                    C.POINTER(gs3_render_opts), C.c_void_p, C.c_void_p, C.c_size_t,
+                                    C.c_size_t, C.c_uint32, C.c_void_p]),
+    "gs3_workspace_read_header": (C.c_int, [C.c_void_p, C.POINTER(gs3_ws_header), C.c_void_p]),
+    "gs3_kernel_launches": (C.c_uint64, []),
+    "gs3_last_error": (C.c_char_p, []),
+}
+
+_lib = None
+
+
+def lib():
+    """Load libgs3.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"libgs3.so not built at {LIB_PATH}; run __graft_entry__.build()")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(st: int, what: str):
+    if st != GS3_OK:
+        raise GS3Error(st, f"{what}: {lib().gs3_last_error().decode()}")
+
+
+def _ptr(t) -> int:
+    if t is None:
+        return 0
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    return t.data_ptr()
+
+
+def gs3_default_opts() -> gs3_render_opts:
+    o = gs3_render_opts()
+    lib().gs3_default_opts(C.byref(o))
+    return o
+
+
+def gs3_create_scene(desc: gs3_scene_desc):
+    out = _SCENE_P()
+    _check(lib().gs3_create_scene(C.byref(desc), C.byref(out)), "gs3_create_scene")
+    return out
+
+
+def gs3_destroy_scene(scene) -> None:
+    _check(lib().gs3_destroy_scene(scene), "gs3_destroy_scene")
+
+
+def gs3_workspace_size(n: int, width: int, height: int, key_capacity: int) -> int:
+    return int(lib().gs3_workspace_size(n, width, height, key_capacity))
+
+
+def gs3_workspace_layout(n: int, width: int, height: int, key_capacity: int) -> gs3_ws_layout:
+    out = gs3_ws_layout()
+    _check(lib().gs3_workspace_layout(n, width, height, key_capacity, C.byref(out)),
+           "gs3_workspace_layout")
+    return out
+
+
+def gs3_render(scene, camera: gs3_camera, light: gs3_light, opts: gs3_render_opts, out_rgb,
+               workspace, key_capacity: int, stream: int) -> None:
+    _check(lib().gs3_render(scene, C.byref(camera), C.byref(light), C.byref(opts), _ptr(out_rgb),
+                            _ptr(workspace), workspace.numel() * workspace.element_size(),
+                            key_capacity, stream), "gs3_render")
+
+
+def gs3_render_stages(scene, camera: gs3_camera, light: gs3_light, opts: gs3_render_opts, out_rgb,
+                      workspace, key_capacity: int, stages: int, stream: int) -> None:
+    _check(lib().gs3_render_stages(scene, C.byref(camera), C.byref(light), C.byref(opts),
+                                   _ptr(out_rgb), _ptr(workspace),
+                                   workspace.numel() * workspace.element_size(), key_capacity,
+                                   stages, stream), "gs3_render_stages")
+
+
+def gs3_workspace_read_header(workspace, stream: int) -> gs3_ws_header:
+    h = gs3_ws_header()
+    _check(lib().gs3_workspace_read_header(_ptr(workspace), C.byref(h), stream),
+           "gs3_workspace_read_header")
+    return h
+
+
+def gs3_kernel_launches() -> int:
+    return int(lib().gs3_kernel_launches())
+
+
+def gs3_last_error() -> str:
+    return lib().gs3_last_error().decode()

@@ -1,0 +1,275 @@
+// C ABI of libgs3 (declared in include/gs3.h): validation, workspace layout
+// and the stream-ordered launch sequence of one frame.
+#include <atomic>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "gs3_internal.cuh"
+
+struct gs3_scene {
+  gs3::SceneDev dev;
+};
+
+namespace gs3 {
+
+std::atomic<uint64_t> g_launches{0};
+
+namespace {
+
+thread_local std::string g_last_error;
+
+gs3_status fail(gs3_status st, const char* msg) {
+  g_last_error = msg;
+  return st;
+}
+
+gs3_status cuda_fail(cudaError_t e, const char* where) {
+  char buf[256];
+  snprintf(buf, sizeof(buf), "%s: %s", where, cudaGetErrorString(e));
+  g_last_error = buf;
+  return GS3_ERR_CUDA;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+struct Planner {
+  size_t cur = 0;
+  size_t take(size_t bytes) {
+    size_t o = cur;
+    cur = align256(cur + (bytes ? bytes : 1));
+    return o;
+  }
+};
+
+bool mlp_ok(const gs3_mlp_desc& m, int in_dim, int out_dim) {
+  if (m.in_dim != in_dim || m.out_dim != out_dim) return false;
+  if (m.n_hidden < 1 || m.n_hidden > 4) return false;
+  if (m.width != 16 && m.width != 32 && m.width != 64 && m.width != 128) return false;
+  if (m.act != GS3_ACT_RELU && m.act != GS3_ACT_LEAKY_RELU) return false;
+  return m.w && m.b;
+}
+
+}  // namespace
+
+Workspace plan_workspace(int n, int width, int height, size_t cap) {
+  Workspace L;
+  L.n = n;
+  L.width = width;
+  L.height = height;
+  L.gx = (width + kTile - 1) / kTile;
+  L.gy = (height + kTile - 1) / kTile;
+  L.ntiles = L.gx * L.gy;
+  L.cap = cap;
+  L.nb_n = (int)((n + kSortTileItems - 1) / kSortTileItems);
+  L.nb_cap = (int)((cap + kSortTileItems - 1) / kSortTileItems);
+  if (L.nb_cap < 1) L.nb_cap = 1;
+  const size_t N = (size_t)n;
+  const int nbmax = L.nb_n > L.nb_cap ? L.nb_n : L.nb_cap;
+  const size_t hist_words = 256ull * nbmax;
+  size_t scan_words = scan_scratch_words(hist_words);
+  if (scan_scratch_words(N) > scan_words) scan_words = scan_scratch_words(N);
+  Planner P;
+  L.header = P.take(256);
+  for (int s = 0; s < 2; ++s) {
+    SplatBufs& b = L.sp[s];
+    b.key = P.take(4 * N);
+    b.sk[0] = P.take(4 * N);
+    b.sk[1] = P.take(4 * N);
+    b.sv[0] = P.take(4 * N);
+    b.sv[1] = P.take(4 * N);
+    b.order = b.sv[1];
+    b.rank_of = P.take(4 * N);
+    b.rect = P.take(16 * N);
+    b.rec = P.take(sizeof(SplatRec) * N);
+    b.rrec = P.take(sizeof(SplatRec) * N);
+    b.cnt = P.take(4 * N);
+    b.off = P.take(4 * N);
+    b.tk[0] = P.take(4 * cap);
+    b.tk[1] = P.take(4 * cap);
+    b.tv[0] = P.take(4 * cap);
+    b.tv[1] = P.take(4 * cap);
+    b.tile_start = P.take(4 * ((size_t)L.ntiles + 1));
+    b.hist = P.take(4 * hist_words);
+    b.scan_part = P.take(4 * scan_words);
+  }
+  L.partial = P.take(8 * cap);
+  L.shade = P.take(16 * N);
+  L.T = P.take(4 * N);
+  L.Tp = P.take(4 * N);
+  L.res = P.take(16 * N);
+  L.ccol = P.take(32 * N);
+  L.final_t = P.take(4 * (size_t)width * height);
+  L.n_contrib = P.take(4 * (size_t)width * height);
+  L.total = P.cur;
+  return L;
+}
+
+}  // namespace gs3
+
+using namespace gs3;
+
+extern "C" {
+
+const char* gs3_last_error(void) { return g_last_error.c_str(); }
+
+uint64_t gs3_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+void gs3_default_opts(gs3_render_opts* o) {
+  if (!o) return;
+  o->near_z = 0.2f;
+  o->lowpass = 0.3f;
+  o->frustum = 1.3f;
+  o->shadow_bias = 0.015f;
+  o->alpha_min = 1.0f / 255.0f;
+  o->alpha_max = 0.99f;
+  o->t_stop = 1e-4f;
+  o->target[0] = o->target[1] = o->target[2] = 0.f;
+  o->falloff = 1;
+  o->tile = kTile;
+  o->ablate = 0;
+}
+
+gs3_status gs3_create_scene(const gs3_scene_desc* d, gs3_scene** out) {
+  if (!d || !out) return fail(GS3_ERR_INVALID_ARG, "gs3_create_scene: null argument");
+  *out = nullptr;
+  if (d->n < 1) return fail(GS3_ERR_INVALID_ARG, "gs3_create_scene: n must be >= 1");
+  if (d->k < 0 || d->k > kMaxLobes) return fail(GS3_ERR_INVALID_ARG, "gs3_create_scene: k must be in [0, 16]");
+  if (!d->mean_op || !d->scale || !d->rot || !d->shade_rot || !d->albedo_d || !d->albedo_s || !d->latent)
+    return fail(GS3_ERR_INVALID_ARG, "gs3_create_scene: null parameter array");
+  if (d->k > 0 && (!d->lobe_rot || !d->lobe_sigma || !d->lobe_amp))
+    return fail(GS3_ERR_INVALID_ARG, "gs3_create_scene: null lobe array");
+  if (!mlp_ok(d->phi, 61, 1)) return fail(GS3_ERR_INVALID_ARG, "gs3_create_scene: unsupported Phi shape");
+  if (!mlp_ok(d->psi, 60, 3)) return fail(GS3_ERR_INVALID_ARG, "gs3_create_scene: unsupported Psi shape");
+  if (d->mlp_dtype != GS3_MLP_FP32)
+    return fail(GS3_ERR_UNSUPPORTED, "gs3_create_scene: only GS3_MLP_FP32 is available in this build");
+  gs3_scene* s = new (std::nothrow) gs3_scene;
+  if (!s) return fail(GS3_ERR_OOM, "gs3_create_scene: host allocation failed");
+  SceneDev& v = s->dev;
+  v.n = d->n;
+  v.k = d->k;
+  auto f4 = [](const float* p) { return reinterpret_cast<const float4*>(p); };
+  v.mean_op = f4(d->mean_op);
+  v.scale = f4(d->scale);
+  v.rot = f4(d->rot);
+  v.shade_rot = f4(d->shade_rot);
+  v.albedo_d = f4(d->albedo_d);
+  v.albedo_s = f4(d->albedo_s);
+  v.latent = f4(d->latent);
+  v.lobe_rot = f4(d->lobe_rot);
+  v.lobe_sigma = f4(d->lobe_sigma);
+  v.lobe_amp = f4(d->lobe_amp);
+  v.phi = {d->phi.in_dim, d->phi.width, d->phi.n_hidden, d->phi.out_dim, d->phi.act, d->phi.w, d->phi.b};
+  v.psi = {d->psi.in_dim, d->psi.width, d->psi.n_hidden, d->psi.out_dim, d->psi.act, d->psi.w, d->psi.b};
+  v.mlp_dtype = d->mlp_dtype;
+  *out = s;
+  return GS3_OK;
+}
+
+gs3_status gs3_destroy_scene(gs3_scene* s) {
+  delete s;
+  return GS3_OK;
+}
+
+size_t gs3_workspace_size(int32_t n, int32_t width, int32_t height, size_t key_capacity) {
+  if (n < 1 || width < 1 || height < 1) return 0;
+  return plan_workspace(n, width, height, key_capacity).total;
+}
+
+gs3_status gs3_workspace_layout(int32_t n, int32_t width, int32_t height, size_t key_capacity,
+                                gs3_ws_layout* out) {
+  if (!out || n < 1 || width < 1 || height < 1) return fail(GS3_ERR_INVALID_ARG, "gs3_workspace_layout: bad argument");
+  Workspace L = plan_workspace(n, width, height, key_capacity);
+  out->total = L.total;
+  out->header = L.header;
+  const int fin = (L.ntiles <= 256 ? 1 : 2) & 1;
+  for (int s = 0; s < 2; ++s) {
+    out->key[s] = L.sp[s].key;
+    out->order[s] = L.sp[s].order;
+    out->tile_start[s] = L.sp[s].tile_start;
+    out->list[s] = L.sp[s].tv[fin];
+    out->rect[s] = L.sp[s].rect;
+  }
+  out->shade = L.shade;
+  out->shadow = L.T;
+  out->shadow_refined = L.Tp;
+  out->residual = L.res;
+  out->final_t = L.final_t;
+  out->n_contrib = L.n_contrib;
+  return GS3_OK;
+}
+
+gs3_status gs3_render_stages(gs3_scene* scene, const gs3_camera* cam, const gs3_light* light,
+                             const gs3_render_opts* opts, float* out_rgb, void* workspace, size_t ws_bytes,
+                             size_t key_capacity, uint32_t stages, void* stream) {
+  if (!scene || !cam || !light || !opts || !out_rgb || !workspace)
+    return fail(GS3_ERR_INVALID_ARG, "gs3_render: null argument");
+  if (cam->width < 1 || cam->height < 1 || cam->width > 16384 || cam->height > 16384)
+    return fail(GS3_ERR_INVALID_ARG, "gs3_render: image size out of range");
+  if (!(cam->fx > 0.f) || !(cam->fy > 0.f)) return fail(GS3_ERR_INVALID_ARG, "gs3_render: focal length must be > 0");
+  if (opts->tile != kTile) return fail(GS3_ERR_INVALID_ARG, "gs3_render: tile must be 16");
+  if (key_capacity < 1 || key_capacity > 0x7FFFFFFFull)
+    return fail(GS3_ERR_INVALID_ARG, "gs3_render: key_capacity must be in [1, 2^31)");
+  if (reinterpret_cast<uintptr_t>(workspace) % 256 != 0)
+    return fail(GS3_ERR_INVALID_ARG, "gs3_render: workspace must be 256-byte aligned");
+  const int ntiles = ((cam->width + kTile - 1) / kTile) * ((cam->height + kTile - 1) / kTile);
+  if (ntiles > 65536) return fail(GS3_ERR_INVALID_ARG, "gs3_render: more than 65536 tiles");
+  if ((double)scene->dev.n * (double)ntiles >= 4294967295.0)
+    return fail(GS3_ERR_INVALID_ARG, "gs3_render: n * tiles must stay below 2^32");
+  float tl[3] = {opts->target[0] - light->pos[0], opts->target[1] - light->pos[1], opts->target[2] - light->pos[2]};
+  if (tl[0] * tl[0] + tl[1] * tl[1] + tl[2] * tl[2] < 1e-12f)
+    return fail(GS3_ERR_INVALID_ARG, "gs3_render: light coincides with the light-camera target");
+  Workspace L = plan_workspace(scene->dev.n, cam->width, cam->height, key_capacity);
+  if (ws_bytes < L.total) return fail(GS3_ERR_INVALID_ARG, "gs3_render: workspace too small");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  FrameArgs f;
+  f.sc = scene->dev;
+  f.cam = *cam;
+  f.light = *light;
+  f.opts = *opts;
+  f.ws = static_cast<unsigned char*>(workspace);
+  f.L = &L;
+  cudaError_t e = cudaSuccess;
+  const bool no_shadow = (opts->ablate & GS3_ABLATE_SHADOW_SPLAT) != 0;
+  if (stages & GS3_STAGE_PREP) {
+    e = cudaMemsetAsync(f.ws + L.header, 0, 256, s);
+    if (e != cudaSuccess) return cuda_fail(e, "gs3_render: header reset");
+    launch_prep(f, s);
+  }
+  if (stages & GS3_STAGE_CAMERA_BIN) {
+    launch_depth_sort(f, 0, s);
+    launch_binning(f, 0, s);
+  }
+  if ((stages & GS3_STAGE_LIGHT_BIN) && !no_shadow) {
+    launch_depth_sort(f, 1, s);
+    launch_binning(f, 1, s);
+  }
+  if ((stages & GS3_STAGE_SHADOW_COMPOSITE) && !no_shadow) launch_shadow_composite(f, s);
+  if (stages & GS3_STAGE_SHADOW_REDUCE) {
+    if (no_shadow) launch_fill_shadow_one(f, s);
+    else launch_shadow_reduce(f, s);
+  }
+  if (stages & GS3_STAGE_MLP) launch_mlp(f, s);
+  if (stages & GS3_STAGE_CAMERA) launch_camera_composite(f, out_rgb, s);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "gs3_render: launch");
+  return GS3_OK;
+}
+
+gs3_status gs3_render(gs3_scene* scene, const gs3_camera* cam, const gs3_light* light,
+                      const gs3_render_opts* opts, float* out_rgb, void* workspace, size_t ws_bytes,
+                      size_t key_capacity, void* stream) {
+  return gs3_render_stages(scene, cam, light, opts, out_rgb, workspace, ws_bytes, key_capacity,
+                           GS3_STAGE_ALL, stream);
+}
+
+gs3_status gs3_workspace_read_header(const void* workspace, gs3_ws_header* out, void* stream) {
+  if (!workspace || !out) return fail(GS3_ERR_INVALID_ARG, "gs3_workspace_read_header: null argument");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemcpyAsync(out, workspace, sizeof(gs3_ws_header), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "gs3_workspace_read_header");
+  return GS3_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,121 @@
+// Internal declarations shared by the CUDA translation units of libgs3.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <stdint.h>
+
+#include "gs3.h"
+
+namespace gs3 {
+
+constexpr int kTile = 16;             // screen tile edge (pixels)
+constexpr int kTilePix = kTile * kTile;
+constexpr int kSortThreads = 256;     // radix-sort block size
+constexpr int kSortRounds = 16;       // items per thread per block tile
+constexpr int kSortTileItems = kSortThreads * kSortRounds;  // 4096 items per block
+constexpr int kScanItems = 4096;      // items per block in the device-wide scan
+constexpr int kMaxLobes = 16;
+
+// Per-Gaussian splat record (one per splat, by Gaussian index or by rank).
+//   a = (u_hi, v_hi, opacity, depth)  screen position (high part), gamma, FP32 sort depth
+//   b = (A, B, C, u_lo)               conic: power = -0.5 (A dx^2 + C dy^2) - B dx dy
+//   c = (v_lo, 0, 0, 0)               low parts: u = u_hi + u_lo, v = v_hi + v_lo
+//   r = (x0, y0, x1, y1)              inclusive tile rectangle, x0 < 0 when culled
+struct __align__(16) SplatRec {
+  float4 a;
+  float4 b;
+  float4 c;
+  int4 r;
+};
+
+struct SplatBufs {
+  size_t key;           // u32[N] depth key by index
+  size_t sk[2], sv[2];  // u32[N] depth-sort ping-pong
+  size_t order;         // u32[N] index of rank r
+  size_t rank_of;       // u32[N] rank of index g
+  size_t rect;          // int4[N] rectangle by index (copy of rec.r, for inspection)
+  size_t rec;           // SplatRec[N] by index
+  size_t rrec;          // SplatRec[N] by rank
+  size_t cnt;           // u32[N] tiles covered, by rank
+  size_t off;           // u32[N] exclusive prefix of cnt
+  size_t tk[2], tv[2];  // u32[cap] tile-sort ping-pong (key = tile, value = rank)
+  size_t tile_start;    // u32[ntiles + 1]
+  size_t hist;          // u32[256 * nblocks] radix histogram / offsets
+  size_t scan_part;     // u32 partial sums of the device-wide scan
+};
+
+struct Workspace {
+  size_t total = 0;
+  size_t header = 0;
+  SplatBufs sp[2];
+  size_t partial = 0;  // float2[cap] shadow partials (num, den) per light entry
+  size_t shade = 0;    // float4[N] shading colour by index
+  size_t T = 0;        // float[N] shadow value by index
+  size_t Tp = 0;       // float[N] refined shadow value by index
+  size_t res = 0;      // float4[N] residual by index
+  size_t ccol = 0;     // float4[2N] camera colours by camera rank: (shade, T'), (res, 0)
+  size_t final_t = 0;  // float[HW]
+  size_t n_contrib = 0;  // u32[HW]
+  int n = 0, width = 0, height = 0, gx = 0, gy = 0, ntiles = 0;
+  size_t cap = 0;
+  int nb_n = 0;    // radix blocks over N
+  int nb_cap = 0;  // radix blocks over the capacity
+};
+
+Workspace plan_workspace(int n, int width, int height, size_t cap);
+
+// Header word indices (u32) -- must match gs3_ws_header.
+enum { H_STATUS = 0, H_PAIRS_CAM = 1, H_PAIRS_LIGHT = 2, H_NEED_CAM = 3, H_NEED_LIGHT = 4,
+       H_LIGHT_VIEW = 8 };
+
+struct MlpDev {
+  int in_dim, width, n_hidden, out_dim, act;
+  const float* w;
+  const float* b;
+};
+
+struct SceneDev {
+  int n, k;
+  const float4 *mean_op, *scale, *rot, *shade_rot, *albedo_d, *albedo_s, *latent;
+  const float4 *lobe_rot, *lobe_sigma, *lobe_amp;
+  MlpDev phi, psi;
+  int mlp_dtype;
+};
+
+// ---- launchers (stream-ordered, no host synchronisation) ----
+struct FrameArgs {
+  SceneDev sc;
+  gs3_camera cam;
+  gs3_light light;
+  gs3_render_opts opts;
+  unsigned char* ws;
+  const Workspace* L;
+};
+
+void launch_prep(const FrameArgs& f, cudaStream_t s);
+void launch_depth_sort(const FrameArgs& f, int splat, cudaStream_t s);
+void launch_binning(const FrameArgs& f, int splat, cudaStream_t s);
+void launch_shadow_composite(const FrameArgs& f, cudaStream_t s);
+void launch_shadow_reduce(const FrameArgs& f, cudaStream_t s);
+void launch_mlp(const FrameArgs& f, cudaStream_t s);
+void launch_camera_composite(const FrameArgs& f, float* out_rgb, cudaStream_t s);
+void launch_fill_shadow_one(const FrameArgs& f, cudaStream_t s);
+
+// exclusive scan of n u32 values (in place allowed: out may equal in);
+// the total goes to *total if non-null
+void device_exclusive_scan(const uint32_t* in, uint32_t* out, uint32_t n, uint32_t* total,
+                           uint32_t* scratch, cudaStream_t s);
+size_t scan_scratch_words(size_t n);
+
+// host-side count of kernel launches (reported by gs3_kernel_launches)
+extern std::atomic<uint64_t> g_launches;
+inline void count_launch(int n = 1) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }
+
+template <typename T>
+__host__ __device__ inline T* at(unsigned char* ws, size_t off) {
+  return reinterpret_cast<T*>(ws + off);
+}
+
+}  // namespace gs3

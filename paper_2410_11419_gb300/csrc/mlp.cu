@@ -1,0 +1,211 @@
+// K8 (FP32 form): the shadow-refinement MLP Phi (Sec. 4.2) and the residual
+// MLP Psi (Sec. 4.3) over all spatial Gaussians.
+//
+// One 256-thread block owns 64 Gaussians.  The prologue builds the inputs in
+// shared memory, feature-major:
+//   Phi: [T, PE(w_i), PE(mu), l]  (61)      Psi: [PE(w_o), PE(mu), l]  (60)
+//   PE(v) = [v, sin(2^k pi v), cos(2^k pi v)], k = 0..3, per component
+// with world-space unit directions w_i = (p_L - mu)/|.|, w_o = (p_C - mu)/|.|.
+// Each hidden layer is a 64 x width register-tiled FP32 product against the
+// layer's weights staged in shared memory; the output layer applies the
+// sigmoid.  Outputs go both by Gaussian index and, for the camera composite,
+// by camera depth rank.
+#include "gs3_internal.cuh"
+
+namespace gs3 {
+namespace {
+
+constexpr int kRows = 64;
+constexpr int kHPad = kRows + 4;  // feature-major activations, padded rows
+
+struct MlpParams {
+  MlpDev net;
+  int n;
+  int which;  // 0 Phi, 1 Psi
+  const float4* mean_op;
+  const float4* latent;
+  const float* T;
+  float light_pos[3], cam_pos[3];
+  float* out_idx;    // Phi: T' [N];   Psi: float4 residual [N] (as floats)
+  float4* ccol;      // camera colours by rank
+  const uint32_t* rank_of;
+  int identity;      // ablation: Phi -> T' = T, Psi -> 0
+};
+
+__device__ __forceinline__ void write_pe(float (*H)[kHPad], int base, int row, int q, float v0, float v1,
+                                         float v2) {
+  if (q == 0) {
+    H[base + 0][row] = v0;
+    H[base + 1][row] = v1;
+    H[base + 2][row] = v2;
+  }
+  const float f = (float)(1 << q);
+  float s, c;
+  const int o = base + 3 + 6 * q;
+  sincospif(f * v0, &s, &c); H[o + 0][row] = s; H[o + 3][row] = c;
+  sincospif(f * v1, &s, &c); H[o + 1][row] = s; H[o + 4][row] = c;
+  sincospif(f * v2, &s, &c); H[o + 2][row] = s; H[o + 5][row] = c;
+}
+
+template <int WIDTH>
+__global__ void __launch_bounds__(256) k_mlp(MlpParams p) {
+  extern __shared__ float4 smem4[];
+  float* smem = reinterpret_cast<float*>(smem4);
+  float (*H)[kHPad] = reinterpret_cast<float (*)[kHPad]>(smem);  // [128][kHPad]
+  float* Ws = smem + 128 * kHPad;                                  // [din][dout]
+  const int t = threadIdx.x;
+  const int g0 = blockIdx.x * kRows;
+
+  if (p.identity) {
+    if (t < kRows && g0 + t < p.n) {
+      const int g = g0 + t;
+      const uint32_t r = p.rank_of[g];
+      if (p.which == 0) {
+        const float v = p.T[g];
+        p.out_idx[g] = v;
+        p.ccol[2 * r].w = v;
+      } else {
+        reinterpret_cast<float4*>(p.out_idx)[g] = make_float4(0.f, 0.f, 0.f, 0.f);
+        p.ccol[2 * r + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+    }
+    return;
+  }
+
+  // ---- prologue: inputs, 4 threads per row (thread q handles band q) ----
+  {
+    const int row = t >> 2, q = t & 3;
+    const int g = min(g0 + row, p.n - 1);
+    const float4 m = p.mean_op[g];
+    const float* src = p.which == 0 ? p.light_pos : p.cam_pos;
+    float dx = src[0] - m.x, dy = src[1] - m.y, dz = src[2] - m.z;
+    const float il = rsqrtf(dx * dx + dy * dy + dz * dz);
+    dx *= il; dy *= il; dz *= il;
+    const int b0 = p.which == 0 ? 1 : 0;
+    write_pe(H, b0, row, q, dx, dy, dz);
+    write_pe(H, b0 + 27, row, q, m.x, m.y, m.z);
+    if (q == 0) {
+      const float4 l0 = p.latent[g], l1 = p.latent[p.n + g];
+      const int lb = b0 + 54;
+      H[lb + 0][row] = l0.x; H[lb + 1][row] = l0.y; H[lb + 2][row] = l0.z; H[lb + 3][row] = l0.w;
+      H[lb + 4][row] = l1.x; H[lb + 5][row] = l1.y;
+      if (p.which == 0) H[0][row] = p.T[g];
+    }
+  }
+
+  constexpr int CPT = WIDTH / 16;  // columns per thread
+  const int tcol = t & 15, trow = t >> 4;
+  int din = p.net.in_dim;
+  const float* w = p.net.w;
+  const float* bias = p.net.b;
+  for (int l = 0; l < p.net.n_hidden; ++l) {
+    __syncthreads();  // H complete, previous Ws no longer read
+    for (int i = t; i < din * WIDTH; i += 256) {
+      const int j = i / din, k = i - j * din;  // W row-major (out, in)
+      Ws[k * WIDTH + j] = w[i];
+    }
+    __syncthreads();
+    float acc[4][CPT];
+#pragma unroll
+    for (int c = 0; c < CPT; ++c) {
+      const float bv = bias[tcol * CPT + c];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) acc[r][c] = bv;
+    }
+    for (int k = 0; k < din; ++k) {
+      const float4 a = *reinterpret_cast<const float4*>(&H[k][trow * 4]);
+      float bv[CPT];
+#pragma unroll
+      for (int c = 0; c < CPT; ++c) bv[c] = Ws[k * WIDTH + tcol * CPT + c];
+#pragma unroll
+      for (int c = 0; c < CPT; ++c) {
+        acc[0][c] = fmaf(a.x, bv[c], acc[0][c]);
+        acc[1][c] = fmaf(a.y, bv[c], acc[1][c]);
+        acc[2][c] = fmaf(a.z, bv[c], acc[2][c]);
+        acc[3][c] = fmaf(a.w, bv[c], acc[3][c]);
+      }
+    }
+    __syncthreads();  // all reads of H done
+    const bool leaky = p.net.act == GS3_ACT_LEAKY_RELU;
+#pragma unroll
+    for (int c = 0; c < CPT; ++c)
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        float v = acc[r][c];
+        v = v > 0.f ? v : (leaky ? 0.01f * v : 0.f);
+        H[tcol * CPT + c][trow * 4 + r] = v;
+      }
+    w += (size_t)din * WIDTH;
+    bias += WIDTH;
+    din = WIDTH;
+  }
+  __syncthreads();
+  // ---- output layer + sigmoid ----
+  const int dout = p.net.out_dim;
+  if (t < kRows * dout) {
+    const int row = t % kRows, o = t / kRows;
+    const int g = g0 + row;
+    float acc = bias[o];
+    const float* wr = w + (size_t)o * din;
+    for (int k = 0; k < din; ++k) acc = fmaf(H[k][row], wr[k], acc);
+    const float y = 1.f / (1.f + __expf(-acc));
+    if (g < p.n) {
+      const uint32_t r = p.rank_of[g];
+      if (p.which == 0) {
+        p.out_idx[g] = y;
+        p.ccol[2 * r].w = y;
+      } else {
+        p.out_idx[4 * g + o] = y;
+        reinterpret_cast<float*>(&p.ccol[2 * r + 1])[o] = y;
+      }
+    }
+  }
+}
+
+template <int WIDTH>
+void launch_width(const MlpParams& p, cudaStream_t s) {
+  const size_t sm = (size_t)(128 * kHPad + 128 * WIDTH) * sizeof(float);
+  static bool configured = false;
+  if (!configured) {
+    cudaFuncSetAttribute(k_mlp<WIDTH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    configured = true;
+  }
+  k_mlp<WIDTH><<<(p.n + kRows - 1) / kRows, 256, sm, s>>>(p);
+  count_launch();
+}
+
+void launch_one(const MlpParams& p, cudaStream_t s) {
+  switch (p.net.width) {
+    case 16: launch_width<16>(p, s); break;
+    case 32: launch_width<32>(p, s); break;
+    case 64: launch_width<64>(p, s); break;
+    default: launch_width<128>(p, s); break;
+  }
+}
+
+}  // namespace
+
+void launch_mlp(const FrameArgs& f, cudaStream_t s) {
+  MlpParams p;
+  p.n = f.sc.n;
+  p.mean_op = f.sc.mean_op;
+  p.latent = f.sc.latent;
+  p.T = at<float>(f.ws, f.L->T);
+  for (int i = 0; i < 3; ++i) { p.light_pos[i] = f.light.pos[i]; p.cam_pos[i] = f.cam.pos[i]; }
+  p.ccol = at<float4>(f.ws, f.L->ccol);
+  p.rank_of = at<uint32_t>(f.ws, f.L->sp[0].rank_of);
+
+  p.net = f.sc.phi;
+  p.which = 0;
+  p.out_idx = at<float>(f.ws, f.L->Tp);
+  p.identity = (f.opts.ablate & GS3_ABLATE_PHI) != 0;
+  launch_one(p, s);
+
+  p.net = f.sc.psi;
+  p.which = 1;
+  p.out_idx = at<float>(f.ws, f.L->res);
+  p.identity = (f.opts.ablate & GS3_ABLATE_PSI) != 0;
+  launch_one(p, s);
+}
+
+}  // namespace gs3

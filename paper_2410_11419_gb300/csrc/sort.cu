@@ -1,0 +1,344 @@
+// K2-K5: binning of one splat (camera or light) into per-tile depth-ordered
+// lists, the "same pipeline as screen-space splatting" the paper reuses for
+// both the camera view (Sec. 3) and the light view (Sec. 4.2).
+//
+// Order of operations (LSD radix on the composite (tile, depth) key, with the
+// depth digits sorted once per Gaussian before duplication):
+//   1. stable radix sort of the N FP32 depth keys (index payload, emitted in
+//      index order)  -> rank r, order[r]
+//   2. records gathered into rank order, tile counts per rank, exclusive scan
+//   3. one (tile, rank) pair per covered tile, written in rank order
+//   4. stable radix sort of the pairs on the tile bits only
+//   5. per-tile [start, end) ranges
+// Within a tile the result is ascending (depth bits, index), identical to a
+// stable sort of 64-bit (tile << 32 | depth) keys emitted in index order.
+#include "gs3_internal.cuh"
+
+namespace gs3 {
+namespace {
+
+// ---------------------------------------------------------------------------
+// Device-wide exclusive scan: reduce, scan of block sums, down-sweep.  No
+// block ever waits on another block.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_scan_reduce(const uint32_t* in, uint32_t n, uint32_t* part) {
+  __shared__ uint32_t red[8];
+  const uint32_t base = blockIdx.x * kScanItems;
+  uint32_t s = 0;
+#pragma unroll 4
+  for (int r = 0; r < kScanItems / 256; ++r) {
+    uint32_t i = base + r * 256 + threadIdx.x;
+    if (i < n) s += in[i];
+  }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t t = 0;
+    for (int w = 0; w < 8; ++w) t += red[w];
+    part[blockIdx.x] = t;
+  }
+}
+
+// single block: exclusive scan of the block sums, any length
+__global__ void __launch_bounds__(1024) k_scan_part(uint32_t* part, uint32_t nb, uint32_t* total) {
+  __shared__ uint32_t wsum[32];
+  __shared__ uint32_t carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (uint32_t base = 0; base < nb; base += 1024) {
+    uint32_t i = base + threadIdx.x;
+    uint32_t v = i < nb ? part[i] : 0;
+    uint32_t x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+      uint32_t w = wsum[lane];
+      for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+        if (lane >= o) w += y;
+      }
+      wsum[lane] = w;
+    }
+    __syncthreads();
+    uint32_t incl = x + (warp ? wsum[warp - 1] : 0u);
+    if (i < nb) part[i] = carry + incl - v;
+    __syncthreads();
+    if (threadIdx.x == 1023) carry += incl;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && total) *total = carry;
+}
+
+__global__ void __launch_bounds__(256) k_scan_down(const uint32_t* in, uint32_t* out, uint32_t n,
+                                                   const uint32_t* part) {
+  __shared__ uint32_t sm[kScanItems];
+  __shared__ uint32_t wsum[8];
+  const uint32_t base = blockIdx.x * kScanItems;
+  for (int r = 0; r < kScanItems / 256; ++r) {
+    uint32_t i = base + r * 256 + threadIdx.x;
+    sm[r * 256 + threadIdx.x] = i < n ? in[i] : 0u;
+  }
+  __syncthreads();
+  constexpr int per = kScanItems / 256;  // 16 consecutive items per thread
+  uint32_t loc[per];
+  uint32_t s = 0;
+#pragma unroll
+  for (int j = 0; j < per; ++j) {
+    loc[j] = s;
+    s += sm[threadIdx.x * per + j];
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t x = s;
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) wsum[warp] = x;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t a = 0;
+    for (int w = 0; w < 8; ++w) { uint32_t t = wsum[w]; wsum[w] = a; a += t; }
+  }
+  __syncthreads();
+  const uint32_t off = part[blockIdx.x] + wsum[warp] + (x - s);
+#pragma unroll
+  for (int j = 0; j < per; ++j) sm[threadIdx.x * per + j] = off + loc[j];
+  __syncthreads();
+  for (int r = 0; r < kScanItems / 256; ++r) {
+    uint32_t i = base + r * 256 + threadIdx.x;
+    if (i < n) out[i] = sm[r * 256 + threadIdx.x];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Stable LSD radix sort pass, 8-bit digit, u32 key + u32 value.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t load_n(const uint32_t* n_ptr, uint32_t n_fixed) {
+  return n_ptr ? *n_ptr : n_fixed;
+}
+
+__global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint32_t* __restrict__ keys,
+                                                             const uint32_t* n_ptr, uint32_t n_fixed,
+                                                             int shift, uint32_t* hist, int nblocks) {
+  __shared__ uint32_t cnt[256];
+  const uint32_t n = load_n(n_ptr, n_fixed);
+  cnt[threadIdx.x] = 0;
+  __syncthreads();
+  const uint32_t base = blockIdx.x * kSortTileItems;
+  const int lane = threadIdx.x & 31;
+  for (int r = 0; r < kSortRounds; ++r) {
+    uint32_t i = base + r * kSortThreads + threadIdx.x;
+    uint32_t d = i < n ? (keys[i] >> shift) & 255u : 256u;
+    uint32_t peers = __match_any_sync(0xffffffffu, d);
+    if (d < 256u && lane == __ffs(peers) - 1) atomicAdd(&cnt[d], __popc(peers));
+  }
+  __syncthreads();
+  hist[threadIdx.x * nblocks + blockIdx.x] = cnt[threadIdx.x];
+}
+
+__global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
+    const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint32_t* __restrict__ kout,
+    uint32_t* __restrict__ vout, const uint32_t* n_ptr, uint32_t n_fixed, int shift,
+    const uint32_t* __restrict__ hist, int nblocks) {
+  __shared__ uint32_t s_base[256];
+  __shared__ uint32_t s_run[256];
+  __shared__ uint32_t s_wc[2][kSortThreads / 32][256];
+  const uint32_t n = load_n(n_ptr, n_fixed);
+  const uint32_t base = blockIdx.x * kSortTileItems;
+  if (base >= n) return;
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  const uint32_t lt = (1u << lane) - 1u;
+  s_base[t] = hist[t * nblocks + blockIdx.x];
+  s_run[t] = 0;
+#pragma unroll
+  for (int w = 0; w < kSortThreads / 32; ++w) { s_wc[0][w][t] = 0; s_wc[1][w][t] = 0; }
+  __syncthreads();
+  for (int r = 0; r < kSortRounds; ++r) {
+    const int buf = r & 1;
+    const uint32_t i = base + r * kSortThreads + t;
+    const bool valid = i < n;
+    const uint32_t k = valid ? kin[i] : 0u;
+    const uint32_t v = valid ? (vin ? vin[i] : i) : 0u;
+    const uint32_t d = valid ? (k >> shift) & 255u : 256u;
+    const uint32_t peers = __match_any_sync(0xffffffffu, d);
+    const uint32_t lrank = __popc(peers & lt);
+    if (valid && lrank == 0) s_wc[buf][warp][d] = __popc(peers);
+    __syncthreads();
+    uint32_t acc = s_run[t];
+#pragma unroll
+    for (int w = 0; w < kSortThreads / 32; ++w) {
+      uint32_t c = s_wc[buf][w][t];
+      s_wc[buf][w][t] = acc;
+      acc += c;
+      s_wc[buf ^ 1][w][t] = 0;
+    }
+    s_run[t] = acc;
+    __syncthreads();
+    if (valid) {
+      const uint32_t pos = s_base[d] + s_wc[buf][warp][d] + lrank;
+      if (pos < n) {
+        kout[pos] = k;
+        vout[pos] = v;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Rank order, counts, emission, ranges
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_reorder(int n, const uint32_t* __restrict__ order,
+                                                 const SplatRec* __restrict__ rec, SplatRec* __restrict__ rrec,
+                                                 uint32_t* __restrict__ rank_of, uint32_t* __restrict__ cnt,
+                                                 const float4* __restrict__ shade, float4* __restrict__ ccol) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  const uint32_t g = order[r];
+  if (g >= (uint32_t)n) return;
+  const SplatRec q = rec[g];
+  rrec[r] = q;
+  rank_of[g] = r;
+  cnt[r] = q.r.x >= 0 ? (uint32_t)(q.r.z - q.r.x + 1) * (uint32_t)(q.r.w - q.r.y + 1) : 0u;
+  if (ccol) {
+    float4 c = shade[g];
+    ccol[2 * r] = make_float4(c.x, c.y, c.z, 0.f);
+  }
+}
+
+__global__ void __launch_bounds__(256) k_emit(int n, uint32_t cap, const SplatRec* __restrict__ rrec,
+                                              const uint32_t* __restrict__ off, uint32_t* header, int h_need,
+                                              int h_pairs, uint32_t* __restrict__ tk, uint32_t* __restrict__ tv,
+                                              int gx) {
+  __shared__ uint32_t s_off[257];
+  __shared__ int s_x0[256], s_y0[256], s_w[256];
+  const uint32_t need = header[h_need];
+  if (need > cap) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      header[h_pairs] = 0;
+      atomicCAS(&header[H_STATUS], 0u, (uint32_t)GS3_ERR_CAPACITY);
+    }
+    return;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) header[h_pairs] = need;
+  const int t = threadIdx.x;
+  const int r0 = blockIdx.x * 256;
+  const int r = r0 + t;
+  s_off[t] = r < n ? off[r] : need;
+  if (t == 0) s_off[256] = (r0 + 256 < n) ? off[r0 + 256] : need;
+  if (r < n) {
+    int4 q = rrec[r].r;
+    s_x0[t] = q.x; s_y0[t] = q.y; s_w[t] = q.z - q.x + 1;
+  } else {
+    s_x0[t] = 0; s_y0[t] = 0; s_w[t] = 1;
+  }
+  __syncthreads();
+  const uint32_t end = s_off[256];
+  for (uint32_t e = s_off[0] + t; e < end; e += 256) {
+    int lo = 0, hi = 255;
+    while (lo < hi) {
+      int mid = (lo + hi + 1) >> 1;
+      if (s_off[mid] <= e) lo = mid; else hi = mid - 1;
+    }
+    const uint32_t local = e - s_off[lo];
+    const int w = s_w[lo];
+    const int ty = s_y0[lo] + (int)(local / (uint32_t)w);
+    const int tx = s_x0[lo] + (int)(local % (uint32_t)w);
+    tk[e] = (uint32_t)(ty * gx + tx);
+    tv[e] = (uint32_t)(r0 + lo);
+  }
+}
+
+__global__ void __launch_bounds__(256) k_ranges(const uint32_t* __restrict__ keys, const uint32_t* header,
+                                                int h_pairs, uint32_t* __restrict__ start, int ntiles,
+                                                uint32_t limit) {
+  const uint32_t P = header[h_pairs];
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i <= P && i <= limit; i += gridDim.x * blockDim.x) {
+    const int prev = i == 0 ? -1 : (int)keys[i - 1];
+    const int cur = i == P ? ntiles : (int)keys[i];
+    for (int t = prev + 1; t <= cur && t <= ntiles; ++t) start[t] = i;
+  }
+}
+
+void radix_sort(const uint32_t* kin, const uint32_t* vin, uint32_t* k0, uint32_t* v0, uint32_t* k1,
+                uint32_t* v1, const uint32_t* n_ptr, uint32_t n_fixed, int nblocks, int passes,
+                uint32_t* hist, uint32_t* scan_part, cudaStream_t s) {
+  const uint32_t* ki = kin;
+  const uint32_t* vi = vin;
+  for (int p = 0; p < passes; ++p) {
+    uint32_t* ko = (p & 1) ? k1 : k0;
+    uint32_t* vo = (p & 1) ? v1 : v0;
+    k_radix_hist<<<nblocks, kSortThreads, 0, s>>>(ki, n_ptr, n_fixed, 8 * p, hist, nblocks);
+    device_exclusive_scan(hist, hist, 256u * nblocks, nullptr, scan_part, s);
+    k_radix_scatter<<<nblocks, kSortThreads, 0, s>>>(ki, vi, ko, vo, n_ptr, n_fixed, 8 * p, hist, nblocks);
+    count_launch(2);
+    ki = ko;
+    vi = vo;
+  }
+}
+
+}  // namespace
+
+size_t scan_scratch_words(size_t n) { return (n + kScanItems - 1) / kScanItems + 1; }
+
+void device_exclusive_scan(const uint32_t* in, uint32_t* out, uint32_t n, uint32_t* total,
+                           uint32_t* scratch, cudaStream_t s) {
+  const uint32_t nb = (n + kScanItems - 1) / kScanItems;
+  if (nb == 0) return;
+  k_scan_reduce<<<nb, 256, 0, s>>>(in, n, scratch);
+  k_scan_part<<<1, 1024, 0, s>>>(scratch, nb, total);
+  k_scan_down<<<nb, 256, 0, s>>>(in, out, n, scratch);
+  count_launch(3);
+}
+
+int tile_sort_passes(int ntiles) { return ntiles <= 256 ? 1 : 2; }
+
+void launch_depth_sort(const FrameArgs& f, int sp, cudaStream_t s) {
+  const SplatBufs& b = f.L->sp[sp];
+  unsigned char* ws = f.ws;
+  const int n = f.sc.n;
+  radix_sort(at<uint32_t>(ws, b.key), nullptr, at<uint32_t>(ws, b.sk[0]), at<uint32_t>(ws, b.sv[0]),
+             at<uint32_t>(ws, b.sk[1]), at<uint32_t>(ws, b.sv[1]), nullptr, (uint32_t)n, f.L->nb_n, 4,
+             at<uint32_t>(ws, b.hist), at<uint32_t>(ws, b.scan_part), s);
+  // 4 passes end in buffer 1: sv[1] holds the index of each depth rank
+  k_reorder<<<(n + 255) / 256, 256, 0, s>>>(
+      n, at<uint32_t>(ws, b.sv[1]), at<SplatRec>(ws, b.rec), at<SplatRec>(ws, b.rrec),
+      at<uint32_t>(ws, b.rank_of), at<uint32_t>(ws, b.cnt), at<float4>(ws, f.L->shade),
+      sp == 0 ? at<float4>(ws, f.L->ccol) : nullptr);
+  count_launch();
+}
+
+void launch_binning(const FrameArgs& f, int sp, cudaStream_t s) {
+  const SplatBufs& b = f.L->sp[sp];
+  unsigned char* ws = f.ws;
+  const int n = f.sc.n;
+  uint32_t* header = at<uint32_t>(ws, f.L->header);
+  const int h_need = sp ? H_NEED_LIGHT : H_NEED_CAM;
+  const int h_pairs = sp ? H_PAIRS_LIGHT : H_PAIRS_CAM;
+  device_exclusive_scan(at<uint32_t>(ws, b.cnt), at<uint32_t>(ws, b.off), (uint32_t)n, header + h_need,
+                        at<uint32_t>(ws, b.scan_part), s);
+  k_emit<<<(n + 255) / 256, 256, 0, s>>>(n, (uint32_t)f.L->cap, at<SplatRec>(ws, b.rrec),
+                                         at<uint32_t>(ws, b.off), header, h_need, h_pairs,
+                                         at<uint32_t>(ws, b.tk[0]), at<uint32_t>(ws, b.tv[0]), f.L->gx);
+  count_launch();
+  const int passes = tile_sort_passes(f.L->ntiles);
+  // sort (tile, rank) pairs on the tile bits; start from buffer 0, alternate
+  radix_sort(at<uint32_t>(ws, b.tk[0]), at<uint32_t>(ws, b.tv[0]), at<uint32_t>(ws, b.tk[1]),
+             at<uint32_t>(ws, b.tv[1]), at<uint32_t>(ws, b.tk[0]), at<uint32_t>(ws, b.tv[0]),
+             header + h_pairs, 0, f.L->nb_cap, passes, at<uint32_t>(ws, b.hist),
+             at<uint32_t>(ws, b.scan_part), s);
+  const int fin = passes & 1;  // 1 pass ends in buffer 1, 2 passes in buffer 0
+  const uint32_t* keys = at<uint32_t>(ws, b.tk[fin]);
+  int blocks = (int)((f.L->cap + 1 + 255) / 256);
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  k_ranges<<<blocks, 256, 0, s>>>(keys, header, h_pairs, at<uint32_t>(ws, b.tile_start), f.L->ntiles,
+                                  (uint32_t)f.L->cap);
+  count_launch();
+}
+
+}  // namespace gs3

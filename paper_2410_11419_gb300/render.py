@@ -1,0 +1,153 @@
+"""Device-resident scenes and a frame renderer over the C ABI.
+
+torch provides device memory and streams; every step of the frame runs in
+libgs3's CUDA kernels.  `DeviceScene` uploads a host scene (structure of
+arrays) once; `Renderer` owns a workspace and renders frames into a device
+image, exposing the workspace's intermediate buffers for inspection.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+import torch
+
+from . import _native as N
+
+
+def camera_struct(cam) -> N.gs3_camera:
+    c = N.gs3_camera()
+    c.R = (C.c_float * 9)(*np.asarray(cam.R, dtype=np.float32).reshape(-1).tolist())
+    c.t = (C.c_float * 3)(*np.asarray(cam.t, dtype=np.float32).tolist())
+    c.pos = (C.c_float * 3)(*np.asarray(cam.pos, dtype=np.float32).tolist())
+    c.fx, c.fy, c.cx, c.cy = cam.fx, cam.fy, cam.cx, cam.cy
+    c.width, c.height = cam.width, cam.height
+    return c
+
+
+def light_struct(light) -> N.gs3_light:
+    return N.gs3_light((C.c_float * 3)(*np.asarray(light.pos, dtype=np.float32).tolist()),
+                       float(light.intensity))
+
+
+def opts_struct(ablate: int = 0, falloff: int = 1, **kw) -> N.gs3_render_opts:
+    o = N.gs3_default_opts()
+    o.ablate = ablate
+    o.falloff = falloff
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+class DeviceScene:
+    """Scene parameters resident on the GPU plus the library's scene handle."""
+
+    def __init__(self, scene, device="cuda", mlp_dtype: int = N.GS3_MLP_FP32):
+        self.n, self.k = scene.n, scene.k
+        dev = torch.device(device)
+        self.t = {}
+        for a in scene.ARRAYS:
+            arr = np.ascontiguousarray(getattr(scene, a), dtype=np.float32)
+            if arr.size == 0:
+                arr = np.zeros(4, dtype=np.float32)
+            self.t[a] = torch.from_numpy(arr).to(dev)
+        for nm in ("phi", "psi"):
+            w, b = getattr(scene, nm).packed()
+            self.t[nm + "_w"] = torch.from_numpy(w).to(dev)
+            self.t[nm + "_b"] = torch.from_numpy(b).to(dev)
+        d = N.gs3_scene_desc()
+        d.n, d.k = scene.n, scene.k
+        for a in scene.ARRAYS:
+            setattr(d, a, self.t[a].data_ptr())
+        for nm in ("phi", "psi"):
+            m = getattr(scene, nm)
+            setattr(d, nm, N.gs3_mlp_desc(m.in_dim, m.width, m.n_hidden, m.out_dim, m.act,
+                                          self.t[nm + "_w"].data_ptr(), self.t[nm + "_b"].data_ptr()))
+        d.mlp_dtype = mlp_dtype
+        self.desc = d
+        self.handle = N.gs3_create_scene(d)
+
+    def close(self):
+        if self.handle:
+            N.gs3_destroy_scene(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Renderer:
+    """One workspace sized for (n, width, height, key_capacity)."""
+
+    def __init__(self, dscene: DeviceScene, width: int, height: int, key_capacity: int,
+                 device="cuda"):
+        self.scene = dscene
+        self.width, self.height, self.cap = width, height, int(key_capacity)
+        nbytes = N.gs3_workspace_size(dscene.n, width, height, self.cap)
+        self.ws = torch.empty(nbytes + 256, dtype=torch.uint8, device=device)
+        pad = (-self.ws.data_ptr()) % 256
+        self.ws = self.ws[pad:pad + nbytes]
+        self.layout = N.gs3_workspace_layout(dscene.n, width, height, self.cap)
+        self.image = torch.empty((height, width, 3), dtype=torch.float32, device=device)
+
+    def render(self, cam, light, opts=None, out=None, stream=None):
+        opts = opts if opts is not None else opts_struct()
+        out = self.image if out is None else out
+        s = torch.cuda.current_stream() if stream is None else stream
+        N.gs3_render(self.scene.handle, camera_struct(cam), light_struct(light), opts, out, self.ws,
+                     self.cap, s.cuda_stream)
+        return out
+
+    def render_stages(self, cam, light, stages: int, opts=None, out=None, stream=None):
+        opts = opts if opts is not None else opts_struct()
+        out = self.image if out is None else out
+        s = torch.cuda.current_stream() if stream is None else stream
+        N.gs3_render_stages(self.scene.handle, camera_struct(cam), light_struct(light), opts, out,
+                            self.ws, self.cap, stages, s.cuda_stream)
+        return out
+
+    def header(self, stream=None) -> N.gs3_ws_header:
+        s = torch.cuda.current_stream() if stream is None else stream
+        return N.gs3_workspace_read_header(self.ws, s.cuda_stream)
+
+    def check(self):
+        h = self.header()
+        if h.status != N.GS3_OK:
+            raise N.GS3Error(h.status, f"device status (pairs needed: camera {h.pairs_cam_needed}, "
+                                       f"light {h.pairs_light_needed}, capacity {self.cap})")
+        return h
+
+    # -- inspection views ------------------------------------------------------
+    def _view(self, off: int, count: int, dtype) -> torch.Tensor:
+        nb = count * torch.empty((), dtype=dtype).element_size()
+        return self.ws[off:off + nb].view(dtype)
+
+    def stage(self, name: str, splat: int = 0) -> torch.Tensor:
+        L, n = self.layout, self.scene.n
+        ntiles = ((self.width + 15) // 16) * ((self.height + 15) // 16)
+        if name == "key":
+            return self._view(L.key[splat], n, torch.int32)
+        if name == "order":
+            return self._view(L.order[splat], n, torch.int32)
+        if name == "tile_start":
+            return self._view(L.tile_start[splat], ntiles + 1, torch.int32)
+        if name == "list":
+            return self._view(L.list[splat], self.cap, torch.int32)
+        if name == "rect":
+            return self._view(L.rect[splat], 4 * n, torch.int32).view(n, 4)
+        if name == "shade":
+            return self._view(L.shade, 4 * n, torch.float32).view(n, 4)
+        if name == "T":
+            return self._view(L.shadow, n, torch.float32)
+        if name == "Tp":
+            return self._view(L.shadow_refined, n, torch.float32)
+        if name == "res":
+            return self._view(L.residual, 4 * n, torch.float32).view(n, 4)
+        if name == "final_t":
+            return self._view(L.final_t, self.width * self.height, torch.float32).view(self.height, self.width)
+        if name == "n_contrib":
+            return self._view(L.n_contrib, self.width * self.height, torch.int32).view(self.height, self.width)
+        raise KeyError(name)
