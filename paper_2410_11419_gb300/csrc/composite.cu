@@ -9,110 +9,214 @@
 namespace gs3 {
 namespace {
 
-constexpr float kSkipPower = -5.6f;  // below ln(1/255): alpha < 1/255 for any opacity <= 1
+// Pixel of thread t inside its 16x16 tile: warp w covers the 8x4 block at
+// (8 (w & 1), 4 (w >> 1)); lane l is pixel (l & 7, l >> 3) of that block.
+__device__ __forceinline__ int tile_px(int t) { return ((t >> 5) & 1) * 8 + (t & 7); }
+__device__ __forceinline__ int tile_py(int t) { return ((t >> 5) >> 1) * 4 + ((t & 31) >> 3); }
 
-// Evaluate one splat at a pixel centre: beta = exp(power), alpha = min(amax, gamma beta).
-// The centre is (a.x + b.w, a.y + vlo): high part first, so the difference to
-// the pixel keeps its precision.
-__device__ __forceinline__ bool splat_alpha(const float4 a, const float4 b, float vlo, float fx, float fy,
-                                            float amin, float amax, float& beta, float& alpha) {
+// Bit w set when the splat's alpha >= alpha_min box can reach warp w's 8x4
+// pixel block of tile (tx, ty); a warp whose bit is clear has no passing
+// pixel and skips the splat.
+__device__ __forceinline__ uint32_t warp_mask(const SplatRec& q, int tx, int ty) {
+  const float hx = q.c.y, hy = q.c.z;
+  if (!(hx >= 0.f)) return 0u;
+  const float u = q.a.x + q.b.w, v = q.a.y + q.c.x;
+  uint32_t m = 0u;
+#pragma unroll
+  for (int w = 0; w < 8; ++w) {
+    const float x0 = tx * kTile + (w & 1) * 8 + 0.5f, y0 = ty * kTile + (w >> 1) * 4 + 0.5f;
+    const bool hit = (u + hx >= x0) && (u - hx <= x0 + 7.f) && (v + hy >= y0) && (v - hy <= y0 + 3.f);
+    m |= hit ? (1u << w) : 0u;
+  }
+  return m;
+}
+
+// power of a splat at a pixel centre; the centre is (a.x + b.w, a.y + c.x),
+// high part subtracted first so the offset keeps its precision.
+__device__ __forceinline__ float splat_power(const float4 a, const float4 b, float vlo, float fx, float fy) {
   const float dx = (fx - a.x) - b.w, dy = (fy - a.y) - vlo;
-  const float power = -0.5f * (b.x * dx * dx + b.z * dy * dy) - b.y * dx * dy;
-  if (power > 0.f || power < kSkipPower) return false;
-  beta = __expf(power);
-  alpha = fminf(amax, a.z * beta);
-  return alpha >= amin;
+  return -0.5f * (b.x * dx * dx + b.z * dy * dy) - b.y * dx * dy;
 }
 
 // ---------------------------------------------------------------------------
 // K6: shadow composite.
 // For every shadow ray m (light pixel) and every list entry j that passes the
 // alpha test, T_m(j) = prod (1 - alpha_k,m) over passing k with
-// d_k < d_j - bias.  The list is ordered by distance, so the occluder set of
-// j is a prefix of the list; an occluder cursor k trails the receiver cursor
-// j and advances, block-uniformly, while d_k < d_j - bias.  Each thread keeps
-// its ray's product over the consumed occluders.  Per receiver the block sums
-// beta T_m and beta over its 256 rays (warp shuffles, then 8 warps in fixed
-// order) and writes one (num, den) partial for the (tile, Gaussian) pair.
+// d_k < d_j - bias.  The list is ordered by distance, so the occluders of j
+// form a prefix of the tile's list; its end K(j) is precomputed per entry
+// (k_occluder_bound) and is non-decreasing in j.
+//
+// 128 threads per 16x16 tile, two pixels per thread: warp w owns the 8x8
+// block at (8 (w & 1), 8 (w >> 1)), lane l the pixels (l & 7, l >> 3) and
+// (l & 7, (l >> 3) + 4) of it.  Receivers are staged 128 at a time, the
+// occluders they need through a window of up to kOccWin records; each thread
+// keeps its two rays' products A over the consumed occluders.  Records hold
+// the splat centre relative to the tile origin (pixel offsets are one exact
+// subtraction), the pre-scaled conic and a mask of the warps whose 8x8 block
+// the splat's alpha >= alpha_min box reaches; other warps skip the entry.
+// Per receiver each warp sums (beta A, beta) over its 64 rays; the warps'
+// sums are added in fixed order into one (num, den) partial per
+// (tile, Gaussian) pair.
 // ---------------------------------------------------------------------------
+constexpr int kRecv = 128;
+constexpr int kOccWin = 512;
+constexpr int kShadowThreads = 128;
+
 struct ShadowParams {
   const uint32_t* list;
   const uint32_t* tile_start;
   const SplatRec* rrec;
   const uint32_t* off;
+  const uint32_t* kbound;
   float2* partial;
   int W, H, gx;
-  float bias, amin, amax;
+  float amax;
 };
 
-__global__ void __launch_bounds__(256) k_shadow(ShadowParams p) {
-  __shared__ float4 Ra[256], Rb[256];
-  __shared__ float Rc[256];
-  __shared__ uint32_t Rslot[256];
-  __shared__ float4 Oa[256], Ob[256];
-  __shared__ float Oc[256];
-  __shared__ float2 red[8][256];
+struct ShadowSmem {
+  float4 r0[kRecv], r1[kRecv];
+  uint32_t rk[kRecv], rslot[kRecv];
+  float4 o0[kOccWin], o1[kOccWin];
+  float2 red[4][kRecv];
+};
+
+// Bit w set when the splat's alpha >= alpha_min box can reach warp w's 8x8
+// block (tile-relative centre (ux, vy), half extents hx, hy).
+__device__ __forceinline__ uint32_t warp_mask8(float ux, float vy, float hx, float hy) {
+  if (!(hx >= 0.f)) return 0u;
+  uint32_t m = 0u;
+#pragma unroll
+  for (int w = 0; w < 4; ++w) {
+    const float x0 = (w & 1) * 8 + 0.5f, y0 = (w >> 1) * 8 + 0.5f;
+    const bool hit = (ux + hx >= x0) && (ux - hx <= x0 + 7.f) && (vy + hy >= y0) && (vy - hy <= y0 + 7.f);
+    m |= hit ? (1u << w) : 0u;
+  }
+  return m;
+}
+
+// e0 = (ux, vy, -A/2, -C/2) centre relative to the tile origin (ox, oy);
+// e1 = (-B, pthr, gamma, warp mask bits)
+__device__ __forceinline__ void make_entry(const SplatRec& q, float ox, float oy, float4& e0, float4& e1) {
+  const float ux = (q.a.x - ox) + q.b.w, vy = (q.a.y - oy) + q.c.x;
+  const uint32_t m = warp_mask8(ux, vy, q.c.y, q.c.z);
+  e0 = make_float4(ux, vy, -0.5f * q.b.x, -0.5f * q.b.z);
+  e1 = make_float4(-q.b.y, q.c.w, q.a.z, __uint_as_float(m));
+}
+
+__device__ __forceinline__ float power_at(const float4 e0, float r, float lx, float ly) {
+  const float dx = lx - e0.x, dy = ly - e0.y;
+  return fmaf(dx, fmaf(e0.z, dx, r * dy), (e0.w * dy) * dy);
+}
+
+__global__ void __launch_bounds__(kShadowThreads, 8) k_shadow(ShadowParams p) {
+  extern __shared__ float4 smem_raw[];
+  ShadowSmem& S = *reinterpret_cast<ShadowSmem*>(smem_raw);
   const int tile = blockIdx.x;
   const int tx = tile % p.gx, ty = tile / p.gx;
+  const float ox = (float)(tx * kTile), oy = (float)(ty * kTile);
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-  const int px = tx * kTile + (t & 15), py = ty * kTile + (t >> 4);
-  const bool inside = px < p.W && py < p.H;
-  const float fx = px + 0.5f, fy = py + 0.5f;
+  const uint32_t wbit = 1u << warp;
+  const int lxi = (warp & 1) * 8 + (lane & 7), lyi = (warp >> 1) * 8 + (lane >> 3);
+  const float lx = lxi + 0.5f, ly0 = lyi + 0.5f, ly1 = lyi + 4.5f;
+  const bool in0 = tx * kTile + lxi < p.W && ty * kTile + lyi < p.H;
+  const bool in1 = tx * kTile + lxi < p.W && ty * kTile + lyi + 4 < p.H;
+  const bool hi_lane = (lane & 16) != 0;
+  const float amax = p.amax;
   const uint32_t b = p.tile_start[tile], e = p.tile_start[tile + 1];
-  float A = 1.f;
-  uint32_t k = b, ob = b, oc = 0;
-  for (uint32_t rb = b; rb < e; rb += 256) {
-    const int rc = (int)min(256u, e - rb);
-    __syncthreads();
+  float A0 = 1.f, A1 = 1.f;
+  uint32_t k = b;
+  for (uint32_t rb = b; rb < e; rb += kRecv) {
+    const int rc = (int)min((uint32_t)kRecv, e - rb);
+    __syncthreads();  // previous receivers fully reduced and written
     if (t < rc) {
       const uint32_t rank = p.list[rb + t];
       const SplatRec q = p.rrec[rank];
-      Ra[t] = q.a;
-      Rb[t] = q.b;
-      Rc[t] = q.c.x;
-      Rslot[t] = p.off[rank] + (uint32_t)((ty - q.r.y) * (q.r.z - q.r.x + 1) + (tx - q.r.x));
+      make_entry(q, ox, oy, S.r0[t], S.r1[t]);
+      S.rk[t] = p.kbound[rb + t];
+      S.rslot[t] = p.off[rank] + (uint32_t)((ty - q.r.y) * (q.r.z - q.r.x + 1) + (tx - q.r.x));
     }
     __syncthreads();
-    for (int jj = 0; jj < rc; ++jj) {
-      const float thr = __fsub_rn(Ra[jj].w, p.bias);
-      while (k < e) {
-        if (k >= ob + oc) {
-          __syncthreads();
-          ob = k;
-          oc = min(256u, e - k);
-          if (t < (int)oc) {
-            const SplatRec q = p.rrec[p.list[ob + t]];
-            Oa[t] = q.a;
-            Ob[t] = q.b;
-            Oc[t] = q.c.x;
+    const uint32_t klast = S.rk[rc - 1];
+    int jj = 0;
+    while (jj < rc) {
+      const uint32_t kt = min(klast, k + (uint32_t)kOccWin);
+      __syncthreads();  // the previous window is consumed
+      for (uint32_t i = t; i < kt - k; i += kShadowThreads) make_entry(p.rrec[p.list[k + i]], ox, oy, S.o0[i], S.o1[i]);
+      __syncthreads();
+      const uint32_t ow = k;
+      for (; jj < rc; ++jj) {
+        const uint32_t kend = S.rk[jj];
+        if (kend > kt) break;
+        for (; k < kend; ++k) {
+          const float4 o1 = S.o1[k - ow];
+          if (__float_as_uint(o1.w) & wbit) {
+            const float4 o0 = S.o0[k - ow];
+            const float p0 = power_at(o0, o1.x, lx, ly0), p1 = power_at(o0, o1.x, lx, ly1);
+            if (p0 >= o1.y && p0 <= 0.f) A0 *= 1.f - fminf(amax, o1.z * __expf(p0));
+            if (p1 >= o1.y && p1 <= 0.f) A1 *= 1.f - fminf(amax, o1.z * __expf(p1));
           }
-          __syncthreads();
         }
-        const float4 oa = Oa[k - ob];
-        if (!(oa.w < thr)) break;
-        float beta, alpha;
-        if (splat_alpha(oa, Ob[k - ob], Oc[k - ob], fx, fy, p.amin, p.amax, beta, alpha)) A *= 1.f - alpha;
-        ++k;
-      }
-      float beta = 0.f, alpha;
-      const bool pass = inside && splat_alpha(Ra[jj], Rb[jj], Rc[jj], fx, fy, p.amin, p.amax, beta, alpha);
-      float cn = pass ? beta * A : 0.f, cd = pass ? beta : 0.f;
-      if (__any_sync(0xffffffffu, pass)) {
+        const float4 r1 = S.r1[jj];
+        if (__float_as_uint(r1.w) & wbit) {
+          const float4 r0 = S.r0[jj];
+          const float p0 = power_at(r0, r1.x, lx, ly0), p1 = power_at(r0, r1.x, lx, ly1);
+          const float b0 = (in0 && p0 >= r1.y && p0 <= 0.f) ? __expf(p0) : 0.f;
+          const float b1 = (in1 && p1 >= r1.y && p1 <= 0.f) ? __expf(p1) : 0.f;
+          const float num = fmaf(b0, A0, b1 * A1), den = b0 + b1;
+          // two sums with one butterfly: lanes 0-15 end with num, 16-31 with den
+          float v = (hi_lane ? den : num) + __shfl_xor_sync(0xffffffffu, hi_lane ? num : den, 16);
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          cn += __shfl_xor_sync(0xffffffffu, cn, o);
-          cd += __shfl_xor_sync(0xffffffffu, cd, o);
+          for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+          if (lane == 0) S.red[warp][jj].x = v;
+          if (lane == 16) S.red[warp][jj].y = v;
         }
       }
-      if (lane == 0) red[warp][jj] = make_float2(cn, cd);
+      for (; k < kt; ++k) {  // the next receiver needs occluders past this window
+        const float4 o1 = S.o1[k - ow];
+        if (__float_as_uint(o1.w) & wbit) {
+          const float4 o0 = S.o0[k - ow];
+          const float p0 = power_at(o0, o1.x, lx, ly0), p1 = power_at(o0, o1.x, lx, ly1);
+          if (p0 >= o1.y && p0 <= 0.f) A0 *= 1.f - fminf(amax, o1.z * __expf(p0));
+          if (p1 >= o1.y && p1 <= 0.f) A1 *= 1.f - fminf(amax, o1.z * __expf(p1));
+        }
+      }
     }
     __syncthreads();
     if (t < rc) {
-      float2 s = red[0][t];
+      const uint32_t m = __float_as_uint(S.r1[t].w);
+      float2 sum = make_float2(0.f, 0.f);
 #pragma unroll
-      for (int w = 1; w < 8; ++w) { s.x += red[w][t].x; s.y += red[w][t].y; }
-      p.partial[Rslot[t]] = s;
+      for (int w = 0; w < 4; ++w)
+        if (m & (1u << w)) { sum.x += S.red[w][t].x; sum.y += S.red[w][t].y; }
+      p.partial[S.rslot[t]] = sum;
     }
+  }
+}
+
+// K(i) for every entry i of the light lists: the first index of i's tile
+// segment whose distance is >= d_i - bias (the end of i's occluder prefix).
+__global__ void __launch_bounds__(256) k_gather_depth(const uint32_t* __restrict__ list,
+                                                      const SplatRec* __restrict__ rrec,
+                                                      const uint32_t* header, float* __restrict__ dl,
+                                                      uint32_t limit) {
+  const uint32_t P = min(header[H_PAIRS_LIGHT], limit);
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < P; i += gridDim.x * blockDim.x)
+    dl[i] = rrec[list[i]].a.w;
+}
+
+__global__ void __launch_bounds__(256) k_occluder_bound(const uint32_t* __restrict__ keys,
+                                                        const uint32_t* __restrict__ tile_start,
+                                                        const float* __restrict__ dl, const uint32_t* header,
+                                                        float bias, uint32_t* __restrict__ kb, uint32_t limit) {
+  const uint32_t P = min(header[H_PAIRS_LIGHT], limit);
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < P; i += gridDim.x * blockDim.x) {
+    const float thr = __fsub_rn(dl[i], bias);
+    uint32_t lo = tile_start[keys[i]], hi = i;
+    while (lo < hi) {
+      const uint32_t mid = (lo + hi) >> 1;
+      if (dl[mid] < thr) lo = mid + 1; else hi = mid;
+    }
+    kb[i] = lo;
   }
 }
 
@@ -164,16 +268,17 @@ struct CamParams {
   float* final_t;
   uint32_t* n_contrib;
   int W, H, gx;
-  float amin, amax, tstop;
+  float amax, tstop;
 };
 
 __global__ void __launch_bounds__(256) k_camera(CamParams p) {
-  __shared__ float4 Ga[256], Gb[256], C0[256], C1[256];
-  __shared__ float Gc[256];
+  __shared__ float4 Ga[256], Gb[256], Gc[256], C0[256], C1[256];
+  __shared__ uint32_t Gmask[256];
   const int tile = blockIdx.x;
   const int tx = tile % p.gx, ty = tile / p.gx;
   const int t = threadIdx.x;
-  const int px = tx * kTile + (t & 15), py = ty * kTile + (t >> 4);
+  const uint32_t wbit = 1u << (t >> 5);
+  const int px = tx * kTile + tile_px(t), py = ty * kTile + tile_py(t);
   const bool inside = px < p.W && py < p.H;
   const float fx = px + 0.5f, fy = py + 0.5f;
   const uint32_t b = p.tile_start[tile], e = p.tile_start[tile + 1];
@@ -188,20 +293,23 @@ __global__ void __launch_bounds__(256) k_camera(CamParams p) {
       const SplatRec q = p.rrec[rank];
       Ga[t] = q.a;
       Gb[t] = q.b;
-      Gc[t] = q.c.x;
+      Gc[t] = q.c;
+      Gmask[t] = warp_mask(q, tx, ty);
       C0[t] = p.ccol[2 * rank];
       C1[t] = p.ccol[2 * rank + 1];
     }
     __syncthreads();
     if (!done) {
       for (int jj = 0; jj < rc; ++jj) {
-        consumed = rb - b + jj + 1;
-        float beta, alpha;
-        if (!splat_alpha(Ga[jj], Gb[jj], Gc[jj], fx, fy, p.amin, p.amax, beta, alpha)) continue;
+        if (!(Gmask[jj] & wbit)) continue;
+        const float4 ga = Ga[jj], gc = Gc[jj];
+        const float pw = splat_power(ga, Gb[jj], gc.x, fx, fy);
+        if (!(pw >= gc.w && pw <= 0.f)) continue;
+        const float alpha = fminf(p.amax, ga.z * __expf(pw));
         const float Tn = T * (1.f - alpha);
         if (Tn < p.tstop) {
           done = true;
-          consumed -= 1;
+          consumed = rb - b + jj;
           break;
         }
         const float w = alpha * T;
@@ -211,6 +319,7 @@ __global__ void __launch_bounds__(256) k_camera(CamParams p) {
         R0 += w * c1.x; R1 += w * c1.y; R2 += w * c1.z;
         T = Tn;
       }
+      if (!done) consumed = rb - b + rc;
     }
   }
   if (inside) {
@@ -229,15 +338,32 @@ void launch_shadow_composite(const FrameArgs& f, cudaStream_t s) {
   const SplatBufs& b = f.L->sp[1];
   unsigned char* ws = f.ws;
   const int fin = (f.L->ntiles <= 256 ? 1 : 2) & 1;
+  // the non-final tile-sort buffers are free after the sort: depth per entry, occluder bound
+  float* dl = at<float>(ws, b.tk[1 - fin]);
+  uint32_t* kb = at<uint32_t>(ws, b.tv[1 - fin]);
+  const uint32_t* header = at<uint32_t>(ws, f.L->header);
+  int blocks = (int)((f.L->cap + 255) / 256);
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  k_gather_depth<<<blocks, 256, 0, s>>>(at<uint32_t>(ws, b.tv[fin]), at<SplatRec>(ws, b.rrec), header, dl,
+                                        (uint32_t)f.L->cap);
+  k_occluder_bound<<<blocks, 256, 0, s>>>(at<uint32_t>(ws, b.tk[fin]), at<uint32_t>(ws, b.tile_start), dl, header,
+                                          f.opts.shadow_bias, kb, (uint32_t)f.L->cap);
+  count_launch(2);
   ShadowParams p;
   p.list = at<uint32_t>(ws, b.tv[fin]);
   p.tile_start = at<uint32_t>(ws, b.tile_start);
   p.rrec = at<SplatRec>(ws, b.rrec);
   p.off = at<uint32_t>(ws, b.off);
+  p.kbound = kb;
   p.partial = at<float2>(ws, f.L->partial);
   p.W = f.L->width; p.H = f.L->height; p.gx = f.L->gx;
-  p.bias = f.opts.shadow_bias; p.amin = f.opts.alpha_min; p.amax = f.opts.alpha_max;
-  k_shadow<<<f.L->ntiles, 256, 0, s>>>(p);
+  p.amax = f.opts.alpha_max;
+  static bool configured = false;
+  if (!configured) {
+    cudaFuncSetAttribute(k_shadow, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(ShadowSmem));
+    configured = true;
+  }
+  k_shadow<<<f.L->ntiles, kShadowThreads, sizeof(ShadowSmem), s>>>(p);
   count_launch();
 }
 
@@ -270,7 +396,7 @@ void launch_camera_composite(const FrameArgs& f, float* out_rgb, cudaStream_t s)
   p.final_t = at<float>(ws, f.L->final_t);
   p.n_contrib = at<uint32_t>(ws, f.L->n_contrib);
   p.W = f.L->width; p.H = f.L->height; p.gx = f.L->gx;
-  p.amin = f.opts.alpha_min; p.amax = f.opts.alpha_max; p.tstop = f.opts.t_stop;
+  p.amax = f.opts.alpha_max; p.tstop = f.opts.t_stop;
   k_camera<<<f.L->ntiles, 256, 0, s>>>(p);
   count_launch();
 }

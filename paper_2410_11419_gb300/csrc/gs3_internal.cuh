@@ -21,7 +21,9 @@ constexpr int kMaxLobes = 16;
 // Per-Gaussian splat record (one per splat, by Gaussian index or by rank).
 //   a = (u_hi, v_hi, opacity, depth)  screen position (high part), gamma, FP32 sort depth
 //   b = (A, B, C, u_lo)               conic: power = -0.5 (A dx^2 + C dy^2) - B dx dy
-//   c = (v_lo, 0, 0, 0)               low parts: u = u_hi + u_lo, v = v_hi + v_lo
+//   c = (v_lo, hx, hy, pthr)          v = v_hi + v_lo; half extents of the box holding
+//                                     every pixel with alpha >= alpha_min; power threshold
+//                                     ln(alpha_min / gamma) (alpha >= alpha_min <=> power >= pthr)
 //   r = (x0, y0, x1, y1)              inclusive tile rectangle, x0 < 0 when culled
 struct __align__(16) SplatRec {
   float4 a;

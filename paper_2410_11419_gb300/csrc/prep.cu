@@ -53,11 +53,11 @@ struct View {
 };
 
 __device__ void accurate_geometry(const float4 m, const float Rq[9], const float sv[3], const View& v,
-                                  float lowpass, SplatRec& rec);
+                                  float lowpass, float gamma, float amin, SplatRec& rec);
 
 // FP32 recipe: returns false when culled; fills the record otherwise.
 __device__ bool project_rn(const float4 m, const float4 s, const float4 q, const View& v,
-                           const gs3_render_opts& o, int gx, int gy, const float* pL,
+                           const gs3_render_opts& o, int gx, int gy, const float* pL, float gamma,
                            SplatRec& rec) {
   const float* R = v.R;
   float tx = A_(dot3_rn(R[0], R[1], R[2], m.x, m.y, m.z), v.t[0]);
@@ -132,7 +132,7 @@ __device__ bool project_rn(const float4 m, const float4 s, const float4 q, const
   } else {
     depth = tz;
   }
-  accurate_geometry(m, Rq, sv, v, o.lowpass, rec);
+  accurate_geometry(m, Rq, sv, v, o.lowpass, gamma, o.alpha_min, rec);
   rec.a.w = depth;
   return true;
 }
@@ -153,7 +153,7 @@ __device__ __forceinline__ float minor_fma(float a, float b, float c, float d) {
 }
 
 __device__ void accurate_geometry(const float4 m, const float Rq[9], const float sv[3], const View& v,
-                                  float lowpass, SplatRec& rec) {
+                                  float lowpass, float gamma, float amin, SplatRec& rec) {
   const float* R = v.R;
   const double tx = (double)R[0] * m.x + (double)R[1] * m.y + (double)R[2] * m.z + (double)v.t[0];
   const double ty = (double)R[3] * m.x + (double)R[4] * m.y + (double)R[5] * m.z + (double)v.t[1];
@@ -187,9 +187,19 @@ __device__ void accurate_geometry(const float4 m, const float Rq[9], const float
   const float m2 = minor_fma(P0[0], P0[1], P1[0], P1[1]);
   const float det = fmaf(m0, m0, fmaf(m1, m1, m2 * m2)) + lowpass * (a0 + c0) + lowpass * lowpass;
   const float a = a0 + lowpass, c = c0 + lowpass;
-  rec.a = make_float4(uh, vh, 0.f, 0.f);
+  rec.a = make_float4(uh, vh, gamma, 0.f);
   rec.b = make_float4(c / det, -b / det, a / det, ul);
-  rec.c = make_float4(vl, 0.f, 0.f, 0.f);
+  // alpha >= amin  <=>  power >= ln(amin / gamma)  <=>  d^T conic d <= r2 = 2 ln(gamma / amin);
+  // that ellipse lies inside |dx| <= sqrt(r2 a), |dy| <= sqrt(r2 c) (Sigma_2D = [[a, b], [b, c]]).
+  // The box is widened by 0.1 % + 0.01 px so rounding never drops a passing pixel.
+  const float pthr = logf(amin / gamma);
+  const float r2 = -2.f * pthr;
+  float hx = -1.f, hy = -1.f;
+  if (r2 > 0.f) {
+    hx = sqrtf(r2 * a) * 1.001f + 0.01f;
+    hy = sqrtf(r2 * c) * 1.001f + 0.01f;
+  }
+  rec.c = make_float4(vl, hx, hy, pthr);
 }
 
 __device__ __forceinline__ void quat_mat(float4 q, float Rm[9]) {
@@ -255,7 +265,7 @@ __global__ void __launch_bounds__(256) k_prep(PrepParams p) {
   const float4 m = p.sc.mean_op[g];
   const float4 s = p.sc.scale[g];
   const float4 q = p.sc.rot[g];
-  const float gamma = 1.f / (1.f + __expf(-m.w));
+  const float gamma = 1.f / (1.f + expf(-m.w));
 
   View lv = p.cam;
 #pragma unroll
@@ -266,7 +276,7 @@ __global__ void __launch_bounds__(256) k_prep(PrepParams p) {
 #pragma unroll
   for (int sp = 0; sp < 2; ++sp) {
     SplatRec rec;
-    bool vis = project_rn(m, s, q, sp ? lv : p.cam, p.o, p.gx, p.gy, sp ? p.light_pos : nullptr, rec);
+    bool vis = project_rn(m, s, q, sp ? lv : p.cam, p.o, p.gx, p.gy, sp ? p.light_pos : nullptr, gamma, rec);
     if (!vis) {
       rec.a = make_float4(0.f, 0.f, 0.f, 0.f);
       rec.b = make_float4(0.f, 0.f, 0.f, 0.f);
