@@ -204,6 +204,32 @@ gs3_status gs3_render_stages(gs3_scene *scene, const gs3_camera *camera, const g
 /* Copy the workspace header to `out` (host) and synchronise `stream`. */
 gs3_status gs3_workspace_read_header(const void *workspace, gs3_ws_header *out, void *stream);
 
+/* ---- Depth sort without allocation --------------------------------------
+ * The paper has no counterpart to this entry point; it serves callers that
+ * may not allocate device memory at all: a renderer embedded in a host
+ * application that owns the GPU's memory budget, or a real-time loop that
+ * must never risk an allocation stall or an out-of-memory failure in the
+ * middle of a frame.  It is the per-splat depth sort of gs3_render (stable
+ * ascending order of 32-bit keys, the FP32 depth or light-distance bits) with
+ * its scratch in a file-scope device array of GS3_STATIC_SORT_MAX_KEYS keys
+ * (about 12.3 MB), which every GPU that loads the library holds until exit.
+ *   keys:      device, uint32[n], read only
+ *   order_out: device, uint32[n], caller-owned; receives the permutation
+ *              order_out[r] = position of the r-th smallest key (ties in
+ *              input order), the same as the workspace `order` of gs3_render
+ *   n:         0 <= n <= GS3_STATIC_SORT_MAX_KEYS; larger n returns
+ *              GS3_ERR_INVALID_ARG (message in gs3_last_error) and launches
+ *              nothing
+ * Calls no cudaMalloc, cudaFree or other allocating routine.  The first call
+ * on a device, with that device current, looks up the array's device address
+ * (cudaGetSymbolAddress) and caches it; make that first call before any
+ * stream capture.  Every call on a device shares the one array: calls whose
+ * work overlaps on the GPU (other streams, other host threads) race and must
+ * be serialised by the caller.  Nothing in the array needs to start at zero:
+ * each pass overwrites all scratch it reads. */
+#define GS3_STATIC_SORT_MAX_KEYS 1048576u
+gs3_status gs3_depth_order_static(const uint32_t *keys, uint32_t n, uint32_t *order_out, void *stream);
+
 /* Number of CUDA kernels this library has launched in this process (all
  * threads, all devices); a host-side counter for launch accounting. */
 uint64_t gs3_kernel_launches(void);

@@ -98,6 +98,7 @@ SIGNATURES = {
                                     C.POINTER(gs3_render_opts), C.c_void_p, C.c_void_p, C.c_size_t,
                                     C.c_size_t, C.c_uint32, C.c_void_p]),
     "gs3_workspace_read_header": (C.c_int, [C.c_void_p, C.POINTER(gs3_ws_header), C.c_void_p]),
+    "gs3_depth_order_static": (C.c_int, [C.c_void_p, C.c_uint32, C.c_void_p, C.c_void_p]),
     "gs3_kernel_launches": (C.c_uint64, []),
     "gs3_last_error": (C.c_char_p, []),
 }
@@ -180,6 +181,14 @@ def gs3_workspace_read_header(workspace, stream: int) -> gs3_ws_header:
     _check(lib().gs3_workspace_read_header(_ptr(workspace), C.byref(h), stream),
            "gs3_workspace_read_header")
     return h
+
+
+GS3_STATIC_SORT_MAX_KEYS = 1048576
+
+
+def gs3_depth_order_static(keys, n: int, order_out, stream: int) -> None:
+    _check(lib().gs3_depth_order_static(_ptr(keys), n, _ptr(order_out), stream),
+           "gs3_depth_order_static")
 
 
 def gs3_kernel_launches() -> int:

@@ -52,6 +52,8 @@ bool mlp_ok(const gs3_mlp_desc& m, int in_dim, int out_dim) {
 
 }  // namespace
 
+void set_last_error(const char* msg) { g_last_error = msg; }
+
 Workspace plan_workspace(int n, int width, int height, size_t cap) {
   Workspace L;
   L.n = n;

@@ -111,6 +111,16 @@ void device_exclusive_scan(const uint32_t* in, uint32_t* out, uint32_t n, uint32
                            uint32_t* scratch, cudaStream_t s);
 size_t scan_scratch_words(size_t n);
 
+// stable LSD radix sort of n (key, value) pairs on the low 8 * passes key bits
+// (vin null: values are the input positions); the result lands in (k1, v1)
+// for an even number of passes, (k0, v0) for an odd one
+void radix_sort_pairs(const uint32_t* kin, const uint32_t* vin, uint32_t* k0, uint32_t* v0, uint32_t* k1,
+                      uint32_t* v1, uint32_t n, int passes, uint32_t* hist, uint32_t* scan_part,
+                      cudaStream_t s);
+
+// sets the message gs3_last_error returns on this thread
+void set_last_error(const char* msg);
+
 // host-side count of kernel launches (reported by gs3_kernel_launches)
 extern std::atomic<uint64_t> g_launches;
 inline void count_launch(int n = 1) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }

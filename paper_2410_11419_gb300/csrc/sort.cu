@@ -286,6 +286,13 @@ void radix_sort(const uint32_t* kin, const uint32_t* vin, uint32_t* k0, uint32_t
 
 size_t scan_scratch_words(size_t n) { return (n + kScanItems - 1) / kScanItems + 1; }
 
+void radix_sort_pairs(const uint32_t* kin, const uint32_t* vin, uint32_t* k0, uint32_t* v0, uint32_t* k1,
+                      uint32_t* v1, uint32_t n, int passes, uint32_t* hist, uint32_t* scan_part,
+                      cudaStream_t s) {
+  const int nblocks = (int)((n + kSortTileItems - 1) / kSortTileItems);
+  radix_sort(kin, vin, k0, v0, k1, v1, nullptr, n, nblocks, passes, hist, scan_part, s);
+}
+
 void device_exclusive_scan(const uint32_t* in, uint32_t* out, uint32_t n, uint32_t* total,
                            uint32_t* scratch, cudaStream_t s) {
   const uint32_t nb = (n + kScanItems - 1) / kScanItems;

@@ -1,0 +1,80 @@
+// gs3_depth_order_static: the per-splat depth sort with its scratch memory in
+// a file-scope device array instead of a caller workspace, for callers that
+// may not allocate device memory.
+#include <mutex>
+#include <string>
+
+#include "gs3_internal.cuh"
+
+namespace gs3 {
+namespace {
+
+constexpr uint32_t kStaticMaxKeys = GS3_STATIC_SORT_MAX_KEYS;
+constexpr int kStaticBlocks = (int)((kStaticMaxKeys + kSortTileItems - 1) / kSortTileItems);
+constexpr size_t kStaticHistWords = 256ull * kStaticBlocks;
+constexpr size_t kStaticScanWords = 256;  // >= scan_scratch_words(kStaticHistWords), padded
+// ping-pong keys and values (3 of the 4 arrays; the caller's output is the 4th),
+// radix histogram, scan partial sums
+constexpr size_t kStaticWords = 3ull * kStaticMaxKeys + kStaticHistWords + kStaticScanWords;
+
+static __device__ __align__(256) uint32_t g_static_scratch[kStaticWords];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_mu;
+uint32_t* g_scratch_addr[kMaxDevices] = {};
+
+
+}  // namespace
+}  // namespace gs3
+
+using namespace gs3;
+
+extern "C" gs3_status gs3_depth_order_static(const uint32_t* keys, uint32_t n, uint32_t* order_out,
+                                             void* stream) {
+  static_assert(kStaticScanWords >= (kStaticHistWords + kScanItems - 1) / kScanItems + 1,
+                "scan scratch too small");
+  if (n == 0) return GS3_OK;
+  if (!keys || !order_out) {
+    set_last_error("gs3_depth_order_static: null keys or order_out");
+    return GS3_ERR_INVALID_ARG;
+  }
+  if (n > kStaticMaxKeys) {
+    set_last_error("gs3_depth_order_static: n exceeds GS3_STATIC_SORT_MAX_KEYS (1048576)");
+    return GS3_ERR_INVALID_ARG;
+  }
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    set_last_error("gs3_depth_order_static: no usable current device");
+    return GS3_ERR_CUDA;
+  }
+  uint32_t* base = nullptr;
+  {
+    // once per device, with that device current: the host-side symbol is only
+    // a stand-in, the kernels need the device address of the array
+    std::lock_guard<std::mutex> lock(g_mu);
+    if (!g_scratch_addr[dev]) {
+      void* p = nullptr;
+      if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess || !p) {
+        set_last_error("gs3_depth_order_static: cudaGetSymbolAddress of the scratch array failed");
+        return GS3_ERR_CUDA;
+      }
+      g_scratch_addr[dev] = static_cast<uint32_t*>(p);
+    }
+    base = g_scratch_addr[dev];
+  }
+  uint32_t* k0 = base;
+  uint32_t* v0 = base + kStaticMaxKeys;
+  uint32_t* k1 = base + 2ull * kStaticMaxKeys;
+  uint32_t* hist = base + 3ull * kStaticMaxKeys;
+  uint32_t* scan = hist + kStaticHistWords;
+  // four 8-bit passes over the 32-bit keys; the odd passes write the values
+  // into the caller's output, so the last pass leaves the order there
+  radix_sort_pairs(keys, nullptr, k0, v0, k1, order_out, n, 4, hist, scan,
+                   reinterpret_cast<cudaStream_t>(stream));
+  count_launch(4 * 5);
+  if (cudaGetLastError() != cudaSuccess) {
+    set_last_error("gs3_depth_order_static: kernel launch failed");
+    return GS3_ERR_CUDA;
+  }
+  return GS3_OK;
+}
