@@ -9,6 +9,7 @@
 
 struct gs3_scene {
   gs3::SceneDev dev;
+  unsigned char* tc_blob[2] = {nullptr, nullptr};  // BF16 tensor-core weights (owned)
 };
 
 namespace gs3 {
@@ -143,8 +144,8 @@ gs3_status gs3_create_scene(const gs3_scene_desc* d, gs3_scene** out) {
     return fail(GS3_ERR_INVALID_ARG, "gs3_create_scene: null lobe array");
   if (!mlp_ok(d->phi, 61, 1)) return fail(GS3_ERR_INVALID_ARG, "gs3_create_scene: unsupported Phi shape");
   if (!mlp_ok(d->psi, 60, 3)) return fail(GS3_ERR_INVALID_ARG, "gs3_create_scene: unsupported Psi shape");
-  if (d->mlp_dtype != GS3_MLP_FP32)
-    return fail(GS3_ERR_UNSUPPORTED, "gs3_create_scene: only GS3_MLP_FP32 is available in this build");
+  if (d->mlp_dtype != GS3_MLP_FP32 && d->mlp_dtype != GS3_MLP_BF16)
+    return fail(GS3_ERR_INVALID_ARG, "gs3_create_scene: mlp_dtype must be GS3_MLP_FP32 or GS3_MLP_BF16");
   gs3_scene* s = new (std::nothrow) gs3_scene;
   if (!s) return fail(GS3_ERR_OOM, "gs3_create_scene: host allocation failed");
   SceneDev& v = s->dev;
@@ -164,11 +165,35 @@ gs3_status gs3_create_scene(const gs3_scene_desc* d, gs3_scene** out) {
   v.phi = {d->phi.in_dim, d->phi.width, d->phi.n_hidden, d->phi.out_dim, d->phi.act, d->phi.w, d->phi.b};
   v.psi = {d->psi.in_dim, d->psi.width, d->psi.n_hidden, d->psi.out_dim, d->psi.act, d->psi.w, d->psi.b};
   v.mlp_dtype = d->mlp_dtype;
+  if (d->mlp_dtype == GS3_MLP_BF16) {
+    for (int w = 0; w < 2; ++w) {
+      const MlpDev& m = w == 0 ? v.phi : v.psi;
+      if (!mlp_tc_supported(m)) {
+        gs3_destroy_scene(s);
+        return fail(GS3_ERR_UNSUPPORTED, "gs3_create_scene: MLP shape not supported by the BF16 path");
+      }
+      if (cudaMalloc(&s->tc_blob[w], mlp_tc_blob_bytes(m)) != cudaSuccess) {
+        s->tc_blob[w] = nullptr;
+        gs3_destroy_scene(s);
+        return fail(GS3_ERR_OOM, "gs3_create_scene: BF16 weight allocation failed");
+      }
+      pack_mlp_tc(m, s->tc_blob[w], 0);
+    }
+    cudaError_t e = cudaStreamSynchronize(0);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) {
+      gs3_destroy_scene(s);
+      return cuda_fail(e, "gs3_create_scene: BF16 weight packing");
+    }
+  }
   *out = s;
   return GS3_OK;
 }
 
 gs3_status gs3_destroy_scene(gs3_scene* s) {
+  if (!s) return GS3_OK;
+  for (int w = 0; w < 2; ++w)
+    if (s->tc_blob[w]) cudaFree(s->tc_blob[w]);
   delete s;
   return GS3_OK;
 }
@@ -251,7 +276,15 @@ gs3_status gs3_render_stages(gs3_scene* scene, const gs3_camera* cam, const gs3_
     if (no_shadow) launch_fill_shadow_one(f, s);
     else launch_shadow_reduce(f, s);
   }
-  if (stages & GS3_STAGE_MLP) launch_mlp(f, s);
+  if (stages & GS3_STAGE_MLP) {
+    if (scene->dev.mlp_dtype == GS3_MLP_BF16) {
+      launch_mlp(f, s, /*identity_only=*/true);
+      const unsigned char* blobs[2] = {scene->tc_blob[0], scene->tc_blob[1]};
+      launch_mlp_tc(f, blobs, s);
+    } else {
+      launch_mlp(f, s);
+    }
+  }
   if (stages & GS3_STAGE_CAMERA) launch_camera_composite(f, out_rgb, s);
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "gs3_render: launch");

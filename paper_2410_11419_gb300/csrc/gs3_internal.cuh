@@ -101,7 +101,12 @@ void launch_depth_sort(const FrameArgs& f, int splat, cudaStream_t s);
 void launch_binning(const FrameArgs& f, int splat, cudaStream_t s);
 void launch_shadow_composite(const FrameArgs& f, cudaStream_t s);
 void launch_shadow_reduce(const FrameArgs& f, cudaStream_t s);
-void launch_mlp(const FrameArgs& f, cudaStream_t s);
+void launch_mlp(const FrameArgs& f, cudaStream_t s, bool identity_only = false);
+// BF16 tensor-core MLPs (mlp_tc.cu)
+size_t mlp_tc_blob_bytes(const MlpDev& m);
+size_t pack_mlp_tc(const MlpDev& m, unsigned char* dst, cudaStream_t s);
+bool mlp_tc_supported(const MlpDev& m);
+void launch_mlp_tc(const FrameArgs& f, const unsigned char* const blobs[2], cudaStream_t s);
 void launch_camera_composite(const FrameArgs& f, float* out_rgb, cudaStream_t s);
 void launch_fill_shadow_one(const FrameArgs& f, cudaStream_t s);
 

@@ -185,7 +185,7 @@ void launch_one(const MlpParams& p, cudaStream_t s) {
 
 }  // namespace
 
-void launch_mlp(const FrameArgs& f, cudaStream_t s) {
+void launch_mlp(const FrameArgs& f, cudaStream_t s, bool identity_only) {
   MlpParams p;
   p.n = f.sc.n;
   p.mean_op = f.sc.mean_op;
@@ -199,13 +199,13 @@ void launch_mlp(const FrameArgs& f, cudaStream_t s) {
   p.which = 0;
   p.out_idx = at<float>(f.ws, f.L->Tp);
   p.identity = (f.opts.ablate & GS3_ABLATE_PHI) != 0;
-  launch_one(p, s);
+  if (p.identity || !identity_only) launch_one(p, s);
 
   p.net = f.sc.psi;
   p.which = 1;
   p.out_idx = at<float>(f.ws, f.L->res);
   p.identity = (f.opts.ablate & GS3_ABLATE_PSI) != 0;
-  launch_one(p, s);
+  if (p.identity || !identity_only) launch_one(p, s);
 }
 
 }  // namespace gs3
