@@ -42,7 +42,11 @@ def parse():
     ap.add_argument("--impl", default="gs3", choices=["gs3", "reference"])
     ap.add_argument("--n", type=int, default=300_000)
     ap.add_argument("--res", type=int, default=800)
-    ap.add_argument("--mlp", default="fp32", choices=["fp32", "bf16"])
+    ap.add_argument("--mlp", default="bf16", choices=["fp32", "bf16"],
+                    help="MLP precision of the timed arm (the other one is measured too)")
+    ap.add_argument("--no-plain", action="store_true", help="skip the FP32 plain comparison arm")
+    ap.add_argument("--profile-frames", type=int, default=0,
+                    help="render this many frames of the workload (no timing) and exit; for ncu")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-window", type=int, default=96, help="oracle window edge (pixels)")
     return ap.parse_args()
@@ -200,6 +204,16 @@ def main():
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
+    if a.profile_frames:
+        for i in range(a.profile_frames):
+            rd.render(*pairs[i % 100])
+        torch.cuda.synchronize()
+        h = rd.check()
+        print(json.dumps({"profile_frames": a.profile_frames, "pairs_cam": h.pairs_cam,
+                          "pairs_light": h.pairs_light}))
+        ds.close()
+        return
+
     groups = [("prep", N.GS3_STAGE_PREP), ("camera_bin", N.GS3_STAGE_CAMERA_BIN),
               ("light_bin", N.GS3_STAGE_LIGHT_BIN), ("shadow_composite", N.GS3_STAGE_SHADOW_COMPOSITE),
               ("shadow_reduce", N.GS3_STAGE_SHADOW_REDUCE), ("mlp", N.GS3_STAGE_MLP),
@@ -275,6 +289,32 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_val = world * K / float(t.item())
 
+    # ---- FP32 plain comparison arm (one request at a time, FP32 MLPs) ----
+    plain = None
+    if not a.no_plain:
+        other = N.GS3_MLP_FP32 if mlp_dtype == N.GS3_MLP_BF16 else N.GS3_MLP_BF16
+        ds2 = R.DeviceScene(scene, device=dev, mlp_dtype=other)
+        rd2 = R.Renderer(ds2, a.res, a.res, cap, device=dev)
+        for i in range(3):
+            rd2.render(*pairs[i % 100], opts)
+        torch.cuda.synchronize()
+        rd2.check()
+        pe = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+        mlp_ms = []
+        for s_ in range(K):
+            flush.zero_()
+            cam, light = pairs[(a.warmup + s_) % 100]
+            pe[s_][0].record(stream)
+            rd2.render(cam, light, opts)
+            pe[s_][1].record(stream)
+        torch.cuda.synchronize()
+        pms = np.array([x.elapsed_time(y) for x, y in pe])
+        plain = {"mlp": "fp32" if other == N.GS3_MLP_FP32 else "bf16", "value": K / (pms.sum() / 1e3),
+                 "unit": UNIT, "ms_per_step": float(pms.mean()), "p50_ms": float(np.percentile(pms, 50)),
+                 "p99_ms": float(np.percentile(pms, 99))}
+        del rd2
+        ds2.close()
+
     # ---- roofline of the dominant kernel ----
     ts = ts_host.numpy().astype(np.int64)
     gx = (a.res + 15) // 16
@@ -309,7 +349,7 @@ def main():
                 "work": "20 FLOP x entries consumed per pixel",
                 "peak_source": f"derived: {n_sm} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz"}
     elif dominant == "mlp":
-        flops = 2.0 * a.n * (61 * 128 + 2 * 128 * 128 + 128 + 60 * 128 + 2 * 128 * 128 + 3 * 128)
+        flops = 2.0 * a.n * (64 * 128 + 2 * 128 * 128 + 128 + 64 * 128 + 2 * 128 * 128 + 3 * 128)
         achieved = flops / (stage_ms[dominant] / 1e3) / 1e12
         roof = {"kernel": "k_mlp", "bound": "alu", "achieved": achieved, "peak": fp32_peak_tflops,
                 "unit": "TFLOP/s", "frac": achieved / fp32_peak_tflops, "traffic": None,
@@ -331,7 +371,8 @@ def main():
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
         "warmup": a.warmup, "ms_per_step": total_ms / K, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if a.mlp == "fp32" else "bf16+f32",
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if a.mlp == "fp32" else "bf16 MLP operands, f32 elsewhere",
         "data": "synthetic (seeded object scene, random-init MLPs)",
         "config": workload_config(a, a.mlp),
         "p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99)),
@@ -339,6 +380,7 @@ def main():
         "pairs_per_frame": {"camera": float(np.mean(per_step_cam_P)),
                             "light": float(np.mean(per_step_light_P))},
         "roofline": roof,
+        "comparison_arm": plain,
         "clocks": clk,
         "gpu_launches": int(launches),
         "wall_s_timed_region": wall,
