@@ -129,6 +129,7 @@ typedef struct {
     double *S, *Sh, *Rimg; /* composited shading (3), shadow (1), residual (3) images */
     int64_t shadow_evals, shadow_pass, camera_evals;
     int64_t amb_shadow, amb_camera;
+    int64_t camera_pass; /* (pixel, Gaussian) pairs composited by the camera rays */
     double t_prep, t_bin, t_shadow, t_mlp, t_camera; /* wall seconds per stage */
 } go_frame;
 
@@ -645,7 +646,7 @@ static void shadow_splat(go_frame *f, const go_opts *o)
 static void camera_composite(go_frame *f, const go_opts *o)
 {
     int W = f->width, H = f->height, ts = o->tile;
-    int64_t evals = 0, ambs = 0;
+    int64_t evals = 0, ambs = 0, cpass = 0;
     int wx0, wy0, wx1, wy1;
     window(o, W, H, &wx0, &wy0, &wx1, &wy1);
     for (size_t p = 0; p < (size_t)W * H; ++p) { /* outside the window: empty */
@@ -656,7 +657,7 @@ static void camera_composite(go_frame *f, const go_opts *o)
         }
     }
 #ifdef _OPENMP
-#pragma omp parallel for schedule(dynamic, 4) reduction(+ : evals, ambs)
+#pragma omp parallel for schedule(dynamic, 4) reduction(+ : evals, ambs, cpass)
 #endif
     for (int py = wy0; py < wy1; ++py) {
         for (int px = wx0; px < wx1; ++px) {
@@ -707,6 +708,7 @@ static void camera_composite(go_frame *f, const go_opts *o)
                     bSh += T * cmax[3];
                 }
                 if (Tn < o->t_stop) { consumed = (int32_t)(i - b); break; }
+                cpass++;
                 double w = a * T;
                 for (int c = 0; c < 3; ++c) {
                     S[c] += w * f->shade[3 * g + c];
@@ -735,6 +737,7 @@ static void camera_composite(go_frame *f, const go_opts *o)
     }
     f->camera_evals = evals;
     f->amb_camera = ambs;
+    f->camera_pass = cpass;
 }
 
 /* ------------------------------------------------------------------------ */

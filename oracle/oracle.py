@@ -83,7 +83,7 @@ class _Frame(C.Structure):
                 ("n_contrib", _I32), ("S", _D), ("Sh", _D), ("Rimg", _D),
                 ("shadow_evals", C.c_int64), ("shadow_pass", C.c_int64),
                 ("camera_evals", C.c_int64), ("amb_shadow", C.c_int64),
-                ("amb_camera", C.c_int64), ("t_prep", C.c_double), ("t_bin", C.c_double),
+                ("amb_camera", C.c_int64), ("camera_pass", C.c_int64), ("t_prep", C.c_double), ("t_bin", C.c_double),
                 ("t_shadow", C.c_double), ("t_mlp", C.c_double), ("t_camera", C.c_double)]
 
 
@@ -235,7 +235,7 @@ def render(scene, cam, light, opts: Opts | None = None) -> dict:
         Sh=_arr(f.Sh, np_, np.float64).reshape(H, W),
         R=_arr(f.Rimg, 3 * np_, np.float64).reshape(H, W, 3),
         shadow_evals=f.shadow_evals, shadow_pass=f.shadow_pass, camera_evals=f.camera_evals,
-        amb_shadow=f.amb_shadow, amb_camera=f.amb_camera,
+        amb_shadow=f.amb_shadow, amb_camera=f.amb_camera, camera_pass=f.camera_pass,
         times={"prep": f.t_prep, "bin": f.t_bin, "shadow": f.t_shadow, "mlp": f.t_mlp,
                "camera": f.t_camera},
     )
