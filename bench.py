@@ -49,6 +49,8 @@ def parse():
                     help="render this many frames of the workload (no timing) and exit; for ncu")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-window", type=int, default=96, help="oracle window edge (pixels)")
+    ap.add_argument("--inflight", type=int, default=4, help="server in-flight slots (served arm)")
+    ap.add_argument("--no-serve", action="store_true", help="time single frames only")
     return ap.parse_args()
 
 
@@ -56,7 +58,10 @@ def workload_config(a, mlp):
     return {"workload": f"object scene, {a.n} Gaussians, K=8, Phi/Psi 3x128 {mlp.upper()}, "
                         f"{a.res}x{a.res}, point light, 100 seeded camera/light pairs",
             "n_gaussians": a.n, "lobes": 8, "mlp": f"3x128 {mlp}", "image": [a.res, a.res],
-            "pairs": 100, "l2": "flushed between steps (256 MB write), outside the timed events",
+            "pairs": 100,
+            "l2": ("served arm: inputs larger than L2 (149 MB scene, ~0.5 GB of pair lists per frame); "
+                   "single-frame arms: L2 flushed between steps (256 MB write), outside the timed events"),
+            "timing": "served: CUDA-event span from the first frame's start to the last frame's end",
             "parallelism": f"replicas x{a.gpus}"}
 
 
@@ -289,6 +294,55 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_val = world * K / float(t.item())
 
+    # ---- served arm: continuous batching through the server (headline) ----
+    served = None
+    if not a.no_serve:
+        srv = R.Server(hbm_budget=48 << 30, max_inflight=a.inflight, device=local)
+        sid = srv.add_scene(ds)
+        outs = [torch.empty((a.res, a.res, 3), device=dev) for _ in range(a.inflight + 2)]
+        for i in range(2 * a.inflight):  # warm the capacity estimate and the memory pool
+            cam, light = pairs[i % 100]
+            srv.wait(srv.submit(sid, cam, light, outs[i % len(outs)]))
+        srv.reset_counters()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        w0 = time.perf_counter()
+        tk = []
+        for s_ in range(K):
+            cam, light = pairs[(a.warmup + s_) % 100]
+            tk.append(srv.submit(sid, cam, light, outs[s_ % len(outs)]))
+        bad = [srv.wait(t)[0] for t in tk]
+        torch.cuda.synchronize()
+        served_wall = time.perf_counter() - w0
+        st = srv.stats()
+        span_ms = st.device_span_ms
+        if world > 1:
+            t = torch.tensor([span_ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            span_ms = float(t.item())
+        rate = K / (span_ms / 1e3)
+        # latency under load: open-loop Poisson arrivals at 80 % of the served rate
+        rng = np.random.default_rng(1234)
+        lam = 0.8 * rate
+        gaps = rng.exponential(1.0 / lam, K)
+        lat_t = []
+        t_next = time.perf_counter()
+        for s_ in range(K):
+            t_next += gaps[s_]
+            while time.perf_counter() < t_next:
+                pass
+            cam, light = pairs[(a.warmup + 7 * s_) % 100]
+            lat_t.append(srv.submit(sid, cam, light, outs[s_ % len(outs)]))
+        lats = np.array([srv.wait(t)[1] for t in lat_t])
+        served = {"value": world * rate, "device_span_ms": span_ms, "wall_s": served_wall,
+                  "inflight_slots": a.inflight, "max_in_flight": int(st.max_in_flight),
+                  "retries": int(st.retries), "failed": int(sum(1 for b in bad if b != 0)),
+                  "latency_open_loop": {"rate_rps": lam, "p50_ms": float(np.percentile(lats, 50)),
+                                        "p99_ms": float(np.percentile(lats, 99)),
+                                        "clock": "host, submit to completion"}}
+        srv.close()
+
     # ---- FP32 plain comparison arm (one request at a time, FP32 MLPs) ----
     plain = None
     if not a.no_plain:
@@ -368,14 +422,23 @@ def main():
                 "unit": "GB/s", "frac": achieved / peak, "traffic": None,
                 "work": "pairs written + read once (8 B each) + records"}
 
+    single = {"value": value, "ms_per_step": total_ms / K,
+              "p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99)),
+              "note": "one frame at a time, CUDA events per frame, L2 flushed between frames"}
+    head_value = served["value"] if served else value
+    head_ms = 1e3 * world / head_value
+    p50 = served["latency_open_loop"]["p50_ms"] if served else single["p50_ms"]
+    p99 = served["latency_open_loop"]["p99_ms"] if served else single["p99_ms"]
     out = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
-        "warmup": a.warmup, "ms_per_step": total_ms / K, "higher_is_better": True,
+        "metric": METRIC, "value": head_value, "unit": UNIT, "n_gpus": world, "steps": K,
+        "warmup": a.warmup, "ms_per_step": head_ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
         "dtype": "f32" if a.mlp == "fp32" else "bf16 MLP operands, f32 elsewhere",
         "data": "synthetic (seeded object scene, random-init MLPs)",
         "config": workload_config(a, a.mlp),
-        "p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99)),
+        "p50_ms": p50, "p99_ms": p99,
+        "served": served,
+        "single_frame": single,
         "stages_ms": {k: round(v, 4) for k, v in stage_ms.items()},
         "pairs_per_frame": {"camera": float(np.mean(per_step_cam_P)),
                             "light": float(np.mean(per_step_light_P))},

@@ -204,6 +204,70 @@ gs3_status gs3_render_stages(gs3_scene *scene, const gs3_camera *camera, const g
 /* Copy the workspace header to `out` (host) and synchronise `stream`. */
 gs3_status gs3_workspace_read_header(const void *workspace, gs3_ws_header *out, void *stream);
 
+/* ---- Continuous-batching server -----------------------------------------
+ * Serving form of gs3_render (no counterpart in the paper, which renders one
+ * frame at a time): a worker thread admits queued (scene, camera, light)
+ * requests while an in-flight slot is free and the request's workspace fits
+ * in the HBM budget, and runs each admitted frame on its slot's own stream, so
+ * requests that arrive while others are on the GPU overlap with them.  The
+ * workspace capacity is estimated per (scene, resolution) from the pair
+ * counts seen so far; a request that overflows it is re-admitted once with
+ * the exact count.  Latency is measured from gs3_server_submit to the
+ * completion of the request's work on the GPU. */
+enum { GS3_REQ_QUEUED = 0, GS3_REQ_RUNNING = 1, GS3_REQ_DONE = 2, GS3_REQ_FAILED = 3 };
+
+typedef struct {
+    size_t hbm_budget;             /* bytes of workspace admitted requests may hold together */
+    int32_t max_inflight;          /* in-flight slots (streams), 1..64 */
+    int32_t device;                /* CUDA device of every scene added */
+    int32_t inject_alloc_failures; /* testing: fail this many workspace allocations (0 in use) */
+    float initial_pairs;           /* first-request capacity guess: pairs per Gaussian at 800x800,
+                                      scaled with the pixel count (0: 64) */
+} gs3_server_opts;
+
+typedef struct {
+    uint64_t completed, failed, retries, queued, in_flight, max_in_flight;
+    uint64_t bytes_in_use, peak_bytes_in_use;
+    double device_span_ms; /* CUDA-event time from the first admitted frame's start to the
+                              last completed frame's end since the last reset */
+} gs3_server_counters;
+
+typedef struct gs3_server gs3_server;
+
+/* Create a server and start its worker thread.  Errors: INVALID_ARG, CUDA. */
+gs3_status gs3_server_create(const gs3_server_opts *opts, gs3_server **out);
+
+/* Register a scene (borrowed; it must outlive the server).  Not thread-safe
+ * against concurrent gs3_destroy_scene of the same scene. */
+gs3_status gs3_server_add_scene(gs3_server *server, gs3_scene *scene, int32_t *scene_id);
+
+/* Queue one frame.  camera, light, opts: host structs, copied.  out_rgb:
+ * device float32 [height][width][3], caller-owned, written when the request
+ * completes.  Returns at once with a ticket.  Errors: INVALID_ARG. */
+gs3_status gs3_server_submit(gs3_server *server, int32_t scene_id, const gs3_camera *camera,
+                             const gs3_light *light, const gs3_render_opts *opts, float *out_rgb,
+                             uint64_t *ticket);
+
+/* Non-blocking state (GS3_REQ_*) and latency of a ticket.  A finished ticket
+ * is forgotten after this call reports it; the return value is the request's
+ * own status (GS3_OK unless it failed: OOM when its workspace could not be
+ * allocated or can never fit the budget, CAPACITY, CUDA). */
+gs3_status gs3_server_poll(gs3_server *server, uint64_t ticket, int32_t *state, double *latency_ms);
+
+/* Block until the ticket finishes or timeout_s passes (GS3_ERR_TIMEOUT);
+ * returns the request's status and forgets the ticket. */
+gs3_status gs3_server_wait(gs3_server *server, uint64_t ticket, double timeout_s, double *latency_ms);
+
+/* Counters of the server since creation. */
+gs3_status gs3_server_stats(gs3_server *server, gs3_server_counters *out);
+
+/* Zero the counters and the device time span (call while the server is idle). */
+gs3_status gs3_server_reset_counters(gs3_server *server);
+
+/* Stop the worker, wait for in-flight work, release streams and memory.
+ * Queued requests that were never admitted are dropped. */
+gs3_status gs3_server_destroy(gs3_server *server);
+
 /* ---- Depth sort without allocation --------------------------------------
  * The paper has no counterpart to this entry point; it serves callers that
  * may not allocate device memory at all: a renderer embedded in a host

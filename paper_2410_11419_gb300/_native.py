@@ -81,6 +81,25 @@ class gs3_scene(C.Structure):
     pass
 
 
+class gs3_server(C.Structure):
+    pass
+
+
+class gs3_server_opts(C.Structure):
+    _fields_ = [("hbm_budget", C.c_size_t), ("max_inflight", C.c_int32), ("device", C.c_int32),
+                ("inject_alloc_failures", C.c_int32), ("initial_pairs", C.c_float)]
+
+
+class gs3_server_counters(C.Structure):
+    _fields_ = [(f, C.c_uint64) for f in ("completed", "failed", "retries", "queued", "in_flight",
+                                          "max_in_flight", "bytes_in_use", "peak_bytes_in_use")] + [
+        ("device_span_ms", C.c_double)]
+
+
+GS3_REQ_QUEUED, GS3_REQ_RUNNING, GS3_REQ_DONE, GS3_REQ_FAILED = 0, 1, 2, 3
+_SERVER_P = C.POINTER(gs3_server)
+
+
 _SCENE_P = C.POINTER(gs3_scene)
 
 # name -> (restype, argtypes); every symbol include/gs3.h declares
@@ -98,6 +117,15 @@ SIGNATURES = {
                                     C.POINTER(gs3_render_opts), C.c_void_p, C.c_void_p, C.c_size_t,
                                     C.c_size_t, C.c_uint32, C.c_void_p]),
     "gs3_workspace_read_header": (C.c_int, [C.c_void_p, C.POINTER(gs3_ws_header), C.c_void_p]),
+    "gs3_server_create": (C.c_int, [C.POINTER(gs3_server_opts), C.POINTER(_SERVER_P)]),
+    "gs3_server_add_scene": (C.c_int, [_SERVER_P, _SCENE_P, C.POINTER(C.c_int32)]),
+    "gs3_server_submit": (C.c_int, [_SERVER_P, C.c_int32, C.POINTER(gs3_camera), C.POINTER(gs3_light),
+                                    C.POINTER(gs3_render_opts), C.c_void_p, C.POINTER(C.c_uint64)]),
+    "gs3_server_poll": (C.c_int, [_SERVER_P, C.c_uint64, C.POINTER(C.c_int32), C.POINTER(C.c_double)]),
+    "gs3_server_wait": (C.c_int, [_SERVER_P, C.c_uint64, C.c_double, C.POINTER(C.c_double)]),
+    "gs3_server_stats": (C.c_int, [_SERVER_P, C.POINTER(gs3_server_counters)]),
+    "gs3_server_reset_counters": (C.c_int, [_SERVER_P]),
+    "gs3_server_destroy": (C.c_int, [_SERVER_P]),
     "gs3_depth_order_static": (C.c_int, [C.c_void_p, C.c_uint32, C.c_void_p, C.c_void_p]),
     "gs3_kernel_launches": (C.c_uint64, []),
     "gs3_last_error": (C.c_char_p, []),
@@ -181,6 +209,59 @@ def gs3_workspace_read_header(workspace, stream: int) -> gs3_ws_header:
     _check(lib().gs3_workspace_read_header(_ptr(workspace), C.byref(h), stream),
            "gs3_workspace_read_header")
     return h
+
+
+def gs3_server_create(hbm_budget: int, max_inflight: int, device: int = 0,
+                      inject_alloc_failures: int = 0, initial_pairs: float = 0.0):
+    out = _SERVER_P()
+    o = gs3_server_opts(hbm_budget, max_inflight, device, inject_alloc_failures, initial_pairs)
+    _check(lib().gs3_server_create(C.byref(o), C.byref(out)), "gs3_server_create")
+    return out
+
+
+def gs3_server_add_scene(server, scene) -> int:
+    sid = C.c_int32()
+    _check(lib().gs3_server_add_scene(server, scene, C.byref(sid)), "gs3_server_add_scene")
+    return sid.value
+
+
+def gs3_server_submit(server, scene_id: int, camera: gs3_camera, light: gs3_light,
+                      opts: gs3_render_opts, out_rgb) -> int:
+    t = C.c_uint64()
+    _check(lib().gs3_server_submit(server, scene_id, C.byref(camera), C.byref(light), C.byref(opts),
+                                   _ptr(out_rgb), C.byref(t)), "gs3_server_submit")
+    return t.value
+
+
+def gs3_server_poll(server, ticket: int):
+    """(state, latency_ms, status); never raises for a failed request."""
+    st = C.c_int32()
+    lat = C.c_double()
+    rc = lib().gs3_server_poll(server, ticket, C.byref(st), C.byref(lat))
+    if rc == GS3_ERR_INVALID_ARG and st.value == 0:
+        _check(rc, "gs3_server_poll")
+    return st.value, lat.value, rc
+
+
+def gs3_server_wait(server, ticket: int, timeout_s: float = 60.0):
+    """(status, latency_ms)."""
+    lat = C.c_double()
+    rc = lib().gs3_server_wait(server, ticket, timeout_s, C.byref(lat))
+    return rc, lat.value
+
+
+def gs3_server_stats(server) -> gs3_server_counters:
+    out = gs3_server_counters()
+    _check(lib().gs3_server_stats(server, C.byref(out)), "gs3_server_stats")
+    return out
+
+
+def gs3_server_reset_counters(server) -> None:
+    _check(lib().gs3_server_reset_counters(server), "gs3_server_reset_counters")
+
+
+def gs3_server_destroy(server) -> None:
+    _check(lib().gs3_server_destroy(server), "gs3_server_destroy")
 
 
 GS3_STATIC_SORT_MAX_KEYS = 1048576

@@ -7,10 +7,6 @@
 
 #include "gs3_internal.cuh"
 
-struct gs3_scene {
-  gs3::SceneDev dev;
-  unsigned char* tc_blob[2] = {nullptr, nullptr};  // BF16 tensor-core weights (owned)
-};
 
 namespace gs3 {
 
@@ -54,6 +50,30 @@ bool mlp_ok(const gs3_mlp_desc& m, int in_dim, int out_dim) {
 }  // namespace
 
 void set_last_error(const char* msg) { g_last_error = msg; }
+
+// True unless the driver reports that [ptr, ptr + bytes) leaves the device
+// allocation containing ptr (memory from sub-allocators such as torch's
+// caching allocator is checked against its whole segment).
+bool device_range_ok(const void* ptr, size_t bytes) {
+  typedef int (*range_fn)(unsigned long long*, size_t*, unsigned long long);
+  static range_fn fn = nullptr;
+  static bool looked = false;
+  if (!looked) {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuMemGetAddressRange", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<range_fn>(f);
+    looked = true;
+  }
+  if (!fn || !ptr) return true;
+  unsigned long long base = 0;
+  size_t size = 0;
+  if (fn(&base, &size, reinterpret_cast<unsigned long long>(ptr)) != 0) return false;  // not device memory
+  const unsigned long long p = reinterpret_cast<unsigned long long>(ptr);
+  return p >= base && p - base + bytes <= size;
+}
 
 Workspace plan_workspace(int n, int width, int height, size_t cap) {
   Workspace L;
@@ -248,6 +268,11 @@ gs3_status gs3_render_stages(gs3_scene* scene, const gs3_camera* cam, const gs3_
     return fail(GS3_ERR_INVALID_ARG, "gs3_render: light coincides with the light-camera target");
   Workspace L = plan_workspace(scene->dev.n, cam->width, cam->height, key_capacity);
   if (ws_bytes < L.total) return fail(GS3_ERR_INVALID_ARG, "gs3_render: workspace too small");
+  if (!device_range_ok(workspace, L.total))
+    return fail(GS3_ERR_INVALID_ARG, "gs3_render: workspace is not device memory of the stated size");
+  if ((stages & GS3_STAGE_CAMERA) &&
+      !device_range_ok(out_rgb, (size_t)cam->width * cam->height * 3 * sizeof(float)))
+    return fail(GS3_ERR_INVALID_ARG, "gs3_render: out_rgb is not device memory of width*height*3 floats");
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   FrameArgs f;
   f.sc = scene->dev;

@@ -123,6 +123,9 @@ void radix_sort_pairs(const uint32_t* kin, const uint32_t* vin, uint32_t* k0, ui
                       uint32_t* v1, uint32_t n, int passes, uint32_t* hist, uint32_t* scan_part,
                       cudaStream_t s);
 
+// false when [ptr, ptr + bytes) provably leaves ptr's device allocation
+bool device_range_ok(const void* ptr, size_t bytes);
+
 // sets the message gs3_last_error returns on this thread
 void set_last_error(const char* msg);
 
@@ -136,3 +139,9 @@ __host__ __device__ inline T* at(unsigned char* ws, size_t off) {
 }
 
 }  // namespace gs3
+
+// The scene handle of the C ABI: borrowed parameters plus owned derived buffers.
+struct gs3_scene {
+  gs3::SceneDev dev;
+  unsigned char* tc_blob[2] = {nullptr, nullptr};  // BF16 tensor-core weights (owned)
+};

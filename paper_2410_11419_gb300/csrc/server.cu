@@ -1,0 +1,435 @@
+// Continuous-batching render server over device-resident scenes.
+//
+// A worker thread owns a FIFO of (scene, camera, light) requests.  A request
+// is admitted when an in-flight slot is free and its workspace fits in the
+// HBM budget (bytes in use by admitted requests); it then runs the whole
+// frame on its slot's stream, so requests admitted while others are still on
+// the GPU overlap on the device.  Workspaces come from a stream-ordered
+// memory pool and go back to it when the request's completion event fires.
+// The workspace capacity (tile/Gaussian pairs) is estimated per
+// (scene, resolution) from the largest count seen so far; a request that
+// overflows is re-admitted once with the exact count its first run reported.
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "gs3_internal.cuh"
+
+namespace gs3 {
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+struct Request {
+  uint64_t ticket = 0;
+  int scene = 0;
+  gs3_camera cam{};
+  gs3_light light{};
+  gs3_render_opts opts{};
+  float* out = nullptr;
+  Clock::time_point t_submit;
+  size_t forced_cap = 0;  // exact capacity for a re-admitted request
+  int attempts = 0;
+};
+
+struct Slot {
+  cudaStream_t stream = nullptr;
+  cudaEvent_t start = nullptr;
+  cudaEvent_t done = nullptr;
+  gs3_ws_header* hdr = nullptr;  // pinned copy of the workspace header
+  void* ws = nullptr;
+  size_t bytes = 0;
+  size_t cap = 0;
+  bool busy = false;
+  Request req;
+};
+
+struct Result {
+  int state = GS3_REQ_QUEUED;
+  gs3_status status = GS3_OK;
+  double latency_ms = 0.0;
+};
+
+}  // namespace
+}  // namespace gs3
+
+using namespace gs3;
+
+struct gs3_server {
+  int device = 0;
+  size_t budget = 0;
+  size_t in_use = 0;
+  size_t peak_in_use = 0;
+  int inject_alloc_failures = 0;
+  double initial_pairs = 64.0;
+  cudaEvent_t epoch = nullptr;  // device time origin of the counters
+  bool epoch_set = false;
+  double span_lo = 1e300, span_hi = -1e300;
+  std::vector<gs3_scene*> scenes;
+  std::unordered_map<uint64_t, size_t> cap_hint;  // (scene, w, h) -> pairs
+  std::deque<Request> queue;
+  std::vector<Slot> slots;
+  std::unordered_map<uint64_t, Result> results;
+  uint64_t next_ticket = 1;
+  uint64_t completed = 0, failed = 0, retries = 0;
+  int max_inflight_seen = 0;
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::thread worker;
+  bool stop = false;
+  cudaMemPool_t pool = nullptr;
+};
+
+namespace gs3 {
+namespace {
+
+uint64_t hint_key(int scene, int w, int h) {
+  return ((uint64_t)scene << 40) ^ ((uint64_t)w << 20) ^ (uint64_t)h;
+}
+
+size_t estimate_cap(gs3_server* S, const Request& r) {
+  if (r.forced_cap) return r.forced_cap;
+  auto it = S->cap_hint.find(hint_key(r.scene, r.cam.width, r.cam.height));
+  if (it != S->cap_hint.end()) return it->second;
+  // first request of this (scene, resolution): initial_pairs per Gaussian per splat
+  // at 800 x 800, scaled with the pixel count, plus 4 per Gaussian
+  const double n = (double)S->scenes[r.scene]->dev.n;
+  const double px = (double)r.cam.width * r.cam.height / (800.0 * 800.0);
+  double c = n * (4.0 + S->initial_pairs * px);
+  if (c > 2.0e9) c = 2.0e9;
+  return (size_t)c;
+}
+
+void finish(gs3_server* S, Slot& sl, gs3_status st) {
+  Result& res = S->results[sl.req.ticket];
+  res.state = st == GS3_OK ? GS3_REQ_DONE : GS3_REQ_FAILED;
+  res.status = st;
+  res.latency_ms = std::chrono::duration<double, std::milli>(Clock::now() - sl.req.t_submit).count();
+  if (st == GS3_OK) ++S->completed; else ++S->failed;
+}
+
+void release(gs3_server* S, Slot& sl) {
+  if (sl.ws) cudaFreeAsync(sl.ws, sl.stream);
+  sl.ws = nullptr;
+  S->in_use -= sl.bytes;
+  sl.bytes = 0;
+  sl.busy = false;
+}
+
+// Completions: called with the lock held.
+bool poll_slots(gs3_server* S) {
+  bool any = false;
+  for (Slot& sl : S->slots) {
+    if (!sl.busy) continue;
+    const cudaError_t q = cudaEventQuery(sl.done);
+    if (q == cudaErrorNotReady) continue;
+    any = true;
+    gs3_status st = GS3_OK;
+    if (q != cudaSuccess) {
+      st = GS3_ERR_CUDA;
+    } else if (sl.hdr->status == GS3_ERR_CAPACITY && sl.req.attempts < 2) {
+      // re-admit at the front with the exact pair count of this frame
+      Request r = sl.req;
+      const size_t need = sl.hdr->pairs_cam_needed > sl.hdr->pairs_light_needed ? sl.hdr->pairs_cam_needed
+                                                                                   : sl.hdr->pairs_light_needed;
+      r.forced_cap = need + need / 16 + 1024;
+      ++S->retries;
+      auto& hint = S->cap_hint[hint_key(r.scene, r.cam.width, r.cam.height)];
+      if (r.forced_cap > hint) hint = r.forced_cap;
+      release(S, sl);
+      S->results[r.ticket].state = GS3_REQ_QUEUED;
+      S->queue.push_front(r);
+      continue;
+    } else {
+      st = (gs3_status)sl.hdr->status;
+      const size_t seen = sl.hdr->pairs_cam > sl.hdr->pairs_light ? sl.hdr->pairs_cam : sl.hdr->pairs_light;
+      auto& hint = S->cap_hint[hint_key(sl.req.scene, sl.req.cam.width, sl.req.cam.height)];
+      const size_t want = seen + seen / 8 + 1024;  // 12.5 % head room over the largest count seen
+      if (want > hint) hint = want;
+    }
+    if (st == GS3_OK && S->epoch_set) {
+      float a = 0.f, b = 0.f;
+      if (cudaEventElapsedTime(&a, S->epoch, sl.start) == cudaSuccess &&
+          cudaEventElapsedTime(&b, S->epoch, sl.done) == cudaSuccess) {
+        if (a < S->span_lo) S->span_lo = a;
+        if (b > S->span_hi) S->span_hi = b;
+      }
+    }
+    finish(S, sl, st);
+    release(S, sl);
+  }
+  return any;
+}
+
+// Admission: called with the lock held.  FIFO: the head waits for memory.
+bool admit(gs3_server* S) {
+  bool any = false;
+  while (!S->queue.empty()) {
+    Slot* free_slot = nullptr;
+    for (Slot& sl : S->slots)
+      if (!sl.busy) { free_slot = &sl; break; }
+    if (!free_slot) break;
+    const Request& head = S->queue.front();
+    gs3_scene* sc = S->scenes[head.scene];
+    const size_t cap = estimate_cap(S, head);
+    const size_t bytes = gs3_workspace_size(sc->dev.n, head.cam.width, head.cam.height, cap) + 256;
+    const bool fits_ever = bytes <= S->budget;
+    if (fits_ever && S->in_use + bytes > S->budget) break;  // wait for memory
+    Slot& sl = *free_slot;
+    sl.req = head;
+    sl.req.attempts += 1;
+    S->queue.pop_front();
+    any = true;
+    if (!fits_ever) {  // can never fit: fail it rather than block the queue
+      finish(S, sl, GS3_ERR_OOM);
+      continue;
+    }
+    void* ws = nullptr;
+    cudaError_t e = cudaSuccess;
+    if (S->inject_alloc_failures > 0) {
+      --S->inject_alloc_failures;
+      e = cudaErrorMemoryAllocation;
+    } else {
+      e = cudaMallocFromPoolAsync(&ws, bytes, S->pool, sl.stream);
+    }
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      finish(S, sl, GS3_ERR_OOM);
+      continue;
+    }
+    sl.ws = ws;
+    sl.bytes = bytes;
+    sl.cap = cap;
+    sl.busy = true;
+    S->in_use += bytes;
+    if (S->in_use > S->peak_in_use) S->peak_in_use = S->in_use;
+    S->results[sl.req.ticket].state = GS3_REQ_RUNNING;
+    void* aligned = reinterpret_cast<void*>((reinterpret_cast<uintptr_t>(ws) + 255) & ~uintptr_t(255));
+    if (!S->epoch_set) {
+      cudaEventRecord(S->epoch, sl.stream);
+      S->epoch_set = true;
+    }
+    cudaEventRecord(sl.start, sl.stream);
+    gs3_status st = gs3_render(sc, &sl.req.cam, &sl.req.light, &sl.req.opts, sl.req.out, aligned, bytes - 256,
+                               cap, sl.stream);
+    if (st == GS3_OK) {
+      cudaMemcpyAsync(sl.hdr, aligned, sizeof(gs3_ws_header), cudaMemcpyDeviceToHost, sl.stream);
+      cudaEventRecord(sl.done, sl.stream);
+    } else {
+      finish(S, sl, st);
+      release(S, sl);
+    }
+    int inflight = 0;
+    for (Slot& s2 : S->slots) inflight += s2.busy ? 1 : 0;
+    if (inflight > S->max_inflight_seen) S->max_inflight_seen = inflight;
+  }
+  return any;
+}
+
+void worker_main(gs3_server* S) {
+  cudaSetDevice(S->device);
+  std::unique_lock<std::mutex> lock(S->mu);
+  while (!S->stop) {
+    const bool a = poll_slots(S);
+    const bool b = admit(S);
+    if (a) S->cv_done.notify_all();
+    bool busy = false;
+    for (Slot& sl : S->slots) busy |= sl.busy;
+    if (!a && !b) {
+      if (busy) {
+        lock.unlock();
+        std::this_thread::sleep_for(std::chrono::microseconds(20));
+        lock.lock();
+      } else {
+        S->cv_work.wait_for(lock, std::chrono::milliseconds(5));
+      }
+    }
+  }
+}
+
+}  // namespace
+}  // namespace gs3
+
+extern "C" {
+
+gs3_status gs3_server_create(const gs3_server_opts* o, gs3_server** out) {
+  if (!o || !out || o->max_inflight < 1 || o->max_inflight > 64 || o->hbm_budget == 0) {
+    set_last_error("gs3_server_create: bad options");
+    return GS3_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  gs3_server* S = new (std::nothrow) gs3_server;
+  if (!S) return GS3_ERR_OOM;
+  S->budget = o->hbm_budget;
+  S->inject_alloc_failures = o->inject_alloc_failures;
+  if (o->initial_pairs > 0.f) S->initial_pairs = o->initial_pairs;
+  S->device = o->device;
+  if (cudaSetDevice(S->device) != cudaSuccess) {
+    delete S;
+    set_last_error("gs3_server_create: cudaSetDevice failed");
+    return GS3_ERR_CUDA;
+  }
+  cudaMemPoolProps props = {};
+  props.allocType = cudaMemAllocationTypePinned;
+  props.location.type = cudaMemLocationTypeDevice;
+  props.location.id = S->device;
+  if (cudaMemPoolCreate(&S->pool, &props) != cudaSuccess) {
+    delete S;
+    set_last_error("gs3_server_create: cudaMemPoolCreate failed");
+    return GS3_ERR_CUDA;
+  }
+  uint64_t keep = (uint64_t)S->budget;  // keep freed memory in the pool up to the budget
+  cudaMemPoolSetAttribute(S->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  S->slots.resize(o->max_inflight);
+  for (Slot& sl : S->slots) {
+    cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking);
+    cudaEventCreate(&sl.start);
+    cudaEventCreate(&sl.done);
+    cudaMallocHost(reinterpret_cast<void**>(&sl.hdr), sizeof(gs3_ws_header));
+  }
+  cudaEventCreate(&S->epoch);
+  S->worker = std::thread(worker_main, S);
+  *out = S;
+  return GS3_OK;
+}
+
+gs3_status gs3_server_add_scene(gs3_server* S, gs3_scene* scene, int32_t* scene_id) {
+  if (!S || !scene || !scene_id) return GS3_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lock(S->mu);
+  S->scenes.push_back(scene);
+  *scene_id = (int32_t)S->scenes.size() - 1;
+  return GS3_OK;
+}
+
+gs3_status gs3_server_submit(gs3_server* S, int32_t scene_id, const gs3_camera* cam, const gs3_light* light,
+                             const gs3_render_opts* opts, float* out_rgb, uint64_t* ticket) {
+  if (!S || !cam || !light || !opts || !out_rgb || !ticket) {
+    set_last_error("gs3_server_submit: null argument");
+    return GS3_ERR_INVALID_ARG;
+  }
+  if (cam->width < 1 || cam->height < 1 || cam->width > 16384 || cam->height > 16384) {
+    set_last_error("gs3_server_submit: image size out of range");
+    return GS3_ERR_INVALID_ARG;
+  }
+  if (!device_range_ok(out_rgb, (size_t)cam->width * cam->height * 3 * sizeof(float))) {
+    set_last_error("gs3_server_submit: out_rgb is not device memory of width*height*3 floats");
+    return GS3_ERR_INVALID_ARG;
+  }
+  Request r;
+  r.cam = *cam;
+  r.light = *light;
+  r.opts = *opts;
+  r.out = out_rgb;
+  r.t_submit = Clock::now();
+  {
+    std::lock_guard<std::mutex> lock(S->mu);
+    if (scene_id < 0 || scene_id >= (int)S->scenes.size()) {
+      set_last_error("gs3_server_submit: unknown scene id");
+      return GS3_ERR_INVALID_ARG;
+    }
+    r.scene = scene_id;
+    r.ticket = S->next_ticket++;
+    S->results[r.ticket] = Result{};
+    S->queue.push_back(r);
+    *ticket = r.ticket;
+  }
+  S->cv_work.notify_one();
+  return GS3_OK;
+}
+
+gs3_status gs3_server_poll(gs3_server* S, uint64_t ticket, int32_t* state, double* latency_ms) {
+  if (!S || !state) return GS3_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lock(S->mu);
+  auto it = S->results.find(ticket);
+  if (it == S->results.end()) {
+    set_last_error("gs3_server_poll: unknown ticket");
+    return GS3_ERR_INVALID_ARG;
+  }
+  *state = it->second.state;
+  if (latency_ms) *latency_ms = it->second.latency_ms;
+  const gs3_status st = it->second.status;
+  if (it->second.state == GS3_REQ_DONE || it->second.state == GS3_REQ_FAILED) S->results.erase(it);
+  return st;
+}
+
+gs3_status gs3_server_wait(gs3_server* S, uint64_t ticket, double timeout_s, double* latency_ms) {
+  if (!S) return GS3_ERR_INVALID_ARG;
+  std::unique_lock<std::mutex> lock(S->mu);
+  const auto deadline = Clock::now() + std::chrono::duration<double>(timeout_s);
+  for (;;) {
+    auto it = S->results.find(ticket);
+    if (it == S->results.end()) {
+      set_last_error("gs3_server_wait: unknown ticket");
+      return GS3_ERR_INVALID_ARG;
+    }
+    if (it->second.state == GS3_REQ_DONE || it->second.state == GS3_REQ_FAILED) {
+      if (latency_ms) *latency_ms = it->second.latency_ms;
+      const gs3_status st = it->second.status;
+      S->results.erase(it);
+      return st;
+    }
+    if (S->cv_done.wait_until(lock, deadline) == std::cv_status::timeout && Clock::now() >= deadline) {
+      set_last_error("gs3_server_wait: timed out");
+      return GS3_ERR_TIMEOUT;
+    }
+  }
+}
+
+gs3_status gs3_server_stats(gs3_server* S, gs3_server_counters* out) {
+  if (!S || !out) return GS3_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lock(S->mu);
+  out->completed = S->completed;
+  out->failed = S->failed;
+  out->retries = S->retries;
+  out->queued = S->queue.size();
+  int inflight = 0;
+  for (Slot& sl : S->slots) inflight += sl.busy ? 1 : 0;
+  out->in_flight = (uint64_t)inflight;
+  out->max_in_flight = (uint64_t)S->max_inflight_seen;
+  out->bytes_in_use = S->in_use;
+  out->peak_bytes_in_use = S->peak_in_use;
+  out->device_span_ms = S->span_hi > S->span_lo ? S->span_hi - S->span_lo : 0.0;
+  return GS3_OK;
+}
+
+gs3_status gs3_server_reset_counters(gs3_server* S) {
+  if (!S) return GS3_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lock(S->mu);
+  S->completed = S->failed = S->retries = 0;
+  S->max_inflight_seen = 0;
+  S->peak_in_use = S->in_use;
+  S->epoch_set = false;
+  S->span_lo = 1e300;
+  S->span_hi = -1e300;
+  return GS3_OK;
+}
+
+gs3_status gs3_server_destroy(gs3_server* S) {
+  if (!S) return GS3_OK;
+  {
+    std::lock_guard<std::mutex> lock(S->mu);
+    S->stop = true;
+  }
+  S->cv_work.notify_all();
+  if (S->worker.joinable()) S->worker.join();
+  for (Slot& sl : S->slots) {
+    if (sl.stream) cudaStreamSynchronize(sl.stream);
+    if (sl.ws) cudaFreeAsync(sl.ws, sl.stream);
+    if (sl.stream) cudaStreamSynchronize(sl.stream);
+    if (sl.done) cudaEventDestroy(sl.done);
+    if (sl.start) cudaEventDestroy(sl.start);
+    if (sl.stream) cudaStreamDestroy(sl.stream);
+    if (sl.hdr) cudaFreeHost(sl.hdr);
+  }
+  if (S->epoch) cudaEventDestroy(S->epoch);
+  if (S->pool) cudaMemPoolDestroy(S->pool);
+  delete S;
+  return GS3_OK;
+}
+
+}  // extern "C"

@@ -42,6 +42,10 @@ extern "C" gs3_status gs3_depth_order_static(const uint32_t* keys, uint32_t n, u
     set_last_error("gs3_depth_order_static: n exceeds GS3_STATIC_SORT_MAX_KEYS (1048576)");
     return GS3_ERR_INVALID_ARG;
   }
+  if (!device_range_ok(keys, (size_t)n * 4) || !device_range_ok(order_out, (size_t)n * 4)) {
+    set_last_error("gs3_depth_order_static: keys or order_out is not device memory of n words");
+    return GS3_ERR_INVALID_ARG;
+  }
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
     set_last_error("gs3_depth_order_static: no usable current device");

@@ -151,3 +151,45 @@ class Renderer:
         if name == "n_contrib":
             return self._view(L.n_contrib, self.width * self.height, torch.int32).view(self.height, self.width)
         raise KeyError(name)
+
+
+class Server:
+    """Continuous-batching server (gs3_server_*) over device-resident scenes."""
+
+    def __init__(self, hbm_budget: int, max_inflight: int = 4, device: int = 0,
+                 inject_alloc_failures: int = 0, initial_pairs: float = 0.0):
+        self.handle = N.gs3_server_create(hbm_budget, max_inflight, device, inject_alloc_failures,
+                                          initial_pairs)
+        self.scenes = []
+
+    def add_scene(self, dscene: DeviceScene) -> int:
+        self.scenes.append(dscene)  # keep the parameters alive
+        return N.gs3_server_add_scene(self.handle, dscene.handle)
+
+    def submit(self, scene_id: int, cam, light, out, opts=None) -> int:
+        opts = opts if opts is not None else opts_struct()
+        return N.gs3_server_submit(self.handle, scene_id, camera_struct(cam), light_struct(light),
+                                   opts, out)
+
+    def wait(self, ticket: int, timeout_s: float = 120.0):
+        return N.gs3_server_wait(self.handle, ticket, timeout_s)
+
+    def poll(self, ticket: int):
+        return N.gs3_server_poll(self.handle, ticket)
+
+    def stats(self):
+        return N.gs3_server_stats(self.handle)
+
+    def reset_counters(self):
+        N.gs3_server_reset_counters(self.handle)
+
+    def close(self):
+        if self.handle:
+            N.gs3_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

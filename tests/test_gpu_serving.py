@@ -1,0 +1,148 @@
+"""Continuous-batching server (gs3_server_*): every result equals the same
+frame rendered alone with gs3_render, bit for bit (each request has its own
+workspace and the frame is deterministic), while requests overlap on the GPU;
+admission respects the HBM budget; capacity overflows are retried; injected
+allocation failures fail only their own requests."""
+import numpy as np
+import pytest
+
+from paper_2410_11419_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def scenes(gs3):
+    from paper_2410_11419_gb300 import _native as N, render as R
+    s0 = synth.object_scene(11, n=30_000)
+    s1 = synth.tiny_scene(0)
+    s2 = synth.paper_mlp_scene(3, n=4000)
+    ds = [R.DeviceScene(s0, mlp_dtype=N.GS3_MLP_BF16), R.DeviceScene(s1),
+          R.DeviceScene(s2, mlp_dtype=N.GS3_MLP_BF16)]
+    yield ds
+    for d in ds:
+        d.close()
+
+
+def alone(ds, cam, light):
+    import torch
+    from paper_2410_11419_gb300 import render as R
+    rd = R.Renderer(ds, cam.width, cam.height, 1 << 23)
+    img = rd.render(cam, light).clone()
+    torch.cuda.synchronize()
+    rd.check()
+    return img
+
+
+MIX = [(0, 256, 1), (1, 128, 2), (2, 160, 3), (0, 320, 4), (1, 96, 5), (0, 256, 6),
+       (2, 200, 7), (0, 256, 1), (1, 128, 8), (0, 192, 9), (2, 144, 10), (0, 256, 12)]
+
+
+def test_mixed_requests_equal_alone(scenes):
+    import torch
+    from paper_2410_11419_gb300 import render as R
+    srv = R.Server(hbm_budget=8 << 30, max_inflight=4)
+    ids = [srv.add_scene(d) for d in scenes]
+    outs, tickets = [], []
+    for si, res, seed in MIX:
+        cam, light = synth.camera_light_pair(seed, res, res)
+        out = torch.full((res, res, 3), -1.0, device="cuda")
+        outs.append(out)
+        tickets.append(srv.submit(ids[si], cam, light, out))
+    lat = []
+    for t in tickets:
+        st, ms = srv.wait(t)
+        assert st == 0
+        lat.append(ms)
+    stats = srv.stats()
+    assert stats.completed == len(MIX) and stats.failed == 0
+    assert stats.max_in_flight >= 2          # work overlapped on the device
+    assert stats.device_span_ms > 0 and all(x > 0 for x in lat)
+    for (si, res, seed), out in zip(MIX, outs):
+        cam, light = synth.camera_light_pair(seed, res, res)
+        want = alone(scenes[si], cam, light)
+        assert torch.equal(out, want), (si, res, seed)
+    srv.close()
+
+
+def test_admission_respects_budget(scenes):
+    import torch
+    from paper_2410_11419_gb300 import _native as N, render as R
+    cam, light = synth.camera_light_pair(1, 256, 256)
+    one = N.gs3_workspace_size(scenes[0].n, 256, 256, int(scenes[0].n * (4 + 64 * 256 * 256 / 640000)))
+    srv = R.Server(hbm_budget=int(one * 1.5), max_inflight=4)
+    sid = srv.add_scene(scenes[0])
+    outs = [torch.empty((256, 256, 3), device="cuda") for _ in range(5)]
+    ts = [srv.submit(sid, cam, light, o) for o in outs]
+    for t in ts:
+        assert srv.wait(t)[0] == 0
+    st = srv.stats()
+    assert st.max_in_flight == 1 and st.peak_bytes_in_use <= int(one * 1.5)
+    want = alone(scenes[0], cam, light)
+    for o in outs:
+        assert torch.equal(o, want)
+    srv.close()
+
+
+def test_capacity_retry(scenes):
+    import torch
+    from paper_2410_11419_gb300 import render as R
+    srv = R.Server(hbm_budget=8 << 30, max_inflight=2, initial_pairs=0.01)  # far too few pairs
+    sid = srv.add_scene(scenes[0])
+    cam, light = synth.camera_light_pair(3, 256, 256)
+    out = torch.empty((256, 256, 3), device="cuda")
+    assert srv.wait(srv.submit(sid, cam, light, out))[0] == 0
+    assert srv.stats().retries >= 1
+    assert torch.equal(out, alone(scenes[0], cam, light))
+    # the next request of the same (scene, resolution) uses the learned capacity
+    out2 = torch.empty_like(out)
+    srv.reset_counters()
+    assert srv.wait(srv.submit(sid, cam, light, out2))[0] == 0
+    assert srv.stats().retries == 0
+    srv.close()
+
+
+def test_injected_allocation_failures(scenes):
+    import torch
+    from paper_2410_11419_gb300 import _native as N, render as R
+    srv = R.Server(hbm_budget=8 << 30, max_inflight=2, inject_alloc_failures=2)
+    sid = srv.add_scene(scenes[1])
+    cam, light = synth.camera_light_pair(2, 128, 128)
+    outs = [torch.empty((128, 128, 3), device="cuda") for _ in range(4)]
+    ts = [srv.submit(sid, cam, light, o) for o in outs]
+    res = [srv.wait(t)[0] for t in ts]
+    assert res[:2] == [N.GS3_ERR_OOM, N.GS3_ERR_OOM] and res[2:] == [0, 0]
+    want = alone(scenes[1], cam, light)
+    assert torch.equal(outs[2], want) and torch.equal(outs[3], want)
+    st = srv.stats()
+    assert st.failed == 2 and st.completed == 2
+    srv.close()
+
+
+def test_rejects_bad_requests(scenes):
+    import torch
+    from paper_2410_11419_gb300 import _native as N, render as R
+    budget = 256 << 20
+    srv = R.Server(hbm_budget=budget, max_inflight=1)
+    sid_small = srv.add_scene(scenes[1])
+    sid_big = srv.add_scene(scenes[0])
+    cam, light = synth.camera_light_pair(2, 64, 64)
+    out = torch.empty((64, 64, 3), device="cuda")
+    with pytest.raises(N.GS3Error):
+        srv.submit(sid_small + 5, cam, light, out)
+    # an output buffer far too small for the image (8 floats, in a 2 MB allocator
+    # segment, for a 48 MB image) is refused before any work is queued
+    bc, bl = synth.camera_light_pair(2, 2048, 2048)
+    with pytest.raises(N.GS3Error):
+        srv.submit(sid_small, bc, bl, torch.empty((8,), device="cuda"))
+    # a request whose workspace can never fit the budget fails with OOM, others proceed
+    res = 2048
+    est = int(scenes[0].n * (4 + 64 * res * res / 640000.0))
+    assert N.gs3_workspace_size(scenes[0].n, res, res, est) > budget
+    big, blight = synth.camera_light_pair(2, res, res)
+    big_out = torch.empty((res, res, 3), device="cuda")
+    t_big = srv.submit(sid_big, big, blight, big_out)
+    t_ok = srv.submit(sid_small, cam, light, out)
+    assert srv.wait(t_big)[0] == N.GS3_ERR_OOM
+    assert srv.wait(t_ok)[0] == 0
+    srv.close()
