@@ -204,6 +204,37 @@ gs3_status gs3_render_stages(gs3_scene *scene, const gs3_camera *camera, const g
 /* Copy the workspace header to `out` (host) and synchronise `stream`. */
 gs3_status gs3_workspace_read_header(const void *workspace, gs3_ws_header *out, void *stream);
 
+/* ---- Backward (differentiation form) -------------------------------------
+ * Gradients of a scalar loss L with respect to every parameter, given
+ * dL/d(image).  Device float32 arrays in the layouts of gs3_scene_desc
+ * (float4-padded, the pad lanes are written as 0), caller-owned, overwritten:
+ *   mean_op[N]: (dL/dmu, dL/d opacity logit); scale, rot, shade_rot,
+ *   albedo_d, albedo_s [N]; latent [2N]; lobe_rot, lobe_sigma, lobe_amp [K N];
+ *   phi_w, phi_b, psi_w, psi_b: packed like the scene's MLP weights. */
+typedef struct {
+    float *mean_op, *scale, *rot, *shade_rot, *albedo_d, *albedo_s, *latent;
+    float *lobe_rot, *lobe_sigma, *lobe_amp;
+    float *phi_w, *phi_b, *psi_w, *psi_b;
+} gs3_grads;
+
+/* Bytes of the extra backward workspace for a scene. */
+size_t gs3_backward_workspace_size(const gs3_scene *scene);
+
+/* Backward of gs3_render (Sec. 4, Eq. 2-5 and the Phi / Psi MLPs): reverse
+ * camera composite (per-tile recomputation from the stored final
+ * transmittance), MLP backward, reverse shadow sweep from each ray's stored
+ * final occluder product, then both projections and the shading.
+ *   dL_drgb:   device float32 [height][width][3]
+ *   workspace: the workspace of a gs3_render of the same scene, camera,
+ *              light and options, unchanged since (it holds the forward state)
+ *   bwd_ws:    device, >= gs3_backward_workspace_size bytes, caller-owned
+ * The scene must use GS3_MLP_FP32 (GS3_ERR_UNSUPPORTED otherwise).
+ * Asynchronous on `stream`.  Errors: INVALID_ARG, UNSUPPORTED, CUDA. */
+gs3_status gs3_render_backward(gs3_scene *scene, const gs3_camera *camera, const gs3_light *light,
+                               const gs3_render_opts *opts, const float *dL_drgb, void *workspace,
+                               size_t workspace_bytes, size_t key_capacity, void *bwd_ws,
+                               size_t bwd_bytes, const gs3_grads *grads, void *stream);
+
 /* ---- Continuous-batching server -----------------------------------------
  * Serving form of gs3_render (no counterpart in the paper, which renders one
  * frame at a time): a worker thread admits queued (scene, camera, light)

@@ -275,3 +275,26 @@ def render_and_grad(scene, cam, light, target, opts=None):
         grads[nm + "_w"] = [w.grad.numpy().copy() for w in mlps[nm][0]]
         grads[nm + "_b"] = [b.grad.numpy().copy() for b in mlps[nm][1]]
     return float(L), img.detach().numpy(), grads, fr
+
+
+def grads_given_image_grad(scene, cam, light, dimg, opts=None):
+    """Gradients of every parameter for a given dL/d(image) (H, W, 3)."""
+    opts = opts or O.Opts()
+    fr = O.render(scene, cam, light, opts)
+    P, mlps = params_from_scene(scene)
+    img, aux = frame(P, fr, cam, light, opts, mlps)
+    img.backward(torch.as_tensor(np.asarray(dimg, dtype=np.float64)))
+    g = lambda v: np.zeros(tuple(v.shape)) if v.grad is None else v.grad.numpy().copy()
+    grads = {k: g(v) for k, v in P.items()}
+    for nm in ("phi", "psi"):
+        grads[nm + "_w"] = np.concatenate([g(w).reshape(-1) for w in mlps[nm][0]])
+        grads[nm + "_b"] = np.concatenate([g(b).reshape(-1) for b in mlps[nm][1]])
+    return grads, fr
+
+
+def image_grad_of_loss(img, target, lam=0.2):
+    """dL/d(image) of L = (1 - lam) L1 + lam (1 - SSIM)."""
+    x = torch.as_tensor(np.asarray(img, dtype=np.float64)).clone().requires_grad_(True)
+    L = loss(x, torch.as_tensor(np.asarray(target, dtype=np.float64)), lam)
+    L.backward()
+    return x.grad.numpy(), float(L.detach())

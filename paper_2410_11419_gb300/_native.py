@@ -81,6 +81,14 @@ class gs3_scene(C.Structure):
     pass
 
 
+GRAD_FIELDS = ("mean_op", "scale", "rot", "shade_rot", "albedo_d", "albedo_s", "latent", "lobe_rot",
+               "lobe_sigma", "lobe_amp", "phi_w", "phi_b", "psi_w", "psi_b")
+
+
+class gs3_grads(C.Structure):
+    _fields_ = [(f, C.c_void_p) for f in GRAD_FIELDS]
+
+
 class gs3_server(C.Structure):
     pass
 
@@ -117,6 +125,11 @@ SIGNATURES = {
                                     C.POINTER(gs3_render_opts), C.c_void_p, C.c_void_p, C.c_size_t,
                                     C.c_size_t, C.c_uint32, C.c_void_p]),
     "gs3_workspace_read_header": (C.c_int, [C.c_void_p, C.POINTER(gs3_ws_header), C.c_void_p]),
+    "gs3_backward_workspace_size": (C.c_size_t, [_SCENE_P]),
+    "gs3_render_backward": (C.c_int, [_SCENE_P, C.POINTER(gs3_camera), C.POINTER(gs3_light),
+                                      C.POINTER(gs3_render_opts), C.c_void_p, C.c_void_p, C.c_size_t,
+                                      C.c_size_t, C.c_void_p, C.c_size_t, C.POINTER(gs3_grads),
+                                      C.c_void_p]),
     "gs3_server_create": (C.c_int, [C.POINTER(gs3_server_opts), C.POINTER(_SERVER_P)]),
     "gs3_server_add_scene": (C.c_int, [_SERVER_P, _SCENE_P, C.POINTER(C.c_int32)]),
     "gs3_server_submit": (C.c_int, [_SERVER_P, C.c_int32, C.POINTER(gs3_camera), C.POINTER(gs3_light),
@@ -202,6 +215,20 @@ def gs3_render_stages(scene, camera: gs3_camera, light: gs3_light, opts: gs3_ren
                                    _ptr(out_rgb), _ptr(workspace),
                                    workspace.numel() * workspace.element_size(), key_capacity,
                                    stages, stream), "gs3_render_stages")
+
+
+def gs3_backward_workspace_size(scene) -> int:
+    return int(lib().gs3_backward_workspace_size(scene))
+
+
+def gs3_render_backward(scene, camera: gs3_camera, light: gs3_light, opts: gs3_render_opts, dl_drgb,
+                        workspace, key_capacity: int, bwd_ws, grads: dict, stream: int) -> None:
+    g = gs3_grads(*[_ptr(grads[f]) for f in GRAD_FIELDS])
+    _check(lib().gs3_render_backward(scene, C.byref(camera), C.byref(light), C.byref(opts),
+                                     _ptr(dl_drgb), _ptr(workspace),
+                                     workspace.numel() * workspace.element_size(), key_capacity,
+                                     _ptr(bwd_ws), bwd_ws.numel() * bwd_ws.element_size(),
+                                     C.byref(g), stream), "gs3_render_backward")
 
 
 def gs3_workspace_read_header(workspace, stream: int) -> gs3_ws_header:

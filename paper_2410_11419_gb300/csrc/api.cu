@@ -2,6 +2,7 @@
 // and the stream-ordered launch sequence of one frame.
 #include <atomic>
 #include <cstdio>
+#include <cmath>
 #include <cstring>
 #include <string>
 
@@ -124,6 +125,9 @@ Workspace plan_workspace(int n, int width, int height, size_t cap) {
   L.ccol = P.take(32 * N);
   L.final_t = P.take(4 * (size_t)width * height);
   L.n_contrib = P.take(4 * (size_t)width * height);
+  L.pix_aux = P.take(32 * (size_t)width * height);
+  L.light_final = P.take(4 * (size_t)width * height);
+  L.shadow_den = P.take(4 * N);
   L.total = P.cur;
   return L;
 }
@@ -321,6 +325,63 @@ gs3_status gs3_render(gs3_scene* scene, const gs3_camera* cam, const gs3_light* 
                       size_t key_capacity, void* stream) {
   return gs3_render_stages(scene, cam, light, opts, out_rgb, workspace, ws_bytes, key_capacity,
                            GS3_STAGE_ALL, stream);
+}
+
+size_t gs3_backward_workspace_size(const gs3_scene* scene) {
+  if (!scene) return 0;
+  return backward_workspace_bytes(scene->dev.n, scene->dev.phi, scene->dev.psi);
+}
+
+// light camera of the frame, the same FP32 recipe as the forward kernel's
+static void light_view_host(const float pL[3], const float tg[3], float R[9], float t[3]);
+
+gs3_status gs3_render_backward(gs3_scene* scene, const gs3_camera* cam, const gs3_light* light,
+                               const gs3_render_opts* opts, const float* dimg, void* workspace,
+                               size_t ws_bytes, size_t key_capacity, void* bws, size_t bws_bytes,
+                               const gs3_grads* grads, void* stream) {
+  if (!scene || !cam || !light || !opts || !dimg || !workspace || !bws || !grads)
+    return fail(GS3_ERR_INVALID_ARG, "gs3_render_backward: null argument");
+  if (scene->dev.mlp_dtype != GS3_MLP_FP32)
+    return fail(GS3_ERR_UNSUPPORTED, "gs3_render_backward: needs a GS3_MLP_FP32 scene");
+  if (cam->width < 1 || cam->height < 1 || opts->tile != kTile)
+    return fail(GS3_ERR_INVALID_ARG, "gs3_render_backward: bad camera or options");
+  Workspace L = plan_workspace(scene->dev.n, cam->width, cam->height, key_capacity);
+  if (ws_bytes < L.total || !device_range_ok(workspace, L.total))
+    return fail(GS3_ERR_INVALID_ARG, "gs3_render_backward: workspace too small");
+  if (!device_range_ok(dimg, (size_t)cam->width * cam->height * 3 * sizeof(float)))
+    return fail(GS3_ERR_INVALID_ARG, "gs3_render_backward: dL_drgb is not width*height*3 floats");
+  const size_t need = backward_workspace_bytes(scene->dev.n, scene->dev.phi, scene->dev.psi);
+  if (bws_bytes < need || !device_range_ok(bws, need))
+    return fail(GS3_ERR_INVALID_ARG, "gs3_render_backward: backward workspace too small");
+  FrameArgs f;
+  f.sc = scene->dev;
+  f.cam = *cam;
+  f.light = *light;
+  f.opts = *opts;
+  f.ws = static_cast<unsigned char*>(workspace);
+  f.L = &L;
+  light_view_host(light->pos, opts->target, f.light_view, f.light_view + 9);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  gs3_status st = run_backward(f, dimg, bws, bws_bytes, *grads, s);
+  if (st != GS3_OK) return fail(st, "gs3_render_backward: bad workspace");
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "gs3_render_backward: launch");
+  return GS3_OK;
+}
+
+static void light_view_host(const float pL[3], const float tg[3], float R[9], float t[3]) {
+  // gradients only need the rotation to float accuracy; plain float arithmetic
+  float fx = tg[0] - pL[0], fy = tg[1] - pL[1], fz = tg[2] - pL[2];
+  float n = sqrtf(fx * fx + fy * fy + fz * fz);
+  fx /= n; fy /= n; fz /= n;
+  float ux = 0.f, uy = 0.f, uz = 1.f;
+  if (fabsf(fz) > 0.999f) { uy = 1.f; uz = 0.f; }
+  float rx = fy * uz - fz * uy, ry = fz * ux - fx * uz, rz = fx * uy - fy * ux;
+  float rn = sqrtf(rx * rx + ry * ry + rz * rz);
+  rx /= rn; ry /= rn; rz /= rn;
+  const float dx = fy * rz - fz * ry, dy = fz * rx - fx * rz, dz = fx * ry - fy * rx;
+  R[0] = rx; R[1] = ry; R[2] = rz; R[3] = dx; R[4] = dy; R[5] = dz; R[6] = fx; R[7] = fy; R[8] = fz;
+  for (int i = 0; i < 3; ++i) t[i] = -(R[3 * i] * pL[0] + R[3 * i + 1] * pL[1] + R[3 * i + 2] * pL[2]);
 }
 
 gs3_status gs3_workspace_read_header(const void* workspace, gs3_ws_header* out, void* stream) {

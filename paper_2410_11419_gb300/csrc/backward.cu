@@ -1,0 +1,1008 @@
+// Backward of the frame (differentiation form): gradients of a loss with
+// respect to every scene parameter and MLP weight, given dL/d(image).
+//
+// Reverse order of the forward, reading the forward's workspace:
+//   K9b  camera composite, back to front per pixel from the stored final
+//        transmittance, recovering T by division (per-tile recomputation; no
+//        per-pixel lists are stored)                          (Eq. 2, Sec. 4)
+//   K8b  Psi and Phi: forward recomputed per 32-row tile, backward through
+//        the layers, weight gradients as per-block partials summed in a fixed
+//        order                                                  (Sec. 4.2, 4.3)
+//   K6b  shadow splat: per shadow ray, back to front from the stored final
+//        occluder product; receivers j add (dL/dT_j / den_j) beta T_m(j) to a
+//        suffix sum S; an occluder k gets dL/dalpha = -S / (1 - alpha)  (Sec. 4.2)
+//   K1b  per Gaussian: both EWA projections and the shading back to the
+//        parameters                                       (Eq. 1-5, Sec. 3, 4.1)
+// Per-Gaussian accumulators are summed with float atomics (after warp
+// reductions); the result is deterministic up to the order of those atomics.
+#include "gs3_internal.cuh"
+
+namespace gs3 {
+namespace {
+
+constexpr int kGeom = 8;    // du, dv, dA, dB, dC, dgamma
+constexpr int kColor = 8;   // dshade rgb, dT', dres rgb
+constexpr int kMlpIn = 24;  // Phi: dmu 3, dwi 3, dl 6; Psi: dmu 3, dwo 3, dl 6
+constexpr int kBwdBlocksMlp = 296;
+constexpr int kMlpRows = 32;
+
+struct BwdBufs {
+  float* cam_geom;    // [N][8]
+  float* light_geom;  // [N][8]
+  float* color;       // [N][8]
+  float* dT;          // [N]
+  float* mlp_in;      // [N][24]
+  float* wpart[2];    // [kBwdBlocksMlp][params] weight/bias gradient partials
+};
+
+__host__ __device__ size_t mlp_params(const MlpDev& m) {
+  size_t s = 0;
+  int din = m.in_dim;
+  for (int l = 0; l <= m.n_hidden; ++l) {
+    const int dout = l == m.n_hidden ? m.out_dim : m.width;
+    s += (size_t)dout * din + dout;
+    din = dout;
+  }
+  return s;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+struct BwdPlan {
+  size_t cam_geom, light_geom, color, dT, mlp_in, wred[2], wpart[2], total;
+};
+
+BwdPlan plan_bwd(int n, const MlpDev& phi, const MlpDev& psi) {
+  BwdPlan p;
+  size_t c = 0;
+  auto take = [&](size_t b) { size_t o = c; c = align256(c + b); return o; };
+  p.cam_geom = take(4ull * kGeom * n);
+  p.light_geom = take(4ull * kGeom * n);
+  p.color = take(4ull * kColor * n);
+  p.dT = take(4ull * n);
+  p.mlp_in = take(4ull * kMlpIn * n);
+  p.wred[0] = take(4ull * mlp_params(phi));
+  p.wred[1] = take(4ull * mlp_params(psi));
+  p.wpart[0] = take(4ull * kBwdBlocksMlp * mlp_params(phi));
+  p.wpart[1] = take(4ull * kBwdBlocksMlp * mlp_params(psi));
+  p.total = c;
+  return p;
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// sum over the warp and add to dst[0..n) from lane 0 (skipped when all zero)
+template <int NV>
+__device__ __forceinline__ void warp_atomic(float* dst, float (&v)[NV], bool any_lane) {
+  if (!__any_sync(0xffffffffu, any_lane)) return;
+#pragma unroll
+  for (int i = 0; i < NV; ++i) v[i] = warp_sum(v[i]);
+  if ((threadIdx.x & 31) == 0)
+#pragma unroll
+    for (int i = 0; i < NV; ++i)
+      if (v[i] != 0.f) atomicAdd(dst + i, v[i]);
+}
+
+// pixel offset, power and alpha of a splat record at a pixel centre
+struct Eval {
+  float dx, dy, power, beta, alpha;
+  bool pass, clamped;
+};
+__device__ __forceinline__ Eval eval_rec(const SplatRec& q, float fx, float fy, float amax) {
+  Eval r;
+  r.dx = (fx - q.a.x) - q.b.w;
+  r.dy = (fy - q.a.y) - q.c.x;
+  r.power = -0.5f * (q.b.x * r.dx * r.dx + q.b.z * r.dy * r.dy) - q.b.y * r.dx * r.dy;
+  r.pass = r.power >= q.c.w && r.power <= 0.f;
+  r.beta = r.pass ? __expf(r.power) : 0.f;
+  const float ga = q.a.z * r.beta;
+  r.clamped = ga >= amax;
+  r.alpha = fminf(amax, ga);
+  return r;
+}
+
+// dL/dpower -> (du, dv, dA, dB, dC)
+__device__ __forceinline__ void power_grad(const SplatRec& q, const Eval& e, float dpow, float* g) {
+  const float A = q.b.x, B = q.b.y, C = q.b.z;
+  g[0] = (A * e.dx + B * e.dy) * dpow;
+  g[1] = (C * e.dy + B * e.dx) * dpow;
+  g[2] = -0.5f * e.dx * e.dx * dpow;
+  g[3] = -e.dx * e.dy * dpow;
+  g[4] = -0.5f * e.dy * e.dy * dpow;
+}
+
+// ---------------------------------------------------------------------------
+// K9b: camera composite backward
+// ---------------------------------------------------------------------------
+struct CamBwdParams {
+  const uint32_t* list;
+  const uint32_t* tile_start;
+  const SplatRec* rrec;
+  const float4* ccol;
+  const uint32_t* order;
+  const float* final_t;
+  const uint32_t* n_contrib;
+  const float4* pix_aux;
+  const float* dimg;
+  float* cam_geom;
+  float* color;
+  int W, H, gx;
+  float amax;
+};
+
+__global__ void __launch_bounds__(256) k_camera_bwd(CamBwdParams p) {
+  __shared__ SplatRec R[256];
+  __shared__ float4 C0[256], C1[256];
+  __shared__ uint32_t G[256];
+  __shared__ int s_max;
+  const int tile = blockIdx.x, tx = tile % p.gx, ty = tile / p.gx, t = threadIdx.x;
+  const int px = tx * kTile + (t & 15), py = ty * kTile + (t >> 4);
+  const bool inside = px < p.W && py < p.H;
+  const float fx = px + 0.5f, fy = py + 0.5f;
+  const uint32_t b = p.tile_start[tile];
+  const size_t pix = (size_t)py * p.W + px;
+  uint32_t nc = 0;
+  float T = 1.f, g7[7] = {0, 0, 0, 0, 0, 0, 0};
+  if (inside) {
+    nc = p.n_contrib[pix];
+    T = p.final_t[pix];
+    const float4 s = p.pix_aux[2 * pix], r = p.pix_aux[2 * pix + 1];
+    const float gr = p.dimg[3 * pix], gg = p.dimg[3 * pix + 1], gb = p.dimg[3 * pix + 2];
+    g7[0] = gr * s.w; g7[1] = gg * s.w; g7[2] = gb * s.w;
+    g7[3] = gr * s.x + gg * s.y + gb * s.z;
+    g7[4] = gr; g7[5] = gg; g7[6] = gb;
+    (void)r;
+  }
+  if (t == 0) s_max = 0;
+  __syncthreads();
+  atomicMax(&s_max, (int)nc);
+  __syncthreads();
+  const uint32_t end = min(b + (uint32_t)s_max, p.tile_start[tile + 1]);
+  float B7[7] = {0, 0, 0, 0, 0, 0, 0};
+  for (uint32_t hi = end; hi > b; ) {
+    const uint32_t lo = hi > b + 256 ? hi - 256 : b;
+    const int cnt = (int)(hi - lo);
+    __syncthreads();
+    if (t < cnt) {
+      const uint32_t rank = p.list[lo + t];
+      R[t] = p.rrec[rank];
+      C0[t] = p.ccol[2 * rank];
+      C1[t] = p.ccol[2 * rank + 1];
+      G[t] = p.order[rank];
+    }
+    __syncthreads();
+    for (int jj = cnt - 1; jj >= 0; --jj) {
+      const uint32_t i = lo + jj;
+      const bool active = inside && (i - b) < nc;
+      float gv[13];
+#pragma unroll
+      for (int k = 0; k < 13; ++k) gv[k] = 0.f;
+      bool contrib = false;
+      if (active) {
+        const SplatRec q = R[jj];
+        const Eval ev = eval_rec(q, fx, fy, p.amax);
+        if (ev.pass) {
+          contrib = true;
+          T = T / (1.f - ev.alpha);
+          const float w = ev.alpha * T;
+          const float c[7] = {C0[jj].x, C0[jj].y, C0[jj].z, C0[jj].w, C1[jj].x, C1[jj].y, C1[jj].z};
+          float dalpha = 0.f;
+          const float inv = 1.f / (1.f - ev.alpha);
+#pragma unroll
+          for (int k = 0; k < 7; ++k) {
+            gv[6 + k] = w * g7[k];
+            dalpha += g7[k] * (c[k] * T - B7[k] * inv);
+            B7[k] += w * c[k];
+          }
+          if (!ev.clamped) {
+            gv[5] = dalpha * ev.beta;
+            power_grad(q, ev, dalpha * ev.alpha, gv);
+          }
+        }
+      }
+      if (__any_sync(0xffffffffu, contrib)) {
+#pragma unroll
+        for (int k = 0; k < 13; ++k) gv[k] = warp_sum(gv[k]);
+        if ((t & 31) == 0) {
+          const uint32_t g = G[jj];
+#pragma unroll
+          for (int k = 0; k < 6; ++k)
+            if (gv[k] != 0.f) atomicAdd(p.cam_geom + (size_t)kGeom * g + k, gv[k]);
+#pragma unroll
+          for (int k = 0; k < 7; ++k)
+            if (gv[6 + k] != 0.f) atomicAdd(p.color + (size_t)kColor * g + k, gv[6 + k]);
+        }
+      }
+    }
+    hi = lo;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// K8b: MLP backward (FP32).  Block = 128 threads, tiles of 32 rows.
+// ---------------------------------------------------------------------------
+struct MlpBwdParams {
+  MlpDev net;
+  int n, which;
+  const float4* mean_op;
+  const float4* latent;
+  const float* T;
+  float light_pos[3], cam_pos[3];
+  const float* color;  // [N][8]: dT' at 3, dres at 4..6
+  float* dT;           // Phi: d/d(input T)
+  float* mlp_in;       // [N][24]
+  float* wpart;        // [blocks][params]
+};
+
+__device__ __forceinline__ void pe_fwd(float* x, int base, float v0, float v1, float v2) {
+  x[base + 0] = v0; x[base + 1] = v1; x[base + 2] = v2;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const float f = (float)(1 << q);
+    const int o = base + 3 + 6 * q;
+    sincospif(f * v0, &x[o + 0], &x[o + 3]);
+    sincospif(f * v1, &x[o + 1], &x[o + 4]);
+    sincospif(f * v2, &x[o + 2], &x[o + 5]);
+  }
+}
+// d/dv of PE(v) given d/dPE
+__device__ __forceinline__ void pe_bwd(const float* dpe, float v0, float v1, float v2, float* dv) {
+  const float v[3] = {v0, v1, v2};
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    float g = dpe[c];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float f = (float)(1 << q);
+      float s, co;
+      sincospif(f * v[c], &s, &co);
+      const float k = f * 3.14159265358979323846f;
+      g += k * (co * dpe[3 + 6 * q + c] - s * dpe[3 + 6 * q + 3 + c]);
+    }
+    dv[c] = g;
+  }
+}
+
+constexpr int kMaxW = 128;
+constexpr int kMaxIn = 64;
+
+__global__ void __launch_bounds__(128) k_mlp_bwd(MlpBwdParams p) {
+  extern __shared__ float4 smem4[];
+  float* sm = reinterpret_cast<float*>(smem4);
+  const int nh = p.net.n_hidden, W = p.net.width, din0 = p.net.in_dim, dout = p.net.out_dim;
+  // activations H[l][r][k] for l = 0 (input) .. nh, stride kMaxW + 1; dZ and dH buffers
+  const int S = kMaxW + 1;
+  float* Hbuf = sm;                                   // (nh + 1) x 32 x S
+  float* dZ = Hbuf + (size_t)(nh + 1) * kMlpRows * S;  // 32 x S
+  float* dH = dZ + kMlpRows * S;                       // 32 x S
+  float* Y = dH + kMlpRows * S;                        // 32 x 4 outputs
+  const int t = threadIdx.x;
+  float* part = p.wpart + (size_t)blockIdx.x * mlp_params(p.net);
+  // zero this block's partial
+  for (size_t i = t; i < mlp_params(p.net); i += blockDim.x) part[i] = 0.f;
+  __syncthreads();
+  const int ntiles = (p.n + kMlpRows - 1) / kMlpRows;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int g0 = tile * kMlpRows;
+    // ---- inputs ----
+    if (t < kMlpRows) {
+      const int g = min(g0 + t, p.n - 1);
+      float x[kMaxIn];
+      const float4 m = p.mean_op[g];
+      const float* src = p.which == 0 ? p.light_pos : p.cam_pos;
+      float dx = src[0] - m.x, dy = src[1] - m.y, dz = src[2] - m.z;
+      const float il = rsqrtf(dx * dx + dy * dy + dz * dz);
+      const int b0 = p.which == 0 ? 1 : 0;
+      if (p.which == 0) x[0] = p.T[g];
+      pe_fwd(x, b0, dx * il, dy * il, dz * il);
+      pe_fwd(x, b0 + 27, m.x, m.y, m.z);
+      const float4 l0 = p.latent[g], l1 = p.latent[p.n + g];
+      x[b0 + 54] = l0.x; x[b0 + 55] = l0.y; x[b0 + 56] = l0.z; x[b0 + 57] = l0.w;
+      x[b0 + 58] = l1.x; x[b0 + 59] = l1.y;
+      for (int k = 0; k < din0; ++k) Hbuf[t * S + k] = x[k];
+    }
+    __syncthreads();
+    // ---- forward, hidden layers (thread j owns output column j) ----
+    const float* w = p.net.w;
+    const float* bb = p.net.b;
+    int din = din0;
+    for (int l = 0; l < nh; ++l) {
+      const float* Hin = Hbuf + (size_t)l * kMlpRows * S;
+      float* Hout = Hbuf + (size_t)(l + 1) * kMlpRows * S;
+      if (t < W) {
+        float acc[kMlpRows];
+        const float bj = bb[t];
+#pragma unroll
+        for (int r = 0; r < kMlpRows; ++r) acc[r] = bj;
+        for (int k = 0; k < din; ++k) {
+          const float wk = w[(size_t)t * din + k];
+#pragma unroll
+          for (int r = 0; r < kMlpRows; ++r) acc[r] = fmaf(Hin[r * S + k], wk, acc[r]);
+        }
+        const bool leaky = p.net.act == GS3_ACT_LEAKY_RELU;
+#pragma unroll
+        for (int r = 0; r < kMlpRows; ++r) {
+          const float v = acc[r];
+          Hout[r * S + t] = v > 0.f ? v : (leaky ? 0.01f * v : 0.f);
+        }
+      }
+      __syncthreads();
+      w += (size_t)W * din;
+      bb += W;
+      din = W;
+    }
+    // ---- output layer: y and dz_out ----
+    const float* Hl = Hbuf + (size_t)nh * kMlpRows * S;
+    if (t < kMlpRows * dout) {
+      const int r = t % kMlpRows, o = t / kMlpRows;
+      float acc = bb[o];
+      for (int k = 0; k < W; ++k) acc = fmaf(Hl[r * S + k], w[(size_t)o * W + k], acc);
+      const float y = 1.f / (1.f + expf(-acc));
+      const int g = g0 + r;
+      float dy = 0.f;
+      if (g < p.n) dy = p.which == 0 ? p.color[(size_t)kColor * g + 3] : p.color[(size_t)kColor * g + 4 + o];
+      Y[r * 4 + o] = dy * y * (1.f - y);
+    }
+    __syncthreads();
+    // output-layer weight/bias gradients and dH of the last hidden layer
+    size_t poff = 0;
+    {
+      // offsets of each layer's parameters in the partial: hidden layers first
+      size_t woff_out = 0;
+      int dd = din0;
+      for (int l = 0; l < nh; ++l) { woff_out += (size_t)W * dd + W; dd = W; }
+      poff = woff_out;
+      if (t < W) {
+        for (int o = 0; o < dout; ++o) {
+          float s = 0.f;
+#pragma unroll 8
+          for (int r = 0; r < kMlpRows; ++r) s = fmaf(Y[r * 4 + o], Hl[r * S + t], s);
+          part[poff + (size_t)o * W + t] += s;
+        }
+      }
+      if (t < dout) {
+        float s = 0.f;
+        for (int r = 0; r < kMlpRows; ++r) s += Y[r * 4 + t];
+        part[poff + (size_t)dout * W + t] += s;
+      }
+      if (t < W) {
+        const bool leaky = p.net.act == GS3_ACT_LEAKY_RELU;
+        for (int r = 0; r < kMlpRows; ++r) {
+          float s = 0.f;
+          for (int o = 0; o < dout; ++o) s = fmaf(Y[r * 4 + o], w[(size_t)o * W + t], s);
+          const float h = Hl[r * S + t];
+          dZ[r * S + t] = h > 0.f ? s : (leaky ? 0.01f * s : 0.f);
+        }
+      }
+    }
+    __syncthreads();
+    // ---- hidden layers backward ----
+    for (int l = nh - 1; l >= 0; --l) {
+      const int dinl = l == 0 ? din0 : W;
+      size_t lo = 0;
+      int dd = din0;
+      for (int q = 0; q < l; ++q) { lo += (size_t)W * dd + W; dd = W; }
+      const float* Wl = p.net.w;
+      { int d2 = din0; for (int q = 0; q < l; ++q) { Wl += (size_t)W * d2; d2 = W; } }
+      const float* Hin = Hbuf + (size_t)l * kMlpRows * S;
+      // dW_l[j][k] += sum_r dZ[r][j] Hin[r][k]; thread j owns row j
+      if (t < W) {
+        for (int k = 0; k < dinl; ++k) {
+          float s = 0.f;
+#pragma unroll 8
+          for (int r = 0; r < kMlpRows; ++r) s = fmaf(dZ[r * S + t], Hin[r * S + k], s);
+          part[lo + (size_t)t * dinl + k] += s;
+        }
+        float sb = 0.f;
+        for (int r = 0; r < kMlpRows; ++r) sb += dZ[r * S + t];
+        part[lo + (size_t)W * dinl + t] += sb;
+      }
+      // dH_{l-1}[r][k] = sum_j dZ[r][j] W_l[j][k]; thread k owns column k
+      if (t < dinl) {
+        float acc[kMlpRows];
+#pragma unroll
+        for (int r = 0; r < kMlpRows; ++r) acc[r] = 0.f;
+        for (int j = 0; j < W; ++j) {
+          const float wjk = Wl[(size_t)j * dinl + t];
+#pragma unroll
+          for (int r = 0; r < kMlpRows; ++r) acc[r] = fmaf(dZ[r * S + j], wjk, acc[r]);
+        }
+        const bool leaky = p.net.act == GS3_ACT_LEAKY_RELU;
+#pragma unroll
+        for (int r = 0; r < kMlpRows; ++r) {
+          if (l > 0) {
+            const float h = Hin[r * S + t];
+            dH[r * S + t] = h > 0.f ? acc[r] : (leaky ? 0.01f * acc[r] : 0.f);
+          } else {
+            dH[r * S + t] = acc[r];
+          }
+        }
+      }
+      __syncthreads();
+      // dH becomes the next dZ
+      for (int i = t; i < kMlpRows * S; i += blockDim.x) dZ[i] = dH[i];
+      __syncthreads();
+    }
+    // ---- input gradients: dZ now holds d/dx ----
+    if (t < kMlpRows && g0 + t < p.n) {
+      const int g = g0 + t;
+      const float* dx = dZ + t * S;
+      const float4 m = p.mean_op[g];
+      const float* src = p.which == 0 ? p.light_pos : p.cam_pos;
+      float vx = src[0] - m.x, vy = src[1] - m.y, vz = src[2] - m.z;
+      const float il = rsqrtf(vx * vx + vy * vy + vz * vz);
+      const int b0 = p.which == 0 ? 1 : 0;
+      float dw[3], dm[3];
+      pe_bwd(dx + b0, vx * il, vy * il, vz * il, dw);
+      pe_bwd(dx + b0 + 27, m.x, m.y, m.z, dm);
+      float* out = p.mlp_in + (size_t)kMlpIn * g + (p.which == 0 ? 0 : 12);
+      out[0] = dm[0]; out[1] = dm[1]; out[2] = dm[2];
+      out[3] = dw[0]; out[4] = dw[1]; out[5] = dw[2];
+      for (int k = 0; k < 6; ++k) out[6 + k] = dx[b0 + 54 + k];
+      if (p.which == 0) p.dT[g] = dx[0];
+    }
+    __syncthreads();
+  }
+}
+
+// sum the per-block partials in block order
+__global__ void k_reduce_parts(const float* part, size_t np, int nblocks, float* red) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= np) return;
+  float s = 0.f;
+  for (int b = 0; b < nblocks; ++b) s += part[(size_t)b * np + i];
+  red[i] = s;
+}
+
+__global__ void k_copy_strided(const float* src, int stride, int off, float* dst, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = src[(size_t)stride * i + off];
+}
+
+// ---------------------------------------------------------------------------
+// K6b: shadow splat backward
+// ---------------------------------------------------------------------------
+struct ShadowBwdParams {
+  const uint32_t* list;
+  const uint32_t* tile_start;
+  const SplatRec* rrec;
+  const uint32_t* order;
+  const uint32_t* kbound;
+  const float* light_final;
+  const float* dT;   // by index
+  const float* den;  // by index
+  const float* T;    // by index
+  float* light_geom;
+  int W, H, gx;
+  float amax;
+};
+
+constexpr int kBRecv = 128;
+constexpr int kBOcc = 512;
+
+__global__ void __launch_bounds__(256) k_shadow_bwd(ShadowBwdParams p) {
+  __shared__ SplatRec RR[kBRecv];
+  __shared__ uint32_t RK[kBRecv], RG[kBRecv];
+  __shared__ float RC[kBRecv], RT[kBRecv];
+  __shared__ SplatRec OR[kBOcc];
+  __shared__ uint32_t OG[kBOcc];
+  const int tile = blockIdx.x, tx = tile % p.gx, ty = tile / p.gx, t = threadIdx.x;
+  const int px = tx * kTile + (t & 15), py = ty * kTile + (t >> 4);
+  const bool inside = px < p.W && py < p.H;
+  const float fx = px + 0.5f, fy = py + 0.5f;
+  const uint32_t b = p.tile_start[tile], e = p.tile_start[tile + 1];
+  if (b == e) return;
+  float A = inside ? p.light_final[(size_t)py * p.W + px] : 1.f;
+  float S = 0.f;
+  uint32_t kc = p.kbound[e - 1];
+
+  auto occlude = [&](const SplatRec& q, uint32_t g) {
+    float gv[6] = {0, 0, 0, 0, 0, 0};
+    bool c = false;
+    if (inside) {
+      const Eval ev = eval_rec(q, fx, fy, p.amax);
+      if (ev.pass) {
+        const float inv = 1.f / (1.f - ev.alpha);
+        const float dalpha = -S * inv;
+        A *= inv;
+        if (!ev.clamped && dalpha != 0.f) {
+          c = true;
+          gv[5] = dalpha * ev.beta;
+          power_grad(q, ev, dalpha * ev.alpha, gv);
+        }
+      }
+    }
+    warp_atomic<6>(p.light_geom + (size_t)kGeom * g, gv, c);
+  };
+
+  for (uint32_t re = e; re > b;) {
+    const uint32_t rs = re > b + kBRecv ? re - kBRecv : b;
+    const int rc = (int)(re - rs);
+    __syncthreads();
+    if (t < rc) {
+      const uint32_t rank = p.list[rs + t];
+      const uint32_t g = p.order[rank];
+      RR[t] = p.rrec[rank];
+      RK[t] = p.kbound[rs + t];
+      RG[t] = g;
+      const float den = p.den[g];
+      RC[t] = den > 0.f ? p.dT[g] / den : 0.f;
+      RT[t] = p.T[g];
+    }
+    __syncthreads();
+    int jj = rc - 1;
+    while (jj >= 0) {
+      const uint32_t kfirst = RK[0];
+      const uint32_t kt = kc > kfirst + kBOcc ? kc - kBOcc : kfirst;
+      __syncthreads();
+      for (uint32_t i = t; i < kc - kt; i += blockDim.x) {
+        const uint32_t rank = p.list[kt + i];
+        OR[i] = p.rrec[rank];
+        OG[i] = p.order[rank];
+      }
+      __syncthreads();
+      for (; jj >= 0; --jj) {
+        const uint32_t kend = RK[jj];
+        if (kend < kt) break;
+        for (; kc > kend; --kc) occlude(OR[kc - 1 - kt], OG[kc - 1 - kt]);
+        // receiver jj
+        float gv[6] = {0, 0, 0, 0, 0, 0};
+        bool c = false;
+        if (inside) {
+          const SplatRec q = RR[jj];
+          const Eval ev = eval_rec(q, fx, fy, p.amax);
+          if (ev.pass) {
+            const float coef = RC[jj];
+            S = fmaf(coef * ev.beta, A, S);
+            const float dbeta = coef * (A - RT[jj]);
+            if (dbeta != 0.f) {
+              c = true;
+              power_grad(q, ev, dbeta * ev.beta, gv);
+            }
+          }
+        }
+        warp_atomic<6>(p.light_geom + (size_t)kGeom * RG[jj], gv, c);
+      }
+      for (; kc > kt; --kc) occlude(OR[kc - 1 - kt], OG[kc - 1 - kt]);
+    }
+    re = rs;
+  }
+  // occluders before every receiver's prefix end: S already holds all receivers
+  while (kc > b) {
+    const uint32_t kt = kc > b + kBOcc ? kc - kBOcc : b;
+    __syncthreads();
+    for (uint32_t i = t; i < kc - kt; i += blockDim.x) {
+      const uint32_t rank = p.list[kt + i];
+      OR[i] = p.rrec[rank];
+      OG[i] = p.order[rank];
+    }
+    __syncthreads();
+    for (; kc > kt; --kc) occlude(OR[kc - 1 - kt], OG[kc - 1 - kt]);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// K1b: per-Gaussian backward of both projections and the shading
+// ---------------------------------------------------------------------------
+struct M3 {
+  float m[9];
+};
+
+__device__ __forceinline__ void quat_rot(const float4 qr, float Rm[9], float qn[4], float& len) {
+  len = sqrtf(qr.x * qr.x + qr.y * qr.y + qr.z * qr.z + qr.w * qr.w);
+  const float w = qr.x / len, x = qr.y / len, y = qr.z / len, z = qr.w / len;
+  qn[0] = w; qn[1] = x; qn[2] = y; qn[3] = z;
+  Rm[0] = 1.f - 2.f * (y * y + z * z); Rm[1] = 2.f * (x * y - w * z);       Rm[2] = 2.f * (x * z + w * y);
+  Rm[3] = 2.f * (x * y + w * z);       Rm[4] = 1.f - 2.f * (x * x + z * z); Rm[5] = 2.f * (y * z - w * x);
+  Rm[6] = 2.f * (x * z - w * y);       Rm[7] = 2.f * (y * z + w * x);       Rm[8] = 1.f - 2.f * (x * x + y * y);
+}
+
+// dL/dR (row-major) of R(q / |q|) -> dL/dq
+__device__ __forceinline__ float4 quat_bwd(const float G[9], const float qn[4], float len) {
+  const float w = qn[0], x = qn[1], y = qn[2], z = qn[3];
+  float dw = 2.f * (-z * G[1] + y * G[2] + z * G[3] - x * G[5] - y * G[6] + x * G[7]);
+  float dx = 2.f * (y * G[1] + z * G[2] + y * G[3] - 2.f * x * G[4] - w * G[5] + z * G[6] + w * G[7] - 2.f * x * G[8]);
+  float dy = 2.f * (-2.f * y * G[0] + x * G[1] + w * G[2] + x * G[3] + z * G[5] - w * G[6] + z * G[7] - 2.f * y * G[8]);
+  float dz = 2.f * (-2.f * z * G[0] - w * G[1] + x * G[2] + w * G[3] - 2.f * z * G[4] + y * G[5] + x * G[6] + y * G[7]);
+  const float dot = w * dw + x * dx + y * dy + z * dz;
+  return make_float4((dw - w * dot) / len, (dx - x * dot) / len, (dy - y * dot) / len, (dz - z * dot) / len);
+}
+
+struct ViewB {
+  float R[9], t[3];
+  float fx, fy, lowpass;
+};
+
+// one EWA projection's backward; adds to dmu, ds and dR (of R(q))
+__device__ void proj_bwd(const float4 m, const float4 s, const float Rq[9], const ViewB& v, const float* gg,
+                         float dmu[3], float ds[3], float dRq[9]) {
+  const float* R = v.R;
+  const float x = R[0] * m.x + R[1] * m.y + R[2] * m.z + v.t[0];
+  const float y = R[3] * m.x + R[4] * m.y + R[5] * m.z + v.t[1];
+  const float z = R[6] * m.x + R[7] * m.y + R[8] * m.z + v.t[2];
+  const float iz = 1.f / z, iz2 = iz * iz;
+  const float sv[3] = {s.x, s.y, s.z};
+  float M[9], Sg[9];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) M[3 * i + j] = Rq[3 * i + j] * sv[j];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) Sg[3 * i + j] = M[3 * i] * M[3 * j] + M[3 * i + 1] * M[3 * j + 1] + M[3 * i + 2] * M[3 * j + 2];
+  const float J00 = v.fx * iz, J02 = -v.fx * x * iz2, J11 = v.fy * iz, J12 = -v.fy * y * iz2;
+  float T[6];
+  for (int k = 0; k < 3; ++k) {
+    T[k] = J00 * R[k] + J02 * R[6 + k];
+    T[3 + k] = J11 * R[3 + k] + J12 * R[6 + k];
+  }
+  float TS[6];  // T Sigma
+  for (int i = 0; i < 2; ++i)
+    for (int k = 0; k < 3; ++k)
+      TS[3 * i + k] = T[3 * i] * Sg[k] + T[3 * i + 1] * Sg[3 + k] + T[3 * i + 2] * Sg[6 + k];
+  const float a = TS[0] * T[0] + TS[1] * T[1] + TS[2] * T[2] + v.lowpass;
+  const float b = TS[0] * T[3] + TS[1] * T[4] + TS[2] * T[5];
+  const float c = TS[3] * T[3] + TS[4] * T[4] + TS[5] * T[5] + v.lowpass;
+  const float det = a * c - b * b, id = 1.f / det;
+  const float CA = c * id, CB = -b * id, CC = a * id;
+  // d/d(a, b, c) = -C Gs C with Gs = [[dA, dB/2], [dB/2, dC]]
+  const float gA = gg[2], gB = 0.5f * gg[3], gC = gg[4];
+  const float X00 = CA * gA + CB * gB, X01 = CA * gB + CB * gC;
+  const float X10 = CB * gA + CC * gB, X11 = CB * gB + CC * gC;
+  const float D00 = -(X00 * CA + X01 * CB), D01 = -(X00 * CB + X01 * CC), D11 = -(X10 * CB + X11 * CC);
+  // G2 (symmetric) = [[D00, D01], [D01, D11]];  dT = 2 G2 T Sigma;  dSigma = T^T G2 T
+  float dT[6];
+  for (int k = 0; k < 3; ++k) {
+    dT[k] = 2.f * (D00 * TS[k] + D01 * TS[3 + k]);
+    dT[3 + k] = 2.f * (D01 * TS[k] + D11 * TS[3 + k]);
+  }
+  float dS[9];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j)
+      dS[3 * i + j] = T[i] * (D00 * T[j] + D01 * T[3 + j]) + T[3 + i] * (D01 * T[j] + D11 * T[3 + j]);
+  // dM = 2 dSigma M;  M = Rq diag(s)
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      const float dM = 2.f * (dS[3 * i] * M[j] + dS[3 * i + 1] * M[3 + j] + dS[3 * i + 2] * M[6 + j]);
+      dRq[3 * i + j] += dM * sv[j];
+      ds[j] += dM * Rq[3 * i + j];
+    }
+  // T = J R:  dJ = dT R^T
+  const float dJ00 = dT[0] * R[0] + dT[1] * R[1] + dT[2] * R[2];
+  const float dJ02 = dT[0] * R[6] + dT[1] * R[7] + dT[2] * R[8];
+  const float dJ11 = dT[3] * R[3] + dT[4] * R[4] + dT[5] * R[5];
+  const float dJ12 = dT[3] * R[6] + dT[4] * R[7] + dT[5] * R[8];
+  const float du = gg[0], dv = gg[1];
+  const float dx = du * v.fx * iz + dJ02 * (-v.fx * iz2);
+  const float dy = dv * v.fy * iz + dJ12 * (-v.fy * iz2);
+  const float dz = du * (-v.fx * x * iz2) + dv * (-v.fy * y * iz2) + dJ00 * (-v.fx * iz2) +
+                   dJ02 * (2.f * v.fx * x * iz2 * iz) + dJ11 * (-v.fy * iz2) + dJ12 * (2.f * v.fy * y * iz2 * iz);
+  dmu[0] += R[0] * dx + R[3] * dy + R[6] * dz;
+  dmu[1] += R[1] * dx + R[4] * dy + R[7] * dz;
+  dmu[2] += R[2] * dx + R[5] * dy + R[8] * dz;
+}
+
+struct PrepBwdParams {
+  SceneDev sc;
+  ViewB cam, light;
+  float light_pos[3], cam_pos[3], intensity;
+  int falloff;
+  const float* cam_geom;
+  const float* light_geom;
+  const float* color;
+  const float* mlp_in;
+  gs3_grads out;
+};
+
+__global__ void __launch_bounds__(128) k_prep_bwd(PrepBwdParams p) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = p.sc.n;
+  if (g >= n) return;
+  const float4 m = p.sc.mean_op[g], s = p.sc.scale[g];
+  const float gamma = 1.f / (1.f + expf(-m.w));
+  const float* gc = p.cam_geom + (size_t)kGeom * g;
+  const float* gl = p.light_geom + (size_t)kGeom * g;
+  float dmu[3] = {0, 0, 0}, ds[3] = {0, 0, 0}, dRq[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  float Rq[9], qn[4], qlen;
+  quat_rot(p.sc.rot[g], Rq, qn, qlen);
+  proj_bwd(m, s, Rq, p.cam, gc, dmu, ds, dRq);
+  proj_bwd(m, s, Rq, p.light, gl, dmu, ds, dRq);
+  const float4 dq = quat_bwd(dRq, qn, qlen);
+  const float dgamma = gc[5] + gl[5];
+  const float dlogit = dgamma * gamma * (1.f - gamma);
+
+  // ---- shading backward (Eq. 2-5) ----
+  const float* dcol = p.color + (size_t)kColor * g;
+  const float lx = p.light_pos[0] - m.x, ly = p.light_pos[1] - m.y, lz = p.light_pos[2] - m.z;
+  const float d2 = lx * lx + ly * ly + lz * lz, dl = sqrtf(d2);
+  const float wi[3] = {lx / dl, ly / dl, lz / dl};
+  const float vx = p.cam_pos[0] - m.x, vy = p.cam_pos[1] - m.y, vz = p.cam_pos[2] - m.z;
+  const float dvn = sqrtf(vx * vx + vy * vy + vz * vz);
+  const float wo[3] = {vx / dvn, vy / dvn, vz / dvn};
+  float Rs[9], qs[4], qslen;
+  quat_rot(p.sc.shade_rot[g], Rs, qs, qslen);
+  float wil[3], wol[3];
+  for (int i = 0; i < 3; ++i) {
+    wil[i] = Rs[3 * i] * wi[0] + Rs[3 * i + 1] * wi[1] + Rs[3 * i + 2] * wi[2];
+    wol[i] = Rs[3 * i] * wo[0] + Rs[3 * i + 1] * wo[1] + Rs[3 * i + 2] * wo[2];
+  }
+  const float off = 0.01f * (1.f - 0.36787944117144233f);
+  const float xz = wil[2];
+  const float fd = ((xz > 0.f ? xz : 0.01f * expm1f(xz)) + off) / ((1.f + off) * 3.14159265358979323846f);
+  const float dfd_dx = (xz > 0.f ? 1.f : 0.01f * expf(xz)) / ((1.f + off) * 3.14159265358979323846f);
+  float hs[3] = {wil[0] + wol[0], wil[1] + wol[1], wil[2] + wol[2]};
+  const float hn = sqrtf(hs[0] * hs[0] + hs[1] * hs[1] + hs[2] * hs[2]);
+  const bool have_h = hn * hn >= 1e-24f;
+  float h[3] = {0, 0, 0};
+  if (have_h) { h[0] = hs[0] / hn; h[1] = hs[1] / hn; h[2] = hs[2] / hn; }
+  const float E = p.falloff ? p.intensity / d2 : p.intensity;
+  const float4 rd = p.sc.albedo_d[g], rsp = p.sc.albedo_s[g];
+  const float rdv[3] = {rd.x, rd.y, rd.z}, rsv[3] = {rsp.x, rsp.y, rsp.z};
+  // f_s (recomputed) and the lobe gradients
+  float fs[3] = {0, 0, 0};
+  const int K = p.sc.k;
+  float dfs[3];
+  for (int c = 0; c < 3; ++c) dfs[c] = dcol[c] * E * rsv[c];
+  float dh[3] = {0, 0, 0};
+  if (have_h) {
+    for (int j = 0; j < K; ++j) {
+      const size_t li = (size_t)j * n + g;
+      float Rl[9], ql[4], qllen;
+      quat_rot(p.sc.lobe_rot[li], Rl, ql, qllen);
+      const float4 sig = p.sc.lobe_sigma[li];
+      const float4 amp = p.sc.lobe_amp[li];
+      const float hx = Rl[0] * h[0] + Rl[3] * h[1] + Rl[6] * h[2];
+      const float hy = Rl[1] * h[0] + Rl[4] * h[1] + Rl[7] * h[2];
+      const float hz = Rl[2] * h[0] + Rl[5] * h[1] + Rl[8] * h[2];
+      const float sxy = sqrtf(hx * hx + hy * hy);
+      const float theta = atan2f(sxy, hz);
+      float Pq = 0.f, e2 = 0.f, G;
+      const float iz = 1.f / sig.z;
+      if (sxy > 1e-20f) {
+        Pq = (hx / sig.x) * (hx / sig.x) + (hy / sig.y) * (hy / sig.y);
+        e2 = theta * theta / (sxy * sxy) * Pq * iz * iz;
+      } else if (hz < 0.f) {
+        e2 = (3.14159265358979323846f / sig.x) * (3.14159265358979323846f / sig.x) * iz * iz;
+      }
+      G = expf(-0.5f * e2) * iz;
+      fs[0] += amp.x * G; fs[1] += amp.y * G; fs[2] += amp.z * G;
+      const float dG = dfs[0] * amp.x + dfs[1] * amp.y + dfs[2] * amp.z;
+      p.out.lobe_amp[4 * li + 0] = dfs[0] * G;
+      p.out.lobe_amp[4 * li + 1] = dfs[1] * G;
+      p.out.lobe_amp[4 * li + 2] = dfs[2] * G;
+      p.out.lobe_amp[4 * li + 3] = 0.f;
+      float dsx = 0.f, dsy = 0.f, dsz = dG * G * (e2 - 1.f) * iz;
+      float dhl[3] = {0.f, 0.f, 0.f};
+      if (sxy > 1e-20f) {
+        const float de2 = dG * (-0.5f * G);
+        const float dF = de2 * iz * iz;
+        const float is2 = 1.f / (sxy * sxy);
+        dsx = dF * theta * theta * is2 * (-2.f * hx * hx / (sig.x * sig.x * sig.x));
+        dsy = dF * theta * theta * is2 * (-2.f * hy * hy / (sig.y * sig.y * sig.y));
+        const float r2 = sxy * sxy + hz * hz;
+        const float th_s = hz / r2, th_z = -sxy / r2;
+        const float dF_dsxy = 2.f * theta * th_s * Pq * is2 - 2.f * theta * theta * Pq * is2 / sxy;
+        dhl[0] = dF * (dF_dsxy * hx / sxy + theta * theta * is2 * 2.f * hx / (sig.x * sig.x));
+        dhl[1] = dF * (dF_dsxy * hy / sxy + theta * theta * is2 * 2.f * hy / (sig.y * sig.y));
+        dhl[2] = dF * 2.f * theta * th_z * Pq * is2;
+      }
+      p.out.lobe_sigma[4 * li + 0] = dsx;
+      p.out.lobe_sigma[4 * li + 1] = dsy;
+      p.out.lobe_sigma[4 * li + 2] = dsz;
+      p.out.lobe_sigma[4 * li + 3] = 0.f;
+      // hl = Rl^T h: dh += Rl dhl; dRl[k][i] += h_k dhl_i
+      float dRl[9];
+      for (int k = 0; k < 3; ++k) {
+        dh[k] += Rl[3 * k] * dhl[0] + Rl[3 * k + 1] * dhl[1] + Rl[3 * k + 2] * dhl[2];
+        for (int i = 0; i < 3; ++i) dRl[3 * k + i] = h[k] * dhl[i];
+      }
+      const float4 dql = quat_bwd(dRl, ql, qllen);
+      reinterpret_cast<float4*>(p.out.lobe_rot)[li] = dql;
+    }
+  } else {
+    for (int j = 0; j < K; ++j) {
+      const size_t li = (size_t)j * n + g;
+      reinterpret_cast<float4*>(p.out.lobe_amp)[li] = make_float4(0, 0, 0, 0);
+      reinterpret_cast<float4*>(p.out.lobe_sigma)[li] = make_float4(0, 0, 0, 0);
+      reinterpret_cast<float4*>(p.out.lobe_rot)[li] = make_float4(0, 0, 0, 0);
+    }
+  }
+  float dE = 0.f, dfd = 0.f;
+  float drd[3], drs[3];
+  for (int c = 0; c < 3; ++c) {
+    drd[c] = dcol[c] * E * fd;
+    drs[c] = dcol[c] * E * fs[c];
+    dE += dcol[c] * (rdv[c] * fd + rsv[c] * fs[c]);
+    dfd += dcol[c] * E * rdv[c];
+  }
+  reinterpret_cast<float4*>(p.out.albedo_d)[g] = make_float4(drd[0], drd[1], drd[2], 0.f);
+  reinterpret_cast<float4*>(p.out.albedo_s)[g] = make_float4(drs[0], drs[1], drs[2], 0.f);
+  // h = hs / |hs|
+  float dwil[3] = {0, 0, 0}, dwol[3] = {0, 0, 0};
+  if (have_h) {
+    const float hd = h[0] * dh[0] + h[1] * dh[1] + h[2] * dh[2];
+    for (int i = 0; i < 3; ++i) {
+      const float dhs = (dh[i] - h[i] * hd) / hn;
+      dwil[i] = dhs;
+      dwol[i] = dhs;
+    }
+  }
+  dwil[2] += dfd * dfd_dx;
+  // local = Rs w
+  float dRs[9];
+  float dwi[3], dwo[3];
+  for (int i = 0; i < 3; ++i)
+    for (int k = 0; k < 3; ++k) dRs[3 * i + k] = dwil[i] * wi[k] + dwol[i] * wo[k];
+  for (int k = 0; k < 3; ++k) {
+    dwi[k] = Rs[k] * dwil[0] + Rs[3 + k] * dwil[1] + Rs[6 + k] * dwil[2];
+    dwo[k] = Rs[k] * dwol[0] + Rs[3 + k] * dwol[1] + Rs[6 + k] * dwol[2];
+  }
+  const float4 dqs = quat_bwd(dRs, qs, qslen);
+  // MLP inputs
+  const float* mi = p.mlp_in + (size_t)kMlpIn * g;
+  for (int k = 0; k < 3; ++k) {
+    dmu[k] += mi[k] + mi[12 + k];
+    dwi[k] += mi[3 + k];
+    dwo[k] += mi[15 + k];
+  }
+  // w_i = (pL - mu)/|.|, w_o = (pC - mu)/|.|, E = I / |pL - mu|^2
+  const float wid = wi[0] * dwi[0] + wi[1] * dwi[1] + wi[2] * dwi[2];
+  const float wod = wo[0] * dwo[0] + wo[1] * dwo[1] + wo[2] * dwo[2];
+  const float dd2 = p.falloff ? -dE * E / d2 : 0.f;
+  const float lv[3] = {lx, ly, lz};
+  for (int k = 0; k < 3; ++k) {
+    dmu[k] -= (dwi[k] - wi[k] * wid) / dl;
+    dmu[k] -= (dwo[k] - wo[k] * wod) / dvn;
+    dmu[k] -= 2.f * lv[k] * dd2;
+  }
+  reinterpret_cast<float4*>(p.out.mean_op)[g] = make_float4(dmu[0], dmu[1], dmu[2], dlogit);
+  reinterpret_cast<float4*>(p.out.scale)[g] = make_float4(ds[0], ds[1], ds[2], 0.f);
+  reinterpret_cast<float4*>(p.out.rot)[g] = dq;
+  reinterpret_cast<float4*>(p.out.shade_rot)[g] = dqs;
+  reinterpret_cast<float4*>(p.out.latent)[g] =
+      make_float4(mi[6] + mi[18], mi[7] + mi[19], mi[8] + mi[20], mi[9] + mi[21]);
+  reinterpret_cast<float4*>(p.out.latent)[n + g] = make_float4(mi[10] + mi[22], mi[11] + mi[23], 0.f, 0.f);
+}
+
+// scatter the reduced MLP parameter gradients into the (weights, biases) layout
+__global__ void k_split_params(const float* red, int in_dim, int width, int nh, int out_dim, float* dw, float* db) {
+  // red holds, per layer: W (out x in) then b (out)
+  size_t ro = 0, wo = 0, bo = 0;
+  int din = in_dim;
+  for (int l = 0; l <= nh; ++l) {
+    const int dout = l == nh ? out_dim : width;
+    const size_t nw = (size_t)dout * din;
+    for (size_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nw; i += gridDim.x * blockDim.x)
+      dw[wo + i] = red[ro + i];
+    for (size_t i = blockIdx.x * blockDim.x + threadIdx.x; i < (size_t)dout; i += gridDim.x * blockDim.x)
+      db[bo + i] = red[ro + nw + i];
+    ro += nw + dout;
+    wo += nw;
+    bo += dout;
+    din = dout;
+  }
+}
+
+}  // namespace
+
+size_t backward_workspace_bytes(int n, const MlpDev& phi, const MlpDev& psi) {
+  return plan_bwd(n, phi, psi).total;
+}
+
+gs3_status run_backward(const FrameArgs& f, const float* dimg, void* bws, size_t bws_bytes,
+                        const gs3_grads& out, cudaStream_t s) {
+  const int n = f.sc.n;
+  const BwdPlan bp = plan_bwd(n, f.sc.phi, f.sc.psi);
+  if (bws_bytes < bp.total) return GS3_ERR_INVALID_ARG;
+  unsigned char* B = static_cast<unsigned char*>(bws);
+  float* cam_geom = reinterpret_cast<float*>(B + bp.cam_geom);
+  float* light_geom = reinterpret_cast<float*>(B + bp.light_geom);
+  float* color = reinterpret_cast<float*>(B + bp.color);
+  float* dT = reinterpret_cast<float*>(B + bp.dT);
+  float* mlp_in = reinterpret_cast<float*>(B + bp.mlp_in);
+  cudaMemsetAsync(B, 0, bp.wpart[0], s);  // per-Gaussian accumulators start at zero
+  unsigned char* ws = f.ws;
+  const Workspace& L = *f.L;
+  const int fin = (L.ntiles <= 256 ? 1 : 2) & 1;
+  // K9b
+  {
+    CamBwdParams p;
+    p.list = at<uint32_t>(ws, L.sp[0].tv[fin]);
+    p.tile_start = at<uint32_t>(ws, L.sp[0].tile_start);
+    p.rrec = at<SplatRec>(ws, L.sp[0].rrec);
+    p.ccol = at<float4>(ws, L.ccol);
+    p.order = at<uint32_t>(ws, L.sp[0].sv[1]);
+    p.final_t = at<float>(ws, L.final_t);
+    p.n_contrib = at<uint32_t>(ws, L.n_contrib);
+    p.pix_aux = at<float4>(ws, L.pix_aux);
+    p.dimg = dimg;
+    p.cam_geom = cam_geom;
+    p.color = color;
+    p.W = L.width; p.H = L.height; p.gx = L.gx;
+    p.amax = f.opts.alpha_max;
+    k_camera_bwd<<<L.ntiles, 256, 0, s>>>(p);
+    count_launch();
+  }
+  // K8b: Psi and Phi, then the weight gradients in fixed block order
+  for (int which = 1; which >= 0; --which) {
+    const MlpDev& m = which == 0 ? f.sc.phi : f.sc.psi;
+    float* wpart = reinterpret_cast<float*>(B + bp.wpart[which]);
+    float* wred = reinterpret_cast<float*>(B + bp.wred[which]);
+    const bool identity = (f.opts.ablate & (which == 0 ? GS3_ABLATE_PHI : GS3_ABLATE_PSI)) != 0;
+    float* dw = which == 0 ? out.phi_w : out.psi_w;
+    float* db = which == 0 ? out.phi_b : out.psi_b;
+    const size_t np = mlp_params(m);
+    if (identity) {
+      cudaMemsetAsync(wred, 0, 4 * np, s);
+      if (which == 0) {  // T' = T: the gradient passes straight through
+        k_copy_strided<<<(n + 255) / 256, 256, 0, s>>>(color, kColor, 3, dT, n);
+        count_launch();
+      }
+    } else {
+      MlpBwdParams p;
+      p.net = m;
+      p.n = n;
+      p.which = which;
+      p.mean_op = f.sc.mean_op;
+      p.latent = f.sc.latent;
+      p.T = at<float>(ws, L.T);
+      for (int i = 0; i < 3; ++i) { p.light_pos[i] = f.light.pos[i]; p.cam_pos[i] = f.cam.pos[i]; }
+      p.color = color;
+      p.dT = dT;
+      p.mlp_in = mlp_in;
+      p.wpart = wpart;
+      const size_t smem = 4 * ((size_t)(m.n_hidden + 1 + 2) * kMlpRows * (kMaxW + 1) + kMlpRows * 4);
+      cudaFuncSetAttribute(k_mlp_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      k_mlp_bwd<<<kBwdBlocksMlp, 128, smem, s>>>(p);
+      k_reduce_parts<<<(int)((np + 255) / 256), 256, 0, s>>>(wpart, np, kBwdBlocksMlp, wred);
+      count_launch(2);
+    }
+    k_split_params<<<64, 256, 0, s>>>(wred, m.in_dim, m.width, m.n_hidden, m.out_dim, dw, db);
+    count_launch();
+  }
+  // K6b
+  if (!(f.opts.ablate & GS3_ABLATE_SHADOW_SPLAT)) {
+    ShadowBwdParams p;
+    p.list = at<uint32_t>(ws, L.sp[1].tv[fin]);
+    p.tile_start = at<uint32_t>(ws, L.sp[1].tile_start);
+    p.rrec = at<SplatRec>(ws, L.sp[1].rrec);
+    p.order = at<uint32_t>(ws, L.sp[1].sv[1]);
+    p.kbound = at<uint32_t>(ws, L.sp[1].tv[1 - fin]);
+    p.light_final = at<float>(ws, L.light_final);
+    p.dT = dT;
+    p.den = at<float>(ws, L.shadow_den);
+    p.T = at<float>(ws, L.T);
+    p.light_geom = light_geom;
+    p.W = L.width; p.H = L.height; p.gx = L.gx;
+    p.amax = f.opts.alpha_max;
+    k_shadow_bwd<<<L.ntiles, 256, 0, s>>>(p);
+    count_launch();
+  }
+  // K1b
+  {
+    PrepBwdParams p;
+    p.sc = f.sc;
+    const float* hv = reinterpret_cast<const float*>(at<uint32_t>(ws, L.header) + H_LIGHT_VIEW);
+    (void)hv;
+    for (int i = 0; i < 9; ++i) p.cam.R[i] = f.cam.R[i];
+    for (int i = 0; i < 3; ++i) p.cam.t[i] = f.cam.t[i];
+    p.cam.fx = f.cam.fx; p.cam.fy = f.cam.fy; p.cam.lowpass = f.opts.lowpass;
+    p.light = p.cam;  // rotation and translation filled from the frame's light view below
+    for (int i = 0; i < 9; ++i) p.light.R[i] = f.light_view[i];
+    for (int i = 0; i < 3; ++i) p.light.t[i] = f.light_view[9 + i];
+    for (int i = 0; i < 3; ++i) { p.light_pos[i] = f.light.pos[i]; p.cam_pos[i] = f.cam.pos[i]; }
+    p.intensity = f.light.intensity;
+    p.falloff = f.opts.falloff;
+    p.cam_geom = cam_geom;
+    p.light_geom = light_geom;
+    p.color = color;
+    p.mlp_in = mlp_in;
+    p.out = out;
+    k_prep_bwd<<<(n + 127) / 128, 128, 0, s>>>(p);
+    count_launch();
+  }
+  return GS3_OK;
+}
+
+}  // namespace gs3

@@ -69,6 +69,7 @@ struct ShadowParams {
   const uint32_t* off;
   const uint32_t* kbound;
   float2* partial;
+  float* light_final;
   int W, H, gx;
   float amax;
 };
@@ -191,6 +192,10 @@ __global__ void __launch_bounds__(kShadowThreads, 8) k_shadow(ShadowParams p) {
       p.partial[S.rslot[t]] = sum;
     }
   }
+  // the product over every occluder of the ray (the backward starts from it)
+  const int gxp = tx * kTile + lxi;
+  if (in0) p.light_final[(size_t)(ty * kTile + lyi) * p.W + gxp] = A0;
+  if (in1) p.light_final[(size_t)(ty * kTile + lyi + 4) * p.W + gxp] = A1;
 }
 
 // K(i) for every entry i of the light lists: the first index of i's tile
@@ -226,7 +231,8 @@ __global__ void __launch_bounds__(256) k_shadow_reduce(int n, const uint32_t* __
                                                        const uint32_t* __restrict__ cnt,
                                                        const float2* __restrict__ partial,
                                                        const uint32_t* __restrict__ order,
-                                                       const uint32_t* header, float* __restrict__ T) {
+                                                       const uint32_t* header, float* __restrict__ T,
+                                                       float* __restrict__ den_out) {
   const int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (r >= n) return;
@@ -245,7 +251,10 @@ __global__ void __launch_bounds__(256) k_shadow_reduce(int n, const uint32_t* __
     num += __shfl_xor_sync(0xffffffffu, num, s);
     den += __shfl_xor_sync(0xffffffffu, den, s);
   }
-  if (lane == 0) T[order[r]] = den > 0.f ? num / den : 1.f;
+  if (lane == 0) {
+    T[order[r]] = den > 0.f ? num / den : 1.f;
+    den_out[order[r]] = den;
+  }
 }
 
 __global__ void k_fill(float* x, int n, float v) {
@@ -267,6 +276,7 @@ struct CamParams {
   float* out;
   float* final_t;
   uint32_t* n_contrib;
+  float4* pix_aux;
   int W, H, gx;
   float amax, tstop;
 };
@@ -329,6 +339,8 @@ __global__ void __launch_bounds__(256) k_camera(CamParams p) {
     p.out[3 * pix + 2] = S2 * Sh + R2;
     p.final_t[pix] = T;
     p.n_contrib[pix] = consumed;
+    p.pix_aux[2 * pix] = make_float4(S0, S1, S2, Sh);
+    p.pix_aux[2 * pix + 1] = make_float4(R0, R1, R2, 0.f);
   }
 }
 
@@ -356,6 +368,7 @@ void launch_shadow_composite(const FrameArgs& f, cudaStream_t s) {
   p.off = at<uint32_t>(ws, b.off);
   p.kbound = kb;
   p.partial = at<float2>(ws, f.L->partial);
+  p.light_final = at<float>(ws, f.L->light_final);
   p.W = f.L->width; p.H = f.L->height; p.gx = f.L->gx;
   p.amax = f.opts.alpha_max;
   static bool configured = false;
@@ -373,13 +386,16 @@ void launch_shadow_reduce(const FrameArgs& f, cudaStream_t s) {
   const int n = f.sc.n;
   k_shadow_reduce<<<(n * 32 + 255) / 256, 256, 0, s>>>(
       n, at<uint32_t>(ws, b.off), at<uint32_t>(ws, b.cnt), at<float2>(ws, f.L->partial),
-      at<uint32_t>(ws, b.sv[1]), at<uint32_t>(ws, f.L->header), at<float>(ws, f.L->T));
+      at<uint32_t>(ws, b.sv[1]), at<uint32_t>(ws, f.L->header), at<float>(ws, f.L->T),
+      at<float>(ws, f.L->shadow_den));
   count_launch();
 }
 
 void launch_fill_shadow_one(const FrameArgs& f, cudaStream_t s) {
   const int n = f.sc.n;
   k_fill<<<(n + 255) / 256, 256, 0, s>>>(at<float>(f.ws, f.L->T), n, 1.f);
+  k_fill<<<(n + 255) / 256, 256, 0, s>>>(at<float>(f.ws, f.L->shadow_den), n, 0.f);
+  count_launch();
   count_launch();
 }
 
@@ -395,6 +411,7 @@ void launch_camera_composite(const FrameArgs& f, float* out_rgb, cudaStream_t s)
   p.out = out_rgb;
   p.final_t = at<float>(ws, f.L->final_t);
   p.n_contrib = at<uint32_t>(ws, f.L->n_contrib);
+  p.pix_aux = at<float4>(ws, f.L->pix_aux);
   p.W = f.L->width; p.H = f.L->height; p.gx = f.L->gx;
   p.amax = f.opts.alpha_max; p.tstop = f.opts.t_stop;
   k_camera<<<f.L->ntiles, 256, 0, s>>>(p);

@@ -60,6 +60,9 @@ struct Workspace {
   size_t ccol = 0;     // float4[2N] camera colours by camera rank: (shade, T'), (res, 0)
   size_t final_t = 0;  // float[HW]
   size_t n_contrib = 0;  // u32[HW]
+  size_t pix_aux = 0;    // float4[2 HW]: (S rgb, Sh), (R rgb, 0) composited per camera pixel
+  size_t light_final = 0;  // float[HW] occluder product at the end of each shadow ray
+  size_t shadow_den = 0;   // float[N] sum of beta per Gaussian (by index)
   int n = 0, width = 0, height = 0, gx = 0, gy = 0, ntiles = 0;
   size_t cap = 0;
   int nb_n = 0;    // radix blocks over N
@@ -94,7 +97,12 @@ struct FrameArgs {
   gs3_render_opts opts;
   unsigned char* ws;
   const Workspace* L;
+  float light_view[12];  // light camera R (9), t (3); filled on the host for the backward
 };
+
+size_t backward_workspace_bytes(int n, const MlpDev& phi, const MlpDev& psi);
+gs3_status run_backward(const FrameArgs& f, const float* dimg, void* bws, size_t bws_bytes,
+                        const gs3_grads& out, cudaStream_t s);
 
 void launch_prep(const FrameArgs& f, cudaStream_t s);
 void launch_depth_sort(const FrameArgs& f, int splat, cudaStream_t s);

@@ -42,6 +42,8 @@ def opts_struct(ablate: int = 0, falloff: int = 1, **kw) -> N.gs3_render_opts:
 class DeviceScene:
     """Scene parameters resident on the GPU plus the library's scene handle."""
 
+    ARRAYS_DEV = N.GRAD_FIELDS
+
     def __init__(self, scene, device="cuda", mlp_dtype: int = N.GS3_MLP_FP32):
         self.n, self.k = scene.n, scene.k
         dev = torch.device(device)
@@ -108,6 +110,19 @@ class Renderer:
         N.gs3_render_stages(self.scene.handle, camera_struct(cam), light_struct(light), opts, out,
                             self.ws, self.cap, stages, s.cuda_stream)
         return out
+
+    def backward(self, cam, light, dl_drgb, opts=None, stream=None) -> dict:
+        """Gradients of every scene parameter for dL/d(image) of the last
+        render() of the same (cam, light, opts); arrays shaped like the scene's."""
+        opts = opts if opts is not None else opts_struct()
+        s = torch.cuda.current_stream() if stream is None else stream
+        if getattr(self, "bws", None) is None:
+            nb = N.gs3_backward_workspace_size(self.scene.handle)
+            self.bws = torch.empty(nb, dtype=torch.uint8, device=self.ws.device)
+        grads = {f: torch.zeros_like(self.scene.t[f]) for f in self.scene.ARRAYS_DEV}
+        N.gs3_render_backward(self.scene.handle, camera_struct(cam), light_struct(light), opts,
+                              dl_drgb.contiguous(), self.ws, self.cap, self.bws, grads, s.cuda_stream)
+        return grads
 
     def header(self, stream=None) -> N.gs3_ws_header:
         s = torch.cuda.current_stream() if stream is None else stream
@@ -193,3 +208,29 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+class RenderFunction(torch.autograd.Function):
+    """Differentiable frame: forward gs3_render, backward gs3_render_backward.
+
+    Inputs after (renderer, cam, light, opts) are the scene's device tensors
+    in N.GRAD_FIELDS order; they are read by the library through the scene
+    handle, and their gradients come from the hand-written backward."""
+
+    @staticmethod
+    def forward(ctx, renderer, cam, light, opts, *params):
+        img = renderer.render(cam, light, opts).clone()
+        ctx.renderer, ctx.cam, ctx.light, ctx.opts = renderer, cam, light, opts
+        return img
+
+    @staticmethod
+    def backward(ctx, grad_img):
+        g = ctx.renderer.backward(ctx.cam, ctx.light, grad_img, ctx.opts)
+        return (None, None, None, None) + tuple(g[f] for f in N.GRAD_FIELDS)
+
+
+def render_differentiable(renderer, cam, light, opts=None):
+    """Image tensor whose backward flows into renderer.scene.t[...] tensors."""
+    sc = renderer.scene
+    opts = opts if opts is not None else opts_struct()
+    return RenderFunction.apply(renderer, cam, light, opts, *[sc.t[f] for f in N.GRAD_FIELDS])

@@ -1,0 +1,121 @@
+"""Backward (differentiation form) on the GPU through gs3_render_backward,
+against the FP64 autograd gradient oracle (itself pinned to finite
+differences of the C oracle in test_oracle_grad.py).
+
+Both sides get the same dL/d(image): that of L = 0.8 L1 + 0.2 (1 - SSIM)
+(Sec. 4.4) at the oracle's image.  Per parameter group the GPU gradient
+must satisfy ||g - o|| <= 2e-3 ||o|| (FP32 accumulation over thousands of
+pixels and Gaussians) and, element-wise, |g - o| <= 2e-3 max|o| + 1e-2 |o|.
+Measured relative norm errors are 1e-7 to 1e-6 per group."""
+import numpy as np
+import pytest
+
+from paper_2410_11419_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+REL_NORM, REL_MAX = 2e-3, 2e-3
+
+
+def _gpu_grads(scene, cam, light, dimg, ablate=0):
+    import torch
+    from paper_2410_11419_gb300 import render as R
+    ds = R.DeviceScene(scene)
+    rd = R.Renderer(ds, cam.width, cam.height, 1 << 20)
+    opts = R.opts_struct(ablate=ablate)
+    rd.render(cam, light, opts)
+    g = rd.backward(cam, light, torch.from_numpy(dimg.astype(np.float32)).cuda(), opts)
+    torch.cuda.synchronize()
+    rd.check()
+    out = {k: v.cpu().numpy() for k, v in g.items()}
+    ds.close()
+    return out
+
+
+def _as_ref_layout(scene, ref):
+    """Reference gradients in the float4-padded device layouts."""
+    n, k = scene.n, scene.k
+    lay = {
+        "mean_op": np.concatenate([ref["mu"], ref["logit"][:, None]], 1),
+        "scale": np.concatenate([ref["scale"], np.zeros((n, 1))], 1),
+        "rot": ref["rot"], "shade_rot": ref["shade_rot"],
+        "albedo_d": np.concatenate([ref["albedo_d"], np.zeros((n, 1))], 1),
+        "albedo_s": np.concatenate([ref["albedo_s"], np.zeros((n, 1))], 1),
+        "latent": np.stack([ref["latent"][:, :4], np.concatenate([ref["latent"][:, 4:], np.zeros((n, 2))], 1)]),
+        "lobe_rot": ref["lobe_rot"],
+        "lobe_sigma": np.concatenate([ref["lobe_sigma"], np.zeros((k, n, 1))], 2),
+        "lobe_amp": np.concatenate([ref["lobe_amp"], np.zeros((k, n, 1))], 2),
+        "phi_w": ref["phi_w"], "phi_b": ref["phi_b"], "psi_w": ref["psi_w"], "psi_b": ref["psi_b"],
+    }
+    return lay
+
+
+def _compare(gpu, ref, skip=()):
+    report = {}
+    for kname, o in ref.items():
+        if kname in skip:
+            continue
+        g = gpu[kname].reshape(o.shape).astype(np.float64)
+        no = np.linalg.norm(o)
+        err = np.linalg.norm(g - o)
+        report[kname] = err / max(no, 1e-30)
+        if no == 0:
+            assert np.abs(g).max() < 1e-12, kname
+            continue
+        assert err <= REL_NORM * no, f"{kname}: relative norm error {err / no:.2e}"
+        bad = np.abs(g - o) > REL_MAX * np.abs(o).max() + 1e-2 * np.abs(o)
+        assert not bad.any(), f"{kname}: {bad.sum()} elements off, worst {np.abs(g - o).max():.3e}"
+    return report
+
+
+@pytest.mark.parametrize("make,res,seed", [
+    (lambda: synth.make_scene(21, 500, 4, "ball"), 64, 21),
+    (lambda: synth.tiny_scene(0), 96, 3),
+    (lambda: synth.paper_mlp_scene(5, n=800, k=2), 80, 8),
+], ids=["fd500_64", "tiny_96", "paper_mlp_80"])
+def test_backward_matches_gradient_oracle(gs3, oracle, make, res, seed):
+    from oracle import torch_ref as TR
+    scene = make()
+    cam, light = synth.camera_light_pair(seed, res, res)
+    target = oracle.render(synth.perturbed(scene, seed + 1), cam, light)["img"]
+    fr = oracle.render(scene, cam, light)
+    dimg, _ = TR.image_grad_of_loss(fr["img"], target)
+    ref, _ = TR.grads_given_image_grad(scene, cam, light, dimg)
+    gpu = _gpu_grads(scene, cam, light, dimg)
+    rep = _compare(gpu, _as_ref_layout(scene, ref))
+    assert len(rep) == 14
+
+
+@pytest.mark.parametrize("ablate", [1, 2, 4])
+def test_backward_with_ablations(gs3, oracle, ablate):
+    from oracle import torch_ref as TR
+    scene = synth.make_scene(9, 400, 3, "ball")
+    cam, light = synth.camera_light_pair(9, 64, 64)
+    opts = oracle.Opts(ablate=ablate)
+    target = oracle.render(synth.perturbed(scene, 10), cam, light, opts)["img"]
+    fr = oracle.render(scene, cam, light, opts)
+    dimg, _ = TR.image_grad_of_loss(fr["img"], target)
+    ref, _ = TR.grads_given_image_grad(scene, cam, light, dimg, opts)
+    gpu = _gpu_grads(scene, cam, light, dimg, ablate=ablate)
+    _compare(gpu, _as_ref_layout(scene, ref))
+
+
+def test_autograd_function(gs3):
+    """torch.autograd through RenderFunction gives the same gradients as the
+    direct backward call."""
+    import torch
+    from paper_2410_11419_gb300 import _native as N, render as R
+    scene = synth.make_scene(4, 600, 4, "ball")
+    cam, light = synth.camera_light_pair(4, 64, 64)
+    ds = R.DeviceScene(scene)
+    for f in N.GRAD_FIELDS:
+        ds.t[f].requires_grad_(True)
+    rd = R.Renderer(ds, 64, 64, 1 << 20)
+    target = torch.rand((64, 64, 3), device="cuda", generator=torch.Generator("cuda").manual_seed(0))
+    img = R.render_differentiable(rd, cam, light)
+    loss = (img - target).abs().mean()
+    loss.backward()
+    direct = rd.backward(cam, light, torch.sign(img.detach() - target) / img.numel())
+    for f in N.GRAD_FIELDS:
+        assert torch.allclose(ds.t[f].grad, direct[f], rtol=1e-4, atol=1e-8), f
+    ds.close()
