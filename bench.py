@@ -42,15 +42,20 @@ def parse():
     ap.add_argument("--impl", default="gs3", choices=["gs3", "reference"])
     ap.add_argument("--n", type=int, default=300_000)
     ap.add_argument("--res", type=int, default=800)
-    ap.add_argument("--mlp", default="bf16", choices=["fp32", "bf16"],
+    ap.add_argument("--mlp", default="bf16", choices=["fp32", "bf16", "fp8"],
                     help="MLP precision of the timed arm (the other one is measured too)")
     ap.add_argument("--no-plain", action="store_true", help="skip the FP32 plain comparison arm")
     ap.add_argument("--profile-frames", type=int, default=0,
                     help="render this many frames of the workload (no timing) and exit; for ncu")
+    ap.add_argument("--profile-backward", action="store_true",
+                    help="with --profile-frames and --mlp fp32: also run each frame's backward")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-window", type=int, default=96, help="oracle window edge (pixels)")
     ap.add_argument("--inflight", type=int, default=4, help="server in-flight slots (served arm)")
     ap.add_argument("--no-serve", action="store_true", help="time single frames only")
+    ap.add_argument("--no-mix", action="store_true", help="skip the mixed-scene serving measurement")
+    ap.add_argument("--mix-requests", type=int, default=160,
+                    help="requests per arrival rate in the mixed-scene serving measurement")
     return ap.parse_args()
 
 
@@ -180,6 +185,98 @@ def run_reference(a):
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
+MIX_SIZES = (100_000, 250_000, 500_000, 1_000_000)
+MIX_RES = (256, 512, 800, 1024)
+MIX_RATES = (50, 200, 500, 1000, 2000)
+
+
+def serving_mix(a, dev, np, torch, N, R, synth):
+    """Mixed serving workload: 8 device-resident scenes (two each of 100k,
+    250k, 500k and 1M Gaussians, K = 8, BF16 MLPs), requests (scene, camera,
+    light) with resolution uniform over 256^2..1024^2, Poisson arrivals at
+    each rate, through the continuous-batching server; beside it the same
+    requests rendered one at a time with FP32 MLPs (service times by CUDA
+    events, FIFO latency under the same arrivals by Lindley's recursion)."""
+    rng = np.random.default_rng(2024)
+    scenes = [synth.object_scene(100 + 2 * j + c, n=n) for j, n in enumerate(MIX_SIZES) for c in range(2)]
+    nreq = a.mix_requests
+    reqs = [(int(rng.integers(len(scenes))), int(rng.choice(MIX_RES))) for _ in range(nreq)]
+    views = [synth.camera_light_pair(1000 + i, res, res) for i, (_, res) in enumerate(reqs)]
+    outs = [torch.empty((res, res, 3), device=dev) for _, res in reqs]
+    ds = [R.DeviceScene(sc, device=dev, mlp_dtype=N.GS3_MLP_BF16) for sc in scenes]
+    srv = R.Server(hbm_budget=96 << 30, max_inflight=a.inflight, device=dev.index or 0)
+    ids = [srv.add_scene(d) for d in ds]
+    for si in range(len(scenes)):  # learn every (scene, resolution) capacity, warm the pool
+        for res in MIX_RES:
+            cam, light = synth.camera_light_pair(7, res, res)
+            st = srv.wait(srv.submit(ids[si], cam, light, torch.empty((res, res, 3), device=dev)))[0]
+            assert st == 0, st
+    torch.cuda.synchronize()
+    gaps = {rate: np.random.default_rng(rate).exponential(1.0 / rate, nreq) for rate in MIX_RATES}
+    served = {}
+    for rate in MIX_RATES:
+        srv.reset_counters()
+        tk = []
+        t0 = time.perf_counter()
+        t_next = t0
+        for i, (si, _) in enumerate(reqs):
+            t_next += gaps[rate][i]
+            while time.perf_counter() < t_next:
+                pass
+            tk.append(srv.submit(ids[si], *views[i], outs[i]))
+        res_ = [srv.wait(t) for t in tk]
+        wall = time.perf_counter() - t0
+        st = srv.stats()
+        lat = np.array([r[1] for r in res_])
+        served[str(rate)] = {
+            "offered_rps": rate, "frames_per_s": nreq / wall,
+            "device_frames_per_s": nreq / (st.device_span_ms / 1e3),
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "max_in_flight": int(st.max_in_flight), "retries": int(st.retries),
+            "failed": int(sum(1 for r in res_ if r[0] != 0))}
+    srv.close()
+    for d in ds:
+        d.close()
+    del ds
+    torch.cuda.synchronize()
+    # one request at a time, FP32 MLPs: service time of every request
+    svc = np.zeros(nreq)
+    for si in range(len(scenes)):
+        d32 = R.DeviceScene(scenes[si], device=dev, mlp_dtype=N.GS3_MLP_FP32)
+        for res in MIX_RES:
+            idx = [i for i, r in enumerate(reqs) if r == (si, res)]
+            if not idx:
+                continue
+            cap = int(scenes[si].n * (8 + 96 * res * res / 640000.0))
+            rd = R.Renderer(d32, res, res, cap, device=dev)
+            rd.render(*views[idx[0]])  # warm
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in idx]
+            for (e0, e1), i in zip(ev, idx):
+                e0.record()
+                rd.render(*views[i])
+                e1.record()
+            torch.cuda.synchronize()
+            rd.check()
+            for (e0, e1), i in zip(ev, idx):
+                svc[i] = e0.elapsed_time(e1)
+            del rd
+        d32.close()
+    one = {"frames_per_s": nreq / (svc.sum() / 1e3),
+           "service_p50_ms": float(np.percentile(svc, 50)), "service_p99_ms": float(np.percentile(svc, 99))}
+    for rate in MIX_RATES:  # FIFO single server under the same arrivals
+        arr = np.cumsum(gaps[rate]) * 1e3
+        fin, lat = 0.0, np.zeros(nreq)
+        for i in range(nreq):
+            fin = max(arr[i], fin) + svc[i]
+            lat[i] = fin - arr[i]
+        one[str(rate)] = {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99))}
+    return {"scenes": [s.n for s in scenes], "resolutions": list(MIX_RES), "requests_per_rate": nreq,
+            "inflight_slots": a.inflight, "served_bf16": served, "one_at_a_time_fp32": one,
+            "note": "served: host wall clock from the first arrival to the last completion; latency "
+                    "submit to completion. one_at_a_time: CUDA-event service times, latency from a FIFO "
+                    "recursion over the same Poisson arrivals"}
+
+
 def main():
     a = parse()
     if a.impl == "reference":
@@ -202,7 +299,7 @@ def main():
 
     scene = synth.object_scene(0, n=a.n)
     pairs = [synth.camera_light_pair(i, a.res, a.res) for i in range(100)]
-    mlp_dtype = N.GS3_MLP_BF16 if a.mlp == "bf16" else N.GS3_MLP_FP32
+    mlp_dtype = {"fp32": N.GS3_MLP_FP32, "bf16": N.GS3_MLP_BF16, "fp8": N.GS3_MLP_FP8_E4M3}[a.mlp]
     ds = R.DeviceScene(scene, device=dev, mlp_dtype=mlp_dtype)
     cap = 40_000_000 if a.n <= 300_000 else int(a.n * 140)
     rd = R.Renderer(ds, a.res, a.res, cap, device=dev)
@@ -211,7 +308,9 @@ def main():
 
     if a.profile_frames:
         for i in range(a.profile_frames):
-            rd.render(*pairs[i % 100])
+            img = rd.render(*pairs[i % 100])
+            if a.profile_backward:
+                rd.backward(*pairs[i % 100], torch.sign(img - 0.5))
         torch.cuda.synchronize()
         h = rd.check()
         print(json.dumps({"profile_frames": a.profile_frames, "pairs_cam": h.pairs_cam,
@@ -346,7 +445,7 @@ def main():
     # ---- FP32 plain comparison arm (one request at a time, FP32 MLPs) ----
     plain = None
     if not a.no_plain:
-        other = N.GS3_MLP_FP32 if mlp_dtype == N.GS3_MLP_BF16 else N.GS3_MLP_BF16
+        other = N.GS3_MLP_FP32 if mlp_dtype != N.GS3_MLP_FP32 else N.GS3_MLP_BF16
         ds2 = R.DeviceScene(scene, device=dev, mlp_dtype=other)
         rd2 = R.Renderer(ds2, a.res, a.res, cap, device=dev)
         for i in range(3):
@@ -366,6 +465,27 @@ def main():
         plain = {"mlp": "fp32" if other == N.GS3_MLP_FP32 else "bf16", "value": K / (pms.sum() / 1e3),
                  "unit": UNIT, "ms_per_step": float(pms.mean()), "p50_ms": float(np.percentile(pms, 50)),
                  "p99_ms": float(np.percentile(pms, 99))}
+        # differentiation form: forward + hand-written backward of the same frames (FP32)
+        if other == N.GS3_MLP_FP32:
+            tgt = torch.rand((a.res, a.res, 3), device=dev, generator=torch.Generator(dev).manual_seed(7))
+            dimg = torch.empty_like(tgt)
+            be = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
+            for s_ in range(K):
+                flush.zero_()
+                cam, light = pairs[(a.warmup + s_) % 100]
+                be[s_][0].record(stream)
+                img = rd2.render(cam, light, opts)
+                torch.sign(img - tgt, out=dimg)
+                be[s_][1].record(stream)
+                rd2.backward(cam, light, dimg, opts)
+                be[s_][2].record(stream)
+            torch.cuda.synchronize()
+            fb = np.array([x[0].elapsed_time(x[2]) for x in be])
+            bw = np.array([x[1].elapsed_time(x[2]) for x in be])
+            plain["differentiation"] = {
+                "fwd_bwd_ms": float(fb.mean()), "bwd_ms": float(bw.mean()),
+                "fwd_bwd_per_s": K / (fb.sum() / 1e3),
+                "note": "gs3_render + gs3_render_backward per frame, FP32 MLPs, dL/dI = sign(I - target)"}
         del rd2
         ds2.close()
 
@@ -433,7 +553,7 @@ def main():
         "metric": METRIC, "value": head_value, "unit": UNIT, "n_gpus": world, "steps": K,
         "warmup": a.warmup, "ms_per_step": head_ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32" if a.mlp == "fp32" else "bf16 MLP operands, f32 elsewhere",
+        "dtype": "f32" if a.mlp == "fp32" else f"{a.mlp} MLP operands, f32 elsewhere",
         "data": "synthetic (seeded object scene, random-init MLPs)",
         "config": workload_config(a, a.mlp),
         "p50_ms": p50, "p99_ms": p99,
@@ -452,6 +572,8 @@ def main():
                 "note": "gs3_render through the C ABI, camera/light host structs in, image copied "
                         "to pinned host memory and synchronised every step"},
     }
+    if world == 1 and not a.no_mix:
+        out["serving_mix"] = serving_mix(a, dev, np, torch, N, R, synth)
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(a, scene)
     if rank == 0:

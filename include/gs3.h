@@ -48,7 +48,15 @@ typedef enum {
 } gs3_status;
 
 enum { GS3_ACT_RELU = 0, GS3_ACT_LEAKY_RELU = 1 };         /* hidden-layer activation */
-enum { GS3_MLP_FP32 = 0, GS3_MLP_BF16 = 1 };               /* MLP operand precision */
+/* MLP operand precision of the hidden layers (the output layer and the
+ * sigmoid stay FP32).  BF16 and FP8 run on the tensor cores with FP32
+ * accumulation.  FP8 E4M3 uses per-tensor scales: each weight matrix is
+ * scaled by max|W| / 448, each hidden layer's input by twice its largest
+ * magnitude over a calibration pass that gs3_create_scene runs (FP32, on a
+ * strided sample of up to 16384 Gaussians for 8 fixed directions); inputs
+ * beyond the calibrated range saturate at 448.  FP8 needs hidden widths of
+ * 32, 64 or 128. */
+enum { GS3_MLP_FP32 = 0, GS3_MLP_BF16 = 1, GS3_MLP_FP8_E4M3 = 2 };
 enum { GS3_ABLATE_SHADOW_SPLAT = 1, GS3_ABLATE_PHI = 2, GS3_ABLATE_PSI = 4 };
 
 /* Fully connected network in_dim -> [width] x n_hidden -> out_dim with a
@@ -82,7 +90,7 @@ typedef struct {
     const float *mean_op, *scale, *rot, *shade_rot, *albedo_d, *albedo_s, *latent;
     const float *lobe_rot, *lobe_sigma, *lobe_amp;
     gs3_mlp_desc phi, psi;
-    int32_t mlp_dtype; /* GS3_MLP_FP32 or GS3_MLP_BF16 (tensor cores, FP32 accumulate) */
+    int32_t mlp_dtype; /* GS3_MLP_FP32, GS3_MLP_BF16 or GS3_MLP_FP8_E4M3 */
 } gs3_scene_desc;
 
 /* Pinhole camera, host struct.  R: world -> camera rotation rows (x right,
@@ -150,6 +158,13 @@ void gs3_default_opts(gs3_render_opts *o);
  * weight pointers and owns derived buffers (packed / BF16 MLP weights).
  * Errors: INVALID_ARG (sizes, NULL pointers, unsupported MLP shape), OOM. */
 gs3_status gs3_create_scene(const gs3_scene_desc *desc, gs3_scene **out);
+
+/* The per-tensor scales of an FP8 scene's MLP (which = 0: Phi, 1: Psi):
+ * out[2l] = sx_l (input of hidden layer l), out[2l + 1] = sw_l (its weights),
+ * so that layer l computes (sum_k q(x_k / sx_l) q(w_jk / sw_l)) sx_l sw_l + b_j
+ * with q = round to E4M3, saturating.  out: host, cap >= 2 n_hidden floats.
+ * Synchronous.  GS3_ERR_UNSUPPORTED unless the scene is GS3_MLP_FP8_E4M3. */
+gs3_status gs3_scene_mlp_scales(const gs3_scene *scene, int32_t which, float *out, int32_t cap);
 
 /* Release a scene; waits for nothing (the caller synchronises first). */
 gs3_status gs3_destroy_scene(gs3_scene *scene);
@@ -234,6 +249,20 @@ gs3_status gs3_render_backward(gs3_scene *scene, const gs3_camera *camera, const
                                const gs3_render_opts *opts, const float *dL_drgb, void *workspace,
                                size_t workspace_bytes, size_t key_capacity, void *bwd_ws,
                                size_t bwd_bytes, const gs3_grads *grads, void *stream);
+
+/* Loss of Sec. 4.4 and its image gradient:
+ *   L = (1 - lambda) mean|I - I*| + lambda (1 - SSIM(I, I*)),
+ * SSIM with an 11x11 Gaussian window (sigma 1.5), C1 = 0.01^2, C2 = 0.03^2,
+ * zero padding, averaged over pixels and channels (lambda = 0.2 in the paper).
+ *   img, target: device float32 [height][width][3]
+ *   loss_out:    device float32 [1]
+ *   dL_dimg:     device float32 [height][width][3], overwritten
+ *   scratch:     device, >= gs3_loss_scratch_size(width, height) bytes
+ * Asynchronous; deterministic (fixed-order reductions). */
+size_t gs3_loss_scratch_size(int32_t width, int32_t height);
+gs3_status gs3_loss_l1_dssim(const float *img, const float *target, int32_t width, int32_t height,
+                             float lambda, float *loss_out, float *dL_dimg, void *scratch,
+                             size_t scratch_bytes, void *stream);
 
 /* ---- Continuous-batching server -----------------------------------------
  * Serving form of gs3_render (no counterpart in the paper, which renders one

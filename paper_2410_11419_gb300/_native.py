@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(HERE, "libgs3.so")
 GS3_OK, GS3_ERR_INVALID_ARG, GS3_ERR_OOM, GS3_ERR_CAPACITY, GS3_ERR_CUDA, GS3_ERR_TIMEOUT, \
     GS3_ERR_UNSUPPORTED = range(7)
 GS3_ACT_RELU, GS3_ACT_LEAKY_RELU = 0, 1
-GS3_MLP_FP32, GS3_MLP_BF16 = 0, 1
+GS3_MLP_FP32, GS3_MLP_BF16, GS3_MLP_FP8_E4M3 = 0, 1, 2
 GS3_ABLATE_SHADOW_SPLAT, GS3_ABLATE_PHI, GS3_ABLATE_PSI = 1, 2, 4
 GS3_STAGE_PREP, GS3_STAGE_CAMERA_BIN, GS3_STAGE_LIGHT_BIN, GS3_STAGE_SHADOW_COMPOSITE, \
     GS3_STAGE_SHADOW_REDUCE, GS3_STAGE_MLP, GS3_STAGE_CAMERA, GS3_STAGE_ALL = 1, 2, 4, 8, 16, 32, 64, 127
@@ -115,6 +115,7 @@ SIGNATURES = {
     "gs3_default_opts": (None, [C.POINTER(gs3_render_opts)]),
     "gs3_create_scene": (C.c_int, [C.POINTER(gs3_scene_desc), C.POINTER(_SCENE_P)]),
     "gs3_destroy_scene": (C.c_int, [_SCENE_P]),
+    "gs3_scene_mlp_scales": (C.c_int, [_SCENE_P, C.c_int32, C.POINTER(C.c_float), C.c_int32]),
     "gs3_workspace_size": (C.c_size_t, [C.c_int32, C.c_int32, C.c_int32, C.c_size_t]),
     "gs3_workspace_layout": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_size_t,
                                        C.POINTER(gs3_ws_layout)]),
@@ -126,6 +127,9 @@ SIGNATURES = {
                                     C.c_size_t, C.c_uint32, C.c_void_p]),
     "gs3_workspace_read_header": (C.c_int, [C.c_void_p, C.POINTER(gs3_ws_header), C.c_void_p]),
     "gs3_backward_workspace_size": (C.c_size_t, [_SCENE_P]),
+    "gs3_loss_scratch_size": (C.c_size_t, [C.c_int32, C.c_int32]),
+    "gs3_loss_l1_dssim": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_float, C.c_void_p,
+                                    C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]),
     "gs3_render_backward": (C.c_int, [_SCENE_P, C.POINTER(gs3_camera), C.POINTER(gs3_light),
                                       C.POINTER(gs3_render_opts), C.c_void_p, C.c_void_p, C.c_size_t,
                                       C.c_size_t, C.c_void_p, C.c_size_t, C.POINTER(gs3_grads),
@@ -187,6 +191,13 @@ def gs3_create_scene(desc: gs3_scene_desc):
     return out
 
 
+def gs3_scene_mlp_scales(scene, which: int, n_hidden: int):
+    """FP8 scene: [(sx_l, sw_l)] for every hidden layer of Phi (0) or Psi (1)."""
+    buf = (C.c_float * (2 * n_hidden))()
+    _check(lib().gs3_scene_mlp_scales(scene, which, buf, 2 * n_hidden), "gs3_scene_mlp_scales")
+    return [(buf[2 * l], buf[2 * l + 1]) for l in range(n_hidden)]
+
+
 def gs3_destroy_scene(scene) -> None:
     _check(lib().gs3_destroy_scene(scene), "gs3_destroy_scene")
 
@@ -215,6 +226,17 @@ def gs3_render_stages(scene, camera: gs3_camera, light: gs3_light, opts: gs3_ren
                                    _ptr(out_rgb), _ptr(workspace),
                                    workspace.numel() * workspace.element_size(), key_capacity,
                                    stages, stream), "gs3_render_stages")
+
+
+def gs3_loss_scratch_size(width: int, height: int) -> int:
+    return int(lib().gs3_loss_scratch_size(width, height))
+
+
+def gs3_loss_l1_dssim(img, target, lam: float, loss_out, dimg_out, scratch, stream: int) -> None:
+    h, w = img.shape[0], img.shape[1]
+    _check(lib().gs3_loss_l1_dssim(_ptr(img), _ptr(target), w, h, lam, _ptr(loss_out), _ptr(dimg_out),
+                                   _ptr(scratch), scratch.numel() * scratch.element_size(), stream),
+           "gs3_loss_l1_dssim")
 
 
 def gs3_backward_workspace_size(scene) -> int:

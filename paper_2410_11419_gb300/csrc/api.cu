@@ -168,8 +168,9 @@ gs3_status gs3_create_scene(const gs3_scene_desc* d, gs3_scene** out) {
     return fail(GS3_ERR_INVALID_ARG, "gs3_create_scene: null lobe array");
   if (!mlp_ok(d->phi, 61, 1)) return fail(GS3_ERR_INVALID_ARG, "gs3_create_scene: unsupported Phi shape");
   if (!mlp_ok(d->psi, 60, 3)) return fail(GS3_ERR_INVALID_ARG, "gs3_create_scene: unsupported Psi shape");
-  if (d->mlp_dtype != GS3_MLP_FP32 && d->mlp_dtype != GS3_MLP_BF16)
-    return fail(GS3_ERR_INVALID_ARG, "gs3_create_scene: mlp_dtype must be GS3_MLP_FP32 or GS3_MLP_BF16");
+  if (d->mlp_dtype != GS3_MLP_FP32 && d->mlp_dtype != GS3_MLP_BF16 && d->mlp_dtype != GS3_MLP_FP8_E4M3)
+    return fail(GS3_ERR_INVALID_ARG,
+                "gs3_create_scene: mlp_dtype must be GS3_MLP_FP32, GS3_MLP_BF16 or GS3_MLP_FP8_E4M3");
   gs3_scene* s = new (std::nothrow) gs3_scene;
   if (!s) return fail(GS3_ERR_OOM, "gs3_create_scene: host allocation failed");
   SceneDev& v = s->dev;
@@ -189,29 +190,40 @@ gs3_status gs3_create_scene(const gs3_scene_desc* d, gs3_scene** out) {
   v.phi = {d->phi.in_dim, d->phi.width, d->phi.n_hidden, d->phi.out_dim, d->phi.act, d->phi.w, d->phi.b};
   v.psi = {d->psi.in_dim, d->psi.width, d->psi.n_hidden, d->psi.out_dim, d->psi.act, d->psi.w, d->psi.b};
   v.mlp_dtype = d->mlp_dtype;
-  if (d->mlp_dtype == GS3_MLP_BF16) {
+  if (d->mlp_dtype != GS3_MLP_FP32) {
     for (int w = 0; w < 2; ++w) {
       const MlpDev& m = w == 0 ? v.phi : v.psi;
-      if (!mlp_tc_supported(m)) {
+      if (!mlp_tc_supported(m, d->mlp_dtype)) {
         gs3_destroy_scene(s);
-        return fail(GS3_ERR_UNSUPPORTED, "gs3_create_scene: MLP shape not supported by the BF16 path");
+        return fail(GS3_ERR_UNSUPPORTED, "gs3_create_scene: MLP shape not supported by the tensor-core path");
       }
-      if (cudaMalloc(&s->tc_blob[w], mlp_tc_blob_bytes(m)) != cudaSuccess) {
+      if (cudaMalloc(&s->tc_blob[w], mlp_tc_blob_bytes(m, d->mlp_dtype)) != cudaSuccess) {
         s->tc_blob[w] = nullptr;
         gs3_destroy_scene(s);
-        return fail(GS3_ERR_OOM, "gs3_create_scene: BF16 weight allocation failed");
+        return fail(GS3_ERR_OOM, "gs3_create_scene: tensor-core weight allocation failed");
       }
-      pack_mlp_tc(m, s->tc_blob[w], 0);
+      pack_mlp_tc(m, d->mlp_dtype, v, w, s->tc_blob[w], 0);
     }
     cudaError_t e = cudaStreamSynchronize(0);
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) {
       gs3_destroy_scene(s);
-      return cuda_fail(e, "gs3_create_scene: BF16 weight packing");
+      return cuda_fail(e, "gs3_create_scene: tensor-core weight packing");
     }
   }
   *out = s;
   return GS3_OK;
+}
+
+gs3_status gs3_scene_mlp_scales(const gs3_scene* s, int32_t which, float* out, int32_t cap) {
+  if (!s || !out || (which != 0 && which != 1)) return fail(GS3_ERR_INVALID_ARG, "gs3_scene_mlp_scales: bad argument");
+  if (s->dev.mlp_dtype != GS3_MLP_FP8_E4M3)
+    return fail(GS3_ERR_UNSUPPORTED, "gs3_scene_mlp_scales: the scene's MLPs are not FP8");
+  const MlpDev& m = which == 0 ? s->dev.phi : s->dev.psi;
+  if (cap < 2 * m.n_hidden) return fail(GS3_ERR_INVALID_ARG, "gs3_scene_mlp_scales: out holds fewer than 2 n_hidden");
+  const cudaError_t e = cudaMemcpy(out, s->tc_blob[which] + mlp_tc_scale_offset(m, s->dev.mlp_dtype),
+                                   sizeof(float) * 2 * m.n_hidden, cudaMemcpyDeviceToHost);
+  return e == cudaSuccess ? GS3_OK : cuda_fail(e, "gs3_scene_mlp_scales");
 }
 
 gs3_status gs3_destroy_scene(gs3_scene* s) {
@@ -306,7 +318,7 @@ gs3_status gs3_render_stages(gs3_scene* scene, const gs3_camera* cam, const gs3_
     else launch_shadow_reduce(f, s);
   }
   if (stages & GS3_STAGE_MLP) {
-    if (scene->dev.mlp_dtype == GS3_MLP_BF16) {
+    if (scene->dev.mlp_dtype != GS3_MLP_FP32) {
       launch_mlp(f, s, /*identity_only=*/true);
       const unsigned char* blobs[2] = {scene->tc_blob[0], scene->tc_blob[1]};
       launch_mlp_tc(f, blobs, s);
@@ -382,6 +394,27 @@ static void light_view_host(const float pL[3], const float tg[3], float R[9], fl
   const float dx = fy * rz - fz * ry, dy = fz * rx - fx * rz, dz = fx * ry - fy * rx;
   R[0] = rx; R[1] = ry; R[2] = rz; R[3] = dx; R[4] = dy; R[5] = dz; R[6] = fx; R[7] = fy; R[8] = fz;
   for (int i = 0; i < 3; ++i) t[i] = -(R[3 * i] * pL[0] + R[3 * i + 1] * pL[1] + R[3 * i + 2] * pL[2]);
+}
+
+size_t gs3_loss_scratch_size(int32_t width, int32_t height) {
+  if (width < 1 || height < 1) return 0;
+  return loss_scratch_bytes(width, height);
+}
+
+gs3_status gs3_loss_l1_dssim(const float* img, const float* target, int32_t width, int32_t height, float lambda,
+                             float* loss_out, float* dimg, void* scratch, size_t scratch_bytes, void* stream) {
+  if (!img || !target || !loss_out || !dimg || !scratch || width < 1 || height < 1)
+    return fail(GS3_ERR_INVALID_ARG, "gs3_loss_l1_dssim: bad argument");
+  const size_t img_bytes = (size_t)width * height * 3 * sizeof(float);
+  const size_t need = loss_scratch_bytes(width, height);
+  if (scratch_bytes < need || !device_range_ok(scratch, need) || !device_range_ok(img, img_bytes) ||
+      !device_range_ok(target, img_bytes) || !device_range_ok(dimg, img_bytes) ||
+      !device_range_ok(loss_out, sizeof(float)))
+    return fail(GS3_ERR_INVALID_ARG, "gs3_loss_l1_dssim: a buffer is smaller than stated");
+  const gs3_status st = run_loss(img, target, width, height, lambda, loss_out, dimg, scratch,
+                                 reinterpret_cast<cudaStream_t>(stream));
+  if (st != GS3_OK) return fail(st, "gs3_loss_l1_dssim: launch failed");
+  return GS3_OK;
 }
 
 gs3_status gs3_workspace_read_header(const void* workspace, gs3_ws_header* out, void* stream) {

@@ -68,6 +68,7 @@ struct ShadowParams {
   const SplatRec* rrec;
   const uint32_t* off;
   const uint32_t* kbound;
+  uint8_t* pass_mask;  // per list entry: warps with a passing pixel (written as receiver)
   float2* partial;
   float* light_final;
   int W, H, gx;
@@ -77,6 +78,7 @@ struct ShadowParams {
 struct ShadowSmem {
   float4 r0[kRecv], r1[kRecv];
   uint32_t rk[kRecv], rslot[kRecv];
+  uint32_t rpass[kRecv];  // warps in which the receiver passed at some pixel
   float4 o0[kOccWin], o1[kOccWin];
   float2 red[4][kRecv];
 };
@@ -95,18 +97,44 @@ __device__ __forceinline__ uint32_t warp_mask8(float ux, float vy, float hx, flo
   return m;
 }
 
-// e0 = (ux, vy, -A/2, -C/2) centre relative to the tile origin (ox, oy);
-// e1 = (-B, pthr, gamma, warp mask bits)
+// Entries carry the conic pre-multiplied by log2(e), so beta = 2^power2 with
+//   power2 = a dx^2 + r dx dy + c dy^2 = dx (a dx) + dy (c dy + r dx),
+//   a = -A/2 log2e, r = -B log2e, c = -C/2 log2e, (dx, dy) = pixel - centre.
+// e0 = (ux, vy, a, c): centre relative to the tile origin (ox, oy);
+// e1 = (r, pthr log2e, gamma, warp mask bits).
+constexpr float kLog2e = 1.4426950408889634f;
+
+__device__ __forceinline__ float ex2(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 __device__ __forceinline__ void make_entry(const SplatRec& q, float ox, float oy, float4& e0, float4& e1) {
   const float ux = (q.a.x - ox) + q.b.w, vy = (q.a.y - oy) + q.c.x;
   const uint32_t m = warp_mask8(ux, vy, q.c.y, q.c.z);
-  e0 = make_float4(ux, vy, -0.5f * q.b.x, -0.5f * q.b.z);
-  e1 = make_float4(-q.b.y, q.c.w, q.a.z, __uint_as_float(m));
+  e0 = make_float4(ux, vy, -0.5f * kLog2e * q.b.x, -0.5f * kLog2e * q.b.z);
+  e1 = make_float4(-kLog2e * q.b.y, kLog2e * q.c.w, q.a.z, __uint_as_float(m));
 }
 
-__device__ __forceinline__ float power_at(const float4 e0, float r, float lx, float ly) {
-  const float dx = lx - e0.x, dy = ly - e0.y;
-  return fmaf(dx, fmaf(e0.z, dx, r * dy), (e0.w * dy) * dy);
+// power2 at the thread's two pixels (lx, ly0), (lx, ly1): the dx terms are shared
+__device__ __forceinline__ void powers2(const float4 e0, float r, float lx, float ly0, float ly1, float& p0,
+                                        float& p1) {
+  const float dx = lx - e0.x;
+  const float sx = (e0.z * dx) * dx, v = r * dx;
+  const float dy0 = ly0 - e0.y, dy1 = ly1 - e0.y;
+  p0 = fmaf(dy0, fmaf(e0.w, dy0, v), sx);
+  p1 = fmaf(dy1, fmaf(e0.w, dy1, v), sx);
+}
+
+// one occluder on both rays: A *= 1 - min(amax, gamma beta) where it passes,
+// written as max(1 - amax, 1 - gamma beta)
+__device__ __forceinline__ void occlude(const float4 o0, const float4 o1, float lx, float ly0, float ly1,
+                                        float omin, float& A0, float& A1) {
+  float p0, p1;
+  powers2(o0, o1.x, lx, ly0, ly1, p0, p1);
+  if (p0 >= o1.y && p0 <= 0.f) A0 *= fmaxf(omin, fmaf(-o1.z, ex2(p0), 1.f));
+  if (p1 >= o1.y && p1 <= 0.f) A1 *= fmaxf(omin, fmaf(-o1.z, ex2(p1), 1.f));
 }
 
 __global__ void __launch_bounds__(kShadowThreads, 8) k_shadow(ShadowParams p) {
@@ -118,11 +146,14 @@ __global__ void __launch_bounds__(kShadowThreads, 8) k_shadow(ShadowParams p) {
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   const uint32_t wbit = 1u << warp;
   const int lxi = (warp & 1) * 8 + (lane & 7), lyi = (warp >> 1) * 8 + (lane >> 3);
-  const float lx = lxi + 0.5f, ly0 = lyi + 0.5f, ly1 = lyi + 4.5f;
   const bool in0 = tx * kTile + lxi < p.W && ty * kTile + lyi < p.H;
   const bool in1 = tx * kTile + lxi < p.W && ty * kTile + lyi + 4 < p.H;
+  // A pixel outside the image is moved far from every splat: its power is
+  // then far below any threshold, it never passes, and its A is never used.
+  const float kFar = 1.0e6f;
+  const float lx = lxi + 0.5f, ly0 = in0 ? lyi + 0.5f : kFar, ly1 = in1 ? lyi + 4.5f : kFar;
   const bool hi_lane = (lane & 16) != 0;
-  const float amax = p.amax;
+  const float omin = 1.f - p.amax;
   const uint32_t b = p.tile_start[tile], e = p.tile_start[tile + 1];
   float A0 = 1.f, A1 = 1.f;
   uint32_t k = b;
@@ -135,6 +166,7 @@ __global__ void __launch_bounds__(kShadowThreads, 8) k_shadow(ShadowParams p) {
       make_entry(q, ox, oy, S.r0[t], S.r1[t]);
       S.rk[t] = p.kbound[rb + t];
       S.rslot[t] = p.off[rank] + (uint32_t)((ty - q.r.y) * (q.r.z - q.r.x + 1) + (tx - q.r.x));
+      S.rpass[t] = 0u;
     }
     __syncthreads();
     const uint32_t klast = S.rk[rc - 1];
@@ -142,7 +174,14 @@ __global__ void __launch_bounds__(kShadowThreads, 8) k_shadow(ShadowParams p) {
     while (jj < rc) {
       const uint32_t kt = min(klast, k + (uint32_t)kOccWin);
       __syncthreads();  // the previous window is consumed
-      for (uint32_t i = t; i < kt - k; i += kShadowThreads) make_entry(p.rrec[p.list[k + i]], ox, oy, S.o0[i], S.o1[i]);
+      // An occluder of an earlier receiver batch is needed only by the warps in
+      // which it passed as a receiver (same power test; pixels outside the
+      // image never pass).  Occluders of this batch keep their bounding-box
+      // mask: their pass bits are still being gathered.
+      for (uint32_t i = t; i < kt - k; i += kShadowThreads) {
+        make_entry(p.rrec[p.list[k + i]], ox, oy, S.o0[i], S.o1[i]);
+        if (k + i < rb) S.o1[i].w = __uint_as_float((uint32_t)p.pass_mask[k + i]);
+      }
       __syncthreads();
       const uint32_t ow = k;
       for (; jj < rc; ++jj) {
@@ -150,46 +189,43 @@ __global__ void __launch_bounds__(kShadowThreads, 8) k_shadow(ShadowParams p) {
         if (kend > kt) break;
         for (; k < kend; ++k) {
           const float4 o1 = S.o1[k - ow];
-          if (__float_as_uint(o1.w) & wbit) {
-            const float4 o0 = S.o0[k - ow];
-            const float p0 = power_at(o0, o1.x, lx, ly0), p1 = power_at(o0, o1.x, lx, ly1);
-            if (p0 >= o1.y && p0 <= 0.f) A0 *= 1.f - fminf(amax, o1.z * __expf(p0));
-            if (p1 >= o1.y && p1 <= 0.f) A1 *= 1.f - fminf(amax, o1.z * __expf(p1));
-          }
+          if (__float_as_uint(o1.w) & wbit) occlude(S.o0[k - ow], o1, lx, ly0, ly1, omin, A0, A1);
         }
         const float4 r1 = S.r1[jj];
         if (__float_as_uint(r1.w) & wbit) {
           const float4 r0 = S.r0[jj];
-          const float p0 = power_at(r0, r1.x, lx, ly0), p1 = power_at(r0, r1.x, lx, ly1);
-          const float b0 = (in0 && p0 >= r1.y && p0 <= 0.f) ? __expf(p0) : 0.f;
-          const float b1 = (in1 && p1 >= r1.y && p1 <= 0.f) ? __expf(p1) : 0.f;
-          const float num = fmaf(b0, A0, b1 * A1), den = b0 + b1;
-          // two sums with one butterfly: lanes 0-15 end with num, 16-31 with den
-          float v = (hi_lane ? den : num) + __shfl_xor_sync(0xffffffffu, hi_lane ? num : den, 16);
+          float p0, p1;
+          powers2(r0, r1.x, lx, ly0, ly1, p0, p1);
+          const bool q0 = p0 >= r1.y && p0 <= 0.f, q1 = p1 >= r1.y && p1 <= 0.f;
+          if (__any_sync(0xffffffffu, q0 || q1)) {
+            if (lane == 0) atomicOr(&S.rpass[jj], wbit);
+            const float b0 = q0 ? ex2(p0) : 0.f;
+            const float b1 = q1 ? ex2(p1) : 0.f;
+            const float num = fmaf(b0, A0, b1 * A1), den = b0 + b1;
+            // two sums with one butterfly: lanes 0-15 end with num, 16-31 with den
+            float v = (hi_lane ? den : num) + __shfl_xor_sync(0xffffffffu, hi_lane ? num : den, 16);
 #pragma unroll
-          for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-          if (lane == 0) S.red[warp][jj].x = v;
-          if (lane == 16) S.red[warp][jj].y = v;
+            for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0) S.red[warp][jj].x = v;
+            if (lane == 16) S.red[warp][jj].y = v;
+          }
         }
       }
       for (; k < kt; ++k) {  // the next receiver needs occluders past this window
         const float4 o1 = S.o1[k - ow];
-        if (__float_as_uint(o1.w) & wbit) {
-          const float4 o0 = S.o0[k - ow];
-          const float p0 = power_at(o0, o1.x, lx, ly0), p1 = power_at(o0, o1.x, lx, ly1);
-          if (p0 >= o1.y && p0 <= 0.f) A0 *= 1.f - fminf(amax, o1.z * __expf(p0));
-          if (p1 >= o1.y && p1 <= 0.f) A1 *= 1.f - fminf(amax, o1.z * __expf(p1));
-        }
+        if (__float_as_uint(o1.w) & wbit) occlude(S.o0[k - ow], o1, lx, ly0, ly1, omin, A0, A1);
       }
     }
     __syncthreads();
     if (t < rc) {
-      const uint32_t m = __float_as_uint(S.r1[t].w);
+      // only the warps with a passing pixel wrote a sum; added in fixed order
+      const uint32_t m = S.rpass[t];
       float2 sum = make_float2(0.f, 0.f);
 #pragma unroll
       for (int w = 0; w < 4; ++w)
         if (m & (1u << w)) { sum.x += S.red[w][t].x; sum.y += S.red[w][t].y; }
       p.partial[S.rslot[t]] = sum;
+      p.pass_mask[rb + t] = (uint8_t)m;
     }
   }
   // the product over every occluder of the ray (the backward starts from it)
@@ -367,6 +403,7 @@ void launch_shadow_composite(const FrameArgs& f, cudaStream_t s) {
   p.rrec = at<SplatRec>(ws, b.rrec);
   p.off = at<uint32_t>(ws, b.off);
   p.kbound = kb;
+  p.pass_mask = reinterpret_cast<uint8_t*>(dl);  // the depths are consumed by k_occluder_bound
   p.partial = at<float2>(ws, f.L->partial);
   p.light_final = at<float>(ws, f.L->light_final);
   p.W = f.L->width; p.H = f.L->height; p.gx = f.L->gx;
@@ -374,6 +411,7 @@ void launch_shadow_composite(const FrameArgs& f, cudaStream_t s) {
   static bool configured = false;
   if (!configured) {
     cudaFuncSetAttribute(k_shadow, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(ShadowSmem));
+    cudaFuncSetAttribute(k_shadow, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
     configured = true;
   }
   k_shadow<<<f.L->ntiles, kShadowThreads, sizeof(ShadowSmem), s>>>(p);

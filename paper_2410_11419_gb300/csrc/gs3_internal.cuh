@@ -100,6 +100,9 @@ struct FrameArgs {
   float light_view[12];  // light camera R (9), t (3); filled on the host for the backward
 };
 
+size_t loss_scratch_bytes(int W, int H);
+gs3_status run_loss(const float* img, const float* tgt, int W, int H, float lambda, float* loss, float* dimg,
+                    void* scratch, cudaStream_t s);
 size_t backward_workspace_bytes(int n, const MlpDev& phi, const MlpDev& psi);
 gs3_status run_backward(const FrameArgs& f, const float* dimg, void* bws, size_t bws_bytes,
                         const gs3_grads& out, cudaStream_t s);
@@ -110,10 +113,11 @@ void launch_binning(const FrameArgs& f, int splat, cudaStream_t s);
 void launch_shadow_composite(const FrameArgs& f, cudaStream_t s);
 void launch_shadow_reduce(const FrameArgs& f, cudaStream_t s);
 void launch_mlp(const FrameArgs& f, cudaStream_t s, bool identity_only = false);
-// BF16 tensor-core MLPs (mlp_tc.cu)
-size_t mlp_tc_blob_bytes(const MlpDev& m);
-size_t pack_mlp_tc(const MlpDev& m, unsigned char* dst, cudaStream_t s);
-bool mlp_tc_supported(const MlpDev& m);
+// BF16 / FP8 tensor-core MLPs (mlp_tc.cu)
+size_t mlp_tc_blob_bytes(const MlpDev& m, int dtype);
+size_t mlp_tc_scale_offset(const MlpDev& m, int dtype);  // FP8: (sx, sw) per hidden layer
+void pack_mlp_tc(const MlpDev& m, int dtype, const SceneDev& sc, int which, unsigned char* dst, cudaStream_t s);
+bool mlp_tc_supported(const MlpDev& m, int dtype);
 void launch_mlp_tc(const FrameArgs& f, const unsigned char* const blobs[2], cudaStream_t s);
 void launch_camera_composite(const FrameArgs& f, float* out_rgb, cudaStream_t s);
 void launch_fill_shadow_one(const FrameArgs& f, cudaStream_t s);
@@ -151,5 +155,5 @@ __host__ __device__ inline T* at(unsigned char* ws, size_t off) {
 // The scene handle of the C ABI: borrowed parameters plus owned derived buffers.
 struct gs3_scene {
   gs3::SceneDev dev;
-  unsigned char* tc_blob[2] = {nullptr, nullptr};  // BF16 tensor-core weights (owned)
+  unsigned char* tc_blob[2] = {nullptr, nullptr};  // tensor-core weights and FP8 scales (owned)
 };

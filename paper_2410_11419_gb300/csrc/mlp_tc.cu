@@ -1,5 +1,15 @@
-// K8 (BF16 form): Phi (Sec. 4.2) and Psi (Sec. 4.3) on the 5th-generation
-// tensor cores.  Operands in BF16, accumulation in FP32 in tensor memory.
+// K8 (tensor-core forms): Phi (Sec. 4.2) and Psi (Sec. 4.3) on the
+// 5th-generation tensor cores, accumulation in FP32 in tensor memory.
+// Operands are BF16 (kind::f16, K = 16 per instruction) or FP8 E4M3 with
+// per-tensor scales (kind::f8f6f4, K = 32 per instruction).  Both read the
+// same K-major, no-swizzle core-matrix layout (8 rows x 16 bytes).
+//
+// FP8 scales: hidden layer l computes acc = sum_k q(x_k / sx_l) q(w_jk / sw_l)
+// and dequantises h = acc sx_l sw_l + b.  sw_l = max|W_l| / 448 (the E4M3
+// maximum); sx_l = 2 max|x| / 448 over a calibration pass at scene creation
+// (FP32 evaluation of the network on a strided sample of the Gaussians for
+// eight fixed directions), so inputs up to twice the calibrated range stay
+// finite; larger ones saturate.
 //
 // One persistent CTA per SM, 128 threads, thread t owns row t of a 128-row
 // tile of Gaussians:
@@ -17,6 +27,7 @@
 // Every wait is bounded: a timeout sets GS3_ERR_TIMEOUT in the workspace
 // header and the CTA frees its tensor memory and returns.
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 
 #include "gs3_internal.cuh"
 
@@ -90,6 +101,14 @@ __device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint3
       "l"(a), "l"(b), "r"(idesc), "r"(acc)
       : "memory");
 }
+__device__ __forceinline__ void tc_mma_f8(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
 __device__ __forceinline__ void tc_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
                : "memory");
@@ -119,18 +138,23 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint
   return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
          ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
 }
-// Instruction descriptor, kind::f16: D F32, A and B BF16, both K-major, dense.
-__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+// Instruction descriptor: D F32, A and B K-major, dense.  kind::f16 with
+// A = B = BF16 (format 1), or kind::f8f6f4 with A = B = E4M3 (format 0).
+__host__ __device__ constexpr uint32_t idesc_mma(int EB, int M, int N) {
+  return (1u << 4) | (EB == 2 ? (1u << 7) | (1u << 10) : 0u) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
 }
-// byte offset of element (r, k) in a K-major no-swizzle tile of kdim columns
-__host__ __device__ inline uint32_t canon_off(int r, int k, int kdim) {
-  return (uint32_t)((r >> 3) * (kdim * 16) + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2);
+// byte offset of byte kb of row r in a K-major no-swizzle tile whose rows
+// hold krow bytes: core matrices of 8 rows x 16 bytes, 128 bytes apart
+// along K (leading offset), 8 * krow bytes apart along M/N (stride offset)
+__host__ __device__ inline uint32_t canon_off(int r, int kb, int krow) {
+  return (uint32_t)((r >> 3) * (krow * 8) + (kb >> 4) * 128 + (r & 7) * 16 + (kb & 15));
 }
 
 struct TcParams {
   int n, which, nh, width, out_dim, act;
-  const unsigned char* wblob;  // BF16 hidden-layer tiles, canonical layout
+  const unsigned char* wblob;  // hidden-layer weight tiles, canonical layout
+  const float* scales;         // FP8: (sx_l, sw_l) per hidden layer; null for BF16
   uint32_t wblob_bytes;
   const float* bias;  // nh x width
   const float* wout;  // out_dim x width
@@ -157,14 +181,28 @@ __device__ __forceinline__ void pe_row(float* x, int base, float v0, float v1, f
   }
 }
 
-__device__ __forceinline__ void store_bf16x8(unsigned char* tile, int row, int k0, int kdim, const float* v) {
-  __nv_bfloat162 h[4];
+// 16 bytes of row `row` starting at element k0: 8 BF16 or 16 E4M3 values (times inv)
+template <int EB>
+__device__ __forceinline__ void store16(unsigned char* tile, int row, int k0, int kdim, const float* v, float inv) {
+  uint4 u;
+  if constexpr (EB == 2) {
+    __nv_bfloat162 h[4];
 #pragma unroll
-  for (int i = 0; i < 4; ++i) h[i] = __float22bfloat162_rn(make_float2(v[2 * i], v[2 * i + 1]));
-  *reinterpret_cast<uint4*>(tile + canon_off(row, k0, kdim)) = *reinterpret_cast<uint4*>(h);
+    for (int i = 0; i < 4; ++i) h[i] = __float22bfloat162_rn(make_float2(v[2 * i], v[2 * i + 1]));
+    u = *reinterpret_cast<uint4*>(h);
+  } else {
+    __nv_fp8x2_storage_t h[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+      h[i] = __nv_cvt_float2_to_fp8x2(make_float2(v[2 * i] * inv, v[2 * i + 1] * inv), __NV_SATFINITE, __NV_E4M3);
+    u = *reinterpret_cast<uint4*>(h);
+  }
+  *reinterpret_cast<uint4*>(tile + canon_off(row, k0 * EB, kdim * EB)) = u;
 }
 
+template <int EB>
 __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_tc(TcParams p) {
+  constexpr int kChunk = 16 / EB;  // elements per 16-byte store
   extern __shared__ __align__(1024) unsigned char sm[];
   __shared__ __align__(8) uint64_t bar_w, bar_mma;
   __shared__ uint32_t tmem_slot;
@@ -174,8 +212,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_tc(TcParams p) {
   // shared layout: [weights blob][X 128 x 64][H 128 x W][bias][wout][bout]
   unsigned char* wsm = sm;
   unsigned char* xsm = sm + ((p.wblob_bytes + 1023) & ~1023u);
-  unsigned char* hsm = xsm + kTcRows * kK0 * 2;
-  float* bsm = reinterpret_cast<float*>(hsm + kTcRows * W * 2);
+  unsigned char* hsm = xsm + kTcRows * kK0 * EB;
+  float* bsm = reinterpret_cast<float*>(hsm + kTcRows * W * EB);
   float* wosm = bsm + nh * W;
   float* bosm = wosm + p.out_dim * W;
 
@@ -204,7 +242,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_tc(TcParams p) {
   if (t < p.out_dim) bosm[t] = p.bout[t];
   const bool w_ok = mbar_wait_bounded(smem_u32(&bar_w), 0);
   int fail = __syncthreads_or(!w_ok);
-  const uint32_t idesc = idesc_bf16(kTcRows, W);
+  const uint32_t idesc = idesc_mma(EB, kTcRows, W);
   const uint32_t my_lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
   const bool leaky = p.act == GS3_ACT_LEAKY_RELU;
   uint32_t phase = 0;
@@ -228,8 +266,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_tc(TcParams p) {
       x[b0 + 58] = l1.x; x[b0 + 59] = l1.y;
 #pragma unroll
       for (int k = b0 + 60; k < kK0; ++k) x[k] = 0.f;
+      const float inv0 = EB == 1 ? 1.f / p.scales[0] : 1.f;
 #pragma unroll
-      for (int k0 = 0; k0 < kK0; k0 += 8) store_bf16x8(xsm, t, k0, kK0, x + k0);
+      for (int k0 = 0; k0 < kK0; k0 += kChunk) store16<EB>(xsm, t, k0, kK0, x + k0, inv0);
     }
     fence_proxy_async();
     __syncthreads();
@@ -240,27 +279,32 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_tc(TcParams p) {
       if (t == 0) {
         tc_fence_after();
         const uint32_t a0 = smem_u32(l == 0 ? xsm : hsm), b0 = smem_u32(wsm + woff);
-        for (int s = 0; s < kdim / 16; ++s)
-          tc_mma(tmem, smem_desc(a0 + s * 256, 128, kdim * 16), smem_desc(b0 + s * 256, 128, kdim * 16), idesc,
-                 s > 0 ? 1u : 0u);
+        const uint32_t sbo = (uint32_t)(kdim * EB * 8);
+        for (int s = 0; s < kdim * EB / 32; ++s) {  // 32 bytes of K per instruction
+          const uint64_t da = smem_desc(a0 + s * 256, 128, sbo), db = smem_desc(b0 + s * 256, 128, sbo);
+          if (EB == 2) tc_mma(tmem, da, db, idesc, s > 0 ? 1u : 0u);
+          else tc_mma_f8(tmem, da, db, idesc, s > 0 ? 1u : 0u);
+        }
         tc_commit(smem_u32(&bar_mma));
       }
-      woff += (uint32_t)(W * kdim * 2);
+      woff += (uint32_t)(W * kdim * EB);
       const bool mma_ok = mbar_wait_bounded(smem_u32(&bar_mma), phase);
       phase ^= 1u;
       tc_fence_after();
       const float* bl = bsm + l * W;
+      const float deq = EB == 1 ? p.scales[2 * l] * p.scales[2 * l + 1] : 1.f;
+      const float inv_next = EB == 1 && l + 1 < nh ? 1.f / p.scales[2 * l + 2] : 1.f;
       for (int c0 = 0; c0 < W; c0 += 32) {
         float v[32];
         tmem_ld32(my_lane_addr + (uint32_t)c0, v);
 #pragma unroll
         for (int i = 0; i < 32; ++i) {
-          float h = v[i] + bl[c0 + i];
+          float h = EB == 1 ? fmaf(v[i], deq, bl[c0 + i]) : v[i] + bl[c0 + i];
           v[i] = h > 0.f ? h : (leaky ? 0.01f * h : 0.f);
         }
         if (l + 1 < nh) {
 #pragma unroll
-          for (int i = 0; i < 32; i += 8) store_bf16x8(hsm, t, c0 + i, W, v + i);
+          for (int i = 0; i < 32; i += kChunk) store16<EB>(hsm, t, c0 + i, W, v + i, inv_next);
         } else {
           for (int o = 0; o < p.out_dim; ++o) {
             const float* wr = wosm + o * W + c0;
@@ -303,50 +347,168 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_tc(TcParams p) {
   if (warp == 0) tmem_dealloc(tmem, ncols);
 }
 
-// FP32 (out, in) row-major weights -> BF16 canonical tile [out rows][kdim] (K zero-padded)
-__global__ void k_pack_bf16(const float* __restrict__ w, int out, int in, int kdim, unsigned char* dst) {
+// FP32 (out, in) row-major weights -> canonical tile [out rows][kdim] (K
+// zero-padded), BF16, or E4M3 of w / sw with sw read from *scale (FP8)
+__global__ void k_pack(const float* __restrict__ w, int out, int in, int kdim, int eb, const float* scale,
+                       unsigned char* dst) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= out * kdim) return;
   const int r = i / kdim, k = i - r * kdim;
   const float v = k < in ? w[(size_t)r * in + k] : 0.f;
-  *reinterpret_cast<__nv_bfloat16*>(dst + canon_off(r, k, kdim)) = __float2bfloat16_rn(v);
+  if (eb == 2) {
+    *reinterpret_cast<__nv_bfloat16*>(dst + canon_off(r, 2 * k, 2 * kdim)) = __float2bfloat16_rn(v);
+  } else {
+    dst[canon_off(r, k, kdim)] = __nv_cvt_float_to_fp8(v / *scale, __NV_SATFINITE, __NV_E4M3);
+  }
+}
+
+constexpr float kE4M3Max = 448.f;
+
+// sw = max|W| / 448 of one layer (one block; layers hold at most 128 x 128 values)
+__global__ void k_weight_scale(const float* __restrict__ w, int count, float* scale) {
+  __shared__ float red[256];
+  float m = 0.f;
+  for (int i = threadIdx.x; i < count; i += blockDim.x) m = fmaxf(m, fabsf(w[i]));
+  red[threadIdx.x] = m;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] = fmaxf(red[threadIdx.x], red[threadIdx.x + o]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *scale = red[0] > 0.f ? red[0] / kE4M3Max : 1.f;
+}
+
+constexpr int kCalibDirs = 8;
+constexpr int kCalibSample = 16384;
+constexpr int kCalibThreads = 64;  // 64 rows x (width + 1) floats of shared memory: <= 33 KB
+
+// Calibration forward pass in FP32: row = (sample i, direction d); records
+// max |input| of every hidden layer (as float bits; all values >= 0) in amax[l].
+__global__ void __launch_bounds__(kCalibThreads) k_calib(MlpDev m, int which, int n, const float4* __restrict__ mean_op,
+                                               const float4* __restrict__ latent, int samples,
+                                               uint32_t* __restrict__ amax) {
+  extern __shared__ float hs[];  // [kCalibThreads][W + 1]
+  const int W = m.width, t = threadIdx.x;
+  const int row = blockIdx.x * kCalibThreads + t;
+  const bool live = row < samples * kCalibDirs;
+  const int i = live ? row / kCalibDirs : 0, d = row % kCalibDirs;
+  const int g = (int)(((long long)i * n) / samples);
+  // direction d of a Fibonacci sphere of kCalibDirs points
+  const float zc = 1.f - (2.f * d + 1.f) / kCalibDirs, rc = sqrtf(fmaxf(0.f, 1.f - zc * zc));
+  const float ph = 2.39996323f * d;
+  float x[kK0];
+  const float4 mu = mean_op[g];
+  const int b0 = which == 0 ? 1 : 0;
+  if (which == 0) x[0] = (d & 1) ? 1.f : 0.f;
+  pe_row(x, b0, rc * cosf(ph), rc * sinf(ph), zc);
+  pe_row(x, b0 + 27, mu.x, mu.y, mu.z);
+  const float4 l0 = latent[g], l1 = latent[n + g];
+  x[b0 + 54] = l0.x; x[b0 + 55] = l0.y; x[b0 + 56] = l0.z; x[b0 + 57] = l0.w;
+  x[b0 + 58] = l1.x; x[b0 + 59] = l1.y;
+  float* h = hs + t * (W + 1);
+  __shared__ float red[kCalibThreads];
+  const float* w = m.w;
+  const float* b = m.b;
+  const bool leaky = m.act == GS3_ACT_LEAKY_RELU;
+  for (int l = 0; l < m.n_hidden; ++l) {
+    const int din = l == 0 ? m.in_dim : W;
+    float mx = 0.f;
+    for (int k = 0; k < din; ++k) mx = fmaxf(mx, fabsf(l == 0 ? x[k] : h[k]));
+    red[t] = live ? mx : 0.f;
+    __syncthreads();
+    for (int o = kCalibThreads / 2; o > 0; o >>= 1) {
+      if (t < o) red[t] = fmaxf(red[t], red[t + o]);
+      __syncthreads();
+    }
+    if (t == 0) atomicMax(&amax[l], __float_as_uint(red[0]));
+    __syncthreads();  // red is reused by the next layer
+    float out[128];
+    for (int j = 0; j < W; ++j) {
+      float s = b[j];
+      for (int k = 0; k < din; ++k) s = fmaf(l == 0 ? x[k] : h[k], w[(size_t)j * din + k], s);
+      out[j] = s > 0.f ? s : (leaky ? 0.01f * s : 0.f);
+    }
+    for (int j = 0; j < W; ++j) h[j] = out[j];
+    w += (size_t)W * din;
+    b += W;
+  }
+}
+
+__global__ void k_calib_finish(const uint32_t* amax, int nh, float* scales) {
+  const int l = threadIdx.x;
+  if (l < nh) {
+    const float a = __uint_as_float(amax[l]);
+    scales[2 * l] = a > 0.f ? 2.f * a / kE4M3Max : 1.f;
+  }
 }
 
 }  // namespace
 
-size_t mlp_tc_blob_bytes(const MlpDev& m) {
+static int elem_bytes(int dtype) { return dtype == GS3_MLP_FP8_E4M3 ? 1 : 2; }
+
+static size_t weight_bytes(const MlpDev& m, int eb) {
   size_t b = 0;
-  for (int l = 0; l < m.n_hidden; ++l) b += (size_t)m.width * (l == 0 ? kK0 : m.width) * 2;
+  for (int l = 0; l < m.n_hidden; ++l) b += (size_t)m.width * (l == 0 ? kK0 : m.width) * eb;
   return b;
 }
+static size_t scale_offset(const MlpDev& m, int eb) { return (weight_bytes(m, eb) + 255) & ~size_t(255); }
 
-// Arrange the hidden layers' weights for the tensor cores; returns the bytes written.
-size_t pack_mlp_tc(const MlpDev& m, unsigned char* dst, cudaStream_t s) {
+size_t mlp_tc_scale_offset(const MlpDev& m, int dtype) { return scale_offset(m, elem_bytes(dtype)); }
+
+// blob = [weight tiles][FP8: scales (sx, sw) x n_hidden][FP8: amax scratch]
+size_t mlp_tc_blob_bytes(const MlpDev& m, int dtype) {
+  const int eb = elem_bytes(dtype);
+  return eb == 2 ? weight_bytes(m, eb) : scale_offset(m, eb) + 2 * 4 * 4 + 4 * 4;
+}
+
+// Arrange the hidden layers' weights for the tensor cores (and, for FP8,
+// derive the per-tensor scales); stream-ordered.
+void pack_mlp_tc(const MlpDev& m, int dtype, const SceneDev& sc, int which, unsigned char* dst, cudaStream_t s) {
+  const int eb = elem_bytes(dtype);
+  float* scales = reinterpret_cast<float*>(dst + scale_offset(m, eb));
+  uint32_t* amax = reinterpret_cast<uint32_t*>(scales + 8);
+  if (eb == 1) {
+    cudaMemsetAsync(amax, 0, 4 * sizeof(uint32_t), s);
+    const int samples = sc.n < kCalibSample ? sc.n : kCalibSample;
+    const int rows = samples * kCalibDirs;
+    const size_t shm = (size_t)kCalibThreads * (m.width + 1) * sizeof(float);
+    k_calib<<<(rows + kCalibThreads - 1) / kCalibThreads, kCalibThreads, shm, s>>>(m, which, sc.n, sc.mean_op,
+                                                                                  sc.latent, samples, amax);
+    k_calib_finish<<<1, 32, 0, s>>>(amax, m.n_hidden, scales);
+    count_launch(2);
+  }
   size_t off = 0;
   const float* w = m.w;
   for (int l = 0; l < m.n_hidden; ++l) {
     const int in = l == 0 ? m.in_dim : m.width, kdim = l == 0 ? kK0 : m.width;
     const int nel = m.width * kdim;
-    k_pack_bf16<<<(nel + 255) / 256, 256, 0, s>>>(w, m.width, in, kdim, dst + off);
+    if (eb == 1) {
+      k_weight_scale<<<1, 256, 0, s>>>(w, m.width * in, scales + 2 * l + 1);
+      count_launch();
+    }
+    k_pack<<<(nel + 255) / 256, 256, 0, s>>>(w, m.width, in, kdim, eb, scales + 2 * l + 1, dst + off);
     count_launch();
-    off += (size_t)nel * 2;
+    off += (size_t)nel * eb;
     w += (size_t)m.width * in;
   }
-  return off;
 }
 
-static size_t tc_smem_bytes(const MlpDev& m) {
-  const size_t blob = (mlp_tc_blob_bytes(m) + 1023) & ~size_t(1023);
-  return blob + kTcRows * kK0 * 2 + (size_t)kTcRows * m.width * 2 +
+static size_t tc_smem_bytes(const MlpDev& m, int eb) {
+  const size_t blob = (weight_bytes(m, eb) + 1023) & ~size_t(1023);
+  return blob + kTcRows * kK0 * eb + (size_t)kTcRows * m.width * eb +
          4 * ((size_t)m.n_hidden * m.width + (size_t)m.out_dim * m.width + m.out_dim);
 }
 
-bool mlp_tc_supported(const MlpDev& m) {
-  return m.in_dim <= kK0 && m.out_dim <= 4 && m.n_hidden >= 1 &&
-         (m.width == 16 || m.width == 32 || m.width == 64 || m.width == 128) && tc_smem_bytes(m) <= 220 * 1024;
+bool mlp_tc_supported(const MlpDev& m, int dtype) {
+  const int eb = elem_bytes(dtype);
+  // an FP8 instruction consumes K = 32: hidden widths of 16 cannot be fed
+  const bool width_ok = m.width == 32 || m.width == 64 || m.width == 128 || (m.width == 16 && eb == 2);
+  return m.in_dim <= kK0 && m.out_dim <= 4 && m.n_hidden >= 1 && m.n_hidden <= 4 && width_ok &&
+         tc_smem_bytes(m, eb) <= 220 * 1024;
 }
 
 void launch_mlp_tc(const FrameArgs& f, const unsigned char* const blobs[2], cudaStream_t s) {
+  const int eb = elem_bytes(f.sc.mlp_dtype);
   for (int which = 0; which < 2; ++which) {
     const MlpDev& m = which == 0 ? f.sc.phi : f.sc.psi;
     const bool identity = (f.opts.ablate & (which == 0 ? GS3_ABLATE_PHI : GS3_ABLATE_PSI)) != 0;
@@ -359,7 +521,8 @@ void launch_mlp_tc(const FrameArgs& f, const unsigned char* const blobs[2], cuda
     p.out_dim = m.out_dim;
     p.act = m.act;
     p.wblob = blobs[which];
-    p.wblob_bytes = (uint32_t)mlp_tc_blob_bytes(m);
+    p.wblob_bytes = (uint32_t)weight_bytes(m, eb);
+    p.scales = eb == 1 ? reinterpret_cast<const float*>(blobs[which] + scale_offset(m, eb)) : nullptr;
     size_t hidden_w = 0;
     for (int l = 0; l < m.n_hidden; ++l) hidden_w += (size_t)m.width * (l == 0 ? m.in_dim : m.width);
     p.bias = m.b;
@@ -373,14 +536,15 @@ void launch_mlp_tc(const FrameArgs& f, const unsigned char* const blobs[2], cuda
     p.ccol = at<float4>(f.ws, f.L->ccol);
     p.rank_of = at<uint32_t>(f.ws, f.L->sp[0].rank_of);
     p.status = at<uint32_t>(f.ws, f.L->header) + H_STATUS;
-    const size_t smem = tc_smem_bytes(m);
-    cudaFuncSetAttribute(k_mlp_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const size_t smem = tc_smem_bytes(m, eb);
+    auto kern = eb == 2 ? k_mlp_tc<2> : k_mlp_tc<1>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int dev = 0, nsm = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     const int ntiles = (f.sc.n + kTcRows - 1) / kTcRows;
     const int grid = ntiles < nsm ? ntiles : nsm;
-    k_mlp_tc<<<grid, kTcThreads, smem, s>>>(p);
+    kern<<<grid, kTcThreads, smem, s>>>(p);
     count_launch();
   }
 }

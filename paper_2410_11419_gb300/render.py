@@ -234,3 +234,14 @@ def render_differentiable(renderer, cam, light, opts=None):
     sc = renderer.scene
     opts = opts if opts is not None else opts_struct()
     return RenderFunction.apply(renderer, cam, light, opts, *[sc.t[f] for f in N.GRAD_FIELDS])
+
+
+def loss_l1_dssim(img, target, lam: float = 0.2, stream=None):
+    """(loss tensor [1], dL/d(img)) of (1 - lam) L1 + lam (1 - SSIM), on the GPU."""
+    s = torch.cuda.current_stream() if stream is None else stream
+    h, w = img.shape[0], img.shape[1]
+    scratch = torch.empty(N.gs3_loss_scratch_size(w, h), dtype=torch.uint8, device=img.device)
+    loss = torch.empty(1, dtype=torch.float32, device=img.device)
+    dimg = torch.empty_like(img)
+    N.gs3_loss_l1_dssim(img.contiguous(), target.contiguous(), lam, loss, dimg, scratch, s.cuda_stream)
+    return loss, dimg

@@ -119,3 +119,22 @@ def test_autograd_function(gs3):
     for f in N.GRAD_FIELDS:
         assert torch.allclose(ds.t[f].grad, direct[f], rtol=1e-4, atol=1e-8), f
     ds.close()
+
+
+@pytest.mark.parametrize("h,w", [(64, 64), (50, 77)])
+def test_loss_kernel_matches_reference(gs3, h, w):
+    """gs3_loss_l1_dssim against the FP64 reference loss (Sec. 4.4) and its
+    autograd gradient."""
+    import torch
+    from oracle import torch_ref as TR
+    from paper_2410_11419_gb300 import render as R
+    g = torch.Generator().manual_seed(h * w)
+    img = torch.rand((h, w, 3), generator=g, dtype=torch.float64)
+    tgt = (img + 0.1 * torch.randn((h, w, 3), generator=g, dtype=torch.float64)).clamp(0, 1)
+    dref, lref = TR.image_grad_of_loss(img.numpy(), tgt.numpy())
+    loss, dimg = R.loss_l1_dssim(img.float().cuda(), tgt.float().cuda())
+    torch.cuda.synchronize()
+    assert abs(float(loss.item()) - lref) <= 1e-5 * abs(lref) + 1e-7
+    d = dimg.cpu().double().numpy()
+    assert np.abs(d - dref).max() <= 2e-3 * np.abs(dref).max()
+    assert np.linalg.norm(d - dref) <= 1e-3 * np.linalg.norm(dref)
