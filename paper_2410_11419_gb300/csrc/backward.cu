@@ -16,6 +16,7 @@
 // Per-Gaussian accumulators are summed with float atomics (after warp
 // reductions); the result is deterministic up to the order of those atomics.
 #include "gs3_internal.cuh"
+#include "splat_eval.cuh"
 
 namespace gs3 {
 namespace {
@@ -23,8 +24,6 @@ namespace {
 constexpr int kGeom = 8;    // du, dv, dA, dB, dC, dgamma
 constexpr int kColor = 8;   // dshade rgb, dT', dres rgb
 constexpr int kMlpIn = 24;  // Phi: dmu 3, dwi 3, dl 6; Psi: dmu 3, dwo 3, dl 6
-constexpr int kBwdBlocksMlp = 296;
-constexpr int kMlpRows = 32;
 
 struct BwdBufs {
   float* cam_geom;    // [N][8]
@@ -32,7 +31,6 @@ struct BwdBufs {
   float* color;       // [N][8]
   float* dT;          // [N]
   float* mlp_in;      // [N][24]
-  float* wpart[2];    // [kBwdBlocksMlp][params] weight/bias gradient partials
 };
 
 __host__ __device__ size_t mlp_params(const MlpDev& m) {
@@ -49,7 +47,7 @@ __host__ __device__ size_t mlp_params(const MlpDev& m) {
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct BwdPlan {
-  size_t cam_geom, light_geom, color, dT, mlp_in, wred[2], wpart[2], total;
+  size_t cam_geom, light_geom, color, dT, mlp_in, wred[2], mlp_scratch, total;
 };
 
 BwdPlan plan_bwd(int n, const MlpDev& phi, const MlpDev& psi) {
@@ -63,8 +61,8 @@ BwdPlan plan_bwd(int n, const MlpDev& phi, const MlpDev& psi) {
   p.mlp_in = take(4ull * kMlpIn * n);
   p.wred[0] = take(4ull * mlp_params(phi));
   p.wred[1] = take(4ull * mlp_params(psi));
-  p.wpart[0] = take(4ull * kBwdBlocksMlp * mlp_params(phi));
-  p.wpart[1] = take(4ull * kBwdBlocksMlp * mlp_params(psi));
+  const size_t sa = mlp_bwd_scratch_bytes(n, phi), sb = mlp_bwd_scratch_bytes(n, psi);
+  p.mlp_scratch = take(sa > sb ? sa : sb);  // Phi and Psi use it in turn
   p.total = c;
   return p;
 }
@@ -222,249 +220,26 @@ __global__ void __launch_bounds__(256) k_camera_bwd(CamBwdParams p) {
   }
 }
 
-// ---------------------------------------------------------------------------
-// K8b: MLP backward (FP32).  Block = 128 threads, tiles of 32 rows.
-// ---------------------------------------------------------------------------
-struct MlpBwdParams {
-  MlpDev net;
-  int n, which;
-  const float4* mean_op;
-  const float4* latent;
-  const float* T;
-  float light_pos[3], cam_pos[3];
-  const float* color;  // [N][8]: dT' at 3, dres at 4..6
-  float* dT;           // Phi: d/d(input T)
-  float* mlp_in;       // [N][24]
-  float* wpart;        // [blocks][params]
-};
-
-__device__ __forceinline__ void pe_fwd(float* x, int base, float v0, float v1, float v2) {
-  x[base + 0] = v0; x[base + 1] = v1; x[base + 2] = v2;
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const float f = (float)(1 << q);
-    const int o = base + 3 + 6 * q;
-    sincospif(f * v0, &x[o + 0], &x[o + 3]);
-    sincospif(f * v1, &x[o + 1], &x[o + 4]);
-    sincospif(f * v2, &x[o + 2], &x[o + 5]);
-  }
-}
-// d/dv of PE(v) given d/dPE
-__device__ __forceinline__ void pe_bwd(const float* dpe, float v0, float v1, float v2, float* dv) {
-  const float v[3] = {v0, v1, v2};
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    float g = dpe[c];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const float f = (float)(1 << q);
-      float s, co;
-      sincospif(f * v[c], &s, &co);
-      const float k = f * 3.14159265358979323846f;
-      g += k * (co * dpe[3 + 6 * q + c] - s * dpe[3 + 6 * q + 3 + c]);
-    }
-    dv[c] = g;
-  }
-}
-
-constexpr int kMaxW = 128;
-constexpr int kMaxIn = 64;
-
-__global__ void __launch_bounds__(128) k_mlp_bwd(MlpBwdParams p) {
-  extern __shared__ float4 smem4[];
-  float* sm = reinterpret_cast<float*>(smem4);
-  const int nh = p.net.n_hidden, W = p.net.width, din0 = p.net.in_dim, dout = p.net.out_dim;
-  // activations H[l][r][k] for l = 0 (input) .. nh, stride kMaxW + 1; dZ and dH buffers
-  const int S = kMaxW + 1;
-  float* Hbuf = sm;                                   // (nh + 1) x 32 x S
-  float* dZ = Hbuf + (size_t)(nh + 1) * kMlpRows * S;  // 32 x S
-  float* dH = dZ + kMlpRows * S;                       // 32 x S
-  float* Y = dH + kMlpRows * S;                        // 32 x 4 outputs
-  const int t = threadIdx.x;
-  float* part = p.wpart + (size_t)blockIdx.x * mlp_params(p.net);
-  // zero this block's partial
-  for (size_t i = t; i < mlp_params(p.net); i += blockDim.x) part[i] = 0.f;
-  __syncthreads();
-  const int ntiles = (p.n + kMlpRows - 1) / kMlpRows;
-  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int g0 = tile * kMlpRows;
-    // ---- inputs ----
-    if (t < kMlpRows) {
-      const int g = min(g0 + t, p.n - 1);
-      float x[kMaxIn];
-      const float4 m = p.mean_op[g];
-      const float* src = p.which == 0 ? p.light_pos : p.cam_pos;
-      float dx = src[0] - m.x, dy = src[1] - m.y, dz = src[2] - m.z;
-      const float il = rsqrtf(dx * dx + dy * dy + dz * dz);
-      const int b0 = p.which == 0 ? 1 : 0;
-      if (p.which == 0) x[0] = p.T[g];
-      pe_fwd(x, b0, dx * il, dy * il, dz * il);
-      pe_fwd(x, b0 + 27, m.x, m.y, m.z);
-      const float4 l0 = p.latent[g], l1 = p.latent[p.n + g];
-      x[b0 + 54] = l0.x; x[b0 + 55] = l0.y; x[b0 + 56] = l0.z; x[b0 + 57] = l0.w;
-      x[b0 + 58] = l1.x; x[b0 + 59] = l1.y;
-      for (int k = 0; k < din0; ++k) Hbuf[t * S + k] = x[k];
-    }
-    __syncthreads();
-    // ---- forward, hidden layers (thread j owns output column j) ----
-    const float* w = p.net.w;
-    const float* bb = p.net.b;
-    int din = din0;
-    for (int l = 0; l < nh; ++l) {
-      const float* Hin = Hbuf + (size_t)l * kMlpRows * S;
-      float* Hout = Hbuf + (size_t)(l + 1) * kMlpRows * S;
-      if (t < W) {
-        float acc[kMlpRows];
-        const float bj = bb[t];
-#pragma unroll
-        for (int r = 0; r < kMlpRows; ++r) acc[r] = bj;
-        for (int k = 0; k < din; ++k) {
-          const float wk = w[(size_t)t * din + k];
-#pragma unroll
-          for (int r = 0; r < kMlpRows; ++r) acc[r] = fmaf(Hin[r * S + k], wk, acc[r]);
-        }
-        const bool leaky = p.net.act == GS3_ACT_LEAKY_RELU;
-#pragma unroll
-        for (int r = 0; r < kMlpRows; ++r) {
-          const float v = acc[r];
-          Hout[r * S + t] = v > 0.f ? v : (leaky ? 0.01f * v : 0.f);
-        }
-      }
-      __syncthreads();
-      w += (size_t)W * din;
-      bb += W;
-      din = W;
-    }
-    // ---- output layer: y and dz_out ----
-    const float* Hl = Hbuf + (size_t)nh * kMlpRows * S;
-    if (t < kMlpRows * dout) {
-      const int r = t % kMlpRows, o = t / kMlpRows;
-      float acc = bb[o];
-      for (int k = 0; k < W; ++k) acc = fmaf(Hl[r * S + k], w[(size_t)o * W + k], acc);
-      const float y = 1.f / (1.f + expf(-acc));
-      const int g = g0 + r;
-      float dy = 0.f;
-      if (g < p.n) dy = p.which == 0 ? p.color[(size_t)kColor * g + 3] : p.color[(size_t)kColor * g + 4 + o];
-      Y[r * 4 + o] = dy * y * (1.f - y);
-    }
-    __syncthreads();
-    // output-layer weight/bias gradients and dH of the last hidden layer
-    size_t poff = 0;
-    {
-      // offsets of each layer's parameters in the partial: hidden layers first
-      size_t woff_out = 0;
-      int dd = din0;
-      for (int l = 0; l < nh; ++l) { woff_out += (size_t)W * dd + W; dd = W; }
-      poff = woff_out;
-      if (t < W) {
-        for (int o = 0; o < dout; ++o) {
-          float s = 0.f;
-#pragma unroll 8
-          for (int r = 0; r < kMlpRows; ++r) s = fmaf(Y[r * 4 + o], Hl[r * S + t], s);
-          part[poff + (size_t)o * W + t] += s;
-        }
-      }
-      if (t < dout) {
-        float s = 0.f;
-        for (int r = 0; r < kMlpRows; ++r) s += Y[r * 4 + t];
-        part[poff + (size_t)dout * W + t] += s;
-      }
-      if (t < W) {
-        const bool leaky = p.net.act == GS3_ACT_LEAKY_RELU;
-        for (int r = 0; r < kMlpRows; ++r) {
-          float s = 0.f;
-          for (int o = 0; o < dout; ++o) s = fmaf(Y[r * 4 + o], w[(size_t)o * W + t], s);
-          const float h = Hl[r * S + t];
-          dZ[r * S + t] = h > 0.f ? s : (leaky ? 0.01f * s : 0.f);
-        }
-      }
-    }
-    __syncthreads();
-    // ---- hidden layers backward ----
-    for (int l = nh - 1; l >= 0; --l) {
-      const int dinl = l == 0 ? din0 : W;
-      size_t lo = 0;
-      int dd = din0;
-      for (int q = 0; q < l; ++q) { lo += (size_t)W * dd + W; dd = W; }
-      const float* Wl = p.net.w;
-      { int d2 = din0; for (int q = 0; q < l; ++q) { Wl += (size_t)W * d2; d2 = W; } }
-      const float* Hin = Hbuf + (size_t)l * kMlpRows * S;
-      // dW_l[j][k] += sum_r dZ[r][j] Hin[r][k]; thread j owns row j
-      if (t < W) {
-        for (int k = 0; k < dinl; ++k) {
-          float s = 0.f;
-#pragma unroll 8
-          for (int r = 0; r < kMlpRows; ++r) s = fmaf(dZ[r * S + t], Hin[r * S + k], s);
-          part[lo + (size_t)t * dinl + k] += s;
-        }
-        float sb = 0.f;
-        for (int r = 0; r < kMlpRows; ++r) sb += dZ[r * S + t];
-        part[lo + (size_t)W * dinl + t] += sb;
-      }
-      // dH_{l-1}[r][k] = sum_j dZ[r][j] W_l[j][k]; thread k owns column k
-      if (t < dinl) {
-        float acc[kMlpRows];
-#pragma unroll
-        for (int r = 0; r < kMlpRows; ++r) acc[r] = 0.f;
-        for (int j = 0; j < W; ++j) {
-          const float wjk = Wl[(size_t)j * dinl + t];
-#pragma unroll
-          for (int r = 0; r < kMlpRows; ++r) acc[r] = fmaf(dZ[r * S + j], wjk, acc[r]);
-        }
-        const bool leaky = p.net.act == GS3_ACT_LEAKY_RELU;
-#pragma unroll
-        for (int r = 0; r < kMlpRows; ++r) {
-          if (l > 0) {
-            const float h = Hin[r * S + t];
-            dH[r * S + t] = h > 0.f ? acc[r] : (leaky ? 0.01f * acc[r] : 0.f);
-          } else {
-            dH[r * S + t] = acc[r];
-          }
-        }
-      }
-      __syncthreads();
-      // dH becomes the next dZ
-      for (int i = t; i < kMlpRows * S; i += blockDim.x) dZ[i] = dH[i];
-      __syncthreads();
-    }
-    // ---- input gradients: dZ now holds d/dx ----
-    if (t < kMlpRows && g0 + t < p.n) {
-      const int g = g0 + t;
-      const float* dx = dZ + t * S;
-      const float4 m = p.mean_op[g];
-      const float* src = p.which == 0 ? p.light_pos : p.cam_pos;
-      float vx = src[0] - m.x, vy = src[1] - m.y, vz = src[2] - m.z;
-      const float il = rsqrtf(vx * vx + vy * vy + vz * vz);
-      const int b0 = p.which == 0 ? 1 : 0;
-      float dw[3], dm[3];
-      pe_bwd(dx + b0, vx * il, vy * il, vz * il, dw);
-      pe_bwd(dx + b0 + 27, m.x, m.y, m.z, dm);
-      float* out = p.mlp_in + (size_t)kMlpIn * g + (p.which == 0 ? 0 : 12);
-      out[0] = dm[0]; out[1] = dm[1]; out[2] = dm[2];
-      out[3] = dw[0]; out[4] = dw[1]; out[5] = dw[2];
-      for (int k = 0; k < 6; ++k) out[6 + k] = dx[b0 + 54 + k];
-      if (p.which == 0) p.dT[g] = dx[0];
-    }
-    __syncthreads();
-  }
-}
-
-// sum the per-block partials in block order
-__global__ void k_reduce_parts(const float* part, size_t np, int nblocks, float* red) {
-  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= np) return;
-  float s = 0.f;
-  for (int b = 0; b < nblocks; ++b) s += part[(size_t)b * np + i];
-  red[i] = s;
-}
-
 __global__ void k_copy_strided(const float* src, int stride, int off, float* dst, int n) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) dst[i] = src[(size_t)stride * i + off];
 }
 
 // ---------------------------------------------------------------------------
-// K6b: shadow splat backward
+// K6b: shadow splat backward.
+// Reverse sweep of the forward's two-cursor pass over each light tile, with
+// the forward's thread layout, entries and alpha decisions (splat_eval.cuh).
+// Per ray m the thread restarts from the product over every occluder A_m
+// (stored by the forward) and a suffix sum S_m = sum coef_j beta_jm T_m(j)
+// over the receivers already visited (coef_j = dL/dT_j / den_j):
+//   occluder k (passing):  A /= (1 - alpha_k),  dL/dalpha_k = -S / (1 - alpha_k)
+//   receiver j (passing):  dL/dbeta_j = coef_j (A - T_j),  S += coef_j beta_j A
+// with A = T_m(j) when receiver j is reached.  Occluders are undone before
+// the receiver whose prefix end K(j) they reach, so S holds exactly the
+// receivers with K(j) > k.  A warp skips every entry that passed nowhere in
+// its 8x8 block in the forward (the pass masks it stored).  Per entry and
+// role a warp sums its 64 rays' (du, dv, dA, dB, dC, dgamma) with one
+// transposing butterfly and adds them to the Gaussian's accumulators.
 // ---------------------------------------------------------------------------
 struct ShadowBwdParams {
   const uint32_t* list;
@@ -472,6 +247,7 @@ struct ShadowBwdParams {
   const SplatRec* rrec;
   const uint32_t* order;
   const uint32_t* kbound;
+  const uint8_t* pass_mask;
   const float* light_final;
   const float* dT;   // by index
   const float* den;  // by index
@@ -483,40 +259,98 @@ struct ShadowBwdParams {
 
 constexpr int kBRecv = 128;
 constexpr int kBOcc = 512;
+constexpr int kBThreads = 128;
+constexpr float kLn2 = 0.6931471805599453f;
 
-__global__ void __launch_bounds__(256) k_shadow_bwd(ShadowBwdParams p) {
-  __shared__ SplatRec RR[kBRecv];
-  __shared__ uint32_t RK[kBRecv], RG[kBRecv];
-  __shared__ float RC[kBRecv], RT[kBRecv];
-  __shared__ SplatRec OR[kBOcc];
-  __shared__ uint32_t OG[kBOcc];
+struct ShadowBwdSmem {
+  float4 r0[kBRecv], r1[kBRecv];
+  uint32_t rk[kBRecv], rg[kBRecv];
+  float rc[kBRecv], rt[kBRecv];
+  float4 o0[kBOcc], o1[kBOcc];
+  uint32_t og[kBOcc];
+};
+
+// Sums v[0..7] over the warp with 9 shuffles.  Lane L ends with the total of
+// value ((L >> 4) & 1) * 4 + ((L >> 3) & 1) * 2 + ((L >> 2) & 1).
+__device__ __forceinline__ float warp_sum8(const float (&v)[8], int lane) {
+  const bool h16 = (lane & 16) != 0, h8 = (lane & 8) != 0, h4 = (lane & 4) != 0;
+  float w4[4], w2[2];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+    w4[i] = (h16 ? v[4 + i] : v[i]) + __shfl_xor_sync(0xffffffffu, h16 ? v[i] : v[4 + i], 16);
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+    w2[i] = (h8 ? w4[2 + i] : w4[i]) + __shfl_xor_sync(0xffffffffu, h8 ? w4[i] : w4[2 + i], 8);
+  float w = (h4 ? w2[1] : w2[0]) + __shfl_xor_sync(0xffffffffu, h4 ? w2[0] : w2[1], 4);
+  w += __shfl_xor_sync(0xffffffffu, w, 2);
+  w += __shfl_xor_sync(0xffffffffu, w, 1);
+  return w;
+}
+
+// add d/dpower2-weighted geometry terms of one pixel: power2 = a dx^2 + r dx dy + c dy^2
+// (log2 units, dx = pixel - centre); dpw = dL/dpower in natural units
+__device__ __forceinline__ void add_power_grad(const float4 e0, float r, float dx, float dy, float dpw, float (&g)[8]) {
+  g[0] += -(2.f * e0.z * dx + r * dy) * kLn2 * dpw;  // d/du = A dx + B dy
+  g[1] += -(2.f * e0.w * dy + r * dx) * kLn2 * dpw;  // d/dv = C dy + B dx
+  g[2] += -0.5f * dx * dx * dpw;                     // d/dA
+  g[3] += -dx * dy * dpw;                            // d/dB
+  g[4] += -0.5f * dy * dy * dpw;                     // d/dC
+}
+
+__device__ __forceinline__ void flush_grad(float* dst, const float (&g)[8], int lane) {
+  const float v = warp_sum8(g, lane);
+  const int idx = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
+  if ((lane & 3) == 0 && idx < 6 && v != 0.f) atomicAdd(dst + idx, v);
+}
+
+__global__ void __launch_bounds__(kBThreads, 8) k_shadow_bwd(ShadowBwdParams p) {
+  extern __shared__ float4 smem_raw[];
+  ShadowBwdSmem& S = *reinterpret_cast<ShadowBwdSmem*>(smem_raw);
   const int tile = blockIdx.x, tx = tile % p.gx, ty = tile / p.gx, t = threadIdx.x;
-  const int px = tx * kTile + (t & 15), py = ty * kTile + (t >> 4);
-  const bool inside = px < p.W && py < p.H;
-  const float fx = px + 0.5f, fy = py + 0.5f;
+  const int lane = t & 31, warp = t >> 5;
+  const uint32_t wbit = 1u << warp;
+  const int lxi = (warp & 1) * 8 + (lane & 7), lyi = (warp >> 1) * 8 + (lane >> 3);
+  const bool in0 = tx * kTile + lxi < p.W && ty * kTile + lyi < p.H;
+  const bool in1 = tx * kTile + lxi < p.W && ty * kTile + lyi + 4 < p.H;
+  const float kFar = 1.0e6f;  // off-image pixels never pass (same rule as the forward)
+  const float lx = lxi + 0.5f, ly0 = in0 ? lyi + 0.5f : kFar, ly1 = in1 ? lyi + 4.5f : kFar;
+  const float ox = (float)(tx * kTile), oy = (float)(ty * kTile);
+  const float omin = 1.f - p.amax;
   const uint32_t b = p.tile_start[tile], e = p.tile_start[tile + 1];
   if (b == e) return;
-  float A = inside ? p.light_final[(size_t)py * p.W + px] : 1.f;
-  float S = 0.f;
+  const int gxp = tx * kTile + lxi;
+  float A0 = in0 ? p.light_final[(size_t)(ty * kTile + lyi) * p.W + gxp] : 1.f;
+  float A1 = in1 ? p.light_final[(size_t)(ty * kTile + lyi + 4) * p.W + gxp] : 1.f;
+  float S0 = 0.f, S1 = 0.f;
   uint32_t kc = p.kbound[e - 1];
 
-  auto occlude = [&](const SplatRec& q, uint32_t g) {
-    float gv[6] = {0, 0, 0, 0, 0, 0};
-    bool c = false;
-    if (inside) {
-      const Eval ev = eval_rec(q, fx, fy, p.amax);
-      if (ev.pass) {
-        const float inv = 1.f / (1.f - ev.alpha);
-        const float dalpha = -S * inv;
-        A *= inv;
-        if (!ev.clamped && dalpha != 0.f) {
-          c = true;
-          gv[5] = dalpha * ev.beta;
-          power_grad(q, ev, dalpha * ev.alpha, gv);
+  // undo occluder i of the window at both rays; accumulate its gradient
+  auto occlude_bwd = [&](int i) {
+    const float4 o1 = S.o1[i];
+    if (!(__float_as_uint(o1.w) & wbit)) return;
+    const float4 o0 = S.o0[i];
+    float pw0, pw1;
+    powers2(o0, o1.x, lx, ly0, ly1, pw0, pw1);
+    float g[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    const float pws[2] = {pw0, pw1}, lys[2] = {ly0, ly1};
+    float* As[2] = {&A0, &A1};
+    const float Ss[2] = {S0, S1};
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const float pw = pws[q];
+      if (pw >= o1.y && pw <= 0.f) {
+        const float beta = ex2(pw), ga = o1.z * beta;
+        const float f = fmaxf(omin, fmaf(-o1.z, beta, 1.f));
+        const float inv = __frcp_rn(f);
+        *As[q] *= inv;
+        if (ga < p.amax) {  // alpha = gamma beta (not clamped)
+          const float dalpha = -Ss[q] * inv;
+          g[5] += dalpha * beta;  // d/dgamma
+          add_power_grad(o0, o1.x, lx - o0.x, lys[q] - o0.y, dalpha * ga, g);
         }
       }
     }
-    warp_atomic<6>(p.light_geom + (size_t)kGeom * g, gv, c);
+    flush_grad(p.light_geom + (size_t)kGeom * S.og[i], g, lane);
   };
 
   for (uint32_t re = e; re > b;) {
@@ -526,62 +360,66 @@ __global__ void __launch_bounds__(256) k_shadow_bwd(ShadowBwdParams p) {
     if (t < rc) {
       const uint32_t rank = p.list[rs + t];
       const uint32_t g = p.order[rank];
-      RR[t] = p.rrec[rank];
-      RK[t] = p.kbound[rs + t];
-      RG[t] = g;
+      make_entry(p.rrec[rank], ox, oy, S.r0[t], S.r1[t]);
+      S.r1[t].w = __uint_as_float((uint32_t)p.pass_mask[rs + t]);
+      S.rk[t] = p.kbound[rs + t];
+      S.rg[t] = g;
       const float den = p.den[g];
-      RC[t] = den > 0.f ? p.dT[g] / den : 0.f;
-      RT[t] = p.T[g];
+      S.rc[t] = den > 0.f ? p.dT[g] / den : 0.f;
+      S.rt[t] = p.T[g];
     }
     __syncthreads();
     int jj = rc - 1;
     while (jj >= 0) {
-      const uint32_t kfirst = RK[0];
+      const uint32_t kfirst = S.rk[0];
       const uint32_t kt = kc > kfirst + kBOcc ? kc - kBOcc : kfirst;
       __syncthreads();
-      for (uint32_t i = t; i < kc - kt; i += blockDim.x) {
+      for (uint32_t i = t; i < kc - kt; i += kBThreads) {
         const uint32_t rank = p.list[kt + i];
-        OR[i] = p.rrec[rank];
-        OG[i] = p.order[rank];
+        make_entry(p.rrec[rank], ox, oy, S.o0[i], S.o1[i]);
+        S.o1[i].w = __uint_as_float((uint32_t)p.pass_mask[kt + i]);
+        S.og[i] = p.order[rank];
       }
       __syncthreads();
       for (; jj >= 0; --jj) {
-        const uint32_t kend = RK[jj];
+        const uint32_t kend = S.rk[jj];
         if (kend < kt) break;
-        for (; kc > kend; --kc) occlude(OR[kc - 1 - kt], OG[kc - 1 - kt]);
-        // receiver jj
-        float gv[6] = {0, 0, 0, 0, 0, 0};
-        bool c = false;
-        if (inside) {
-          const SplatRec q = RR[jj];
-          const Eval ev = eval_rec(q, fx, fy, p.amax);
-          if (ev.pass) {
-            const float coef = RC[jj];
-            S = fmaf(coef * ev.beta, A, S);
-            const float dbeta = coef * (A - RT[jj]);
-            if (dbeta != 0.f) {
-              c = true;
-              power_grad(q, ev, dbeta * ev.beta, gv);
-            }
-          }
+        for (; kc > kend; --kc) occlude_bwd((int)(kc - 1 - kt));
+        const float4 r1 = S.r1[jj];
+        if (!(__float_as_uint(r1.w) & wbit)) continue;
+        const float4 r0 = S.r0[jj];
+        float pw0, pw1;
+        powers2(r0, r1.x, lx, ly0, ly1, pw0, pw1);
+        const float coef = S.rc[jj], Tj = S.rt[jj];
+        float g[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        if (pw0 >= r1.y && pw0 <= 0.f) {
+          const float beta = ex2(pw0);
+          S0 = fmaf(coef * beta, A0, S0);
+          add_power_grad(r0, r1.x, lx - r0.x, ly0 - r0.y, coef * (A0 - Tj) * beta, g);
         }
-        warp_atomic<6>(p.light_geom + (size_t)kGeom * RG[jj], gv, c);
+        if (pw1 >= r1.y && pw1 <= 0.f) {
+          const float beta = ex2(pw1);
+          S1 = fmaf(coef * beta, A1, S1);
+          add_power_grad(r0, r1.x, lx - r0.x, ly1 - r0.y, coef * (A1 - Tj) * beta, g);
+        }
+        flush_grad(p.light_geom + (size_t)kGeom * S.rg[jj], g, lane);
       }
-      for (; kc > kt; --kc) occlude(OR[kc - 1 - kt], OG[kc - 1 - kt]);
+      for (; kc > kt; --kc) occlude_bwd((int)(kc - 1 - kt));
     }
     re = rs;
   }
-  // occluders before every receiver's prefix end: S already holds all receivers
+  // occluders below every receiver's prefix end: S holds all receivers
   while (kc > b) {
     const uint32_t kt = kc > b + kBOcc ? kc - kBOcc : b;
     __syncthreads();
-    for (uint32_t i = t; i < kc - kt; i += blockDim.x) {
+    for (uint32_t i = t; i < kc - kt; i += kBThreads) {
       const uint32_t rank = p.list[kt + i];
-      OR[i] = p.rrec[rank];
-      OG[i] = p.order[rank];
+      make_entry(p.rrec[rank], ox, oy, S.o0[i], S.o1[i]);
+      S.o1[i].w = __uint_as_float((uint32_t)p.pass_mask[kt + i]);
+      S.og[i] = p.order[rank];
     }
     __syncthreads();
-    for (; kc > kt; --kc) occlude(OR[kc - 1 - kt], OG[kc - 1 - kt]);
+    for (; kc > kt; --kc) occlude_bwd((int)(kc - 1 - kt));
   }
 }
 
@@ -901,7 +739,7 @@ gs3_status run_backward(const FrameArgs& f, const float* dimg, void* bws, size_t
   float* color = reinterpret_cast<float*>(B + bp.color);
   float* dT = reinterpret_cast<float*>(B + bp.dT);
   float* mlp_in = reinterpret_cast<float*>(B + bp.mlp_in);
-  cudaMemsetAsync(B, 0, bp.wpart[0], s);  // per-Gaussian accumulators start at zero
+  cudaMemsetAsync(B, 0, bp.mlp_scratch, s);  // per-Gaussian accumulators start at zero
   unsigned char* ws = f.ws;
   const Workspace& L = *f.L;
   const int fin = (L.ntiles <= 256 ? 1 : 2) & 1;
@@ -927,7 +765,6 @@ gs3_status run_backward(const FrameArgs& f, const float* dimg, void* bws, size_t
   // K8b: Psi and Phi, then the weight gradients in fixed block order
   for (int which = 1; which >= 0; --which) {
     const MlpDev& m = which == 0 ? f.sc.phi : f.sc.psi;
-    float* wpart = reinterpret_cast<float*>(B + bp.wpart[which]);
     float* wred = reinterpret_cast<float*>(B + bp.wred[which]);
     const bool identity = (f.opts.ablate & (which == 0 ? GS3_ABLATE_PHI : GS3_ABLATE_PSI)) != 0;
     float* dw = which == 0 ? out.phi_w : out.psi_w;
@@ -940,23 +777,18 @@ gs3_status run_backward(const FrameArgs& f, const float* dimg, void* bws, size_t
         count_launch();
       }
     } else {
-      MlpBwdParams p;
-      p.net = m;
-      p.n = n;
-      p.which = which;
-      p.mean_op = f.sc.mean_op;
-      p.latent = f.sc.latent;
-      p.T = at<float>(ws, L.T);
-      for (int i = 0; i < 3; ++i) { p.light_pos[i] = f.light.pos[i]; p.cam_pos[i] = f.cam.pos[i]; }
-      p.color = color;
-      p.dT = dT;
-      p.mlp_in = mlp_in;
-      p.wpart = wpart;
-      const size_t smem = 4 * ((size_t)(m.n_hidden + 1 + 2) * kMlpRows * (kMaxW + 1) + kMlpRows * 4);
-      cudaFuncSetAttribute(k_mlp_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      k_mlp_bwd<<<kBwdBlocksMlp, 128, smem, s>>>(p);
-      k_reduce_parts<<<(int)((np + 255) / 256), 256, 0, s>>>(wpart, np, kBwdBlocksMlp, wred);
-      count_launch(2);
+      MlpArgs a;
+      a.net = m;
+      a.n = n;
+      a.which = which;
+      a.mean_op = f.sc.mean_op;
+      a.latent = f.sc.latent;
+      a.T = at<float>(ws, L.T);
+      for (int i = 0; i < 3; ++i) { a.light_pos[i] = f.light.pos[i]; a.cam_pos[i] = f.cam.pos[i]; }
+      a.color = color;
+      a.dT = dT;
+      a.mlp_in = mlp_in;
+      run_mlp_backward(a, B + bp.mlp_scratch, wred, s);
     }
     k_split_params<<<64, 256, 0, s>>>(wred, m.in_dim, m.width, m.n_hidden, m.out_dim, dw, db);
     count_launch();
@@ -969,6 +801,7 @@ gs3_status run_backward(const FrameArgs& f, const float* dimg, void* bws, size_t
     p.rrec = at<SplatRec>(ws, L.sp[1].rrec);
     p.order = at<uint32_t>(ws, L.sp[1].sv[1]);
     p.kbound = at<uint32_t>(ws, L.sp[1].tv[1 - fin]);
+    p.pass_mask = reinterpret_cast<const uint8_t*>(at<float>(ws, L.sp[1].tk[1 - fin]));
     p.light_final = at<float>(ws, L.light_final);
     p.dT = dT;
     p.den = at<float>(ws, L.shadow_den);
@@ -976,7 +809,13 @@ gs3_status run_backward(const FrameArgs& f, const float* dimg, void* bws, size_t
     p.light_geom = light_geom;
     p.W = L.width; p.H = L.height; p.gx = L.gx;
     p.amax = f.opts.alpha_max;
-    k_shadow_bwd<<<L.ntiles, 256, 0, s>>>(p);
+    static bool configured = false;
+    if (!configured) {
+      cudaFuncSetAttribute(k_shadow_bwd, cudaFuncAttributePreferredSharedMemoryCarveout,
+                           (int)cudaSharedmemCarveoutMaxShared);
+      configured = true;
+    }
+    k_shadow_bwd<<<L.ntiles, kBThreads, sizeof(ShadowBwdSmem), s>>>(p);
     count_launch();
   }
   // K1b

@@ -5,6 +5,7 @@
 // pixel, and stream the tile's depth-ordered list through shared memory in
 // batches of 256 records.
 #include "gs3_internal.cuh"
+#include "splat_eval.cuh"
 
 namespace gs3 {
 namespace {
@@ -82,60 +83,6 @@ struct ShadowSmem {
   float4 o0[kOccWin], o1[kOccWin];
   float2 red[4][kRecv];
 };
-
-// Bit w set when the splat's alpha >= alpha_min box can reach warp w's 8x8
-// block (tile-relative centre (ux, vy), half extents hx, hy).
-__device__ __forceinline__ uint32_t warp_mask8(float ux, float vy, float hx, float hy) {
-  if (!(hx >= 0.f)) return 0u;
-  uint32_t m = 0u;
-#pragma unroll
-  for (int w = 0; w < 4; ++w) {
-    const float x0 = (w & 1) * 8 + 0.5f, y0 = (w >> 1) * 8 + 0.5f;
-    const bool hit = (ux + hx >= x0) && (ux - hx <= x0 + 7.f) && (vy + hy >= y0) && (vy - hy <= y0 + 7.f);
-    m |= hit ? (1u << w) : 0u;
-  }
-  return m;
-}
-
-// Entries carry the conic pre-multiplied by log2(e), so beta = 2^power2 with
-//   power2 = a dx^2 + r dx dy + c dy^2 = dx (a dx) + dy (c dy + r dx),
-//   a = -A/2 log2e, r = -B log2e, c = -C/2 log2e, (dx, dy) = pixel - centre.
-// e0 = (ux, vy, a, c): centre relative to the tile origin (ox, oy);
-// e1 = (r, pthr log2e, gamma, warp mask bits).
-constexpr float kLog2e = 1.4426950408889634f;
-
-__device__ __forceinline__ float ex2(float x) {
-  float y;
-  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
-}
-
-__device__ __forceinline__ void make_entry(const SplatRec& q, float ox, float oy, float4& e0, float4& e1) {
-  const float ux = (q.a.x - ox) + q.b.w, vy = (q.a.y - oy) + q.c.x;
-  const uint32_t m = warp_mask8(ux, vy, q.c.y, q.c.z);
-  e0 = make_float4(ux, vy, -0.5f * kLog2e * q.b.x, -0.5f * kLog2e * q.b.z);
-  e1 = make_float4(-kLog2e * q.b.y, kLog2e * q.c.w, q.a.z, __uint_as_float(m));
-}
-
-// power2 at the thread's two pixels (lx, ly0), (lx, ly1): the dx terms are shared
-__device__ __forceinline__ void powers2(const float4 e0, float r, float lx, float ly0, float ly1, float& p0,
-                                        float& p1) {
-  const float dx = lx - e0.x;
-  const float sx = (e0.z * dx) * dx, v = r * dx;
-  const float dy0 = ly0 - e0.y, dy1 = ly1 - e0.y;
-  p0 = fmaf(dy0, fmaf(e0.w, dy0, v), sx);
-  p1 = fmaf(dy1, fmaf(e0.w, dy1, v), sx);
-}
-
-// one occluder on both rays: A *= 1 - min(amax, gamma beta) where it passes,
-// written as max(1 - amax, 1 - gamma beta)
-__device__ __forceinline__ void occlude(const float4 o0, const float4 o1, float lx, float ly0, float ly1,
-                                        float omin, float& A0, float& A1) {
-  float p0, p1;
-  powers2(o0, o1.x, lx, ly0, ly1, p0, p1);
-  if (p0 >= o1.y && p0 <= 0.f) A0 *= fmaxf(omin, fmaf(-o1.z, ex2(p0), 1.f));
-  if (p1 >= o1.y && p1 <= 0.f) A1 *= fmaxf(omin, fmaf(-o1.z, ex2(p1), 1.f));
-}
 
 __global__ void __launch_bounds__(kShadowThreads, 8) k_shadow(ShadowParams p) {
   extern __shared__ float4 smem_raw[];

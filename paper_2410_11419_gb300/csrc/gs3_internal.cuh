@@ -104,6 +104,21 @@ size_t loss_scratch_bytes(int W, int H);
 gs3_status run_loss(const float* img, const float* tgt, int W, int H, float lambda, float* loss, float* dimg,
                     void* scratch, cudaStream_t s);
 size_t backward_workspace_bytes(int n, const MlpDev& phi, const MlpDev& psi);
+// MLP backward (mlp_bwd.cu): one network's parameter gradients into wred
+// (its parameter order) and its input gradients into mlp_in / dT
+struct MlpArgs {
+  MlpDev net;
+  int n, which;  // 0 Phi, 1 Psi
+  const float4* mean_op;
+  const float4* latent;
+  const float* T;
+  float light_pos[3], cam_pos[3];
+  const float* color;  // [N][8]: dT' at 3, dres at 4..6
+  float* dT;           // Phi: d/d(input T)
+  float* mlp_in;       // [N][24]
+};
+size_t mlp_bwd_scratch_bytes(int n, const MlpDev& m);
+void run_mlp_backward(const MlpArgs& a, void* scratch, float* wred, cudaStream_t s);
 gs3_status run_backward(const FrameArgs& f, const float* dimg, void* bws, size_t bws_bytes,
                         const gs3_grads& out, cudaStream_t s);
 
