@@ -89,9 +89,15 @@ typedef struct {
     int width, height;
 } go_camera;
 
+/* type 0: point light at pos (Sec. 4.2); type 1: directional light from the
+ * scene towards dir (Sec. 4.5), orthographic light view of half-width
+ * extent (world units) centred at the options' target. */
 typedef struct {
     float pos[3];
     float intensity;
+    int type;
+    float dir[3];
+    float extent;
 } go_light;
 
 typedef struct {
@@ -106,6 +112,7 @@ typedef struct {
 typedef struct {
     int n, width, height, gx, gy, ntiles;
     float light_R[9], light_t[3];
+    float light_ortho; /* orthographic light view: pixels per world unit (0: perspective) */
     /* per splat s = 0 camera, 1 light */
     uint32_t *key[2];      /* FP32 depth (camera) / distance (light) bits, 0xFFFFFFFF if culled */
     int32_t *rect[2];      /* x0, y0, x1, y1 tile rectangle (inclusive); x0 = -1 if culled */
@@ -181,6 +188,25 @@ void go_light_view(const float pL[3], const float target[3], float R[9], float t
         t[i] = -(R[3 * i] * e.x + R[3 * i + 1] * e.y + R[3 * i + 2] * e.z);
 }
 
+/* Light view of either kind.  Directional (Sec. 4.5): the perspective
+ * shadow camera is replaced by an orthographic one looking along -dir at the
+ * target from the eye e = target + dir (4 extent), with pixel scale
+ * s = (min(W, H) / 2) / extent (so the view's half-width is extent) and the
+ * depth along the view axis as the sorting distance.  FP32, one rounding per
+ * operation.  Returns s (0 for a point light). */
+float go_light_view_any(const go_light *L, const float target[3], int W, int H, float R[9], float t[3])
+{
+    if (L->type != 1) {
+        go_light_view(L->pos, target, R, t);
+        return 0.0f;
+    }
+    float reach = 4.0f * L->extent;
+    float e[3] = {target[0] + L->dir[0] * reach, target[1] + L->dir[1] * reach, target[2] + L->dir[2] * reach};
+    go_light_view(e, target, R, t);
+    float half = 0.5f * (float)(W < H ? W : H);
+    return half / L->extent;
+}
+
 typedef struct { uint32_t key; int x0, y0, x1, y1; float u, v; } keyrec;
 
 static uint32_t f32_bits(float f) { uint32_t u; memcpy(&u, &f, 4); return u; }
@@ -188,7 +214,7 @@ static uint32_t f32_bits(float f) { uint32_t u; memcpy(&u, &f, 4); return u; }
 /* One Gaussian through the FP32 recipe.  Returns 0 when culled. */
 static int key_recipe(const float m[3], const float s[3], const float q[4],
                       const float R[9], const float t[3], float fx, float fy, float cx, float cy,
-                      int W, int H, const go_opts *o, const float *pL, keyrec *out)
+                      int W, int H, const go_opts *o, const float *pL, float ortho, keyrec *out)
 {
     out->key = 0xFFFFFFFFu; out->x0 = -1; out->y0 = -1; out->x1 = -2; out->y1 = -2;
     out->u = 0.0f; out->v = 0.0f;
@@ -196,11 +222,22 @@ static int key_recipe(const float m[3], const float s[3], const float q[4],
     float ty = R[3] * m[0] + R[4] * m[1] + R[5] * m[2] + t[1];
     float tz = R[6] * m[0] + R[7] * m[1] + R[8] * m[2] + t[2];
     if (!(tz > o->near_z)) return 0;
-    float xz = tx / tz, yz = ty / tz;
-    float limx = o->frustum * ((0.5f * (float)W) / fx);
-    float limy = o->frustum * ((0.5f * (float)H) / fy);
-    if (xz < -limx || xz > limx || yz < -limy || yz > limy) return 0;
-    float u = fx * xz + cx, v = fy * yz + cy;
+    float xz = 0.0f, yz = 0.0f, u, v;
+    if (ortho > 0.0f) { /* orthographic: u = s x + cx, v = s y + cy */
+        float limx = o->frustum * ((0.5f * (float)W) / ortho);
+        float limy = o->frustum * ((0.5f * (float)H) / ortho);
+        if (tx < -limx || tx > limx || ty < -limy || ty > limy) return 0;
+        u = ortho * tx + cx;
+        v = ortho * ty + cy;
+    } else {
+        xz = tx / tz;
+        yz = ty / tz;
+        float limx = o->frustum * ((0.5f * (float)W) / fx);
+        float limy = o->frustum * ((0.5f * (float)H) / fy);
+        if (xz < -limx || xz > limx || yz < -limy || yz > limy) return 0;
+        u = fx * xz + cx;
+        v = fy * yz + cy;
+    }
 
     float n2 = q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3];
     if (!(n2 > 0.0f)) return 0;
@@ -223,12 +260,19 @@ static int key_recipe(const float m[3], const float s[3], const float q[4],
     for (int i = 0; i < 3; ++i)
         for (int j = 0; j < 3; ++j)
             Sg[3 * i + j] = M[3 * i] * M[3 * j] + M[3 * i + 1] * M[3 * j + 1] + M[3 * i + 2] * M[3 * j + 2];
-    float j00 = fx / tz, j02 = -((fx * xz) / tz);
-    float j11 = fy / tz, j12 = -((fy * yz) / tz);
     float T0[3], T1[3];
-    for (int k = 0; k < 3; ++k) {
-        T0[k] = j00 * R[k] + j02 * R[6 + k];
-        T1[k] = j11 * R[3 + k] + j12 * R[6 + k];
+    if (ortho > 0.0f) { /* J = [[s, 0, 0], [0, s, 0]] */
+        for (int k = 0; k < 3; ++k) {
+            T0[k] = ortho * R[k];
+            T1[k] = ortho * R[3 + k];
+        }
+    } else {
+        float j00 = fx / tz, j02 = -((fx * xz) / tz);
+        float j11 = fy / tz, j12 = -((fy * yz) / tz);
+        for (int k = 0; k < 3; ++k) {
+            T0[k] = j00 * R[k] + j02 * R[6 + k];
+            T1[k] = j11 * R[3 + k] + j12 * R[6 + k];
+        }
     }
     float U0[3], U1[3];
     for (int k = 0; k < 3; ++k) {
@@ -254,11 +298,11 @@ static int key_recipe(const float m[3], const float s[3], const float q[4],
     out->y0 = (int)fmaxf(fy0, 0.0f);
     out->y1 = (int)fminf(fy1, (float)(gy - 1));
     out->u = u; out->v = v;
-    if (pL) {
+    if (pL && !(ortho > 0.0f)) {
         float dx = m[0] - pL[0], dy = m[1] - pL[1], dz = m[2] - pL[2];
         out->key = f32_bits(sqrtf(dx * dx + dy * dy + dz * dz));
     } else {
-        out->key = f32_bits(tz);
+        out->key = f32_bits(tz); /* camera depth, or depth along an orthographic light view */
     }
     return 1;
 }
@@ -332,9 +376,10 @@ static void shade_one(const go_scene *sc, int g, const go_camera *cam, const go_
                       const go_opts *o, double rgb[3], d3 *wi_out, d3 *wo_out)
 {
     d3 mu = {sc->mean_op[4 * g], sc->mean_op[4 * g + 1], sc->mean_op[4 * g + 2]};
-    d3 pl = {L->pos[0], L->pos[1], L->pos[2]};
     d3 pc = {cam->pos[0], cam->pos[1], cam->pos[2]};
-    d3 tol = d3_sub(pl, mu);
+    int directional = L->type == 1;
+    d3 tol = directional ? (d3){L->dir[0], L->dir[1], L->dir[2]}
+                         : d3_sub((d3){L->pos[0], L->pos[1], L->pos[2]}, mu);
     double dist2 = d3_dot(tol, tol);
     d3 wi = d3_unit(tol);
     d3 wo = d3_unit(d3_sub(pc, mu));
@@ -355,7 +400,8 @@ static void shade_one(const go_scene *sc, int g, const go_camera *cam, const go_
             for (int c = 0; c < 3; ++c) fs[c] += sc->lobe_amp[4 * li + c] * G;
         }
     }
-    double E = o->falloff ? L->intensity / dist2 : L->intensity;
+    /* a directional light's irradiance does not fall off (Sec. 4.5) */
+    double E = (o->falloff && !directional) ? L->intensity / dist2 : L->intensity;
     for (int c = 0; c < 3; ++c)
         rgb[c] = E * (sc->albedo_d[4 * g + c] * fd + sc->albedo_s[4 * g + c] * fs[c]);
 }
@@ -363,7 +409,7 @@ static void shade_one(const go_scene *sc, int g, const go_camera *cam, const go_
 /* FP64 EWA projection (same conventions as the FP32 recipe, no culling). */
 static void project_f64(const float mf[3], const float sf[3], const float qf[4],
                         const float Rf[9], const float tf[3], double fx, double fy, double cx,
-                        double cy, double lowpass, double uv[2], double conic[3])
+                        double cy, double lowpass, double ortho, double uv[2], double conic[3])
 {
     double R[9], t[3], m[3] = {mf[0], mf[1], mf[2]}, s[3] = {sf[0], sf[1], sf[2]};
     for (int i = 0; i < 9; ++i) R[i] = Rf[i];
@@ -371,8 +417,13 @@ static void project_f64(const float mf[3], const float sf[3], const float qf[4],
     double tx = R[0] * m[0] + R[1] * m[1] + R[2] * m[2] + t[0];
     double ty = R[3] * m[0] + R[4] * m[1] + R[5] * m[2] + t[1];
     double tz = R[6] * m[0] + R[7] * m[1] + R[8] * m[2] + t[2];
-    uv[0] = fx * tx / tz + cx;
-    uv[1] = fy * ty / tz + cy;
+    if (ortho > 0.0) {
+        uv[0] = ortho * tx + cx;
+        uv[1] = ortho * ty + cy;
+    } else {
+        uv[0] = fx * tx / tz + cx;
+        uv[1] = fy * ty / tz + cy;
+    }
     double Rq[9];
     quat_to_mat(qf, Rq);
     double Sg[9];
@@ -383,6 +434,10 @@ static void project_f64(const float mf[3], const float sf[3], const float qf[4],
             Sg[3 * i + j] = acc;
         }
     double J[6] = {fx / tz, 0.0, -fx * tx / (tz * tz), 0.0, fy / tz, -fy * ty / (tz * tz)};
+    if (ortho > 0.0) {
+        J[0] = ortho; J[2] = 0.0;
+        J[4] = ortho; J[5] = 0.0;
+    }
     double T[6];
     for (int i = 0; i < 2; ++i)
         for (int k = 0; k < 3; ++k)
@@ -754,7 +809,7 @@ go_frame *go_render(const go_scene *sc, const go_camera *cam, const go_light *L,
     f->gx = (cam->width + o->tile - 1) / o->tile;
     f->gy = (cam->height + o->tile - 1) / o->tile;
     f->ntiles = f->gx * f->gy;
-    go_light_view(L->pos, o->target, f->light_R, f->light_t);
+    f->light_ortho = go_light_view_any(L, o->target, cam->width, cam->height, f->light_R, f->light_t);
     for (int s = 0; s < 2; ++s) {
         f->key[s] = malloc(sizeof(uint32_t) * n);
         f->rect[s] = malloc(sizeof(int32_t) * 4 * n);
@@ -789,8 +844,9 @@ go_frame *go_render(const go_scene *sc, const go_camera *cam, const go_light *L,
         for (int sp = 0; sp < 2; ++sp) {
             keyrec kr;
             const float *R = sp ? f->light_R : cam->R, *t = sp ? f->light_t : cam->t;
+            const float ortho = sp ? f->light_ortho : 0.0f;
             int vis = key_recipe(m, s, q, R, t, cam->fx, cam->fy, cam->cx, cam->cy, cam->width,
-                                 cam->height, o, sp ? L->pos : NULL, &kr);
+                                 cam->height, o, sp ? L->pos : NULL, ortho, &kr);
             f->key[sp][g] = kr.key;
             f->rect[sp][4 * g] = vis ? kr.x0 : -1;
             f->rect[sp][4 * g + 1] = vis ? kr.y0 : -1;
@@ -798,7 +854,7 @@ go_frame *go_render(const go_scene *sc, const go_camera *cam, const go_light *L,
             f->rect[sp][4 * g + 3] = vis ? kr.y1 : -2;
             f->uv_f32[sp][2 * g] = kr.u;
             f->uv_f32[sp][2 * g + 1] = kr.v;
-            project_f64(m, s, q, R, t, cam->fx, cam->fy, cam->cx, cam->cy, o->lowpass,
+            project_f64(m, s, q, R, t, cam->fx, cam->fy, cam->cx, cam->cy, o->lowpass, ortho,
                         f->uv[sp] + 2 * g, f->conic[sp] + 3 * g);
         }
         shade_one(sc, g, cam, L, o, f->shade + 3 * g, wi + g, wo + g);
@@ -890,10 +946,11 @@ void go_shade(const go_scene *sc, int g, const go_camera *cam, const go_light *L
 /* FP32 recipe of one Gaussian (for pins on the key recipe). */
 int go_key_recipe(const float m[3], const float s[3], const float q[4], const float R[9],
                   const float t[3], float fx, float fy, float cx, float cy, int W, int H,
-                  const go_opts *o, const float *pL, uint32_t *key, int32_t rect[4], float uv[2])
+                  const go_opts *o, const float *pL, float ortho, uint32_t *key, int32_t rect[4],
+                  float uv[2])
 {
     keyrec kr;
-    int vis = key_recipe(m, s, q, R, t, fx, fy, cx, cy, W, H, o, pL, &kr);
+    int vis = key_recipe(m, s, q, R, t, fx, fy, cx, cy, W, H, o, pL, ortho, &kr);
     *key = kr.key;
     rect[0] = kr.x0; rect[1] = kr.y0; rect[2] = kr.x1; rect[3] = kr.y1;
     uv[0] = kr.u; uv[1] = kr.v;
@@ -903,9 +960,9 @@ int go_key_recipe(const float m[3], const float s[3], const float q[4], const fl
 /* FP64 projection of one Gaussian (for pins). */
 void go_project(const float m[3], const float s[3], const float q[4], const float R[9],
                 const float t[3], double fx, double fy, double cx, double cy, double lowpass,
-                double uv[2], double conic[3])
+                double ortho, double uv[2], double conic[3])
 {
-    project_f64(m, s, q, R, t, fx, fy, cx, cy, lowpass, uv, conic);
+    project_f64(m, s, q, R, t, fx, fy, cx, cy, lowpass, ortho, uv, conic);
 }
 
 /* Positional encoding of one 3-vector (for pins). */

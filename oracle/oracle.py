@@ -54,7 +54,8 @@ class _Camera(C.Structure):
 
 
 class _Light(C.Structure):
-    _fields_ = [("pos", C.c_float * 3), ("intensity", C.c_float)]
+    _fields_ = [("pos", C.c_float * 3), ("intensity", C.c_float), ("type", C.c_int),
+                ("dir", C.c_float * 3), ("extent", C.c_float)]
 
 
 class _Opts(C.Structure):
@@ -74,7 +75,7 @@ _D = C.POINTER(C.c_double)
 class _Frame(C.Structure):
     _fields_ = [("n", C.c_int), ("width", C.c_int), ("height", C.c_int), ("gx", C.c_int),
                 ("gy", C.c_int), ("ntiles", C.c_int), ("light_R", C.c_float * 9),
-                ("light_t", C.c_float * 3),
+                ("light_t", C.c_float * 3), ("light_ortho", C.c_float),
                 ("key", _U32 * 2), ("rect", _I32 * 2), ("uv_f32", _FP * 2), ("uv", _D * 2),
                 ("conic", _D * 2), ("opacity", _D), ("P", C.c_uint32 * 2),
                 ("tile_start", _U32 * 2), ("list", _U32 * 2),
@@ -107,10 +108,12 @@ def lib():
                                   C.POINTER(_Light), C.POINTER(_Opts), _D]
         _lib.go_key_recipe.restype = C.c_int
         _lib.go_key_recipe.argtypes = [_FP, _FP, _FP, _FP, _FP, C.c_float, C.c_float, C.c_float,
-                                       C.c_float, C.c_int, C.c_int, C.POINTER(_Opts), _FP, _U32,
-                                       _I32, _FP]
+                                       C.c_float, C.c_int, C.c_int, C.POINTER(_Opts), _FP, C.c_float,
+                                       _U32, _I32, _FP]
         _lib.go_project.argtypes = [_FP, _FP, _FP, _FP, _FP, C.c_double, C.c_double, C.c_double,
-                                    C.c_double, C.c_double, _D, _D]
+                                    C.c_double, C.c_double, C.c_double, _D, _D]
+        _lib.go_light_view_any.restype = C.c_float
+        _lib.go_light_view_any.argtypes = [C.POINTER(_Light), _FP, C.c_int, C.c_int, _FP, _FP]
         _lib.go_pos_enc.restype = C.c_int
         _lib.go_pos_enc.argtypes = [_D, _D]
         _lib.go_light_view.argtypes = [_FP, _FP, _FP, _FP]
@@ -188,8 +191,11 @@ def c_camera(cam) -> _Camera:
 
 
 def c_light(light) -> _Light:
+    d = getattr(light, "dir", None)
+    d = (0.0, 0.0, 0.0) if d is None else np.asarray(d, dtype=np.float32).tolist()
     return _Light((C.c_float * 3)(*np.asarray(light.pos, dtype=np.float32).tolist()),
-                  float(light.intensity))
+                  float(light.intensity), int(getattr(light, "type", 0)), (C.c_float * 3)(*d),
+                  float(getattr(light, "extent", 0.0)))
 
 
 def _arr(ptr, n, dtype):
@@ -209,7 +215,8 @@ def render(scene, cam, light, opts: Opts | None = None) -> dict:
     n, W, H, nt = f.n, f.width, f.height, f.ntiles
     out = {"n": n, "width": W, "height": H, "gx": f.gx, "gy": f.gy, "ntiles": nt,
            "light_R": np.array(f.light_R[:], dtype=np.float32).reshape(3, 3),
-           "light_t": np.array(f.light_t[:], dtype=np.float32)}
+           "light_t": np.array(f.light_t[:], dtype=np.float32),
+           "light_ortho": float(f.light_ortho)}
     for s, nm in ((0, "cam"), (1, "light")):
         P = int(f.P[s])
         out[f"{nm}_key"] = _arr(f.key[s], n, np.uint32)
@@ -276,7 +283,8 @@ def shade(scene, g: int, cam, light, opts: Opts | None = None) -> np.ndarray:
     return out
 
 
-def key_recipe(m, s, q, R, t, fx, fy, cx, cy, W, H, opts: Opts | None = None, light_pos=None):
+def key_recipe(m, s, q, R, t, fx, fy, cx, cy, W, H, opts: Opts | None = None, light_pos=None,
+               ortho: float = 0.0):
     f32 = lambda a: np.ascontiguousarray(a, dtype=np.float32)
     m, s, q, R, t = f32(m), f32(s), f32(q), f32(np.asarray(R).reshape(-1)), f32(t)
     key = C.c_uint32()
@@ -285,18 +293,18 @@ def key_recipe(m, s, q, R, t, fx, fy, cx, cy, W, H, opts: Opts | None = None, li
     pl = _fp(f32(light_pos)) if light_pos is not None else None
     keep = [light_pos]
     vis = lib().go_key_recipe(_fp(m), _fp(s), _fp(q), _fp(R), _fp(t), fx, fy, cx, cy, W, H,
-                              C.byref((opts or Opts()).c()), pl, C.byref(key),
+                              C.byref((opts or Opts()).c()), pl, ortho, C.byref(key),
                               rect.ctypes.data_as(_I32), _fp(uv))
     del keep
     return bool(vis), int(key.value), rect, uv
 
 
-def project(m, s, q, R, t, fx, fy, cx, cy, lowpass=0.3):
+def project(m, s, q, R, t, fx, fy, cx, cy, lowpass=0.3, ortho=0.0):
     f32 = lambda a: np.ascontiguousarray(a, dtype=np.float32)
     uv = np.zeros(2)
     con = np.zeros(3)
     lib().go_project(_fp(f32(m)), _fp(f32(s)), _fp(f32(q)), _fp(f32(np.asarray(R).reshape(-1))),
-                     _fp(f32(t)), fx, fy, cx, cy, lowpass, uv.ctypes.data_as(_D),
+                     _fp(f32(t)), fx, fy, cx, cy, lowpass, ortho, uv.ctypes.data_as(_D),
                      con.ctypes.data_as(_D))
     return uv, con
 
@@ -306,6 +314,27 @@ def pos_enc(v) -> np.ndarray:
     out = np.zeros(27)
     lib().go_pos_enc(v.ctypes.data_as(_D), out.ctypes.data_as(_D))
     return out
+
+
+def environment(scene, cam, lights, weights, opts: Opts | None = None) -> np.ndarray:
+    """Sec. 4.5: an environment light as the linear combination
+    sum_l w_l render(directional light l) of whole rendered images."""
+    out = None
+    for L, w in zip(lights, weights):
+        img = render(scene, cam, L, opts)["img"]
+        out = float(w) * img if out is None else out + float(w) * img
+    return out
+
+
+def light_view_any(light, width, height, target=(0.0, 0.0, 0.0)):
+    """(R, t, s) of the light camera: perspective at a point light (s = 0) or
+    orthographic along a directional light (s = pixels per world unit)."""
+    R = np.zeros(9, dtype=np.float32)
+    t = np.zeros(3, dtype=np.float32)
+    lc = c_light(light)
+    tg = np.ascontiguousarray(target, dtype=np.float32)
+    s = lib().go_light_view_any(C.byref(lc), _fp(tg), width, height, _fp(R), _fp(t))
+    return R.reshape(3, 3), t, float(s)
 
 
 def light_view(light_pos, target=(0.0, 0.0, 0.0)):

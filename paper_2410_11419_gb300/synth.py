@@ -40,7 +40,7 @@ _STREAMS = {
     "pos": 1, "pos_dir": 2, "pos_r": 3, "scale": 4, "rot": 5, "opacity": 6,
     "albedo": 7, "shade_rot": 8, "latent": 9, "lobe_axis": 10, "lobe_sharp": 11,
     "lobe_amp": 12, "phi": 13, "psi": 14, "camera": 15, "light": 16,
-    "shell_noise": 17, "perturb": 18,
+    "shell_noise": 17, "perturb": 18, "environment": 19,
 }
 
 RELU = 0
@@ -178,8 +178,15 @@ class Camera:
 
 @dataclass
 class Light:
+    """Point light at pos (type 0, Sec. 4.2) or directional light from the scene
+    towards dir (type 1, Sec. 4.5) with an orthographic light view of
+    half-width extent; intensity is I of the point light's I / d^2, or the
+    directional light's irradiance."""
     pos: np.ndarray
     intensity: float
+    type: int = 0
+    dir: np.ndarray | None = None
+    extent: float = 0.0
 
 
 def _positions(g_dir, g_r, g_noise, n: int, kind: str) -> np.ndarray:
@@ -273,6 +280,27 @@ def camera_light_pair(seed: int, width: int, height: int, radius: float = 3.0,
     cam = look_at_camera(radius * cdir, fov_y_deg=fov_y_deg, width=width, height=height)
     light = Light(pos=(radius * ldir).astype(np.float32), intensity=float(np.float32(intensity)))
     return cam, light
+
+
+def directional_light(seed: int, intensity: float = 10.0 / 9.0, extent: float = 1.25) -> Light:
+    """Seeded directional light (the point light's direction of the same seed;
+    irradiance 10/9 = the point light's I / d^2 at the scene centre)."""
+    ldir = _unit_vectors(rng(seed, "light"), 1)[0].astype(np.float32)
+    return Light(pos=np.zeros(3, dtype=np.float32), intensity=float(np.float32(intensity)), type=1,
+                 dir=ldir, extent=float(np.float32(extent)))
+
+
+def environment_lights(seed: int, count: int, extent: float = 1.25):
+    """`count` seeded directional lights on the sphere with weights summing to
+    the solid angle per sample (an environment light sampled uniformly;
+    radiance U[0, 1] per direction)."""
+    g = rng(seed, "environment")
+    dirs = _unit_vectors(g, count).astype(np.float32)
+    radiance = g.uniform(0.0, 1.0, count)
+    weights = (4.0 * np.pi / count * radiance).astype(np.float32)
+    lights = [Light(pos=np.zeros(3, dtype=np.float32), intensity=1.0, type=1, dir=d, extent=float(np.float32(extent)))
+              for d in dirs]
+    return lights, weights
 
 
 def perturbed(scene: Scene, seed: int) -> Scene:
