@@ -83,6 +83,7 @@ def parse():
     ap.add_argument("--inflight", type=int, default=4, help="server in-flight slots (served arm)")
     ap.add_argument("--no-serve", action="store_true", help="time single frames only")
     ap.add_argument("--no-mix", action="store_true", help="skip the mixed-scene serving measurement")
+    ap.add_argument("--no-ksweep", action="store_true", help="skip the lobe-count sweep")
     ap.add_argument("--mix-requests", type=int, default=160,
                     help="requests per arrival rate in the mixed-scene serving measurement")
     return ap.parse_args()
@@ -217,6 +218,43 @@ def run_reference(a):
 MIX_SIZES = (100_000, 250_000, 500_000, 1_000_000)
 MIX_RES = (256, 512, 800, 1024)
 MIX_RATES = (50, 200, 500, 1000, 2000)
+
+
+KSWEEP = (1, 2, 4, 8, 16)
+
+
+def lobe_sweep(a, dev, np, torch, N, R, synth, frames=10):
+    """Frames/s and K1 (k_prep) time of the object workload (BF16 MLPs, one
+    frame at a time, L2 flushed) for K = 1, 2, 4, 8, 16 angular Gaussians per
+    spatial Gaussian (the paper's lobe-count ablation)."""
+    pairs = [synth.camera_light_pair(i, a.res, a.res) for i in range(frames)]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    out = {}
+    for k in KSWEEP:
+        sc = synth.object_scene(0, n=a.n, k=k)
+        ds = R.DeviceScene(sc, device=dev, mlp_dtype=N.GS3_MLP_BF16)
+        rd = R.Renderer(ds, a.res, a.res, 40_000_000 if a.n <= 300_000 else int(a.n * 140), device=dev)
+        for i in range(2):
+            rd.render(*pairs[i])
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+               torch.cuda.Event(enable_timing=True)) for _ in range(frames)]
+        for i in range(frames):
+            flush.zero_()
+            ev[i][0].record()
+            rd.render_stages(*pairs[i], N.GS3_STAGE_PREP)
+            ev[i][1].record()
+            rd.render_stages(*pairs[i], N.GS3_STAGE_ALL & ~N.GS3_STAGE_PREP)
+            ev[i][2].record()
+        torch.cuda.synchronize()
+        rd.check()
+        tot = np.array([e0.elapsed_time(e2) for e0, _, e2 in ev])
+        prep = np.array([e0.elapsed_time(e1) for e0, e1, _ in ev])
+        out[str(k)] = {"frames_per_s": frames / (tot.sum() / 1e3), "ms_per_frame": float(tot.mean()),
+                       "prep_ms": float(prep.mean())}
+        del rd
+        ds.close()
+    return out
 
 
 def serving_mix(a, dev, np, torch, N, R, synth):
@@ -603,6 +641,8 @@ def main():
     }
     if world == 1 and not a.no_mix:
         out["serving_mix"] = serving_mix(a, dev, np, torch, N, R, synth)
+    if world == 1 and not a.no_ksweep:
+        out["lobe_sweep"] = lobe_sweep(a, dev, np, torch, N, R, synth)
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(a, scene)
     if rank == 0:

@@ -57,7 +57,10 @@ enum { GS3_ACT_RELU = 0, GS3_ACT_LEAKY_RELU = 1 };         /* hidden-layer activ
  * beyond the calibrated range saturate at 448.  FP8 needs hidden widths of
  * 32, 64 or 128. */
 enum { GS3_MLP_FP32 = 0, GS3_MLP_BF16 = 1, GS3_MLP_FP8_E4M3 = 2 };
-enum { GS3_ABLATE_SHADOW_SPLAT = 1, GS3_ABLATE_PHI = 2, GS3_ABLATE_PSI = 4 };
+/* Ablations (render modes): no shadow splat (T = 1), no Phi (T' = T), no Psi
+ * (residual 0), Lambertian only (no angular-Gaussian lobes: the first stage
+ * of the two-stage training of Sec. 4.4). */
+enum { GS3_ABLATE_SHADOW_SPLAT = 1, GS3_ABLATE_PHI = 2, GS3_ABLATE_PSI = 4, GS3_ABLATE_SPECULAR = 8 };
 
 /* Fully connected network in_dim -> [width] x n_hidden -> out_dim with a
  * sigmoid output (Sec. 4.2: Phi, Sec. 4.3: Psi).
@@ -104,10 +107,22 @@ typedef struct {
     int32_t width, height;
 } gs3_camera;
 
-/* Point light (Sec. 4.2), host struct. */
+/* Light, host struct.
+ *   GS3_LIGHT_POINT (Sec. 4.2): at pos; irradiance intensity / d^2 when
+ *     opts.falloff is set, else intensity; perspective shadow splat from pos.
+ *   GS3_LIGHT_DIRECTIONAL (Sec. 4.5): from the scene towards dir (normalised
+ *     inside); irradiance intensity (no fall-off); orthographic shadow splat
+ *     along -dir over a view of half-width `extent` world units centred at
+ *     opts.target (pixel scale min(W, H) / (2 extent)), its eye at
+ *     target + dir * 4 extent; Gaussians are sorted by depth along the axis.
+ * Zero-initialised type, dir and extent give a point light. */
+enum { GS3_LIGHT_POINT = 0, GS3_LIGHT_DIRECTIONAL = 1 };
 typedef struct {
     float pos[3];
     float intensity;
+    int32_t type;
+    float dir[3];
+    float extent;
 } gs3_light;
 
 /* Render options, host struct; gs3_default_opts fills the paper's values:
@@ -131,6 +146,7 @@ typedef struct {
     uint32_t pairs_cam_needed, pairs_light_needed; /* before clamping to the capacity */
     uint32_t reserved[3];
     float light_R[9], light_t[3]; /* light camera used by the shadow splat */
+    float light_ortho;            /* its pixels per world unit if orthographic, else 0 */
 } gs3_ws_header;
 
 /* Byte offsets of the named intermediate buffers inside a workspace (for
@@ -216,6 +232,19 @@ gs3_status gs3_render_stages(gs3_scene *scene, const gs3_camera *camera, const g
                              size_t workspace_bytes, size_t key_capacity, uint32_t stages,
                              void *stream);
 
+/* Environment light (Sec. 4.5): out_rgb = sum_l weights[l] * (the image
+ * gs3_render gives for lights[l]), the lights directional (or point).
+ *   lights, weights: host arrays of `count` >= 1 entries
+ *   out_rgb:         device float32 [height][width][3], overwritten
+ *   scratch_rgb:     device float32 [height][width][3], caller-owned
+ * The frames run one after another in `workspace`; the header then reports
+ * the first non-OK status and the largest pair counts over the lights.
+ * Asynchronous.  Errors: as gs3_render. */
+gs3_status gs3_render_environment(gs3_scene *scene, const gs3_camera *camera, const gs3_light *lights,
+                                  const float *weights, int32_t count, const gs3_render_opts *opts,
+                                  float *out_rgb, float *scratch_rgb, void *workspace, size_t workspace_bytes,
+                                  size_t key_capacity, void *stream);
+
 /* Copy the workspace header to `out` (host) and synchronise `stream`. */
 gs3_status gs3_workspace_read_header(const void *workspace, gs3_ws_header *out, void *stream);
 
@@ -263,6 +292,15 @@ size_t gs3_loss_scratch_size(int32_t width, int32_t height);
 gs3_status gs3_loss_l1_dssim(const float *img, const float *target, int32_t width, int32_t height,
                              float lambda, float *loss_out, float *dL_dimg, void *scratch,
                              size_t scratch_bytes, void *stream);
+
+/* One Adam step (Kingma and Ba; the optimiser of Sec. 4.4) on n parameters,
+ * in place:  m = b1 m + (1 - b1) g,  v = b2 v + (1 - b2) g^2,
+ *            p = max(lower_bound, p - lr (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps)).
+ *   param, m, v: device float32 [n], updated;  grad: device float32 [n]
+ *   step: t >= 1 (bias correction);  lower_bound: -INFINITY for none
+ * Asynchronous on `stream`.  Errors: INVALID_ARG, CUDA. */
+gs3_status gs3_adam_step(float *param, const float *grad, float *m, float *v, size_t n, float lr,
+                         float beta1, float beta2, float eps, int32_t step, float lower_bound, void *stream);
 
 /* ---- Continuous-batching server -----------------------------------------
  * Serving form of gs3_render (no counterpart in the paper, which renders one

@@ -103,7 +103,8 @@ typedef struct {
 typedef struct {
     float near_z, lowpass, frustum, shadow_bias, alpha_min, alpha_max, t_stop;
     float target[3];
-    int falloff, tile, ablate; /* ablate bits: 1 no shadow splat, 2 no Phi, 4 no Psi */
+    int falloff, tile, ablate; /* ablate bits: 1 no shadow splat, 2 no Phi, 4 no Psi,
+                                  8 Lambertian only (no lobes: the first training stage, Sec. 4.4) */
     int threads;
     double margin_alpha, margin_tstop;
     int crop[4]; /* x0, y0, x1, y1 (exclusive) pixel window of both composites; all 0 = full */
@@ -391,7 +392,7 @@ static void shade_one(const go_scene *sc, int g, const go_camera *cam, const go_
     double fs[3] = {0, 0, 0};
     d3 hs = {wil.x + wol.x, wil.y + wol.y, wil.z + wol.z};
     double hn = sqrt(d3_dot(hs, hs));
-    if (hn >= 1e-12) {
+    if (hn >= 1e-12 && !(o->ablate & 8)) {
         double h[3] = {hs.x / hn, hs.y / hn, hs.z / hn};
         for (int j = 0; j < sc->k; ++j) {
             size_t li = (size_t)j * sc->n + g;

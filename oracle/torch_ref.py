@@ -55,18 +55,27 @@ def mlp(params, act, x):
     return h
 
 
-def project(mu, scale, rot, R, t, fx, fy, cx, cy, lowpass=0.3):
-    """Screen position (N, 2) and conic (N, 3) = (A, B, C) of every Gaussian."""
+def project(mu, scale, rot, R, t, fx, fy, cx, cy, lowpass=0.3, ortho=0.0):
+    """Screen position (N, 2) and conic (N, 3) = (A, B, C) of every Gaussian;
+    perspective, or orthographic with `ortho` pixels per unit (Sec. 4.5)."""
     p = mu @ R.T + t
     tx, ty, tz = p.unbind(1)
-    u = fx * tx / tz + cx
-    v = fy * ty / tz + cy
+    if ortho > 0:
+        u = ortho * tx + cx
+        v = ortho * ty + cy
+    else:
+        u = fx * tx / tz + cx
+        v = fy * ty / tz + cy
     Rq = quat_mat(rot)
     M = Rq * scale[:, None, :]
     Sig = M @ M.transpose(1, 2)
     zero = torch.zeros_like(tz)
-    J = torch.stack([torch.stack([fx / tz, zero, -fx * tx / (tz * tz)], 1),
-                     torch.stack([zero, fy / tz, -fy * ty / (tz * tz)], 1)], 1)
+    if ortho > 0:
+        s_ = torch.full_like(tz, ortho)
+        J = torch.stack([torch.stack([s_, zero, zero], 1), torch.stack([zero, s_, zero], 1)], 1)
+    else:
+        J = torch.stack([torch.stack([fx / tz, zero, -fx * tx / (tz * tz)], 1),
+                         torch.stack([zero, fy / tz, -fy * ty / (tz * tz)], 1)], 1)
     T = J @ R
     S2 = T @ Sig @ T.transpose(1, 2)
     a = S2[:, 0, 0] + lowpass
@@ -76,9 +85,15 @@ def project(mu, scale, rot, R, t, fx, fy, cx, cy, lowpass=0.3):
     return torch.stack([u, v], 1), torch.stack([c / det, -b / det, a / det], 1)
 
 
-def shade(P, cam_pos, light_pos, intensity, falloff=True):
+def shade(P, cam_pos, light_pos, intensity, falloff=True, light_dir=None, specular=True):
+    """Colour (Eq. 2-5), omega_i and omega_o.  A directional light (Sec. 4.5)
+    gives omega_i = light_dir for every Gaussian and no fall-off."""
     mu = P["mu"]
-    tol = light_pos[None] - mu
+    if light_dir is not None:
+        tol = light_dir[None].expand_as(mu)
+        falloff = False
+    else:
+        tol = light_pos[None] - mu
     d2 = (tol * tol).sum(1)
     wi = tol / d2.sqrt()[:, None]
     vo = cam_pos[None] - mu
@@ -93,7 +108,7 @@ def shade(P, cam_pos, light_pos, intensity, falloff=True):
     hs = wil + wol
     h = hs / hs.norm(dim=1, keepdim=True)
     fs = torch.zeros_like(mu)
-    K = P["lobe_rot"].shape[0]
+    K = P["lobe_rot"].shape[0] if specular else 0
     for j in range(K):
         Rl = quat_mat(P["lobe_rot"][j])
         hl = (Rl.transpose(1, 2) @ h[:, :, None])[:, :, 0]
@@ -138,10 +153,16 @@ def frame(P, fr, cam, light, opts, mlps):
     f = [float(cam.fx), float(cam.fy), float(cam.cx), float(cam.cy)]
     lp = float(np.float32(opts.lowpass))
     uv_c, con_c = project(P["mu"], P["scale"], P["rot"], Rc, tc, *f, lowpass=lp)
-    uv_l, con_l = project(P["mu"], P["scale"], P["rot"], Rl, tl, *f, lowpass=lp)
+    uv_l, con_l = project(P["mu"], P["scale"], P["rot"], Rl, tl, *f, lowpass=lp,
+                          ortho=float(fr.get("light_ortho", 0.0)))
     cam_pos = torch.tensor(cam.pos, dtype=DT)
     light_pos = torch.tensor(light.pos, dtype=DT)
-    col, wi, wo = shade(P, cam_pos, light_pos, float(light.intensity), bool(opts.falloff))
+    ldir = None
+    if getattr(light, "type", 0) == 1:
+        ldir = torch.tensor(np.asarray(light.dir, dtype=np.float32), dtype=DT)
+        ldir = ldir / ldir.norm()
+    col, wi, wo = shade(P, cam_pos, light_pos, float(light.intensity), bool(opts.falloff), light_dir=ldir,
+                        specular=not (opts.ablate & 8))
 
     # ---- shadow splatting (Sec. 4.2) ----
     num = torch.zeros(n, dtype=DT)

@@ -17,7 +17,7 @@ GS3_OK, GS3_ERR_INVALID_ARG, GS3_ERR_OOM, GS3_ERR_CAPACITY, GS3_ERR_CUDA, GS3_ER
     GS3_ERR_UNSUPPORTED = range(7)
 GS3_ACT_RELU, GS3_ACT_LEAKY_RELU = 0, 1
 GS3_MLP_FP32, GS3_MLP_BF16, GS3_MLP_FP8_E4M3 = 0, 1, 2
-GS3_ABLATE_SHADOW_SPLAT, GS3_ABLATE_PHI, GS3_ABLATE_PSI = 1, 2, 4
+GS3_ABLATE_SHADOW_SPLAT, GS3_ABLATE_PHI, GS3_ABLATE_PSI, GS3_ABLATE_SPECULAR = 1, 2, 4, 8
 GS3_STAGE_PREP, GS3_STAGE_CAMERA_BIN, GS3_STAGE_LIGHT_BIN, GS3_STAGE_SHADOW_COMPOSITE, \
     GS3_STAGE_SHADOW_REDUCE, GS3_STAGE_MLP, GS3_STAGE_CAMERA, GS3_STAGE_ALL = 1, 2, 4, 8, 16, 32, 64, 127
 
@@ -52,8 +52,12 @@ class gs3_camera(C.Structure):
                 ("width", C.c_int32), ("height", C.c_int32)]
 
 
+GS3_LIGHT_POINT, GS3_LIGHT_DIRECTIONAL = 0, 1
+
+
 class gs3_light(C.Structure):
-    _fields_ = [("pos", C.c_float * 3), ("intensity", C.c_float)]
+    _fields_ = [("pos", C.c_float * 3), ("intensity", C.c_float), ("type", C.c_int32),
+                ("dir", C.c_float * 3), ("extent", C.c_float)]
 
 
 class gs3_render_opts(C.Structure):
@@ -66,7 +70,8 @@ class gs3_render_opts(C.Structure):
 class gs3_ws_header(C.Structure):
     _fields_ = [("status", C.c_uint32), ("pairs_cam", C.c_uint32), ("pairs_light", C.c_uint32),
                 ("pairs_cam_needed", C.c_uint32), ("pairs_light_needed", C.c_uint32),
-                ("reserved", C.c_uint32 * 3), ("light_R", C.c_float * 9), ("light_t", C.c_float * 3)]
+                ("reserved", C.c_uint32 * 3), ("light_R", C.c_float * 9), ("light_t", C.c_float * 3),
+                ("light_ortho", C.c_float)]
 
 
 class gs3_ws_layout(C.Structure):
@@ -126,6 +131,12 @@ SIGNATURES = {
                                     C.POINTER(gs3_render_opts), C.c_void_p, C.c_void_p, C.c_size_t,
                                     C.c_size_t, C.c_uint32, C.c_void_p]),
     "gs3_workspace_read_header": (C.c_int, [C.c_void_p, C.POINTER(gs3_ws_header), C.c_void_p]),
+    "gs3_adam_step": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t, C.c_float,
+                                C.c_float, C.c_float, C.c_float, C.c_int32, C.c_float, C.c_void_p]),
+    "gs3_render_environment": (C.c_int, [_SCENE_P, C.POINTER(gs3_camera), C.POINTER(gs3_light),
+                                         C.POINTER(C.c_float), C.c_int32, C.POINTER(gs3_render_opts),
+                                         C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t, C.c_size_t,
+                                         C.c_void_p]),
     "gs3_backward_workspace_size": (C.c_size_t, [_SCENE_P]),
     "gs3_loss_scratch_size": (C.c_size_t, [C.c_int32, C.c_int32]),
     "gs3_loss_l1_dssim": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_float, C.c_void_p,
@@ -211,6 +222,25 @@ def gs3_workspace_layout(n: int, width: int, height: int, key_capacity: int) -> 
     _check(lib().gs3_workspace_layout(n, width, height, key_capacity, C.byref(out)),
            "gs3_workspace_layout")
     return out
+
+
+def gs3_adam_step(param, grad, m, v, lr: float, beta1: float, beta2: float, eps: float, step: int,
+                  lower_bound: float, stream: int) -> None:
+    n = param.numel()
+    assert grad.numel() == n and m.numel() == n and v.numel() == n
+    _check(lib().gs3_adam_step(_ptr(param), _ptr(grad), _ptr(m), _ptr(v), n, lr, beta1, beta2, eps, step,
+                               lower_bound, stream), "gs3_adam_step")
+
+
+def gs3_render_environment(scene, camera: gs3_camera, lights, weights, opts: gs3_render_opts, out_rgb,
+                           scratch_rgb, workspace, key_capacity: int, stream: int) -> None:
+    n = len(lights)
+    la = (gs3_light * n)(*lights)
+    wa = (C.c_float * n)(*[float(w) for w in weights])
+    _check(lib().gs3_render_environment(scene, C.byref(camera), la, wa, n, C.byref(opts), _ptr(out_rgb),
+                                        _ptr(scratch_rgb), _ptr(workspace),
+                                        workspace.numel() * workspace.element_size(), key_capacity, stream),
+           "gs3_render_environment")
 
 
 def gs3_render(scene, camera: gs3_camera, light: gs3_light, opts: gs3_render_opts, out_rgb,

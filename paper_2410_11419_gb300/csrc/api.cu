@@ -48,6 +48,22 @@ bool mlp_ok(const gs3_mlp_desc& m, int in_dim, int out_dim) {
   return m.w && m.b;
 }
 
+// out (+)= w * img over n floats; block 0 also folds the frame's header into
+// the environment words (first non-OK status, largest pair counts)
+__global__ void k_env_accumulate(float* out, const float* img, size_t n, float w, int first, uint32_t* header) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    out[i] = first ? w * img[i] : fmaf(w, img[i], out[i]);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    uint32_t* env = header + H_ENV;
+    if (first) env[0] = env[1] = env[2] = env[3] = env[4] = 0u;
+    if (env[0] == 0u) env[0] = header[H_STATUS];
+    for (int k = 1; k < 5; ++k) env[k] = max(env[k], header[k]);
+  }
+}
+__global__ void k_env_finish(uint32_t* header) {
+  if (threadIdx.x == 0)
+    for (int k = 0; k < 5; ++k) header[k] = header[H_ENV + k];
+}
 }  // namespace
 
 void set_last_error(const char* msg) { g_last_error = msg; }
@@ -262,6 +278,21 @@ gs3_status gs3_workspace_layout(int32_t n, int32_t width, int32_t height, size_t
   return GS3_OK;
 }
 
+// Why a light cannot be rendered, or null.
+static const char* light_problem(const gs3_light& l, const gs3_render_opts& o) {
+  if (l.type == GS3_LIGHT_POINT) {
+    const float tl[3] = {o.target[0] - l.pos[0], o.target[1] - l.pos[1], o.target[2] - l.pos[2]};
+    if (!(tl[0] * tl[0] + tl[1] * tl[1] + tl[2] * tl[2] >= 1e-12f))
+      return "gs3_render: light coincides with the light-camera target";
+    return nullptr;
+  }
+  if (l.type != GS3_LIGHT_DIRECTIONAL) return "gs3_render: light type must be GS3_LIGHT_POINT or GS3_LIGHT_DIRECTIONAL";
+  if (!(l.dir[0] * l.dir[0] + l.dir[1] * l.dir[1] + l.dir[2] * l.dir[2] >= 1e-12f))
+    return "gs3_render: directional light needs a non-zero direction";
+  if (!(l.extent > 0.f) || !(l.extent < 1e30f)) return "gs3_render: directional light needs extent > 0";
+  return nullptr;
+}
+
 gs3_status gs3_render_stages(gs3_scene* scene, const gs3_camera* cam, const gs3_light* light,
                              const gs3_render_opts* opts, float* out_rgb, void* workspace, size_t ws_bytes,
                              size_t key_capacity, uint32_t stages, void* stream) {
@@ -279,9 +310,10 @@ gs3_status gs3_render_stages(gs3_scene* scene, const gs3_camera* cam, const gs3_
   if (ntiles > 65536) return fail(GS3_ERR_INVALID_ARG, "gs3_render: more than 65536 tiles");
   if ((double)scene->dev.n * (double)ntiles >= 4294967295.0)
     return fail(GS3_ERR_INVALID_ARG, "gs3_render: n * tiles must stay below 2^32");
-  float tl[3] = {opts->target[0] - light->pos[0], opts->target[1] - light->pos[1], opts->target[2] - light->pos[2]};
-  if (tl[0] * tl[0] + tl[1] * tl[1] + tl[2] * tl[2] < 1e-12f)
-    return fail(GS3_ERR_INVALID_ARG, "gs3_render: light coincides with the light-camera target");
+  {
+    const char* why = light_problem(*light, *opts);
+    if (why) return fail(GS3_ERR_INVALID_ARG, why);
+  }
   Workspace L = plan_workspace(scene->dev.n, cam->width, cam->height, key_capacity);
   if (ws_bytes < L.total) return fail(GS3_ERR_INVALID_ARG, "gs3_render: workspace too small");
   if (!device_range_ok(workspace, L.total))
@@ -300,7 +332,7 @@ gs3_status gs3_render_stages(gs3_scene* scene, const gs3_camera* cam, const gs3_
   cudaError_t e = cudaSuccess;
   const bool no_shadow = (opts->ablate & GS3_ABLATE_SHADOW_SPLAT) != 0;
   if (stages & GS3_STAGE_PREP) {
-    e = cudaMemsetAsync(f.ws + L.header, 0, 256, s);
+    e = cudaMemsetAsync(f.ws + L.header, 0, 4 * H_RESET_WORDS, s);
     if (e != cudaSuccess) return cuda_fail(e, "gs3_render: header reset");
     launch_prep(f, s);
   }
@@ -339,13 +371,40 @@ gs3_status gs3_render(gs3_scene* scene, const gs3_camera* cam, const gs3_light* 
                            GS3_STAGE_ALL, stream);
 }
 
+gs3_status gs3_render_environment(gs3_scene* scene, const gs3_camera* cam, const gs3_light* lights,
+                                  const float* weights, int32_t count, const gs3_render_opts* opts, float* out_rgb,
+                                  float* scratch_rgb, void* workspace, size_t ws_bytes, size_t key_capacity,
+                                  void* stream) {
+  if (!lights || !weights || count < 1 || !scratch_rgb || !cam)
+    return fail(GS3_ERR_INVALID_ARG, "gs3_render_environment: bad light list or scratch");
+  const size_t n = (size_t)cam->width * cam->height * 3;
+  if (!device_range_ok(scratch_rgb, n * sizeof(float)) || !device_range_ok(out_rgb, n * sizeof(float)))
+    return fail(GS3_ERR_INVALID_ARG, "gs3_render_environment: out_rgb / scratch_rgb not width*height*3 floats");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  for (int32_t l = 0; l < count; ++l) {
+    const gs3_status st = gs3_render(scene, cam, &lights[l], opts, scratch_rgb, workspace, ws_bytes, key_capacity, stream);
+    if (st != GS3_OK) return st;  // argument errors are found on the first light, before any launch
+    uint32_t* header = reinterpret_cast<uint32_t*>(static_cast<unsigned char*>(workspace) +
+                                                   plan_workspace(scene->dev.n, cam->width, cam->height,
+                                                                  key_capacity).header);
+    const size_t want = (n + 255) / 256;
+    const int blocks = (int)(want < 152 * 8 ? want : 152 * 8);
+    k_env_accumulate<<<blocks, 256, 0, s>>>(out_rgb, scratch_rgb, n, weights[l], l == 0, header);
+    count_launch();
+  }
+  k_env_finish<<<1, 32, 0, s>>>(reinterpret_cast<uint32_t*>(
+      static_cast<unsigned char*>(workspace) + plan_workspace(scene->dev.n, cam->width, cam->height, key_capacity).header));
+  count_launch();
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? GS3_OK : cuda_fail(e, "gs3_render_environment: launch");
+}
+
 size_t gs3_backward_workspace_size(const gs3_scene* scene) {
   if (!scene) return 0;
   return backward_workspace_bytes(scene->dev.n, scene->dev.phi, scene->dev.psi);
 }
 
 // light camera of the frame, the same FP32 recipe as the forward kernel's
-static void light_view_host(const float pL[3], const float tg[3], float R[9], float t[3]);
 
 gs3_status gs3_render_backward(gs3_scene* scene, const gs3_camera* cam, const gs3_light* light,
                                const gs3_render_opts* opts, const float* dimg, void* workspace,
@@ -357,6 +416,7 @@ gs3_status gs3_render_backward(gs3_scene* scene, const gs3_camera* cam, const gs
     return fail(GS3_ERR_UNSUPPORTED, "gs3_render_backward: needs a GS3_MLP_FP32 scene");
   if (cam->width < 1 || cam->height < 1 || opts->tile != kTile)
     return fail(GS3_ERR_INVALID_ARG, "gs3_render_backward: bad camera or options");
+  if (light_problem(*light, *opts)) return fail(GS3_ERR_INVALID_ARG, "gs3_render_backward: invalid light");
   Workspace L = plan_workspace(scene->dev.n, cam->width, cam->height, key_capacity);
   if (ws_bytes < L.total || !device_range_ok(workspace, L.total))
     return fail(GS3_ERR_INVALID_ARG, "gs3_render_backward: workspace too small");
@@ -372,7 +432,6 @@ gs3_status gs3_render_backward(gs3_scene* scene, const gs3_camera* cam, const gs
   f.opts = *opts;
   f.ws = static_cast<unsigned char*>(workspace);
   f.L = &L;
-  light_view_host(light->pos, opts->target, f.light_view, f.light_view + 9);
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   gs3_status st = run_backward(f, dimg, bws, bws_bytes, *grads, s);
   if (st != GS3_OK) return fail(st, "gs3_render_backward: bad workspace");
@@ -381,19 +440,18 @@ gs3_status gs3_render_backward(gs3_scene* scene, const gs3_camera* cam, const gs
   return GS3_OK;
 }
 
-static void light_view_host(const float pL[3], const float tg[3], float R[9], float t[3]) {
-  // gradients only need the rotation to float accuracy; plain float arithmetic
-  float fx = tg[0] - pL[0], fy = tg[1] - pL[1], fz = tg[2] - pL[2];
-  float n = sqrtf(fx * fx + fy * fy + fz * fz);
-  fx /= n; fy /= n; fz /= n;
-  float ux = 0.f, uy = 0.f, uz = 1.f;
-  if (fabsf(fz) > 0.999f) { uy = 1.f; uz = 0.f; }
-  float rx = fy * uz - fz * uy, ry = fz * ux - fx * uz, rz = fx * uy - fy * ux;
-  float rn = sqrtf(rx * rx + ry * ry + rz * rz);
-  rx /= rn; ry /= rn; rz /= rn;
-  const float dx = fy * rz - fz * ry, dy = fz * rx - fx * rz, dz = fx * ry - fy * rx;
-  R[0] = rx; R[1] = ry; R[2] = rz; R[3] = dx; R[4] = dy; R[5] = dz; R[6] = fx; R[7] = fy; R[8] = fz;
-  for (int i = 0; i < 3; ++i) t[i] = -(R[3 * i] * pL[0] + R[3 * i + 1] * pL[1] + R[3 * i + 2] * pL[2]);
+gs3_status gs3_adam_step(float* param, const float* grad, float* m, float* v, size_t n, float lr, float beta1,
+                         float beta2, float eps, int32_t step, float lower_bound, void* stream) {
+  if (!param || !grad || !m || !v || n == 0 || step < 1)
+    return fail(GS3_ERR_INVALID_ARG, "gs3_adam_step: null array, n = 0 or step < 1");
+  if (!(beta1 >= 0.f && beta1 < 1.f) || !(beta2 >= 0.f && beta2 < 1.f) || !(eps >= 0.f) || !(lr >= 0.f))
+    return fail(GS3_ERR_INVALID_ARG, "gs3_adam_step: betas must be in [0, 1), lr and eps >= 0");
+  const size_t b = n * sizeof(float);
+  if (!device_range_ok(param, b) || !device_range_ok(grad, b) || !device_range_ok(m, b) || !device_range_ok(v, b))
+    return fail(GS3_ERR_INVALID_ARG, "gs3_adam_step: an array is shorter than n floats");
+  launch_adam(param, grad, m, v, n, lr, beta1, beta2, eps, step, lower_bound, reinterpret_cast<cudaStream_t>(stream));
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? GS3_OK : cuda_fail(e, "gs3_adam_step");
 }
 
 size_t gs3_loss_scratch_size(int32_t width, int32_t height) {

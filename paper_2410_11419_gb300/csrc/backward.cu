@@ -453,6 +453,7 @@ __device__ __forceinline__ float4 quat_bwd(const float G[9], const float qn[4], 
 struct ViewB {
   float R[9], t[3];
   float fx, fy, lowpass;
+  float ortho;  // > 0: orthographic view with this many pixels per world unit
 };
 
 // one EWA projection's backward; adds to dmu, ds and dR (of R(q))
@@ -462,6 +463,7 @@ __device__ void proj_bwd(const float4 m, const float4 s, const float Rq[9], cons
   const float x = R[0] * m.x + R[1] * m.y + R[2] * m.z + v.t[0];
   const float y = R[3] * m.x + R[4] * m.y + R[5] * m.z + v.t[1];
   const float z = R[6] * m.x + R[7] * m.y + R[8] * m.z + v.t[2];
+  const bool ortho = v.ortho > 0.f;
   const float iz = 1.f / z, iz2 = iz * iz;
   const float sv[3] = {s.x, s.y, s.z};
   float M[9], Sg[9];
@@ -469,7 +471,9 @@ __device__ void proj_bwd(const float4 m, const float4 s, const float Rq[9], cons
     for (int j = 0; j < 3; ++j) M[3 * i + j] = Rq[3 * i + j] * sv[j];
   for (int i = 0; i < 3; ++i)
     for (int j = 0; j < 3; ++j) Sg[3 * i + j] = M[3 * i] * M[3 * j] + M[3 * i + 1] * M[3 * j + 1] + M[3 * i + 2] * M[3 * j + 2];
-  const float J00 = v.fx * iz, J02 = -v.fx * x * iz2, J11 = v.fy * iz, J12 = -v.fy * y * iz2;
+  // J = [[fx / z, 0, -fx x / z^2], [0, fy / z, -fy y / z^2]], or [[s, 0, 0], [0, s, 0]]
+  const float J00 = ortho ? v.ortho : v.fx * iz, J02 = ortho ? 0.f : -v.fx * x * iz2;
+  const float J11 = ortho ? v.ortho : v.fy * iz, J12 = ortho ? 0.f : -v.fy * y * iz2;
   float T[6];
   for (int k = 0; k < 3; ++k) {
     T[k] = J00 * R[k] + J02 * R[6 + k];
@@ -512,6 +516,13 @@ __device__ void proj_bwd(const float4 m, const float4 s, const float Rq[9], cons
   const float dJ11 = dT[3] * R[3] + dT[4] * R[4] + dT[5] * R[5];
   const float dJ12 = dT[3] * R[6] + dT[4] * R[7] + dT[5] * R[8];
   const float du = gg[0], dv = gg[1];
+  if (ortho) {  // u = s x + cx, v = s y + cy; J constant
+    const float dx = du * v.ortho, dy = dv * v.ortho;
+    dmu[0] += R[0] * dx + R[3] * dy;
+    dmu[1] += R[1] * dx + R[4] * dy;
+    dmu[2] += R[2] * dx + R[5] * dy;
+    return;
+  }
   const float dx = du * v.fx * iz + dJ02 * (-v.fx * iz2);
   const float dy = dv * v.fy * iz + dJ12 * (-v.fy * iz2);
   const float dz = du * (-v.fx * x * iz2) + dv * (-v.fy * y * iz2) + dJ00 * (-v.fx * iz2) +
@@ -523,8 +534,11 @@ __device__ void proj_bwd(const float4 m, const float4 s, const float Rq[9], cons
 
 struct PrepBwdParams {
   SceneDev sc;
-  ViewB cam, light;
-  float light_pos[3], cam_pos[3], intensity;
+  ViewB cam, light;  // the light view's R, t and scale come from the forward's header
+  const float* header_view;  // R (9), t (3) at H_LIGHT_VIEW, scale at H_LIGHT_ORTHO
+  float4 lh;                 // homogeneous light (light_h)
+  float cam_pos[3], intensity;
+  int ablate;
   int falloff;
   const float* cam_geom;
   const float* light_geom;
@@ -544,15 +558,19 @@ __global__ void __launch_bounds__(128) k_prep_bwd(PrepBwdParams p) {
   float dmu[3] = {0, 0, 0}, ds[3] = {0, 0, 0}, dRq[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
   float Rq[9], qn[4], qlen;
   quat_rot(p.sc.rot[g], Rq, qn, qlen);
+  ViewB lv = p.light;
+#pragma unroll
+  for (int i = 0; i < 12; ++i) (i < 9 ? lv.R[i] : lv.t[i - 9]) = p.header_view[H_LIGHT_VIEW + i];
+  lv.ortho = p.header_view[H_LIGHT_ORTHO];
   proj_bwd(m, s, Rq, p.cam, gc, dmu, ds, dRq);
-  proj_bwd(m, s, Rq, p.light, gl, dmu, ds, dRq);
+  proj_bwd(m, s, Rq, lv, gl, dmu, ds, dRq);
   const float4 dq = quat_bwd(dRq, qn, qlen);
   const float dgamma = gc[5] + gl[5];
   const float dlogit = dgamma * gamma * (1.f - gamma);
 
   // ---- shading backward (Eq. 2-5) ----
   const float* dcol = p.color + (size_t)kColor * g;
-  const float lx = p.light_pos[0] - m.x, ly = p.light_pos[1] - m.y, lz = p.light_pos[2] - m.z;
+  const float lx = p.lh.x - p.lh.w * m.x, ly = p.lh.y - p.lh.w * m.y, lz = p.lh.z - p.lh.w * m.z;
   const float d2 = lx * lx + ly * ly + lz * lz, dl = sqrtf(d2);
   const float wi[3] = {lx / dl, ly / dl, lz / dl};
   const float vx = p.cam_pos[0] - m.x, vy = p.cam_pos[1] - m.y, vz = p.cam_pos[2] - m.z;
@@ -571,10 +589,12 @@ __global__ void __launch_bounds__(128) k_prep_bwd(PrepBwdParams p) {
   const float dfd_dx = (xz > 0.f ? 1.f : 0.01f * expf(xz)) / ((1.f + off) * 3.14159265358979323846f);
   float hs[3] = {wil[0] + wol[0], wil[1] + wol[1], wil[2] + wol[2]};
   const float hn = sqrtf(hs[0] * hs[0] + hs[1] * hs[1] + hs[2] * hs[2]);
-  const bool have_h = hn * hn >= 1e-24f;
+  // the Lambertian-only stage has no lobes: no specular term and no lobe gradients
+  const bool have_h = hn * hn >= 1e-24f && !(p.ablate & GS3_ABLATE_SPECULAR);
   float h[3] = {0, 0, 0};
   if (have_h) { h[0] = hs[0] / hn; h[1] = hs[1] / hn; h[2] = hs[2] / hn; }
-  const float E = p.falloff ? p.intensity / d2 : p.intensity;
+  const bool falloff = p.falloff && p.lh.w != 0.f;  // a directional light's E is constant
+  const float E = falloff ? p.intensity / d2 : p.intensity;
   const float4 rd = p.sc.albedo_d[g], rsp = p.sc.albedo_s[g];
   const float rdv[3] = {rd.x, rd.y, rd.z}, rsv[3] = {rsp.x, rsp.y, rsp.z};
   // f_s (recomputed) and the lobe gradients
@@ -684,15 +704,15 @@ __global__ void __launch_bounds__(128) k_prep_bwd(PrepBwdParams p) {
     dwi[k] += mi[3 + k];
     dwo[k] += mi[15 + k];
   }
-  // w_i = (pL - mu)/|.|, w_o = (pC - mu)/|.|, E = I / |pL - mu|^2
+  // w_i = (L.xyz - L.w mu)/|.|, w_o = (pC - mu)/|.|, E = I / |pL - mu|^2 (point light)
   const float wid = wi[0] * dwi[0] + wi[1] * dwi[1] + wi[2] * dwi[2];
   const float wod = wo[0] * dwo[0] + wo[1] * dwo[1] + wo[2] * dwo[2];
-  const float dd2 = p.falloff ? -dE * E / d2 : 0.f;
-  const float lv[3] = {lx, ly, lz};
+  const float dd2 = falloff ? -dE * E / d2 : 0.f;
+  const float lvv[3] = {lx, ly, lz};
   for (int k = 0; k < 3; ++k) {
-    dmu[k] -= (dwi[k] - wi[k] * wid) / dl;
+    dmu[k] -= p.lh.w * (dwi[k] - wi[k] * wid) / dl;
     dmu[k] -= (dwo[k] - wo[k] * wod) / dvn;
-    dmu[k] -= 2.f * lv[k] * dd2;
+    dmu[k] -= 2.f * lvv[k] * dd2;
   }
   reinterpret_cast<float4*>(p.out.mean_op)[g] = make_float4(dmu[0], dmu[1], dmu[2], dlogit);
   reinterpret_cast<float4*>(p.out.scale)[g] = make_float4(ds[0], ds[1], ds[2], 0.f);
@@ -784,7 +804,9 @@ gs3_status run_backward(const FrameArgs& f, const float* dimg, void* bws, size_t
       a.mean_op = f.sc.mean_op;
       a.latent = f.sc.latent;
       a.T = at<float>(ws, L.T);
-      for (int i = 0; i < 3; ++i) { a.light_pos[i] = f.light.pos[i]; a.cam_pos[i] = f.cam.pos[i]; }
+      const float4 lh = light_h(f.light);
+      a.light_pos[0] = lh.x; a.light_pos[1] = lh.y; a.light_pos[2] = lh.z; a.light_w = lh.w;
+      for (int i = 0; i < 3; ++i) a.cam_pos[i] = f.cam.pos[i];
       a.color = color;
       a.dT = dT;
       a.mlp_in = mlp_in;
@@ -822,15 +844,15 @@ gs3_status run_backward(const FrameArgs& f, const float* dimg, void* bws, size_t
   {
     PrepBwdParams p;
     p.sc = f.sc;
-    const float* hv = reinterpret_cast<const float*>(at<uint32_t>(ws, L.header) + H_LIGHT_VIEW);
-    (void)hv;
+    p.header_view = reinterpret_cast<const float*>(at<uint32_t>(ws, L.header));
     for (int i = 0; i < 9; ++i) p.cam.R[i] = f.cam.R[i];
     for (int i = 0; i < 3; ++i) p.cam.t[i] = f.cam.t[i];
     p.cam.fx = f.cam.fx; p.cam.fy = f.cam.fy; p.cam.lowpass = f.opts.lowpass;
-    p.light = p.cam;  // rotation and translation filled from the frame's light view below
-    for (int i = 0; i < 9; ++i) p.light.R[i] = f.light_view[i];
-    for (int i = 0; i < 3; ++i) p.light.t[i] = f.light_view[9 + i];
-    for (int i = 0; i < 3; ++i) { p.light_pos[i] = f.light.pos[i]; p.cam_pos[i] = f.cam.pos[i]; }
+    p.cam.ortho = 0.f;
+    p.light = p.cam;  // rotation, translation and scale are read from the header
+    p.lh = light_h(f.light);
+    p.ablate = f.opts.ablate;
+    for (int i = 0; i < 3; ++i) p.cam_pos[i] = f.cam.pos[i];
     p.intensity = f.light.intensity;
     p.falloff = f.opts.falloff;
     p.cam_geom = cam_geom;

@@ -73,7 +73,20 @@ Workspace plan_workspace(int n, int width, int height, size_t cap);
 
 // Header word indices (u32) -- must match gs3_ws_header.
 enum { H_STATUS = 0, H_PAIRS_CAM = 1, H_PAIRS_LIGHT = 2, H_NEED_CAM = 3, H_NEED_LIGHT = 4,
-       H_LIGHT_VIEW = 8 };
+       H_LIGHT_VIEW = 8, H_LIGHT_ORTHO = 20,
+       H_RESET_WORDS = 24,  // words a render resets; the rest survive across renders
+       H_ENV = 24 };        // environment render: status, pairs cam/light, needed cam/light
+
+// The light in homogeneous form (x, y, z, w): a point light (pos, 1) or a
+// directional light (dir / |dir|, 0).  omega_i = normalize(L.xyz - L.w mu)
+// covers both, and the inverse-square fall-off applies only when w = 1.
+inline float4 light_h(const gs3_light& l) {
+  if (l.type == GS3_LIGHT_DIRECTIONAL) {
+    const float n = sqrtf(l.dir[0] * l.dir[0] + l.dir[1] * l.dir[1] + l.dir[2] * l.dir[2]);
+    return make_float4(l.dir[0] / n, l.dir[1] / n, l.dir[2] / n, 0.f);
+  }
+  return make_float4(l.pos[0], l.pos[1], l.pos[2], 1.f);
+}
 
 struct MlpDev {
   int in_dim, width, n_hidden, out_dim, act;
@@ -97,9 +110,10 @@ struct FrameArgs {
   gs3_render_opts opts;
   unsigned char* ws;
   const Workspace* L;
-  float light_view[12];  // light camera R (9), t (3); filled on the host for the backward
 };
 
+void launch_adam(float* p, const float* g, float* m, float* v, size_t n, float lr, float b1, float b2, float eps,
+                 int step, float lo, cudaStream_t s);
 size_t loss_scratch_bytes(int W, int H);
 gs3_status run_loss(const float* img, const float* tgt, int W, int H, float lambda, float* loss, float* dimg,
                     void* scratch, cudaStream_t s);
@@ -113,6 +127,7 @@ struct MlpArgs {
   const float4* latent;
   const float* T;
   float light_pos[3], cam_pos[3];
+  float light_w;       // homogeneous light (see light_h)
   const float* color;  // [N][8]: dT' at 3, dres at 4..6
   float* dT;           // Phi: d/d(input T)
   float* mlp_in;       // [N][24]

@@ -26,6 +26,7 @@ struct MlpParams {
   const float4* latent;
   const float* T;
   float light_pos[3], cam_pos[3];
+  float light_w;     // 1: point light at light_pos; 0: directional, light_pos = unit direction
   float* out_idx;    // Phi: T' [N];   Psi: float4 residual [N] (as floats)
   float4* ccol;      // camera colours by rank
   const uint32_t* rank_of;
@@ -78,7 +79,8 @@ __global__ void __launch_bounds__(256) k_mlp(MlpParams p) {
     const int g = min(g0 + row, p.n - 1);
     const float4 m = p.mean_op[g];
     const float* src = p.which == 0 ? p.light_pos : p.cam_pos;
-    float dx = src[0] - m.x, dy = src[1] - m.y, dz = src[2] - m.z;
+    const float sw = p.which == 0 ? p.light_w : 1.f;
+    float dx = src[0] - sw * m.x, dy = src[1] - sw * m.y, dz = src[2] - sw * m.z;
     const float il = rsqrtf(dx * dx + dy * dy + dz * dz);
     dx *= il; dy *= il; dz *= il;
     const int b0 = p.which == 0 ? 1 : 0;
@@ -191,7 +193,9 @@ void launch_mlp(const FrameArgs& f, cudaStream_t s, bool identity_only) {
   p.mean_op = f.sc.mean_op;
   p.latent = f.sc.latent;
   p.T = at<float>(f.ws, f.L->T);
-  for (int i = 0; i < 3; ++i) { p.light_pos[i] = f.light.pos[i]; p.cam_pos[i] = f.cam.pos[i]; }
+  const float4 lh = light_h(f.light);
+  p.light_pos[0] = lh.x; p.light_pos[1] = lh.y; p.light_pos[2] = lh.z; p.light_w = lh.w;
+  for (int i = 0; i < 3; ++i) p.cam_pos[i] = f.cam.pos[i];
   p.ccol = at<float4>(f.ws, f.L->ccol);
   p.rank_of = at<uint32_t>(f.ws, f.L->sp[0].rank_of);
 

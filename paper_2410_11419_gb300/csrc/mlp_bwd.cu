@@ -213,6 +213,7 @@ struct RowArgs {
   const float4* latent;
   const float* T;
   float light_pos[3], cam_pos[3];
+  float light_w;       // 1: point light at light_pos; 0: directional, light_pos = unit direction
   const float* w_out;  // out_dim x width
   const float* b_out;
   const float* color;  // [N][8]: dT' at 3, dres at 4..6
@@ -255,8 +256,9 @@ __device__ __forceinline__ void pe_bwd(const float* dpe, float v0, float v1, flo
   }
 }
 
-__device__ __forceinline__ void unit_dir(const float* src, const float4 m, float& x, float& y, float& z) {
-  x = src[0] - m.x; y = src[1] - m.y; z = src[2] - m.z;
+// omega = normalize(src - w mu): w = 1 towards a point, w = 0 a fixed direction
+__device__ __forceinline__ void unit_dir(const float* src, float w, const float4 m, float& x, float& y, float& z) {
+  x = src[0] - w * m.x; y = src[1] - w * m.y; z = src[2] - w * m.z;
   const float il = rsqrtf(x * x + y * y + z * z);
   x *= il; y *= il; z *= il;
 }
@@ -270,7 +272,7 @@ __global__ void k_encode(RowArgs p) {
   for (int k = 0; k < kXdim; ++k) x[k] = 0.f;
   const float4 m = p.mean_op[g];
   float dx, dy, dz;
-  unit_dir(p.which == 0 ? p.light_pos : p.cam_pos, m, dx, dy, dz);
+  unit_dir(p.which == 0 ? p.light_pos : p.cam_pos, p.which == 0 ? p.light_w : 1.f, m, dx, dy, dz);
   const int b0 = p.which == 0 ? 1 : 0;
   if (p.which == 0) x[0] = p.T[g];
   pe_fwd(x, b0, dx, dy, dz);
@@ -329,7 +331,7 @@ __global__ void k_input_grad(RowArgs p) {
   }
   const float4 m = p.mean_op[g];
   float vx, vy, vz;
-  unit_dir(p.which == 0 ? p.light_pos : p.cam_pos, m, vx, vy, vz);
+  unit_dir(p.which == 0 ? p.light_pos : p.cam_pos, p.which == 0 ? p.light_w : 1.f, m, vx, vy, vz);
   const int b0 = p.which == 0 ? 1 : 0;
   float dw[3], dm[3];
   pe_bwd(dx + b0, vx, vy, vz, dw);
@@ -390,6 +392,7 @@ void run_mlp_backward(const MlpArgs& a, void* scratch, float* wred, cudaStream_t
   r.n = n; r.which = a.which; r.nh = nh; r.width = W; r.out_dim = m.out_dim; r.act = m.act;
   r.mean_op = a.mean_op; r.latent = a.latent; r.T = a.T;
   for (int i = 0; i < 3; ++i) { r.light_pos[i] = a.light_pos[i]; r.cam_pos[i] = a.cam_pos[i]; }
+  r.light_w = a.light_w;
   // parameter offsets: hidden layers (weights then biases), then the output layer
   const float* wl[8];
   const float* bl[8];

@@ -46,10 +46,25 @@ __device__ void light_view_rn(const float pL[3], const float tg[3], float R[9], 
   for (int i = 0; i < 3; ++i) t[i] = -dot3_rn(R[3 * i], R[3 * i + 1], R[3 * i + 2], pL[0], pL[1], pL[2]);
 }
 
+// Light view of either kind (Sec. 4.2 point, Sec. 4.5 directional): a
+// directional light looks along -dir from the eye target + dir (4 extent)
+// with pixel scale s = (min(W, H) / 2) / extent; returns s (0 for a point).
+__device__ float light_view_any_rn(const gs3_light& L, const float tg[3], int W, int H, float R[9], float t[3]) {
+  if (L.type != GS3_LIGHT_DIRECTIONAL) {
+    light_view_rn(L.pos, tg, R, t);
+    return 0.f;
+  }
+  const float reach = M_(4.f, L.extent);
+  const float e[3] = {A_(tg[0], M_(L.dir[0], reach)), A_(tg[1], M_(L.dir[1], reach)), A_(tg[2], M_(L.dir[2], reach))};
+  light_view_rn(e, tg, R, t);
+  return D_(M_(0.5f, (float)(W < H ? W : H)), L.extent);
+}
+
 struct View {
   float R[9], t[3];
   float fx, fy, cx, cy;
   int W, H;
+  float ortho;  // > 0: orthographic with this many pixels per world unit
 };
 
 __device__ void accurate_geometry(const float4 m, const float Rq[9], const float sv[3], const View& v,
@@ -64,11 +79,23 @@ __device__ bool project_rn(const float4 m, const float4 s, const float4 q, const
   float ty = A_(dot3_rn(R[3], R[4], R[5], m.x, m.y, m.z), v.t[1]);
   float tz = A_(dot3_rn(R[6], R[7], R[8], m.x, m.y, m.z), v.t[2]);
   if (!(tz > o.near_z)) return false;
-  float xz = D_(tx, tz), yz = D_(ty, tz);
-  float limx = M_(o.frustum, D_(M_(0.5f, (float)v.W), v.fx));
-  float limy = M_(o.frustum, D_(M_(0.5f, (float)v.H), v.fy));
-  if (xz < -limx || xz > limx || yz < -limy || yz > limy) return false;
-  float u = A_(M_(v.fx, xz), v.cx), vv = A_(M_(v.fy, yz), v.cy);
+  const bool ortho = v.ortho > 0.f;
+  float xz = 0.f, yz = 0.f, u, vv;
+  if (ortho) {  // u = s x + cx, v = s y + cy
+    const float limx = M_(o.frustum, D_(M_(0.5f, (float)v.W), v.ortho));
+    const float limy = M_(o.frustum, D_(M_(0.5f, (float)v.H), v.ortho));
+    if (tx < -limx || tx > limx || ty < -limy || ty > limy) return false;
+    u = A_(M_(v.ortho, tx), v.cx);
+    vv = A_(M_(v.ortho, ty), v.cy);
+  } else {
+    xz = D_(tx, tz);
+    yz = D_(ty, tz);
+    const float limx = M_(o.frustum, D_(M_(0.5f, (float)v.W), v.fx));
+    const float limy = M_(o.frustum, D_(M_(0.5f, (float)v.H), v.fy));
+    if (xz < -limx || xz > limx || yz < -limy || yz > limy) return false;
+    u = A_(M_(v.fx, xz), v.cx);
+    vv = A_(M_(v.fy, yz), v.cy);
+  }
 
   float n2 = A_(A_(A_(M_(q.x, q.x), M_(q.y, q.y)), M_(q.z, q.z)), M_(q.w, q.w));
   if (!(n2 > 0.f)) return false;
@@ -96,13 +123,21 @@ __device__ bool project_rn(const float4 m, const float4 s, const float4 q, const
 #pragma unroll
     for (int j = 0; j < 3; ++j)
       Sg[3 * i + j] = dot3_rn(Mm[3 * i], Mm[3 * i + 1], Mm[3 * i + 2], Mm[3 * j], Mm[3 * j + 1], Mm[3 * j + 2]);
-  float j00 = D_(v.fx, tz), j02 = -D_(M_(v.fx, xz), tz);
-  float j11 = D_(v.fy, tz), j12 = -D_(M_(v.fy, yz), tz);
   float T0[3], T1[3];
+  if (ortho) {  // J = [[s, 0, 0], [0, s, 0]]
 #pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    T0[k] = A_(M_(j00, R[k]), M_(j02, R[6 + k]));
-    T1[k] = A_(M_(j11, R[3 + k]), M_(j12, R[6 + k]));
+    for (int k = 0; k < 3; ++k) {
+      T0[k] = M_(v.ortho, R[k]);
+      T1[k] = M_(v.ortho, R[3 + k]);
+    }
+  } else {
+    float j00 = D_(v.fx, tz), j02 = -D_(M_(v.fx, xz), tz);
+    float j11 = D_(v.fy, tz), j12 = -D_(M_(v.fy, yz), tz);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      T0[k] = A_(M_(j00, R[k]), M_(j02, R[6 + k]));
+      T1[k] = A_(M_(j11, R[3 + k]), M_(j12, R[6 + k]));
+    }
   }
   float U0[3], U1[3];
 #pragma unroll
@@ -126,7 +161,7 @@ __device__ bool project_rn(const float4 m, const float4 s, const float4 q, const
   rec.r = make_int4((int)fmaxf(fx0, 0.f), (int)fmaxf(fy0, 0.f), (int)fminf(fx1, (float)(gx - 1)),
                     (int)fminf(fy1, (float)(gy - 1)));
   float depth;
-  if (pL) {
+  if (pL && !ortho) {
     float dx = S_(m.x, pL[0]), dy = S_(m.y, pL[1]), dz = S_(m.z, pL[2]);
     depth = Q_(dot3_rn(dx, dy, dz, dx, dy, dz));
   } else {
@@ -158,19 +193,28 @@ __device__ void accurate_geometry(const float4 m, const float Rq[9], const float
   const double tx = (double)R[0] * m.x + (double)R[1] * m.y + (double)R[2] * m.z + (double)v.t[0];
   const double ty = (double)R[3] * m.x + (double)R[4] * m.y + (double)R[5] * m.z + (double)v.t[1];
   const double tz = (double)R[6] * m.x + (double)R[7] * m.y + (double)R[8] * m.z + (double)v.t[2];
+  const bool ortho = v.ortho > 0.f;
   const double itz = 1.0 / tz;
-  const double u = (double)v.fx * (tx * itz) + (double)v.cx;
-  const double vv = (double)v.fy * (ty * itz) + (double)v.cy;
+  const double u = ortho ? (double)v.ortho * tx + (double)v.cx : (double)v.fx * (tx * itz) + (double)v.cx;
+  const double vv = ortho ? (double)v.ortho * ty + (double)v.cy : (double)v.fy * (ty * itz) + (double)v.cy;
   const float uh = (float)u, vh = (float)vv;
   const float ul = (float)(u - (double)uh), vl = (float)(vv - (double)vh);
-  const float fz = (float)tz, xz = (float)(tx * itz), yz = (float)(ty * itz);
-  const float j00 = v.fx / fz, j02 = -v.fx * xz / fz;
-  const float j11 = v.fy / fz, j12 = -v.fy * yz / fz;
   float T0[3], T1[3];
+  if (ortho) {
 #pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    T0[k] = fmaf(j00, R[k], j02 * R[6 + k]);
-    T1[k] = fmaf(j11, R[3 + k], j12 * R[6 + k]);
+    for (int k = 0; k < 3; ++k) {
+      T0[k] = v.ortho * R[k];
+      T1[k] = v.ortho * R[3 + k];
+    }
+  } else {
+    const float fz = (float)tz, xz = (float)(tx * itz), yz = (float)(ty * itz);
+    const float j00 = v.fx / fz, j02 = -v.fx * xz / fz;
+    const float j11 = v.fy / fz, j12 = -v.fy * yz / fz;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      T0[k] = fmaf(j00, R[k], j02 * R[6 + k]);
+      T1[k] = fmaf(j11, R[3 + k], j12 * R[6 + k]);
+    }
   }
   float P0[3], P1[3];  // P = T (R_q S)
 #pragma unroll
@@ -236,7 +280,8 @@ __device__ __forceinline__ float angular_gaussian(float hx, float hy, float hz, 
 struct PrepParams {
   SceneDev sc;
   View cam;
-  float light_pos[3];
+  gs3_light light;
+  float4 lh;  // homogeneous light (light_h)
   float cam_pos[3];
   float intensity;
   gs3_render_opts o;
@@ -249,13 +294,14 @@ struct PrepParams {
 };
 
 __global__ void __launch_bounds__(256) k_prep(PrepParams p) {
-  __shared__ float sR[9], st[3];
+  __shared__ float sR[9], st[3], sortho;
   if (threadIdx.x == 0) {
-    light_view_rn(p.light_pos, p.o.target, sR, st);
+    sortho = light_view_any_rn(p.light, p.o.target, p.cam.W, p.cam.H, sR, st);
     if (blockIdx.x == 0) {
       float* hv = reinterpret_cast<float*>(p.header + H_LIGHT_VIEW);
       for (int i = 0; i < 9; ++i) hv[i] = sR[i];
       for (int i = 0; i < 3; ++i) hv[9 + i] = st[i];
+      reinterpret_cast<float*>(p.header)[H_LIGHT_ORTHO] = sortho;
     }
   }
   __syncthreads();
@@ -272,11 +318,12 @@ __global__ void __launch_bounds__(256) k_prep(PrepParams p) {
   for (int i = 0; i < 9; ++i) lv.R[i] = sR[i];
 #pragma unroll
   for (int i = 0; i < 3; ++i) lv.t[i] = st[i];
+  lv.ortho = sortho;
 
 #pragma unroll
   for (int sp = 0; sp < 2; ++sp) {
     SplatRec rec;
-    bool vis = project_rn(m, s, q, sp ? lv : p.cam, p.o, p.gx, p.gy, sp ? p.light_pos : nullptr, gamma, rec);
+    bool vis = project_rn(m, s, q, sp ? lv : p.cam, p.o, p.gx, p.gy, sp ? p.light.pos : nullptr, gamma, rec);
     if (!vis) {
       rec.a = make_float4(0.f, 0.f, 0.f, 0.f);
       rec.b = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -289,8 +336,8 @@ __global__ void __launch_bounds__(256) k_prep(PrepParams p) {
     p.rect[sp][g] = rec.r;
   }
 
-  // ---- shading colour (Sec. 4.1) ----
-  float lx = p.light_pos[0] - m.x, ly = p.light_pos[1] - m.y, lz = p.light_pos[2] - m.z;
+  // ---- shading colour (Sec. 4.1); omega_i = normalize(L.xyz - L.w mu) ----
+  float lx = p.lh.x - p.lh.w * m.x, ly = p.lh.y - p.lh.w * m.y, lz = p.lh.z - p.lh.w * m.z;
   float d2 = lx * lx + ly * ly + lz * lz;
   float il = rsqrtf(d2);
   float wi[3] = {lx * il, ly * il, lz * il};
@@ -309,7 +356,7 @@ __global__ void __launch_bounds__(256) k_prep(PrepParams p) {
   float fs[3] = {0.f, 0.f, 0.f};
   float hx = wil[0] + wol[0], hy = wil[1] + wol[1], hz = wil[2] + wol[2];
   float hn2 = hx * hx + hy * hy + hz * hz;
-  if (hn2 >= 1e-24f) {
+  if (hn2 >= 1e-24f && !(p.o.ablate & GS3_ABLATE_SPECULAR)) {
     float ih = rsqrtf(hn2);
     hx *= ih; hy *= ih; hz *= ih;
     for (int j = 0; j < p.sc.k; ++j) {
@@ -325,7 +372,8 @@ __global__ void __launch_bounds__(256) k_prep(PrepParams p) {
       fs[0] += amp.x * G; fs[1] += amp.y * G; fs[2] += amp.z * G;
     }
   }
-  const float E = p.o.falloff ? p.intensity / d2 : p.intensity;
+  // a directional light's irradiance does not fall off (Sec. 4.5)
+  const float E = (p.o.falloff && p.lh.w != 0.f) ? p.intensity / d2 : p.intensity;
   const float4 rd = p.sc.albedo_d[g], rs = p.sc.albedo_s[g];
   p.shade[g] = make_float4(E * (rd.x * fd + rs.x * fs[0]), E * (rd.y * fd + rs.y * fs[1]),
                            E * (rd.z * fd + rs.z * fs[2]), 0.f);
@@ -337,7 +385,10 @@ void launch_prep(const FrameArgs& f, cudaStream_t s) {
   PrepParams p;
   p.sc = f.sc;
   for (int i = 0; i < 9; ++i) p.cam.R[i] = f.cam.R[i];
-  for (int i = 0; i < 3; ++i) { p.cam.t[i] = f.cam.t[i]; p.cam_pos[i] = f.cam.pos[i]; p.light_pos[i] = f.light.pos[i]; }
+  for (int i = 0; i < 3; ++i) { p.cam.t[i] = f.cam.t[i]; p.cam_pos[i] = f.cam.pos[i]; }
+  p.cam.ortho = 0.f;
+  p.light = f.light;
+  p.lh = light_h(f.light);
   p.cam.fx = f.cam.fx; p.cam.fy = f.cam.fy; p.cam.cx = f.cam.cx; p.cam.cy = f.cam.cy;
   p.cam.W = f.cam.width; p.cam.H = f.cam.height;
   p.intensity = f.light.intensity;

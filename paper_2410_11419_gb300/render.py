@@ -26,8 +26,11 @@ def camera_struct(cam) -> N.gs3_camera:
 
 
 def light_struct(light) -> N.gs3_light:
+    d = getattr(light, "dir", None)
+    d = (0.0, 0.0, 0.0) if d is None else np.asarray(d, dtype=np.float32).tolist()
     return N.gs3_light((C.c_float * 3)(*np.asarray(light.pos, dtype=np.float32).tolist()),
-                       float(light.intensity))
+                       float(light.intensity), int(getattr(light, "type", 0)), (C.c_float * 3)(*d),
+                       float(getattr(light, "extent", 0.0)))
 
 
 def opts_struct(ablate: int = 0, falloff: int = 1, **kw) -> N.gs3_render_opts:
@@ -101,6 +104,17 @@ class Renderer:
         s = torch.cuda.current_stream() if stream is None else stream
         N.gs3_render(self.scene.handle, camera_struct(cam), light_struct(light), opts, out, self.ws,
                      self.cap, s.cuda_stream)
+        return out
+
+    def render_environment(self, cam, lights, weights, opts=None, out=None, stream=None):
+        """Sec. 4.5: sum_l weights[l] * render(lights[l]) (directional lights)."""
+        opts = opts if opts is not None else opts_struct()
+        out = self.image if out is None else out
+        if getattr(self, "env_scratch", None) is None:
+            self.env_scratch = torch.empty_like(self.image)
+        s = torch.cuda.current_stream() if stream is None else stream
+        N.gs3_render_environment(self.scene.handle, camera_struct(cam), [light_struct(L) for L in lights],
+                                 weights, opts, out, self.env_scratch, self.ws, self.cap, s.cuda_stream)
         return out
 
     def render_stages(self, cam, light, stages: int, opts=None, out=None, stream=None):

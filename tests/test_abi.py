@@ -40,9 +40,9 @@ def test_struct_sizes_match_header_layout(libgs3):
     N = libgs3
     # field-for-field mirrors of the C structs (natural alignment)
     assert ctypes.sizeof(N.gs3_camera) == 4 * (9 + 3 + 3 + 4 + 2)
-    assert ctypes.sizeof(N.gs3_light) == 16
+    assert ctypes.sizeof(N.gs3_light) == 4 * (3 + 1 + 1 + 3 + 1)   # pos, intensity, type, dir, extent
     assert ctypes.sizeof(N.gs3_render_opts) == 4 * (7 + 3 + 3)
-    assert ctypes.sizeof(N.gs3_ws_header) == 4 * (8 + 12)
+    assert ctypes.sizeof(N.gs3_ws_header) == 4 * (8 + 12 + 1)
 
 
 def test_host_only_entry_points(libgs3):

@@ -156,3 +156,59 @@ def test_mlp_weight_gradients_match_finite_differences(oracle, fd_case):
                 assert abs(fd - ad) <= 1e-4 * max(abs(ad), abs(fd)) + 5e-9, (nm, layer, i, j, fd, ad)
                 checked += 1
     assert checked == 2 * 2 * len(scene.phi.weights)
+
+
+@pytest.fixture(scope="module")
+def fd_case_directional(oracle):
+    from oracle import torch_ref as TR
+    scene = synth.make_scene(23, 500, 4, "ball")
+    cam, _ = synth.camera_light_pair(23, 64, 64)
+    light = synth.directional_light(23)
+    target = oracle.render(synth.perturbed(scene, 24), cam, light)["img"]
+    L, img, grads, fr = TR.render_and_grad(scene, cam, light, target)
+    return scene, cam, light, target, L, img, grads, fr
+
+
+def test_forward_matches_c_oracle_directional(fd_case_directional):
+    """Sec. 4.5: the restatement's orthographic shadow splat and directional
+    shading equal the C oracle's frame."""
+    scene, cam, light, target, L, img, grads, fr = fd_case_directional
+    np.testing.assert_allclose(img, fr["img"], rtol=1e-12, atol=1e-13)
+    assert fr["light_ortho"] > 0 and fr["T"].min() < 0.9
+
+
+def test_gradients_match_finite_differences_directional(oracle, fd_case_directional):
+    """Central FD of the C oracle's loss under a directional light (same rules
+    as the point-light check)."""
+    scene, cam, light, target, L0, img, grads, fr0 = fd_case_directional
+    rng = np.random.default_rng(7)
+    visible = np.nonzero((fr0["cam_rect"][:, 0] >= 0) & (fr0["light_rect"][:, 0] >= 0))[0]
+    checked = 0
+    for name, attr, make_idx in GROUPS:
+        ncomp = 4 if name in ("rot", "shade_rot", "lobe_rot") else 3
+        for _ in range(2):
+            g = int(rng.choice(visible))
+            c = int(rng.integers(0, ncomp))
+            idx = make_idx(g, c)
+            if name == "logit":
+                ad = grads["logit"][g]
+            elif name.startswith("lobe_"):
+                ad = grads[name][idx]
+            else:
+                ad = grads[name][g, c]
+            vals, frames = [], []
+            for sgn in (1, -1):
+                sc = scene.copy()
+                arr = getattr(sc, attr)
+                arr[idx] = np.float32(float(arr[idx]) + sgn * H_FD)
+                Lv, fr = _loss_of(oracle, sc, cam, light, target)
+                h_eff = float(np.float32(float(getattr(scene, attr)[idx]) + sgn * H_FD)) - float(getattr(scene, attr)[idx])
+                vals.append((Lv, h_eff))
+                frames.append(fr)
+            if not (_same_decisions(frames[0], fr0, target) and _same_decisions(frames[1], fr0, target)):
+                continue
+            (Lp, hp), (Lm, hm) = vals
+            fd = (Lp - Lm) / (hp - hm)
+            assert abs(fd - ad) <= 1e-4 * max(abs(ad), abs(fd)) + 5e-9, f"{name}{idx}: FD {fd:.6e} AD {ad:.6e}"
+            checked += 1
+    assert checked >= 12, checked

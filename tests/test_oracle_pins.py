@@ -178,6 +178,9 @@ def test_shading_closed_form(oracle):
     # switching the inverse-square fall-off off gives E = I
     rgb2 = oracle.shade(sc, 0, cam, light, oracle.Opts(falloff=0))
     np.testing.assert_allclose(rgb2, want / E * 10.0, rtol=1e-12)
+    # the Lambertian-only first training stage (Sec. 4.4) drops every lobe
+    rgb3 = oracle.shade(sc, 0, cam, light, oracle.Opts(ablate=8))
+    np.testing.assert_allclose(rgb3, E * rho / math.pi, rtol=1e-12)
 
 
 # -- positional encoding, MLPs (Sec. 4.2, 4.3) --------------------------------
