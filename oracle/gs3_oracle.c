@@ -76,11 +76,17 @@ typedef struct {
     const float *b;                            /* biases, concatenated */
 } go_mlp;
 
+/* lobe_shared = 0: every spatial Gaussian has its own K lobes (lobe-major
+ * [j n + g] arrays).  lobe_shared = 1: a basis of K angular Gaussians (frame,
+ * sigma) shared by all spatial Gaussians, lobe_rot / lobe_sigma hold K
+ * entries, and each spatial Gaussian keeps its weights lobe_amp[j n + g]
+ * (the shared basis of Sec. 4.1). */
 typedef struct {
     int n, k;
     const float *mean_op, *scale, *rot, *shade_rot, *albedo_d, *albedo_s, *latent;
     const float *lobe_rot, *lobe_sigma, *lobe_amp;
     go_mlp phi, psi;
+    int lobe_shared;
 } go_scene;
 
 typedef struct {
@@ -396,8 +402,9 @@ static void shade_one(const go_scene *sc, int g, const go_camera *cam, const go_
         double h[3] = {hs.x / hn, hs.y / hn, hs.z / hn};
         for (int j = 0; j < sc->k; ++j) {
             size_t li = (size_t)j * sc->n + g;
-            double sig[3] = {sc->lobe_sigma[4 * li], sc->lobe_sigma[4 * li + 1], sc->lobe_sigma[4 * li + 2]};
-            double G = go_angular_gaussian(h, sc->lobe_rot + 4 * li, sig);
+            size_t ls = sc->lobe_shared ? (size_t)j : li; /* the lobe's frame and deviations */
+            double sig[3] = {sc->lobe_sigma[4 * ls], sc->lobe_sigma[4 * ls + 1], sc->lobe_sigma[4 * ls + 2]};
+            double G = go_angular_gaussian(h, sc->lobe_rot + 4 * ls, sig);
             for (int c = 0; c < 3; ++c) fs[c] += sc->lobe_amp[4 * li + c] * G;
         }
     }

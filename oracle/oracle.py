@@ -44,7 +44,7 @@ class _Scene(C.Structure):
     _fields_ = [("n", C.c_int), ("k", C.c_int)] + [
         (a, _FP) for a in ("mean_op", "scale", "rot", "shade_rot", "albedo_d", "albedo_s",
                            "latent", "lobe_rot", "lobe_sigma", "lobe_amp")] + [
-        ("phi", _MLP), ("psi", _MLP)]
+        ("phi", _MLP), ("psi", _MLP), ("lobe_shared", C.c_int)]
 
 
 class _Camera(C.Structure):
@@ -177,6 +177,7 @@ def c_scene(scene, keep: list) -> _Scene:
         setattr(s, a, _fp(arr))
     s.phi = _mlp(scene.phi, keep)
     s.psi = _mlp(scene.psi, keep)
+    s.lobe_shared = int(getattr(scene, "lobe_shared", False))
     return s
 
 

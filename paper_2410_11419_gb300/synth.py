@@ -40,7 +40,7 @@ _STREAMS = {
     "pos": 1, "pos_dir": 2, "pos_r": 3, "scale": 4, "rot": 5, "opacity": 6,
     "albedo": 7, "shade_rot": 8, "latent": 9, "lobe_axis": 10, "lobe_sharp": 11,
     "lobe_amp": 12, "phi": 13, "psi": 14, "camera": 15, "light": 16,
-    "shell_noise": 17, "perturb": 18, "environment": 19,
+    "shell_noise": 17, "perturb": 18, "environment": 19, "init": 20, "basis": 21,
 }
 
 RELU = 0
@@ -137,6 +137,7 @@ class Scene:
     lobe_amp: np.ndarray
     phi: MLP
     psi: MLP
+    lobe_shared: bool = False  # lobe_rot / lobe_sigma are one shared basis [K, 1, 4]
 
     ARRAYS = ("mean_op", "scale", "rot", "shade_rot", "albedo_d", "albedo_s",
               "latent", "lobe_rot", "lobe_sigma", "lobe_amp")
@@ -153,7 +154,8 @@ class Scene:
                   psi=MLP(self.psi.in_dim, self.psi.width, self.psi.n_hidden,
                           self.psi.out_dim, self.psi.act,
                           [w.copy() for w in self.psi.weights],
-                          [b.copy() for b in self.psi.biases]))
+                          [b.copy() for b in self.psi.biases]),
+                  lobe_shared=self.lobe_shared)
         return s
 
     def nbytes(self) -> int:
@@ -253,6 +255,25 @@ def make_scene(seed: int, n: int, k: int, kind: str = "ball", *, mlp_width: int 
     )
 
 
+def with_shared_basis(scene: Scene, seed: int) -> Scene:
+    """The scene with its lobes replaced by one basis of K anisotropic angular
+    Gaussians shared by every spatial Gaussian (Sec. 4.1): uniform random lobe
+    frames, sigma_x, sigma_y ~ U[0.3, 1], sigma_z = lambda^-1/2 with lambda
+    log-uniform in [1, 100]; each spatial Gaussian keeps its RGB weights."""
+    s = scene.copy()
+    k = s.k
+    g = rng(seed, "basis")
+    rot = _unit_quats(g, k)
+    sig = np.zeros((k, 1, 4))
+    sig[:, 0, 0] = g.uniform(0.3, 1.0, k)
+    sig[:, 0, 1] = g.uniform(0.3, 1.0, k)
+    sig[:, 0, 2] = np.exp(g.uniform(0.0, math.log(100.0), k)) ** -0.5
+    s.lobe_rot = np.ascontiguousarray(rot.reshape(k, 1, 4), dtype=np.float32)
+    s.lobe_sigma = np.ascontiguousarray(sig, dtype=np.float32)
+    s.lobe_shared = True
+    return s
+
+
 def look_at_camera(pos, target=(0.0, 0.0, 0.0), fov_y_deg: float = 40.0,
                    width: int = 128, height: int = 128) -> Camera:
     """Camera at pos looking at target, world +z up (+y when nearly parallel)."""
@@ -301,6 +322,25 @@ def environment_lights(seed: int, count: int, extent: float = 1.25):
     lights = [Light(pos=np.zeros(3, dtype=np.float32), intensity=1.0, type=1, dir=d, extent=float(np.float32(extent)))
               for d in dirs]
     return lights, weights
+
+
+def paper_initialisation(scene: Scene, seed: int) -> Scene:
+    """Copy with the appearance reset to the initial values of Sec. 4.4:
+    sigma_x = 0.5, sigma_y = 1, sigma_z ~ U[0.13, 0.69]; rho_d = rho_s = 1;
+    every lobe weight 0.5; shading and lobe frames aligned with the world
+    axes (identity quaternions).  Geometry, latent and MLPs are kept."""
+    s = scene.copy()
+    g = rng(seed, "init")
+    s.albedo_d[:, :3] = 1.0
+    s.albedo_s[:, :3] = 1.0
+    s.shade_rot[:] = np.array([1.0, 0.0, 0.0, 0.0], dtype=np.float32)
+    if s.k:
+        s.lobe_rot[:] = np.array([1.0, 0.0, 0.0, 0.0], dtype=np.float32)
+        s.lobe_sigma[..., 0] = 0.5
+        s.lobe_sigma[..., 1] = 1.0
+        s.lobe_sigma[..., 2] = g.uniform(0.13, 0.69, s.lobe_sigma.shape[:2]).astype(np.float32)
+        s.lobe_amp[..., :3] = 0.5
+    return s
 
 
 def perturbed(scene: Scene, seed: int) -> Scene:
