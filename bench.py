@@ -553,6 +553,26 @@ def main():
                 "fwd_bwd_ms": float(fb.mean()), "bwd_ms": float(bw.mean()),
                 "fwd_bwd_per_s": K / (fb.sum() / 1e3),
                 "note": "gs3_render + gs3_render_backward per frame, FP32 MLPs, dL/dI = sign(I - target)"}
+            # one training iteration (Sec. 4.4): render, L1 + D-SSIM loss, backward, Adam on every group
+            from paper_2410_11419_gb300.train import Trainer
+            del rd2
+            tr = Trainer(ds2, a.res, a.res, cap, device=dev)
+            for s_ in range(2):
+                tr.step(*pairs[s_ % 100], tgt)
+            torch.cuda.synchronize()
+            te = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(K)]
+            for s_ in range(K):
+                flush.zero_()
+                te[s_][0].record(stream)
+                tr.step(*pairs[(a.warmup + s_) % 100], tgt)
+                te[s_][1].record(stream)
+            torch.cuda.synchronize()
+            tr.rd.check()
+            it_ms = np.array([x[0].elapsed_time(x[1]) for x in te])
+            plain["differentiation"]["train_iter_ms"] = float(it_ms.mean())
+            plain["differentiation"]["train_iters_per_s"] = K / (it_ms.sum() / 1e3)
+            del tr
+            rd2 = None
         del rd2
         ds2.close()
 

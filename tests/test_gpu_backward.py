@@ -86,7 +86,7 @@ def test_backward_matches_gradient_oracle(gs3, oracle, make, res, seed):
     assert len(rep) == 14
 
 
-@pytest.mark.parametrize("ablate", [1, 2, 4])
+@pytest.mark.parametrize("ablate", [1, 2, 4, 8])
 def test_backward_with_ablations(gs3, oracle, ablate):
     from oracle import torch_ref as TR
     scene = synth.make_scene(9, 400, 3, "ball")

@@ -115,7 +115,7 @@ def test_frame_parity(gs3, oracle, name, make, seed, w, h):
     check_float_stages(g, fr)
 
 
-@pytest.mark.parametrize("ablate", [1, 2, 4, 7])
+@pytest.mark.parametrize("ablate", [1, 2, 4, 7, 8])
 def test_ablations(gs3, oracle, ablate):
     scene = synth.tiny_scene(0)
     cam, light = synth.camera_light_pair(1, 96, 96)
