@@ -34,7 +34,7 @@ sys.path.insert(0, ROOT)
 # one ncu capture of the kernel, valid only while its sources are unchanged:
 # kernel -> (bytes, SHA-256 of the concatenated sources, the summary file).
 PROFILED_TRAFFIC = {
-    "k_shadow": (487.5e6, "e3ddcd0e494d6169bf8fd1232faad1c20ef2016c57d74b367fe64eb9abb62b79",
+    "k_shadow": (579.2e6, "b8c5b4d18258a3bb580df7fa4fe029d39f24c754029b99b0e3bcf7fe1fe51ce4",
                  "profiles/k_shadow_object_300k_800.md"),
 }
 TRAFFIC_SOURCES = {
@@ -226,12 +226,16 @@ KSWEEP = (1, 2, 4, 8, 16)
 def lobe_sweep(a, dev, np, torch, N, R, synth, frames=10):
     """Frames/s and K1 (k_prep) time of the object workload (BF16 MLPs, one
     frame at a time, L2 flushed) for K = 1, 2, 4, 8, 16 angular Gaussians per
-    spatial Gaussian (the paper's lobe-count ablation)."""
+    spatial Gaussian (the paper's lobe-count ablation), and for a basis of 8
+    lobes shared by every Gaussian ("8_shared")."""
     pairs = [synth.camera_light_pair(i, a.res, a.res) for i in range(frames)]
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     out = {}
-    for k in KSWEEP:
-        sc = synth.object_scene(0, n=a.n, k=k)
+    for k in KSWEEP + ("8_shared",):
+        if k == "8_shared":  # the paper's main configuration: a basis of 8 lobes shared by all Gaussians
+            sc = synth.with_shared_basis(synth.object_scene(0, n=a.n, k=8), 1)
+        else:
+            sc = synth.object_scene(0, n=a.n, k=k)
         ds = R.DeviceScene(sc, device=dev, mlp_dtype=N.GS3_MLP_BF16)
         rd = R.Renderer(ds, a.res, a.res, 40_000_000 if a.n <= 300_000 else int(a.n * 140), device=dev)
         for i in range(2):

@@ -94,6 +94,9 @@ typedef struct {
     const float *lobe_rot, *lobe_sigma, *lobe_amp;
     gs3_mlp_desc phi, psi;
     int32_t mlp_dtype; /* GS3_MLP_FP32, GS3_MLP_BF16 or GS3_MLP_FP8_E4M3 */
+    int32_t lobe_shared; /* 1: lobe_rot and lobe_sigma are one basis of K angular Gaussians
+                            shared by every spatial Gaussian (K entries each, Sec. 4.1);
+                            lobe_amp stays per Gaussian.  0: K lobes per Gaussian. */
 } gs3_scene_desc;
 
 /* Pinhole camera, host struct.  R: world -> camera rotation rows (x right,

@@ -43,7 +43,8 @@ class gs3_scene_desc(C.Structure):
     _fields_ = [("n", C.c_int32), ("k", C.c_int32)] + [
         (a, C.c_void_p) for a in ("mean_op", "scale", "rot", "shade_rot", "albedo_d", "albedo_s",
                                   "latent", "lobe_rot", "lobe_sigma", "lobe_amp")] + [
-        ("phi", gs3_mlp_desc), ("psi", gs3_mlp_desc), ("mlp_dtype", C.c_int32)]
+        ("phi", gs3_mlp_desc), ("psi", gs3_mlp_desc), ("mlp_dtype", C.c_int32),
+                ("lobe_shared", C.c_int32)]
 
 
 class gs3_camera(C.Structure):

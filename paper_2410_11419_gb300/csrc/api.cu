@@ -134,6 +134,7 @@ Workspace plan_workspace(int n, int width, int height, size_t cap) {
     b.scan_part = P.take(4 * scan_words);
   }
   L.partial = P.take(8 * cap);
+  L.tile_order = P.take(4 * (size_t)L.ntiles);
   L.shade = P.take(16 * N);
   L.T = P.take(4 * N);
   L.Tp = P.take(4 * N);
@@ -206,6 +207,11 @@ gs3_status gs3_create_scene(const gs3_scene_desc* d, gs3_scene** out) {
   v.phi = {d->phi.in_dim, d->phi.width, d->phi.n_hidden, d->phi.out_dim, d->phi.act, d->phi.w, d->phi.b};
   v.psi = {d->psi.in_dim, d->psi.width, d->psi.n_hidden, d->psi.out_dim, d->psi.act, d->psi.w, d->psi.b};
   v.mlp_dtype = d->mlp_dtype;
+  if (d->lobe_shared != 0 && d->lobe_shared != 1) {
+    delete s;
+    return fail(GS3_ERR_INVALID_ARG, "gs3_create_scene: lobe_shared must be 0 or 1");
+  }
+  v.lobe_shared = d->lobe_shared;
   if (d->mlp_dtype != GS3_MLP_FP32) {
     for (int w = 0; w < 2; ++w) {
       const MlpDev& m = w == 0 ? v.phi : v.psi;

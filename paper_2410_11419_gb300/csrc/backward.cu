@@ -247,6 +247,7 @@ struct ShadowBwdParams {
   const SplatRec* rrec;
   const uint32_t* order;
   const uint32_t* kbound;
+  const uint32_t* tile_order;  // the forward's launch order of the light tiles
   const uint8_t* pass_mask;
   const float* light_final;
   const float* dT;   // by index
@@ -306,7 +307,7 @@ __device__ __forceinline__ void flush_grad(float* dst, const float (&g)[8], int 
 __global__ void __launch_bounds__(kBThreads, 8) k_shadow_bwd(ShadowBwdParams p) {
   extern __shared__ float4 smem_raw[];
   ShadowBwdSmem& S = *reinterpret_cast<ShadowBwdSmem*>(smem_raw);
-  const int tile = blockIdx.x, tx = tile % p.gx, ty = tile / p.gx, t = threadIdx.x;
+  const int tile = (int)p.tile_order[blockIdx.x], tx = tile % p.gx, ty = tile / p.gx, t = threadIdx.x;
   const int lane = t & 31, warp = t >> 5;
   const uint32_t wbit = 1u << warp;
   const int lxi = (warp & 1) * 8 + (lane & 7), lyi = (warp >> 1) * 8 + (lane >> 3);
@@ -547,10 +548,11 @@ struct PrepBwdParams {
   gs3_grads out;
 };
 
-__global__ void __launch_bounds__(128) k_prep_bwd(PrepBwdParams p) {
-  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+// One Gaussian of K1b.  With a shared lobe basis the frame and deviation
+// gradients of lobe j go to the block's accumulators sacc[8 j + 0..6]
+// (rotation 4, sigma 3) instead of per-Gaussian outputs.
+__device__ __forceinline__ void prep_bwd_one(const PrepBwdParams& p, int g, float* sacc) {
   const int n = p.sc.n;
-  if (g >= n) return;
   const float4 m = p.sc.mean_op[g], s = p.sc.scale[g];
   const float gamma = 1.f / (1.f + expf(-m.w));
   const float* gc = p.cam_geom + (size_t)kGeom * g;
@@ -607,8 +609,9 @@ __global__ void __launch_bounds__(128) k_prep_bwd(PrepBwdParams p) {
     for (int j = 0; j < K; ++j) {
       const size_t li = (size_t)j * n + g;
       float Rl[9], ql[4], qllen;
-      quat_rot(p.sc.lobe_rot[li], Rl, ql, qllen);
-      const float4 sig = p.sc.lobe_sigma[li];
+      const size_t ls = p.sc.lobe_shared ? (size_t)j : li;
+      quat_rot(p.sc.lobe_rot[ls], Rl, ql, qllen);
+      const float4 sig = p.sc.lobe_sigma[ls];
       const float4 amp = p.sc.lobe_amp[li];
       const float hx = Rl[0] * h[0] + Rl[3] * h[1] + Rl[6] * h[2];
       const float hy = Rl[1] * h[0] + Rl[4] * h[1] + Rl[7] * h[2];
@@ -645,10 +648,12 @@ __global__ void __launch_bounds__(128) k_prep_bwd(PrepBwdParams p) {
         dhl[1] = dF * (dF_dsxy * hy / sxy + theta * theta * is2 * 2.f * hy / (sig.y * sig.y));
         dhl[2] = dF * 2.f * theta * th_z * Pq * is2;
       }
-      p.out.lobe_sigma[4 * li + 0] = dsx;
-      p.out.lobe_sigma[4 * li + 1] = dsy;
-      p.out.lobe_sigma[4 * li + 2] = dsz;
-      p.out.lobe_sigma[4 * li + 3] = 0.f;
+      if (!p.sc.lobe_shared) {
+        p.out.lobe_sigma[4 * li + 0] = dsx;
+        p.out.lobe_sigma[4 * li + 1] = dsy;
+        p.out.lobe_sigma[4 * li + 2] = dsz;
+        p.out.lobe_sigma[4 * li + 3] = 0.f;
+      }
       // hl = Rl^T h: dh += Rl dhl; dRl[k][i] += h_k dhl_i
       float dRl[9];
       for (int k = 0; k < 3; ++k) {
@@ -656,14 +661,22 @@ __global__ void __launch_bounds__(128) k_prep_bwd(PrepBwdParams p) {
         for (int i = 0; i < 3; ++i) dRl[3 * k + i] = h[k] * dhl[i];
       }
       const float4 dql = quat_bwd(dRl, ql, qllen);
-      reinterpret_cast<float4*>(p.out.lobe_rot)[li] = dql;
+      if (p.sc.lobe_shared) {
+        float* a = sacc + 8 * j;
+        atomicAdd(a + 0, dql.x); atomicAdd(a + 1, dql.y); atomicAdd(a + 2, dql.z); atomicAdd(a + 3, dql.w);
+        atomicAdd(a + 4, dsx); atomicAdd(a + 5, dsy); atomicAdd(a + 6, dsz);
+      } else {
+        reinterpret_cast<float4*>(p.out.lobe_rot)[li] = dql;
+      }
     }
   } else {
     for (int j = 0; j < K; ++j) {
       const size_t li = (size_t)j * n + g;
       reinterpret_cast<float4*>(p.out.lobe_amp)[li] = make_float4(0, 0, 0, 0);
-      reinterpret_cast<float4*>(p.out.lobe_sigma)[li] = make_float4(0, 0, 0, 0);
-      reinterpret_cast<float4*>(p.out.lobe_rot)[li] = make_float4(0, 0, 0, 0);
+      if (!p.sc.lobe_shared) {
+        reinterpret_cast<float4*>(p.out.lobe_sigma)[li] = make_float4(0, 0, 0, 0);
+        reinterpret_cast<float4*>(p.out.lobe_rot)[li] = make_float4(0, 0, 0, 0);
+      }
     }
   }
   float dE = 0.f, dfd = 0.f;
@@ -721,6 +734,25 @@ __global__ void __launch_bounds__(128) k_prep_bwd(PrepBwdParams p) {
   reinterpret_cast<float4*>(p.out.latent)[g] =
       make_float4(mi[6] + mi[18], mi[7] + mi[19], mi[8] + mi[20], mi[9] + mi[21]);
   reinterpret_cast<float4*>(p.out.latent)[n + g] = make_float4(mi[10] + mi[22], mi[11] + mi[23], 0.f, 0.f);
+}
+
+__global__ void __launch_bounds__(128) k_prep_bwd(PrepBwdParams p) {
+  __shared__ float sacc[8 * kMaxLobes];
+  const bool shared = p.sc.lobe_shared != 0;
+  if (shared) {
+    for (int i = threadIdx.x; i < 8 * p.sc.k; i += blockDim.x) sacc[i] = 0.f;
+    __syncthreads();
+  }
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g < p.sc.n) prep_bwd_one(p, g, sacc);
+  if (shared) {  // the block's sums of the shared basis gradients
+    __syncthreads();
+    for (int i = threadIdx.x; i < 8 * p.sc.k; i += blockDim.x) {
+      const int j = i >> 3, c = i & 7;
+      if (c < 4) atomicAdd(p.out.lobe_rot + 4 * j + c, sacc[i]);
+      else if (c < 7) atomicAdd(p.out.lobe_sigma + 4 * j + (c - 4), sacc[i]);
+    }
+  }
 }
 
 // scatter the reduced MLP parameter gradients into the (weights, biases) layout
@@ -824,6 +856,7 @@ gs3_status run_backward(const FrameArgs& f, const float* dimg, void* bws, size_t
     p.order = at<uint32_t>(ws, L.sp[1].sv[1]);
     p.kbound = at<uint32_t>(ws, L.sp[1].tv[1 - fin]);
     p.pass_mask = reinterpret_cast<const uint8_t*>(at<float>(ws, L.sp[1].tk[1 - fin]));
+    p.tile_order = at<uint32_t>(ws, L.tile_order);
     p.light_final = at<float>(ws, L.light_final);
     p.dT = dT;
     p.den = at<float>(ws, L.shadow_den);
@@ -860,6 +893,10 @@ gs3_status run_backward(const FrameArgs& f, const float* dimg, void* bws, size_t
     p.color = color;
     p.mlp_in = mlp_in;
     p.out = out;
+    if (f.sc.lobe_shared && f.sc.k > 0) {  // accumulated with atomics
+      cudaMemsetAsync(out.lobe_rot, 0, 16ull * f.sc.k, s);
+      cudaMemsetAsync(out.lobe_sigma, 0, 16ull * f.sc.k, s);
+    }
     k_prep_bwd<<<(n + 127) / 128, 128, 0, s>>>(p);
     count_launch();
   }

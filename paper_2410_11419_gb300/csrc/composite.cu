@@ -69,6 +69,7 @@ struct ShadowParams {
   const SplatRec* rrec;
   const uint32_t* off;
   const uint32_t* kbound;
+  const uint32_t* tile_order;  // block b renders tile tile_order[b]
   uint8_t* pass_mask;  // per list entry: warps with a passing pixel (written as receiver)
   float2* partial;
   float* light_final;
@@ -87,7 +88,7 @@ struct ShadowSmem {
 __global__ void __launch_bounds__(kShadowThreads, 8) k_shadow(ShadowParams p) {
   extern __shared__ float4 smem_raw[];
   ShadowSmem& S = *reinterpret_cast<ShadowSmem*>(smem_raw);
-  const int tile = blockIdx.x;
+  const int tile = (int)p.tile_order[blockIdx.x];
   const int tx = tile % p.gx, ty = tile / p.gx;
   const float ox = (float)(tx * kTile), oy = (float)(ty * kTile);
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
@@ -327,7 +328,59 @@ __global__ void __launch_bounds__(256) k_camera(CamParams p) {
   }
 }
 
+// Launch order of the light tiles: longest list first, so that the last
+// blocks to start are the short ones and the final partial wave stays short
+// (a longest-processing-time-first schedule; the tiles' results do not depend
+// on the order).  One block sorts packed 32-bit keys (inverted list length
+// capped to 19 bits | 13-bit tile index, so ties keep tile order) with a
+// bitonic network in shared memory.
+__global__ void __launch_bounds__(1024) k_tile_order(const uint32_t* __restrict__ tile_start, int ntiles,
+                                                     uint32_t* __restrict__ order) {
+  __shared__ uint32_t key[kOrderTiles];
+  constexpr uint32_t kLenMax = (1u << 19) - 1u;
+  int np = 1;
+  while (np < ntiles) np <<= 1;
+  for (int i = threadIdx.x; i < np; i += blockDim.x) {
+    if (i < ntiles) {
+      const uint32_t len = min(tile_start[i + 1] - tile_start[i], kLenMax);
+      key[i] = ((kLenMax - len) << 13) | (uint32_t)i;
+    } else {
+      key[i] = 0xFFFFFFFFu;  // padding sorts last
+    }
+  }
+  __syncthreads();
+  for (int k = 2; k <= np; k <<= 1)
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = threadIdx.x; i < np; i += blockDim.x) {
+        const int l = i ^ j;
+        if (l > i) {
+          const uint32_t a = key[i], b = key[l];
+          const bool up = (i & k) == 0;
+          if ((a > b) == up) { key[i] = b; key[l] = a; }
+        }
+      }
+      __syncthreads();
+    }
+  for (int i = threadIdx.x; i < ntiles; i += blockDim.x) order[i] = key[i] & 0x1FFFu;
+}
+
+__global__ void k_identity_order(uint32_t* order, int ntiles) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < ntiles) order[i] = (uint32_t)i;
+}
+
 }  // namespace
+
+void launch_tile_order(const FrameArgs& f, cudaStream_t s) {
+  const Workspace& L = *f.L;
+  uint32_t* order = at<uint32_t>(f.ws, L.tile_order);
+  if (L.ntiles <= kOrderTiles) {
+    k_tile_order<<<1, 1024, 0, s>>>(at<uint32_t>(f.ws, L.sp[1].tile_start), L.ntiles, order);
+  } else {
+    k_identity_order<<<(L.ntiles + 255) / 256, 256, 0, s>>>(order, L.ntiles);
+  }
+  count_launch();
+}
 
 void launch_shadow_composite(const FrameArgs& f, cudaStream_t s) {
   const SplatBufs& b = f.L->sp[1];
@@ -344,7 +397,9 @@ void launch_shadow_composite(const FrameArgs& f, cudaStream_t s) {
   k_occluder_bound<<<blocks, 256, 0, s>>>(at<uint32_t>(ws, b.tk[fin]), at<uint32_t>(ws, b.tile_start), dl, header,
                                           f.opts.shadow_bias, kb, (uint32_t)f.L->cap);
   count_launch(2);
+  launch_tile_order(f, s);
   ShadowParams p;
+  p.tile_order = at<uint32_t>(ws, f.L->tile_order);
   p.list = at<uint32_t>(ws, b.tv[fin]);
   p.tile_start = at<uint32_t>(ws, b.tile_start);
   p.rrec = at<SplatRec>(ws, b.rrec);

@@ -361,13 +361,14 @@ __global__ void __launch_bounds__(256) k_prep(PrepParams p) {
     hx *= ih; hy *= ih; hz *= ih;
     for (int j = 0; j < p.sc.k; ++j) {
       const size_t li = (size_t)j * n + g;
+      const size_t ls = p.sc.lobe_shared ? (size_t)j : li;  // frame and deviations of lobe j
       float Rl[9];
-      quat_mat(p.sc.lobe_rot[li], Rl);
+      quat_mat(p.sc.lobe_rot[ls], Rl);
       // components of h' in the lobe frame: columns of Rl are the lobe axes
       float ax = Rl[0] * hx + Rl[3] * hy + Rl[6] * hz;
       float ay = Rl[1] * hx + Rl[4] * hy + Rl[7] * hz;
       float az = Rl[2] * hx + Rl[5] * hy + Rl[8] * hz;
-      float G = angular_gaussian(ax, ay, az, p.sc.lobe_sigma[li]);
+      float G = angular_gaussian(ax, ay, az, p.sc.lobe_sigma[ls]);
       float4 amp = p.sc.lobe_amp[li];
       fs[0] += amp.x * G; fs[1] += amp.y * G; fs[2] += amp.z * G;
     }

@@ -69,6 +69,7 @@ class DeviceScene:
             setattr(d, nm, N.gs3_mlp_desc(m.in_dim, m.width, m.n_hidden, m.out_dim, m.act,
                                           self.t[nm + "_w"].data_ptr(), self.t[nm + "_b"].data_ptr()))
         d.mlp_dtype = mlp_dtype
+        d.lobe_shared = int(getattr(scene, "lobe_shared", False))
         self.desc = d
         self.handle = N.gs3_create_scene(d)
 

@@ -43,7 +43,7 @@ def _as_ref_layout(scene, ref):
         "albedo_s": np.concatenate([ref["albedo_s"], np.zeros((n, 1))], 1),
         "latent": np.stack([ref["latent"][:, :4], np.concatenate([ref["latent"][:, 4:], np.zeros((n, 2))], 1)]),
         "lobe_rot": ref["lobe_rot"],
-        "lobe_sigma": np.concatenate([ref["lobe_sigma"], np.zeros((k, n, 1))], 2),
+        "lobe_sigma": np.concatenate([ref["lobe_sigma"], np.zeros(ref["lobe_sigma"].shape[:2] + (1,))], 2),
         "lobe_amp": np.concatenate([ref["lobe_amp"], np.zeros((k, n, 1))], 2),
         "phi_w": ref["phi_w"], "phi_b": ref["phi_b"], "psi_w": ref["psi_w"], "psi_b": ref["psi_b"],
     }
