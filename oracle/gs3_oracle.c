@@ -219,10 +219,15 @@ typedef struct { uint32_t key; int x0, y0, x1, y1; float u, v; } keyrec;
 static uint32_t f32_bits(float f) { uint32_t u; memcpy(&u, &f, 4); return u; }
 
 /* One Gaussian through the FP32 recipe.  Returns 0 when culled. */
-static int key_recipe(const float m[3], const float s[3], const float q[4],
+/* -ln(alpha_min) as FP32, the one transcendental of the rectangle rule,
+ * taken once per frame from the FP32 option in double precision */
+static float neg_log_amin(const go_opts *o) { return (float)(-log((double)o->alpha_min)); }
+
+static int key_recipe(const float m[4], const float s[3], const float q[4],
                       const float R[9], const float t[3], float fx, float fy, float cx, float cy,
                       int W, int H, const go_opts *o, const float *pL, float ortho, keyrec *out)
 {
+    const float nl_amin = neg_log_amin(o);
     out->key = 0xFFFFFFFFu; out->x0 = -1; out->y0 = -1; out->x1 = -2; out->y1 = -2;
     out->u = 0.0f; out->v = 0.0f;
     float tx = R[0] * m[0] + R[1] * m[1] + R[2] * m[2] + t[0];
@@ -299,6 +304,19 @@ static int key_recipe(const float m[3], const float s[3], const float q[4],
     int gx = (W + o->tile - 1) / o->tile, gy = (H + o->tile - 1) / o->tile;
     float fx0 = floorf((u - r) / ts), fx1 = floorf((u + r) / ts);
     float fy0 = floorf((v - r) / ts), fy1 = floorf((v + r) / ts);
+    /* Tiles no pixel can reach with alpha >= alpha_min are dropped: that
+     * region is the ellipse d^T Sigma^-1 d <= 2 ln(gamma / alpha_min), inside
+     * the box |dx| <= sqrt(r2 Sigma_xx), |dy| <= sqrt(r2 Sigma_yy) for any
+     * r2 >= 2 ln(gamma / alpha_min).  With ln(gamma) = ln sigmoid(l) <= min(0, l),
+     * r2 = 2 (min(0, l) - ln alpha_min) is such a bound without a
+     * transcendental of per-Gaussian data; r2 <= 0 means no pixel can pass. */
+    float r2 = 2.0f * (fminf(0.0f, m[3]) + nl_amin);
+    if (!(r2 > 0.0f)) return 0;
+    float hx = sqrtf(r2 * a), hy = sqrtf(r2 * c);
+    fx0 = fmaxf(fx0, floorf((u - hx) / ts));
+    fx1 = fminf(fx1, floorf((u + hx) / ts));
+    fy0 = fmaxf(fy0, floorf((v - hy) / ts));
+    fy1 = fminf(fy1, floorf((v + hy) / ts));
     if (fx1 < 0.0f || fx0 > (float)(gx - 1) || fy1 < 0.0f || fy0 > (float)(gy - 1)) return 0;
     out->x0 = (int)fmaxf(fx0, 0.0f);
     out->x1 = (int)fminf(fx1, (float)(gx - 1));
@@ -952,7 +970,7 @@ void go_shade(const go_scene *sc, int g, const go_camera *cam, const go_light *L
 }
 
 /* FP32 recipe of one Gaussian (for pins on the key recipe). */
-int go_key_recipe(const float m[3], const float s[3], const float q[4], const float R[9],
+int go_key_recipe(const float m[4], const float s[3], const float q[4], const float R[9],
                   const float t[3], float fx, float fy, float cx, float cy, int W, int H,
                   const go_opts *o, const float *pL, float ortho, uint32_t *key, int32_t rect[4],
                   float uv[2])

@@ -286,8 +286,10 @@ def shade(scene, g: int, cam, light, opts: Opts | None = None) -> np.ndarray:
 
 def key_recipe(m, s, q, R, t, fx, fy, cx, cy, W, H, opts: Opts | None = None, light_pos=None,
                ortho: float = 0.0):
+    """FP32 key recipe of one Gaussian; m = (x, y, z, opacity logit)."""
     f32 = lambda a: np.ascontiguousarray(a, dtype=np.float32)
     m, s, q, R, t = f32(m), f32(s), f32(q), f32(np.asarray(R).reshape(-1)), f32(t)
+    assert m.size == 4, "mean and opacity logit"
     key = C.c_uint32()
     rect = np.zeros(4, dtype=np.int32)
     uv = np.zeros(2, dtype=np.float32)

@@ -288,29 +288,79 @@ def test_keys_are_fp32_depths(oracle, tiny_frame):
     assert not np.any(fr["cam_key"][~vis] != 0xFFFFFFFF)
 
 
-def test_rects_cover_three_sigma(oracle, tiny_frame):
-    """Each rectangle is the set of 16x16 tiles touched by the square of half
-    side ceil(3 sqrt(lambda_max)) around the mean (FP64 check, 1-tile slack at
+def _sigma2d(fr, nm):
+    con = fr[f"{nm}_conic"]
+    det = con[:, 0] * con[:, 2] - con[:, 1] ** 2
+    return con[:, 2] / det, -con[:, 1] / det, con[:, 0] / det   # Sigma_2D = inverse(conic)
+
+
+def test_rects_are_three_sigma_square_cut_to_alpha_box(oracle, tiny_frame):
+    """Each rectangle is the set of 16x16 tiles touched both by the square of
+    half side ceil(3 sqrt(lambda_max)) around the mean and by the box
+    |dx| <= sqrt(r2 Sigma_xx), |dy| <= sqrt(r2 Sigma_yy) with
+    r2 = 2 (min(0, logit) - ln alpha_min) (FP64 check, 1-tile slack at
     rounding boundaries)."""
     sc, cam, light, fr = tiny_frame
-    con = fr["cam_conic"]
-    det = con[:, 0] * con[:, 2] - con[:, 1] ** 2
-    # Sigma_2D = inverse(conic)
-    a, b, c = con[:, 2] / det, -con[:, 1] / det, con[:, 0] / det
+    a, b, c = _sigma2d(fr, "cam")
     mid = 0.5 * (a + c)
     lam = mid + np.sqrt(np.maximum(0.1, mid * mid - (a * c - b * b)))
     r = np.ceil(3 * np.sqrt(lam))
+    logit = sc.mean_op[:, 3].astype(np.float64)
+    r2 = 2 * (np.minimum(0.0, logit) - math.log(float(np.float32(1 / 255))))
+    hx, hy = np.sqrt(r2 * a), np.sqrt(r2 * c)
     u, v = fr["cam_uv"][:, 0], fr["cam_uv"][:, 1]
     vis = fr["cam_rect"][:, 0] >= 0
     gx, gy = fr["gx"], fr["gy"]
-    x0 = np.clip(np.floor((u - r) / 16), 0, gx - 1)
-    x1 = np.clip(np.floor((u + r) / 16), 0, gx - 1)
-    y0 = np.clip(np.floor((v - r) / 16), 0, gy - 1)
-    y1 = np.clip(np.floor((v + r) / 16), 0, gy - 1)
+    x0 = np.clip(np.maximum(np.floor((u - r) / 16), np.floor((u - hx) / 16)), 0, gx - 1)
+    x1 = np.clip(np.minimum(np.floor((u + r) / 16), np.floor((u + hx) / 16)), 0, gx - 1)
+    y0 = np.clip(np.maximum(np.floor((v - r) / 16), np.floor((v - hy) / 16)), 0, gy - 1)
+    y1 = np.clip(np.minimum(np.floor((v + r) / 16), np.floor((v + hy) / 16)), 0, gy - 1)
     R = fr["cam_rect"][vis]
     for got, want in ((R[:, 0], x0[vis]), (R[:, 2], x1[vis]), (R[:, 1], y0[vis]), (R[:, 3], y1[vis])):
         assert np.all(np.abs(got - want) <= 1)
         assert np.mean(got == want) > 0.97
+    # the cut is real: some rectangles are smaller than the 3-sigma square
+    sq = (np.clip(np.floor((u + r) / 16), 0, gx - 1) - np.clip(np.floor((u - r) / 16), 0, gx - 1))[vis]
+    assert np.any(R[:, 2] - R[:, 0] < sq)
+
+
+@pytest.mark.parametrize("splat", ["cam", "light"])
+def test_rects_hold_every_passing_pixel(oracle, tiny_frame, splat):
+    """Dropping tiles changes nothing: every pixel where a Gaussian has
+    alpha >= 1/255 inside its 3-sigma square (FP64, exact opacity) lies in a
+    tile of its rectangle, in both splats."""
+    sc, cam, light, fr = tiny_frame
+    con, uv, rect = fr[f"{splat}_conic"], fr[f"{splat}_uv"], fr[f"{splat}_rect"]
+    a, b, c = _sigma2d(fr, splat)
+    mid = 0.5 * (a + c)
+    lam = mid + np.sqrt(np.maximum(0.1, mid * mid - (a * c - b * b)))
+    rr = np.ceil(3 * np.sqrt(lam))
+    gam = fr["opacity"]
+    amin = float(np.float32(1 / 255))
+    W, H = cam.width, cam.height
+    checked = 0
+    for g in range(sc.n):
+        if rect[g, 0] < 0 and not np.isfinite(rr[g]):
+            continue
+        u, v = uv[g]
+        xs = np.arange(max(0, int(u - rr[g]) - 1), min(W, int(u + rr[g]) + 2)) + 0.5
+        ys = np.arange(max(0, int(v - rr[g]) - 1), min(H, int(v + rr[g]) + 2)) + 0.5
+        if xs.size == 0 or ys.size == 0:
+            continue
+        X, Y = np.meshgrid(xs, ys)
+        dx, dy = X - u, Y - v
+        pw = -0.5 * (con[g, 0] * dx * dx + con[g, 2] * dy * dy) - con[g, 1] * dx * dy
+        ok = (gam[g] * np.exp(pw) >= amin) & (np.abs(dx) <= rr[g] + 16) & (np.abs(dy) <= rr[g] + 16)
+        sq = (np.floor(X / 16) >= np.floor((u - rr[g]) / 16)) & (np.floor(X / 16) <= np.floor((u + rr[g]) / 16)) & \
+             (np.floor(Y / 16) >= np.floor((v - rr[g]) / 16)) & (np.floor(Y / 16) <= np.floor((v + rr[g]) / 16))
+        need = ok & sq
+        if not need.any():
+            continue
+        assert rect[g, 0] >= 0, g
+        tx, ty = np.floor(X[need] / 16), np.floor(Y[need] / 16)
+        assert np.all((tx >= rect[g, 0]) & (tx <= rect[g, 2]) & (ty >= rect[g, 1]) & (ty <= rect[g, 3])), g
+        checked += 1
+    assert checked > 0.5 * sc.n
 
 
 def test_tile_lists_definition(oracle, tiny_frame):
