@@ -34,7 +34,7 @@ sys.path.insert(0, ROOT)
 # one ncu capture of the kernel, valid only while its sources are unchanged:
 # kernel -> (bytes, SHA-256 of the concatenated sources, the summary file).
 PROFILED_TRAFFIC = {
-    "k_shadow": (579.2e6, "b8c5b4d18258a3bb580df7fa4fe029d39f24c754029b99b0e3bcf7fe1fe51ce4",
+    "k_shadow": (363.9e6, "aa717f43c4579d3f7d744d307570b7ce7185016eea5f7cc1fff4e5db55442eeb",
                  "profiles/k_shadow_object_300k_800.md"),
 }
 TRAFFIC_SOURCES = {

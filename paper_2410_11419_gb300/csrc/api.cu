@@ -134,7 +134,8 @@ Workspace plan_workspace(int n, int width, int height, size_t cap) {
     b.scan_part = P.take(4 * scan_words);
   }
   L.partial = P.take(8 * cap);
-  L.tile_order = P.take(4 * (size_t)L.ntiles);
+  L.tile_order[0] = P.take(4 * (size_t)L.ntiles);
+  L.tile_order[1] = P.take(4 * (size_t)L.ntiles);
   L.shade = P.take(16 * N);
   L.T = P.take(4 * N);
   L.Tp = P.take(4 * N);

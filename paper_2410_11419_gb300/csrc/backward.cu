@@ -119,6 +119,7 @@ __device__ __forceinline__ void power_grad(const SplatRec& q, const Eval& e, flo
 struct CamBwdParams {
   const uint32_t* list;
   const uint32_t* tile_start;
+  const uint32_t* tile_order;  // the forward's launch order of the camera tiles
   const SplatRec* rrec;
   const float4* ccol;
   const uint32_t* order;
@@ -137,7 +138,7 @@ __global__ void __launch_bounds__(256) k_camera_bwd(CamBwdParams p) {
   __shared__ float4 C0[256], C1[256];
   __shared__ uint32_t G[256];
   __shared__ int s_max;
-  const int tile = blockIdx.x, tx = tile % p.gx, ty = tile / p.gx, t = threadIdx.x;
+  const int tile = (int)p.tile_order[blockIdx.x], tx = tile % p.gx, ty = tile / p.gx, t = threadIdx.x;
   const int px = tx * kTile + (t & 15), py = ty * kTile + (t >> 4);
   const bool inside = px < p.W && py < p.H;
   const float fx = px + 0.5f, fy = py + 0.5f;
@@ -800,6 +801,7 @@ gs3_status run_backward(const FrameArgs& f, const float* dimg, void* bws, size_t
     CamBwdParams p;
     p.list = at<uint32_t>(ws, L.sp[0].tv[fin]);
     p.tile_start = at<uint32_t>(ws, L.sp[0].tile_start);
+    p.tile_order = at<uint32_t>(ws, L.tile_order[0]);
     p.rrec = at<SplatRec>(ws, L.sp[0].rrec);
     p.ccol = at<float4>(ws, L.ccol);
     p.order = at<uint32_t>(ws, L.sp[0].sv[1]);
@@ -856,7 +858,7 @@ gs3_status run_backward(const FrameArgs& f, const float* dimg, void* bws, size_t
     p.order = at<uint32_t>(ws, L.sp[1].sv[1]);
     p.kbound = at<uint32_t>(ws, L.sp[1].tv[1 - fin]);
     p.pass_mask = reinterpret_cast<const uint8_t*>(at<float>(ws, L.sp[1].tk[1 - fin]));
-    p.tile_order = at<uint32_t>(ws, L.tile_order);
+    p.tile_order = at<uint32_t>(ws, L.tile_order[1]);
     p.light_final = at<float>(ws, L.light_final);
     p.dT = dT;
     p.den = at<float>(ws, L.shadow_den);

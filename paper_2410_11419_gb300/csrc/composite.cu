@@ -255,6 +255,7 @@ __global__ void k_fill(float* x, int n, float v) {
 struct CamParams {
   const uint32_t* list;
   const uint32_t* tile_start;
+  const uint32_t* tile_order;  // block b renders tile tile_order[b] (longest list first)
   const SplatRec* rrec;
   const float4* ccol;
   float* out;
@@ -268,7 +269,7 @@ struct CamParams {
 __global__ void __launch_bounds__(256) k_camera(CamParams p) {
   __shared__ float4 Ga[256], Gb[256], Gc[256], C0[256], C1[256];
   __shared__ uint32_t Gmask[256];
-  const int tile = blockIdx.x;
+  const int tile = (int)p.tile_order[blockIdx.x];
   const int tx = tile % p.gx, ty = tile / p.gx;
   const int t = threadIdx.x;
   const uint32_t wbit = 1u << (t >> 5);
@@ -328,7 +329,7 @@ __global__ void __launch_bounds__(256) k_camera(CamParams p) {
   }
 }
 
-// Launch order of the light tiles: longest list first, so that the last
+// Launch order of a splat's tiles: longest list first, so that the last
 // blocks to start are the short ones and the final partial wave stays short
 // (a longest-processing-time-first schedule; the tiles' results do not depend
 // on the order).  One block sorts packed 32-bit keys (inverted list length
@@ -371,11 +372,11 @@ __global__ void k_identity_order(uint32_t* order, int ntiles) {
 
 }  // namespace
 
-void launch_tile_order(const FrameArgs& f, cudaStream_t s) {
+void launch_tile_order(const FrameArgs& f, int splat, cudaStream_t s) {
   const Workspace& L = *f.L;
-  uint32_t* order = at<uint32_t>(f.ws, L.tile_order);
+  uint32_t* order = at<uint32_t>(f.ws, L.tile_order[splat]);
   if (L.ntiles <= kOrderTiles) {
-    k_tile_order<<<1, 1024, 0, s>>>(at<uint32_t>(f.ws, L.sp[1].tile_start), L.ntiles, order);
+    k_tile_order<<<1, 1024, 0, s>>>(at<uint32_t>(f.ws, L.sp[splat].tile_start), L.ntiles, order);
   } else {
     k_identity_order<<<(L.ntiles + 255) / 256, 256, 0, s>>>(order, L.ntiles);
   }
@@ -397,9 +398,9 @@ void launch_shadow_composite(const FrameArgs& f, cudaStream_t s) {
   k_occluder_bound<<<blocks, 256, 0, s>>>(at<uint32_t>(ws, b.tk[fin]), at<uint32_t>(ws, b.tile_start), dl, header,
                                           f.opts.shadow_bias, kb, (uint32_t)f.L->cap);
   count_launch(2);
-  launch_tile_order(f, s);
+  launch_tile_order(f, 1, s);
   ShadowParams p;
-  p.tile_order = at<uint32_t>(ws, f.L->tile_order);
+  p.tile_order = at<uint32_t>(ws, f.L->tile_order[1]);
   p.list = at<uint32_t>(ws, b.tv[fin]);
   p.tile_start = at<uint32_t>(ws, b.tile_start);
   p.rrec = at<SplatRec>(ws, b.rrec);
@@ -454,6 +455,8 @@ void launch_camera_composite(const FrameArgs& f, float* out_rgb, cudaStream_t s)
   p.pix_aux = at<float4>(ws, f.L->pix_aux);
   p.W = f.L->width; p.H = f.L->height; p.gx = f.L->gx;
   p.amax = f.opts.alpha_max; p.tstop = f.opts.t_stop;
+  launch_tile_order(f, 0, s);
+  p.tile_order = at<uint32_t>(ws, f.L->tile_order[0]);
   k_camera<<<f.L->ntiles, 256, 0, s>>>(p);
   count_launch();
 }

@@ -63,7 +63,7 @@ struct Workspace {
   size_t pix_aux = 0;    // float4[2 HW]: (S rgb, Sh), (R rgb, 0) composited per camera pixel
   size_t light_final = 0;  // float[HW] occluder product at the end of each shadow ray
   size_t shadow_den = 0;   // float[N] sum of beta per Gaussian (by index)
-  size_t tile_order = 0;   // u32[ntiles] light tiles by decreasing list length (launch order)
+  size_t tile_order[2] = {0, 0};  // u32[ntiles] per splat: tiles by decreasing list length (launch order)
   int n = 0, width = 0, height = 0, gx = 0, gy = 0, ntiles = 0;
   size_t cap = 0;
   int nb_n = 0;    // radix blocks over N
@@ -143,9 +143,9 @@ void launch_prep(const FrameArgs& f, cudaStream_t s);
 void launch_depth_sort(const FrameArgs& f, int splat, cudaStream_t s);
 void launch_binning(const FrameArgs& f, int splat, cudaStream_t s);
 void launch_shadow_composite(const FrameArgs& f, cudaStream_t s);
-// light tiles ordered longest list first, into L.tile_order (identity past kOrderTiles tiles)
+// a splat's tiles ordered longest list first, into L.tile_order[splat] (identity past kOrderTiles tiles)
 constexpr int kOrderTiles = 8192;
-void launch_tile_order(const FrameArgs& f, cudaStream_t s);
+void launch_tile_order(const FrameArgs& f, int splat, cudaStream_t s);
 void launch_shadow_reduce(const FrameArgs& f, cudaStream_t s);
 void launch_mlp(const FrameArgs& f, cudaStream_t s, bool identity_only = false);
 // BF16 / FP8 tensor-core MLPs (mlp_tc.cu)

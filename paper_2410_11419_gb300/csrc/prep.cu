@@ -73,7 +73,7 @@ __device__ void accurate_geometry(const float4 m, const float Rq[9], const float
 // FP32 recipe: returns false when culled; fills the record otherwise.
 __device__ bool project_rn(const float4 m, const float4 s, const float4 q, const View& v,
                            const gs3_render_opts& o, int gx, int gy, const float* pL, float gamma,
-                           SplatRec& rec) {
+                           float nl_amin, SplatRec& rec) {
   const float* R = v.R;
   float tx = A_(dot3_rn(R[0], R[1], R[2], m.x, m.y, m.z), v.t[0]);
   float ty = A_(dot3_rn(R[3], R[4], R[5], m.x, m.y, m.z), v.t[1]);
@@ -157,6 +157,16 @@ __device__ bool project_rn(const float4 m, const float4 s, const float4 q, const
   const float ts = (float)kTile;
   float fx0 = floorf(D_(S_(u, r), ts)), fx1 = floorf(D_(A_(u, r), ts));
   float fy0 = floorf(D_(S_(vv, r), ts)), fy1 = floorf(D_(A_(vv, r), ts));
+  // Cut the square to the box holding every pixel with alpha >= alpha_min:
+  // ln(gamma) <= min(0, logit), so r2 = 2 (min(0, logit) - ln alpha_min) bounds
+  // 2 ln(gamma / alpha_min) without a transcendental of per-Gaussian data.
+  const float r2 = M_(2.f, A_(fminf(0.f, m.w), nl_amin));
+  if (!(r2 > 0.f)) return false;  // gamma < alpha_min: no pixel passes
+  const float hx = Q_(M_(r2, a)), hy = Q_(M_(r2, c));
+  fx0 = fmaxf(fx0, floorf(D_(S_(u, hx), ts)));
+  fx1 = fminf(fx1, floorf(D_(A_(u, hx), ts)));
+  fy0 = fmaxf(fy0, floorf(D_(S_(vv, hy), ts)));
+  fy1 = fminf(fy1, floorf(D_(A_(vv, hy), ts)));
   if (fx1 < 0.f || fx0 > (float)(gx - 1) || fy1 < 0.f || fy0 > (float)(gy - 1)) return false;
   rec.r = make_int4((int)fmaxf(fx0, 0.f), (int)fmaxf(fy0, 0.f), (int)fminf(fx1, (float)(gx - 1)),
                     (int)fminf(fy1, (float)(gy - 1)));
@@ -282,6 +292,7 @@ struct PrepParams {
   View cam;
   gs3_light light;
   float4 lh;  // homogeneous light (light_h)
+  float nl_amin;  // -ln(alpha_min) as FP32, from double precision on the host
   float cam_pos[3];
   float intensity;
   gs3_render_opts o;
@@ -323,7 +334,8 @@ __global__ void __launch_bounds__(256) k_prep(PrepParams p) {
 #pragma unroll
   for (int sp = 0; sp < 2; ++sp) {
     SplatRec rec;
-    bool vis = project_rn(m, s, q, sp ? lv : p.cam, p.o, p.gx, p.gy, sp ? p.light.pos : nullptr, gamma, rec);
+    bool vis = project_rn(m, s, q, sp ? lv : p.cam, p.o, p.gx, p.gy, sp ? p.light.pos : nullptr, gamma,
+                          p.nl_amin, rec);
     if (!vis) {
       rec.a = make_float4(0.f, 0.f, 0.f, 0.f);
       rec.b = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -390,6 +402,7 @@ void launch_prep(const FrameArgs& f, cudaStream_t s) {
   p.cam.ortho = 0.f;
   p.light = f.light;
   p.lh = light_h(f.light);
+  p.nl_amin = (float)(-log((double)f.opts.alpha_min));
   p.cam.fx = f.cam.fx; p.cam.fy = f.cam.fy; p.cam.cx = f.cam.cx; p.cam.cy = f.cam.cy;
   p.cam.W = f.cam.width; p.cam.H = f.cam.height;
   p.intensity = f.light.intensity;
