@@ -657,8 +657,10 @@ static void shadow_splat(go_frame *f, const go_opts *o)
                     if (a > o->alpha_max) a = o->alpha_max;
                     al[i] = a; be[i] = beta; gi[i] = g;
                     d[i] = key_to_float(f->key[1][g]);
-                    pass[i] = (power <= 0.0) && (a >= o->alpha_min);
-                    amb[i] = (power <= 0.0) && fabs(a - o->alpha_min) <= o->margin_alpha * o->alpha_min;
+                    /* the conic is positive definite, so the power is never positive:
+                     * no test on its sign (Eq. 2 has none) */
+                    pass[i] = a >= o->alpha_min;
+                    amb[i] = fabs(a - o->alpha_min) <= o->margin_alpha * o->alpha_min;
                     evals++;
                     passes += pass[i];
                 }
@@ -767,8 +769,7 @@ static void camera_composite(go_frame *f, const go_opts *o)
                 const double *C = f->conic[0] + 3 * g;
                 double power = -0.5 * (C[0] * dx * dx + C[2] * dy * dy) - C[1] * dx * dy;
                 evals++;
-                if (power > 0.0) continue;
-                double a = f->opacity[g] * exp(power);
+                double a = f->opacity[g] * exp(power); /* power <= 0: the conic is positive definite */
                 if (a > o->alpha_max) a = o->alpha_max;
                 int amb = fabs(a - o->alpha_min) <= o->margin_alpha * o->alpha_min;
                 if (amb) {

@@ -179,7 +179,7 @@ def frame(P, fr, cam, light, opts, mlps):
         pw = _power(uv_l, con_l, lst, px, py)
         beta = torch.exp(pw)
         alpha = torch.clamp(gamma[lst][None] * beta, max=amax)
-        passing = ((pw <= 0) & (alpha >= amin)).detach()
+        passing = (alpha >= amin).detach()
         l1a = torch.where(passing, torch.log1p(-alpha), torch.zeros_like(alpha))
         cs = torch.cat([torch.zeros((px.shape[0], 1), dtype=DT), torch.cumsum(l1a, 1)], 1)
         dd = d32[lst_l[b:e]]
@@ -220,7 +220,7 @@ def frame(P, fr, cam, light, opts, mlps):
         lst = torch.from_numpy(lst_c[b:e].astype(np.int64))
         pw = _power(uv_c, con_c, lst, px, py)
         alpha = torch.clamp(gamma[lst][None] * torch.exp(pw), max=amax)
-        passing = ((pw <= 0) & (alpha >= amin)).detach()
+        passing = (alpha >= amin).detach()
         a = torch.where(passing, alpha, torch.zeros_like(alpha))
         l1a = torch.log1p(-a)
         incl = torch.cumsum(l1a, 1)

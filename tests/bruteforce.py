@@ -45,7 +45,7 @@ def shadow_values(fr, opts):
             for py in range(ty * ts, min(H, ty * ts + ts)):
                 for px in range(tx * ts, min(W, tx * ts + ts)):
                     power, beta, a = _alpha(uv, con, op, px + 0.5, py + 0.5, opts.alpha_max)
-                    ok = (power <= 0) & (a >= opts.alpha_min)
+                    ok = a >= opts.alpha_min
                     if not ok.any():
                         continue
                     occ = (d[None, :] < thr[:, None]) & ok[None, :]
@@ -73,9 +73,7 @@ def composite(fr, opts, shade, Tp, res):
                 dx = px + 0.5 - fr["cam_uv"][g, 0]
                 dy = py + 0.5 - fr["cam_uv"][g, 1]
                 A, B, Cc = fr["cam_conic"][g]
-                power = -0.5 * (A * dx * dx + Cc * dy * dy) - B * dx * dy
-                if power > 0:
-                    continue
+                power = -0.5 * (A * dx * dx + Cc * dy * dy) - B * dx * dy  # <= 0: positive-definite conic
                 a = min(opts.alpha_max, fr["opacity"][g] * np.exp(power))
                 if a < opts.alpha_min:
                     continue
