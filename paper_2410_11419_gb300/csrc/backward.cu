@@ -95,7 +95,7 @@ __device__ __forceinline__ Eval eval_rec(const SplatRec& q, float fx, float fy, 
   r.dx = (fx - q.a.x) - q.b.w;
   r.dy = (fy - q.a.y) - q.c.x;
   r.power = -0.5f * (q.b.x * r.dx * r.dx + q.b.z * r.dy * r.dy) - q.b.y * r.dx * r.dy;
-  r.pass = r.power >= q.c.w && r.power <= 0.f;
+  r.pass = r.power >= q.c.w;
   r.beta = r.pass ? __expf(r.power) : 0.f;
   const float ga = q.a.z * r.beta;
   r.clamped = ga >= amax;
@@ -340,7 +340,7 @@ __global__ void __launch_bounds__(kBThreads, 8) k_shadow_bwd(ShadowBwdParams p) 
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
       const float pw = pws[q];
-      if (pw >= o1.y && pw <= 0.f) {
+      if (pw >= o1.y) {
         const float beta = ex2(pw), ga = o1.z * beta;
         const float f = fmaxf(omin, fmaf(-o1.z, beta, 1.f));
         const float inv = __frcp_rn(f);
@@ -394,12 +394,12 @@ __global__ void __launch_bounds__(kBThreads, 8) k_shadow_bwd(ShadowBwdParams p) 
         powers2(r0, r1.x, lx, ly0, ly1, pw0, pw1);
         const float coef = S.rc[jj], Tj = S.rt[jj];
         float g[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        if (pw0 >= r1.y && pw0 <= 0.f) {
+        if (pw0 >= r1.y) {
           const float beta = ex2(pw0);
           S0 = fmaf(coef * beta, A0, S0);
           add_power_grad(r0, r1.x, lx - r0.x, ly0 - r0.y, coef * (A0 - Tj) * beta, g);
         }
-        if (pw1 >= r1.y && pw1 <= 0.f) {
+        if (pw1 >= r1.y) {
           const float beta = ex2(pw1);
           S1 = fmaf(coef * beta, A1, S1);
           add_power_grad(r0, r1.x, lx - r0.x, ly1 - r0.y, coef * (A1 - Tj) * beta, g);

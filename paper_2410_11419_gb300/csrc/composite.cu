@@ -144,7 +144,7 @@ __global__ void __launch_bounds__(kShadowThreads, 8) k_shadow(ShadowParams p) {
           const float4 r0 = S.r0[jj];
           float p0, p1;
           powers2(r0, r1.x, lx, ly0, ly1, p0, p1);
-          const bool q0 = p0 >= r1.y && p0 <= 0.f, q1 = p1 >= r1.y && p1 <= 0.f;
+          const bool q0 = p0 >= r1.y, q1 = p1 >= r1.y;
           if (__any_sync(0xffffffffu, q0 || q1)) {
             if (lane == 0) atomicOr(&S.rpass[jj], wbit);
             const float b0 = q0 ? ex2(p0) : 0.f;
@@ -299,7 +299,7 @@ __global__ void __launch_bounds__(256) k_camera(CamParams p) {
         if (!(Gmask[jj] & wbit)) continue;
         const float4 ga = Ga[jj], gc = Gc[jj];
         const float pw = splat_power(ga, Gb[jj], gc.x, fx, fy);
-        if (!(pw >= gc.w && pw <= 0.f)) continue;
+        if (!(pw >= gc.w)) continue;
         const float alpha = fminf(p.amax, ga.z * __expf(pw));
         const float Tn = T * (1.f - alpha);
         if (Tn < p.tstop) {

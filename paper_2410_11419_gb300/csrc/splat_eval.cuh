@@ -55,14 +55,15 @@ __device__ __forceinline__ void powers2(const float4 e0, float r, float lx, floa
   p1 = fmaf(dy1, fmaf(e0.w, dy1, v), sx);
 }
 
-// one occluder on both rays: A *= 1 - min(amax, gamma beta) where it passes,
-// written as max(1 - amax, 1 - gamma beta)
+// one occluder on both rays: A *= 1 - min(amax, gamma beta) where it passes
+// (alpha >= alpha_min, i.e. power2 >= thr; the conic is positive definite, so
+// the power needs no sign test), written as max(1 - amax, 1 - gamma beta)
 __device__ __forceinline__ void occlude(const float4 o0, const float4 o1, float lx, float ly0, float ly1,
                                         float omin, float& A0, float& A1) {
   float p0, p1;
   powers2(o0, o1.x, lx, ly0, ly1, p0, p1);
-  if (p0 >= o1.y && p0 <= 0.f) A0 *= fmaxf(omin, fmaf(-o1.z, ex2(p0), 1.f));
-  if (p1 >= o1.y && p1 <= 0.f) A1 *= fmaxf(omin, fmaf(-o1.z, ex2(p1), 1.f));
+  if (p0 >= o1.y) A0 *= fmaxf(omin, fmaf(-o1.z, ex2(p0), 1.f));
+  if (p1 >= o1.y) A1 *= fmaxf(omin, fmaf(-o1.z, ex2(p1), 1.f));
 }
 
 }  // namespace
