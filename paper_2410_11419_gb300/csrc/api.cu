@@ -303,6 +303,49 @@ static const char* light_problem(const gs3_light& l, const gs3_render_opts& o) {
 gs3_status gs3_render_stages(gs3_scene* scene, const gs3_camera* cam, const gs3_light* light,
                              const gs3_render_opts* opts, float* out_rgb, void* workspace, size_t ws_bytes,
                              size_t key_capacity, uint32_t stages, void* stream) {
+  // a whole frame forks its light chain onto the calling thread's side stream
+  SideStream* side = stages == GS3_STAGE_ALL ? thread_side_stream() : nullptr;
+  return render_frame(scene, cam, light, opts, out_rgb, workspace, ws_bytes, key_capacity, stages,
+                      reinterpret_cast<cudaStream_t>(stream), side);
+}
+
+}  // extern "C"
+
+namespace gs3 {
+
+bool SideStream::create() {
+  if (s) return true;
+  if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) { s = nullptr; return false; }
+  if (cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&join, cudaEventDisableTiming) != cudaSuccess) {
+    destroy();
+    return false;
+  }
+  return true;
+}
+
+void SideStream::destroy() {
+  if (fork) cudaEventDestroy(fork);
+  if (join) cudaEventDestroy(join);
+  if (s) cudaStreamDestroy(s);
+  s = nullptr;
+  fork = join = nullptr;
+}
+
+SideStream* thread_side_stream() {
+  struct PerThread {
+    SideStream dev[64];
+    ~PerThread() {}  // streams live until the process ends (a thread may exit mid-use elsewhere)
+  };
+  thread_local PerThread t;
+  int d = 0;
+  if (cudaGetDevice(&d) != cudaSuccess || d < 0 || d >= 64) return nullptr;
+  return t.dev[d].create() ? &t.dev[d] : nullptr;
+}
+
+gs3_status render_frame(gs3_scene* scene, const gs3_camera* cam, const gs3_light* light,
+                        const gs3_render_opts* opts, float* out_rgb, void* workspace, size_t ws_bytes,
+                        size_t key_capacity, uint32_t stages, cudaStream_t stream, SideStream* side) {
   if (!scene || !cam || !light || !opts || !out_rgb || !workspace)
     return fail(GS3_ERR_INVALID_ARG, "gs3_render: null argument");
   if (cam->width < 1 || cam->height < 1 || cam->width > 16384 || cam->height > 16384)
@@ -328,7 +371,7 @@ gs3_status gs3_render_stages(gs3_scene* scene, const gs3_camera* cam, const gs3_
   if ((stages & GS3_STAGE_CAMERA) &&
       !device_range_ok(out_rgb, (size_t)cam->width * cam->height * 3 * sizeof(float)))
     return fail(GS3_ERR_INVALID_ARG, "gs3_render: out_rgb is not device memory of width*height*3 floats");
-  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  cudaStream_t s = stream;
   FrameArgs f;
   f.sc = scene->dev;
   f.cam = *cam;
@@ -343,18 +386,31 @@ gs3_status gs3_render_stages(gs3_scene* scene, const gs3_camera* cam, const gs3_
     if (e != cudaSuccess) return cuda_fail(e, "gs3_render: header reset");
     launch_prep(f, s);
   }
+  // The light chain (light binning, shadow composite, shadow reduce) and the
+  // camera binning use disjoint buffers: with a side stream they overlap.
+  const bool fork = side && !no_shadow && (stages & GS3_STAGE_CAMERA_BIN) && (stages & GS3_STAGE_LIGHT_BIN);
+  cudaStream_t sl = s;
+  if (fork) {
+    cudaEventRecord(side->fork, s);
+    cudaStreamWaitEvent(side->s, side->fork, 0);
+    sl = side->s;
+  }
+  if ((stages & GS3_STAGE_LIGHT_BIN) && !no_shadow) {
+    launch_depth_sort(f, 1, sl);
+    launch_binning(f, 1, sl);
+  }
+  if ((stages & GS3_STAGE_SHADOW_COMPOSITE) && !no_shadow) launch_shadow_composite(f, sl);
+  if (stages & GS3_STAGE_SHADOW_REDUCE) {
+    if (no_shadow) launch_fill_shadow_one(f, sl);
+    else launch_shadow_reduce(f, sl);
+  }
   if (stages & GS3_STAGE_CAMERA_BIN) {
     launch_depth_sort(f, 0, s);
     launch_binning(f, 0, s);
   }
-  if ((stages & GS3_STAGE_LIGHT_BIN) && !no_shadow) {
-    launch_depth_sort(f, 1, s);
-    launch_binning(f, 1, s);
-  }
-  if ((stages & GS3_STAGE_SHADOW_COMPOSITE) && !no_shadow) launch_shadow_composite(f, s);
-  if (stages & GS3_STAGE_SHADOW_REDUCE) {
-    if (no_shadow) launch_fill_shadow_one(f, s);
-    else launch_shadow_reduce(f, s);
+  if (fork) {
+    cudaEventRecord(side->join, sl);
+    cudaStreamWaitEvent(s, side->join, 0);
   }
   if (stages & GS3_STAGE_MLP) {
     if (scene->dev.mlp_dtype != GS3_MLP_FP32) {
@@ -370,6 +426,10 @@ gs3_status gs3_render_stages(gs3_scene* scene, const gs3_camera* cam, const gs3_
   if (e != cudaSuccess) return cuda_fail(e, "gs3_render: launch");
   return GS3_OK;
 }
+
+}  // namespace gs3
+
+extern "C" {
 
 gs3_status gs3_render(gs3_scene* scene, const gs3_camera* cam, const gs3_light* light,
                       const gs3_render_opts* opts, float* out_rgb, void* workspace, size_t ws_bytes,

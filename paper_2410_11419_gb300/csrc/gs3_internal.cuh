@@ -104,6 +104,21 @@ struct SceneDev {
   int lobe_shared;  // lobe_rot / lobe_sigma: K shared entries instead of K x N
 };
 
+// A side stream and fork/join events for running a frame's light chain
+// (light binning, shadow composite, shadow reduce) beside its camera binning.
+struct SideStream {
+  cudaStream_t s = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
+  bool create();
+  void destroy();
+};
+// the calling thread's side stream on the current device (created on first use)
+SideStream* thread_side_stream();
+// the frame with an explicit side stream (null: everything on `stream`)
+gs3_status render_frame(gs3_scene* scene, const gs3_camera* cam, const gs3_light* light,
+                        const gs3_render_opts* opts, float* out_rgb, void* workspace, size_t ws_bytes,
+                        size_t key_capacity, uint32_t stages, cudaStream_t stream, SideStream* side);
+
 // ---- launchers (stream-ordered, no host synchronisation) ----
 struct FrameArgs {
   SceneDev sc;

@@ -39,6 +39,7 @@ struct Request {
 
 struct Slot {
   cudaStream_t stream = nullptr;
+  SideStream side;  // the slot's own stream for its frames' light chains
   cudaEvent_t start = nullptr;
   cudaEvent_t done = nullptr;
   gs3_ws_header* hdr = nullptr;  // pinned copy of the workspace header
@@ -215,8 +216,8 @@ bool admit(gs3_server* S) {
       S->epoch_set = true;
     }
     cudaEventRecord(sl.start, sl.stream);
-    gs3_status st = gs3_render(sc, &sl.req.cam, &sl.req.light, &sl.req.opts, sl.req.out, aligned, bytes - 256,
-                               cap, sl.stream);
+    gs3_status st = render_frame(sc, &sl.req.cam, &sl.req.light, &sl.req.opts, sl.req.out, aligned, bytes - 256,
+                                 cap, GS3_STAGE_ALL, sl.stream, sl.side.s ? &sl.side : nullptr);
     if (st == GS3_OK) {
       cudaMemcpyAsync(sl.hdr, aligned, sizeof(gs3_ws_header), cudaMemcpyDeviceToHost, sl.stream);
       cudaEventRecord(sl.done, sl.stream);
@@ -288,6 +289,7 @@ gs3_status gs3_server_create(const gs3_server_opts* o, gs3_server** out) {
   S->slots.resize(o->max_inflight);
   for (Slot& sl : S->slots) {
     cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking);
+    sl.side.create();
     cudaEventCreate(&sl.start);
     cudaEventCreate(&sl.done);
     cudaMallocHost(reinterpret_cast<void**>(&sl.hdr), sizeof(gs3_ws_header));
@@ -424,6 +426,7 @@ gs3_status gs3_server_destroy(gs3_server* S) {
     if (sl.done) cudaEventDestroy(sl.done);
     if (sl.start) cudaEventDestroy(sl.start);
     if (sl.stream) cudaStreamDestroy(sl.stream);
+    sl.side.destroy();
     if (sl.hdr) cudaFreeHost(sl.hdr);
   }
   if (S->epoch) cudaEventDestroy(S->epoch);

@@ -205,3 +205,24 @@ def test_deterministic_repeat(gs3):
     b = rd.render(cam, light).clone()
     torch.cuda.synchronize()
     assert torch.equal(a, b) and torch.equal(ta, rd.stage("T"))
+
+
+def test_overlapped_frame_equals_staged(gs3):
+    """A whole gs3_render runs the light chain on a side stream beside the
+    camera binning; the frame equals the same frame rendered stage by stage
+    on one stream, bit for bit (the two chains share no buffer)."""
+    import torch
+    from paper_2410_11419_gb300 import _native as N, render as R
+    scene = synth.object_scene(3, n=20000)
+    cam, light = synth.camera_light_pair(9, 256, 256)
+    ds = R.DeviceScene(scene)
+    rd = R.Renderer(ds, 256, 256, 1 << 22)
+    whole = rd.render(cam, light).clone()
+    staged = torch.empty_like(whole)
+    for st in (N.GS3_STAGE_PREP, N.GS3_STAGE_CAMERA_BIN, N.GS3_STAGE_LIGHT_BIN, N.GS3_STAGE_SHADOW_COMPOSITE,
+               N.GS3_STAGE_SHADOW_REDUCE, N.GS3_STAGE_MLP, N.GS3_STAGE_CAMERA):
+        rd.render_stages(cam, light, st, out=staged)
+    torch.cuda.synchronize()
+    rd.check()
+    assert torch.equal(whole, staged)
+    ds.close()
