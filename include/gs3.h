@@ -168,6 +168,10 @@ typedef struct {
     size_t residual;      /* float4[N] Psi(...) rgb by Gaussian */
     size_t final_t;       /* float[H*W] transmittance left after the camera ray */
     size_t n_contrib;     /* uint32[H*W] list entries consumed by the camera ray */
+    size_t light_final;   /* float[H*W] occluder product where each shadow ray ended */
+    size_t light_stop;    /* uint32[H*W] 1 + light-list index of the occluder after which the
+                             shadow ray's product fell below 2^-40 and took no more
+                             occluders, or 0xFFFFFFFF when it never did */
 } gs3_ws_layout;
 
 /* Fill `o` with the paper's defaults (see gs3_render_opts). */

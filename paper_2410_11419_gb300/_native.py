@@ -80,7 +80,7 @@ class gs3_ws_layout(C.Structure):
                 ("order", C.c_size_t * 2), ("tile_start", C.c_size_t * 2), ("list", C.c_size_t * 2),
                 ("rect", C.c_size_t * 2), ("shade", C.c_size_t), ("shadow", C.c_size_t),
                 ("shadow_refined", C.c_size_t), ("residual", C.c_size_t), ("final_t", C.c_size_t),
-                ("n_contrib", C.c_size_t)]
+                ("n_contrib", C.c_size_t), ("light_final", C.c_size_t), ("light_stop", C.c_size_t)]
 
 
 class gs3_scene(C.Structure):

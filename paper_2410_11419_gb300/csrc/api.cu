@@ -145,6 +145,7 @@ Workspace plan_workspace(int n, int width, int height, size_t cap) {
   L.n_contrib = P.take(4 * (size_t)width * height);
   L.pix_aux = P.take(32 * (size_t)width * height);
   L.light_final = P.take(4 * (size_t)width * height);
+  L.light_stop = P.take(4 * (size_t)width * height);
   L.shadow_den = P.take(4 * N);
   L.total = P.cur;
   return L;
@@ -282,6 +283,8 @@ gs3_status gs3_workspace_layout(int32_t n, int32_t width, int32_t height, size_t
   out->residual = L.res;
   out->final_t = L.final_t;
   out->n_contrib = L.n_contrib;
+  out->light_final = L.light_final;
+  out->light_stop = L.light_stop;
   return GS3_OK;
 }
 

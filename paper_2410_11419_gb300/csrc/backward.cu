@@ -230,10 +230,13 @@ __global__ void k_copy_strided(const float* src, int stride, int off, float* dst
 // K6b: shadow splat backward.
 // Reverse sweep of the forward's two-cursor pass over each light tile, with
 // the forward's thread layout, entries and alpha decisions (splat_eval.cuh).
-// Per ray m the thread restarts from the product over every occluder A_m
-// (stored by the forward) and a suffix sum S_m = sum coef_j beta_jm T_m(j)
-// over the receivers already visited (coef_j = dL/dT_j / den_j):
-//   occluder k (passing):  A /= (1 - alpha_k),  dL/dalpha_k = -S / (1 - alpha_k)
+// Per ray m the thread restarts from the product A_m where the forward's ray
+// ended and the limit below which it took occluders (both stored by the
+// forward; a ray that stopped keeps its frozen product past the limit, so
+// occluders at or past it are skipped), and a suffix sum
+// S_m = sum coef_j beta_jm T_m(j) over the receivers already visited
+// (coef_j = dL/dT_j / den_j):
+//   occluder k (passing, taken):  A /= (1 - alpha_k),  dL/dalpha_k = -S / (1 - alpha_k)
 //   receiver j (passing):  dL/dbeta_j = coef_j (A - T_j),  S += coef_j beta_j A
 // with A = T_m(j) when receiver j is reached.  Occluders are undone before
 // the receiver whose prefix end K(j) they reach, so S holds exactly the
@@ -250,7 +253,8 @@ struct ShadowBwdParams {
   const uint32_t* kbound;
   const uint32_t* tile_order;  // the forward's launch order of the light tiles
   const uint8_t* pass_mask;
-  const float* light_final;
+  const float* light_final;    // the product where each ray ended
+  const uint32_t* light_stop;  // each ray took the occluders below this list index
   const float* dT;   // by index
   const float* den;  // by index
   const float* T;    // by index
@@ -270,6 +274,7 @@ struct ShadowBwdSmem {
   float rc[kBRecv], rt[kBRecv];
   float4 o0[kBOcc], o1[kBOcc];
   uint32_t og[kBOcc];
+  uint32_t wlim[4];
 };
 
 // Sums v[0..7] over the warp with 9 shuffles.  Lane L ends with the total of
@@ -321,13 +326,22 @@ __global__ void __launch_bounds__(kBThreads, 8) k_shadow_bwd(ShadowBwdParams p) 
   const uint32_t b = p.tile_start[tile], e = p.tile_start[tile + 1];
   if (b == e) return;
   const int gxp = tx * kTile + lxi;
-  float A0 = in0 ? p.light_final[(size_t)(ty * kTile + lyi) * p.W + gxp] : 1.f;
-  float A1 = in1 ? p.light_final[(size_t)(ty * kTile + lyi + 4) * p.W + gxp] : 1.f;
+  const size_t pix0 = (size_t)(ty * kTile + lyi) * p.W + gxp, pix1 = pix0 + (size_t)4 * p.W;
+  float A0 = in0 ? p.light_final[pix0] : 1.f;
+  float A1 = in1 ? p.light_final[pix1] : 1.f;
+  // a ray took the occluders below its limit; the warp skips those at or past
+  // all of its rays' limits, the block those past every warp's
+  const uint32_t lim0 = in0 ? p.light_stop[pix0] : 0u, lim1 = in1 ? p.light_stop[pix1] : 0u;
+  const uint32_t wlim = __reduce_max_sync(0xffffffffu, max(lim0, lim1));
+  if (lane == 0) S.wlim[warp] = wlim;
+  __syncthreads();
+  const uint32_t blim = max(max(S.wlim[0], S.wlim[1]), max(S.wlim[2], S.wlim[3]));
   float S0 = 0.f, S1 = 0.f;
-  uint32_t kc = p.kbound[e - 1];
+  uint32_t kc = min(p.kbound[e - 1], max(blim, b));
 
-  // undo occluder i of the window at both rays; accumulate its gradient
-  auto occlude_bwd = [&](int i) {
+  // undo occluder kk (window slot i) at both rays; accumulate its gradient
+  auto occlude_bwd = [&](int i, uint32_t kk) {
+    if (kk >= wlim) return;
     const float4 o1 = S.o1[i];
     if (!(__float_as_uint(o1.w) & wbit)) return;
     const float4 o0 = S.o0[i];
@@ -335,12 +349,13 @@ __global__ void __launch_bounds__(kBThreads, 8) k_shadow_bwd(ShadowBwdParams p) 
     powers2(o0, o1.x, lx, ly0, ly1, pw0, pw1);
     float g[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     const float pws[2] = {pw0, pw1}, lys[2] = {ly0, ly1};
+    const bool took[2] = {kk < lim0, kk < lim1};
     float* As[2] = {&A0, &A1};
     const float Ss[2] = {S0, S1};
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
       const float pw = pws[q];
-      if (pw >= o1.y) {
+      if (pw >= o1.y && took[q]) {
         const float beta = ex2(pw), ga = o1.z * beta;
         const float f = fmaxf(omin, fmaf(-o1.z, beta, 1.f));
         const float inv = __frcp_rn(f);
@@ -374,7 +389,7 @@ __global__ void __launch_bounds__(kBThreads, 8) k_shadow_bwd(ShadowBwdParams p) 
     int jj = rc - 1;
     while (jj >= 0) {
       const uint32_t kfirst = S.rk[0];
-      const uint32_t kt = kc > kfirst + kBOcc ? kc - kBOcc : kfirst;
+      const uint32_t kt = kc > kfirst + kBOcc ? kc - kBOcc : min(kfirst, kc);
       __syncthreads();
       for (uint32_t i = t; i < kc - kt; i += kBThreads) {
         const uint32_t rank = p.list[kt + i];
@@ -386,7 +401,7 @@ __global__ void __launch_bounds__(kBThreads, 8) k_shadow_bwd(ShadowBwdParams p) 
       for (; jj >= 0; --jj) {
         const uint32_t kend = S.rk[jj];
         if (kend < kt) break;
-        for (; kc > kend; --kc) occlude_bwd((int)(kc - 1 - kt));
+        for (; kc > kend; --kc) occlude_bwd((int)(kc - 1 - kt), kc - 1);
         const float4 r1 = S.r1[jj];
         if (!(__float_as_uint(r1.w) & wbit)) continue;
         const float4 r0 = S.r0[jj];
@@ -406,7 +421,7 @@ __global__ void __launch_bounds__(kBThreads, 8) k_shadow_bwd(ShadowBwdParams p) 
         }
         flush_grad(p.light_geom + (size_t)kGeom * S.rg[jj], g, lane);
       }
-      for (; kc > kt; --kc) occlude_bwd((int)(kc - 1 - kt));
+      for (; kc > kt; --kc) occlude_bwd((int)(kc - 1 - kt), kc - 1);
     }
     re = rs;
   }
@@ -421,7 +436,7 @@ __global__ void __launch_bounds__(kBThreads, 8) k_shadow_bwd(ShadowBwdParams p) 
       S.og[i] = p.order[rank];
     }
     __syncthreads();
-    for (; kc > kt; --kc) occlude_bwd((int)(kc - 1 - kt));
+    for (; kc > kt; --kc) occlude_bwd((int)(kc - 1 - kt), kc - 1);
   }
 }
 
@@ -860,6 +875,7 @@ gs3_status run_backward(const FrameArgs& f, const float* dimg, void* bws, size_t
     p.pass_mask = reinterpret_cast<const uint8_t*>(at<float>(ws, L.sp[1].tk[1 - fin]));
     p.tile_order = at<uint32_t>(ws, L.tile_order[1]);
     p.light_final = at<float>(ws, L.light_final);
+    p.light_stop = at<uint32_t>(ws, L.light_stop);
     p.dT = dT;
     p.den = at<float>(ws, L.shadow_den);
     p.T = at<float>(ws, L.T);

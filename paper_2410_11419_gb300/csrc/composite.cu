@@ -57,7 +57,9 @@ __device__ __forceinline__ float splat_power(const float4 a, const float4 b, flo
 // the splat's alpha >= alpha_min box reaches; other warps skip the entry.
 // Per receiver each warp sums (beta A, beta) over its 64 rays; the warps'
 // sums are added in fixed order into one (num, den) partial per
-// (tile, Gaussian) pair.
+// (tile, Gaussian) pair.  A ray stops taking occluders once its product is
+// below kShadowStop; a warp whose 64 rays all stopped skips the occluders,
+// and the block loads no occluder window once all four warps stopped.
 // ---------------------------------------------------------------------------
 constexpr int kRecv = 128;
 constexpr int kOccWin = 512;
@@ -72,7 +74,8 @@ struct ShadowParams {
   const uint32_t* tile_order;  // block b renders tile tile_order[b]
   uint8_t* pass_mask;  // per list entry: warps with a passing pixel (written as receiver)
   float2* partial;
-  float* light_final;
+  float* light_final;     // per light pixel: the product where the ray ended
+  uint32_t* light_stop;   // per light pixel: 1 + index of the occluder that stopped it, or kNoStop
   int W, H, gx;
   float amax;
 };
@@ -103,7 +106,10 @@ __global__ void __launch_bounds__(kShadowThreads, 8) k_shadow(ShadowParams p) {
   const bool hi_lane = (lane & 16) != 0;
   const float omin = 1.f - p.amax;
   const uint32_t b = p.tile_start[tile], e = p.tile_start[tile + 1];
-  float A0 = 1.f, A1 = 1.f;
+  // off-image rays start stopped (they never pass, so nothing reads them)
+  float A0 = in0 ? 1.f : 0.f, A1 = in1 ? 1.f : 0.f;
+  uint32_t lim0 = kNoStop, lim1 = kNoStop;
+  bool dead = !__any_sync(0xffffffffu, in0 || in1);  // warp-uniform: all 64 rays stopped
   uint32_t k = b;
   for (uint32_t rb = b; rb < e; rb += kRecv) {
     const int rc = (int)min((uint32_t)kRecv, e - rb);
@@ -120,24 +126,33 @@ __global__ void __launch_bounds__(kShadowThreads, 8) k_shadow(ShadowParams p) {
     const uint32_t klast = S.rk[rc - 1];
     int jj = 0;
     while (jj < rc) {
-      const uint32_t kt = min(klast, k + (uint32_t)kOccWin);
-      __syncthreads();  // the previous window is consumed
+      // the previous window is consumed; once every ray of the block stopped,
+      // the rest of the batch's occluders form one window that nobody loads
+      const bool all_dead = __syncthreads_and(dead) != 0;
+      const uint32_t kt = all_dead ? klast : min(klast, k + (uint32_t)kOccWin);
       // An occluder of an earlier receiver batch is needed only by the warps in
       // which it passed as a receiver (same power test; pixels outside the
       // image never pass).  Occluders of this batch keep their bounding-box
       // mask: their pass bits are still being gathered.
-      for (uint32_t i = t; i < kt - k; i += kShadowThreads) {
-        make_entry(p.rrec[p.list[k + i]], ox, oy, S.o0[i], S.o1[i]);
-        if (k + i < rb) S.o1[i].w = __uint_as_float((uint32_t)p.pass_mask[k + i]);
+      if (!all_dead) {
+        for (uint32_t i = t; i < kt - k; i += kShadowThreads) {
+          make_entry(p.rrec[p.list[k + i]], ox, oy, S.o0[i], S.o1[i]);
+          if (k + i < rb) S.o1[i].w = __uint_as_float((uint32_t)p.pass_mask[k + i]);
+        }
       }
       __syncthreads();
       const uint32_t ow = k;
       for (; jj < rc; ++jj) {
         const uint32_t kend = S.rk[jj];
         if (kend > kt) break;
-        for (; k < kend; ++k) {
-          const float4 o1 = S.o1[k - ow];
-          if (__float_as_uint(o1.w) & wbit) occlude(S.o0[k - ow], o1, lx, ly0, ly1, omin, A0, A1);
+        if (dead) {
+          k = max(k, kend);
+        } else if (k < kend) {
+          for (; k < kend; ++k) {
+            const float4 o1 = S.o1[k - ow];
+            if (__float_as_uint(o1.w) & wbit) occlude(S.o0[k - ow], o1, lx, ly0, ly1, omin, k + 1, A0, A1, lim0, lim1);
+          }
+          dead = __all_sync(0xffffffffu, !(A0 >= kShadowStop) && !(A1 >= kShadowStop));
         }
         const float4 r1 = S.r1[jj];
         if (__float_as_uint(r1.w) & wbit) {
@@ -159,9 +174,14 @@ __global__ void __launch_bounds__(kShadowThreads, 8) k_shadow(ShadowParams p) {
           }
         }
       }
-      for (; k < kt; ++k) {  // the next receiver needs occluders past this window
-        const float4 o1 = S.o1[k - ow];
-        if (__float_as_uint(o1.w) & wbit) occlude(S.o0[k - ow], o1, lx, ly0, ly1, omin, A0, A1);
+      if (dead) {  // the next receiver needs occluders past this window
+        k = max(k, kt);
+      } else if (k < kt) {
+        for (; k < kt; ++k) {
+          const float4 o1 = S.o1[k - ow];
+          if (__float_as_uint(o1.w) & wbit) occlude(S.o0[k - ow], o1, lx, ly0, ly1, omin, k + 1, A0, A1, lim0, lim1);
+        }
+        dead = __all_sync(0xffffffffu, !(A0 >= kShadowStop) && !(A1 >= kShadowStop));
       }
     }
     __syncthreads();
@@ -176,10 +196,16 @@ __global__ void __launch_bounds__(kShadowThreads, 8) k_shadow(ShadowParams p) {
       p.pass_mask[rb + t] = (uint8_t)m;
     }
   }
-  // the product over every occluder of the ray (the backward starts from it)
+  // the product where the ray ended and where it stopped (the backward starts from them)
   const int gxp = tx * kTile + lxi;
-  if (in0) p.light_final[(size_t)(ty * kTile + lyi) * p.W + gxp] = A0;
-  if (in1) p.light_final[(size_t)(ty * kTile + lyi + 4) * p.W + gxp] = A1;
+  if (in0) {
+    p.light_final[(size_t)(ty * kTile + lyi) * p.W + gxp] = A0;
+    p.light_stop[(size_t)(ty * kTile + lyi) * p.W + gxp] = lim0;
+  }
+  if (in1) {
+    p.light_final[(size_t)(ty * kTile + lyi + 4) * p.W + gxp] = A1;
+    p.light_stop[(size_t)(ty * kTile + lyi + 4) * p.W + gxp] = lim1;
+  }
 }
 
 // K(i) for every entry i of the light lists: the first index of i's tile
@@ -409,6 +435,7 @@ void launch_shadow_composite(const FrameArgs& f, cudaStream_t s) {
   p.pass_mask = reinterpret_cast<uint8_t*>(dl);  // the depths are consumed by k_occluder_bound
   p.partial = at<float2>(ws, f.L->partial);
   p.light_final = at<float>(ws, f.L->light_final);
+  p.light_stop = at<uint32_t>(ws, f.L->light_stop);
   p.W = f.L->width; p.H = f.L->height; p.gx = f.L->gx;
   p.amax = f.opts.alpha_max;
   static bool configured = false;

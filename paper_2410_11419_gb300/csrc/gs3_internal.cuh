@@ -61,7 +61,8 @@ struct Workspace {
   size_t final_t = 0;  // float[HW]
   size_t n_contrib = 0;  // u32[HW]
   size_t pix_aux = 0;    // float4[2 HW]: (S rgb, Sh), (R rgb, 0) composited per camera pixel
-  size_t light_final = 0;  // float[HW] occluder product at the end of each shadow ray
+  size_t light_final = 0;  // float[HW] occluder product where each shadow ray ended
+  size_t light_stop = 0;   // u32[HW] 1 + list index of the occluder that stopped the ray, or all ones
   size_t shadow_den = 0;   // float[N] sum of beta per Gaussian (by index)
   size_t tile_order[2] = {0, 0};  // u32[ntiles] per splat: tiles by decreasing list length (launch order)
   int n = 0, width = 0, height = 0, gx = 0, gy = 0, ntiles = 0;

@@ -55,15 +55,37 @@ __device__ __forceinline__ void powers2(const float4 e0, float r, float lx, floa
   p1 = fmaf(dy1, fmaf(e0.w, dy1, v), sx);
 }
 
-// one occluder on both rays: A *= 1 - min(amax, gamma beta) where it passes
-// (alpha >= alpha_min, i.e. power2 >= thr; the conic is positive definite, so
-// the power needs no sign test), written as max(1 - amax, 1 - gamma beta)
+// A shadow ray stops taking occluders once its product A falls below
+// kShadowStop: the occluder that takes A below it is the last one applied,
+// and A stays frozen after it.  Every receiver behind the stop would see an
+// exact product in [0, kShadowStop) and sees the frozen one, also in
+// [0, kShadowStop), so each T_m(j) and every beta-weighted average of them
+// moves by less than kShadowStop.  Without the stop, FP32 products underflow
+// on deep rays (thousands of passing entries through an object), and the
+// backward, which rebuilds A from the ray's final product, would rebuild 0
+// for every receiver of such a ray.  A frozen A is at least
+// kShadowStop (1 - alpha_max), far from the denormals.
+constexpr float kShadowStop = 0x1p-40f;
+constexpr uint32_t kNoStop = 0xFFFFFFFFu;  // the ray never stopped
+
+// one occluder (list index k) on both rays: A *= 1 - min(amax, gamma beta)
+// where it passes (alpha >= alpha_min, i.e. power2 >= thr; the conic is
+// positive definite, so the power needs no sign test), written as
+// max(1 - amax, 1 - gamma beta), on rays that have not stopped; a ray that
+// stops here records lim = k + 1 (it took the occluders below lim).
 __device__ __forceinline__ void occlude(const float4 o0, const float4 o1, float lx, float ly0, float ly1,
-                                        float omin, float& A0, float& A1) {
+                                        float omin, uint32_t k1, float& A0, float& A1, uint32_t& lim0,
+                                        uint32_t& lim1) {
   float p0, p1;
   powers2(o0, o1.x, lx, ly0, ly1, p0, p1);
-  if (p0 >= o1.y) A0 *= fmaxf(omin, fmaf(-o1.z, ex2(p0), 1.f));
-  if (p1 >= o1.y) A1 *= fmaxf(omin, fmaf(-o1.z, ex2(p1), 1.f));
+  if (p0 >= o1.y && A0 >= kShadowStop) {
+    A0 *= fmaxf(omin, fmaf(-o1.z, ex2(p0), 1.f));
+    if (A0 < kShadowStop) lim0 = k1;
+  }
+  if (p1 >= o1.y && A1 >= kShadowStop) {
+    A1 *= fmaxf(omin, fmaf(-o1.z, ex2(p1), 1.f));
+    if (A1 < kShadowStop) lim1 = k1;
+  }
 }
 
 }  // namespace

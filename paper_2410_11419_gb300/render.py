@@ -180,6 +180,10 @@ class Renderer:
             return self._view(L.final_t, self.width * self.height, torch.float32).view(self.height, self.width)
         if name == "n_contrib":
             return self._view(L.n_contrib, self.width * self.height, torch.int32).view(self.height, self.width)
+        if name == "light_final":
+            return self._view(L.light_final, self.width * self.height, torch.float32).view(self.height, self.width)
+        if name == "light_stop":
+            return self._view(L.light_stop, self.width * self.height, torch.int32).view(self.height, self.width)
         raise KeyError(name)
 
 

@@ -41,6 +41,7 @@ _STREAMS = {
     "albedo": 7, "shade_rot": 8, "latent": 9, "lobe_axis": 10, "lobe_sharp": 11,
     "lobe_amp": 12, "phi": 13, "psi": 14, "camera": 15, "light": 16,
     "shell_noise": 17, "perturb": 18, "environment": 19, "init": 20, "basis": 21,
+    "layers": 22,
 }
 
 RELU = 0
@@ -350,6 +351,30 @@ def perturbed(scene: Scene, seed: int) -> Scene:
     s.mean_op[:, :3] += (0.01 * g.standard_normal((s.n, 3))).astype(np.float32)
     s.albedo_d[:, :3] *= g.uniform(0.9, 1.1, (s.n, 3)).astype(np.float32)
     return s
+
+
+def layered_scene(seed: int, layers: int = 24, grid: int = 10, k: int = 2, pitch: float = 0.06,
+                  gap: float = 0.03) -> Scene:
+    """A stack of `layers` planes of grid x grid nearly opaque Gaussians
+    (logit N(6, 1), flattened scales U[0.035, 0.05] x U[0.035, 0.05] x 0.01,
+    centres on a `pitch` grid jittered by N(0, (pitch / 10)^2)) normal to z, the
+    planes `gap` apart from z = +(layers - 1) gap / 2 down.  Seen from a
+    light on the +z axis every shadow ray through the stack crosses all
+    planes, so its occluder product falls far below the FP32 range."""
+    n = layers * grid * grid
+    base = make_scene(seed, n, k, "ball", mlp_width=32, mlp_hidden=2)
+    g = rng(seed, "layers")
+    ij = (np.arange(grid) - (grid - 1) / 2.0) * pitch
+    X, Y = np.meshgrid(ij, ij)
+    xy = np.tile(np.stack([X.ravel(), Y.ravel()], 1), (layers, 1)) + g.normal(0.0, pitch / 10.0, (n, 2))
+    z = np.repeat((layers - 1) / 2.0 * gap - gap * np.arange(layers), grid * grid)
+    base.mean_op[:, :3] = np.concatenate([xy, z[:, None]], 1).astype(np.float32)
+    base.mean_op[:, 3] = g.normal(6.0, 1.0, n).astype(np.float32)
+    base.scale[:, :2] = g.uniform(0.035, 0.05, (n, 2)).astype(np.float32)
+    base.scale[:, 2] = np.float32(0.01)
+    q = np.concatenate([np.ones((n, 1)), 0.05 * g.standard_normal((n, 3))], 1)
+    base.rot = np.ascontiguousarray(q / np.linalg.norm(q, axis=1, keepdims=True), dtype=np.float32)
+    return base
 
 
 # Named workloads -----------------------------------------------------------

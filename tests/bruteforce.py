@@ -19,6 +19,16 @@ def _alpha(uv, conic, opac, px, py, amax):
     return power, beta, a
 
 
+def _amin(opts):
+    """alpha_min as the renderers hold it: an FP32 number."""
+    return float(np.float32(opts.alpha_min))
+
+
+def _amax(opts):
+    """alpha_max as the renderers hold it: an FP32 number."""
+    return float(np.float32(opts.alpha_max))
+
+
 def candidates(rect, key, tx, ty):
     inside = (rect[:, 0] >= 0) & (rect[:, 0] <= tx) & (tx <= rect[:, 2]) & \
              (rect[:, 1] <= ty) & (ty <= rect[:, 3])
@@ -44,8 +54,8 @@ def shadow_values(fr, opts):
             thr = (d - bias).astype(np.float32)
             for py in range(ty * ts, min(H, ty * ts + ts)):
                 for px in range(tx * ts, min(W, tx * ts + ts)):
-                    power, beta, a = _alpha(uv, con, op, px + 0.5, py + 0.5, opts.alpha_max)
-                    ok = a >= opts.alpha_min
+                    power, beta, a = _alpha(uv, con, op, px + 0.5, py + 0.5, _amax(opts))
+                    ok = a >= _amin(opts)
                     if not ok.any():
                         continue
                     occ = (d[None, :] < thr[:, None]) & ok[None, :]
@@ -53,6 +63,48 @@ def shadow_values(fr, opts):
                     np.add.at(num, lst[ok], (beta * Tm)[ok])
                     np.add.at(den, lst[ok], beta[ok])
     return np.where(den > 0, num / np.where(den > 0, den, 1), 1.0)
+
+
+def shadow_values_stopped(fr, opts, stop):
+    """Shadow values when a ray stops taking occluders once its product is
+    below `stop`: walking the ray's entries in depth order, a passing entry
+    multiplies the running product only while that product is >= stop, and
+    receiver j sees the running product after the entries with
+    d_k < d_j - bias.  Also returns, per ray, the exact product over every
+    passing entry (log2) and the smallest frozen product."""
+    n, W, H, ts = fr["n"], fr["width"], fr["height"], opts.tile
+    num = np.zeros(n)
+    den = np.zeros(n)
+    d_all = fr["light_key"].view(np.float32)
+    bias = np.float32(opts.shadow_bias)
+    log2_exact, frozen_min = [], []
+    for ty in range((H + ts - 1) // ts):
+        for tx in range((W + ts - 1) // ts):
+            lst = candidates(fr["light_rect"], fr["light_key"], tx, ty)
+            if lst.size == 0:
+                continue
+            uv, con, op = fr["light_uv"][lst], fr["light_conic"][lst], fr["opacity"][lst]
+            d = d_all[lst]
+            thr = (d - bias).astype(np.float32)
+            K = np.searchsorted(d, thr, side="left")  # entries with d_k < thr_j (d is sorted)
+            for py in range(ty * ts, min(H, ty * ts + ts)):
+                for px in range(tx * ts, min(W, tx * ts + ts)):
+                    power, beta, a = _alpha(uv, con, op, px + 0.5, py + 0.5, _amax(opts))
+                    ok = a >= _amin(opts)
+                    if not ok.any():
+                        continue
+                    run = np.empty(lst.size + 1)
+                    run[0] = 1.0
+                    for i in range(lst.size):
+                        take = ok[i] and run[i] >= stop
+                        run[i + 1] = run[i] * (1.0 - a[i]) if take else run[i]
+                    log2_exact.append(np.log2(np.where(ok, 1.0 - a, 1.0)).sum())
+                    frozen_min.append(run[-1])
+                    Tm = run[K]
+                    np.add.at(num, lst[ok], (beta * Tm)[ok])
+                    np.add.at(den, lst[ok], beta[ok])
+    T = np.where(den > 0, num / np.where(den > 0, den, 1), 1.0)
+    return T, np.array(log2_exact), np.array(frozen_min)
 
 
 def composite(fr, opts, shade, Tp, res):
@@ -74,8 +126,8 @@ def composite(fr, opts, shade, Tp, res):
                 dy = py + 0.5 - fr["cam_uv"][g, 1]
                 A, B, Cc = fr["cam_conic"][g]
                 power = -0.5 * (A * dx * dx + Cc * dy * dy) - B * dx * dy  # <= 0: positive-definite conic
-                a = min(opts.alpha_max, fr["opacity"][g] * np.exp(power))
-                if a < opts.alpha_min:
+                a = min(_amax(opts), fr["opacity"][g] * np.exp(power))
+                if a < _amin(opts):
                     continue
                 Tn = T * (1 - a)
                 if Tn < opts.t_stop:

@@ -43,6 +43,7 @@ def test_struct_sizes_match_header_layout(libgs3):
     assert ctypes.sizeof(N.gs3_light) == 4 * (3 + 1 + 1 + 3 + 1)   # pos, intensity, type, dir, extent
     assert ctypes.sizeof(N.gs3_render_opts) == 4 * (7 + 3 + 3)
     assert ctypes.sizeof(N.gs3_ws_header) == 4 * (8 + 12 + 1)
+    assert ctypes.sizeof(N.gs3_ws_layout) == 8 * (2 + 5 * 2 + 8)
 
 
 def test_host_only_entry_points(libgs3):
@@ -56,7 +57,7 @@ def test_host_only_entry_points(libgs3):
     lay = N.gs3_workspace_layout(1000, 128, 128, 1 << 20)
     assert lay.total == a
     offs = [lay.header, *lay.key, *lay.order, *lay.tile_start, *lay.list, lay.shade, lay.shadow,
-            lay.shadow_refined, lay.residual, lay.final_t, lay.n_contrib]
+            lay.shadow_refined, lay.residual, lay.final_t, lay.n_contrib, lay.light_final, lay.light_stop]
     assert all(o % 256 == 0 and o < a for o in offs)
     assert N.gs3_workspace_size(0, 128, 128, 10) == 0
     with pytest.raises(N.GS3Error):

@@ -36,6 +36,8 @@ def run_both(gs3, oracle, scene, cam, light, ablate=0, cap=1 << 20, falloff=1):
     g["list"] = rd.stage("list", 0)[:hdr.pairs_cam].cpu().numpy()
     g["llist"] = rd.stage("list", 1)[:hdr.pairs_light].cpu().numpy()
     g["img"] = img.cpu().numpy()
+    g["light_final"] = rd.stage("light_final").cpu().numpy()
+    g["light_stop"] = rd.stage("light_stop").cpu().numpy().view(np.uint32)
     g["hdr"] = hdr
     fr = oracle.render(scene, cam, light, oracle.Opts(ablate=ablate, falloff=falloff))
     ds.close()
