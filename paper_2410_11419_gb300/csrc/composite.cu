@@ -47,23 +47,27 @@ __device__ __forceinline__ float splat_power(const float4 a, const float4 b, flo
 // form a prefix of the tile's list; its end K(j) is precomputed per entry
 // (k_occluder_bound) and is non-decreasing in j.
 //
-// 128 threads per 16x16 tile, two pixels per thread: warp w owns the 8x8
-// block at (8 (w & 1), 8 (w >> 1)), lane l the pixels (l & 7, l >> 3) and
-// (l & 7, (l >> 3) + 4) of it.  Receivers are staged 128 at a time, the
-// occluders they need through a window of up to kOccWin records; each thread
-// keeps its two rays' products A over the consumed occluders.  Records hold
-// the splat centre relative to the tile origin (pixel offsets are one exact
-// subtraction), the pre-scaled conic and a mask of the warps whose 8x8 block
-// the splat's alpha >= alpha_min box reaches; other warps skip the entry.
-// Per receiver each warp sums (beta A, beta) over its 64 rays; the warps'
-// sums are added in fixed order into one (num, den) partial per
-// (tile, Gaussian) pair.  A ray stops taking occluders once its product is
-// below kShadowStop; a warp whose 64 rays all stopped skips the occluders,
-// and the block loads no occluder window once all four warps stopped.
+// One warp per 16x16 tile, eight pixels per lane: lane l owns column l & 15,
+// rows (l >> 4) + 2 i, i = 0..7 (i < 4: the tile's top half).  The warp walks
+// the tile's list once: receivers are staged 128 at a time, the occluders
+// they need through a window of up to kOccWin records, and each lane keeps
+// its eight rays' products A over the consumed occluders.  Records hold the
+// splat centre relative to the tile origin (pixel offsets are one exact
+// subtraction), the pre-scaled conic and the quadrants (8x8 blocks) the
+// splat's alpha >= alpha_min box reaches; a half of the tile that no
+// quadrant bit covers is not evaluated.  Per receiver the warp sums
+// (beta A, beta) over its 256 rays into the (tile, Gaussian) partial and
+// records the quadrants where it passed (ballots); an occluder is evaluated
+// only in the halves where it passed as a receiver (same power test).  A ray
+// stops taking occluders once its product is below kShadowStop, and the
+// warp skips occluders, and loads no occluder window, once all its rays
+// stopped.
 // ---------------------------------------------------------------------------
 constexpr int kRecv = 128;
-constexpr int kOccWin = 512;
-constexpr int kShadowThreads = 128;
+constexpr int kOccWin = 192;
+constexpr int kShadowThreads = 32;
+constexpr int kPx = 8;  // pixels per lane
+constexpr uint32_t kLeft = 0x00FF00FFu;  // lanes of columns 0-7
 
 struct ShadowParams {
   const uint32_t* list;
@@ -72,7 +76,7 @@ struct ShadowParams {
   const uint32_t* off;
   const uint32_t* kbound;
   const uint32_t* tile_order;  // block b renders tile tile_order[b]
-  uint8_t* pass_mask;  // per list entry: warps with a passing pixel (written as receiver)
+  uint8_t* pass_mask;  // per list entry: quadrants with a passing pixel (written as receiver)
   float2* partial;
   float* light_final;     // per light pixel: the product where the ray ended
   uint32_t* light_stop;   // per light pixel: 1 + index of the occluder that stopped it, or kNoStop
@@ -83,64 +87,100 @@ struct ShadowParams {
 struct ShadowSmem {
   float4 r0[kRecv], r1[kRecv];
   uint32_t rk[kRecv], rslot[kRecv];
-  uint32_t rpass[kRecv];  // warps in which the receiver passed at some pixel
+  uint32_t rpass[kRecv];  // quadrants in which the receiver passed
   float4 o0[kOccWin], o1[kOccWin];
-  float2 red[4][kRecv];
 };
 
-__global__ void __launch_bounds__(kShadowThreads, 8) k_shadow(ShadowParams p) {
-  extern __shared__ float4 smem_raw[];
-  ShadowSmem& S = *reinterpret_cast<ShadowSmem*>(smem_raw);
+// quadrant bits of a half-tile ballot pair: bit 0/1 top left/right, 2/3 bottom
+__device__ __forceinline__ uint32_t quadrants(uint32_t top, uint32_t bottom) {
+  return ((top & kLeft) ? 1u : 0u) | ((top & ~kLeft) ? 2u : 0u) | ((bottom & kLeft) ? 4u : 0u) |
+         ((bottom & ~kLeft) ? 8u : 0u);
+}
+
+__global__ void __launch_bounds__(kShadowThreads, 17) k_shadow(ShadowParams p) {
+  __shared__ ShadowSmem S;
   const int tile = (int)p.tile_order[blockIdx.x];
   const int tx = tile % p.gx, ty = tile / p.gx;
   const float ox = (float)(tx * kTile), oy = (float)(ty * kTile);
-  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-  const uint32_t wbit = 1u << warp;
-  const int lxi = (warp & 1) * 8 + (lane & 7), lyi = (warp >> 1) * 8 + (lane >> 3);
-  const bool in0 = tx * kTile + lxi < p.W && ty * kTile + lyi < p.H;
-  const bool in1 = tx * kTile + lxi < p.W && ty * kTile + lyi + 4 < p.H;
+  const int lane = threadIdx.x;
+  const int lxi = lane & 15, lyi = lane >> 4;
+  const bool inx = tx * kTile + lxi < p.W;
+  const float lx = lxi + 0.5f;
   // A pixel outside the image is moved far from every splat: its power is
-  // then far below any threshold, it never passes, and its A is never used.
+  // then far below any threshold and it never passes.  It starts stopped.
   const float kFar = 1.0e6f;
-  const float lx = lxi + 0.5f, ly0 = in0 ? lyi + 0.5f : kFar, ly1 = in1 ? lyi + 4.5f : kFar;
-  const bool hi_lane = (lane & 16) != 0;
+  float ly[kPx], A[kPx];
+  uint32_t lim[kPx];
+  bool any_in = false;
+#pragma unroll
+  for (int i = 0; i < kPx; ++i) {
+    const bool in = inx && ty * kTile + lyi + 2 * i < p.H;
+    ly[i] = in ? lyi + 2 * i + 0.5f : kFar;
+    A[i] = in ? 1.f : 0.f;
+    lim[i] = kNoStop;
+    any_in |= in;
+  }
   const float omin = 1.f - p.amax;
   const uint32_t b = p.tile_start[tile], e = p.tile_start[tile + 1];
-  // off-image rays start stopped (they never pass, so nothing reads them)
-  float A0 = in0 ? 1.f : 0.f, A1 = in1 ? 1.f : 0.f;
-  uint32_t lim0 = kNoStop, lim1 = kNoStop;
-  bool dead = !__any_sync(0xffffffffu, in0 || in1);  // warp-uniform: all 64 rays stopped
+  bool dead = !__any_sync(0xffffffffu, any_in);  // all 256 rays stopped
   uint32_t k = b;
+
+  // one occluder (list index kk, window slot i) on the lane's rays
+  auto occlude8 = [&](int i, uint32_t kk, uint32_t rb) {
+    const float4 o1 = S.o1[i];
+    const uint32_t bits = kk >= rb ? S.rpass[kk - rb] : __float_as_uint(o1.w);
+    if (!bits) return;
+    const float4 o0 = S.o0[i];
+    const float dx = lx - o0.x;
+    const float sx = (o0.z * dx) * dx, v = o1.x * dx;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      if (!(bits & (3u << (2 * h)))) continue;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int i8 = 4 * h + q;
+        const float dy = ly[i8] - o0.y;
+        const float pw = fmaf(dy, fmaf(o0.w, dy, v), sx);
+        if (pw >= o1.y && A[i8] >= kShadowStop) {
+          A[i8] *= fmaxf(omin, fmaf(-o1.z, ex2(pw), 1.f));
+          if (A[i8] < kShadowStop) lim[i8] = kk + 1;
+        }
+      }
+    }
+  };
+  auto still_alive = [&]() {
+    bool alive = false;
+#pragma unroll
+    for (int i = 0; i < kPx; ++i) alive |= A[i] >= kShadowStop;
+    return __any_sync(0xffffffffu, alive);
+  };
+
   for (uint32_t rb = b; rb < e; rb += kRecv) {
     const int rc = (int)min((uint32_t)kRecv, e - rb);
-    __syncthreads();  // previous receivers fully reduced and written
-    if (t < rc) {
+    __syncwarp();  // the previous batch is consumed
+    for (int t = lane; t < rc; t += kShadowThreads) {
       const uint32_t rank = p.list[rb + t];
       const SplatRec q = p.rrec[rank];
       make_entry(q, ox, oy, S.r0[t], S.r1[t]);
       S.rk[t] = p.kbound[rb + t];
       S.rslot[t] = p.off[rank] + (uint32_t)((ty - q.r.y) * (q.r.z - q.r.x + 1) + (tx - q.r.x));
-      S.rpass[t] = 0u;
     }
-    __syncthreads();
+    __syncwarp();
     const uint32_t klast = S.rk[rc - 1];
     int jj = 0;
     while (jj < rc) {
-      // the previous window is consumed; once every ray of the block stopped,
-      // the rest of the batch's occluders form one window that nobody loads
-      const bool all_dead = __syncthreads_and(dead) != 0;
-      const uint32_t kt = all_dead ? klast : min(klast, k + (uint32_t)kOccWin);
-      // An occluder of an earlier receiver batch is needed only by the warps in
-      // which it passed as a receiver (same power test; pixels outside the
-      // image never pass).  Occluders of this batch keep their bounding-box
-      // mask: their pass bits are still being gathered.
-      if (!all_dead) {
-        for (uint32_t i = t; i < kt - k; i += kShadowThreads) {
+      // once every ray stopped the rest of the batch's occluders form one
+      // window that nobody loads
+      const uint32_t kt = dead ? klast : min(klast, k + (uint32_t)kOccWin);
+      if (!dead) {
+        // an occluder of an earlier batch carries the quadrants where it passed
+        // as a receiver; one of this batch is looked up when it is used
+        for (uint32_t i = lane; i < kt - k; i += kShadowThreads) {
           make_entry(p.rrec[p.list[k + i]], ox, oy, S.o0[i], S.o1[i]);
           if (k + i < rb) S.o1[i].w = __uint_as_float((uint32_t)p.pass_mask[k + i]);
         }
       }
-      __syncthreads();
+      __syncwarp();
       const uint32_t ow = k;
       for (; jj < rc; ++jj) {
         const uint32_t kend = S.rk[jj];
@@ -148,63 +188,70 @@ __global__ void __launch_bounds__(kShadowThreads, 8) k_shadow(ShadowParams p) {
         if (dead) {
           k = max(k, kend);
         } else if (k < kend) {
-          for (; k < kend; ++k) {
-            const float4 o1 = S.o1[k - ow];
-            if (__float_as_uint(o1.w) & wbit) occlude(S.o0[k - ow], o1, lx, ly0, ly1, omin, k + 1, A0, A1, lim0, lim1);
-          }
-          dead = __all_sync(0xffffffffu, !(A0 >= kShadowStop) && !(A1 >= kShadowStop));
+          for (; k < kend; ++k) occlude8((int)(k - ow), k, rb);
+          dead = !still_alive();
         }
+        // receiver jj: sum (beta A, beta) over the tile's 256 rays
         const float4 r1 = S.r1[jj];
-        if (__float_as_uint(r1.w) & wbit) {
-          const float4 r0 = S.r0[jj];
-          float p0, p1;
-          powers2(r0, r1.x, lx, ly0, ly1, p0, p1);
-          const bool q0 = p0 >= r1.y, q1 = p1 >= r1.y;
-          if (__any_sync(0xffffffffu, q0 || q1)) {
-            if (lane == 0) atomicOr(&S.rpass[jj], wbit);
-            const float b0 = q0 ? ex2(p0) : 0.f;
-            const float b1 = q1 ? ex2(p1) : 0.f;
-            const float num = fmaf(b0, A0, b1 * A1), den = b0 + b1;
-            // two sums with one butterfly: lanes 0-15 end with num, 16-31 with den
-            float v = (hi_lane ? den : num) + __shfl_xor_sync(0xffffffffu, hi_lane ? num : den, 16);
+        const uint32_t box = __float_as_uint(r1.w);
+        const float4 r0 = S.r0[jj];
+        const float dx = lx - r0.x;
+        const float sx = (r0.z * dx) * dx, v = r1.x * dx;
+        float num = 0.f, den = 0.f;
+        bool hit[2] = {false, false};
 #pragma unroll
-            for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-            if (lane == 0) S.red[warp][jj].x = v;
-            if (lane == 16) S.red[warp][jj].y = v;
+        for (int h = 0; h < 2; ++h) {
+          if (!(box & (3u << (2 * h)))) continue;
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int i8 = 4 * h + q;
+            const float dy = ly[i8] - r0.y;
+            const float pw = fmaf(dy, fmaf(r0.w, dy, v), sx);
+            if (pw >= r1.y) {
+              const float beta = ex2(pw);
+              num = fmaf(beta, A[i8], num);
+              den += beta;
+              hit[h] = true;
+            }
           }
         }
+        const uint32_t bits = quadrants(__ballot_sync(0xffffffffu, hit[0]), __ballot_sync(0xffffffffu, hit[1]));
+        float2 sum = make_float2(0.f, 0.f);
+        if (bits) {
+          // two sums with one butterfly: lanes 0-15 end with num, 16-31 with den
+          const bool hi = (lane & 16) != 0;
+          float s2 = (hi ? den : num) + __shfl_xor_sync(0xffffffffu, hi ? num : den, 16);
+#pragma unroll
+          for (int o = 8; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+          sum = make_float2(s2, __shfl_sync(0xffffffffu, s2, 16));
+        }
+        if (lane == 0) {
+          p.partial[S.rslot[jj]] = sum;
+          p.pass_mask[rb + jj] = (uint8_t)bits;
+          S.rpass[jj] = bits;
+        }
+        __syncwarp();  // rpass is read by later occluders
       }
       if (dead) {  // the next receiver needs occluders past this window
         k = max(k, kt);
       } else if (k < kt) {
-        for (; k < kt; ++k) {
-          const float4 o1 = S.o1[k - ow];
-          if (__float_as_uint(o1.w) & wbit) occlude(S.o0[k - ow], o1, lx, ly0, ly1, omin, k + 1, A0, A1, lim0, lim1);
-        }
-        dead = __all_sync(0xffffffffu, !(A0 >= kShadowStop) && !(A1 >= kShadowStop));
+        for (; k < kt; ++k) occlude8((int)(k - ow), k, rb);
+        dead = !still_alive();
+      }
+      __syncwarp();  // the window is consumed
+    }
+  }
+  // the product where each ray ended and where it stopped (the backward starts from them)
+  if (inx) {
+#pragma unroll
+    for (int i = 0; i < kPx; ++i) {
+      const int y = ty * kTile + lyi + 2 * i;
+      if (y < p.H) {
+        const size_t pix = (size_t)y * p.W + tx * kTile + lxi;
+        p.light_final[pix] = A[i];
+        p.light_stop[pix] = lim[i];
       }
     }
-    __syncthreads();
-    if (t < rc) {
-      // only the warps with a passing pixel wrote a sum; added in fixed order
-      const uint32_t m = S.rpass[t];
-      float2 sum = make_float2(0.f, 0.f);
-#pragma unroll
-      for (int w = 0; w < 4; ++w)
-        if (m & (1u << w)) { sum.x += S.red[w][t].x; sum.y += S.red[w][t].y; }
-      p.partial[S.rslot[t]] = sum;
-      p.pass_mask[rb + t] = (uint8_t)m;
-    }
-  }
-  // the product where the ray ended and where it stopped (the backward starts from them)
-  const int gxp = tx * kTile + lxi;
-  if (in0) {
-    p.light_final[(size_t)(ty * kTile + lyi) * p.W + gxp] = A0;
-    p.light_stop[(size_t)(ty * kTile + lyi) * p.W + gxp] = lim0;
-  }
-  if (in1) {
-    p.light_final[(size_t)(ty * kTile + lyi + 4) * p.W + gxp] = A1;
-    p.light_stop[(size_t)(ty * kTile + lyi + 4) * p.W + gxp] = lim1;
   }
 }
 
@@ -440,11 +487,10 @@ void launch_shadow_composite(const FrameArgs& f, cudaStream_t s) {
   p.amax = f.opts.alpha_max;
   static bool configured = false;
   if (!configured) {
-    cudaFuncSetAttribute(k_shadow, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(ShadowSmem));
     cudaFuncSetAttribute(k_shadow, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
     configured = true;
   }
-  k_shadow<<<f.L->ntiles, kShadowThreads, sizeof(ShadowSmem), s>>>(p);
+  k_shadow<<<f.L->ntiles, kShadowThreads, 0, s>>>(p);
   count_launch();
 }
 

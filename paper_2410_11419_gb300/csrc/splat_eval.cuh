@@ -1,10 +1,9 @@
 // Shadow-splat evaluation shared by the forward composite (composite.cu) and
 // its backward (backward.cu), so both take every alpha decision with the
-// same arithmetic.
-//
-// A 16x16 light tile is covered by 128 threads, two pixels each: warp w owns
-// the 8x8 block at (8 (w & 1), 8 (w >> 1)); lane l the pixels (l & 7, l >> 3)
-// and (l & 7, (l >> 3) + 4) of it.
+// same arithmetic: the power at pixel (lx, ly) of a tile is
+// fma(dy, fma(c, dy, r dx), (a dx) dx) with dx = lx - ux, dy = ly - vy,
+// whatever the thread layout.  Quadrant w of a 16x16 tile is the 8x8 block
+// at (8 (w & 1), 8 (w >> 1)).
 #pragma once
 #include "gs3_internal.cuh"
 
@@ -67,26 +66,6 @@ __device__ __forceinline__ void powers2(const float4 e0, float r, float lx, floa
 // kShadowStop (1 - alpha_max), far from the denormals.
 constexpr float kShadowStop = 0x1p-40f;
 constexpr uint32_t kNoStop = 0xFFFFFFFFu;  // the ray never stopped
-
-// one occluder (list index k) on both rays: A *= 1 - min(amax, gamma beta)
-// where it passes (alpha >= alpha_min, i.e. power2 >= thr; the conic is
-// positive definite, so the power needs no sign test), written as
-// max(1 - amax, 1 - gamma beta), on rays that have not stopped; a ray that
-// stops here records lim = k + 1 (it took the occluders below lim).
-__device__ __forceinline__ void occlude(const float4 o0, const float4 o1, float lx, float ly0, float ly1,
-                                        float omin, uint32_t k1, float& A0, float& A1, uint32_t& lim0,
-                                        uint32_t& lim1) {
-  float p0, p1;
-  powers2(o0, o1.x, lx, ly0, ly1, p0, p1);
-  if (p0 >= o1.y && A0 >= kShadowStop) {
-    A0 *= fmaxf(omin, fmaf(-o1.z, ex2(p0), 1.f));
-    if (A0 < kShadowStop) lim0 = k1;
-  }
-  if (p1 >= o1.y && A1 >= kShadowStop) {
-    A1 *= fmaxf(omin, fmaf(-o1.z, ex2(p1), 1.f));
-    if (A1 < kShadowStop) lim1 = k1;
-  }
-}
 
 }  // namespace
 }  // namespace gs3
