@@ -280,7 +280,8 @@ def serving_mix(a, dev, np, torch, N, R, synth):
     for si in range(len(scenes)):  # learn every (scene, resolution) capacity, warm the pool
         for res in MIX_RES:
             cam, light = synth.camera_light_pair(7, res, res)
-            st = srv.wait(srv.submit(ids[si], cam, light, torch.empty((res, res, 3), device=dev)))[0]
+            out = torch.empty((res, res, 3), device=dev)  # alive until the request completes
+            st = srv.wait(srv.submit(ids[si], cam, light, out))[0]
             assert st == 0, st
     torch.cuda.synchronize()
     gaps = {rate: np.random.default_rng(rate).exponential(1.0 / rate, nreq) for rate in MIX_RATES}

@@ -348,6 +348,9 @@ gs3_status gs3_server_add_scene(gs3_server *server, gs3_scene *scene, int32_t *s
 
 /* Queue one frame.  camera, light, opts: host structs, copied.  out_rgb:
  * device float32 [height][width][3], caller-owned, written when the request
+ * completes.  The server's streams do not wait for work queued on other
+ * streams: nothing may still be writing out_rgb when it is submitted (the
+ * caller synchronises first), and it must stay allocated until the request
  * completes.  Returns at once with a ticket.  Errors: INVALID_ARG. */
 gs3_status gs3_server_submit(gs3_server *server, int32_t scene_id, const gs3_camera *camera,
                              const gs3_light *light, const gs3_render_opts *opts, float *out_rgb,

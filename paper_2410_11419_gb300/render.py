@@ -201,6 +201,9 @@ class Server:
         return N.gs3_server_add_scene(self.handle, dscene.handle)
 
     def submit(self, scene_id: int, cam, light, out, opts=None) -> int:
+        """Queue a frame into `out` (device [H, W, 3] float32).  The server's
+        streams do not wait for torch's: no pending kernel may write `out`,
+        and it must stay alive until the request completes."""
         opts = opts if opts is not None else opts_struct()
         return N.gs3_server_submit(self.handle, scene_id, camera_struct(cam), light_struct(light),
                                    opts, out)

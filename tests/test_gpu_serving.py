@@ -43,11 +43,11 @@ def test_mixed_requests_equal_alone(scenes):
     from paper_2410_11419_gb300 import render as R
     srv = R.Server(hbm_budget=8 << 30, max_inflight=4)
     ids = [srv.add_scene(d) for d in scenes]
-    outs, tickets = [], []
-    for si, res, seed in MIX:
+    outs = [torch.full((res, res, 3), -1.0, device="cuda") for _, res, _ in MIX]
+    torch.cuda.synchronize()  # the server's streams do not wait for torch's fills
+    tickets = []
+    for (si, res, seed), out in zip(MIX, outs):
         cam, light = synth.camera_light_pair(seed, res, res)
-        out = torch.full((res, res, 3), -1.0, device="cuda")
-        outs.append(out)
         tickets.append(srv.submit(ids[si], cam, light, out))
     lat = []
     for t in tickets:
