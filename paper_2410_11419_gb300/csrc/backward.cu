@@ -229,21 +229,25 @@ __global__ void k_copy_strided(const float* src, int stride, int off, float* dst
 // ---------------------------------------------------------------------------
 // K6b: shadow splat backward.
 // Reverse sweep of the forward's two-cursor pass over each light tile, with
-// the forward's thread layout, entries and alpha decisions (splat_eval.cuh).
-// Per ray m the thread restarts from the product A_m where the forward's ray
-// ended and the limit below which it took occluders (both stored by the
-// forward; a ray that stopped keeps its frozen product past the limit, so
-// occluders at or past it are skipped), and a suffix sum
-// S_m = sum coef_j beta_jm T_m(j) over the receivers already visited
-// (coef_j = dL/dT_j / den_j):
+// the forward's thread layout (one warp per tile, eight rays per lane), its
+// entries and alpha decisions (splat_eval.cuh).  Per ray m the lane restarts
+// from the product A_m where the forward's ray ended and the limit below
+// which it took occluders (both stored by the forward; a ray that stopped
+// keeps its frozen product past the limit, so occluders at or past it are
+// skipped), and a suffix sum S_m = sum coef_j beta_jm T_m(j) over the
+// receivers already visited (coef_j = dL/dT_j / den_j):
 //   occluder k (passing, taken):  A /= (1 - alpha_k),  dL/dalpha_k = -S / (1 - alpha_k)
 //   receiver j (passing):  dL/dbeta_j = coef_j (A - T_j),  S += coef_j beta_j A
 // with A = T_m(j) when receiver j is reached.  Occluders are undone before
 // the receiver whose prefix end K(j) they reach, so S holds exactly the
-// receivers with K(j) > k.  A warp skips every entry that passed nowhere in
-// its 8x8 block in the forward (the pass masks it stored).  Per entry and
-// role a warp sums its 64 rays' (du, dv, dA, dB, dC, dgamma) with one
-// transposing butterfly and adds them to the Gaussian's accumulators.
+// receivers with K(j) > k.  An entry is evaluated only in the halves of the
+// tile where it passed in the forward (the pass quadrants it stored).
+// With dL/dpower = w at a pixel (dx, dy) from the splat centre, the centre
+// and conic gradients are linear in (w, w dy, w dy^2) for a fixed dx, and
+// a lane's eight pixels share dx: each lane sums those three moments and
+// forms (du, dv, dA, dB, dC) once per entry; the warp then sums them and
+// dgamma over its 256 rays with one transposing butterfly and adds them to
+// the Gaussian's accumulators.
 // ---------------------------------------------------------------------------
 struct ShadowBwdParams {
   const uint32_t* list;
@@ -264,8 +268,9 @@ struct ShadowBwdParams {
 };
 
 constexpr int kBRecv = 128;
-constexpr int kBOcc = 512;
-constexpr int kBThreads = 128;
+constexpr int kBOcc = 160;
+constexpr int kBThreads = 32;
+constexpr int kBPx = 8;  // rays per lane: column lane & 15, rows (lane >> 4) + 2 i
 constexpr float kLn2 = 0.6931471805599453f;
 
 struct ShadowBwdSmem {
@@ -274,7 +279,6 @@ struct ShadowBwdSmem {
   float rc[kBRecv], rt[kBRecv];
   float4 o0[kBOcc], o1[kBOcc];
   uint32_t og[kBOcc];
-  uint32_t wlim[4];
 };
 
 // Sums v[0..7] over the warp with 9 shuffles.  Lane L ends with the total of
@@ -294,14 +298,18 @@ __device__ __forceinline__ float warp_sum8(const float (&v)[8], int lane) {
   return w;
 }
 
-// add d/dpower2-weighted geometry terms of one pixel: power2 = a dx^2 + r dx dy + c dy^2
-// (log2 units, dx = pixel - centre); dpw = dL/dpower in natural units
-__device__ __forceinline__ void add_power_grad(const float4 e0, float r, float dx, float dy, float dpw, float (&g)[8]) {
-  g[0] += -(2.f * e0.z * dx + r * dy) * kLn2 * dpw;  // d/du = A dx + B dy
-  g[1] += -(2.f * e0.w * dy + r * dx) * kLn2 * dpw;  // d/dv = C dy + B dx
-  g[2] += -0.5f * dx * dx * dpw;                     // d/dA
-  g[3] += -dx * dy * dpw;                            // d/dB
-  g[4] += -0.5f * dy * dy * dpw;                     // d/dC
+// The lane's (du, dv, dA, dB, dC) from its moments m0 = sum w, m1 = sum w dy,
+// m2 = sum w dy^2 at column offset dx, in g[0..4]: the power (log2 units) is
+// a dx^2 + r dx dy + c dy^2 (e0.z = a, e0.w = c), with the conic
+// (A, B, C) = -(2 a, r, 2 c) ln 2 and d/du = A dx + B dy, d/dv = C dy + B dx,
+// d/dA = -dx^2 / 2, d/dB = -dx dy, d/dC = -dy^2 / 2 (natural units).
+__device__ __forceinline__ void moments_to_grad(const float4 e0, float r, float dx, float m0, float m1, float m2,
+                                                float (&g)[8]) {
+  g[0] = -(2.f * e0.z * dx * m0 + r * m1) * kLn2;
+  g[1] = -(2.f * e0.w * m1 + r * dx * m0) * kLn2;
+  g[2] = -0.5f * dx * dx * m0;
+  g[3] = -dx * m1;
+  g[4] = -0.5f * m2;
 }
 
 __device__ __forceinline__ void flush_grad(float* dst, const float (&g)[8], int lane) {
@@ -310,71 +318,92 @@ __device__ __forceinline__ void flush_grad(float* dst, const float (&g)[8], int 
   if ((lane & 3) == 0 && idx < 6 && v != 0.f) atomicAdd(dst + idx, v);
 }
 
-__global__ void __launch_bounds__(kBThreads, 8) k_shadow_bwd(ShadowBwdParams p) {
-  extern __shared__ float4 smem_raw[];
-  ShadowBwdSmem& S = *reinterpret_cast<ShadowBwdSmem*>(smem_raw);
-  const int tile = (int)p.tile_order[blockIdx.x], tx = tile % p.gx, ty = tile / p.gx, t = threadIdx.x;
-  const int lane = t & 31, warp = t >> 5;
-  const uint32_t wbit = 1u << warp;
-  const int lxi = (warp & 1) * 8 + (lane & 7), lyi = (warp >> 1) * 8 + (lane >> 3);
-  const bool in0 = tx * kTile + lxi < p.W && ty * kTile + lyi < p.H;
-  const bool in1 = tx * kTile + lxi < p.W && ty * kTile + lyi + 4 < p.H;
+__global__ void __launch_bounds__(kBThreads, 17) k_shadow_bwd(ShadowBwdParams p) {
+  __shared__ ShadowBwdSmem S;
+  const int tile = (int)p.tile_order[blockIdx.x], tx = tile % p.gx, ty = tile / p.gx;
+  const int lane = threadIdx.x;
+  const int lxi = lane & 15, lyi = lane >> 4;
+  const bool inx = tx * kTile + lxi < p.W;
+  const float lx = lxi + 0.5f;
   const float kFar = 1.0e6f;  // off-image pixels never pass (same rule as the forward)
-  const float lx = lxi + 0.5f, ly0 = in0 ? lyi + 0.5f : kFar, ly1 = in1 ? lyi + 4.5f : kFar;
   const float ox = (float)(tx * kTile), oy = (float)(ty * kTile);
   const float omin = 1.f - p.amax;
   const uint32_t b = p.tile_start[tile], e = p.tile_start[tile + 1];
   if (b == e) return;
-  const int gxp = tx * kTile + lxi;
-  const size_t pix0 = (size_t)(ty * kTile + lyi) * p.W + gxp, pix1 = pix0 + (size_t)4 * p.W;
-  float A0 = in0 ? p.light_final[pix0] : 1.f;
-  float A1 = in1 ? p.light_final[pix1] : 1.f;
-  // a ray took the occluders below its limit; the warp skips those at or past
-  // all of its rays' limits, the block those past every warp's
-  const uint32_t lim0 = in0 ? p.light_stop[pix0] : 0u, lim1 = in1 ? p.light_stop[pix1] : 0u;
-  const uint32_t wlim = __reduce_max_sync(0xffffffffu, max(lim0, lim1));
-  if (lane == 0) S.wlim[warp] = wlim;
-  __syncthreads();
-  const uint32_t blim = max(max(S.wlim[0], S.wlim[1]), max(S.wlim[2], S.wlim[3]));
-  float S0 = 0.f, S1 = 0.f;
-  uint32_t kc = min(p.kbound[e - 1], max(blim, b));
-
-  // undo occluder kk (window slot i) at both rays; accumulate its gradient
-  auto occlude_bwd = [&](int i, uint32_t kk) {
-    if (kk >= wlim) return;
-    const float4 o1 = S.o1[i];
-    if (!(__float_as_uint(o1.w) & wbit)) return;
-    const float4 o0 = S.o0[i];
-    float pw0, pw1;
-    powers2(o0, o1.x, lx, ly0, ly1, pw0, pw1);
-    float g[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    const float pws[2] = {pw0, pw1}, lys[2] = {ly0, ly1};
-    const bool took[2] = {kk < lim0, kk < lim1};
-    float* As[2] = {&A0, &A1};
-    const float Ss[2] = {S0, S1};
+  float ly[kBPx], A[kBPx], Sm[kBPx];
+  uint32_t lim[kBPx];
+  uint32_t lmax = 0u;
 #pragma unroll
-    for (int q = 0; q < 2; ++q) {
-      const float pw = pws[q];
-      if (pw >= o1.y && took[q]) {
-        const float beta = ex2(pw), ga = o1.z * beta;
-        const float f = fmaxf(omin, fmaf(-o1.z, beta, 1.f));
-        const float inv = __frcp_rn(f);
-        *As[q] *= inv;
-        if (ga < p.amax) {  // alpha = gamma beta (not clamped)
-          const float dalpha = -Ss[q] * inv;
-          g[5] += dalpha * beta;  // d/dgamma
-          add_power_grad(o0, o1.x, lx - o0.x, lys[q] - o0.y, dalpha * ga, g);
+  for (int i = 0; i < kBPx; ++i) {
+    const int y = ty * kTile + lyi + 2 * i;
+    const bool in = inx && y < p.H;
+    const size_t pix = (size_t)y * p.W + tx * kTile + lxi;
+    ly[i] = in ? lyi + 2 * i + 0.5f : kFar;
+    A[i] = in ? p.light_final[pix] : 1.f;
+    lim[i] = in ? p.light_stop[pix] : 0u;  // an off-image ray took nothing
+    Sm[i] = 0.f;
+    lmax = max(lmax, lim[i]);
+  }
+  // occluders at or past every ray's limit were taken by none
+  const uint32_t wlim = __reduce_max_sync(0xffffffffu, lmax);
+  uint32_t kc = min(p.kbound[e - 1], max(wlim, b));
+
+  // undo occluder kk (window slot i) on the lane's rays; accumulate its gradient
+  auto occlude_bwd = [&](int i, uint32_t kk) {
+    const float4 o1 = S.o1[i];
+    const uint32_t bits = __float_as_uint(o1.w);
+    if (!bits) return;
+    const float4 o0 = S.o0[i];
+    const float dx = lx - o0.x;
+    const float sx = (o0.z * dx) * dx, v = o1.x * dx;
+    float m0 = 0.f, m1 = 0.f, m2 = 0.f, dg = 0.f;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      if (!(bits & (3u << (2 * h)))) continue;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int i8 = 4 * h + q;
+        const float dy = ly[i8] - o0.y;
+        const float pw = fmaf(dy, fmaf(o0.w, dy, v), sx);
+        if (pw >= o1.y && kk < lim[i8]) {
+          const float beta = ex2(pw), ga = o1.z * beta;
+          const float f = fmaxf(omin, fmaf(-o1.z, beta, 1.f));
+          const float inv = __frcp_rn(f);
+          A[i8] *= inv;
+          if (ga < p.amax) {  // alpha = gamma beta (not clamped)
+            const float dalpha = -Sm[i8] * inv;
+            dg = fmaf(dalpha, beta, dg);  // d/dgamma
+            const float w = dalpha * ga, wdy = w * dy;
+            m0 += w;
+            m1 += wdy;
+            m2 = fmaf(wdy, dy, m2);
+          }
         }
       }
     }
+    float g[8];
+    moments_to_grad(o0, o1.x, dx, m0, m1, m2, g);
+    g[5] = dg;
+    g[6] = g[7] = 0.f;
     flush_grad(p.light_geom + (size_t)kGeom * S.og[i], g, lane);
+  };
+  // load the occluder window [kt, kc)
+  auto load_window = [&](uint32_t kt) {
+    __syncwarp();
+    for (uint32_t i = lane; i < kc - kt; i += kBThreads) {
+      const uint32_t rank = p.list[kt + i];
+      make_entry(p.rrec[rank], ox, oy, S.o0[i], S.o1[i]);
+      S.o1[i].w = __uint_as_float((uint32_t)p.pass_mask[kt + i]);
+      S.og[i] = p.order[rank];
+    }
+    __syncwarp();
   };
 
   for (uint32_t re = e; re > b;) {
     const uint32_t rs = re > b + kBRecv ? re - kBRecv : b;
     const int rc = (int)(re - rs);
-    __syncthreads();
-    if (t < rc) {
+    __syncwarp();
+    for (int t = lane; t < rc; t += kBThreads) {
       const uint32_t rank = p.list[rs + t];
       const uint32_t g = p.order[rank];
       make_entry(p.rrec[rank], ox, oy, S.r0[t], S.r1[t]);
@@ -385,40 +414,45 @@ __global__ void __launch_bounds__(kBThreads, 8) k_shadow_bwd(ShadowBwdParams p) 
       S.rc[t] = den > 0.f ? p.dT[g] / den : 0.f;
       S.rt[t] = p.T[g];
     }
-    __syncthreads();
+    __syncwarp();
     int jj = rc - 1;
     while (jj >= 0) {
       const uint32_t kfirst = S.rk[0];
       const uint32_t kt = kc > kfirst + kBOcc ? kc - kBOcc : min(kfirst, kc);
-      __syncthreads();
-      for (uint32_t i = t; i < kc - kt; i += kBThreads) {
-        const uint32_t rank = p.list[kt + i];
-        make_entry(p.rrec[rank], ox, oy, S.o0[i], S.o1[i]);
-        S.o1[i].w = __uint_as_float((uint32_t)p.pass_mask[kt + i]);
-        S.og[i] = p.order[rank];
-      }
-      __syncthreads();
+      load_window(kt);
       for (; jj >= 0; --jj) {
         const uint32_t kend = S.rk[jj];
         if (kend < kt) break;
         for (; kc > kend; --kc) occlude_bwd((int)(kc - 1 - kt), kc - 1);
         const float4 r1 = S.r1[jj];
-        if (!(__float_as_uint(r1.w) & wbit)) continue;
+        const uint32_t bits = __float_as_uint(r1.w);
+        if (!bits) continue;
         const float4 r0 = S.r0[jj];
-        float pw0, pw1;
-        powers2(r0, r1.x, lx, ly0, ly1, pw0, pw1);
+        const float dx = lx - r0.x;
+        const float sx = (r0.z * dx) * dx, v = r1.x * dx;
         const float coef = S.rc[jj], Tj = S.rt[jj];
-        float g[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        if (pw0 >= r1.y) {
-          const float beta = ex2(pw0);
-          S0 = fmaf(coef * beta, A0, S0);
-          add_power_grad(r0, r1.x, lx - r0.x, ly0 - r0.y, coef * (A0 - Tj) * beta, g);
+        float m0 = 0.f, m1 = 0.f, m2 = 0.f;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          if (!(bits & (3u << (2 * h)))) continue;
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int i8 = 4 * h + q;
+            const float dy = ly[i8] - r0.y;
+            const float pw = fmaf(dy, fmaf(r0.w, dy, v), sx);
+            if (pw >= r1.y) {
+              const float cb = coef * ex2(pw);
+              Sm[i8] = fmaf(cb, A[i8], Sm[i8]);
+              const float w = cb * (A[i8] - Tj), wdy = w * dy;
+              m0 += w;
+              m1 += wdy;
+              m2 = fmaf(wdy, dy, m2);
+            }
+          }
         }
-        if (pw1 >= r1.y) {
-          const float beta = ex2(pw1);
-          S1 = fmaf(coef * beta, A1, S1);
-          add_power_grad(r0, r1.x, lx - r0.x, ly1 - r0.y, coef * (A1 - Tj) * beta, g);
-        }
+        float g[8];
+        moments_to_grad(r0, r1.x, dx, m0, m1, m2, g);
+        g[5] = g[6] = g[7] = 0.f;
         flush_grad(p.light_geom + (size_t)kGeom * S.rg[jj], g, lane);
       }
       for (; kc > kt; --kc) occlude_bwd((int)(kc - 1 - kt), kc - 1);
@@ -428,14 +462,7 @@ __global__ void __launch_bounds__(kBThreads, 8) k_shadow_bwd(ShadowBwdParams p) 
   // occluders below every receiver's prefix end: S holds all receivers
   while (kc > b) {
     const uint32_t kt = kc > b + kBOcc ? kc - kBOcc : b;
-    __syncthreads();
-    for (uint32_t i = t; i < kc - kt; i += kBThreads) {
-      const uint32_t rank = p.list[kt + i];
-      make_entry(p.rrec[rank], ox, oy, S.o0[i], S.o1[i]);
-      S.o1[i].w = __uint_as_float((uint32_t)p.pass_mask[kt + i]);
-      S.og[i] = p.order[rank];
-    }
-    __syncthreads();
+    load_window(kt);
     for (; kc > kt; --kc) occlude_bwd((int)(kc - 1 - kt), kc - 1);
   }
 }
@@ -888,7 +915,7 @@ gs3_status run_backward(const FrameArgs& f, const float* dimg, void* bws, size_t
                            (int)cudaSharedmemCarveoutMaxShared);
       configured = true;
     }
-    k_shadow_bwd<<<L.ntiles, kBThreads, sizeof(ShadowBwdSmem), s>>>(p);
+    k_shadow_bwd<<<L.ntiles, kBThreads, 0, s>>>(p);
     count_launch();
   }
   // K1b
