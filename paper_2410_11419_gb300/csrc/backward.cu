@@ -241,7 +241,7 @@ __global__ void k_copy_strided(const float* src, int stride, int off, float* dst
 // with A = T_m(j) when receiver j is reached.  Occluders are undone before
 // the receiver whose prefix end K(j) they reach, so S holds exactly the
 // receivers with K(j) > k.  An entry is evaluated only in the halves of the
-// tile where it passed in the forward (the pass quadrants it stored).
+// tile where it passed in the forward (the pass halves it stored).
 // With dL/dpower = w at a pixel (dx, dy) from the splat centre, the centre
 // and conic gradients are linear in (w, w dy, w dy^2) for a fixed dx, and
 // a lane's eight pixels share dx: each lane sums those three moments and

@@ -53,11 +53,11 @@ __device__ __forceinline__ float splat_power(const float4 a, const float4 b, flo
 // they need through a window of up to kOccWin records, and each lane keeps
 // its eight rays' products A over the consumed occluders.  Records hold the
 // splat centre relative to the tile origin (pixel offsets are one exact
-// subtraction), the pre-scaled conic and the quadrants (8x8 blocks) the
-// splat's alpha >= alpha_min box reaches; a half of the tile that no
-// quadrant bit covers is not evaluated.  Per receiver the warp sums
-// (beta A, beta) over its 256 rays into the (tile, Gaussian) partial and
-// records the quadrants where it passed (ballots); an occluder is evaluated
+// subtraction) and the pre-scaled conic.  A receiver is evaluated only in
+// the halves of the tile (8 rows each) that both its alpha >= alpha_min box
+// and its ellipse reach.  Per receiver the warp sums (beta A, beta) over its
+// 256 rays into the (tile, Gaussian) partial and records the halves where it
+// passed (two votes, as quadrant bits 0x3 / 0xC); an occluder is evaluated
 // only in the halves where it passed as a receiver (same power test).  A ray
 // stops taking occluders once its product is below kShadowStop, and the
 // warp skips occluders, and loads no occluder window, once all its rays
@@ -67,7 +67,6 @@ constexpr int kRecv = 128;
 constexpr int kOccWin = 192;
 constexpr int kShadowThreads = 32;
 constexpr int kPx = 8;  // pixels per lane
-constexpr uint32_t kLeft = 0x00FF00FFu;  // lanes of columns 0-7
 
 struct ShadowParams {
   const uint32_t* list;
@@ -76,7 +75,7 @@ struct ShadowParams {
   const uint32_t* off;
   const uint32_t* kbound;
   const uint32_t* tile_order;  // block b renders tile tile_order[b]
-  uint8_t* pass_mask;  // per list entry: quadrants with a passing pixel (written as receiver)
+  uint8_t* pass_mask;  // per list entry: halves with a passing pixel, 0x3 rows 0-7, 0xC rows 8-15
   float2* partial;
   float* light_final;     // per light pixel: the product where the ray ended
   uint32_t* light_stop;   // per light pixel: 1 + index of the occluder that stopped it, or kNoStop
@@ -87,14 +86,38 @@ struct ShadowParams {
 struct ShadowSmem {
   float4 r0[kRecv], r1[kRecv];
   uint32_t rk[kRecv], rslot[kRecv];
-  uint32_t rpass[kRecv];  // quadrants in which the receiver passed
+  uint32_t rpass[kRecv];  // halves in which the receiver passed
   float4 o0[kOccWin], o1[kOccWin];
 };
 
-// quadrant bits of a half-tile ballot pair: bit 0/1 top left/right, 2/3 bottom
-__device__ __forceinline__ uint32_t quadrants(uint32_t top, uint32_t bottom) {
-  return ((top & kLeft) ? 1u : 0u) | ((top & ~kLeft) ? 2u : 0u) | ((bottom & kLeft) ? 4u : 0u) |
-         ((bottom & ~kLeft) ? 8u : 0u);
+// Halves of a tile (0x3: rows 0-7, 0xC: rows 8-15, as quadrant bits) where
+// the entry's alpha >= alpha_min ellipse can hold a pixel centre.  With
+// q = -power2 = al dx^2 + be dx dy + ga dy^2 (positive definite), a pixel
+// passes where q <= -thr.  The minimum of q over a half's rectangle of pixel
+// centres is 0 if the splat centre lies inside, else it lies on an edge: on
+// x = X the minimiser is dy = -be X / (2 ga) clamped to the edge, on y = Y
+// dx = -be Y / (2 al).  The margin, 1e-4 of a bound on the terms' size, is far
+// above the FP32 rounding of either side, so a half with a passing pixel is
+// never dropped; only the work is culled, not the result.
+__device__ __forceinline__ uint32_t ellipse_halves(const float4 e0, const float4 e1) {
+  const float al = -e0.z, ga = -e0.w, be = -e1.x, lim = -e1.y;
+  const float X0 = 0.5f - e0.x, X1 = 15.5f - e0.x;
+  const float mx = fmaxf(X0 * X0, X1 * X1);
+  auto q = [&](float dx, float dy) { return fmaf(dx, fmaf(al, dx, be * dy), ga * dy * dy); };
+  uint32_t m = 0u;
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const float Y0 = 8.f * h + 0.5f - e0.y, Y1 = 8.f * h + 7.5f - e0.y;
+    float best = 0.f;
+    if (!(X0 <= 0.f && X1 >= 0.f && Y0 <= 0.f && Y1 >= 0.f)) {
+      const float kx = -be / (2.f * ga), ky = -be / (2.f * al);
+      best = fminf(fminf(q(X0, fminf(fmaxf(kx * X0, Y0), Y1)), q(X1, fminf(fmaxf(kx * X1, Y0), Y1))),
+                   fminf(q(fminf(fmaxf(ky * Y0, X0), X1), Y0), q(fminf(fmaxf(ky * Y1, X0), X1), Y1)));
+    }
+    const float size = 2.f * (al * mx + ga * fmaxf(Y0 * Y0, Y1 * Y1));
+    if (best <= lim + 1e-4f * (1.f + size)) m |= 3u << (2 * h);
+  }
+  return m;
 }
 
 __global__ void __launch_bounds__(kShadowThreads, 17) k_shadow(ShadowParams p) {
@@ -161,7 +184,12 @@ __global__ void __launch_bounds__(kShadowThreads, 17) k_shadow(ShadowParams p) {
     for (int t = lane; t < rc; t += kShadowThreads) {
       const uint32_t rank = p.list[rb + t];
       const SplatRec q = p.rrec[rank];
-      make_entry(q, ox, oy, S.r0[t], S.r1[t]);
+      float4 e0, e1;
+      make_entry(q, ox, oy, e0, e1);
+      // a half must be reached by the alpha box (one of its quadrants) and by the ellipse
+      e1.w = __uint_as_float(__float_as_uint(e1.w) & ellipse_halves(e0, e1));
+      S.r0[t] = e0;
+      S.r1[t] = e1;
       S.rk[t] = p.kbound[rb + t];
       S.rslot[t] = p.off[rank] + (uint32_t)((ty - q.r.y) * (q.r.z - q.r.x + 1) + (tx - q.r.x));
     }
@@ -173,7 +201,7 @@ __global__ void __launch_bounds__(kShadowThreads, 17) k_shadow(ShadowParams p) {
       // window that nobody loads
       const uint32_t kt = dead ? klast : min(klast, k + (uint32_t)kOccWin);
       if (!dead) {
-        // an occluder of an earlier batch carries the quadrants where it passed
+        // an occluder of an earlier batch carries the halves where it passed
         // as a receiver; one of this batch is looked up when it is used
         for (uint32_t i = lane; i < kt - k; i += kShadowThreads) {
           make_entry(p.rrec[p.list[k + i]], ox, oy, S.o0[i], S.o1[i]);
@@ -194,6 +222,15 @@ __global__ void __launch_bounds__(kShadowThreads, 17) k_shadow(ShadowParams p) {
         // receiver jj: sum (beta A, beta) over the tile's 256 rays
         const float4 r1 = S.r1[jj];
         const uint32_t box = __float_as_uint(r1.w);
+        if (!box) {  // its ellipse reaches no pixel centre of the tile
+          if (lane == 0) {
+            p.partial[S.rslot[jj]] = make_float2(0.f, 0.f);
+            p.pass_mask[rb + jj] = 0;
+            S.rpass[jj] = 0u;
+          }
+          __syncwarp();
+          continue;
+        }
         const float4 r0 = S.r0[jj];
         const float dx = lx - r0.x;
         const float sx = (r0.z * dx) * dx, v = r1.x * dx;
@@ -215,7 +252,7 @@ __global__ void __launch_bounds__(kShadowThreads, 17) k_shadow(ShadowParams p) {
             }
           }
         }
-        const uint32_t bits = quadrants(__ballot_sync(0xffffffffu, hit[0]), __ballot_sync(0xffffffffu, hit[1]));
+        const uint32_t bits = (__any_sync(0xffffffffu, hit[0]) ? 0x3u : 0u) | (__any_sync(0xffffffffu, hit[1]) ? 0xCu : 0u);
         float2 sum = make_float2(0.f, 0.f);
         if (bits) {
           // two sums with one butterfly: lanes 0-15 end with num, 16-31 with den
