@@ -49,22 +49,26 @@ __device__ __forceinline__ float splat_power(const float4 a, const float4 b, flo
 //
 // One warp per 16x16 tile, eight pixels per lane: lane l owns column l & 15,
 // rows (l >> 4) + 2 i, i = 0..7 (i < 4: the tile's top half).  The warp walks
-// the tile's list once: receivers are staged 128 at a time, the occluders
+// the tile's list once: receivers are staged kRecv at a time, the occluders
 // they need through a window of up to kOccWin records, and each lane keeps
 // its eight rays' products A over the consumed occluders.  Records hold the
 // splat centre relative to the tile origin (pixel offsets are one exact
 // subtraction) and the pre-scaled conic.  A receiver is evaluated only in
 // the halves of the tile (8 rows each) that both its alpha >= alpha_min box
-// and its ellipse reach.  Per receiver the warp sums (beta A, beta) over its
-// 256 rays into the (tile, Gaussian) partial and records the halves where it
-// passed (two votes, as quadrant bits 0x3 / 0xC); an occluder is evaluated
+// and its ellipse reach.  Per receiver each lane sums (beta A, beta) over its
+// eight rays into a shared-memory row; every kRedGroup receivers the warp
+// adds the rows' 32 lane sums per receiver, in lane order, into the
+// (tile, Gaussian) partials (no shuffle chain per receiver).  The halves
+// where a receiver passed are recorded at once (two votes, as quadrant bits
+// 0x3 / 0xC); an occluder is evaluated
 // only in the halves where it passed as a receiver (same power test).  A ray
 // stops taking occluders once its product is below kShadowStop, and the
 // warp skips occluders, and loads no occluder window, once all its rays
 // stopped.
 // ---------------------------------------------------------------------------
-constexpr int kRecv = 128;
-constexpr int kOccWin = 192;
+constexpr int kRecv = 64;
+constexpr int kOccWin = 128;
+constexpr int kRedGroup = 16;  // receivers whose per-lane sums are reduced together
 constexpr int kShadowThreads = 32;
 constexpr int kPx = 8;  // pixels per lane
 
@@ -88,6 +92,7 @@ struct ShadowSmem {
   uint32_t rk[kRecv], rslot[kRecv];
   uint32_t rpass[kRecv];  // halves in which the receiver passed
   float4 o0[kOccWin], o1[kOccWin];
+  float2 red[kRedGroup][33];  // per receiver of the group, per lane: (num, den); padded row
 };
 
 // Halves of a tile (0x3: rows 0-7, 0xC: rows 8-15, as quadrant bits) where
@@ -120,7 +125,7 @@ __device__ __forceinline__ uint32_t ellipse_halves(const float4 e0, const float4
   return m;
 }
 
-__global__ void __launch_bounds__(kShadowThreads, 17) k_shadow(ShadowParams p) {
+__global__ void __launch_bounds__(kShadowThreads, 18) k_shadow(ShadowParams p) {
   __shared__ ShadowSmem S;
   const int tile = (int)p.tile_order[blockIdx.x];
   const int tx = tile % p.gx, ty = tile / p.gx;
@@ -178,6 +183,23 @@ __global__ void __launch_bounds__(kShadowThreads, 17) k_shadow(ShadowParams p) {
     return __any_sync(0xffffffffu, alive);
   };
 
+  // Sums of the receivers of group [j0, jl]: lane t < 16 adds num of receiver
+  // j0 + t over the 32 lanes, lane 16 + t its den, in lane order.
+  auto reduce_group = [&](int jl) {
+    const int j0 = jl - jl % kRedGroup;
+    const int t = lane & 15, c = lane >> 4;
+    if (j0 + t <= jl) {
+      const float* row = reinterpret_cast<const float*>(S.red[t]) + c;
+      float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+#pragma unroll
+      for (int l = 0; l < 32; l += 4) {
+        a0 += row[2 * l]; a1 += row[2 * l + 2]; a2 += row[2 * l + 4]; a3 += row[2 * l + 6];
+      }
+      reinterpret_cast<float*>(p.partial)[2 * (size_t)S.rslot[j0 + t] + c] = (a0 + a1) + (a2 + a3);
+    }
+    __syncwarp();  // the group's rows are free again
+  };
+
   for (uint32_t rb = b; rb < e; rb += kRecv) {
     const int rc = (int)min((uint32_t)kRecv, e - rb);
     __syncwarp();  // the previous batch is consumed
@@ -223,12 +245,13 @@ __global__ void __launch_bounds__(kShadowThreads, 17) k_shadow(ShadowParams p) {
         const float4 r1 = S.r1[jj];
         const uint32_t box = __float_as_uint(r1.w);
         if (!box) {  // its ellipse reaches no pixel centre of the tile
+          S.red[jj % kRedGroup][lane] = make_float2(0.f, 0.f);
           if (lane == 0) {
-            p.partial[S.rslot[jj]] = make_float2(0.f, 0.f);
             p.pass_mask[rb + jj] = 0;
             S.rpass[jj] = 0u;
           }
           __syncwarp();
+          if (jj % kRedGroup == kRedGroup - 1 || jj == rc - 1) reduce_group(jj);
           continue;
         }
         const float4 r0 = S.r0[jj];
@@ -253,21 +276,13 @@ __global__ void __launch_bounds__(kShadowThreads, 17) k_shadow(ShadowParams p) {
           }
         }
         const uint32_t bits = (__any_sync(0xffffffffu, hit[0]) ? 0x3u : 0u) | (__any_sync(0xffffffffu, hit[1]) ? 0xCu : 0u);
-        float2 sum = make_float2(0.f, 0.f);
-        if (bits) {
-          // two sums with one butterfly: lanes 0-15 end with num, 16-31 with den
-          const bool hi = (lane & 16) != 0;
-          float s2 = (hi ? den : num) + __shfl_xor_sync(0xffffffffu, hi ? num : den, 16);
-#pragma unroll
-          for (int o = 8; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
-          sum = make_float2(s2, __shfl_sync(0xffffffffu, s2, 16));
-        }
+        S.red[jj % kRedGroup][lane] = make_float2(num, den);
         if (lane == 0) {
-          p.partial[S.rslot[jj]] = sum;
           p.pass_mask[rb + jj] = (uint8_t)bits;
           S.rpass[jj] = bits;
         }
-        __syncwarp();  // rpass is read by later occluders
+        __syncwarp();  // rpass is read by later occluders; red by reduce_group
+        if (jj % kRedGroup == kRedGroup - 1 || jj == rc - 1) reduce_group(jj);
       }
       if (dead) {  // the next receiver needs occluders past this window
         k = max(k, kt);
