@@ -246,8 +246,8 @@ __global__ void k_copy_strided(const float* src, int stride, int off, float* dst
 // and conic gradients are linear in (w, w dy, w dy^2) for a fixed dx, and
 // a lane's eight pixels share dx: each lane sums those three moments and
 // forms (du, dv, dA, dB, dC) once per entry; the warp then sums them and
-// dgamma over its 256 rays with one transposing butterfly and adds them to
-// the Gaussian's accumulators.
+// dgamma over its 256 rays through shared-memory rows, four entries at a
+// time, and adds them to the Gaussian's accumulators.
 // ---------------------------------------------------------------------------
 struct ShadowBwdParams {
   const uint32_t* list;
@@ -267,8 +267,9 @@ struct ShadowBwdParams {
   float amax;
 };
 
-constexpr int kBRecv = 128;
-constexpr int kBOcc = 160;
+constexpr int kBRecv = 64;
+constexpr int kBOcc = 128;
+constexpr int kGradGroup = 4;  // entries whose per-lane gradients are reduced together
 constexpr int kBThreads = 32;
 constexpr int kBPx = 8;  // rays per lane: column lane & 15, rows (lane >> 4) + 2 i
 constexpr float kLn2 = 0.6931471805599453f;
@@ -279,24 +280,9 @@ struct ShadowBwdSmem {
   float rc[kBRecv], rt[kBRecv];
   float4 o0[kBOcc], o1[kBOcc];
   uint32_t og[kBOcc];
+  float gr[kGradGroup][6][33];  // per entry of the group, per gradient term, per lane (padded row)
+  uint32_t gg[kGradGroup];      // the entries' Gaussians
 };
-
-// Sums v[0..7] over the warp with 9 shuffles.  Lane L ends with the total of
-// value ((L >> 4) & 1) * 4 + ((L >> 3) & 1) * 2 + ((L >> 2) & 1).
-__device__ __forceinline__ float warp_sum8(const float (&v)[8], int lane) {
-  const bool h16 = (lane & 16) != 0, h8 = (lane & 8) != 0, h4 = (lane & 4) != 0;
-  float w4[4], w2[2];
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-    w4[i] = (h16 ? v[4 + i] : v[i]) + __shfl_xor_sync(0xffffffffu, h16 ? v[i] : v[4 + i], 16);
-#pragma unroll
-  for (int i = 0; i < 2; ++i)
-    w2[i] = (h8 ? w4[2 + i] : w4[i]) + __shfl_xor_sync(0xffffffffu, h8 ? w4[i] : w4[2 + i], 8);
-  float w = (h4 ? w2[1] : w2[0]) + __shfl_xor_sync(0xffffffffu, h4 ? w2[0] : w2[1], 4);
-  w += __shfl_xor_sync(0xffffffffu, w, 2);
-  w += __shfl_xor_sync(0xffffffffu, w, 1);
-  return w;
-}
 
 // The lane's (du, dv, dA, dB, dC) from its moments m0 = sum w, m1 = sum w dy,
 // m2 = sum w dy^2 at column offset dx, in g[0..4]: the power (log2 units) is
@@ -312,13 +298,7 @@ __device__ __forceinline__ void moments_to_grad(const float4 e0, float r, float 
   g[4] = -0.5f * m2;
 }
 
-__device__ __forceinline__ void flush_grad(float* dst, const float (&g)[8], int lane) {
-  const float v = warp_sum8(g, lane);
-  const int idx = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
-  if ((lane & 3) == 0 && idx < 6 && v != 0.f) atomicAdd(dst + idx, v);
-}
-
-__global__ void __launch_bounds__(kBThreads, 17) k_shadow_bwd(ShadowBwdParams p) {
+__global__ void __launch_bounds__(kBThreads, 18) k_shadow_bwd(ShadowBwdParams p) {
   __shared__ ShadowBwdSmem S;
   const int tile = (int)p.tile_order[blockIdx.x], tx = tile % p.gx, ty = tile / p.gx;
   const int lane = threadIdx.x;
@@ -347,6 +327,34 @@ __global__ void __launch_bounds__(kBThreads, 17) k_shadow_bwd(ShadowBwdParams p)
   // occluders at or past every ray's limit were taken by none
   const uint32_t wlim = __reduce_max_sync(0xffffffffu, lmax);
   uint32_t kc = min(p.kbound[e - 1], max(wlim, b));
+
+  // An entry's gradient terms, per lane, go to a shared-memory row; every
+  // kGradGroup entries lane 6 e + c (< 24) adds term c of entry e over the
+  // 32 lanes, in lane order, and adds the total to the Gaussian's
+  // accumulator.  No shuffle chain per entry.
+  int ng = 0;
+  auto reduce_grads = [&]() {
+    const int ge = lane / 6, gc = lane % 6;
+    if (ge < ng) {
+      const float* row = S.gr[ge][gc];
+      float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+#pragma unroll
+      for (int l = 0; l < 32; l += 4) {
+        a0 += row[l]; a1 += row[l + 1]; a2 += row[l + 2]; a3 += row[l + 3];
+      }
+      const float v = (a0 + a1) + (a2 + a3);
+      if (v != 0.f) atomicAdd(p.light_geom + (size_t)kGeom * S.gg[ge] + gc, v);
+    }
+    __syncwarp();  // the rows are free again
+    ng = 0;
+  };
+  auto push_grad = [&](uint32_t g, const float (&v)[8]) {
+#pragma unroll
+    for (int c = 0; c < 6; ++c) S.gr[ng][c][lane] = v[c];
+    if (lane == 0) S.gg[ng] = g;
+    __syncwarp();
+    if (++ng == kGradGroup) reduce_grads();
+  };
 
   // undo occluder kk (window slot i) on the lane's rays; accumulate its gradient
   auto occlude_bwd = [&](int i, uint32_t kk) {
@@ -385,7 +393,7 @@ __global__ void __launch_bounds__(kBThreads, 17) k_shadow_bwd(ShadowBwdParams p)
     moments_to_grad(o0, o1.x, dx, m0, m1, m2, g);
     g[5] = dg;
     g[6] = g[7] = 0.f;
-    flush_grad(p.light_geom + (size_t)kGeom * S.og[i], g, lane);
+    push_grad(S.og[i], g);
   };
   // load the occluder window [kt, kc)
   auto load_window = [&](uint32_t kt) {
@@ -453,7 +461,7 @@ __global__ void __launch_bounds__(kBThreads, 17) k_shadow_bwd(ShadowBwdParams p)
         float g[8];
         moments_to_grad(r0, r1.x, dx, m0, m1, m2, g);
         g[5] = g[6] = g[7] = 0.f;
-        flush_grad(p.light_geom + (size_t)kGeom * S.rg[jj], g, lane);
+        push_grad(S.rg[jj], g);
       }
       for (; kc > kt; --kc) occlude_bwd((int)(kc - 1 - kt), kc - 1);
     }
@@ -465,6 +473,7 @@ __global__ void __launch_bounds__(kBThreads, 17) k_shadow_bwd(ShadowBwdParams p)
     load_window(kt);
     for (; kc > kt; --kc) occlude_bwd((int)(kc - 1 - kt), kc - 1);
   }
+  if (ng) reduce_grads();
 }
 
 // ---------------------------------------------------------------------------
