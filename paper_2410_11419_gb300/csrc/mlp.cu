@@ -7,7 +7,10 @@
 //   PE(v) = [v, sin(2^k pi v), cos(2^k pi v)], k = 0..3, per component
 // with world-space unit directions w_i = (p_L - mu)/|.|, w_o = (p_C - mu)/|.|.
 // Each hidden layer is a 64 x width register-tiled FP32 product against the
-// layer's weights staged in shared memory; the output layer applies the
+// layer's weights staged in shared memory, transposed, in rows padded to
+// width + 4 floats: the staging stores of a warp (consecutive inputs k, one
+// output j) then spread over 8 banks instead of one, and the rows stay
+// 16-byte aligned for the vector loads of the product.  The output layer applies the
 // sigmoid.  Outputs go both by Gaussian index and, for the camera composite,
 // by camera depth rank.
 #include "gs3_internal.cuh"
@@ -104,7 +107,7 @@ __global__ void __launch_bounds__(256) k_mlp(MlpParams p) {
     __syncthreads();  // H complete, previous Ws no longer read
     for (int i = t; i < din * WIDTH; i += 256) {
       const int j = i / din, k = i - j * din;  // W row-major (out, in)
-      Ws[k * WIDTH + j] = w[i];
+      Ws[k * (WIDTH + 4) + j] = w[i];
     }
     __syncthreads();
     float acc[4][CPT];
@@ -118,7 +121,7 @@ __global__ void __launch_bounds__(256) k_mlp(MlpParams p) {
       const float4 a = *reinterpret_cast<const float4*>(&H[k][trow * 4]);
       float bv[CPT];
 #pragma unroll
-      for (int c = 0; c < CPT; ++c) bv[c] = Ws[k * WIDTH + tcol * CPT + c];
+      for (int c = 0; c < CPT; ++c) bv[c] = Ws[k * (WIDTH + 4) + tcol * CPT + c];
 #pragma unroll
       for (int c = 0; c < CPT; ++c) {
         acc[0][c] = fmaf(a.x, bv[c], acc[0][c]);
@@ -166,7 +169,7 @@ __global__ void __launch_bounds__(256) k_mlp(MlpParams p) {
 
 template <int WIDTH>
 void launch_width(const MlpParams& p, cudaStream_t s) {
-  const size_t sm = (size_t)(128 * kHPad + 128 * WIDTH) * sizeof(float);
+  const size_t sm = (size_t)(128 * kHPad + 128 * (WIDTH + 4)) * sizeof(float);
   static bool configured = false;
   if (!configured) {
     cudaFuncSetAttribute(k_mlp<WIDTH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
