@@ -142,50 +142,92 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint32_t* __r
   hist[threadIdx.x * nblocks + blockIdx.x] = cnt[threadIdx.x];
 }
 
+// The block's items are ranked within their digit (stable: rounds in order,
+// warps in order, lanes in order), staged in shared memory sorted by digit,
+// then written out by consecutive threads, so each digit's run of the block
+// leaves as contiguous stores instead of one scattered store per item.
+struct ScatterSmem {
+  uint32_t base[256];   // the block's first output slot per digit (scanned histogram)
+  uint32_t run[256];    // the block's items per digit so far
+  uint32_t start[256];  // first staging slot per digit
+  uint32_t wc[2][kSortThreads / 32][256];
+  uint32_t key[kSortTileItems], val[kSortTileItems];
+};
+
 __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
     const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint32_t* __restrict__ kout,
     uint32_t* __restrict__ vout, const uint32_t* n_ptr, uint32_t n_fixed, int shift,
     const uint32_t* __restrict__ hist, int nblocks) {
-  __shared__ uint32_t s_base[256];
-  __shared__ uint32_t s_run[256];
-  __shared__ uint32_t s_wc[2][kSortThreads / 32][256];
+  extern __shared__ uint4 scatter_raw[];
+  ScatterSmem& S = *reinterpret_cast<ScatterSmem*>(scatter_raw);
   const uint32_t n = load_n(n_ptr, n_fixed);
   const uint32_t base = blockIdx.x * kSortTileItems;
   if (base >= n) return;
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
   const uint32_t lt = (1u << lane) - 1u;
-  s_base[t] = hist[t * nblocks + blockIdx.x];
-  s_run[t] = 0;
+  S.base[t] = hist[t * nblocks + blockIdx.x];
+  S.run[t] = 0;
 #pragma unroll
-  for (int w = 0; w < kSortThreads / 32; ++w) { s_wc[0][w][t] = 0; s_wc[1][w][t] = 0; }
+  for (int w = 0; w < kSortThreads / 32; ++w) { S.wc[0][w][t] = 0; S.wc[1][w][t] = 0; }
   __syncthreads();
+  uint32_t kk[kSortRounds], vv[kSortRounds], rk[kSortRounds];
+#pragma unroll
   for (int r = 0; r < kSortRounds; ++r) {
     const int buf = r & 1;
     const uint32_t i = base + r * kSortThreads + t;
     const bool valid = i < n;
-    const uint32_t k = valid ? kin[i] : 0u;
-    const uint32_t v = valid ? (vin ? vin[i] : i) : 0u;
-    const uint32_t d = valid ? (k >> shift) & 255u : 256u;
+    kk[r] = valid ? kin[i] : 0u;
+    vv[r] = valid ? (vin ? vin[i] : i) : 0u;
+    const uint32_t d = valid ? (kk[r] >> shift) & 255u : 256u;
     const uint32_t peers = __match_any_sync(0xffffffffu, d);
     const uint32_t lrank = __popc(peers & lt);
-    if (valid && lrank == 0) s_wc[buf][warp][d] = __popc(peers);
+    if (valid && lrank == 0) S.wc[buf][warp][d] = __popc(peers);
     __syncthreads();
-    uint32_t acc = s_run[t];
+    uint32_t acc = S.run[t];
 #pragma unroll
     for (int w = 0; w < kSortThreads / 32; ++w) {
-      uint32_t c = s_wc[buf][w][t];
-      s_wc[buf][w][t] = acc;
+      uint32_t c = S.wc[buf][w][t];
+      S.wc[buf][w][t] = acc;
       acc += c;
-      s_wc[buf ^ 1][w][t] = 0;
+      S.wc[buf ^ 1][w][t] = 0;
     }
-    s_run[t] = acc;
+    S.run[t] = acc;
     __syncthreads();
-    if (valid) {
-      const uint32_t pos = s_base[d] + s_wc[buf][warp][d] + lrank;
-      if (pos < n) {
-        kout[pos] = k;
-        vout[pos] = v;
-      }
+    rk[r] = valid ? S.wc[buf][warp][d] + lrank : 0u;  // rank within the digit in the block
+  }
+  // first staging slot per digit: exclusive scan of the block's digit counts
+  {
+    const uint32_t c = S.run[t];
+    uint32_t x = c;
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    __syncthreads();  // every read of wc is done: reuse wc[0][0] for the warp sums
+    if (lane == 31) S.wc[0][0][warp] = x;
+    __syncthreads();
+    uint32_t before = 0;
+    for (int w = 0; w < warp; ++w) before += S.wc[0][0][w];
+    S.start[t] = before + x - c;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < kSortRounds; ++r) {
+    if (base + r * kSortThreads + t < n) {
+      const uint32_t lp = S.start[(kk[r] >> shift) & 255u] + rk[r];
+      S.key[lp] = kk[r];
+      S.val[lp] = vv[r];
+    }
+  }
+  __syncthreads();
+  const uint32_t cnt = min((uint32_t)kSortTileItems, n - base);
+  for (uint32_t i = t; i < cnt; i += kSortThreads) {
+    const uint32_t k = S.key[i];
+    const uint32_t d = (k >> shift) & 255u;
+    const uint32_t pos = S.base[d] + (i - S.start[d]);
+    if (pos < n) {
+      kout[pos] = k;
+      vout[pos] = S.val[i];
     }
   }
 }
@@ -275,7 +317,13 @@ void radix_sort(const uint32_t* kin, const uint32_t* vin, uint32_t* k0, uint32_t
     uint32_t* vo = (p & 1) ? v1 : v0;
     k_radix_hist<<<nblocks, kSortThreads, 0, s>>>(ki, n_ptr, n_fixed, 8 * p, hist, nblocks);
     device_exclusive_scan(hist, hist, 256u * nblocks, nullptr, scan_part, s);
-    k_radix_scatter<<<nblocks, kSortThreads, 0, s>>>(ki, vi, ko, vo, n_ptr, n_fixed, 8 * p, hist, nblocks);
+    static bool configured = false;
+    if (!configured) {
+      cudaFuncSetAttribute(k_radix_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(ScatterSmem));
+      configured = true;
+    }
+    k_radix_scatter<<<nblocks, kSortThreads, sizeof(ScatterSmem), s>>>(ki, vi, ko, vo, n_ptr, n_fixed, 8 * p, hist,
+                                                                      nblocks);
     count_launch(2);
     ki = ko;
     vi = vo;
