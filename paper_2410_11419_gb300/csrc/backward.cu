@@ -67,24 +67,6 @@ BwdPlan plan_bwd(int n, const MlpDev& phi, const MlpDev& psi) {
   return p;
 }
 
-__device__ __forceinline__ float warp_sum(float v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
-// sum over the warp and add to dst[0..n) from lane 0 (skipped when all zero)
-template <int NV>
-__device__ __forceinline__ void warp_atomic(float* dst, float (&v)[NV], bool any_lane) {
-  if (!__any_sync(0xffffffffu, any_lane)) return;
-#pragma unroll
-  for (int i = 0; i < NV; ++i) v[i] = warp_sum(v[i]);
-  if ((threadIdx.x & 31) == 0)
-#pragma unroll
-    for (int i = 0; i < NV; ++i)
-      if (v[i] != 0.f) atomicAdd(dst + i, v[i]);
-}
-
 // pixel offset, power and alpha of a splat record at a pixel centre
 struct Eval {
   float dx, dy, power, beta, alpha;
@@ -133,6 +115,26 @@ struct CamBwdParams {
   float amax;
 };
 
+// Sums v[0..15] over the warp with one transposing butterfly (16 shuffles):
+// each level sends the half of the remaining values that the partner lane
+// keeps.  Lane L ends with the total of value
+// 8 ((L >> 4) & 1) + 4 ((L >> 3) & 1) + 2 ((L >> 2) & 1) + ((L >> 1) & 1).
+__device__ __forceinline__ float warp_sum16(const float (&v)[16], int lane) {
+  float a8[8], a4[4], a2[2];
+  const bool h16 = (lane & 16) != 0, h8 = (lane & 8) != 0, h4 = (lane & 4) != 0, h2 = (lane & 2) != 0;
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+    a8[i] = (h16 ? v[8 + i] : v[i]) + __shfl_xor_sync(0xffffffffu, h16 ? v[i] : v[8 + i], 16);
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+    a4[i] = (h8 ? a8[4 + i] : a8[i]) + __shfl_xor_sync(0xffffffffu, h8 ? a8[i] : a8[4 + i], 8);
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+    a2[i] = (h4 ? a4[2 + i] : a4[i]) + __shfl_xor_sync(0xffffffffu, h4 ? a4[i] : a4[2 + i], 4);
+  float x = (h2 ? a2[1] : a2[0]) + __shfl_xor_sync(0xffffffffu, h2 ? a2[0] : a2[1], 2);
+  return x + __shfl_xor_sync(0xffffffffu, x, 1);
+}
+
 __global__ void __launch_bounds__(256) k_camera_bwd(CamBwdParams p) {
   __shared__ SplatRec R[256];
   __shared__ float4 C0[256], C1[256];
@@ -177,9 +179,9 @@ __global__ void __launch_bounds__(256) k_camera_bwd(CamBwdParams p) {
     for (int jj = cnt - 1; jj >= 0; --jj) {
       const uint32_t i = lo + jj;
       const bool active = inside && (i - b) < nc;
-      float gv[13];
+      float gv[16];
 #pragma unroll
-      for (int k = 0; k < 13; ++k) gv[k] = 0.f;
+      for (int k = 0; k < 16; ++k) gv[k] = 0.f;
       bool contrib = false;
       if (active) {
         const SplatRec q = R[jj];
@@ -204,16 +206,15 @@ __global__ void __launch_bounds__(256) k_camera_bwd(CamBwdParams p) {
         }
       }
       if (__any_sync(0xffffffffu, contrib)) {
-#pragma unroll
-        for (int k = 0; k < 13; ++k) gv[k] = warp_sum(gv[k]);
-        if ((t & 31) == 0) {
+        // geometry terms 0-5 and colour terms 6-12 in one butterfly; lane pair
+        // (2 k', 2 k' + 1) holds term k', and the even lane adds it
+        const int lane = t & 31;
+        const float v = warp_sum16(gv, lane);
+        const int k = ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
+        if ((lane & 1) == 0 && k < 13 && v != 0.f) {
           const uint32_t g = G[jj];
-#pragma unroll
-          for (int k = 0; k < 6; ++k)
-            if (gv[k] != 0.f) atomicAdd(p.cam_geom + (size_t)kGeom * g + k, gv[k]);
-#pragma unroll
-          for (int k = 0; k < 7; ++k)
-            if (gv[6 + k] != 0.f) atomicAdd(p.color + (size_t)kColor * g + k, gv[6 + k]);
+          if (k < 6) atomicAdd(p.cam_geom + (size_t)kGeom * g + k, v);
+          else atomicAdd(p.color + (size_t)kColor * g + (k - 6), v);
         }
       }
     }
