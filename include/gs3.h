@@ -219,7 +219,7 @@ gs3_status gs3_render(gs3_scene *scene, const gs3_camera *camera, const gs3_ligh
 /* Stage bits of gs3_render_stages (in pipeline order). */
 enum {
     GS3_STAGE_PREP = 1,             /* K1: shading colour, both projections, keys */
-    GS3_STAGE_CAMERA_BIN = 2,       /* camera splat: depth sort, pairs, tile sort, ranges */
+    GS3_STAGE_CAMERA_BIN = 2,       /* camera splat: depth sort, pairs, tile sort, ranges, tile launch order */
     GS3_STAGE_LIGHT_BIN = 4,        /* light splat: the same toward the light */
     GS3_STAGE_SHADOW_COMPOSITE = 8, /* shadow rays: biased transmittance, partial sums (Sec. 4.2) */
     GS3_STAGE_SHADOW_REDUCE = 16,   /* per-Gaussian beta-weighted average (Sec. 4.2) */

@@ -410,6 +410,7 @@ gs3_status render_frame(gs3_scene* scene, const gs3_camera* cam, const gs3_light
   if (stages & GS3_STAGE_CAMERA_BIN) {
     launch_depth_sort(f, 0, s);
     launch_binning(f, 0, s);
+    launch_tile_order(f, 0, s);  // the camera composite's launch order
   }
   if (fork) {
     cudaEventRecord(side->join, sl);

@@ -580,8 +580,7 @@ void launch_camera_composite(const FrameArgs& f, float* out_rgb, cudaStream_t s)
   p.pix_aux = at<float4>(ws, f.L->pix_aux);
   p.W = f.L->width; p.H = f.L->height; p.gx = f.L->gx;
   p.amax = f.opts.alpha_max; p.tstop = f.opts.t_stop;
-  launch_tile_order(f, 0, s);
-  p.tile_order = at<uint32_t>(ws, f.L->tile_order[0]);
+  p.tile_order = at<uint32_t>(ws, f.L->tile_order[0]);  // from the camera binning stage
   k_camera<<<f.L->ntiles, 256, 0, s>>>(p);
   count_launch();
 }
