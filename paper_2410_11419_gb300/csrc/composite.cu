@@ -200,6 +200,37 @@ __global__ void __launch_bounds__(kShadowThreads, 18) k_shadow(ShadowParams p) {
     __syncwarp();  // the group's rows are free again
   };
 
+  // receiver jj of the staged batch: the lane's (beta A, beta) sums over its
+  // eight rays, and the halves where it passed somewhere in the tile
+  auto eval_receiver = [&](int jj, float& num, float& den) -> uint32_t {
+    const float4 r1 = S.r1[jj];
+    const uint32_t box = __float_as_uint(r1.w);
+    num = 0.f;
+    den = 0.f;
+    if (!box) return 0u;  // its ellipse reaches no pixel centre of the tile
+    const float4 r0 = S.r0[jj];
+    const float dx = lx - r0.x;
+    const float sx = (r0.z * dx) * dx, v = r1.x * dx;
+    bool hit[2] = {false, false};
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      if (!(box & (3u << (2 * h)))) continue;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int i8 = 4 * h + q;
+        const float dy = ly[i8] - r0.y;
+        const float pw = fmaf(dy, fmaf(r0.w, dy, v), sx);
+        if (pw >= r1.y) {
+          const float beta = ex2(pw);
+          num = fmaf(beta, A[i8], num);
+          den += beta;
+          hit[h] = true;
+        }
+      }
+    }
+    return (__any_sync(0xffffffffu, hit[0]) ? 0x3u : 0u) | (__any_sync(0xffffffffu, hit[1]) ? 0xCu : 0u);
+  };
+
   for (uint32_t rb = b; rb < e; rb += kRecv) {
     const int rc = (int)min((uint32_t)kRecv, e - rb);
     __syncwarp();  // the previous batch is consumed
@@ -212,10 +243,25 @@ __global__ void __launch_bounds__(kShadowThreads, 18) k_shadow(ShadowParams p) {
       e1.w = __uint_as_float(__float_as_uint(e1.w) & ellipse_halves(e0, e1));
       S.r0[t] = e0;
       S.r1[t] = e1;
-      S.rk[t] = p.kbound[rb + t];
+      if (!dead) S.rk[t] = p.kbound[rb + t];
       S.rslot[t] = p.off[rank] + (uint32_t)((ty - q.r.y) * (q.r.z - q.r.x + 1) + (tx - q.r.x));
     }
     __syncwarp();
+    if (dead) {
+      // every ray stopped: no occluders, no windows, no pass lookups by
+      // occluders; the receivers only
+      for (int jj = 0; jj < rc; ++jj) {
+        float num, den;
+        const uint32_t bits = eval_receiver(jj, num, den);
+        S.red[jj % kRedGroup][lane] = make_float2(num, den);
+        if (lane == 0) p.pass_mask[rb + jj] = (uint8_t)bits;
+        if (jj % kRedGroup == kRedGroup - 1 || jj == rc - 1) {
+          __syncwarp();
+          reduce_group(jj);
+        }
+      }
+      continue;
+    }
     const uint32_t klast = S.rk[rc - 1];
     int jj = 0;
     while (jj < rc) {
@@ -242,40 +288,8 @@ __global__ void __launch_bounds__(kShadowThreads, 18) k_shadow(ShadowParams p) {
           dead = !still_alive();
         }
         // receiver jj: sum (beta A, beta) over the tile's 256 rays
-        const float4 r1 = S.r1[jj];
-        const uint32_t box = __float_as_uint(r1.w);
-        if (!box) {  // its ellipse reaches no pixel centre of the tile
-          S.red[jj % kRedGroup][lane] = make_float2(0.f, 0.f);
-          if (lane == 0) {
-            p.pass_mask[rb + jj] = 0;
-            S.rpass[jj] = 0u;
-          }
-          __syncwarp();
-          if (jj % kRedGroup == kRedGroup - 1 || jj == rc - 1) reduce_group(jj);
-          continue;
-        }
-        const float4 r0 = S.r0[jj];
-        const float dx = lx - r0.x;
-        const float sx = (r0.z * dx) * dx, v = r1.x * dx;
-        float num = 0.f, den = 0.f;
-        bool hit[2] = {false, false};
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          if (!(box & (3u << (2 * h)))) continue;
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const int i8 = 4 * h + q;
-            const float dy = ly[i8] - r0.y;
-            const float pw = fmaf(dy, fmaf(r0.w, dy, v), sx);
-            if (pw >= r1.y) {
-              const float beta = ex2(pw);
-              num = fmaf(beta, A[i8], num);
-              den += beta;
-              hit[h] = true;
-            }
-          }
-        }
-        const uint32_t bits = (__any_sync(0xffffffffu, hit[0]) ? 0x3u : 0u) | (__any_sync(0xffffffffu, hit[1]) ? 0xCu : 0u);
+        float num, den;
+        const uint32_t bits = eval_receiver(jj, num, den);
         S.red[jj % kRedGroup][lane] = make_float2(num, den);
         if (lane == 0) {
           p.pass_mask[rb + jj] = (uint8_t)bits;
