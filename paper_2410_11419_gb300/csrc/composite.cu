@@ -60,11 +60,10 @@ __device__ __forceinline__ float splat_power(const float4 a, const float4 b, flo
 // adds the rows' 32 lane sums per receiver, in lane order, into the
 // (tile, Gaussian) partials (no shuffle chain per receiver).  The halves
 // where a receiver passed are recorded at once (two votes, as quadrant bits
-// 0x3 / 0xC); an occluder is evaluated
-// only in the halves where it passed as a receiver (same power test).  A ray
-// stops taking occluders once its product is below kShadowStop, and the
-// warp skips occluders, and loads no occluder window, once all its rays
-// stopped.
+// 0x3 / 0xC); an occluder is evaluated only in the halves where it passed as
+// a receiver (same power test) and where some ray has not stopped.  A ray
+// stops taking occluders once its product is below kShadowStop; once all
+// 256 rays stopped, the warp walks the rest of the list as receivers only.
 // ---------------------------------------------------------------------------
 constexpr int kRecv = 64;
 constexpr int kOccWin = 128;
@@ -151,12 +150,13 @@ __global__ void __launch_bounds__(kShadowThreads, 18) k_shadow(ShadowParams p) {
   const float omin = 1.f - p.amax;
   const uint32_t b = p.tile_start[tile], e = p.tile_start[tile + 1];
   bool dead = !__any_sync(0xffffffffu, any_in);  // all 256 rays stopped
+  uint32_t live = dead ? 0u : 0xFu;  // halves (0x3, 0xC) with a ray that has not stopped
   uint32_t k = b;
 
   // one occluder (list index kk, window slot i) on the lane's rays
   auto occlude8 = [&](int i, uint32_t kk, uint32_t rb) {
     const float4 o1 = S.o1[i];
-    const uint32_t bits = kk >= rb ? S.rpass[kk - rb] : __float_as_uint(o1.w);
+    const uint32_t bits = (kk >= rb ? S.rpass[kk - rb] : __float_as_uint(o1.w)) & live;
     if (!bits) return;
     const float4 o0 = S.o0[i];
     const float dx = lx - o0.x;
@@ -176,11 +176,13 @@ __global__ void __launch_bounds__(kShadowThreads, 18) k_shadow(ShadowParams p) {
       }
     }
   };
+  // refreshes the live halves after an occluder run; false once every ray stopped
   auto still_alive = [&]() {
-    bool alive = false;
+    bool al[2] = {false, false};
 #pragma unroll
-    for (int i = 0; i < kPx; ++i) alive |= A[i] >= kShadowStop;
-    return __any_sync(0xffffffffu, alive);
+    for (int i = 0; i < kPx; ++i) al[i >> 2] |= A[i] >= kShadowStop;
+    live = (__any_sync(0xffffffffu, al[0]) ? 0x3u : 0u) | (__any_sync(0xffffffffu, al[1]) ? 0xCu : 0u);
+    return live != 0u;
   };
 
   // Sums of the receivers of group [j0, jl]: lane t < 16 adds num of receiver
