@@ -101,7 +101,7 @@ Workspace plan_workspace(int n, int width, int height, size_t cap) {
   L.gy = (height + kTile - 1) / kTile;
   L.ntiles = L.gx * L.gy;
   L.cap = cap;
-  L.nb_n = (int)((n + kSortTileItems - 1) / kSortTileItems);
+  L.nb_n = (int)((n + kDepthSortItems - 1) / kDepthSortItems);
   L.nb_cap = (int)((cap + kSortTileItems - 1) / kSortTileItems);
   if (L.nb_cap < 1) L.nb_cap = 1;
   const size_t N = (size_t)n;

@@ -123,6 +123,7 @@ __device__ __forceinline__ uint32_t load_n(const uint32_t* n_ptr, uint32_t n_fix
   return n_ptr ? *n_ptr : n_fixed;
 }
 
+template <int ROUNDS>
 __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint32_t* __restrict__ keys,
                                                              const uint32_t* n_ptr, uint32_t n_fixed,
                                                              int shift, uint32_t* hist, int nblocks) {
@@ -130,9 +131,9 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint32_t* __r
   const uint32_t n = load_n(n_ptr, n_fixed);
   cnt[threadIdx.x] = 0;
   __syncthreads();
-  const uint32_t base = blockIdx.x * kSortTileItems;
+  const uint32_t base = blockIdx.x * (uint32_t)(kSortThreads * ROUNDS);
   const int lane = threadIdx.x & 31;
-  for (int r = 0; r < kSortRounds; ++r) {
+  for (int r = 0; r < ROUNDS; ++r) {
     uint32_t i = base + r * kSortThreads + threadIdx.x;
     uint32_t d = i < n ? (keys[i] >> shift) & 255u : 256u;
     uint32_t peers = __match_any_sync(0xffffffffu, d);
@@ -146,22 +147,25 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint32_t* __r
 // warps in order, lanes in order), staged in shared memory sorted by digit,
 // then written out by consecutive threads, so each digit's run of the block
 // leaves as contiguous stores instead of one scattered store per item.
+template <int ROUNDS>
 struct ScatterSmem {
   uint32_t base[256];   // the block's first output slot per digit (scanned histogram)
   uint32_t run[256];    // the block's items per digit so far
   uint32_t start[256];  // first staging slot per digit
   uint32_t wc[2][kSortThreads / 32][256];
-  uint32_t key[kSortTileItems], val[kSortTileItems];
+  uint32_t key[kSortThreads * ROUNDS], val[kSortThreads * ROUNDS];
 };
 
+template <int ROUNDS>
 __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
     const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint32_t* __restrict__ kout,
     uint32_t* __restrict__ vout, const uint32_t* n_ptr, uint32_t n_fixed, int shift,
     const uint32_t* __restrict__ hist, int nblocks) {
+  constexpr int kItems = kSortThreads * ROUNDS;
   extern __shared__ uint4 scatter_raw[];
-  ScatterSmem& S = *reinterpret_cast<ScatterSmem*>(scatter_raw);
+  ScatterSmem<ROUNDS>& S = *reinterpret_cast<ScatterSmem<ROUNDS>*>(scatter_raw);
   const uint32_t n = load_n(n_ptr, n_fixed);
-  const uint32_t base = blockIdx.x * kSortTileItems;
+  const uint32_t base = blockIdx.x * (uint32_t)kItems;
   if (base >= n) return;
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
   const uint32_t lt = (1u << lane) - 1u;
@@ -170,9 +174,9 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
 #pragma unroll
   for (int w = 0; w < kSortThreads / 32; ++w) { S.wc[0][w][t] = 0; S.wc[1][w][t] = 0; }
   __syncthreads();
-  uint32_t kk[kSortRounds], vv[kSortRounds], rk[kSortRounds];
+  uint32_t kk[ROUNDS], vv[ROUNDS], rk[ROUNDS];
 #pragma unroll
-  for (int r = 0; r < kSortRounds; ++r) {
+  for (int r = 0; r < ROUNDS; ++r) {
     const int buf = r & 1;
     const uint32_t i = base + r * kSortThreads + t;
     const bool valid = i < n;
@@ -212,7 +216,7 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
   }
   __syncthreads();
 #pragma unroll
-  for (int r = 0; r < kSortRounds; ++r) {
+  for (int r = 0; r < ROUNDS; ++r) {
     if (base + r * kSortThreads + t < n) {
       const uint32_t lp = S.start[(kk[r] >> shift) & 255u] + rk[r];
       S.key[lp] = kk[r];
@@ -220,7 +224,7 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
     }
   }
   __syncthreads();
-  const uint32_t cnt = min((uint32_t)kSortTileItems, n - base);
+  const uint32_t cnt = min((uint32_t)kItems, n - base);
   for (uint32_t i = t; i < cnt; i += kSortThreads) {
     const uint32_t k = S.key[i];
     const uint32_t d = (k >> shift) & 255u;
@@ -307,23 +311,50 @@ __global__ void __launch_bounds__(256) k_ranges(const uint32_t* __restrict__ key
   }
 }
 
-void radix_sort(const uint32_t* kin, const uint32_t* vin, uint32_t* k0, uint32_t* v0, uint32_t* k1,
-                uint32_t* v1, const uint32_t* n_ptr, uint32_t n_fixed, int nblocks, int passes,
-                uint32_t* hist, uint32_t* scan_part, cudaStream_t s) {
+template <int ROUNDS>
+void radix_sort_t(const uint32_t* kin, const uint32_t* vin, uint32_t* k0, uint32_t* v0, uint32_t* k1,
+                  uint32_t* v1, const uint32_t* n_ptr, uint32_t n_fixed, int nblocks, int passes,
+                  uint32_t* hist, uint32_t* scan_part, cudaStream_t s) {
+  static bool configured = false;
+  if (!configured) {
+    cudaFuncSetAttribute(k_radix_scatter<ROUNDS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sizeof(ScatterSmem<ROUNDS>));
+    configured = true;
+  }
   const uint32_t* ki = kin;
   const uint32_t* vi = vin;
   for (int p = 0; p < passes; ++p) {
     uint32_t* ko = (p & 1) ? k1 : k0;
     uint32_t* vo = (p & 1) ? v1 : v0;
-    k_radix_hist<<<nblocks, kSortThreads, 0, s>>>(ki, n_ptr, n_fixed, 8 * p, hist, nblocks);
+    k_radix_hist<ROUNDS><<<nblocks, kSortThreads, 0, s>>>(ki, n_ptr, n_fixed, 8 * p, hist, nblocks);
     device_exclusive_scan(hist, hist, 256u * nblocks, nullptr, scan_part, s);
-    static bool configured = false;
-    if (!configured) {
-      cudaFuncSetAttribute(k_radix_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(ScatterSmem));
-      configured = true;
-    }
-    k_radix_scatter<<<nblocks, kSortThreads, sizeof(ScatterSmem), s>>>(ki, vi, ko, vo, n_ptr, n_fixed, 8 * p, hist,
-                                                                      nblocks);
+    k_radix_scatter<ROUNDS><<<nblocks, kSortThreads, sizeof(ScatterSmem<ROUNDS>), s>>>(
+        ki, vi, ko, vo, n_ptr, n_fixed, 8 * p, hist, nblocks);
+    count_launch(2);
+    ki = ko;
+    vi = vo;
+  }
+}
+
+// the pair sorts and gs3_depth_order_static: 4096 items per block, three-kernel scans
+void radix_sort(const uint32_t* kin, const uint32_t* vin, uint32_t* k0, uint32_t* v0, uint32_t* k1,
+                uint32_t* v1, const uint32_t* n_ptr, uint32_t n_fixed, int nblocks, int passes,
+                uint32_t* hist, uint32_t* scan_part, cudaStream_t s) {
+  static bool configured = false;
+  if (!configured) {
+    cudaFuncSetAttribute(k_radix_scatter<kSortRounds>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sizeof(ScatterSmem<kSortRounds>));
+    configured = true;
+  }
+  const uint32_t* ki = kin;
+  const uint32_t* vi = vin;
+  for (int p = 0; p < passes; ++p) {
+    uint32_t* ko = (p & 1) ? k1 : k0;
+    uint32_t* vo = (p & 1) ? v1 : v0;
+    k_radix_hist<kSortRounds><<<nblocks, kSortThreads, 0, s>>>(ki, n_ptr, n_fixed, 8 * p, hist, nblocks);
+    device_exclusive_scan(hist, hist, 256u * nblocks, nullptr, scan_part, s);
+    k_radix_scatter<kSortRounds><<<nblocks, kSortThreads, sizeof(ScatterSmem<kSortRounds>), s>>>(
+        ki, vi, ko, vo, n_ptr, n_fixed, 8 * p, hist, nblocks);
     count_launch(2);
     ki = ko;
     vi = vo;
@@ -357,9 +388,12 @@ void launch_depth_sort(const FrameArgs& f, int sp, cudaStream_t s) {
   const SplatBufs& b = f.L->sp[sp];
   unsigned char* ws = f.ws;
   const int n = f.sc.n;
-  radix_sort(at<uint32_t>(ws, b.key), nullptr, at<uint32_t>(ws, b.sk[0]), at<uint32_t>(ws, b.sv[0]),
-             at<uint32_t>(ws, b.sk[1]), at<uint32_t>(ws, b.sv[1]), nullptr, (uint32_t)n, f.L->nb_n, 4,
-             at<uint32_t>(ws, b.hist), at<uint32_t>(ws, b.scan_part), s);
+  // 1024 keys per block: four times the blocks of the pair sorts, for a
+  // sort of a few hundred thousand keys that would otherwise leave SMs idle
+  radix_sort_t<kDepthSortRounds>(at<uint32_t>(ws, b.key), nullptr, at<uint32_t>(ws, b.sk[0]),
+                                 at<uint32_t>(ws, b.sv[0]), at<uint32_t>(ws, b.sk[1]), at<uint32_t>(ws, b.sv[1]),
+                                 nullptr, (uint32_t)n, f.L->nb_n, 4, at<uint32_t>(ws, b.hist),
+                                 at<uint32_t>(ws, b.scan_part), s);
   // 4 passes end in buffer 1: sv[1] holds the index of each depth rank
   k_reorder<<<(n + 255) / 256, 256, 0, s>>>(
       n, at<uint32_t>(ws, b.sv[1]), at<SplatRec>(ws, b.rec), at<SplatRec>(ws, b.rrec),
