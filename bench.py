@@ -357,9 +357,8 @@ def main():
     import torch
     import torch.distributed as dist
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    from paper_2410_11419_gb300 import replicas
+    world, rank, local = replicas.rank_env()
     if world > 1:
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
@@ -371,6 +370,11 @@ def main():
 
     scene = synth.object_scene(0, n=a.n)
     pairs = [synth.camera_light_pair(i, a.res, a.res) for i in range(100)]
+
+    def view(step, offset=None):
+        """The camera/light pair this rank renders at a timed step (ranks interleave)."""
+        return replicas.view_index(step, rank, world, a.warmup if offset is None else offset)
+
     mlp_dtype = {"fp32": N.GS3_MLP_FP32, "bf16": N.GS3_MLP_BF16, "fp8": N.GS3_MLP_FP8_E4M3}[a.mlp]
     ds = R.DeviceScene(scene, device=dev, mlp_dtype=mlp_dtype)
     cap = 40_000_000 if a.n <= 300_000 else int(a.n * 140)
@@ -432,22 +436,20 @@ def main():
     clocks.start()
     time.sleep(0.3)
     launches0 = N.gs3_kernel_launches()
-    if world > 1:
-        dist.barrier()
+    replicas.barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for s in range(K):  # whole frames: gs3_render overlaps the light chain with the camera binning
         flush.zero_()
         fev[s][0].record(stream)
-        frame(a.warmup + s)
+        frame(view(s))
         fev[s][1].record(stream)
         ts_host[s, 0].copy_(rd.stage("tile_start", 0), non_blocking=True)
         ts_host[s, 1].copy_(rd.stage("tile_start", 1), non_blocking=True)
         nc_host[s].copy_(rd.stage("n_contrib").view(-1), non_blocking=True)
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
-    if world > 1:
-        dist.barrier()
+    replicas.barrier()
     launches = N.gs3_kernel_launches() - launches0
     clk = clocks.stop()
     rd.check()
@@ -458,16 +460,12 @@ def main():
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(len(groups) + 1)] for _ in range(KS)]
     for s in range(KS):
         flush.zero_()
-        frame(a.warmup + s, evs[s])
+        frame(view(s), evs[s])
     torch.cuda.synchronize()
     stage_ms = {nm: float(np.mean([evs[s][j].elapsed_time(evs[s][j + 1]) for s in range(KS)]))
                 for j, (nm, _) in enumerate(groups)}
-    total_ms = float(step_ms.sum())
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * K / (total_ms / 1e3)
+    total_ms = replicas.max_over_ranks(float(step_ms.sum()), dev)
+    value = replicas.whole_job_rate(K, total_ms / 1e3, world)
 
     # ---- end to end through the public API with host buffers ----
     host_img = torch.empty((a.res, a.res, 3), dtype=torch.float32, pin_memory=True)
@@ -475,15 +473,11 @@ def main():
     torch.cuda.synchronize()
     e0 = time.perf_counter()
     for s in range(K):
-        img = rd.render(*pairs[(a.warmup + s) % 100], opts)
+        img = rd.render(*pairs[view(s)], opts)
         host_img.copy_(img, non_blocking=True)
         torch.cuda.current_stream().synchronize()
-    e2e_s = time.perf_counter() - e0
-    e2e_val = world * K / e2e_s if world == 1 else None
-    if world > 1:
-        t = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_val = world * K / float(t.item())
+    e2e_s = replicas.max_over_ranks(time.perf_counter() - e0, dev)
+    e2e_val = replicas.whole_job_rate(K, e2e_s, world)
 
     # ---- served arm: continuous batching through the server (headline) ----
     served = None
@@ -495,23 +489,18 @@ def main():
             cam, light = pairs[i % 100]
             srv.wait(srv.submit(sid, cam, light, outs[i % len(outs)]))
         srv.reset_counters()
-        if world > 1:
-            dist.barrier()
+        replicas.barrier()
         torch.cuda.synchronize()
         w0 = time.perf_counter()
         tk = []
         for s_ in range(K):
-            cam, light = pairs[(a.warmup + s_) % 100]
+            cam, light = pairs[view(s_)]
             tk.append(srv.submit(sid, cam, light, outs[s_ % len(outs)]))
         bad = [srv.wait(t)[0] for t in tk]
         torch.cuda.synchronize()
         served_wall = time.perf_counter() - w0
         st = srv.stats()
-        span_ms = st.device_span_ms
-        if world > 1:
-            t = torch.tensor([span_ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            span_ms = float(t.item())
+        span_ms = replicas.max_over_ranks(st.device_span_ms, dev)
         rate = K / (span_ms / 1e3)
         # latency under load: open-loop Poisson arrivals at 80 % of the served rate
         rng = np.random.default_rng(1234)
