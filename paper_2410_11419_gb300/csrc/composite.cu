@@ -1,9 +1,10 @@
 // K6, K7: shadow splatting (Sec. 4.2, Fig. 3) and K9: camera compositing
 // (Sec. 3, Eq. 2) with the deferred per-pixel combination (Sec. 4).
 //
-// Both composites run one 256-thread block per 16x16 tile, one thread per
-// pixel, and stream the tile's depth-ordered list through shared memory in
-// batches of 256 records.
+// Both composites stream a 16x16 tile's depth-ordered list through shared
+// memory: the shadow composite with one warp per tile (eight rays per lane),
+// the camera composite with one 256-thread block per tile (one pixel per
+// thread, batches of 256 records).
 #include "gs3_internal.cuh"
 #include "splat_eval.cuh"
 

@@ -10,8 +10,8 @@
 namespace gs3 {
 namespace {
 
-// Bit w set when the splat's alpha >= alpha_min box can reach warp w's 8x8
-// block (tile-relative centre (ux, vy), half extents hx, hy).
+// Bit w set when the splat's alpha >= alpha_min box can reach quadrant w
+// (tile-relative centre (ux, vy), half extents hx, hy).
 __device__ __forceinline__ uint32_t warp_mask8(float ux, float vy, float hx, float hy) {
   if (!(hx >= 0.f)) return 0u;
   uint32_t m = 0u;
@@ -28,7 +28,7 @@ __device__ __forceinline__ uint32_t warp_mask8(float ux, float vy, float hx, flo
 //   power2 = a dx^2 + r dx dy + c dy^2 = dx (a dx) + dy (c dy + r dx),
 //   a = -A/2 log2e, r = -B log2e, c = -C/2 log2e, (dx, dy) = pixel - centre.
 // e0 = (ux, vy, a, c): centre relative to the tile origin (ox, oy);
-// e1 = (r, pthr log2e, gamma, warp mask bits).
+// e1 = (r, pthr log2e, gamma, quadrant bits of the alpha box).
 constexpr float kLog2e = 1.4426950408889634f;
 
 __device__ __forceinline__ float ex2(float x) {
