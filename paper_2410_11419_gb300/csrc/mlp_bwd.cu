@@ -285,36 +285,44 @@ __global__ void k_encode(RowArgs p) {
   for (int k = 0; k < kXdim / 4; ++k) dst[k] = make_float4(x[4 * k], x[4 * k + 1], x[4 * k + 2], x[4 * k + 3]);
 }
 
-// Output layer, one warp per Gaussian: y = sigmoid(W_o h_L + b_o),
+// Output layer, one warp per Gaussian (kOutRowsPerWarp Gaussians per warp in
+// turn, the weights staged once per block): y = sigmoid(W_o h_L + b_o),
 // dz_o = dL/dy y (1 - y), dz_L = (dz_o W_o) * act'(h_L).  Lane l owns the
 // columns l, l + 32, l + 64, l + 96 that exist (widths 16..128).
-__global__ void k_out_layer(RowArgs p) {
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-  if (warp >= p.n) return;
-  const int g = warp, W = p.width, nq = (W + 31) / 32;
-  const float* h = p.Hlast + (size_t)g * W;
-  float hv[4] = {0.f, 0.f, 0.f, 0.f};
-  for (int q = 0; q < nq; ++q)
-    if (lane + 32 * q < W) hv[q] = h[lane + 32 * q];
-  float dzo[4] = {0.f, 0.f, 0.f, 0.f};
-  for (int o = 0; o < p.out_dim; ++o) {
-    float s = 0.f;
-    for (int q = 0; q < nq; ++q)
-      if (lane + 32 * q < W) s = fmaf(hv[q], p.w_out[o * W + lane + 32 * q], s);
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-    const float y = 1.f / (1.f + expf(-(s + p.b_out[o])));
-    const float dy = p.which == 0 ? p.color[(size_t)kColorStride * g + 3] : p.color[(size_t)kColorStride * g + 4 + o];
-    dzo[o] = dy * y * (1.f - y);
-  }
-  if (lane < 4) p.dzo[(size_t)4 * g + lane] = lane < p.out_dim ? dzo[lane] : 0.f;
+constexpr int kOutRowsPerWarp = 8;
+__global__ void __launch_bounds__(256) k_out_layer(RowArgs p) {
+  __shared__ float wo[4 * 128];  // the output layer's weights (out_dim <= 3, width <= 128)
+  __shared__ float bo[4];
+  const int W = p.width, nq = (W + 31) / 32, lane = threadIdx.x & 31;
+  for (int i = threadIdx.x; i < p.out_dim * W; i += blockDim.x) wo[i] = p.w_out[i];
+  if (threadIdx.x < p.out_dim) bo[threadIdx.x] = p.b_out[threadIdx.x];
+  __syncthreads();
   const bool leaky = p.act == GS3_ACT_LEAKY_RELU;
-  for (int q = 0; q < nq; ++q) {
-    const int j = lane + 32 * q;
-    if (j >= W) break;
-    float s = 0.f;
-    for (int o = 0; o < p.out_dim; ++o) s = fmaf(dzo[o], p.w_out[o * W + j], s);
-    p.dZlast[(size_t)g * W + j] = hv[q] > 0.f ? s : (leaky ? 0.01f * s : 0.f);
+  const int warp0 = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * kOutRowsPerWarp;
+  for (int g = warp0; g < min(p.n, warp0 + kOutRowsPerWarp); ++g) {
+    const float* h = p.Hlast + (size_t)g * W;
+    float hv[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int q = 0; q < nq; ++q)
+      if (lane + 32 * q < W) hv[q] = h[lane + 32 * q];
+    float dzo[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int o = 0; o < p.out_dim; ++o) {
+      float s = 0.f;
+      for (int q = 0; q < nq; ++q)
+        if (lane + 32 * q < W) s = fmaf(hv[q], wo[o * W + lane + 32 * q], s);
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+      const float y = 1.f / (1.f + expf(-(s + bo[o])));
+      const float dy = p.which == 0 ? p.color[(size_t)kColorStride * g + 3] : p.color[(size_t)kColorStride * g + 4 + o];
+      dzo[o] = dy * y * (1.f - y);
+    }
+    if (lane < 4) p.dzo[(size_t)4 * g + lane] = lane < p.out_dim ? dzo[lane] : 0.f;
+    for (int q = 0; q < nq; ++q) {
+      const int j = lane + 32 * q;
+      if (j >= W) break;
+      float s = 0.f;
+      for (int o = 0; o < p.out_dim; ++o) s = fmaf(dzo[o], wo[o * W + j], s);
+      p.dZlast[(size_t)g * W + j] = hv[q] > 0.f ? s : (leaky ? 0.01f * s : 0.f);
+    }
   }
 }
 
@@ -431,7 +439,8 @@ void run_mlp_backward(const MlpArgs& a, void* scratch, float* wred, cudaStream_t
   r.Hlast = S.H + (size_t)(nh - 1) * n * W;
   r.dzo = S.dzo;
   r.dZlast = S.dz[0];
-  k_out_layer<<<(n * 32 + 255) / 256, 256, 0, s>>>(r);
+  const int out_warps = (n + kOutRowsPerWarp - 1) / kOutRowsPerWarp;
+  k_out_layer<<<(out_warps * 32 + 255) / 256, 256, 0, s>>>(r);
   count_launch();
   const int nb = wgemm_blocks(n);
   const int rpb = ((n + nb - 1) / nb + kKc - 1) / kKc * kKc;
