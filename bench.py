@@ -34,7 +34,7 @@ sys.path.insert(0, ROOT)
 # one ncu capture of the kernel, valid only while its sources are unchanged:
 # kernel -> (bytes, SHA-256 of the concatenated sources, the summary file).
 PROFILED_TRAFFIC = {
-    "k_shadow": (276.1e6, "faeaa7e3bb9a57fe090a273a483b778ff2d053520d1287ff2cc191a985a8e2bb",
+    "k_shadow": (276.1e6, "a58956ce99523339ac1370313dc475c32523cdbe67d4626593e73b2d23e6ca55",
                  "profiles/k_shadow_object_300k_800.md"),
 }
 TRAFFIC_SOURCES = {

@@ -351,33 +351,37 @@ __global__ void __launch_bounds__(256) k_occluder_bound(const uint32_t* __restri
   }
 }
 
-// K7: per Gaussian, sum its (tile) partials in tile order; T = num / den, or 1
-// when the Gaussian meets no shadow ray.  One warp per Gaussian rank.
+// K7: per Gaussian, sum its (tile) partials; T = num / den, or 1 when the
+// Gaussian meets no shadow ray.  Eight lanes per Gaussian rank (four per
+// warp): lane s adds partials s, s + 8, ... in order, then three shuffle
+// levels combine the eight sums in a fixed order.
 __global__ void __launch_bounds__(256) k_shadow_reduce(int n, const uint32_t* __restrict__ off,
                                                        const uint32_t* __restrict__ cnt,
                                                        const float2* __restrict__ partial,
                                                        const uint32_t* __restrict__ order,
                                                        const uint32_t* header, float* __restrict__ T,
                                                        float* __restrict__ den_out) {
-  const int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (r >= n) return;
+  const int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 3;
+  const int sub = threadIdx.x & 7;
+  const bool valid = r < n;
   const uint32_t P = header[H_PAIRS_LIGHT];
-  const uint32_t o = off[r], c = cnt[r];
   float num = 0.f, den = 0.f;
-  if (o + c <= P) {
-    for (uint32_t i = lane; i < c; i += 32) {
-      const float2 v = partial[o + i];
-      num += v.x;
-      den += v.y;
+  if (valid) {
+    const uint32_t o = off[r], c = cnt[r];
+    if (o + c <= P) {
+      for (uint32_t i = sub; i < c; i += 8) {
+        const float2 v = partial[o + i];
+        num += v.x;
+        den += v.y;
+      }
     }
   }
 #pragma unroll
-  for (int s = 16; s > 0; s >>= 1) {
-    num += __shfl_xor_sync(0xffffffffu, num, s);
-    den += __shfl_xor_sync(0xffffffffu, den, s);
+  for (int sh = 4; sh > 0; sh >>= 1) {
+    num += __shfl_xor_sync(0xffffffffu, num, sh);
+    den += __shfl_xor_sync(0xffffffffu, den, sh);
   }
-  if (lane == 0) {
+  if (valid && sub == 0) {
     T[order[r]] = den > 0.f ? num / den : 1.f;
     den_out[order[r]] = den;
   }
@@ -567,7 +571,7 @@ void launch_shadow_reduce(const FrameArgs& f, cudaStream_t s) {
   const SplatBufs& b = f.L->sp[1];
   unsigned char* ws = f.ws;
   const int n = f.sc.n;
-  k_shadow_reduce<<<(n * 32 + 255) / 256, 256, 0, s>>>(
+  k_shadow_reduce<<<(n * 8 + 255) / 256, 256, 0, s>>>(
       n, at<uint32_t>(ws, b.off), at<uint32_t>(ws, b.cnt), at<float2>(ws, f.L->partial),
       at<uint32_t>(ws, b.sv[1]), at<uint32_t>(ws, f.L->header), at<float>(ws, f.L->T),
       at<float>(ws, f.L->shadow_den));
