@@ -257,12 +257,12 @@ __global__ void __launch_bounds__(256) k_reorder(int n, const uint32_t* __restri
   }
 }
 
+// One warp per depth rank: the lanes write the rank's (tile, rank) pairs, its
+// rectangle's tiles in row-major order, at off[r] + i.
 __global__ void __launch_bounds__(256) k_emit(int n, uint32_t cap, const SplatRec* __restrict__ rrec,
                                               const uint32_t* __restrict__ off, uint32_t* header, int h_need,
                                               int h_pairs, uint32_t* __restrict__ tk, uint32_t* __restrict__ tv,
                                               int gx) {
-  __shared__ uint32_t s_off[257];
-  __shared__ int s_x0[256], s_y0[256], s_w[256];
   const uint32_t need = header[h_need];
   if (need > cap) {
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -272,31 +272,17 @@ __global__ void __launch_bounds__(256) k_emit(int n, uint32_t cap, const SplatRe
     return;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) header[h_pairs] = need;
-  const int t = threadIdx.x;
-  const int r0 = blockIdx.x * 256;
-  const int r = r0 + t;
-  s_off[t] = r < n ? off[r] : need;
-  if (t == 0) s_off[256] = (r0 + 256 < n) ? off[r0 + 256] : need;
-  if (r < n) {
-    int4 q = rrec[r].r;
-    s_x0[t] = q.x; s_y0[t] = q.y; s_w[t] = q.z - q.x + 1;
-  } else {
-    s_x0[t] = 0; s_y0[t] = 0; s_w[t] = 1;
-  }
-  __syncthreads();
-  const uint32_t end = s_off[256];
-  for (uint32_t e = s_off[0] + t; e < end; e += 256) {
-    int lo = 0, hi = 255;
-    while (lo < hi) {
-      int mid = (lo + hi + 1) >> 1;
-      if (s_off[mid] <= e) lo = mid; else hi = mid - 1;
-    }
-    const uint32_t local = e - s_off[lo];
-    const int w = s_w[lo];
-    const int ty = s_y0[lo] + (int)(local / (uint32_t)w);
-    const int tx = s_x0[lo] + (int)(local % (uint32_t)w);
-    tk[e] = (uint32_t)(ty * gx + tx);
-    tv[e] = (uint32_t)(r0 + lo);
+  const int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (r >= n) return;
+  const int4 q = rrec[r].r;
+  if (q.x < 0) return;  // culled: no pairs
+  const uint32_t w = (uint32_t)(q.z - q.x + 1);
+  const uint32_t cnt = w * (uint32_t)(q.w - q.y + 1);
+  const uint32_t base = off[r];
+  for (uint32_t i = lane; i < cnt; i += 32) {
+    const int ty = q.y + (int)(i / w), tx = q.x + (int)(i % w);
+    tk[base + i] = (uint32_t)(ty * gx + tx);
+    tv[base + i] = (uint32_t)r;
   }
 }
 
@@ -411,7 +397,7 @@ void launch_binning(const FrameArgs& f, int sp, cudaStream_t s) {
   const int h_pairs = sp ? H_PAIRS_LIGHT : H_PAIRS_CAM;
   device_exclusive_scan(at<uint32_t>(ws, b.cnt), at<uint32_t>(ws, b.off), (uint32_t)n, header + h_need,
                         at<uint32_t>(ws, b.scan_part), s);
-  k_emit<<<(n + 255) / 256, 256, 0, s>>>(n, (uint32_t)f.L->cap, at<SplatRec>(ws, b.rrec),
+  k_emit<<<(int)(((size_t)n * 32 + 255) / 256), 256, 0, s>>>(n, (uint32_t)f.L->cap, at<SplatRec>(ws, b.rrec),
                                          at<uint32_t>(ws, b.off), header, h_need, h_pairs,
                                          at<uint32_t>(ws, b.tk[0]), at<uint32_t>(ws, b.tv[0]), f.L->gx);
   count_launch();
