@@ -34,7 +34,7 @@ sys.path.insert(0, ROOT)
 # one ncu capture of the kernel, valid only while its sources are unchanged:
 # kernel -> (bytes, SHA-256 of the concatenated sources, the summary file).
 PROFILED_TRAFFIC = {
-    "k_shadow": (276.1e6, "a58956ce99523339ac1370313dc475c32523cdbe67d4626593e73b2d23e6ca55",
+    "k_shadow": (276.1e6, "3a8b5ab89d3b83b7d81cb073c1f5a007e7985d6d99ea92de8d8835c8493ad0c3",
                  "profiles/k_shadow_object_300k_800.md"),
 }
 TRAFFIC_SOURCES = {

@@ -324,17 +324,20 @@ __global__ void __launch_bounds__(kShadowThreads, 18) k_shadow(ShadowParams p) {
   }
 }
 
-// K(i) for every entry i of the light lists: the first index of i's tile
-// segment whose distance is >= d_i - bias (the end of i's occluder prefix).
+// The distance of every list entry, from the depth sort's keys: the key of
+// depth rank r is the FP32 bit pattern of rank r's light distance (the
+// record's a.w), so this reads 4 bytes per entry instead of a record.
 __global__ void __launch_bounds__(256) k_gather_depth(const uint32_t* __restrict__ list,
-                                                      const SplatRec* __restrict__ rrec,
+                                                      const uint32_t* __restrict__ rank_key,
                                                       const uint32_t* header, float* __restrict__ dl,
                                                       uint32_t limit) {
   const uint32_t P = min(header[H_PAIRS_LIGHT], limit);
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < P; i += gridDim.x * blockDim.x)
-    dl[i] = rrec[list[i]].a.w;
+    dl[i] = __uint_as_float(rank_key[list[i]]);
 }
 
+// K(i) for every entry i of the light lists: the first index of i's tile
+// segment whose distance is >= d_i - bias (the end of i's occluder prefix).
 __global__ void __launch_bounds__(256) k_occluder_bound(const uint32_t* __restrict__ keys,
                                                         const uint32_t* __restrict__ tile_start,
                                                         const float* __restrict__ dl, const uint32_t* header,
@@ -539,7 +542,8 @@ void launch_shadow_composite(const FrameArgs& f, cudaStream_t s) {
   const uint32_t* header = at<uint32_t>(ws, f.L->header);
   int blocks = (int)((f.L->cap + 255) / 256);
   if (blocks > 152 * 16) blocks = 152 * 16;
-  k_gather_depth<<<blocks, 256, 0, s>>>(at<uint32_t>(ws, b.tv[fin]), at<SplatRec>(ws, b.rrec), header, dl,
+  // the depth sort's four passes leave the keys in rank order in sk[1]
+  k_gather_depth<<<blocks, 256, 0, s>>>(at<uint32_t>(ws, b.tv[fin]), at<uint32_t>(ws, b.sk[1]), header, dl,
                                         (uint32_t)f.L->cap);
   k_occluder_bound<<<blocks, 256, 0, s>>>(at<uint32_t>(ws, b.tk[fin]), at<uint32_t>(ws, b.tile_start), dl, header,
                                           f.opts.shadow_bias, kb, (uint32_t)f.L->cap);
