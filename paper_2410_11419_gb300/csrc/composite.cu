@@ -480,43 +480,46 @@ __global__ void __launch_bounds__(256) k_camera(CamParams p) {
 
 // Launch order of a splat's tiles: longest list first, so that the last
 // blocks to start are the short ones and the final partial wave stays short
-// (a longest-processing-time-first schedule; the tiles' results do not depend
-// on the order).  One block sorts packed 32-bit keys (inverted list length
-// capped to 19 bits | 13-bit tile index, so ties keep tile order) with a
-// bitonic network in shared memory.
+// (a longest-processing-time-first schedule).  One block: a counting sort on
+// the list length in steps of 8 (1024 buckets; longer lists share the first),
+// placed by shared-memory atomics.  The order within a bucket may vary from
+// run to run; no result depends on it, since every tile writes only its own
+// outputs.
 __global__ void __launch_bounds__(1024) k_tile_order(const uint32_t* __restrict__ tile_start, int ntiles,
                                                      uint32_t* __restrict__ order) {
-  __shared__ uint32_t key[kOrderTiles];
-  constexpr uint32_t kLenMax = (1u << 19) - 1u;
-  int np = 1;
-  while (np < ntiles) np <<= 1;
-  for (int i = threadIdx.x; i < np; i += blockDim.x) {
-    if (i < ntiles) {
-      const uint32_t len = min(tile_start[i + 1] - tile_start[i], kLenMax);
-      key[i] = ((kLenMax - len) << 13) | (uint32_t)i;
-    } else {
-      key[i] = 0xFFFFFFFFu;  // padding sorts last
+  constexpr int kBuckets = 1024;
+  __shared__ uint32_t cnt[kBuckets];
+  __shared__ uint32_t wsum[32];
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  auto bucket = [&](int i) {
+    const uint32_t len = tile_start[i + 1] - tile_start[i];
+    return (uint32_t)(kBuckets - 1) - min(len >> 3, (uint32_t)(kBuckets - 1));  // longest first
+  };
+  cnt[t] = 0u;
+  __syncthreads();
+  for (int i = t; i < ntiles; i += blockDim.x) atomicAdd(&cnt[bucket(i)], 1u);
+  __syncthreads();
+  // exclusive scan of the 1024 bucket counts (thread t owns bucket t)
+  const uint32_t c = cnt[t];
+  uint32_t x = c;
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) wsum[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t w = wsum[lane];
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
     }
+    wsum[lane] = w;
   }
   __syncthreads();
-  for (int k = 2; k <= np; k <<= 1)
-    for (int j = k >> 1; j > 0; j >>= 1) {
-      for (int i = threadIdx.x; i < np; i += blockDim.x) {
-        const int l = i ^ j;
-        if (l > i) {
-          const uint32_t a = key[i], b = key[l];
-          const bool up = (i & k) == 0;
-          if ((a > b) == up) { key[i] = b; key[l] = a; }
-        }
-      }
-      __syncthreads();
-    }
-  for (int i = threadIdx.x; i < ntiles; i += blockDim.x) order[i] = key[i] & 0x1FFFu;
-}
-
-__global__ void k_identity_order(uint32_t* order, int ntiles) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < ntiles) order[i] = (uint32_t)i;
+  cnt[t] = (warp ? wsum[warp - 1] : 0u) + x - c;
+  __syncthreads();
+  for (int i = t; i < ntiles; i += blockDim.x) order[atomicAdd(&cnt[bucket(i)], 1u)] = (uint32_t)i;
 }
 
 }  // namespace
@@ -524,11 +527,7 @@ __global__ void k_identity_order(uint32_t* order, int ntiles) {
 void launch_tile_order(const FrameArgs& f, int splat, cudaStream_t s) {
   const Workspace& L = *f.L;
   uint32_t* order = at<uint32_t>(f.ws, L.tile_order[splat]);
-  if (L.ntiles <= kOrderTiles) {
-    k_tile_order<<<1, 1024, 0, s>>>(at<uint32_t>(f.ws, L.sp[splat].tile_start), L.ntiles, order);
-  } else {
-    k_identity_order<<<(L.ntiles + 255) / 256, 256, 0, s>>>(order, L.ntiles);
-  }
+  k_tile_order<<<1, 1024, 0, s>>>(at<uint32_t>(f.ws, L.sp[splat].tile_start), L.ntiles, order);
   count_launch();
 }
 

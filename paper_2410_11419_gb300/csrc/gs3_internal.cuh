@@ -161,8 +161,7 @@ void launch_prep(const FrameArgs& f, cudaStream_t s);
 void launch_depth_sort(const FrameArgs& f, int splat, cudaStream_t s);
 void launch_binning(const FrameArgs& f, int splat, cudaStream_t s);
 void launch_shadow_composite(const FrameArgs& f, cudaStream_t s);
-// a splat's tiles ordered longest list first, into L.tile_order[splat] (identity past kOrderTiles tiles)
-constexpr int kOrderTiles = 8192;
+// a splat's tiles ordered longest list first (in length steps of 8), into L.tile_order[splat]
 void launch_tile_order(const FrameArgs& f, int splat, cudaStream_t s);
 void launch_shadow_reduce(const FrameArgs& f, cudaStream_t s);
 void launch_mlp(const FrameArgs& f, cudaStream_t s, bool identity_only = false);
