@@ -123,45 +123,62 @@ __device__ __forceinline__ uint32_t load_n(const uint32_t* n_ptr, uint32_t n_fix
   return n_ptr ? *n_ptr : n_fixed;
 }
 
+// Per block of kSortThreads * ROUNDS consecutive items: the count of each
+// digit.  Warp w counts its own 32 * ROUNDS consecutive items (all keys loaded
+// first) into its own row of counters; the rows are added at the end.
 template <int ROUNDS>
 __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint32_t* __restrict__ keys,
                                                              const uint32_t* n_ptr, uint32_t n_fixed,
                                                              int shift, uint32_t* hist, int nblocks) {
-  __shared__ uint32_t cnt[256];
+  __shared__ uint32_t cnt[kSortThreads / 32][256];
   const uint32_t n = load_n(n_ptr, n_fixed);
-  cnt[threadIdx.x] = 0;
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+#pragma unroll
+  for (int w = 0; w < kSortThreads / 32; ++w) cnt[w][t] = 0;
   __syncthreads();
-  const uint32_t base = blockIdx.x * (uint32_t)(kSortThreads * ROUNDS);
-  const int lane = threadIdx.x & 31;
+  const uint32_t wbase = blockIdx.x * (uint32_t)(kSortThreads * ROUNDS) + (uint32_t)warp * (32u * ROUNDS);
+  uint32_t d[ROUNDS];
+#pragma unroll
   for (int r = 0; r < ROUNDS; ++r) {
-    uint32_t i = base + r * kSortThreads + threadIdx.x;
-    uint32_t d = i < n ? (keys[i] >> shift) & 255u : 256u;
-    uint32_t peers = __match_any_sync(0xffffffffu, d);
-    if (d < 256u && lane == __ffs(peers) - 1) atomicAdd(&cnt[d], __popc(peers));
+    const uint32_t i = wbase + r * 32 + lane;
+    d[r] = i < n ? (keys[i] >> shift) & 255u : 256u;
+  }
+#pragma unroll
+  for (int r = 0; r < ROUNDS; ++r) {
+    const uint32_t peers = __match_any_sync(0xffffffffu, d[r]);
+    if (d[r] < 256u && lane == __ffs(peers) - 1) cnt[warp][d[r]] += __popc(peers);
+    __syncwarp();
   }
   __syncthreads();
-  hist[threadIdx.x * nblocks + blockIdx.x] = cnt[threadIdx.x];
+  uint32_t c = 0;
+#pragma unroll
+  for (int w = 0; w < kSortThreads / 32; ++w) c += cnt[w][t];
+  hist[t * nblocks + blockIdx.x] = c;
 }
 
-// The block's items are ranked within their digit (stable: rounds in order,
-// warps in order, lanes in order), staged in shared memory sorted by digit,
-// then written out by consecutive threads, so each digit's run of the block
-// leaves as contiguous stores instead of one scattered store per item.
+// The block's items are ranked within their digit and staged in shared
+// memory sorted by digit, then written out by consecutive threads, so each
+// digit's run of the block leaves as contiguous stores instead of one
+// scattered store per item.  Warp w ranks its own 32 * ROUNDS consecutive
+// items against its own digit counters (no block barrier per round); a
+// block scan over (digit, warp) then places the warps' runs, so the order
+// within a digit is the items' order (stable).
 template <int ROUNDS>
 struct ScatterSmem {
-  uint32_t base[256];   // the block's first output slot per digit (scanned histogram)
-  uint32_t run[256];    // the block's items per digit so far
-  uint32_t start[256];  // first staging slot per digit
-  uint32_t wc[2][kSortThreads / 32][256];
+  uint32_t base[256];    // the block's first output slot per digit (scanned histogram)
+  uint32_t start[256];   // first staging slot per digit
+  uint32_t cnt[kSortThreads / 32][256];  // per warp and digit: items so far, then the warp's first slot
+  uint32_t wsum[kSortThreads / 32];
   uint32_t key[kSortThreads * ROUNDS], val[kSortThreads * ROUNDS];
 };
 
 template <int ROUNDS>
-__global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
+__global__ void __launch_bounds__(kSortThreads, 3) k_radix_scatter(
     const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint32_t* __restrict__ kout,
     uint32_t* __restrict__ vout, const uint32_t* n_ptr, uint32_t n_fixed, int shift,
     const uint32_t* __restrict__ hist, int nblocks) {
   constexpr int kItems = kSortThreads * ROUNDS;
+  constexpr int kWarps = kSortThreads / 32;
   extern __shared__ uint4 scatter_raw[];
   ScatterSmem<ROUNDS>& S = *reinterpret_cast<ScatterSmem<ROUNDS>*>(scatter_raw);
   const uint32_t n = load_n(n_ptr, n_fixed);
@@ -170,55 +187,63 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
   const uint32_t lt = (1u << lane) - 1u;
   S.base[t] = hist[t * nblocks + blockIdx.x];
-  S.run[t] = 0;
 #pragma unroll
-  for (int w = 0; w < kSortThreads / 32; ++w) { S.wc[0][w][t] = 0; S.wc[1][w][t] = 0; }
-  __syncthreads();
-  uint32_t kk[ROUNDS], vv[ROUNDS], rk[ROUNDS];
+  for (int w = 0; w < kWarps; ++w) S.cnt[w][t] = 0;
+  const uint32_t wbase = base + (uint32_t)warp * (32u * ROUNDS);
+  uint32_t kk[ROUNDS], vv[ROUNDS];
+  uint32_t rk[(ROUNDS + 1) / 2];  // two 16-bit ranks per word (a warp ranks at most 32 * ROUNDS items)
 #pragma unroll
   for (int r = 0; r < ROUNDS; ++r) {
-    const int buf = r & 1;
-    const uint32_t i = base + r * kSortThreads + t;
+    const uint32_t i = wbase + r * 32 + lane;
     const bool valid = i < n;
     kk[r] = valid ? kin[i] : 0u;
     vv[r] = valid ? (vin ? vin[i] : i) : 0u;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < ROUNDS; ++r) {
+    const bool valid = wbase + r * 32 + lane < n;
     const uint32_t d = valid ? (kk[r] >> shift) & 255u : 256u;
     const uint32_t peers = __match_any_sync(0xffffffffu, d);
-    const uint32_t lrank = __popc(peers & lt);
-    if (valid && lrank == 0) S.wc[buf][warp][d] = __popc(peers);
-    __syncthreads();
-    uint32_t acc = S.run[t];
-#pragma unroll
-    for (int w = 0; w < kSortThreads / 32; ++w) {
-      uint32_t c = S.wc[buf][w][t];
-      S.wc[buf][w][t] = acc;
-      acc += c;
-      S.wc[buf ^ 1][w][t] = 0;
-    }
-    S.run[t] = acc;
-    __syncthreads();
-    rk[r] = valid ? S.wc[buf][warp][d] + lrank : 0u;  // rank within the digit in the block
+    const int leader = __ffs(peers) - 1;
+    uint32_t c = 0;
+    if (valid && lane == leader) c = S.cnt[warp][d];
+    c = __shfl_sync(0xffffffffu, c, leader);
+    const uint32_t rank = c + __popc(peers & lt);  // rank within the digit among the warp's items
+    rk[r >> 1] = (r & 1) ? (rk[r >> 1] | (rank << 16)) : rank;
+    if (valid && lane == leader) S.cnt[warp][d] = c + __popc(peers);
+    __syncwarp();
   }
-  // first staging slot per digit: exclusive scan of the block's digit counts
+  __syncthreads();
+  // thread t = digit t: the warps' first slots within the digit, the digit's
+  // total, then an exclusive scan of the totals over the digits
   {
-    const uint32_t c = S.run[t];
-    uint32_t x = c;
+    uint32_t tot = 0;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) {
+      const uint32_t c = S.cnt[w][t];
+      S.cnt[w][t] = tot;
+      tot += c;
+    }
+    uint32_t x = tot;
     for (int o = 1; o < 32; o <<= 1) {
       const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
       if (lane >= o) x += y;
     }
-    __syncthreads();  // every read of wc is done: reuse wc[0][0] for the warp sums
-    if (lane == 31) S.wc[0][0][warp] = x;
+    if (lane == 31) S.wsum[warp] = x;
     __syncthreads();
     uint32_t before = 0;
-    for (int w = 0; w < warp; ++w) before += S.wc[0][0][w];
-    S.start[t] = before + x - c;
+    for (int w = 0; w < warp; ++w) before += S.wsum[w];
+    const uint32_t st = before + x - tot;
+    S.start[t] = st;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) S.cnt[w][t] += st;
   }
   __syncthreads();
 #pragma unroll
   for (int r = 0; r < ROUNDS; ++r) {
-    if (base + r * kSortThreads + t < n) {
-      const uint32_t lp = S.start[(kk[r] >> shift) & 255u] + rk[r];
+    if (wbase + r * 32 + lane < n) {
+      const uint32_t lp = S.cnt[warp][(kk[r] >> shift) & 255u] + ((rk[r >> 1] >> (16 * (r & 1))) & 0xFFFFu);
       S.key[lp] = kk[r];
       S.val[lp] = vv[r];
     }
@@ -322,10 +347,12 @@ void radix_sort_t(const uint32_t* kin, const uint32_t* vin, uint32_t* k0, uint32
   }
 }
 
-// the pair sorts and gs3_depth_order_static: 4096 items per block, three-kernel scans
+// the pair sorts and gs3_depth_order_static: 4096 items per block, three-kernel scans.
+// The last pass's digits are below last_digits, so only those rows of its
+// histogram are scanned (the other rows are zero and no item reads them).
 void radix_sort(const uint32_t* kin, const uint32_t* vin, uint32_t* k0, uint32_t* v0, uint32_t* k1,
                 uint32_t* v1, const uint32_t* n_ptr, uint32_t n_fixed, int nblocks, int passes,
-                uint32_t* hist, uint32_t* scan_part, cudaStream_t s) {
+                uint32_t last_digits, uint32_t* hist, uint32_t* scan_part, cudaStream_t s) {
   static bool configured = false;
   if (!configured) {
     cudaFuncSetAttribute(k_radix_scatter<kSortRounds>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -338,7 +365,8 @@ void radix_sort(const uint32_t* kin, const uint32_t* vin, uint32_t* k0, uint32_t
     uint32_t* ko = (p & 1) ? k1 : k0;
     uint32_t* vo = (p & 1) ? v1 : v0;
     k_radix_hist<kSortRounds><<<nblocks, kSortThreads, 0, s>>>(ki, n_ptr, n_fixed, 8 * p, hist, nblocks);
-    device_exclusive_scan(hist, hist, 256u * nblocks, nullptr, scan_part, s);
+    const uint32_t rows = p == passes - 1 ? last_digits : 256u;
+    device_exclusive_scan(hist, hist, rows * nblocks, nullptr, scan_part, s);
     k_radix_scatter<kSortRounds><<<nblocks, kSortThreads, sizeof(ScatterSmem<kSortRounds>), s>>>(
         ki, vi, ko, vo, n_ptr, n_fixed, 8 * p, hist, nblocks);
     count_launch(2);
@@ -355,7 +383,7 @@ void radix_sort_pairs(const uint32_t* kin, const uint32_t* vin, uint32_t* k0, ui
                       uint32_t* v1, uint32_t n, int passes, uint32_t* hist, uint32_t* scan_part,
                       cudaStream_t s) {
   const int nblocks = (int)((n + kSortTileItems - 1) / kSortTileItems);
-  radix_sort(kin, vin, k0, v0, k1, v1, nullptr, n, nblocks, passes, hist, scan_part, s);
+  radix_sort(kin, vin, k0, v0, k1, v1, nullptr, n, nblocks, passes, 256u, hist, scan_part, s);
 }
 
 void device_exclusive_scan(const uint32_t* in, uint32_t* out, uint32_t n, uint32_t* total,
@@ -405,7 +433,8 @@ void launch_binning(const FrameArgs& f, int sp, cudaStream_t s) {
   // sort (tile, rank) pairs on the tile bits; start from buffer 0, alternate
   radix_sort(at<uint32_t>(ws, b.tk[0]), at<uint32_t>(ws, b.tv[0]), at<uint32_t>(ws, b.tk[1]),
              at<uint32_t>(ws, b.tv[1]), at<uint32_t>(ws, b.tk[0]), at<uint32_t>(ws, b.tv[0]),
-             header + h_pairs, 0, f.L->nb_cap, passes, at<uint32_t>(ws, b.hist),
+             header + h_pairs, 0, f.L->nb_cap, passes, ((uint32_t)(f.L->ntiles - 1) >> (8 * (passes - 1))) + 1u,
+             at<uint32_t>(ws, b.hist),
              at<uint32_t>(ws, b.scan_part), s);
   const int fin = passes & 1;  // 1 pass ends in buffer 1, 2 passes in buffer 0
   const uint32_t* keys = at<uint32_t>(ws, b.tk[fin]);
