@@ -76,6 +76,8 @@ def parse():
     ap.add_argument("--no-plain", action="store_true", help="skip the FP32 plain comparison arm")
     ap.add_argument("--profile-frames", type=int, default=0,
                     help="render this many frames of the workload (no timing) and exit; for ncu")
+    ap.add_argument("--profile-capacity", type=int, default=0,
+                    help="with --profile-frames: the pair capacity (default 40M, or 140 per Gaussian past 300k)")
     ap.add_argument("--profile-backward", action="store_true",
                     help="with --profile-frames and --mlp fp32: also run each frame's backward")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -378,6 +380,8 @@ def main():
     mlp_dtype = {"fp32": N.GS3_MLP_FP32, "bf16": N.GS3_MLP_BF16, "fp8": N.GS3_MLP_FP8_E4M3}[a.mlp]
     ds = R.DeviceScene(scene, device=dev, mlp_dtype=mlp_dtype)
     cap = 40_000_000 if a.n <= 300_000 else int(a.n * 140)
+    if a.profile_frames and a.profile_capacity:
+        cap = a.profile_capacity
     rd = R.Renderer(ds, a.res, a.res, cap, device=dev)
     if not a.profile_frames:
         # size the pair capacity as a deployment would (untimed): the most pairs

@@ -105,8 +105,8 @@ Workspace plan_workspace(int n, int width, int height, size_t cap) {
   L.nb_cap = (int)((cap + kSortTileItems - 1) / kSortTileItems);
   if (L.nb_cap < 1) L.nb_cap = 1;
   const size_t N = (size_t)n;
-  const int nbmax = L.nb_n > L.nb_cap ? L.nb_n : L.nb_cap;
-  const size_t hist_words = 256ull * nbmax;
+  // the depth sort's histograms (the tile sort counts through its look-back region)
+  const size_t hist_words = 256ull * L.nb_n;
   size_t scan_words = scan_scratch_words(hist_words);
   if (scan_scratch_words(N) > scan_words) scan_words = scan_scratch_words(N);
   Planner P;
@@ -132,6 +132,7 @@ Workspace plan_workspace(int n, int width, int height, size_t cap) {
     b.tile_start = P.take(4 * ((size_t)L.ntiles + 1));
     b.hist = P.take(4 * hist_words);
     b.scan_part = P.take(4 * scan_words);
+    b.look = P.take(look_bytes(L.nb_cap));
   }
   L.partial = P.take(8 * cap);
   L.tile_order[0] = P.take(4 * (size_t)L.ntiles);

@@ -48,6 +48,7 @@ struct SplatBufs {
   size_t tile_start;    // u32[ntiles + 1]
   size_t hist;          // u32[256 * nblocks] radix histogram / offsets
   size_t scan_part;     // u32 partial sums of the device-wide scan
+  size_t look;          // tile sort: u64[2][256 * nblocks] look-back words, u32 tickets[2], u32 totals[2][256]
 };
 
 struct Workspace {
@@ -179,6 +180,9 @@ void launch_fill_shadow_one(const FrameArgs& f, cudaStream_t s);
 void device_exclusive_scan(const uint32_t* in, uint32_t* out, uint32_t n, uint32_t* total,
                            uint32_t* scratch, cudaStream_t s);
 size_t scan_scratch_words(size_t n);
+
+// bytes of the tile sort's look-back region for nblocks blocks of kSortTileItems
+inline size_t look_bytes(int nblocks) { return 8ull * 2 * 256 * (size_t)nblocks + 4ull * (2 + 2 * 256); }
 
 // stable LSD radix sort of n (key, value) pairs on the low 8 * passes key bits
 // (vin null: values are the input positions); the result lands in (k1, v1)

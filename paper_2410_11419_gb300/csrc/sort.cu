@@ -1,6 +1,6 @@
 // K2-K5: binning of one splat (camera or light) into per-tile depth-ordered
-// lists, the "same pipeline as screen-space splatting" the paper reuses for
-// both the camera view (Sec. 3) and the light view (Sec. 4.2).
+// lists; the paper bins the light view with the same splatting pipeline as
+// the camera view (Sec. 3, Sec. 4.2).
 //
 // Order of operations (LSD radix on the composite (tile, depth) key, with the
 // depth digits sorted once per Gaussian before duplication):
@@ -8,7 +8,8 @@
 //      index order)  -> rank r, order[r]
 //   2. records gathered into rank order, tile counts per rank, exclusive scan
 //   3. one (tile, rank) pair per covered tile, written in rank order
-//   4. stable radix sort of the pairs on the tile bits only
+//   4. stable radix sort of the pairs on the tile bits only: digit totals
+//      counted once, then one pass per 8-bit digit with decoupled look-back
 //   5. per-tile [start, end) ranges
 // Within a tile the result is ascending (depth bits, index), identical to a
 // stable sort of 64-bit (tile << 32 | depth) keys emitted in index order.
@@ -262,6 +263,188 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_radix_scatter(
 }
 
 // ---------------------------------------------------------------------------
+// The tile sort, one kernel per digit pass (decoupled look-back).  Each block
+// takes the next kSortTileItems pairs in order by a ticket, ranks them as
+// k_radix_scatter does, publishes its count of every digit, and adds up the
+// counts of the blocks before it from their published words: a block's own
+// count (kLookAgg) or, once that block finished its look-back, the count of
+// it and of every block before it (kLookPre).  A block waits only on blocks
+// with smaller tickets, which have started and never wait on it; every wait
+// is bounded: past kLookSpin polls the block records GS3_ERR_TIMEOUT in the
+// header and goes on.  The digits' global starts come from totals counted once
+// before the first pass, so no histogram pass or device-wide scan runs between
+// the passes.  The result is that of the stable LSD passes above.
+// ---------------------------------------------------------------------------
+constexpr unsigned long long kLookAgg = 1ull << 32;
+constexpr unsigned long long kLookPre = 2ull << 32;
+constexpr int kLookSpin = 1 << 20;
+
+// Every digit of every pass, counted over the n keys.  Warp-private counters;
+// a warp whose 32 keys share their second digit (the usual case: a splat's
+// tiles are neighbours) adds it once.
+__global__ void __launch_bounds__(256) k_digit_totals(const uint32_t* __restrict__ keys, const uint32_t* n_ptr,
+                                                      int passes, uint32_t* __restrict__ totals) {
+  __shared__ uint32_t h[2][kSortThreads / 32][256];
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+#pragma unroll
+  for (int w = 0; w < kSortThreads / 32; ++w) { h[0][w][t] = 0; h[1][w][t] = 0; }
+  __syncthreads();
+  const uint32_t n = *n_ptr;
+  for (uint32_t wb = (blockIdx.x * (kSortThreads / 32) + warp) * 32u; wb < n; wb += gridDim.x * kSortThreads) {
+    const uint32_t i = wb + lane;
+    const bool valid = i < n;
+    const uint32_t k = valid ? keys[i] : 0u;
+    if (valid) atomicAdd(&h[0][warp][k & 255u], 1u);
+    if (passes > 1) {
+      const uint32_t d1 = (k >> 8) & 255u;
+      const uint32_t first = __shfl_sync(0xffffffffu, d1, 0);
+      const uint32_t vm = __ballot_sync(0xffffffffu, valid);
+      if (__all_sync(0xffffffffu, !valid || d1 == first)) {
+        if (lane == 0) h[1][warp][first] += __popc(vm);
+      } else if (valid) {
+        atomicAdd(&h[1][warp][d1], 1u);
+      }
+    }
+    __syncwarp();
+  }
+  __syncthreads();
+  for (int p = 0; p < passes; ++p) {
+    uint32_t c = 0;
+#pragma unroll
+    for (int w = 0; w < kSortThreads / 32; ++w) c += h[p][w][t];
+    if (c) atomicAdd(&totals[p * 256 + t], c);
+  }
+}
+
+template <int ROUNDS>
+struct OnesweepSmem {
+  uint32_t base[256];    // the block's first output slot per digit
+  uint32_t start[256];   // first staging slot per digit
+  uint32_t cnt[kSortThreads / 32][256];  // per warp and digit: items so far, then the warp's first slot
+  uint32_t wsum[kSortThreads / 32], gsum[kSortThreads / 32];
+  uint32_t ticket;
+  uint32_t key[kSortThreads * ROUNDS], val[kSortThreads * ROUNDS];
+};
+
+template <int ROUNDS>
+__global__ void __launch_bounds__(kSortThreads, 3) k_onesweep(
+    const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint32_t* __restrict__ kout,
+    uint32_t* __restrict__ vout, const uint32_t* n_ptr, int shift, const uint32_t* __restrict__ totals,
+    unsigned long long* look, uint32_t* ticket, uint32_t* header) {
+  constexpr int kItems = kSortThreads * ROUNDS;
+  constexpr int kWarps = kSortThreads / 32;
+  extern __shared__ uint4 onesweep_raw[];
+  OnesweepSmem<ROUNDS>& S = *reinterpret_cast<OnesweepSmem<ROUNDS>*>(onesweep_raw);
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  const uint32_t n = *n_ptr;
+  if (t == 0) S.ticket = atomicAdd(ticket, 1u);
+#pragma unroll
+  for (int w = 0; w < kWarps; ++w) S.cnt[w][t] = 0;
+  __syncthreads();
+  const uint32_t blk = S.ticket;
+  const uint32_t base = blk * (uint32_t)kItems;
+  if (base >= n) return;  // every later ticket is past the end as well
+  const uint32_t lt = (1u << lane) - 1u;
+  const uint32_t wbase = base + (uint32_t)warp * (32u * ROUNDS);
+  uint32_t kk[ROUNDS], vv[ROUNDS];
+  uint32_t rk[(ROUNDS + 1) / 2];  // two 16-bit ranks per word
+#pragma unroll
+  for (int r = 0; r < ROUNDS; ++r) {
+    const uint32_t i = wbase + r * 32 + lane;
+    const bool valid = i < n;
+    kk[r] = valid ? kin[i] : 0u;
+    vv[r] = valid ? vin[i] : 0u;
+  }
+#pragma unroll
+  for (int r = 0; r < ROUNDS; ++r) {
+    const bool valid = wbase + r * 32 + lane < n;
+    const uint32_t d = valid ? (kk[r] >> shift) & 255u : 256u;
+    const uint32_t peers = __match_any_sync(0xffffffffu, d);
+    const int leader = __ffs(peers) - 1;
+    uint32_t c = 0;
+    if (valid && lane == leader) c = S.cnt[warp][d];
+    c = __shfl_sync(0xffffffffu, c, leader);
+    const uint32_t rank = c + __popc(peers & lt);
+    rk[r >> 1] = (r & 1) ? (rk[r >> 1] | (rank << 16)) : rank;
+    if (valid && lane == leader) S.cnt[warp][d] = c + __popc(peers);
+    __syncwarp();
+  }
+  __syncthreads();
+  {
+    // thread t = digit t: the block's count, published at once
+    uint32_t tot = 0;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) {
+      const uint32_t c = S.cnt[w][t];
+      S.cnt[w][t] = tot;
+      tot += c;
+    }
+    volatile unsigned long long* mine = look + (size_t)blk * 256 + t;
+    *mine = (blk == 0 ? kLookPre : kLookAgg) | tot;
+    // staging starts (scan of the block's counts) and the digit's start over
+    // all items (scan of the totals)
+    const uint32_t g = totals[t];
+    uint32_t x = tot, y = g;
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t a = __shfl_up_sync(0xffffffffu, x, o);
+      const uint32_t b = __shfl_up_sync(0xffffffffu, y, o);
+      if (lane >= o) { x += a; y += b; }
+    }
+    if (lane == 31) { S.wsum[warp] = x; S.gsum[warp] = y; }
+    // the blocks before this one
+    uint32_t excl = 0;
+    if (blk > 0) {
+      uint32_t j = blk - 1;
+      int spins = 0;
+      for (;;) {
+        const unsigned long long v = *(volatile const unsigned long long*)(look + (size_t)j * 256 + t);
+        const uint32_t flag = (uint32_t)(v >> 32);
+        if (flag == 0u) {
+          if (++spins > kLookSpin) {
+            atomicCAS(header + H_STATUS, 0u, (uint32_t)GS3_ERR_TIMEOUT);
+            break;
+          }
+          __nanosleep(32);
+          continue;
+        }
+        excl += (uint32_t)v;
+        if (flag == 2u || j == 0u) break;
+        --j;
+      }
+      *mine = kLookPre | (unsigned long long)(excl + tot);
+    }
+    __syncthreads();
+    uint32_t before = 0, gbefore = 0;
+    for (int w = 0; w < warp; ++w) { before += S.wsum[w]; gbefore += S.gsum[w]; }
+    const uint32_t st = before + x - tot;
+    S.start[t] = st;
+    S.base[t] = gbefore + y - g + excl;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) S.cnt[w][t] += st;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < ROUNDS; ++r) {
+    if (wbase + r * 32 + lane < n) {
+      const uint32_t lp = S.cnt[warp][(kk[r] >> shift) & 255u] + ((rk[r >> 1] >> (16 * (r & 1))) & 0xFFFFu);
+      S.key[lp] = kk[r];
+      S.val[lp] = vv[r];
+    }
+  }
+  __syncthreads();
+  const uint32_t cnt = min((uint32_t)kItems, n - base);
+  for (uint32_t i = t; i < cnt; i += kSortThreads) {
+    const uint32_t k = S.key[i];
+    const uint32_t d = (k >> shift) & 255u;
+    const uint32_t pos = S.base[d] + (i - S.start[d]);
+    if (pos < n) {
+      kout[pos] = k;
+      vout[pos] = S.val[i];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Rank order, counts, emission, ranges
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_reorder(int n, const uint32_t* __restrict__ order,
@@ -347,12 +530,10 @@ void radix_sort_t(const uint32_t* kin, const uint32_t* vin, uint32_t* k0, uint32
   }
 }
 
-// the pair sorts and gs3_depth_order_static: 4096 items per block, three-kernel scans.
-// The last pass's digits are below last_digits, so only those rows of its
-// histogram are scanned (the other rows are zero and no item reads them).
+// gs3_depth_order_static: 4096 items per block, three-kernel scans
 void radix_sort(const uint32_t* kin, const uint32_t* vin, uint32_t* k0, uint32_t* v0, uint32_t* k1,
                 uint32_t* v1, const uint32_t* n_ptr, uint32_t n_fixed, int nblocks, int passes,
-                uint32_t last_digits, uint32_t* hist, uint32_t* scan_part, cudaStream_t s) {
+                uint32_t* hist, uint32_t* scan_part, cudaStream_t s) {
   static bool configured = false;
   if (!configured) {
     cudaFuncSetAttribute(k_radix_scatter<kSortRounds>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -365,8 +546,7 @@ void radix_sort(const uint32_t* kin, const uint32_t* vin, uint32_t* k0, uint32_t
     uint32_t* ko = (p & 1) ? k1 : k0;
     uint32_t* vo = (p & 1) ? v1 : v0;
     k_radix_hist<kSortRounds><<<nblocks, kSortThreads, 0, s>>>(ki, n_ptr, n_fixed, 8 * p, hist, nblocks);
-    const uint32_t rows = p == passes - 1 ? last_digits : 256u;
-    device_exclusive_scan(hist, hist, rows * nblocks, nullptr, scan_part, s);
+    device_exclusive_scan(hist, hist, 256u * nblocks, nullptr, scan_part, s);
     k_radix_scatter<kSortRounds><<<nblocks, kSortThreads, sizeof(ScatterSmem<kSortRounds>), s>>>(
         ki, vi, ko, vo, n_ptr, n_fixed, 8 * p, hist, nblocks);
     count_launch(2);
@@ -383,7 +563,7 @@ void radix_sort_pairs(const uint32_t* kin, const uint32_t* vin, uint32_t* k0, ui
                       uint32_t* v1, uint32_t n, int passes, uint32_t* hist, uint32_t* scan_part,
                       cudaStream_t s) {
   const int nblocks = (int)((n + kSortTileItems - 1) / kSortTileItems);
-  radix_sort(kin, vin, k0, v0, k1, v1, nullptr, n, nblocks, passes, 256u, hist, scan_part, s);
+  radix_sort(kin, vin, k0, v0, k1, v1, nullptr, n, nblocks, passes, hist, scan_part, s);
 }
 
 void device_exclusive_scan(const uint32_t* in, uint32_t* out, uint32_t n, uint32_t* total,
@@ -431,11 +611,26 @@ void launch_binning(const FrameArgs& f, int sp, cudaStream_t s) {
   count_launch();
   const int passes = tile_sort_passes(f.L->ntiles);
   // sort (tile, rank) pairs on the tile bits; start from buffer 0, alternate
-  radix_sort(at<uint32_t>(ws, b.tk[0]), at<uint32_t>(ws, b.tv[0]), at<uint32_t>(ws, b.tk[1]),
-             at<uint32_t>(ws, b.tv[1]), at<uint32_t>(ws, b.tk[0]), at<uint32_t>(ws, b.tv[0]),
-             header + h_pairs, 0, f.L->nb_cap, passes, ((uint32_t)(f.L->ntiles - 1) >> (8 * (passes - 1))) + 1u,
-             at<uint32_t>(ws, b.hist),
-             at<uint32_t>(ws, b.scan_part), s);
+  {
+    static bool configured = false;
+    if (!configured) {
+      cudaFuncSetAttribute(k_onesweep<kSortRounds>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)sizeof(OnesweepSmem<kSortRounds>));
+      configured = true;
+    }
+    unsigned long long* look = at<unsigned long long>(ws, b.look);
+    uint32_t* tickets = reinterpret_cast<uint32_t*>(look + 2ull * 256 * (size_t)f.L->nb_cap);
+    uint32_t* totals = tickets + 2;
+    cudaMemsetAsync(look, 0, look_bytes(f.L->nb_cap), s);
+    k_digit_totals<<<152 * 4, kSortThreads, 0, s>>>(at<uint32_t>(ws, b.tk[0]), header + h_pairs, passes, totals);
+    for (int p = 0; p < passes; ++p) {
+      const int i = p & 1, o = i ^ 1;
+      k_onesweep<kSortRounds><<<f.L->nb_cap, kSortThreads, sizeof(OnesweepSmem<kSortRounds>), s>>>(
+          at<uint32_t>(ws, b.tk[i]), at<uint32_t>(ws, b.tv[i]), at<uint32_t>(ws, b.tk[o]), at<uint32_t>(ws, b.tv[o]),
+          header + h_pairs, 8 * p, totals + 256 * p, look + (size_t)p * 256 * f.L->nb_cap, tickets + p, header);
+    }
+    count_launch(1 + passes);
+  }
   const int fin = passes & 1;  // 1 pass ends in buffer 1, 2 passes in buffer 0
   const uint32_t* keys = at<uint32_t>(ws, b.tk[fin]);
   int blocks = (int)((f.L->cap + 1 + 255) / 256);
