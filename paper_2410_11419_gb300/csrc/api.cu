@@ -105,10 +105,7 @@ Workspace plan_workspace(int n, int width, int height, size_t cap) {
   L.nb_cap = (int)((cap + kSortTileItems - 1) / kSortTileItems);
   if (L.nb_cap < 1) L.nb_cap = 1;
   const size_t N = (size_t)n;
-  // the depth sort's histograms (the tile sort counts through its look-back region)
-  const size_t hist_words = 256ull * L.nb_n;
-  size_t scan_words = scan_scratch_words(hist_words);
-  if (scan_scratch_words(N) > scan_words) scan_words = scan_scratch_words(N);
+  const size_t scan_words = scan_scratch_words(N);  // the scan of the tile counts
   Planner P;
   L.header = P.take(256);
   for (int s = 0; s < 2; ++s) {
@@ -130,9 +127,9 @@ Workspace plan_workspace(int n, int width, int height, size_t cap) {
     b.tv[0] = P.take(4 * cap);
     b.tv[1] = P.take(4 * cap);
     b.tile_start = P.take(4 * ((size_t)L.ntiles + 1));
-    b.hist = P.take(4 * hist_words);
     b.scan_part = P.take(4 * scan_words);
-    b.look = P.take(look_bytes(L.nb_cap));
+    b.look = P.take(onesweep_bytes(L.nb_cap, 2));
+    b.dlook = P.take(onesweep_bytes(L.nb_n, 4));
   }
   L.partial = P.take(8 * cap);
   L.tile_order[0] = P.take(4 * (size_t)L.ntiles);

@@ -46,9 +46,9 @@ struct SplatBufs {
   size_t off;           // u32[N] exclusive prefix of cnt
   size_t tk[2], tv[2];  // u32[cap] tile-sort ping-pong (key = tile, value = rank)
   size_t tile_start;    // u32[ntiles + 1]
-  size_t hist;          // u32[256 * nblocks] radix histogram / offsets
   size_t scan_part;     // u32 partial sums of the device-wide scan
-  size_t look;          // tile sort: u64[2][256 * nblocks] look-back words, u32 tickets[2], u32 totals[2][256]
+  size_t look;          // tile sort's look-back region, onesweep_bytes(nb_cap, 2)
+  size_t dlook;         // depth sort's look-back region, onesweep_bytes(nb_n, 4)
 };
 
 struct Workspace {
@@ -181,8 +181,11 @@ void device_exclusive_scan(const uint32_t* in, uint32_t* out, uint32_t n, uint32
                            uint32_t* scratch, cudaStream_t s);
 size_t scan_scratch_words(size_t n);
 
-// bytes of the tile sort's look-back region for nblocks blocks of kSortTileItems
-inline size_t look_bytes(int nblocks) { return 8ull * 2 * 256 * (size_t)nblocks + 4ull * (2 + 2 * 256); }
+// bytes of a look-back sort's region: u64[passes][256 * nblocks] look-back
+// words, u32 tickets[passes], u32 totals[passes][256]
+inline size_t onesweep_bytes(int nblocks, int passes) {
+  return 8ull * passes * 256 * (size_t)nblocks + 4ull * (passes + passes * 256);
+}
 
 // stable LSD radix sort of n (key, value) pairs on the low 8 * passes key bits
 // (vin null: values are the input positions); the result lands in (k1, v1)

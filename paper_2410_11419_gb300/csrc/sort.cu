@@ -279,33 +279,38 @@ constexpr unsigned long long kLookAgg = 1ull << 32;
 constexpr unsigned long long kLookPre = 2ull << 32;
 constexpr int kLookSpin = 1 << 20;
 
-// Every digit of every pass, counted over the n keys.  Warp-private counters;
-// a warp whose 32 keys share their second digit (the usual case: a splat's
-// tiles are neighbours) adds it once.
+// Every digit of every pass (PASSES <= 4 eight-bit digits), counted over the
+// n keys.  Warp-private counters; a warp whose 32 keys share a digit (the
+// usual case for a tile key's second digit, a splat's tiles being
+// neighbours, and for the top digits of the depth keys) adds it once.
+template <int PASSES>
 __global__ void __launch_bounds__(256) k_digit_totals(const uint32_t* __restrict__ keys, const uint32_t* n_ptr,
-                                                      int passes, uint32_t* __restrict__ totals) {
-  __shared__ uint32_t h[2][kSortThreads / 32][256];
+                                                      uint32_t n_fixed, int passes, uint32_t* __restrict__ totals) {
+  __shared__ uint32_t h[PASSES][kSortThreads / 32][256];
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
 #pragma unroll
-  for (int w = 0; w < kSortThreads / 32; ++w) { h[0][w][t] = 0; h[1][w][t] = 0; }
+  for (int p = 0; p < PASSES; ++p)
+#pragma unroll
+    for (int w = 0; w < kSortThreads / 32; ++w) h[p][w][t] = 0;
   __syncthreads();
-  const uint32_t n = *n_ptr;
+  const uint32_t n = load_n(n_ptr, n_fixed);
   for (uint32_t wb = (blockIdx.x * (kSortThreads / 32) + warp) * 32u; wb < n; wb += gridDim.x * kSortThreads) {
     const uint32_t i = wb + lane;
     const bool valid = i < n;
     const uint32_t k = valid ? keys[i] : 0u;
-    if (valid) atomicAdd(&h[0][warp][k & 255u], 1u);
-    if (passes > 1) {
-      const uint32_t d1 = (k >> 8) & 255u;
-      const uint32_t first = __shfl_sync(0xffffffffu, d1, 0);
-      const uint32_t vm = __ballot_sync(0xffffffffu, valid);
-      if (__all_sync(0xffffffffu, !valid || d1 == first)) {
-        if (lane == 0) h[1][warp][first] += __popc(vm);
+    const uint32_t vm = __ballot_sync(0xffffffffu, valid);
+#pragma unroll
+    for (int p = 0; p < PASSES; ++p) {
+      if (p >= passes) break;
+      const uint32_t d = (k >> (8 * p)) & 255u;
+      const uint32_t first = __shfl_sync(0xffffffffu, d, 0);
+      if (__all_sync(0xffffffffu, !valid || d == first)) {
+        if (lane == 0) h[p][warp][first] += __popc(vm);
       } else if (valid) {
-        atomicAdd(&h[1][warp][d1], 1u);
+        atomicAdd(&h[p][warp][d], 1u);
       }
+      __syncwarp();
     }
-    __syncwarp();
   }
   __syncthreads();
   for (int p = 0; p < passes; ++p) {
@@ -329,14 +334,14 @@ struct OnesweepSmem {
 template <int ROUNDS>
 __global__ void __launch_bounds__(kSortThreads, 3) k_onesweep(
     const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint32_t* __restrict__ kout,
-    uint32_t* __restrict__ vout, const uint32_t* n_ptr, int shift, const uint32_t* __restrict__ totals,
-    unsigned long long* look, uint32_t* ticket, uint32_t* header) {
+    uint32_t* __restrict__ vout, const uint32_t* n_ptr, uint32_t n_fixed, int shift,
+    const uint32_t* __restrict__ totals, unsigned long long* look, uint32_t* ticket, uint32_t* header) {
   constexpr int kItems = kSortThreads * ROUNDS;
   constexpr int kWarps = kSortThreads / 32;
   extern __shared__ uint4 onesweep_raw[];
   OnesweepSmem<ROUNDS>& S = *reinterpret_cast<OnesweepSmem<ROUNDS>*>(onesweep_raw);
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
-  const uint32_t n = *n_ptr;
+  const uint32_t n = load_n(n_ptr, n_fixed);
   if (t == 0) S.ticket = atomicAdd(ticket, 1u);
 #pragma unroll
   for (int w = 0; w < kWarps; ++w) S.cnt[w][t] = 0;
@@ -353,7 +358,7 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_onesweep(
     const uint32_t i = wbase + r * 32 + lane;
     const bool valid = i < n;
     kk[r] = valid ? kin[i] : 0u;
-    vv[r] = valid ? vin[i] : 0u;
+    vv[r] = valid ? (vin ? vin[i] : i) : 0u;
   }
 #pragma unroll
   for (int r = 0; r < ROUNDS; ++r) {
@@ -505,31 +510,6 @@ __global__ void __launch_bounds__(256) k_ranges(const uint32_t* __restrict__ key
   }
 }
 
-template <int ROUNDS>
-void radix_sort_t(const uint32_t* kin, const uint32_t* vin, uint32_t* k0, uint32_t* v0, uint32_t* k1,
-                  uint32_t* v1, const uint32_t* n_ptr, uint32_t n_fixed, int nblocks, int passes,
-                  uint32_t* hist, uint32_t* scan_part, cudaStream_t s) {
-  static bool configured = false;
-  if (!configured) {
-    cudaFuncSetAttribute(k_radix_scatter<ROUNDS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)sizeof(ScatterSmem<ROUNDS>));
-    configured = true;
-  }
-  const uint32_t* ki = kin;
-  const uint32_t* vi = vin;
-  for (int p = 0; p < passes; ++p) {
-    uint32_t* ko = (p & 1) ? k1 : k0;
-    uint32_t* vo = (p & 1) ? v1 : v0;
-    k_radix_hist<ROUNDS><<<nblocks, kSortThreads, 0, s>>>(ki, n_ptr, n_fixed, 8 * p, hist, nblocks);
-    device_exclusive_scan(hist, hist, 256u * nblocks, nullptr, scan_part, s);
-    k_radix_scatter<ROUNDS><<<nblocks, kSortThreads, sizeof(ScatterSmem<ROUNDS>), s>>>(
-        ki, vi, ko, vo, n_ptr, n_fixed, 8 * p, hist, nblocks);
-    count_launch(2);
-    ki = ko;
-    vi = vo;
-  }
-}
-
 // gs3_depth_order_static: 4096 items per block, three-kernel scans
 void radix_sort(const uint32_t* kin, const uint32_t* vin, uint32_t* k0, uint32_t* v0, uint32_t* k1,
                 uint32_t* v1, const uint32_t* n_ptr, uint32_t n_fixed, int nblocks, int passes,
@@ -553,6 +533,43 @@ void radix_sort(const uint32_t* kin, const uint32_t* vin, uint32_t* k0, uint32_t
     ki = ko;
     vi = vo;
   }
+}
+
+// Stable LSD sort of (key, value) pairs (vin null: values are the input
+// positions) on the low 8 * passes key bits (passes <= PASSES): one
+// k_digit_totals, then one k_onesweep per pass.  Even passes write (k0, v0),
+// odd passes (k1, v1), each reading the previous pass's output (pass 0 reads
+// (kin, vin)).  look_region: onesweep_bytes(nblocks, PASSES) bytes, zeroed here.
+template <int ROUNDS, int PASSES>
+void onesweep_sort(const uint32_t* kin, const uint32_t* vin, uint32_t* k0, uint32_t* v0, uint32_t* k1,
+                   uint32_t* v1, const uint32_t* n_ptr, uint32_t n_fixed, int nblocks, int passes,
+                   unsigned char* look_region, uint32_t* header, cudaStream_t s) {
+  static bool configured = false;
+  if (!configured) {
+    cudaFuncSetAttribute(k_onesweep<ROUNDS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sizeof(OnesweepSmem<ROUNDS>));
+    configured = true;
+  }
+  unsigned long long* look = reinterpret_cast<unsigned long long*>(look_region);
+  uint32_t* tickets = reinterpret_cast<uint32_t*>(look + (size_t)PASSES * 256 * (size_t)nblocks);
+  uint32_t* totals = tickets + PASSES;
+  cudaMemsetAsync(look_region, 0, onesweep_bytes(nblocks, PASSES), s);
+  int tb = n_ptr ? 152 * 4 : (int)((n_fixed + 4095) / 4096);
+  if (tb < 1) tb = 1;
+  if (tb > 152 * 4) tb = 152 * 4;
+  k_digit_totals<PASSES><<<tb, kSortThreads, 0, s>>>(kin, n_ptr, n_fixed, passes, totals);
+  const uint32_t* ki = kin;
+  const uint32_t* vi = vin;
+  for (int p = 0; p < passes; ++p) {
+    uint32_t* ko = (p & 1) ? k1 : k0;
+    uint32_t* vo = (p & 1) ? v1 : v0;
+    k_onesweep<ROUNDS><<<nblocks, kSortThreads, sizeof(OnesweepSmem<ROUNDS>), s>>>(
+        ki, vi, ko, vo, n_ptr, n_fixed, 8 * p, totals + 256 * p, look + (size_t)p * 256 * nblocks, tickets + p,
+        header);
+    ki = ko;
+    vi = vo;
+  }
+  count_launch(1 + passes);
 }
 
 }  // namespace
@@ -584,10 +601,10 @@ void launch_depth_sort(const FrameArgs& f, int sp, cudaStream_t s) {
   const int n = f.sc.n;
   // 1024 keys per block: four times the blocks of the pair sorts, for a
   // sort of a few hundred thousand keys that would otherwise leave SMs idle
-  radix_sort_t<kDepthSortRounds>(at<uint32_t>(ws, b.key), nullptr, at<uint32_t>(ws, b.sk[0]),
-                                 at<uint32_t>(ws, b.sv[0]), at<uint32_t>(ws, b.sk[1]), at<uint32_t>(ws, b.sv[1]),
-                                 nullptr, (uint32_t)n, f.L->nb_n, 4, at<uint32_t>(ws, b.hist),
-                                 at<uint32_t>(ws, b.scan_part), s);
+  onesweep_sort<kDepthSortRounds, 4>(at<uint32_t>(ws, b.key), nullptr, at<uint32_t>(ws, b.sk[0]),
+                                     at<uint32_t>(ws, b.sv[0]), at<uint32_t>(ws, b.sk[1]), at<uint32_t>(ws, b.sv[1]),
+                                     nullptr, (uint32_t)n, f.L->nb_n, 4, at<unsigned char>(ws, b.dlook),
+                                     at<uint32_t>(ws, f.L->header), s);
   // 4 passes end in buffer 1: sv[1] holds the index of each depth rank
   k_reorder<<<(n + 255) / 256, 256, 0, s>>>(
       n, at<uint32_t>(ws, b.sv[1]), at<SplatRec>(ws, b.rec), at<SplatRec>(ws, b.rrec),
@@ -611,26 +628,9 @@ void launch_binning(const FrameArgs& f, int sp, cudaStream_t s) {
   count_launch();
   const int passes = tile_sort_passes(f.L->ntiles);
   // sort (tile, rank) pairs on the tile bits; start from buffer 0, alternate
-  {
-    static bool configured = false;
-    if (!configured) {
-      cudaFuncSetAttribute(k_onesweep<kSortRounds>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)sizeof(OnesweepSmem<kSortRounds>));
-      configured = true;
-    }
-    unsigned long long* look = at<unsigned long long>(ws, b.look);
-    uint32_t* tickets = reinterpret_cast<uint32_t*>(look + 2ull * 256 * (size_t)f.L->nb_cap);
-    uint32_t* totals = tickets + 2;
-    cudaMemsetAsync(look, 0, look_bytes(f.L->nb_cap), s);
-    k_digit_totals<<<152 * 4, kSortThreads, 0, s>>>(at<uint32_t>(ws, b.tk[0]), header + h_pairs, passes, totals);
-    for (int p = 0; p < passes; ++p) {
-      const int i = p & 1, o = i ^ 1;
-      k_onesweep<kSortRounds><<<f.L->nb_cap, kSortThreads, sizeof(OnesweepSmem<kSortRounds>), s>>>(
-          at<uint32_t>(ws, b.tk[i]), at<uint32_t>(ws, b.tv[i]), at<uint32_t>(ws, b.tk[o]), at<uint32_t>(ws, b.tv[o]),
-          header + h_pairs, 8 * p, totals + 256 * p, look + (size_t)p * 256 * f.L->nb_cap, tickets + p, header);
-    }
-    count_launch(1 + passes);
-  }
+  onesweep_sort<kSortRounds, 2>(at<uint32_t>(ws, b.tk[0]), at<uint32_t>(ws, b.tv[0]), at<uint32_t>(ws, b.tk[1]),
+                                at<uint32_t>(ws, b.tv[1]), at<uint32_t>(ws, b.tk[0]), at<uint32_t>(ws, b.tv[0]),
+                                header + h_pairs, 0, f.L->nb_cap, passes, at<unsigned char>(ws, b.look), header, s);
   const int fin = passes & 1;  // 1 pass ends in buffer 1, 2 passes in buffer 0
   const uint32_t* keys = at<uint32_t>(ws, b.tk[fin]);
   int blocks = (int)((f.L->cap + 1 + 255) / 256);
