@@ -102,7 +102,7 @@ Workspace plan_workspace(int n, int width, int height, size_t cap) {
   L.ntiles = L.gx * L.gy;
   L.cap = cap;
   L.nb_n = (int)((n + kDepthSortItems - 1) / kDepthSortItems);
-  L.nb_cap = (int)((cap + kSortTileItems - 1) / kSortTileItems);
+  L.nb_cap = (int)((cap + kTileSortItems - 1) / kTileSortItems);
   if (L.nb_cap < 1) L.nb_cap = 1;
   const size_t N = (size_t)n;
   const size_t scan_words = scan_scratch_words(N);  // the scan of the tile counts

@@ -15,6 +15,8 @@ constexpr int kTilePix = kTile * kTile;
 constexpr int kSortThreads = 256;     // radix-sort block size
 constexpr int kSortRounds = 16;       // items per thread per block tile
 constexpr int kSortTileItems = kSortThreads * kSortRounds;  // 4096 items per block
+constexpr int kTileSortRounds = 16;   // the look-back tile sort: items per thread per block
+constexpr int kTileSortItems = kSortThreads * kTileSortRounds;
 constexpr int kDepthSortRounds = 4;   // the per-splat depth sort: 1024 keys per block
 constexpr int kDepthSortItems = kSortThreads * kDepthSortRounds;
 constexpr int kScanItems = 4096;      // items per block in the device-wide scan

@@ -628,7 +628,7 @@ void launch_binning(const FrameArgs& f, int sp, cudaStream_t s) {
   count_launch();
   const int passes = tile_sort_passes(f.L->ntiles);
   // sort (tile, rank) pairs on the tile bits; start from buffer 0, alternate
-  onesweep_sort<kSortRounds, 2>(at<uint32_t>(ws, b.tk[0]), at<uint32_t>(ws, b.tv[0]), at<uint32_t>(ws, b.tk[1]),
+  onesweep_sort<kTileSortRounds, 2>(at<uint32_t>(ws, b.tk[0]), at<uint32_t>(ws, b.tv[0]), at<uint32_t>(ws, b.tk[1]),
                                 at<uint32_t>(ws, b.tv[1]), at<uint32_t>(ws, b.tk[0]), at<uint32_t>(ws, b.tv[0]),
                                 header + h_pairs, 0, f.L->nb_cap, passes, at<unsigned char>(ws, b.look), header, s);
   const int fin = passes & 1;  // 1 pass ends in buffer 1, 2 passes in buffer 0
