@@ -294,22 +294,31 @@ __global__ void __launch_bounds__(256) k_digit_totals(const uint32_t* __restrict
     for (int w = 0; w < kSortThreads / 32; ++w) h[p][w][t] = 0;
   __syncthreads();
   const uint32_t n = load_n(n_ptr, n_fixed);
-  for (uint32_t wb = (blockIdx.x * (kSortThreads / 32) + warp) * 32u; wb < n; wb += gridDim.x * kSortThreads) {
-    const uint32_t i = wb + lane;
-    const bool valid = i < n;
-    const uint32_t k = valid ? keys[i] : 0u;
-    const uint32_t vm = __ballot_sync(0xffffffffu, valid);
+  // each warp takes 128 consecutive keys per step, four coalesced loads in flight per lane
+  for (uint32_t wb = (blockIdx.x * (kSortThreads / 32) + warp) * 128u; wb < n; wb += gridDim.x * kSortThreads * 4u) {
+    uint32_t k[4];
 #pragma unroll
-    for (int p = 0; p < PASSES; ++p) {
-      if (p >= passes) break;
-      const uint32_t d = (k >> (8 * p)) & 255u;
-      const uint32_t first = __shfl_sync(0xffffffffu, d, 0);
-      if (__all_sync(0xffffffffu, !valid || d == first)) {
-        if (lane == 0) h[p][warp][first] += __popc(vm);
-      } else if (valid) {
-        atomicAdd(&h[p][warp][d], 1u);
+    for (int u = 0; u < 4; ++u) {
+      const uint32_t i = wb + 32u * u + lane;
+      k[u] = i < n ? keys[i] : 0u;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const bool valid = wb + 32u * u + lane < n;
+      const uint32_t vm = __ballot_sync(0xffffffffu, valid);
+      if (!vm) break;
+#pragma unroll
+      for (int p = 0; p < PASSES; ++p) {
+        if (p >= passes) break;
+        const uint32_t d = (k[u] >> (8 * p)) & 255u;
+        const uint32_t first = __shfl_sync(0xffffffffu, d, 0);
+        if (__all_sync(0xffffffffu, !valid || d == first)) {
+          if (lane == 0) h[p][warp][first] += __popc(vm);
+        } else if (valid) {
+          atomicAdd(&h[p][warp][d], 1u);
+        }
+        __syncwarp();
       }
-      __syncwarp();
     }
   }
   __syncthreads();
@@ -554,7 +563,7 @@ void onesweep_sort(const uint32_t* kin, const uint32_t* vin, uint32_t* k0, uint3
   uint32_t* tickets = reinterpret_cast<uint32_t*>(look + (size_t)PASSES * 256 * (size_t)nblocks);
   uint32_t* totals = tickets + PASSES;
   cudaMemsetAsync(look_region, 0, onesweep_bytes(nblocks, PASSES), s);
-  int tb = n_ptr ? 152 * 4 : (int)((n_fixed + 4095) / 4096);
+  int tb = n_ptr ? 152 * 4 : (int)((n_fixed + 1023) / 1024);
   if (tb < 1) tb = 1;
   if (tb > 152 * 4) tb = 152 * 4;
   k_digit_totals<PASSES><<<tb, kSortThreads, 0, s>>>(kin, n_ptr, n_fixed, passes, totals);
