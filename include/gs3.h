@@ -402,6 +402,23 @@ gs3_status gs3_server_destroy(gs3_server *server);
 #define GS3_STATIC_SORT_MAX_KEYS 1048576u
 gs3_status gs3_depth_order_static(const uint32_t *keys, uint32_t n, uint32_t *order_out, void *stream);
 
+/* ---- Self-test of the bounded device waits ------------------------------
+ * Not an operation of the paper: a check that a device-side wait which can
+ * never end gives up instead of holding the GPU.  Runs one pass of the
+ * look-back tile sort that gs3_render's binning uses (each block waits for
+ * the digit counts of the blocks before it) over n zero keys in scratch it
+ * allocates and frees, with the block tickets starting at 1, so the waits
+ * reach ticket 0's words, which no block writes.  Each such wait gives up
+ * after its poll bound (well under a second) and the pass records
+ * GS3_ERR_TIMEOUT, then finishes; the context stays usable.
+ *   n:          4096 < n <= 1048576 (at least two blocks of 4096 keys)
+ *   status_out: host, one uint32: the pass's status word, GS3_ERR_TIMEOUT
+ *               when the bounded wait works
+ * Synchronous (synchronises the device).  GS3_ERR_INVALID_ARG for n out of
+ * range or a null status_out; GS3_ERR_OOM or GS3_ERR_CUDA (message in
+ * gs3_last_error) when the scratch allocation or a CUDA call fails. */
+gs3_status gs3_selftest_wait_timeout(uint32_t n, uint32_t *status_out);
+
 /* Number of CUDA kernels this library has launched in this process (all
  * threads, all devices); a host-side counter for launch accounting. */
 uint64_t gs3_kernel_launches(void);

@@ -156,6 +156,7 @@ SIGNATURES = {
     "gs3_server_reset_counters": (C.c_int, [_SERVER_P]),
     "gs3_server_destroy": (C.c_int, [_SERVER_P]),
     "gs3_depth_order_static": (C.c_int, [C.c_void_p, C.c_uint32, C.c_void_p, C.c_void_p]),
+    "gs3_selftest_wait_timeout": (C.c_int, [C.c_uint32, C.POINTER(C.c_uint32)]),
     "gs3_kernel_launches": (C.c_uint64, []),
     "gs3_last_error": (C.c_char_p, []),
 }
@@ -350,6 +351,13 @@ GS3_STATIC_SORT_MAX_KEYS = 1048576
 def gs3_depth_order_static(keys, n: int, order_out, stream: int) -> None:
     _check(lib().gs3_depth_order_static(_ptr(keys), n, _ptr(order_out), stream),
            "gs3_depth_order_static")
+
+
+def gs3_selftest_wait_timeout(n: int) -> int:
+    """The status word of a look-back sort pass whose waits can never end."""
+    out = C.c_uint32(0)
+    _check(lib().gs3_selftest_wait_timeout(n, C.byref(out)), "gs3_selftest_wait_timeout")
+    return int(out.value)
 
 
 def gs3_kernel_launches() -> int:

@@ -650,3 +650,50 @@ void launch_binning(const FrameArgs& f, int sp, cudaStream_t s) {
 }
 
 }  // namespace gs3
+
+// Self-test of the bounded waits: one look-back pass over n zero keys whose
+// tickets start at 1, so every block's look-back reaches ticket 0's words,
+// which no block writes.  Each such wait must give up after kLookSpin polls
+// and record GS3_ERR_TIMEOUT; the pass then finishes.
+extern "C" gs3_status gs3_selftest_wait_timeout(uint32_t n, uint32_t* status_out) {
+  using namespace gs3;
+  if (!status_out || n <= (uint32_t)kTileSortItems || n > (1u << 20)) {
+    set_last_error("gs3_selftest_wait_timeout: need status_out and 4096 < n <= 1 << 20");
+    return GS3_ERR_INVALID_ARG;
+  }
+  const int nblocks = (int)((n + kTileSortItems - 1) / kTileSortItems);
+  const size_t look = onesweep_bytes(nblocks, 1);
+  const size_t bytes = 16ull * n + look + 16;
+  unsigned char* d = nullptr;
+  if (cudaMalloc(&d, bytes) != cudaSuccess) {
+    set_last_error("gs3_selftest_wait_timeout: cudaMalloc failed");
+    return GS3_ERR_OOM;
+  }
+  uint32_t* kin = reinterpret_cast<uint32_t*>(d);
+  uint32_t* vin = kin + n;
+  uint32_t* kout = vin + n;
+  uint32_t* vout = kout + n;
+  unsigned long long* lk = reinterpret_cast<unsigned long long*>(d + 16ull * n);
+  uint32_t* tickets = reinterpret_cast<uint32_t*>(lk + 256ull * nblocks);
+  uint32_t* totals = tickets + 1;
+  uint32_t* status = reinterpret_cast<uint32_t*>(d + 16ull * n + look);
+  const uint32_t first_ticket = 1;
+  cudaError_t e = cudaMemset(d, 0, bytes);
+  if (e == cudaSuccess) e = cudaMemcpy(tickets, &first_ticket, 4, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    cudaFuncSetAttribute(k_onesweep<kTileSortRounds>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sizeof(OnesweepSmem<kTileSortRounds>));
+    k_onesweep<kTileSortRounds><<<nblocks, kSortThreads, sizeof(OnesweepSmem<kTileSortRounds>)>>>(
+        kin, vin, kout, vout, nullptr, n, 0, totals, lk, tickets, status);
+    count_launch();
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(status_out, status, 4, cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  if (e != cudaSuccess) {
+    set_last_error("gs3_selftest_wait_timeout: CUDA call failed");
+    return GS3_ERR_CUDA;
+  }
+  return GS3_OK;
+}

@@ -74,8 +74,7 @@ extern "C" gs3_status gs3_depth_order_static(const uint32_t* keys, uint32_t n, u
   // four 8-bit passes over the 32-bit keys; the odd passes write the values
   // into the caller's output, so the last pass leaves the order there
   radix_sort_pairs(keys, nullptr, k0, v0, k1, order_out, n, 4, hist, scan,
-                   reinterpret_cast<cudaStream_t>(stream));
-  count_launch(4 * 5);
+                   reinterpret_cast<cudaStream_t>(stream));  // counts its own launches
   if (cudaGetLastError() != cudaSuccess) {
     set_last_error("gs3_depth_order_static: kernel launch failed");
     return GS3_ERR_CUDA;

@@ -181,6 +181,25 @@ def test_capacity_overflow_reported(gs3):
     rd2.check()
 
 
+def test_bounded_wait_gives_up(gs3):
+    """A look-back wait that can never end (its predecessor's words are never
+    written) gives up, records GS3_ERR_TIMEOUT, and the context still renders."""
+    import time
+    import torch
+    from paper_2410_11419_gb300 import render as R, _native as N
+    t0 = time.perf_counter()
+    assert N.gs3_selftest_wait_timeout(3 * 4096) == N.GS3_ERR_TIMEOUT
+    assert time.perf_counter() - t0 < 30.0
+    with pytest.raises(N.GS3Error):
+        N.gs3_selftest_wait_timeout(4096)  # one block: nothing to wait on, rejected
+    scene = synth.tiny_scene(0)
+    cam, light = synth.camera_light_pair(0, 128, 128)
+    rd = R.Renderer(R.DeviceScene(scene), 128, 128, 1 << 20)
+    rd.render(cam, light)
+    torch.cuda.synchronize()
+    rd.check()
+
+
 def test_invalid_arguments_rejected(gs3):
     from paper_2410_11419_gb300 import render as R, _native as N
     scene = synth.tiny_scene(0)
