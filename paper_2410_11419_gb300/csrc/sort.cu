@@ -479,8 +479,13 @@ __global__ void __launch_bounds__(256) k_reorder(int n, const uint32_t* __restri
   }
 }
 
-// One warp per depth rank: the lanes write the rank's (tile, rank) pairs, its
-// rectangle's tiles in row-major order, at off[r] + i.
+// One warp per kEmitRanks consecutive depth ranks: lanes 0..kEmitRanks-1 load
+// the ranks' rectangles and offsets at once; then for each rank the lanes
+// write its (tile, rank) pairs, its rectangle's tiles in row-major order, at
+// off[r] + i.  The row of pair i is floor((i + 0.5) / w) by an FP32
+// reciprocal, then moved by one where rounding left it off, so it is exact.
+constexpr int kEmitRanks = 8;
+
 __global__ void __launch_bounds__(256) k_emit(int n, uint32_t cap, const SplatRec* __restrict__ rrec,
                                               const uint32_t* __restrict__ off, uint32_t* header, int h_need,
                                               int h_pairs, uint32_t* __restrict__ tk, uint32_t* __restrict__ tv,
@@ -494,17 +499,37 @@ __global__ void __launch_bounds__(256) k_emit(int n, uint32_t cap, const SplatRe
     return;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) header[h_pairs] = need;
-  const int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-  if (r >= n) return;
-  const int4 q = rrec[r].r;
-  if (q.x < 0) return;  // culled: no pairs
-  const uint32_t w = (uint32_t)(q.z - q.x + 1);
-  const uint32_t cnt = w * (uint32_t)(q.w - q.y + 1);
-  const uint32_t base = off[r];
-  for (uint32_t i = lane; i < cnt; i += 32) {
-    const int ty = q.y + (int)(i / w), tx = q.x + (int)(i % w);
-    tk[base + i] = (uint32_t)(ty * gx + tx);
-    tv[base + i] = (uint32_t)r;
+  const int r0 = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * kEmitRanks, lane = threadIdx.x & 31;
+  if (r0 >= n) return;
+  int4 q = make_int4(-1, 0, -1, 0);  // past n: no pairs
+  uint32_t base = 0;
+  if (lane < kEmitRanks && r0 + lane < n) {
+    q = rrec[r0 + lane].r;
+    base = off[r0 + lane];
+  }
+#pragma unroll 1
+  for (int j = 0; j < kEmitRanks; ++j) {
+    const int qx = __shfl_sync(0xffffffffu, q.x, j), qy = __shfl_sync(0xffffffffu, q.y, j);
+    const int qz = __shfl_sync(0xffffffffu, q.z, j), qw = __shfl_sync(0xffffffffu, q.w, j);
+    const uint32_t b = __shfl_sync(0xffffffffu, base, j);
+    if (qx < 0) continue;  // culled: no pairs
+    const int w = qz - qx + 1;
+    const uint32_t cnt = (uint32_t)w * (uint32_t)(qw - qy + 1);
+    const float inv = 1.f / (float)w;
+    const uint32_t r = (uint32_t)(r0 + j);
+    for (uint32_t i = lane; i < cnt; i += 32) {
+      int row = (int)(((float)i + 0.5f) * inv);
+      int col = (int)i - row * w;
+      if (col < 0) {
+        --row;
+        col += w;
+      } else if (col >= w) {
+        ++row;
+        col -= w;
+      }
+      tk[b + i] = (uint32_t)((qy + row) * gx + qx + col);
+      tv[b + i] = r;
+    }
   }
 }
 
@@ -631,9 +656,11 @@ void launch_binning(const FrameArgs& f, int sp, cudaStream_t s) {
   const int h_pairs = sp ? H_PAIRS_LIGHT : H_PAIRS_CAM;
   device_exclusive_scan(at<uint32_t>(ws, b.cnt), at<uint32_t>(ws, b.off), (uint32_t)n, header + h_need,
                         at<uint32_t>(ws, b.scan_part), s);
-  k_emit<<<(int)(((size_t)n * 32 + 255) / 256), 256, 0, s>>>(n, (uint32_t)f.L->cap, at<SplatRec>(ws, b.rrec),
-                                         at<uint32_t>(ws, b.off), header, h_need, h_pairs,
-                                         at<uint32_t>(ws, b.tk[0]), at<uint32_t>(ws, b.tv[0]), f.L->gx);
+  const size_t emit_warps = ((size_t)n + kEmitRanks - 1) / kEmitRanks;
+  k_emit<<<(int)((emit_warps * 32 + 255) / 256), 256, 0, s>>>(n, (uint32_t)f.L->cap, at<SplatRec>(ws, b.rrec),
+                                                              at<uint32_t>(ws, b.off), header, h_need, h_pairs,
+                                                              at<uint32_t>(ws, b.tk[0]), at<uint32_t>(ws, b.tv[0]),
+                                                              f.L->gx);
   count_launch();
   const int passes = tile_sort_passes(f.L->ntiles);
   // sort (tile, rank) pairs on the tile bits; start from buffer 0, alternate
