@@ -34,7 +34,7 @@ sys.path.insert(0, ROOT)
 # one ncu capture of the kernel, valid only while its sources are unchanged:
 # kernel -> (bytes, SHA-256 of the concatenated sources, the summary file).
 PROFILED_TRAFFIC = {
-    "k_shadow": (276.1e6, "f249a572cbae769d5f351df6aaeb3e12e98010345187d9515dde7e1f130bb68e",
+    "k_shadow": (276.1e6, "1b36e2b8dbcc3ae4928db7bc2de7aceeacecbf546ae966bc28be0db6afcf2fe1",
                  "profiles/k_shadow_object_300k_800.md"),
 }
 TRAFFIC_SOURCES = {

@@ -444,17 +444,22 @@ __global__ void __launch_bounds__(256) k_camera(CamParams p) {
     }
     __syncthreads();
     if (!done) {
-      for (int jj = 0; jj < rc; ++jj) {
-        if (!(Gmask[jj] & wbit)) continue;
+      // two records' alphas are formed ahead of the serial update of T (the
+      // same arithmetic, in the same order, as one record at a time)
+      auto alpha_of = [&](int jj, float& alpha) -> bool {
+        if (!(Gmask[jj] & wbit)) return false;
         const float4 ga = Ga[jj], gc = Gc[jj];
         const float pw = splat_power(ga, Gb[jj], gc.x, fx, fy);
-        if (!(pw >= gc.w)) continue;
-        const float alpha = fminf(p.amax, ga.z * __expf(pw));
+        if (!(pw >= gc.w)) return false;
+        alpha = fminf(p.amax, ga.z * __expf(pw));
+        return true;
+      };
+      auto take = [&](int jj, float alpha) -> bool {
         const float Tn = T * (1.f - alpha);
         if (Tn < p.tstop) {
           done = true;
           consumed = rb - b + jj;
-          break;
+          return false;
         }
         const float w = alpha * T;
         const float4 c0 = C0[jj], c1 = C1[jj];
@@ -462,6 +467,14 @@ __global__ void __launch_bounds__(256) k_camera(CamParams p) {
         Sh += w * c0.w;
         R0 += w * c1.x; R1 += w * c1.y; R2 += w * c1.z;
         T = Tn;
+        return true;
+      };
+      for (int jj = 0; jj < rc; jj += 2) {
+        float a0 = 0.f, a1 = 0.f;
+        const bool p0 = alpha_of(jj, a0);
+        const bool p1 = jj + 1 < rc && alpha_of(jj + 1, a1);
+        if (p0 && !take(jj, a0)) break;
+        if (p1 && !take(jj + 1, a1)) break;
       }
       if (!done) consumed = rb - b + rc;
     }
