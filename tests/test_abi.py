@@ -62,3 +62,7 @@ def test_host_only_entry_points(libgs3):
     assert N.gs3_workspace_size(0, 128, 128, 10) == 0
     with pytest.raises(N.GS3Error):
         N.gs3_workspace_layout(0, 128, 128, 10)
+    # the bounded-wait self-test validates its arguments before any CUDA call
+    for bad in (0, 4096, (1 << 20) + 1):
+        with pytest.raises(N.GS3Error):
+            N.gs3_selftest_wait_timeout(bad)
