@@ -263,9 +263,10 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_radix_scatter(
 }
 
 // ---------------------------------------------------------------------------
-// The tile sort, one kernel per digit pass (decoupled look-back).  Each block
-// takes the next kSortTileItems pairs in order by a ticket, ranks them as
-// k_radix_scatter does, publishes its count of every digit, and adds up the
+// The tile and depth sorts, one kernel per digit pass (decoupled look-back).
+// Each block takes the next kSortThreads * ROUNDS items in order by a ticket
+// (4096 tile pairs, 1024 depth keys), ranks them as k_radix_scatter does,
+// publishes its count of every digit, and adds up the
 // counts of the blocks before it from their published words: a block's own
 // count (kLookAgg) or, once that block finished its look-back, the count of
 // it and of every block before it (kLookPre).  A block waits only on blocks
