@@ -394,8 +394,12 @@ gs3_status gs3_server_destroy(gs3_server *server);
  *              nothing
  * Calls no cudaMalloc, cudaFree or other allocating routine.  The first call
  * on a device, with that device current, looks up the array's device address
- * (cudaGetSymbolAddress) and caches it; make that first call before any
- * stream capture.  Every call on a device shares the one array: calls whose
+ * (cudaGetSymbolAddress) and caches it with the id of the device's CUDA
+ * context.  After a cudaDeviceReset the module may load elsewhere in the new
+ * context: the first call there sees another context id and looks the
+ * address up again.  Make the first call on a device, and the first after a
+ * reset, before any stream capture.  Every call on a device shares the one
+ * array: calls whose
  * work overlaps on the GPU (other streams, other host threads) race and must
  * be serialised by the caller.  Nothing in the array needs to start at zero:
  * each pass overwrites all scratch it reads. */

@@ -73,23 +73,35 @@ void set_last_error(const char* msg) { g_last_error = msg; }
 // caching allocator is checked against its whole segment).
 bool device_range_ok(const void* ptr, size_t bytes) {
   typedef int (*range_fn)(unsigned long long*, size_t*, unsigned long long);
-  static range_fn fn = nullptr;
-  static bool looked = false;
-  if (!looked) {
+  static const range_fn fn = [] {
     void* f = nullptr;
     cudaDriverEntryPointQueryResult q;
     if (cudaGetDriverEntryPointByVersion("cuMemGetAddressRange", &f, 12000, cudaEnableDefault, &q) ==
             cudaSuccess &&
         q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<range_fn>(f);
-    looked = true;
-  }
+      return reinterpret_cast<range_fn>(f);
+    return (range_fn) nullptr;
+  }();
   if (!fn || !ptr) return true;
   unsigned long long base = 0;
   size_t size = 0;
   if (fn(&base, &size, reinterpret_cast<unsigned long long>(ptr)) != 0) return false;  // not device memory
   const unsigned long long p = reinterpret_cast<unsigned long long>(ptr);
   return p >= base && p - base + bytes <= size;
+}
+
+int device_sm_count() {
+  static std::atomic<int> cached[kMaxDevices];
+  int d = 0;
+  if (cudaGetDevice(&d) != cudaSuccess || d < 0) return 1;
+  if (d < kMaxDevices) {
+    const int c = cached[d].load(std::memory_order_relaxed);
+    if (c > 0) return c;
+  }
+  int v = 0;
+  if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, d) != cudaSuccess || v < 1) return 1;
+  if (d < kMaxDevices) cached[d].store(v, std::memory_order_relaxed);
+  return v;
 }
 
 Workspace plan_workspace(int n, int width, int height, size_t cap) {
@@ -457,7 +469,8 @@ gs3_status gs3_render_environment(gs3_scene* scene, const gs3_camera* cam, const
                                                    plan_workspace(scene->dev.n, cam->width, cam->height,
                                                                   key_capacity).header);
     const size_t want = (n + 255) / 256;
-    const int blocks = (int)(want < 152 * 8 ? want : 152 * 8);
+    const size_t cap_blocks = (size_t)device_sm_count() * 8;
+    const int blocks = (int)(want < cap_blocks ? want : cap_blocks);
     k_env_accumulate<<<blocks, 256, 0, s>>>(out_rgb, scratch_rgb, n, weights[l], l == 0, header);
     count_launch();
   }

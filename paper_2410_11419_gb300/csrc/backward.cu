@@ -919,12 +919,11 @@ gs3_status run_backward(const FrameArgs& f, const float* dimg, void* bws, size_t
     p.light_geom = light_geom;
     p.W = L.width; p.H = L.height; p.gx = L.gx;
     p.amax = f.opts.alpha_max;
-    static bool configured = false;
-    if (!configured) {
-      cudaFuncSetAttribute(k_shadow_bwd, cudaFuncAttributePreferredSharedMemoryCarveout,
-                           (int)cudaSharedmemCarveoutMaxShared);
-      configured = true;
-    }
+    static DeviceOnce once;
+    once.run([] {
+      return cudaFuncSetAttribute(k_shadow_bwd, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                  (int)cudaSharedmemCarveoutMaxShared) == cudaSuccess;
+    });
     k_shadow_bwd<<<L.ntiles, kBThreads, 0, s>>>(p);
     count_launch();
   }

@@ -553,7 +553,7 @@ void launch_shadow_composite(const FrameArgs& f, cudaStream_t s) {
   uint32_t* kb = at<uint32_t>(ws, b.tv[1 - fin]);
   const uint32_t* header = at<uint32_t>(ws, f.L->header);
   int blocks = (int)((f.L->cap + 255) / 256);
-  if (blocks > 152 * 16) blocks = 152 * 16;
+  if (blocks > device_sm_count() * 16) blocks = device_sm_count() * 16;
   // the depth sort's four passes leave the keys in rank order in sk[1]
   k_gather_depth<<<blocks, 256, 0, s>>>(at<uint32_t>(ws, b.tv[fin]), at<uint32_t>(ws, b.sk[1]), header, dl,
                                         (uint32_t)f.L->cap);
@@ -574,11 +574,11 @@ void launch_shadow_composite(const FrameArgs& f, cudaStream_t s) {
   p.light_stop = at<uint32_t>(ws, f.L->light_stop);
   p.W = f.L->width; p.H = f.L->height; p.gx = f.L->gx;
   p.amax = f.opts.alpha_max;
-  static bool configured = false;
-  if (!configured) {
-    cudaFuncSetAttribute(k_shadow, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
-    configured = true;
-  }
+  static DeviceOnce once;
+  once.run([] {
+    return cudaFuncSetAttribute(k_shadow, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                (int)cudaSharedmemCarveoutMaxShared) == cudaSuccess;
+  });
   k_shadow<<<f.L->ntiles, kShadowThreads, 0, s>>>(p);
   count_launch();
 }

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <atomic>
+#include <mutex>
 #include <stdint.h>
 
 #include "gs3.h"
@@ -201,6 +202,30 @@ bool device_range_ok(const void* ptr, size_t bytes);
 
 // sets the message gs3_last_error returns on this thread
 void set_last_error(const char* msg);
+
+// Per-device one-time set-up (kernel attributes, constant tables): run() calls
+// fn() at most once per CUDA device until it succeeds, with that device
+// current, from any thread.  Devices beyond kMaxDevices run fn() every time.
+constexpr int kMaxDevices = 64;
+struct DeviceOnce {
+  std::mutex mu;
+  std::atomic<bool> done[kMaxDevices];
+  template <typename F>
+  bool run(F&& fn) {
+    int d = 0;
+    if (cudaGetDevice(&d) != cudaSuccess || d < 0 || d >= kMaxDevices) return fn();
+    if (done[d].load(std::memory_order_acquire)) return true;
+    std::lock_guard<std::mutex> lock(mu);
+    if (done[d].load(std::memory_order_relaxed)) return true;
+    const bool ok = fn();
+    if (ok) done[d].store(true, std::memory_order_release);
+    return ok;
+  }
+};
+
+// Streaming multiprocessors of the current device (cudaDevAttrMultiProcessorCount),
+// looked up once per device; grid caps are multiples of it.
+int device_sm_count();
 
 // host-side count of kernel launches (reported by gs3_kernel_launches)
 extern std::atomic<uint64_t> g_launches;

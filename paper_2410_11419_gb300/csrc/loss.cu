@@ -124,8 +124,9 @@ size_t loss_scratch_bytes(int W, int H) {
 
 gs3_status run_loss(const float* img, const float* tgt, int W, int H, float lambda, float* loss, float* dimg,
                     void* scratch, cudaStream_t s) {
-  static bool init = false;
-  if (!init) {
+  // the window lives in constant memory, one copy per device
+  static DeviceOnce once;
+  const bool ready = once.run([] {
     float g[kWin], sum = 0.f;
     for (int k = 0; k < kWin; ++k) {
       const float d = (float)(k - kHalf);
@@ -133,9 +134,9 @@ gs3_status run_loss(const float* img, const float* tgt, int W, int H, float lamb
       sum += g[k];
     }
     for (int k = 0; k < kWin; ++k) g[k] /= sum;
-    if (cudaMemcpyToSymbol(c_gauss, g, sizeof(g)) != cudaSuccess) return GS3_ERR_CUDA;
-    init = true;
-  }
+    return cudaMemcpyToSymbol(c_gauss, g, sizeof(g)) == cudaSuccess;
+  });
+  if (!ready) return GS3_ERR_CUDA;
   const size_t plane = (size_t)W * H;
   float* maps = static_cast<float*>(scratch);
   float* tmp = maps + 15 * plane;

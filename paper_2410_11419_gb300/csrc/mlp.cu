@@ -170,11 +170,10 @@ __global__ void __launch_bounds__(256) k_mlp(MlpParams p) {
 template <int WIDTH>
 void launch_width(const MlpParams& p, cudaStream_t s) {
   const size_t sm = (size_t)(128 * kHPad + 128 * (WIDTH + 4)) * sizeof(float);
-  static bool configured = false;
-  if (!configured) {
-    cudaFuncSetAttribute(k_mlp<WIDTH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    configured = true;
-  }
+  static DeviceOnce once;
+  once.run([sm] {
+    return cudaFuncSetAttribute(k_mlp<WIDTH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) == cudaSuccess;
+  });
   k_mlp<WIDTH><<<(p.n + kRows - 1) / kRows, 256, sm, s>>>(p);
   count_launch();
 }

@@ -556,9 +556,7 @@ void launch_mlp_tc(const FrameArgs& f, const unsigned char* const blobs[2], cuda
     const size_t smem = tc_smem_bytes(m, eb);
     auto kern = eb == 2 ? k_mlp_tc<2> : k_mlp_tc<1>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    int dev = 0, nsm = 148;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const int nsm = device_sm_count();
     const int ntiles = (f.sc.n + kTcRows - 1) / kTcRows;
     const int grid = ntiles < nsm ? ntiles : nsm;
     kern<<<grid, kTcThreads, smem, s>>>(p);

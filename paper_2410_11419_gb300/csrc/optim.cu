@@ -30,7 +30,8 @@ void launch_adam(float* p, const float* g, float* m, float* v, size_t n, float l
                  int step, float lo, cudaStream_t s) {
   const double c1 = 1.0 - pow((double)b1, (double)step), c2 = 1.0 - pow((double)b2, (double)step);
   const size_t want = (n + 255) / 256;
-  const int blocks = (int)(want < 152 * 16 ? want : 152 * 16);
+  const size_t cap_blocks = (size_t)device_sm_count() * 16;
+  const int blocks = (int)(want < cap_blocks ? want : cap_blocks);
   k_adam<<<blocks, 256, 0, s>>>(p, g, m, v, n, lr, b1, b2, eps, (float)c1, (float)c2, lo);
   count_launch();
 }

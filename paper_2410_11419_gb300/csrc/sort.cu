@@ -549,12 +549,11 @@ __global__ void __launch_bounds__(256) k_ranges(const uint32_t* __restrict__ key
 void radix_sort(const uint32_t* kin, const uint32_t* vin, uint32_t* k0, uint32_t* v0, uint32_t* k1,
                 uint32_t* v1, const uint32_t* n_ptr, uint32_t n_fixed, int nblocks, int passes,
                 uint32_t* hist, uint32_t* scan_part, cudaStream_t s) {
-  static bool configured = false;
-  if (!configured) {
-    cudaFuncSetAttribute(k_radix_scatter<kSortRounds>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)sizeof(ScatterSmem<kSortRounds>));
-    configured = true;
-  }
+  static DeviceOnce once;
+  once.run([] {
+    return cudaFuncSetAttribute(k_radix_scatter<kSortRounds>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)sizeof(ScatterSmem<kSortRounds>)) == cudaSuccess;
+  });
   const uint32_t* ki = kin;
   const uint32_t* vi = vin;
   for (int p = 0; p < passes; ++p) {
@@ -579,19 +578,19 @@ template <int ROUNDS, int PASSES>
 void onesweep_sort(const uint32_t* kin, const uint32_t* vin, uint32_t* k0, uint32_t* v0, uint32_t* k1,
                    uint32_t* v1, const uint32_t* n_ptr, uint32_t n_fixed, int nblocks, int passes,
                    unsigned char* look_region, uint32_t* header, cudaStream_t s) {
-  static bool configured = false;
-  if (!configured) {
-    cudaFuncSetAttribute(k_onesweep<ROUNDS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)sizeof(OnesweepSmem<ROUNDS>));
-    configured = true;
-  }
+  static DeviceOnce once;
+  once.run([] {
+    return cudaFuncSetAttribute(k_onesweep<ROUNDS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)sizeof(OnesweepSmem<ROUNDS>)) == cudaSuccess;
+  });
   unsigned long long* look = reinterpret_cast<unsigned long long*>(look_region);
   uint32_t* tickets = reinterpret_cast<uint32_t*>(look + (size_t)PASSES * 256 * (size_t)nblocks);
   uint32_t* totals = tickets + PASSES;
   cudaMemsetAsync(look_region, 0, onesweep_bytes(nblocks, PASSES), s);
-  int tb = n_ptr ? 152 * 4 : (int)((n_fixed + 1023) / 1024);
+  const int tb_cap = device_sm_count() * 4;
+  int tb = n_ptr ? tb_cap : (int)((n_fixed + 1023) / 1024);
   if (tb < 1) tb = 1;
-  if (tb > 152 * 4) tb = 152 * 4;
+  if (tb > tb_cap) tb = tb_cap;
   k_digit_totals<PASSES><<<tb, kSortThreads, 0, s>>>(kin, n_ptr, n_fixed, passes, totals);
   const uint32_t* ki = kin;
   const uint32_t* vi = vin;
@@ -671,7 +670,7 @@ void launch_binning(const FrameArgs& f, int sp, cudaStream_t s) {
   const int fin = passes & 1;  // 1 pass ends in buffer 1, 2 passes in buffer 0
   const uint32_t* keys = at<uint32_t>(ws, b.tk[fin]);
   int blocks = (int)((f.L->cap + 1 + 255) / 256);
-  if (blocks > 152 * 16) blocks = 152 * 16;
+  if (blocks > device_sm_count() * 16) blocks = device_sm_count() * 16;
   k_ranges<<<blocks, 256, 0, s>>>(keys, header, h_pairs, at<uint32_t>(ws, b.tile_start), f.L->ntiles,
                                   (uint32_t)f.L->cap);
   count_launch();

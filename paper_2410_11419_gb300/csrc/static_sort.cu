@@ -19,10 +19,40 @@ constexpr size_t kStaticWords = 3ull * kStaticMaxKeys + kStaticHistWords + kStat
 
 static __device__ __align__(256) uint32_t g_static_scratch[kStaticWords];
 
-constexpr int kMaxDevices = 64;
+// The array's device address per device, with the id of the CUDA context it
+// was looked up in: a cudaDeviceReset destroys that context, and the module
+// (with the array) may load at another address in the next one.
 std::mutex g_mu;
 uint32_t* g_scratch_addr[kMaxDevices] = {};
+unsigned long long g_scratch_ctx[kMaxDevices] = {};
 
+// Id of the calling thread's current CUDA context (0 when it cannot be read),
+// through the driver entry points cuCtxGetCurrent and cuCtxGetId.
+unsigned long long current_context_id() {
+  typedef int (*get_current_fn)(void**);
+  typedef int (*get_id_fn)(void*, unsigned long long*);
+  struct Fns {
+    get_current_fn cur = nullptr;
+    get_id_fn id = nullptr;
+  };
+  static const Fns fns = [] {
+    Fns f;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      f.cur = reinterpret_cast<get_current_fn>(p);
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      f.id = reinterpret_cast<get_id_fn>(p);
+    return f;
+  }();
+  if (!fns.cur || !fns.id) return 0;
+  void* ctx = nullptr;
+  unsigned long long id = 0;
+  if (fns.cur(&ctx) != 0 || !ctx || fns.id(ctx, &id) != 0) return 0;
+  return id;
+}
 
 }  // namespace
 }  // namespace gs3
@@ -47,22 +77,27 @@ extern "C" gs3_status gs3_depth_order_static(const uint32_t* keys, uint32_t n, u
     return GS3_ERR_INVALID_ARG;
   }
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+  // cudaSetDevice makes the device's primary context current on this thread,
+  // so that its id can be compared with the one the address was found in
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices || cudaSetDevice(dev) != cudaSuccess) {
     set_last_error("gs3_depth_order_static: no usable current device");
     return GS3_ERR_CUDA;
   }
   uint32_t* base = nullptr;
   {
-    // once per device, with that device current: the host-side symbol is only
-    // a stand-in, the kernels need the device address of the array
+    // once per device and context, with that device current: the host-side
+    // symbol is only a stand-in, the kernels need the array's device address
     std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_scratch_addr[dev]) {
+    const unsigned long long ctx = current_context_id();
+    if (!g_scratch_addr[dev] || ctx == 0 || ctx != g_scratch_ctx[dev]) {
       void* p = nullptr;
       if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess || !p) {
+        g_scratch_addr[dev] = nullptr;
         set_last_error("gs3_depth_order_static: cudaGetSymbolAddress of the scratch array failed");
         return GS3_ERR_CUDA;
       }
       g_scratch_addr[dev] = static_cast<uint32_t*>(p);
+      g_scratch_ctx[dev] = current_context_id();
     }
     base = g_scratch_addr[dev];
   }
@@ -73,6 +108,9 @@ extern "C" gs3_status gs3_depth_order_static(const uint32_t* keys, uint32_t n, u
   uint32_t* scan = hist + kStaticHistWords;
   // four 8-bit passes over the 32-bit keys; the odd passes write the values
   // into the caller's output, so the last pass leaves the order there
+  // an error left by an earlier, unrelated call on this thread is not this
+  // call's: clear it so that the check below sees only these launches
+  (void)cudaGetLastError();
   radix_sort_pairs(keys, nullptr, k0, v0, k1, order_out, n, 4, hist, scan,
                    reinterpret_cast<cudaStream_t>(stream));  // counts its own launches
   if (cudaGetLastError() != cudaSuccess) {

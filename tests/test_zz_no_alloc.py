@@ -56,3 +56,25 @@ def test_static_depth_order_limits(gs3):
     assert e.value.status == N.GS3_ERR_INVALID_ARG
     assert "GS3_STATIC_SORT_MAX_KEYS" in str(e.value)
     N.gs3_depth_order_static(keys, 0, out, stream)  # empty input is a no-op
+
+
+def test_static_depth_order_allocates_nothing(gs3):
+    """After a first call (which may load the library's device code, and with
+    it the fixed array), a call at the size limit leaves the device's free
+    memory exactly as it was."""
+    import torch
+    from paper_2410_11419_gb300 import _native as N
+    stream = torch.cuda.current_stream().cuda_stream
+    n = N.GS3_STATIC_SORT_MAX_KEYS
+    rng = np.random.default_rng(1)
+    host = rng.integers(0, 1 << 31, n, dtype=np.uint32)
+    keys = torch.from_numpy(host.view(np.int32)).cuda()
+    out = torch.empty(n, dtype=torch.int32, device="cuda")
+    N.gs3_depth_order_static(keys, n, out, stream)
+    torch.cuda.synchronize()
+    free_before, _ = torch.cuda.mem_get_info()
+    N.gs3_depth_order_static(keys, n, out, stream)
+    torch.cuda.synchronize()
+    free_after, _ = torch.cuda.mem_get_info()
+    assert free_after == free_before
+    np.testing.assert_array_equal(out.cpu().numpy(), np.argsort(host, kind="stable"))
