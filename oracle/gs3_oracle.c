@@ -114,7 +114,36 @@ typedef struct {
     int threads;
     double margin_alpha, margin_tstop;
     int crop[4]; /* x0, y0, x1, y1 (exclusive) pixel window of both composites; all 0 = full */
+    /* Testing the bounds of decision-ambiguous cases.  A decision is named by
+     * the code (kind << 60) | (pixel << 32) | list position, with kind 0 the
+     * alpha test of a shadow-ray entry, 1 the alpha test of a camera-ray
+     * entry, 2 the camera ray's stop test after an entry; pixel = y W + x and
+     * the position is the entry's index in that splat's sorted list.
+     *   flip:       nflip codes, ascending: these ambiguous decisions are taken
+     *               on their other side (as an FP32 evaluation may take them)
+     *   record_amb: 1 = list every ambiguous decision in the frame's amb */
+    const int64_t *flip;
+    int nflip;
+    int record_amb;
 } go_opts;
+
+enum { AMB_SHADOW_ALPHA = 0, AMB_CAMERA_ALPHA = 1, AMB_CAMERA_STOP = 2 };
+
+static int64_t amb_code(int kind, size_t pixel, size_t pos)
+{
+    return ((int64_t)kind << 60) | ((int64_t)pixel << 32) | (int64_t)pos;
+}
+
+/* true when the options ask for decision `code` to be flipped */
+static int flipped(const go_opts *o, int64_t code)
+{
+    int lo = 0, hi = o->nflip;
+    while (lo < hi) {
+        int mid = (lo + hi) / 2;
+        if (o->flip[mid] < code) lo = mid + 1; else hi = mid;
+    }
+    return lo < o->nflip && o->flip[lo] == code;
+}
 
 typedef struct {
     int n, width, height, gx, gy, ntiles;
@@ -145,7 +174,25 @@ typedef struct {
     int64_t amb_shadow, amb_camera;
     int64_t camera_pass; /* (pixel, Gaussian) pairs composited by the camera rays */
     double t_prep, t_bin, t_shadow, t_mlp, t_camera; /* wall seconds per stage */
+    int64_t *amb;  /* with record_amb: the codes of every ambiguous decision (unordered) */
+    int64_t namb, amb_cap;
 } go_frame;
+
+/* appends an ambiguous decision to the frame's record (any thread) */
+static void record_amb(go_frame *f, const go_opts *o, int64_t code)
+{
+    if (!o->record_amb) return;
+#ifdef _OPENMP
+#pragma omp critical(go_amb_record)
+#endif
+    {
+        if (f->namb == f->amb_cap) {
+            f->amb_cap = f->amb_cap ? 2 * f->amb_cap : 1024;
+            f->amb = realloc(f->amb, sizeof(int64_t) * (size_t)f->amb_cap);
+        }
+        f->amb[f->namb++] = code;
+    }
+}
 
 /* pixel window of the composites (the whole image unless a crop is set) */
 static void window(const go_opts *o, int W, int H, int *x0, int *y0, int *x1, int *y1)
@@ -623,7 +670,7 @@ static void shadow_splat(go_frame *f, const go_opts *o)
         double *num = acc + (size_t)tid * n * 4, *den = num + n, *bnum = den + n, *bden = bnum + n;
         size_t cap = 1024;
         double *al = malloc(sizeof(double) * cap), *be = malloc(sizeof(double) * cap);
-        double *A = malloc(sizeof(double) * (cap + 1));
+        double *A = malloc(sizeof(double) * (cap + 1)), *Q = malloc(sizeof(double) * (cap + 1));
         float *d = malloc(sizeof(float) * cap);
         uint32_t *gi = malloc(sizeof(uint32_t) * cap);
         int *amb = malloc(sizeof(int) * cap);
@@ -642,6 +689,7 @@ static void shadow_splat(go_frame *f, const go_opts *o)
                     cap = L;
                     al = realloc(al, sizeof(double) * cap); be = realloc(be, sizeof(double) * cap);
                     A = realloc(A, sizeof(double) * (cap + 1)); d = realloc(d, sizeof(float) * cap);
+                    Q = realloc(Q, sizeof(double) * (cap + 1));
                     gi = realloc(gi, sizeof(uint32_t) * cap); amb = realloc(amb, sizeof(int) * cap);
                     pass = realloc(pass, sizeof(int) * cap);
                 }
@@ -661,12 +709,26 @@ static void shadow_splat(go_frame *f, const go_opts *o)
                      * no test on its sign (Eq. 2 has none) */
                     pass[i] = a >= o->alpha_min;
                     amb[i] = fabs(a - o->alpha_min) <= o->margin_alpha * o->alpha_min;
+                    if (amb[i]) {
+                        ambs++;
+                        const int64_t code = amb_code(AMB_SHADOW_ALPHA, (size_t)py * W + px, b + i);
+                        record_amb(f, o, code);
+                        if (o->nflip && flipped(o, code)) pass[i] = !pass[i];
+                    }
                     evals++;
                     passes += pass[i];
                 }
-                /* A[i] = product of (1 - alpha_k) over passing k < i (Eq. 2) */
+                /* A[i] = product of (1 - alpha_k) over passing k < i (Eq. 2);
+                 * Q[i] = product of 1 / (1 - alpha_k) over ambiguous k < i: whichever
+                 * subset of those an FP32 evaluation takes the other way (a removed
+                 * factor divides A by 1 - alpha, an added one multiplies it by
+                 * 1 - alpha), A[i] moves by at most A[i] (Q[i] - 1) */
                 A[0] = 1.0;
-                for (size_t i = 0; i < L; ++i) A[i + 1] = A[i] * (pass[i] ? 1.0 - al[i] : 1.0);
+                Q[0] = 1.0;
+                for (size_t i = 0; i < L; ++i) {
+                    A[i + 1] = A[i] * (pass[i] ? 1.0 - al[i] : 1.0);
+                    Q[i + 1] = Q[i] * (amb[i] ? 1.0 / (1.0 - al[i]) : 1.0);
+                }
                 /* receiver j gets T_m(j) = A[K], K = #entries with d_k < d_j - bias */
                 size_t K = 0;
                 for (size_t j = 0; j < L; ++j) {
@@ -677,29 +739,17 @@ static void shadow_splat(go_frame *f, const go_opts *o)
                     if (pass[j]) {
                         num[gi[j]] += be[j] * Tm;
                         den[gi[j]] += be[j];
+                        /* occluder side: straddling decisions in front of it */
+                        if (Q[K] > 1.0) bnum[gi[j]] += be[j] * Tm * (Q[K] - 1.0);
                     }
-                    if (amb[j]) { /* receiver side of a straddling decision */
-                        bnum[gi[j]] += be[j] * Tm;
+                    if (amb[j]) { /* receiver side: its own term may appear or vanish */
+                        bnum[gi[j]] += be[j] * Tm * Q[K];
                         bden[gi[j]] += be[j];
-                    }
-                }
-                /* occluder side of straddling decisions: every receiver behind it */
-                for (size_t k = 0; k < L; ++k) {
-                    if (!amb[k]) continue;
-                    ambs++;
-                    double fac = al[k] / (1.0 - al[k]);
-                    size_t KK = 0;
-                    for (size_t j = 0; j < L; ++j) {
-                        if (!pass[j] && !amb[j]) continue;
-                        float thr = d[j] - o->shadow_bias;
-                        while (KK < L && d[KK] < thr) ++KK;
-                        if (!(d[k] < thr)) continue;
-                        bnum[gi[j]] += be[j] * A[KK] * fac;
                     }
                 }
             }
         }
-        free(al); free(be); free(A); free(d); free(gi); free(amb); free(pass);
+        free(al); free(be); free(A); free(Q); free(d); free(gi); free(amb); free(pass);
     }
     f->shadow_evals = evals;
     f->shadow_pass = passes;
@@ -749,9 +799,10 @@ static void camera_composite(go_frame *f, const go_opts *o)
             double cxp = px + 0.5, cyp = py + 0.5;
             double T = 1.0, S[3] = {0, 0, 0}, Sh = 0.0, R[3] = {0, 0, 0};
             double bS[3] = {0, 0, 0}, bSh = 0.0, bR[3] = {0, 0, 0};
-            /* absolute weight mass after an ambiguous decision, accumulated lazily:
-             * bound factor times the |contributions| that follow it */
-            double pend = 0.0; /* sum of alpha/(1-alpha) of earlier ambiguous entries */
+            /* P = product of 1 / (1 - alpha) over the earlier ambiguous alpha tests:
+             * whichever subset of them an FP32 evaluation takes the other way, the
+             * transmittance T' it carries lies in [T / P, T P] */
+            double P = 1.0;
             double cmax[7] = {0, 0, 0, 0, 0, 0, 0};
             for (uint32_t i = b; i < e; ++i) {
                 uint32_t g = f->list[0][i];
@@ -772,37 +823,50 @@ static void camera_composite(go_frame *f, const go_opts *o)
                 double a = f->opacity[g] * exp(power); /* power <= 0: the conic is positive definite */
                 if (a > o->alpha_max) a = o->alpha_max;
                 int amb = fabs(a - o->alpha_min) <= o->margin_alpha * o->alpha_min;
+                int take = a >= o->alpha_min;
                 if (amb) {
+                    /* its own term may appear or vanish, at a transmittance up to T P */
                     ambs++;
-                    double w = a * T;
+                    double w = a * T * P;
                     for (int c = 0; c < 3; ++c) {
                         bS[c] += w * fabs(f->shade[3 * g + c]);
                         bR[c] += w * fabs(f->res[3 * g + c]);
                     }
                     bSh += w * fabs(f->Tp[g]);
-                    pend += a / (1.0 - a);
+                    P /= 1.0 - a;
+                    const int64_t code = amb_code(AMB_CAMERA_ALPHA, (size_t)py * W + px, i);
+                    record_amb(f, o, code);
+                    if (o->nflip && flipped(o, code)) take = !take;
                 }
-                if (a < o->alpha_min) continue;
+                if (!take) continue;
                 double Tn = T * (1.0 - a);
-                if (fabs(Tn - o->t_stop) <= o->margin_tstop * o->t_stop) {
+                int stop = Tn < o->t_stop;
+                /* the stop test straddles when Tn lies within the margin of t_stop, or
+                 * when earlier straddling alpha tests can carry it across */
+                if (Tn * P >= o->t_stop * (1.0 - o->margin_tstop) && Tn <= P * o->t_stop * (1.0 + o->margin_tstop)) {
+                    /* the ray may stop here or go on: everything from here on, at most
+                     * the remaining transmittance T P times the largest colour */
                     ambs++;
-                    for (int c = 0; c < 3; ++c) { bS[c] += T * cmax[c]; bR[c] += T * cmax[4 + c]; }
-                    bSh += T * cmax[3];
+                    for (int c = 0; c < 3; ++c) { bS[c] += T * P * cmax[c]; bR[c] += T * P * cmax[4 + c]; }
+                    bSh += T * P * cmax[3];
+                    const int64_t code = amb_code(AMB_CAMERA_STOP, (size_t)py * W + px, i);
+                    record_amb(f, o, code);
+                    if (o->nflip && flipped(o, code)) stop = !stop;
                 }
-                if (Tn < o->t_stop) { consumed = (int32_t)(i - b); break; }
+                if (stop) { consumed = (int32_t)(i - b); break; }
                 cpass++;
                 double w = a * T;
                 for (int c = 0; c < 3; ++c) {
                     S[c] += w * f->shade[3 * g + c];
                     R[c] += w * f->res[3 * g + c];
-                    if (pend > 0.0) {
-                        bS[c] += pend * w * fabs(f->shade[3 * g + c]);
-                        bR[c] += pend * w * fabs(f->res[3 * g + c]);
+                    if (P > 1.0) { /* the same term at a transmittance in [T / P, T P] */
+                        bS[c] += (P - 1.0) * w * fabs(f->shade[3 * g + c]);
+                        bR[c] += (P - 1.0) * w * fabs(f->res[3 * g + c]);
                     }
                 }
                 Sh += w * f->Tp[g];
-                if (pend > 0.0) bSh += pend * w * fabs(f->Tp[g]);
-                bSh += w * f->Tp_bound[g]; /* propagated shadow-value bound */
+                if (P > 1.0) bSh += (P - 1.0) * w * fabs(f->Tp[g]);
+                bSh += P * w * f->Tp_bound[g]; /* propagated shadow-value bound */
                 T = Tn;
             }
             size_t p = (size_t)py * W + px;
@@ -948,7 +1012,7 @@ void go_frame_free(go_frame *f)
     }
     free(f->opacity); free(f->shade); free(f->T); free(f->T_bound); free(f->Tp);
     free(f->Tp_bound); free(f->res); free(f->img); free(f->img_bound); free(f->final_T);
-    free(f->n_contrib); free(f->S); free(f->Sh); free(f->Rimg);
+    free(f->n_contrib); free(f->S); free(f->Sh); free(f->Rimg); free(f->amb);
     free(f);
 }
 

@@ -64,7 +64,8 @@ class _Opts(C.Structure):
                 ("t_stop", C.c_float), ("target", C.c_float * 3), ("falloff", C.c_int),
                 ("tile", C.c_int), ("ablate", C.c_int), ("threads", C.c_int),
                 ("margin_alpha", C.c_double), ("margin_tstop", C.c_double),
-                ("crop", C.c_int * 4)]
+                ("crop", C.c_int * 4), ("flip", C.POINTER(C.c_int64)), ("nflip", C.c_int),
+                ("record_amb", C.c_int)]
 
 
 _U32 = C.POINTER(C.c_uint32)
@@ -85,7 +86,21 @@ class _Frame(C.Structure):
                 ("shadow_evals", C.c_int64), ("shadow_pass", C.c_int64),
                 ("camera_evals", C.c_int64), ("amb_shadow", C.c_int64),
                 ("amb_camera", C.c_int64), ("camera_pass", C.c_int64), ("t_prep", C.c_double), ("t_bin", C.c_double),
-                ("t_shadow", C.c_double), ("t_mlp", C.c_double), ("t_camera", C.c_double)]
+                ("t_shadow", C.c_double), ("t_mlp", C.c_double), ("t_camera", C.c_double),
+                ("amb", C.POINTER(C.c_int64)), ("namb", C.c_int64), ("amb_cap", C.c_int64)]
+
+# kinds of decision-ambiguous cases (the top bits of a decision code)
+AMB_SHADOW_ALPHA, AMB_CAMERA_ALPHA, AMB_CAMERA_STOP = 0, 1, 2
+
+
+def amb_code(kind: int, pixel: int, pos: int) -> int:
+    return (kind << 60) | (pixel << 32) | pos
+
+
+def amb_split(codes: np.ndarray):
+    """(kind, pixel, list position) of decision codes."""
+    codes = np.asarray(codes, dtype=np.int64)
+    return codes >> 60, (codes >> 32) & ((1 << 28) - 1), codes & 0xFFFFFFFF
 
 
 _lib = None
@@ -139,15 +154,24 @@ class Opts:
     margin_alpha: float = 1e-5
     margin_tstop: float = 1e-4
     crop: tuple = (0, 0, 0, 0)
+    flip: tuple = ()       # decision codes to take on their other side (testing the bounds)
+    record_amb: int = 0    # 1: return the codes of every ambiguous decision as "amb"
 
     def c(self) -> _Opts:
         o = _Opts()
         for f, _ in _Opts._fields_:
+            if f == "nflip":
+                continue
             v = getattr(self, f)
             if f == "target":
                 o.target = (C.c_float * 3)(*v)
             elif f == "crop":
                 o.crop = (C.c_int * 4)(*v)
+            elif f == "flip":
+                codes = np.unique(np.asarray(v, dtype=np.int64))
+                self._flip_keep = np.ascontiguousarray(codes)
+                o.flip = self._flip_keep.ctypes.data_as(C.POINTER(C.c_int64)) if codes.size else None
+                o.nflip = int(codes.size)
             else:
                 setattr(o, f, v)
         return o
@@ -246,6 +270,7 @@ def render(scene, cam, light, opts: Opts | None = None) -> dict:
         amb_shadow=f.amb_shadow, amb_camera=f.amb_camera, camera_pass=f.camera_pass,
         times={"prep": f.t_prep, "bin": f.t_bin, "shadow": f.t_shadow, "mlp": f.t_mlp,
                "camera": f.t_camera},
+        amb=np.sort(_arr(f.amb, int(f.namb), np.int64)),
     )
     lib().go_frame_free(fp)
     return out

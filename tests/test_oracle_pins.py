@@ -4,6 +4,7 @@ routines (CPU only).  Each test names the paper passage it fixes.
 A plausible slip in the oracle -- a dropped term, a wrong sign or index, a
 transposed operand -- fails at least one of these.
 """
+import dataclasses
 import math
 import os
 
@@ -530,3 +531,103 @@ def test_ablation_switches(oracle, small_frame):
     f4 = oracle.render(sc, cam, light, oracle.Opts(ablate=4))
     assert np.all(f4["res"] == 0.0)
     np.testing.assert_allclose(f4["img"], f4["S"] * f4["Sh"][..., None], rtol=1e-13)
+
+
+# -- decision-ambiguous cases (the alpha rules of Eq. 2; the camera stop) -------
+#
+# An FP32 path may take a threshold test (alpha vs 1/255, the camera ray's
+# stop) the other way when the FP64 operand lies within a small margin of the
+# cutoff.  The oracle turns every such decision into a bound on each output it
+# can move (T_bound, Tp_bound, img_bound), and the GPU parity tests add those
+# bounds to their tolerance.  These tests force the decisions onto their other
+# side in the oracle itself and check that the bounds cover what moves, and
+# that they are attained (not inflated).
+
+_BOUNDED = (("T", "T_bound"), ("Tp", "Tp_bound"), ("img", "img_bound"))
+
+
+def _moves_within(base, fr):
+    """Largest |change| / bound per output; a change needs no bound when it is
+    at the rounding level of the FP64 values (the threads' summation order)."""
+    worst = {}
+    for nm, bn in _BOUNDED:
+        d = np.abs(fr[nm] - base[nm])
+        slack = 1e-13 * np.maximum(np.abs(fr[nm]), np.abs(base[nm])) + 1e-300
+        assert np.all(d <= base[bn] * (1 + 1e-9) + slack), (
+            f"{nm}: change {d.max():.3e} beyond its bound at {np.unravel_index(np.argmax(d - base[bn]), d.shape)}")
+        moved = d > slack
+        worst[nm] = float((d[moved] / base[bn][moved]).max()) if moved.any() else 0.0
+    return worst
+
+
+def _flip_each(oracle, sc, cam, light, opts, every=1):
+    base = oracle.render(sc, cam, light, dataclasses.replace(opts, record_amb=1))
+    codes = base["amb"]
+    kinds = oracle.amb_split(codes)[0]
+    worst = {nm: 0.0 for nm, _ in _BOUNDED}
+    for c in codes[::every]:
+        w = _moves_within(base, oracle.render(sc, cam, light, dataclasses.replace(opts, flip=(int(c),))))
+        worst = {k: max(worst[k], w[k]) for k in worst}
+    allw = _moves_within(base, oracle.render(sc, cam, light, dataclasses.replace(opts, flip=tuple(codes))))
+    return kinds, worst, allw
+
+
+def test_ambiguity_bounds_cover_flips_small(oracle, small_frame):
+    """300 Gaussians, margins widened so that hundreds of decisions straddle
+    (and a camera stop at transmittance 0.1, which this sparse ball reaches):
+    every one taken the other way alone, then all of them together, moves
+    T, T' and the image by no more than the bounds of the unflipped frame."""
+    sc, cam, light, _, _ = small_frame
+    opts = oracle.Opts(margin_alpha=0.05, margin_tstop=0.3, t_stop=0.1)
+    kinds, worst, allw = _flip_each(oracle, sc, cam, light, opts)
+    counts = np.bincount(kinds, minlength=3)
+    assert counts[oracle.AMB_SHADOW_ALPHA] > 50 and counts[oracle.AMB_CAMERA_ALPHA] > 50
+    assert counts[oracle.AMB_CAMERA_STOP] > 5
+    # the bounds are attained: a single straddling receiver behind an opaque
+    # occluder moves T by exactly its bound; T' carries a factor 2 of safety
+    assert worst["T"] > 0.99 and worst["img"] > 0.9 and worst["Tp"] > 0.45
+    assert allw["T"] > 0.5 and allw["img"] > 0.5
+
+
+def test_ambiguity_bounds_cover_flips_shell_20k(oracle):
+    """20k-Gaussian shell at 256^2 with the margins the parity tests use: a
+    quarter of the straddling decisions (every kind) flipped one at a time, then
+    all of them at once."""
+    sc = synth.object_scene(2, n=20000)
+    cam, light = synth.camera_light_pair(7, 256, 256)
+    kinds, worst, allw = _flip_each(oracle, sc, cam, light, oracle.Opts(), every=4)
+    assert np.all(np.bincount(kinds, minlength=3) > 10)
+    assert worst["T"] > 0.5 and worst["img"] > 0.25
+
+
+def test_ambiguity_bounds_vanish_without_margins(oracle, small_frame):
+    """With zero margins no decision straddles and every bound is exactly 0."""
+    sc, cam, light, _, _ = small_frame
+    fr = oracle.render(sc, cam, light, oracle.Opts(margin_alpha=0.0, margin_tstop=0.0, record_amb=1))
+    assert fr["amb"].size == 0
+    for _, bn in _BOUNDED:
+        assert np.all(fr[bn] == 0.0)
+
+
+# Share of image values whose bound exceeds the parity tolerance
+# 1e-4 |o| + 1e-6 on the 300k-Gaussian object frame at 800^2 (pair 0): 0.28 %
+# measured, every one of them at a pixel where a camera-side decision
+# straddles (653 alpha tests, 1336 stop tests in the frame).  The cap leaves
+# room for other views; a bug that inflates the bounds exceeds it.
+AMBIGUOUS_PIXEL_CAP = 0.004
+
+
+@pytest.mark.slow
+def test_ambiguous_share_full_object_frame(oracle):
+    sc = synth.object_scene(0)
+    cam, light = synth.camera_light_pair(0, 800, 800)
+    fr = oracle.render(sc, cam, light, oracle.Opts(record_amb=1))
+    over = fr["img_bound"] > 1e-4 * np.abs(fr["img"]) + 1e-6
+    share = over.any(-1).mean()
+    assert 0.0 < share < AMBIGUOUS_PIXEL_CAP
+    kinds, pix, _ = oracle.amb_split(fr["amb"])
+    cam_side = np.zeros(fr["img"].shape[0] * fr["img"].shape[1], bool)
+    cam_side[pix[kinds != oracle.AMB_SHADOW_ALPHA]] = True
+    # shadow-side straddles alone never push a pixel over the tolerance here
+    assert not np.any(over.any(-1).reshape(-1) & ~cam_side)
+    assert fr["T_bound"].max() < 1e-4
