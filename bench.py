@@ -5,15 +5,20 @@ Workload (default): 300,000-Gaussian object scene (noisy sphere shell plus
 10 % interior fluff), K = 8 lobes per Gaussian, both MLPs 3x128, 800x800
 image; one step = one full relit frame (shading, shadow splat, Phi, Psi,
 camera splat) for the next of 100 seeded camera / point-light pairs on the
-radius-3 sphere.  Inputs are synthetic and resident in HBM; L2 is flushed
-(256 MB write) between steps, outside the timed events.
+radius-3 sphere.  Inputs are synthetic and resident in HBM and larger than
+L2 (149 MB of scene, ~0.7 GB of intermediates per frame); no timed arm flushes
+L2 between frames.  The headline is the served arm (BF16 MLPs, continuous
+batching, at least 100 frames); single frames, the FP32 plain form and the
+differentiation form are timed beside it.
 
 Prints ONE JSON line (rank 0).  Under torchrun every rank renders its own
 frames (independent replicas, no collective on the data path) and the
 reported value is all frames / the slowest rank's time.
 
---impl reference times the FP64 CPU oracle on the host cores instead (a
-bounded window of each frame, scaled to a whole frame).
+--impl reference times the FP64 CPU oracle on the host cores instead: whole
+frames, each run as four consecutive steps (shading, projections and lists;
+the shadow rays of the upper, then the lower half of the light view; the
+shadow average, Phi, Psi and the camera composite).
 """
 from __future__ import annotations
 
@@ -81,7 +86,12 @@ def parse():
     ap.add_argument("--profile-backward", action="store_true",
                     help="with --profile-frames and --mlp fp32: also run each frame's backward")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-window", type=int, default=96, help="oracle window edge (pixels)")
+    ap.add_argument("--cpu-frames", type=int, default=1,
+                    help="whole oracle frames (pairs 0, 1, ...) the CPU baseline times on all host cores")
+    ap.add_argument("--cpu-single-thread-object", action="store_true",
+                    help="also time one whole object frame on one host thread (minutes)")
+    ap.add_argument("--served-frames", type=int, default=100,
+                    help="frames the served arm times (at least --steps)")
     ap.add_argument("--inflight", type=int, default=4, help="server in-flight slots (served arm)")
     ap.add_argument("--no-serve", action="store_true", help="time single frames only")
     ap.add_argument("--no-mix", action="store_true", help="skip the mixed-scene serving measurement")
@@ -91,13 +101,14 @@ def parse():
     return ap.parse_args()
 
 
-def workload_config(a, mlp):
-    return {"workload": f"object scene, {a.n} Gaussians, K=8, Phi/Psi 3x128 {mlp.upper()}, "
+def workload_config(a):
+    """The workload both arms time (the oracle arm computes it in FP64)."""
+    return {"workload": f"object scene, {a.n} Gaussians, K=8, Phi/Psi 3x128 {a.mlp.upper()}, "
                         f"{a.res}x{a.res}, point light, 100 seeded camera/light pairs",
-            "n_gaussians": a.n, "lobes": 8, "mlp": f"3x128 {mlp}", "image": [a.res, a.res],
+            "n_gaussians": a.n, "lobes": 8, "mlp": f"3x128 {a.mlp}", "image": [a.res, a.res],
             "pairs": 100,
-            "l2": ("served arm: inputs larger than L2 (149 MB scene, ~0.5 GB of pair lists per frame); "
-                   "single-frame arms: L2 flushed between steps (256 MB write), outside the timed events"),
+            "l2": ("inputs larger than L2 in every arm (149 MB scene, ~0.7 GB of intermediates per "
+                   "frame); no flush between frames in any timed arm"),
             "timing": "served: CUDA-event span from the first frame's start to the last frame's end",
             "parallelism": f"replicas x{a.gpus}"}
 
@@ -160,30 +171,91 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # CPU oracle (baseline leg and --impl reference)
 # ---------------------------------------------------------------------------
-def oracle_frame_seconds(scene, pair_seed, res, window):
-    """Oracle time for one frame: every per-Gaussian stage in full, both
-    composites over a centred window of window^2 pixels, composite time scaled
-    by the pixel ratio."""
+REF_SUBSTEPS = 4  # reference arm: steps per whole oracle frame
+
+
+def oracle_substep(state, scene, res, i, O, synth):
+    """Step i of the reference arm: sub-step i % 4 of frame i // 4 (camera /
+    light pair (i // 4) % 100) of the FP64 oracle, continuing `state`."""
+    k = i % REF_SUBSTEPS
+    if k == 0:
+        cam, light = synth.camera_light_pair((i // REF_SUBSTEPS) % 100, res, res)
+        state["frame"] = O.StagedFrame(scene, cam, light)
+    elif k == 1:
+        state["frame"].shadow_rows(0, res // 2)
+    elif k == 2:
+        state["frame"].shadow_rows(res // 2, res)
+    else:
+        state["frame"].finish()
+        state["frame"] = None
+
+
+def oracle_whole_frame(scene, pair_seed, res, threads, O, synth):
+    """One whole oracle frame (every stage, every pixel) on `threads` host threads."""
+    cam, light = synth.camera_light_pair(pair_seed, res, res)
+    t0 = time.perf_counter()
+    fr = O.render(scene, cam, light, O.Opts(threads=threads))
+    return time.perf_counter() - t0, fr
+
+
+def cpu_baseline(a, scene, gpu_frame0=None):
+    """The FP64 oracle on the host cores: whole frames of the object workload
+    on all cores (pairs 0 .. cpu_frames - 1), the tiny scene's frame on one
+    thread and on all cores; with the GPU's frame of pair 0, the error of the
+    timed form against the oracle."""
     from oracle import oracle as O
     from paper_2410_11419_gb300 import synth
-    cam, light = synth.camera_light_pair(pair_seed, res, res)
-    c0 = (res - window) // 2
-    fr = O.render(scene, cam, light, O.Opts(crop=(c0, c0, c0 + window, c0 + window)))
-    t = fr["times"]
-    scale = (res * res) / float(window * window)
-    return t["prep"] + t["bin"] + t["mlp"] + scale * (t["shadow"] + t["camera"]), t
-
-
-def cpu_baseline(a, scene):
-    from oracle import oracle as O
     O.build()
-    secs, t = oracle_frame_seconds(scene, 0, a.res, a.cpu_window)
-    return {"value": 1.0 / secs, "unit": UNIT, "cores": O.max_threads(), "kind": "oracle",
-            "sample": (f"1 frame (pair 0): FP64 oracle prep, binning and MLPs over all {a.n} "
-                       f"Gaussians; shadow and camera composites over a centred "
-                       f"{a.cpu_window}x{a.cpu_window} window, scaled x{(a.res / a.cpu_window) ** 2:.1f} "
-                       f"to the full {a.res}x{a.res} frame"),
-            "stage_s": {k: round(v, 4) for k, v in t.items()}}
+    cores = os.cpu_count() or 1
+    secs, fr0 = [], None
+    for p in range(max(1, a.cpu_frames)):
+        t, fr = oracle_whole_frame(scene, p, a.res, cores, O, synth)
+        secs.append(t)
+        if p == 0:
+            fr0 = fr
+    out = {"value": len(secs) / sum(secs), "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": (f"{len(secs)} whole frame(s) of the object workload (pairs 0..{len(secs) - 1}, "
+                      f"all {a.n} Gaussians, every pixel, {a.res}x{a.res}), FP64, OpenMP on all {cores} "
+                      "host cores"),
+           "s_per_frame": [round(t, 3) for t in secs],
+           "stage_s": {k: round(v, 4) for k, v in fr0["times"].items()},
+           "cpu": cpu_model()}
+    tiny = synth.tiny_scene(0)
+    for threads in (1, cores):
+        t, _ = oracle_whole_frame(tiny, 0, 128, threads, O, synth)
+        out[f"tiny_frame_s_{'1_thread' if threads == 1 else f'{threads}_threads'}"] = round(t, 4)
+    if a.cpu_single_thread_object:
+        t, _ = oracle_whole_frame(scene, 0, a.res, 1, O, synth)
+        out["object_frame_s_1_thread"] = round(t, 3)
+    if gpu_frame0 is not None:
+        out["error_vs_oracle"] = frame_error(gpu_frame0, fr0, a.mlp)
+    return out
+
+
+def frame_error(g, fr, mlp):
+    """Max / mean absolute (and relative where the path is FP32) error of the
+    GPU frame against the FP64 oracle per output, the MLP outputs and the
+    image carrying the timed MLP precision."""
+    import numpy as np
+    out = {"mlp": mlp, "pair": 0}
+    for nm, got, want in (("shade", g["shade"][:, :3], fr["shade"]), ("T", g["T"], fr["T"]),
+                          ("T_refined", g["Tp"], fr["Tp"]), ("residual", g["res"][:, :3], fr["res"]),
+                          ("image", g["img"], fr["img"])):
+        d = np.abs(got.astype(np.float64) - want)
+        out[nm] = {"max_abs": float(d.max()), "mean_abs": float(d.mean()),
+                   "max_rel": float((d / np.maximum(np.abs(want), 1e-6)).max())}
+    return out
+
+
+def cpu_model():
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                if line.lower().startswith(("model name", "cpu part")):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
 
 
 def run_reference(a):
@@ -193,23 +265,27 @@ def run_reference(a):
     from oracle import oracle as O
     from paper_2410_11419_gb300 import synth
     O.build()
+    cores = os.cpu_count() or 1
     scene = synth.object_scene(0, n=a.n)
-    times = []
-    for i in range(a.warmup + a.steps):
-        s, _ = oracle_frame_seconds(scene, i % 100, a.res, a.cpu_window)
-        if i >= a.warmup:
-            times.append(s)
-    tot = sum(times)
-    v = a.steps / tot
-    sample = (f"per step one frame: FP64 oracle over all {a.n} Gaussians, composites over a "
-              f"{a.cpu_window}x{a.cpu_window} window scaled to {a.res}x{a.res}")
+    state = {"frame": None}
+    for i in range(a.warmup):
+        oracle_substep(state, scene, a.res, i, O, synth)
+    t0 = time.perf_counter()
+    for i in range(a.warmup, a.warmup + a.steps):
+        oracle_substep(state, scene, a.res, i, O, synth)
+    tot = time.perf_counter() - t0
+    v = (a.steps / REF_SUBSTEPS) / tot
+    sample = (f"whole FP64 oracle frames of the workload, every {REF_SUBSTEPS} consecutive steps one frame "
+              "(1: shading, projections and per-tile lists; 2, 3: the shadow rays of the upper and the "
+              "lower half of the light view; 4: shadow average, Phi, Psi, camera composite); "
+              f"{a.steps} timed steps = {a.steps / REF_SUBSTEPS:g} frames, OpenMP on {cores} host cores")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": a.gpus,
         "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * tot / a.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": workload_config(a, "fp64"),
-        "cpu_baseline": {"value": v, "unit": UNIT, "cores": O.max_threads(), "kind": "oracle",
-                         "sample": sample},
+        "data": "synthetic", "config": workload_config(a),
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+                         "cpu": cpu_model()},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
 
@@ -432,11 +508,14 @@ def main():
     torch.cuda.synchronize()
     rd.check()
 
+    # measured ALU peaks (FP32 FMA, MUFU ex2): the roofline of the ALU-bound composites
+    ffma_tflops, ex2_gops = N.gs3_measure_alu_peak(5)
+
     K = a.steps
     fev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
     ts_host = torch.empty((K, 2, ntiles + 1), dtype=torch.int32, pin_memory=True)
     nc_host = torch.empty((K, a.res * a.res), dtype=torch.int32, pin_memory=True)
-    clocks = ClockSampler(local)
+    clocks = ClockSampler(local)  # sampled across every timed arm below
     clocks.start()
     time.sleep(0.3)
     launches0 = N.gs3_kernel_launches()
@@ -444,7 +523,6 @@ def main():
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for s in range(K):  # whole frames: gs3_render overlaps the light chain with the camera binning
-        flush.zero_()
         fev[s][0].record(stream)
         frame(view(s))
         fev[s][1].record(stream)
@@ -455,11 +533,11 @@ def main():
     wall = time.perf_counter() - t0
     replicas.barrier()
     launches = N.gs3_kernel_launches() - launches0
-    clk = clocks.stop()
     rd.check()
     step_ms = np.array([e0.elapsed_time(e1) for e0, e1 in fev])
 
-    # stage breakdown: the same frames stage by stage (no overlap between stages)
+    # stage breakdown: the same frames stage by stage (no overlap between stages;
+    # L2 flushed before each frame so that every stage starts as in a cold frame)
     KS = min(K, 10)
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(len(groups) + 1)] for _ in range(KS)]
     for s in range(KS):
@@ -470,6 +548,16 @@ def main():
                 for j, (nm, _) in enumerate(groups)}
     total_ms = replicas.max_over_ranks(float(step_ms.sum()), dev)
     value = replicas.whole_job_rate(K, total_ms / 1e3, world)
+
+    # the GPU frame of pair 0 (the CPU baseline's oracle frame) for the error of the timed form
+    gpu_frame0 = None
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        img0 = rd.render(*pairs[0], opts)
+        torch.cuda.synchronize()
+        rd.check()
+        gpu_frame0 = {"img": img0.cpu().numpy()}
+        for k in ("shade", "T", "Tp", "res"):
+            gpu_frame0[k] = rd.stage(k).cpu().numpy()
 
     # ---- end to end through the public API with host buffers ----
     host_img = torch.empty((a.res, a.res, 3), dtype=torch.float32, pin_memory=True)
@@ -486,6 +574,7 @@ def main():
     # ---- served arm: continuous batching through the server (headline) ----
     served = None
     if not a.no_serve:
+        RS = max(K, a.served_frames)
         srv = R.Server(hbm_budget=48 << 30, max_inflight=a.inflight, device=local)
         sid = srv.add_scene(ds)
         outs = [torch.empty((a.res, a.res, 3), device=dev) for _ in range(a.inflight + 2)]
@@ -497,7 +586,7 @@ def main():
         torch.cuda.synchronize()
         w0 = time.perf_counter()
         tk = []
-        for s_ in range(K):
+        for s_ in range(RS):
             cam, light = pairs[view(s_)]
             tk.append(srv.submit(sid, cam, light, outs[s_ % len(outs)]))
         bad = [srv.wait(t)[0] for t in tk]
@@ -505,24 +594,25 @@ def main():
         served_wall = time.perf_counter() - w0
         st = srv.stats()
         span_ms = replicas.max_over_ranks(st.device_span_ms, dev)
-        rate = K / (span_ms / 1e3)
+        rate = RS / (span_ms / 1e3)
         # latency under load: open-loop Poisson arrivals at 80 % of the served rate
         rng = np.random.default_rng(1234)
         lam = 0.8 * rate
-        gaps = rng.exponential(1.0 / lam, K)
+        gaps = rng.exponential(1.0 / lam, RS)
         lat_t = []
         t_next = time.perf_counter()
-        for s_ in range(K):
+        for s_ in range(RS):
             t_next += gaps[s_]
             while time.perf_counter() < t_next:
                 pass
             cam, light = pairs[(a.warmup + 7 * s_) % 100]
             lat_t.append(srv.submit(sid, cam, light, outs[s_ % len(outs)]))
         lats = np.array([srv.wait(t)[1] for t in lat_t])
-        served = {"value": world * rate, "device_span_ms": span_ms, "wall_s": served_wall,
+        served = {"value": world * rate, "frames": RS, "device_span_ms": span_ms, "wall_s": served_wall,
                   "inflight_slots": a.inflight, "max_in_flight": int(st.max_in_flight),
                   "retries": int(st.retries), "failed": int(sum(1 for b in bad if b != 0)),
-                  "latency_open_loop": {"rate_rps": lam, "p50_ms": float(np.percentile(lats, 50)),
+                  "latency_open_loop": {"rate_rps": lam, "requests": RS,
+                                        "p50_ms": float(np.percentile(lats, 50)),
                                         "p99_ms": float(np.percentile(lats, 99)),
                                         "clock": "host, submit to completion"}}
         srv.close()
@@ -538,9 +628,7 @@ def main():
         torch.cuda.synchronize()
         rd2.check()
         pe = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
-        mlp_ms = []
         for s_ in range(K):
-            flush.zero_()
             cam, light = pairs[(a.warmup + s_) % 100]
             pe[s_][0].record(stream)
             rd2.render(cam, light, opts)
@@ -561,7 +649,6 @@ def main():
             torch.cuda.synchronize()
             be = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
             for s_ in range(K):
-                flush.zero_()
                 cam, light = pairs[(a.warmup + s_) % 100]
                 be[s_][0].record(stream)
                 img = rd2.render(cam, light, opts)
@@ -585,7 +672,6 @@ def main():
             torch.cuda.synchronize()
             te = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(K)]
             for s_ in range(K):
-                flush.zero_()
                 te[s_][0].record(stream)
                 tr.step(*pairs[(a.warmup + s_) % 100], tgt)
                 te[s_][1].record(stream)
@@ -598,6 +684,8 @@ def main():
             rd2 = None
         del rd2
         ds2.close()
+
+    clk = clocks.stop()
 
     # ---- roofline of the dominant kernel ----
     ts = ts_host.numpy().astype(np.int64)
@@ -614,9 +702,9 @@ def main():
     per_step_light_P = [int(ts[s, 1, -1]) for s in range(K)]
     per_step_cam_P = [int(ts[s, 0, -1]) for s in range(K)]
     dominant = max(stage_ms, key=stage_ms.get)
-    sm_max = clk.get("sm_max_mhz") or 2070.0
-    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
-    fp32_peak_tflops = n_sm * 128 * 2 * sm_max * 1e6 / 1e12
+    fp32_peak_tflops = ffma_tflops
+    peak_src = (f"measured: FP32 FMA micro-kernel (gs3_measure_alu_peak, best of 5, all SMs); "
+                f"ex2 {ex2_gops:.0f} G/s measured beside it")
     FLOP_PER_EVAL = 12.0
     roof = None
     if dominant == "shadow_composite":
@@ -625,20 +713,20 @@ def main():
                 "unit": "TFLOP/s", "frac": achieved / fp32_peak_tflops, "traffic": profiled_traffic("k_shadow"),
                 "work": f"{FLOP_PER_EVAL:.0f} FLOP x (light pixel, list entry) pairs "
                         f"({float(np.mean(light_pairs_evals)):.3e} per frame)",
-                "peak_source": f"derived: {n_sm} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz"}
+                "peak_source": peak_src}
     elif dominant == "camera_composite":
         achieved = 20.0 * float(np.mean(cam_evals)) / (stage_ms[dominant] / 1e3) / 1e12
         roof = {"kernel": "k_camera", "bound": "alu", "achieved": achieved, "peak": fp32_peak_tflops,
                 "unit": "TFLOP/s", "frac": achieved / fp32_peak_tflops, "traffic": None,
                 "work": "20 FLOP x entries consumed per pixel",
-                "peak_source": f"derived: {n_sm} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz"}
+                "peak_source": peak_src}
     elif dominant == "mlp":
         flops = 2.0 * a.n * (64 * 128 + 2 * 128 * 128 + 128 + 64 * 128 + 2 * 128 * 128 + 3 * 128)
         achieved = flops / (stage_ms[dominant] / 1e3) / 1e12
         roof = {"kernel": "k_mlp", "bound": "alu", "achieved": achieved, "peak": fp32_peak_tflops,
                 "unit": "TFLOP/s", "frac": achieved / fp32_peak_tflops, "traffic": None,
                 "work": "2 x N x sum(in x out) of both MLPs",
-                "peak_source": f"derived: {n_sm} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz"}
+                "peak_source": peak_src}
     else:
         P = float(np.mean(per_step_light_P if dominant == "light_bin" else per_step_cam_P))
         byts = P * 8 * 2 + a.n * 48 * 2
@@ -652,10 +740,10 @@ def main():
                 "unit": "GB/s", "frac": achieved / peak, "traffic": None,
                 "work": "pairs written + read once (8 B each) + records"}
 
-    single = {"value": value, "ms_per_step": total_ms / K,
+    single = {"value": value, "ms_per_step": total_ms / K, "frames": K,
               "p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99)),
-              "note": "one frame at a time through gs3_render, CUDA events per frame, L2 flushed between "
-                      "frames; stages_ms come from a separate stage-by-stage pass"}
+              "note": "one frame at a time through gs3_render, CUDA events per frame; stages_ms come "
+                      "from a separate stage-by-stage pass with L2 flushed before each frame"}
     head_value = served["value"] if served else value
     head_ms = 1e3 * world / head_value
     p50 = served["latency_open_loop"]["p50_ms"] if served else single["p50_ms"]
@@ -666,7 +754,9 @@ def main():
         "scaling": "weak", "vs_baseline": None,
         "dtype": "f32" if a.mlp == "fp32" else f"{a.mlp} MLP operands, f32 elsewhere",
         "data": "synthetic (seeded object scene, random-init MLPs)",
-        "config": dict(workload_config(a, a.mlp), pair_capacity=cap),
+        "config": workload_config(a),
+        "pair_capacity": cap,
+        "alu_peak": {"ffma_tflops": ffma_tflops, "ex2_gops": ex2_gops},
         "p50_ms": p50, "p99_ms": p99,
         "served": served,
         "single_frame": single,
@@ -688,7 +778,8 @@ def main():
     if world == 1 and not a.no_ksweep:
         out["lobe_sweep"] = lobe_sweep(a, dev, np, torch, N, R, synth)
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(a, scene)
+        out["cpu_baseline"] = cpu_baseline(a, scene, gpu_frame0)
+        out["error_vs_oracle"] = out["cpu_baseline"].pop("error_vs_oracle", None)
     if rank == 0:
         print(json.dumps(out))
     ds.close()

@@ -423,6 +423,21 @@ gs3_status gs3_depth_order_static(const uint32_t *keys, uint32_t n, uint32_t *or
  * gs3_last_error) when the scratch allocation or a CUDA call fails. */
 gs3_status gs3_selftest_wait_timeout(uint32_t n, uint32_t *status_out);
 
+/* ---- Measured ALU peaks --------------------------------------------------
+ * Not an operation of the paper: the denominators of the roofline of the
+ * ALU-bound composites, whose every (pixel, splat) test is FP32 fused
+ * multiply-adds, a compare and one MUFU ex2.  Times two micro-kernels that
+ * fill every SM (64 warps each, eight independent dependency chains per
+ * thread) with CUDA events on the legacy default stream: FP32 FMA (2 FLOP
+ * each) and ex2.approx, and reports the best of `repeats` launches after one
+ * warm-up launch of each.
+ *   ffma_tflops: host, FP32 FMA throughput in TFLOP/s
+ *   ex2_gops:    host, ex2 throughput in G operations/s
+ * The figures hold for the SM clock during the call.  Synchronous (allocates
+ * and frees a small output buffer).  Errors: INVALID_ARG (null output,
+ * repeats outside [1, 100]), CUDA. */
+gs3_status gs3_measure_alu_peak(int32_t repeats, double *ffma_tflops, double *ex2_gops);
+
 /* Number of CUDA kernels this library has launched in this process (all
  * threads, all devices); a host-side counter for launch accounting. */
 uint64_t gs3_kernel_launches(void);

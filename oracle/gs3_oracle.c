@@ -176,6 +176,9 @@ typedef struct {
     double t_prep, t_bin, t_shadow, t_mlp, t_camera; /* wall seconds per stage */
     int64_t *amb;  /* with record_amb: the codes of every ambiguous decision (unordered) */
     int64_t namb, amb_cap;
+    /* between the stages of go_begin / go_shadow_rows / go_finish */
+    double *sacc;       /* N x 4: shadow-ray sums num, den, bnum, bden over the rows done so far */
+    double *wi, *wo;    /* N x 3: unit directions to the light and to the camera (O2) */
 } go_frame;
 
 /* appends an ambiguous decision to the frame's record (any thread) */
@@ -650,7 +653,10 @@ static void build_lists(go_frame *f, int s)
 /* ------------------------------------------------------------------------ */
 static float key_to_float(uint32_t k) { float f; memcpy(&f, &k, 4); return f; }
 
-static void shadow_splat(go_frame *f, const go_opts *o)
+/* O10 for the shadow rays of light-view rows [y0, y1) (inside the crop
+ * window): adds each Gaussian's sums of beta T_m and beta (and of their
+ * bounds) to f->sacc */
+static void shadow_rows(go_frame *f, const go_opts *o, int y0, int y1)
 {
     int n = f->n, W = f->width, H = f->height, ts = o->tile;
     int nthr = 1;
@@ -677,6 +683,8 @@ static void shadow_splat(go_frame *f, const go_opts *o)
         int *pass = malloc(sizeof(int) * cap);
         int wx0, wy0, wx1, wy1;
         window(o, W, H, &wx0, &wy0, &wx1, &wy1);
+        if (wy0 < y0) wy0 = y0;
+        if (wy1 > y1) wy1 = y1;
 #ifdef _OPENMP
 #pragma omp for schedule(dynamic, 4)
 #endif
@@ -751,15 +759,26 @@ static void shadow_splat(go_frame *f, const go_opts *o)
         }
         free(al); free(be); free(A); free(Q); free(d); free(gi); free(amb); free(pass);
     }
-    f->shadow_evals = evals;
-    f->shadow_pass = passes;
-    f->amb_shadow = ambs;
+    f->shadow_evals += evals;
+    f->shadow_pass += passes;
+    f->amb_shadow += ambs;
     for (int g = 0; g < n; ++g) {
-        double num = 0, den = 0, bnum = 0, bden = 0;
         for (int t = 0; t < nthr; ++t) {
             double *a = acc + (size_t)t * n * 4;
-            num += a[g]; den += a[n + g]; bnum += a[2 * n + g]; bden += a[3 * n + g];
+            for (int q = 0; q < 4; ++q) f->sacc[4 * (size_t)g + q] += a[(size_t)q * n + g];
         }
+    }
+    free(acc);
+}
+
+/* O10: T = sum beta T_m / sum beta per Gaussian (1 when no shadow ray meets
+ * it), and the bound of its straddling decisions */
+static void shadow_average(go_frame *f)
+{
+    int n = f->n;
+    for (int g = 0; g < n; ++g) {
+        const double *a = f->sacc + 4 * (size_t)g;
+        double num = a[0], den = a[1], bnum = a[2], bden = a[3];
         f->T[g] = den > 0.0 ? num / den : 1.0;
         if (bnum == 0.0 && bden == 0.0) {
             f->T_bound[g] = 0.0;
@@ -770,7 +789,6 @@ static void shadow_splat(go_frame *f, const go_opts *o)
             f->T_bound[g] = 1.0;
         }
     }
-    free(acc);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -889,7 +907,15 @@ static void camera_composite(go_frame *f, const go_opts *o)
 /* ------------------------------------------------------------------------ */
 /* Whole frame                                                               */
 /* ------------------------------------------------------------------------ */
-go_frame *go_render(const go_scene *sc, const go_camera *cam, const go_light *L, const go_opts *o)
+/* Stages of one frame, for callers that time them apart (the whole frame is
+ * go_render; the same arithmetic in the same order):
+ *   go_begin        O1-O8: parameters, directions, shading, both projections,
+ *                   keys and per-tile lists
+ *   go_shadow_rows  O10 for the shadow rays of light-view rows [y0, y1); every
+ *                   row once, in any number of calls
+ *   go_finish       O10's per-Gaussian average, O11-O12 (Phi, Psi), O9 (the
+ *                   camera composite and the deferred combination) */
+go_frame *go_begin(const go_scene *sc, const go_camera *cam, const go_light *L, const go_opts *o)
 {
 #ifdef _OPENMP
     if (o->threads > 0) omp_set_num_threads(o->threads);
@@ -923,6 +949,7 @@ go_frame *go_render(const go_scene *sc, const go_camera *cam, const go_light *L,
     f->S = malloc(sizeof(double) * 3 * np);
     f->Sh = malloc(sizeof(double) * np);
     f->Rimg = malloc(sizeof(double) * 3 * np);
+    f->sacc = calloc((size_t)n * 4, sizeof(double));
 
     double t0 = now_s();
     d3 *wi = malloc(sizeof(d3) * n), *wo = malloc(sizeof(d3) * n);
@@ -950,18 +977,42 @@ go_frame *go_render(const go_scene *sc, const go_camera *cam, const go_light *L,
         }
         shade_one(sc, g, cam, L, o, f->shade + 3 * g, wi + g, wo + g);
     }
+    f->wi = (double *)wi;
+    f->wo = (double *)wo;
     double t1 = now_s();
     build_lists(f, 0);
     build_lists(f, 1);
     double t2 = now_s();
+    f->t_prep = t1 - t0;
+    f->t_bin = t2 - t1;
+    return f;
+}
 
+void go_shadow_rows(go_frame *f, const go_opts *o, int y0, int y1)
+{
+#ifdef _OPENMP
+    if (o->threads > 0) omp_set_num_threads(o->threads);
+#endif
+    if (o->ablate & 1) return;
+    double t0 = now_s();
+    shadow_rows(f, o, y0, y1);
+    f->t_shadow += now_s() - t0;
+}
+
+void go_finish(go_frame *f, const go_scene *sc, const go_opts *o)
+{
+#ifdef _OPENMP
+    if (o->threads > 0) omp_set_num_threads(o->threads);
+#endif
+    int n = f->n;
+    const d3 *wi = (const d3 *)f->wi, *wo = (const d3 *)f->wo;
+    double t2 = now_s();
     if (o->ablate & 1) {
         for (int g = 0; g < n; ++g) f->T[g] = 1.0;
     } else {
-        shadow_splat(f, o);
+        shadow_average(f);
     }
     double t3 = now_s();
-
     /* Phi and Psi per Gaussian (Sec. 4.2, 4.3) */
 #ifdef _OPENMP
 #pragma omp parallel for schedule(static)
@@ -993,13 +1044,19 @@ go_frame *go_render(const go_scene *sc, const go_camera *cam, const go_light *L,
             for (int c = 0; c < 3; ++c) f->res[3 * g + c] = y[c];
         }
     }
-    free(wi);
-    free(wo);
     double t4 = now_s();
     camera_composite(f, o);
     double t5 = now_s();
-    f->t_prep = t1 - t0; f->t_bin = t2 - t1; f->t_shadow = t3 - t2; f->t_mlp = t4 - t3;
+    f->t_shadow += t3 - t2;
+    f->t_mlp = t4 - t3;
     f->t_camera = t5 - t4;
+}
+
+go_frame *go_render(const go_scene *sc, const go_camera *cam, const go_light *L, const go_opts *o)
+{
+    go_frame *f = go_begin(sc, cam, L, o);
+    go_shadow_rows(f, o, 0, f->height);
+    go_finish(f, sc, o);
     return f;
 }
 
@@ -1013,6 +1070,7 @@ void go_frame_free(go_frame *f)
     free(f->opacity); free(f->shade); free(f->T); free(f->T_bound); free(f->Tp);
     free(f->Tp_bound); free(f->res); free(f->img); free(f->img_bound); free(f->final_T);
     free(f->n_contrib); free(f->S); free(f->Sh); free(f->Rimg); free(f->amb);
+    free(f->sacc); free(f->wi); free(f->wo);
     free(f);
 }
 

@@ -87,7 +87,8 @@ class _Frame(C.Structure):
                 ("camera_evals", C.c_int64), ("amb_shadow", C.c_int64),
                 ("amb_camera", C.c_int64), ("camera_pass", C.c_int64), ("t_prep", C.c_double), ("t_bin", C.c_double),
                 ("t_shadow", C.c_double), ("t_mlp", C.c_double), ("t_camera", C.c_double),
-                ("amb", C.POINTER(C.c_int64)), ("namb", C.c_int64), ("amb_cap", C.c_int64)]
+                ("amb", C.POINTER(C.c_int64)), ("namb", C.c_int64), ("amb_cap", C.c_int64),
+                ("sacc", _D), ("wi", _D), ("wo", _D)]
 
 # kinds of decision-ambiguous cases (the top bits of a decision code)
 AMB_SHADOW_ALPHA, AMB_CAMERA_ALPHA, AMB_CAMERA_STOP = 0, 1, 2
@@ -114,6 +115,11 @@ def lib():
         _lib.go_render.argtypes = [C.POINTER(_Scene), C.POINTER(_Camera), C.POINTER(_Light),
                                    C.POINTER(_Opts)]
         _lib.go_frame_free.argtypes = [C.POINTER(_Frame)]
+        _lib.go_begin.restype = C.POINTER(_Frame)
+        _lib.go_begin.argtypes = [C.POINTER(_Scene), C.POINTER(_Camera), C.POINTER(_Light),
+                                  C.POINTER(_Opts)]
+        _lib.go_shadow_rows.argtypes = [C.POINTER(_Frame), C.POINTER(_Opts), C.c_int, C.c_int]
+        _lib.go_finish.argtypes = [C.POINTER(_Frame), C.POINTER(_Scene), C.POINTER(_Opts)]
         _lib.go_diffuse.restype = C.c_double
         _lib.go_diffuse.argtypes = [C.c_double]
         _lib.go_angular_gaussian.restype = C.c_double
@@ -236,6 +242,34 @@ def render(scene, cam, light, opts: Opts | None = None) -> dict:
     sc = c_scene(scene, keep)
     cc, lc, oc = c_camera(cam), c_light(light), opts.c()
     fp = lib().go_render(C.byref(sc), C.byref(cc), C.byref(lc), C.byref(oc))
+    return _collect(fp)
+
+
+class StagedFrame:
+    """One oracle frame run stage by stage (the arithmetic of render(), for
+    timing the stages apart): construction runs O1-O8 (shading, projections,
+    lists), shadow_rows(y0, y1) the shadow rays of light-view rows [y0, y1)
+    (each row once), finish() the per-Gaussian shadow average, Phi, Psi and
+    the camera composite, and returns what render() returns."""
+
+    def __init__(self, scene, cam, light, opts: Opts | None = None):
+        self.opts = opts or Opts()
+        self.keep: list = []
+        self.sc = c_scene(scene, self.keep)
+        self.cc, self.lc, self.oc = c_camera(cam), c_light(light), self.opts.c()
+        self.fp = lib().go_begin(C.byref(self.sc), C.byref(self.cc), C.byref(self.lc), C.byref(self.oc))
+        self.height = cam.height
+
+    def shadow_rows(self, y0: int, y1: int):
+        lib().go_shadow_rows(self.fp, C.byref(self.oc), int(y0), int(y1))
+
+    def finish(self) -> dict:
+        lib().go_finish(self.fp, C.byref(self.sc), C.byref(self.oc))
+        fp, self.fp = self.fp, None
+        return _collect(fp)
+
+
+def _collect(fp) -> dict:
     f = fp.contents
     n, W, H, nt = f.n, f.width, f.height, f.ntiles
     out = {"n": n, "width": W, "height": H, "gx": f.gx, "gy": f.gy, "ntiles": nt,

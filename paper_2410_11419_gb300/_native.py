@@ -158,6 +158,7 @@ SIGNATURES = {
     "gs3_depth_order_static": (C.c_int, [C.c_void_p, C.c_uint32, C.c_void_p, C.c_void_p]),
     "gs3_selftest_wait_timeout": (C.c_int, [C.c_uint32, C.POINTER(C.c_uint32)]),
     "gs3_kernel_launches": (C.c_uint64, []),
+    "gs3_measure_alu_peak": (C.c_int, [C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "gs3_last_error": (C.c_char_p, []),
 }
 
@@ -358,6 +359,13 @@ def gs3_selftest_wait_timeout(n: int) -> int:
     out = C.c_uint32(0)
     _check(lib().gs3_selftest_wait_timeout(n, C.byref(out)), "gs3_selftest_wait_timeout")
     return int(out.value)
+
+
+def gs3_measure_alu_peak(repeats: int = 5):
+    """(FP32 FMA TFLOP/s, ex2 G ops/s) of the current device, measured."""
+    f, x = C.c_double(0.0), C.c_double(0.0)
+    _check(lib().gs3_measure_alu_peak(repeats, C.byref(f), C.byref(x)), "gs3_measure_alu_peak")
+    return float(f.value), float(x.value)
 
 
 def gs3_kernel_launches() -> int:

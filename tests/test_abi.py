@@ -66,3 +66,7 @@ def test_host_only_entry_points(libgs3):
     for bad in (0, 4096, (1 << 20) + 1):
         with pytest.raises(N.GS3Error):
             N.gs3_selftest_wait_timeout(bad)
+    # so does the ALU peak measurement
+    for bad in (0, 101):
+        with pytest.raises(N.GS3Error):
+            N.gs3_measure_alu_peak(bad)

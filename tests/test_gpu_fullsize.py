@@ -1,22 +1,88 @@
 """Parity at the benchmark's full size: the 300,000-Gaussian object scene,
-K = 8, 3x128 MLPs, 800x800, with the capacity bench.py uses, against the full
-FP64 oracle frame (about a minute of host time).  Integer stages bit for bit;
-shading, shadow values, T', residual and the image within
-|g - o| <= 1e-4 |o| + 1e-6 + bound (the oracle's decision-ambiguity bound)."""
+K = 8, 3x128 MLPs, 800x800, against the full FP64 oracle frame (about half a
+minute of host time per view, shared by the cases of that view).
+
+FP32 MLPs: integer stages bit for bit; shading, shadow values, T', residual
+and the image within |g - o| <= 1e-4 |o| + 1e-6 + bound (the oracle's
+decision-ambiguity bound).
+
+BF16 and FP8 E4M3 MLPs (the precision form; BF16 is the served headline):
+integer stages still bit for bit and the FP32 stages (shading, shadow values)
+still within 1e-4 + bound; T', the residual and the image carry the MLP
+precision, and their max / mean error against the oracle is recorded
+(GS3_PARITY_STATS) and bounded."""
+import json
+import os
+
+import numpy as np
 import pytest
 
 from paper_2410_11419_gb300 import synth
-from tests.test_gpu_parity import check_float_stages, check_integer_stages, run_both
+from tests.test_gpu_parity import assert_close, check_float_stages, check_integer_stages, run_both
 
 pytestmark = [pytest.mark.gpu, pytest.mark.slow]
 
+PAIRS = (0, 57)
 
-@pytest.mark.parametrize("pair", [0, 57])
-def test_object_scene_800(gs3, oracle, pair):
+
+@pytest.fixture(scope="module")
+def object_frames(oracle):
     scene = synth.object_scene(0)
-    cam, light = synth.camera_light_pair(pair, 800, 800)
-    g, fr = run_both(gs3, oracle, scene, cam, light, cap=40_000_000)
+    cache = {}
+
+    def get(pair):
+        if pair not in cache:
+            cam, light = synth.camera_light_pair(pair, 800, 800)
+            cache[pair] = (cam, light, oracle.render(scene, cam, light))
+        return cache[pair]
+    return scene, get
+
+
+@pytest.mark.parametrize("pair", PAIRS)
+def test_object_scene_800(gs3, oracle, object_frames, pair):
+    scene, get = object_frames
+    cam, light, fr = get(pair)
+    g, fr = run_both(gs3, oracle, scene, cam, light, cap=40_000_000, fr=fr)
     assert g["hdr"].pairs_cam == fr["cam_P"] and g["hdr"].pairs_light == fr["light_P"]
     assert fr["cam_P"] > 10_000_000
     check_integer_stages(g, fr)
     check_float_stages(g, fr)
+
+
+def _record(name, stats):
+    path = os.environ.get("GS3_PARITY_STATS")
+    if path:
+        with open(path, "a") as fh:
+            for k, (mx, mn) in stats.items():
+                fh.write(json.dumps({"test": name, "output": k, "max_abs": float(mx),
+                                     "mean_abs": float(mn)}) + "\n")
+
+
+@pytest.mark.parametrize("dtype", ["bf16", "fp8"])
+@pytest.mark.parametrize("pair", PAIRS)
+def test_object_scene_800_reduced_precision(gs3, oracle, object_frames, pair, dtype):
+    from paper_2410_11419_gb300 import _native as N
+    scene, get = object_frames
+    cam, light, fr = get(pair)
+    mlp = N.GS3_MLP_BF16 if dtype == "bf16" else N.GS3_MLP_FP8_E4M3
+    g, fr = run_both(gs3, oracle, scene, cam, light, cap=40_000_000, fr=fr, mlp_dtype=mlp)
+    check_integer_stages(g, fr)
+    assert_close("shade", g["shade"][:, :3].astype(np.float64), fr["shade"])
+    assert_close("shadow T", g["T"].astype(np.float64), fr["T"], fr["T_bound"])
+    err = {nm: np.abs(got.astype(np.float64) - want) for nm, got, want in
+           (("T'", g["Tp"], fr["Tp"]), ("residual", g["res"][:, :3], fr["res"]), ("image", g["img"], fr["img"]))}
+    stats = {k: (float(v.max()), float(v.mean())) for k, v in err.items()}
+    _record(f"{dtype}_object_800_pair{pair}", stats)
+    img_scale = max(1.0, float(np.abs(fr["img"]).mean()))
+    if dtype == "bf16":
+        # BF16 operands (8 mantissa bits) through three 128-wide layers: a few
+        # 1e-3 on the sigmoid outputs
+        assert stats["T'"][0] < 1e-2 and stats["residual"][0] < 1e-2
+        assert stats["T'"][1] < 1e-3 and stats["residual"][1] < 1e-3
+        assert stats["image"][1] < 2e-3 * img_scale
+    else:
+        # E4M3 keeps 3 mantissa bits: a few 1e-2; a wrong scale or layout moves
+        # the outputs by O(0.1 - 1)
+        assert stats["T'"][0] < 0.1 and stats["residual"][0] < 0.1
+        assert stats["T'"][1] < 2e-2 and stats["residual"][1] < 2e-2
+        assert stats["image"][1] < 2e-2 * img_scale

@@ -20,10 +20,12 @@ pytestmark = pytest.mark.gpu
 RTOL, ATOL = 1e-4, 1e-6
 
 
-def run_both(gs3, oracle, scene, cam, light, ablate=0, cap=1 << 20, falloff=1):
+def run_both(gs3, oracle, scene, cam, light, ablate=0, cap=1 << 20, falloff=1, fr=None, mlp_dtype=0):
+    """The GPU frame's stages (through the C ABI) and the oracle frame (`fr`
+    when given, else rendered here)."""
     import torch
     from paper_2410_11419_gb300 import render as R
-    ds = R.DeviceScene(scene)
+    ds = R.DeviceScene(scene, mlp_dtype=mlp_dtype)
     rd = R.Renderer(ds, cam.width, cam.height, cap)
     img = rd.render(cam, light, R.opts_struct(ablate=ablate, falloff=falloff))
     torch.cuda.synchronize()
@@ -39,7 +41,8 @@ def run_both(gs3, oracle, scene, cam, light, ablate=0, cap=1 << 20, falloff=1):
     g["light_final"] = rd.stage("light_final").cpu().numpy()
     g["light_stop"] = rd.stage("light_stop").cpu().numpy().view(np.uint32)
     g["hdr"] = hdr
-    fr = oracle.render(scene, cam, light, oracle.Opts(ablate=ablate, falloff=falloff))
+    if fr is None:
+        fr = oracle.render(scene, cam, light, oracle.Opts(ablate=ablate, falloff=falloff))
     ds.close()
     return g, fr
 

@@ -631,3 +631,18 @@ def test_ambiguous_share_full_object_frame(oracle):
     # shadow-side straddles alone never push a pixel over the tolerance here
     assert not np.any(over.any(-1).reshape(-1) & ~cam_side)
     assert fr["T_bound"].max() < 1e-4
+
+
+def test_staged_frame_equals_whole_frame(oracle, small_frame):
+    """The oracle frame run stage by stage (the shadow rays in three bands of
+    light-view rows, as the timed CPU baseline runs it) gives the whole
+    frame's result, up to the order of the per-Gaussian sums."""
+    sc, cam, light, opts, fr = small_frame
+    st = oracle.StagedFrame(sc, cam, light, opts)
+    for y0, y1 in ((0, 13), (13, 30), (30, cam.height)):
+        st.shadow_rows(y0, y1)
+    got = st.finish()
+    for k in ("T", "Tp", "res", "img", "final_T"):
+        np.testing.assert_allclose(got[k], fr[k], rtol=1e-12, atol=1e-15)
+    np.testing.assert_array_equal(got["n_contrib"], fr["n_contrib"])
+    assert got["shadow_evals"] == fr["shadow_evals"]
