@@ -146,6 +146,10 @@ Workspace plan_workspace(int n, int width, int height, size_t cap) {
   L.partial = P.take(8 * cap);
   L.tile_order[0] = P.take(4 * (size_t)L.ntiles);
   L.tile_order[1] = P.take(4 * (size_t)L.ntiles);
+  const size_t items = shadow_seg_items(L.ntiles, cap);
+  L.seg_lvl = P.take(4 * (1025 + 3));
+  L.seg_flag = P.take(4 * items);
+  L.seg_pub = P.take(4 * 256 * items);
   L.shade = P.take(16 * N);
   L.T = P.take(4 * N);
   L.Tp = P.take(4 * N);

@@ -48,29 +48,46 @@ __device__ __forceinline__ float splat_power(const float4 a, const float4 b, flo
 // form a prefix of the tile's list; its end K(j) is precomputed per entry
 // (k_occluder_bound) and is non-decreasing in j.
 //
-// One warp per 16x16 tile, eight pixels per lane: lane l owns column l & 15,
-// rows (l >> 4) + 2 i, i = 0..7 (i < 4: the tile's top half).  The warp walks
-// the tile's list once: receivers are staged kRecv at a time, the occluders
-// they need through a window of up to kOccWin records, and each lane keeps
-// its eight rays' products A over the consumed occluders.  Records hold the
-// splat centre relative to the tile origin (pixel offsets are one exact
-// subtraction) and the pre-scaled conic.  A receiver is evaluated only in
-// the halves of the tile (8 rows each) that both its alpha >= alpha_min box
-// and its ellipse reach.  Per receiver each lane sums (beta A, beta) over its
-// eight rays into a shared-memory row; every kRedGroup receivers the warp
-// adds the rows' 32 lane sums per receiver, in lane order, into the
-// (tile, Gaussian) partials (no shuffle chain per receiver).  The halves
-// where a receiver passed are recorded at once (two votes, as quadrant bits
-// 0x3 / 0xC); an occluder is evaluated only in the halves where it passed as
-// a receiver (same power test) and where some ray has not stopped.  A ray
-// stops taking occluders once its product is below kShadowStop; once all
-// 256 rays stopped, the warp walks the rest of the list as receivers only.
+// Work is split into segments of a tile's list: segment s holds receivers
+// [R_s, R_s+1) (kSegLen entries; the last takes the rest) and needs the
+// occluders [C_s, C_s+1) on top of the product A(C_s) that every ray carries
+// into it, with C_s = K(R_s).  One warp takes one segment at a time from a
+// ticket counter, in segment-major order (every tile's first segment, then
+// every tile's second, ...), and:
+//   1. computes each of its 256 rays' product Q over its occluder range (a
+//      ray drops out once the product can no longer stay above the stop);
+//   2. takes A(C_s) from the segment before it (published by that warp; a
+//      bounded wait) and publishes A(C_s+1) = A(C_s) Q for the next one;
+//   3. walks its receivers in order with the products P = A(C_s) q, q the
+//      running product of the range's occluders, summing (beta P, beta) per
+//      receiver into the (tile, Gaussian) partials.
+// Step 1 runs before the wait, so the segments of a long list run side by
+// side and only the cheap step 2 is chained.  When A(C_s) is already
+// published as the warp starts, step 1 skips the rays that are stopped.
+//
+// Ray stop: a ray takes occluders only while its product P = A(C_s) q stays
+// >= kShadowStop; the occluder that takes P below it is the ray's last, and
+// P stays frozen for the rest of that segment's receivers.  A(C_s+1) of a ray
+// that stopped is published as 0 (the receivers of later segments see 0; an
+// exact product there is below kShadowStop as well).  The publication and
+// the walk agree on where a ray stops: both multiply the same factors in the
+// same order and compare round(A(C_s) q) with the stop, which is monotone in
+// q.  Thread layout as in the splat evaluation: lane l owns column l & 15,
+// rows (l >> 4) + 2 i, i = 0..7, which is ray 32 i + l of the tile.
 // ---------------------------------------------------------------------------
-constexpr int kRecv = 64;
-constexpr int kOccWin = 128;
-constexpr int kRedGroup = 16;  // receivers whose per-lane sums are reduced together
-constexpr int kShadowThreads = 32;
-constexpr int kPx = 8;  // pixels per lane
+constexpr uint32_t kSegLen = 256;   // receivers per segment
+constexpr int kSegLevels = 1024;    // segments per tile at most (the last takes the rest)
+constexpr int kSegWarps = 4;        // independent warps per block
+constexpr int kRecv = 32;           // receivers staged at a time
+constexpr int kOccWin = 32;         // occluder window
+constexpr int kRedGroup = 16;       // receivers whose per-lane sums are reduced together
+constexpr int kPx = 8;              // rays per lane
+constexpr int kSegSpin = 1 << 20;   // polls of a predecessor's publication before giving up
+
+__host__ __device__ inline uint32_t seg_count(uint32_t len) {
+  const uint32_t n = (len + kSegLen - 1) / kSegLen;
+  return n < 1 ? 1u : (n > (uint32_t)(kSegLevels - 1) ? (uint32_t)(kSegLevels - 1) : n);
+}
 
 struct ShadowParams {
   const uint32_t* list;
@@ -78,19 +95,25 @@ struct ShadowParams {
   const SplatRec* rrec;
   const uint32_t* off;
   const uint32_t* kbound;
-  const uint32_t* tile_order;  // block b renders tile tile_order[b]
+  const uint32_t* tile_order;  // tiles by decreasing segment count
+  const uint32_t* lvl_off;     // [kSegLevels + 1]: first work item of each segment level
+  uint32_t* ticket;            // [3] work counters of K6a, K6b and K6c (zeroed per frame)
+  float* pub_a;                // [item][256]: A(C_s+1) published by item
+  uint32_t* pub_flag;          // [item]: 0 not yet, 1 published, 2 published and every ray stopped
   uint8_t* pass_mask;  // per list entry: halves with a passing pixel, 0x3 rows 0-7, 0xC rows 8-15
   float2* partial;
   float* light_final;     // per light pixel: the product where the ray ended
   uint32_t* light_stop;   // per light pixel: 1 + index of the occluder that stopped it, or kNoStop
+  uint32_t* status;
   int W, H, gx;
   float amax;
 };
 
-struct ShadowSmem {
+struct ShadowSmem {  // one warp's
+  float ain[kPx * 32];     // A(C_s) of the segment's rays (ray 32 i + lane)
+  uint32_t xlim[kPx * 32]; // 1 + the occluder after which a ray stopped in this segment, or 0
   float4 r0[kRecv], r1[kRecv];
   uint32_t rk[kRecv], rslot[kRecv];
-  uint32_t rpass[kRecv];  // halves in which the receiver passed
   float4 o0[kOccWin], o1[kOccWin];
   float2 red[kRedGroup][33];  // per receiver of the group, per lane: (num, den); padded row
 };
@@ -125,73 +148,181 @@ __device__ __forceinline__ uint32_t ellipse_halves(const float4 e0, const float4
   return m;
 }
 
-__global__ void __launch_bounds__(kShadowThreads, 18) k_shadow(ShadowParams p) {
-  __shared__ ShadowSmem S;
-  const int tile = (int)p.tile_order[blockIdx.x];
-  const int tx = tile % p.gx, ty = tile / p.gx;
-  const float ox = (float)(tx * kTile), oy = (float)(ty * kTile);
-  const int lane = threadIdx.x;
-  const int lxi = lane & 15, lyi = lane >> 4;
-  const bool inx = tx * kTile + lxi < p.W;
-  const float lx = lxi + 0.5f;
-  // A pixel outside the image is moved far from every splat: its power is
-  // then far below any threshold and it never passes.  It starts stopped.
-  const float kFar = 1.0e6f;
-  float ly[kPx], A[kPx];
-  uint32_t lim[kPx];
-  bool any_in = false;
-#pragma unroll
-  for (int i = 0; i < kPx; ++i) {
-    const bool in = inx && ty * kTile + lyi + 2 * i < p.H;
-    ly[i] = in ? lyi + 2 * i + 0.5f : kFar;
-    A[i] = in ? 1.f : 0.f;
-    lim[i] = kNoStop;
-    any_in |= in;
-  }
-  const float omin = 1.f - p.amax;
-  const uint32_t b = p.tile_start[tile], e = p.tile_start[tile + 1];
-  bool dead = !__any_sync(0xffffffffu, any_in);  // all 256 rays stopped
-  uint32_t live = dead ? 0u : 0xFu;  // halves (0x3, 0xC) with a ray that has not stopped
-  uint32_t k = b;
+// one list entry, staged: make_entry's record plus the halves its box and
+// ellipse both reach (in e1.w)
+__device__ __forceinline__ void stage_entry(const ShadowParams& p, uint32_t idx, float ox, float oy, float4& e0,
+                                            float4& e1) {
+  make_entry(p.rrec[p.list[idx]], ox, oy, e0, e1);
+  e1.w = __uint_as_float(__float_as_uint(e1.w) & ellipse_halves(e0, e1));
+}
 
-  // one occluder (list index kk, window slot i) on the lane's rays
-  auto occlude8 = [&](int i, uint32_t kk, uint32_t rb) {
-    const float4 o1 = S.o1[i];
-    const uint32_t bits = (kk >= rb ? S.rpass[kk - rb] : __float_as_uint(o1.w)) & live;
-    if (!bits) return;
-    const float4 o0 = S.o0[i];
-    const float dx = lx - o0.x;
-    const float sx = (o0.z * dx) * dx, v = o1.x * dx;
+// 1 - alpha of an occluder entry at a pixel where it passes (power2 >= threshold)
+__device__ __forceinline__ float occ_factor(const float4 o1, float pw, float omin) {
+  return fmaxf(omin, fmaf(-o1.z, ex2(pw), 1.f));
+}
+
+__device__ __forceinline__ uint32_t ld_acquire(const uint32_t* a) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(a) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release(uint32_t* a, uint32_t v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(a), "r"(v) : "memory");
+}
+
+// A receiver's four rays of one half: den += beta and num += beta a_i at the
+// rays where it passes (power2 >= thr), beta = 2^power2.  Predicated, no branch.
+template <bool WITH_NUM, int H>
+__device__ __forceinline__ void recv_half(const float (&ly)[kPx], const float (&a)[kPx], float y, float c, float v,
+                                          float sx, float thr, float& num, float& den) {
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      if (!(bits & (3u << (2 * h)))) continue;
+  for (int qq = 0; qq < 4; ++qq) {
+    const int i = 4 * H + qq;
+    const float dy = ly[i] - y;
+    const float pw = fmaf(dy, fmaf(c, dy, v), sx);
+    if (WITH_NUM)
+      asm("{\n\t.reg .pred p;\n\t.reg .f32 b;\n\t"
+          "setp.ge.f32 p, %2, %3;\n\t"
+          "@p ex2.approx.ftz.f32 b, %2;\n\t"
+          "@p add.rn.f32 %1, %1, b;\n\t"
+          "@p fma.rn.f32 %0, b, %4, %0;\n\t}"
+          : "+f"(num), "+f"(den) : "f"(pw), "f"(thr), "f"(a[i]));
+    else
+      asm("{\n\t.reg .pred p;\n\t.reg .f32 b;\n\t"
+          "setp.ge.f32 p, %1, %2;\n\t"
+          "@p ex2.approx.ftz.f32 b, %1;\n\t"
+          "@p add.rn.f32 %0, %0, b;\n\t}"
+          : "+f"(den) : "f"(pw), "f"(thr));
+  }
+}
+
+// An occluder on four rays of one half, each still taking occluders
+// (A q >= stop): q *= max(omin, 1 - gamma 2^power2) where it passes, then
+// P = A q.  Returns bit qq set for the rays whose P fell below the stop here.
+template <int I>
+__device__ __forceinline__ uint32_t occ_ray(const float (&ly)[kPx], uint32_t ain, float (&q)[kPx], float (&P)[kPx],
+                                            float y, float c, float v, float sx, float thr, float ngamma,
+                                            float omin) {
+  const float dy = ly[I] - y;
+  const float pw = fmaf(dy, fmaf(c, dy, v), sx);
+  uint32_t x;
+  // ain: shared-memory address of the lane's A(C_s) of ray 0; ray I at + 128 I
+  asm("{\n\t.reg .pred a, p, c;\n\t.reg .f32 b, f, e;\n\t"
+      "setp.ge.f32 a, %1, %7;\n\t"           // still taking occluders
+      "setp.ge.and.f32 p, %3, %4, a;\n\t"    // and this one passes
+      "@p ex2.approx.ftz.f32 b, %3;\n\t"
+      "@p ld.shared.f32 e, [%8+%9];\n\t"
+      "@p fma.rn.f32 f, %5, b, 0f3F800000;\n\t"
+      "@p max.f32 f, f, %6;\n\t"
+      "@p mul.rn.f32 %0, %0, f;\n\t"
+      "@p mul.rn.f32 %1, e, %0;\n\t"
+      "setp.lt.and.f32 c, %1, %7, p;\n\t"    // its last one
+      "selp.u32 %2, 1, 0, c;\n\t}"
+      : "+f"(q[I]), "+f"(P[I]), "=r"(x)
+      : "f"(pw), "f"(thr), "f"(ngamma), "f"(omin), "f"(kShadowStop), "r"(ain), "n"(128 * I));
+  return x << I;
+}
+
+template <int H>
+__device__ __forceinline__ uint32_t occ_half(const float (&ly)[kPx], uint32_t ain, float (&q)[kPx], float (&P)[kPx],
+                                             float y, float c, float v, float sx, float thr, float ngamma,
+                                             float omin) {
+  return occ_ray<4 * H + 0>(ly, ain, q, P, y, c, v, sx, thr, ngamma, omin) |
+         occ_ray<4 * H + 1>(ly, ain, q, P, y, c, v, sx, thr, ngamma, omin) |
+         occ_ray<4 * H + 2>(ly, ain, q, P, y, c, v, sx, thr, ngamma, omin) |
+         occ_ray<4 * H + 3>(ly, ain, q, P, y, c, v, sx, thr, ngamma, omin);
+}
+
+// halves (0x3, 0xC) with a ray whose product is still >= the stop
+__device__ __forceinline__ uint32_t live_halves(const float (&P)[kPx]) {
+  bool h0 = false, h1 = false;
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int i8 = 4 * h + q;
-        const float dy = ly[i8] - o0.y;
-        const float pw = fmaf(dy, fmaf(o0.w, dy, v), sx);
-        if (pw >= o1.y && A[i8] >= kShadowStop) {
-          A[i8] *= fmaxf(omin, fmaf(-o1.z, ex2(pw), 1.f));
-          if (A[i8] < kShadowStop) lim[i8] = kk + 1;
-        }
+  for (int i = 0; i < 4; ++i) {
+    h0 |= P[i] >= kShadowStop;
+    h1 |= P[4 + i] >= kShadowStop;
+  }
+  return (__any_sync(0xffffffffu, h0) ? 0x3u : 0u) | (__any_sync(0xffffffffu, h1) ? 0xCu : 0u);
+}
+
+// The per-warp state of one segment (item) of the shadow composite.
+struct SegState {
+  int lane, tx, ty, s;
+  float lx, ox, oy, omin;
+  uint32_t C1;
+  uint32_t k, wb, we;  // next occluder; staged occluder window [wb, we)
+  uint32_t live;       // halves with a ray still taking occluders
+  size_t pix0;         // the lane's first pixel
+};
+
+// Walks occluders up to kend (exclusive), staging windows of the range as it
+// goes; a ray whose product falls below the stop records where it ended.
+__device__ __forceinline__ void walk_to(const ShadowParams& p, ShadowSmem& S, SegState& st, uint32_t kend,
+                                        const float (&ly)[kPx], uint32_t ain, float (&q)[kPx], float (&P)[kPx]) {
+  while (st.live && st.k < kend) {
+    if (st.k == st.we) {
+      __syncwarp();
+      st.wb = st.k;
+      st.we = min(st.k + (uint32_t)kOccWin, st.C1);
+      for (uint32_t t = st.lane; t < st.we - st.wb; t += 32)
+        stage_entry(p, st.wb + t, st.ox, st.oy, S.o0[t], S.o1[t]);
+      __syncwarp();
+    }
+    const uint32_t stop_at = min(kend, st.we);
+    for (; st.k < stop_at; ++st.k) {
+      const int t = (int)(st.k - st.wb);
+      const float4 o1 = S.o1[t];
+      const uint32_t bits = __float_as_uint(o1.w) & st.live;
+      if (!bits) continue;
+      const float4 o0 = S.o0[t];
+      const float dx = st.lx - o0.x;
+      const float sx = (o0.z * dx) * dx, v = o1.x * dx;
+      uint32_t crossed = 0u;
+      if (bits & 0x3u) crossed = occ_half<0>(ly, ain, q, P, o0.y, o0.w, v, sx, o1.y, -o1.z, st.omin);
+      if (bits & 0xCu) crossed |= occ_half<1>(ly, ain, q, P, o0.y, o0.w, v, sx, o1.y, -o1.z, st.omin);
+      if (crossed) {  // rare: the ray's last occluder (its product stays frozen from here)
+#pragma unroll
+        for (int i = 0; i < kPx; ++i)
+          if (crossed & (1u << i)) S.xlim[32 * i + st.lane] = st.k + 1;
       }
     }
-  };
-  // refreshes the live halves after an occluder run; false once every ray stopped
-  auto still_alive = [&]() {
-    bool al[2] = {false, false};
-#pragma unroll
-    for (int i = 0; i < kPx; ++i) al[i >> 2] |= A[i] >= kShadowStop;
-    live = (__any_sync(0xffffffffu, al[0]) ? 0x3u : 0u) | (__any_sync(0xffffffffu, al[1]) ? 0xCu : 0u);
-    return live != 0u;
-  };
+    st.live = live_halves(P);
+  }
+  if (!st.live) st.k = max(st.k, kend);
+}
 
-  // Sums of the receivers of group [j0, jl]: lane t < 16 adds num of receiver
-  // j0 + t over the 32 lanes, lane 16 + t its den, in lane order.
-  auto reduce_group = [&](int jl) {
-    const int j0 = jl - jl % kRedGroup;
+// Stages receivers [rb, rb + rc) of the segment into shared memory.
+__device__ __forceinline__ void stage_receivers(const ShadowParams& p, ShadowSmem& S, const SegState& st, uint32_t rb,
+                                                int rc) {
+  __syncwarp();  // the previous batch is consumed
+  for (int t = st.lane; t < rc; t += 32) {
+    const uint32_t rank = p.list[rb + t];
+    const SplatRec qr = p.rrec[rank];
+    float4 e0, e1;
+    make_entry(qr, st.ox, st.oy, e0, e1);
+    e1.w = __uint_as_float(__float_as_uint(e1.w) & ellipse_halves(e0, e1));
+    S.r0[t] = e0;
+    S.r1[t] = e1;
+    S.rk[t] = p.kbound[rb + t];
+    S.rslot[t] = p.off[rank] + (uint32_t)((st.ty - qr.r.y) * (qr.r.z - qr.r.x + 1) + (st.tx - qr.r.x));
+  }
+  __syncwarp();
+}
+
+// Receiver jj of the batch at rb: its per-lane (num, den) to a row, its pass
+// halves to pass_mask; every kRedGroup receivers (and at the batch's end)
+// lane t < 16 adds num of receiver j0 + t over the 32 lanes, lane 16 + t its
+// den, in lane order, into the (tile, Gaussian) partial.
+__device__ __forceinline__ void finish_receiver(const ShadowParams& p, ShadowSmem& S, int lane, uint32_t rb, int jj,
+                                                int rc, float num, float den0, float den1) {
+  const uint32_t bits = (__any_sync(0xffffffffu, den0 > 0.f) ? 0x3u : 0u) |
+                        (__any_sync(0xffffffffu, den1 > 0.f) ? 0xCu : 0u);
+  S.red[jj % kRedGroup][lane] = make_float2(num, den0 + den1);
+  if (lane == 0) p.pass_mask[rb + jj] = (uint8_t)bits;
+  if (jj % kRedGroup == kRedGroup - 1 || jj == rc - 1) {
+    __syncwarp();
+    const int j0 = jj - jj % kRedGroup;
     const int t = lane & 15, c = lane >> 4;
-    if (j0 + t <= jl) {
+    if (j0 + t <= jj) {
       const float* row = reinterpret_cast<const float*>(S.red[t]) + c;
       float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
 #pragma unroll
@@ -201,124 +332,411 @@ __global__ void __launch_bounds__(kShadowThreads, 18) k_shadow(ShadowParams p) {
       reinterpret_cast<float*>(p.partial)[2 * (size_t)S.rslot[j0 + t] + c] = (a0 + a1) + (a2 + a3);
     }
     __syncwarp();  // the group's rows are free again
-  };
-
-  // receiver jj of the staged batch: the lane's (beta A, beta) sums over its
-  // eight rays, and the halves where it passed somewhere in the tile
-  auto eval_receiver = [&](int jj, float& num, float& den) -> uint32_t {
-    const float4 r1 = S.r1[jj];
-    const uint32_t box = __float_as_uint(r1.w);
-    num = 0.f;
-    den = 0.f;
-    if (!box) return 0u;  // its ellipse reaches no pixel centre of the tile
-    const float4 r0 = S.r0[jj];
-    const float dx = lx - r0.x;
-    const float sx = (r0.z * dx) * dx, v = r1.x * dx;
-    bool hit[2] = {false, false};
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      if (!(box & (3u << (2 * h)))) continue;
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int i8 = 4 * h + q;
-        const float dy = ly[i8] - r0.y;
-        const float pw = fmaf(dy, fmaf(r0.w, dy, v), sx);
-        if (pw >= r1.y) {
-          const float beta = ex2(pw);
-          num = fmaf(beta, A[i8], num);
-          den += beta;
-          hit[h] = true;
-        }
-      }
-    }
-    return (__any_sync(0xffffffffu, hit[0]) ? 0x3u : 0u) | (__any_sync(0xffffffffu, hit[1]) ? 0xCu : 0u);
-  };
-
-  for (uint32_t rb = b; rb < e; rb += kRecv) {
-    const int rc = (int)min((uint32_t)kRecv, e - rb);
-    __syncwarp();  // the previous batch is consumed
-    for (int t = lane; t < rc; t += kShadowThreads) {
-      const uint32_t rank = p.list[rb + t];
-      const SplatRec q = p.rrec[rank];
-      float4 e0, e1;
-      make_entry(q, ox, oy, e0, e1);
-      // a half must be reached by the alpha box (one of its quadrants) and by the ellipse
-      e1.w = __uint_as_float(__float_as_uint(e1.w) & ellipse_halves(e0, e1));
-      S.r0[t] = e0;
-      S.r1[t] = e1;
-      if (!dead) S.rk[t] = p.kbound[rb + t];
-      S.rslot[t] = p.off[rank] + (uint32_t)((ty - q.r.y) * (q.r.z - q.r.x + 1) + (tx - q.r.x));
-    }
-    __syncwarp();
-    if (dead) {
-      // every ray stopped: no occluders, no windows, no pass lookups by
-      // occluders; the receivers only
-      for (int jj = 0; jj < rc; ++jj) {
-        float num, den;
-        const uint32_t bits = eval_receiver(jj, num, den);
-        S.red[jj % kRedGroup][lane] = make_float2(num, den);
-        if (lane == 0) p.pass_mask[rb + jj] = (uint8_t)bits;
-        if (jj % kRedGroup == kRedGroup - 1 || jj == rc - 1) {
-          __syncwarp();
-          reduce_group(jj);
-        }
-      }
-      continue;
-    }
-    const uint32_t klast = S.rk[rc - 1];
-    int jj = 0;
-    while (jj < rc) {
-      // once every ray stopped the rest of the batch's occluders form one
-      // window that nobody loads
-      const uint32_t kt = dead ? klast : min(klast, k + (uint32_t)kOccWin);
-      if (!dead) {
-        // an occluder of an earlier batch carries the halves where it passed
-        // as a receiver; one of this batch is looked up when it is used
-        for (uint32_t i = lane; i < kt - k; i += kShadowThreads) {
-          make_entry(p.rrec[p.list[k + i]], ox, oy, S.o0[i], S.o1[i]);
-          if (k + i < rb) S.o1[i].w = __uint_as_float((uint32_t)p.pass_mask[k + i]);
-        }
-      }
-      __syncwarp();
-      const uint32_t ow = k;
-      for (; jj < rc; ++jj) {
-        const uint32_t kend = S.rk[jj];
-        if (kend > kt) break;
-        if (dead) {
-          k = max(k, kend);
-        } else if (k < kend) {
-          for (; k < kend; ++k) occlude8((int)(k - ow), k, rb);
-          dead = !still_alive();
-        }
-        // receiver jj: sum (beta A, beta) over the tile's 256 rays
-        float num, den;
-        const uint32_t bits = eval_receiver(jj, num, den);
-        S.red[jj % kRedGroup][lane] = make_float2(num, den);
-        if (lane == 0) {
-          p.pass_mask[rb + jj] = (uint8_t)bits;
-          S.rpass[jj] = bits;
-        }
-        __syncwarp();  // rpass is read by later occluders; red by reduce_group
-        if (jj % kRedGroup == kRedGroup - 1 || jj == rc - 1) reduce_group(jj);
-      }
-      if (dead) {  // the next receiver needs occluders past this window
-        k = max(k, kt);
-      } else if (k < kt) {
-        for (; k < kt; ++k) occlude8((int)(k - ow), k, rb);
-        dead = !still_alive();
-      }
-      __syncwarp();  // the window is consumed
-    }
   }
-  // the product where each ray ended and where it stopped (the backward starts from them)
-  if (inx) {
+}
+
+// A(C_s) of the lane's rays: 1 / 0 (in / outside the image) for a tile's
+// first segment, else the predecessor's publication (read from L2: it was
+// written on another SM); flag 2 publishes that every ray stopped.
+__device__ __forceinline__ void load_entering(const ShadowParams& p, int s, uint32_t wpred, uint32_t flag, int lane,
+                                              int rows_in, float (&A)[kPx]) {
+#pragma unroll
+  for (int i = 0; i < kPx; ++i)
+    A[i] = s == 0 ? (i < rows_in ? 1.f : 0.f)
+                  : (flag == 2u ? 0.f : __ldcg(p.pub_a + (size_t)wpred * 256 + 32 * i + lane));
+}
+
+__device__ __forceinline__ bool all_stopped(const float (&A)[kPx]) {
+  bool any = false;
+#pragma unroll
+  for (int i = 0; i < kPx; ++i) any |= A[i] >= kShadowStop;
+  return !__any_sync(0xffffffffu, any);
+}
+
+// den + 2^pw where pw >= thr (predicated, no branch)
+__device__ __forceinline__ float recv_den(float pw, float thr, float den) {
+  asm("{\n\t.reg .pred p;\n\t.reg .f32 b;\n\t"
+      "setp.ge.f32 p, %1, %2;\n\t"
+      "@p ex2.approx.ftz.f32 b, %1;\n\t"
+      "@p add.rn.f32 %0, %0, b;\n\t}"
+      : "+f"(den) : "f"(pw), "f"(thr));
+  return den;
+}
+
+// The segment a work item names: its level s (segment index) and tile, the
+// levels being prefixes of the tile order.
+struct SegItem {
+  int s, tile, tx, ty, rows_in;
+  uint32_t R0, R1, C0, C1, wpred;
+  bool last;
+};
+
+__device__ __forceinline__ SegItem seg_item(const ShadowParams& p, uint32_t w, int lane) {
+  SegItem it;
+  int lo = 0, hi = kSegLevels;  // largest s with lvl_off[s] <= w
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (p.lvl_off[mid] <= w) lo = mid; else hi = mid;
+  }
+  it.s = lo;
+  const uint32_t pos = w - p.lvl_off[lo];
+  it.tile = (int)p.tile_order[pos];
+  it.tx = it.tile % p.gx;
+  it.ty = it.tile / p.gx;
+  const uint32_t b = p.tile_start[it.tile], e = p.tile_start[it.tile + 1];
+  it.last = (uint32_t)lo == seg_count(e - b) - 1;
+  it.R0 = b + (uint32_t)lo * kSegLen;
+  it.R1 = it.last ? e : it.R0 + kSegLen;
+  it.C0 = e > b ? p.kbound[it.R0] : b;
+  it.C1 = e > b ? (it.last ? p.kbound[e - 1] : p.kbound[it.R1]) : b;
+  it.wpred = lo > 0 ? p.lvl_off[lo - 1] + pos : 0u;
+  // ray i of the lane is row (lane >> 4) + 2 i: rows below the image hold no ray
+  const int lxi = lane & 15, lyi = lane >> 4;
+  it.rows_in = it.tx * kTile + lxi < p.W ? min(kPx, (p.H - it.ty * kTile - lyi + 1) / 2) : 0;
+  return it;
+}
+
+// The next work item of the warp (a ticket), or false past the last.
+__device__ __forceinline__ bool next_item(uint32_t* ticket, uint32_t total, int lane, uint32_t& w) {
+  uint32_t t = 0;
+  if (lane == 0) t = atomicAdd(ticket, 1u);
+  w = __shfl_sync(0xffffffffu, t, 0);
+  return w < total;
+}
+
+// K6a: A(C_s+1) of every segment but a tile's last, chained from A(C_s).
+// Step 1 (the range's products Q) runs before the chain is known, so the
+// segments of a list run side by side and only the combination is chained.
+__global__ void __launch_bounds__(kSegWarps * 32, 5) k_shadow_chain(ShadowParams p) {
+  __shared__ ShadowSmem smem[kSegWarps];
+  ShadowSmem& S = smem[threadIdx.x >> 5];
+  const int lane = threadIdx.x & 31;
+  const int lxi = lane & 15, lyi = lane >> 4;
+  const float lx = lxi + 0.5f, omin = 1.f - p.amax;
+  const uint32_t total = p.lvl_off[kSegLevels];
+  const uint32_t ain = (uint32_t)__cvta_generic_to_shared(&S.ain[lane]);
+  uint32_t w;
+  while (next_item(p.ticket, total, lane, w)) {
+    const SegItem it = seg_item(p, w, lane);
+    if (it.last) continue;  // nothing follows it
+    const float ox = (float)(it.tx * kTile), oy = (float)(it.ty * kTile);
+    float ly[kPx];
+#pragma unroll
+    for (int i = 0; i < kPx; ++i) ly[i] = i < it.rows_in ? lyi + 2 * i + 0.5f : 1.0e6f;
+    // A(C_s): known now for the first segment, or when the predecessor
+    // published already; until then A = 1 stands in (A <= 1)
+    uint32_t flag = 1u;
+    if (it.s > 0 && lane == 0) flag = ld_acquire(p.pub_flag + it.wpred);
+    flag = __shfl_sync(0xffffffffu, flag, 0);
+    __syncwarp();  // orders every lane's reads after lane 0's acquire
+    bool known = flag != 0u;
+    float A[kPx];
+    if (known) {
+      load_entering(p, it.s, it.wpred, flag, lane, it.rows_in, A);
+    } else {
+#pragma unroll
+      for (int i = 0; i < kPx; ++i) A[i] = i < it.rows_in ? 1.f : 0.f;
+    }
+    const bool dead = known && all_stopped(A);
+    // the range's products Q; a ray drops out once A Q < stop (it stops
+    // either way); the product so far is the same whichever A stood in
+    float Q[kPx], PQ[kPx];
 #pragma unroll
     for (int i = 0; i < kPx; ++i) {
-      const int y = ty * kTile + lyi + 2 * i;
-      if (y < p.H) {
-        const size_t pix = (size_t)y * p.W + tx * kTile + lxi;
-        p.light_final[pix] = A[i];
-        p.light_stop[pix] = lim[i];
+      Q[i] = 1.f;
+      PQ[i] = A[i] >= kShadowStop ? A[i] : 0.f;
+    }
+    if (!dead) {
+      __syncwarp();
+#pragma unroll
+      for (int i = 0; i < kPx; ++i) S.ain[32 * i + lane] = A[i];
+      uint32_t live = live_halves(PQ);
+      for (uint32_t wb = it.C0; wb < it.C1 && live; wb += kOccWin) {
+        if (!known) {  // the predecessor may have published meanwhile
+          uint32_t fl = 0u;
+          if (lane == 0) fl = ld_acquire(p.pub_flag + it.wpred);
+          fl = __shfl_sync(0xffffffffu, fl, 0);
+          __syncwarp();
+          if (fl != 0u) {
+            known = true;
+            load_entering(p, it.s, it.wpred, fl, lane, it.rows_in, A);
+#pragma unroll
+            for (int i = 0; i < kPx; ++i) {
+              S.ain[32 * i + lane] = A[i];
+              PQ[i] = A[i] >= kShadowStop ? A[i] * Q[i] : 0.f;
+            }
+            live = live_halves(PQ);
+            if (!live) break;
+          }
+        }
+        const int wc = (int)min((uint32_t)kOccWin, it.C1 - wb);
+        __syncwarp();
+        for (int t = lane; t < wc; t += 32) stage_entry(p, wb + t, ox, oy, S.o0[t], S.o1[t]);
+        __syncwarp();
+        for (int t = 0; t < wc; ++t) {
+          const float4 o1 = S.o1[t];
+          const uint32_t bits = __float_as_uint(o1.w) & live;
+          if (!bits) continue;
+          const float4 o0 = S.o0[t];
+          const float dx = lx - o0.x;
+          const float sx = (o0.z * dx) * dx, v = o1.x * dx;
+          if (bits & 0x3u) occ_half<0>(ly, ain, Q, PQ, o0.y, o0.w, v, sx, o1.y, -o1.z, omin);
+          if (bits & 0xCu) occ_half<1>(ly, ain, Q, PQ, o0.y, o0.w, v, sx, o1.y, -o1.z, omin);
+        }
+        live = live_halves(PQ);
+      }
+    }
+    // A(C_s) from the predecessor (bounded wait), then A(C_s+1) for the successor
+    if (!known) {
+      uint32_t fl = 0u;
+      if (lane == 0) {
+        int spins = 0;
+        while ((fl = ld_acquire(p.pub_flag + it.wpred)) == 0u) {
+          if (++spins > kSegSpin) {
+            atomicCAS(p.status, 0u, (uint32_t)GS3_ERR_TIMEOUT);
+            fl = 2u;  // give up: the frame is reported invalid, the warp finishes
+            break;
+          }
+          __nanosleep(64);
+        }
+      }
+      fl = __shfl_sync(0xffffffffu, fl, 0);
+      __syncwarp();
+      load_entering(p, it.s, it.wpred, fl, lane, it.rows_in, A);
+    }
+    const bool dead_in = all_stopped(A);
+    bool any = false;
+#pragma unroll
+    for (int i = 0; i < kPx; ++i) {
+      float a = 0.f;
+      if (A[i] >= kShadowStop) {
+        a = A[i] * Q[i];
+        if (!(a >= kShadowStop)) a = 0.f;  // the ray stops in this range
+      }
+      any |= a != 0.f;
+      if (!dead_in) p.pub_a[(size_t)w * 256 + 32 * i + lane] = a;
+    }
+    const bool any_out = __any_sync(0xffffffffu, any);
+    __threadfence();  // every lane's products before the flag
+    __syncwarp();
+    if (lane == 0) st_release(p.pub_flag + w, any_out ? 1u : 2u);
+  }
+}
+
+// K6c: the receivers of the segments every ray of which stopped before the
+// segment (A(C_s) = 0 throughout, as K6a published).  The products are 0,
+// so a receiver needs only its beta sum over the tile, which depends on no
+// other entry.  A warp stages up to kDeadBatch receivers, lists their
+// (receiver, half) units (the halves their box and ellipse reach), and each
+// lane walks the 16 x 8 pixels of one unit at a time, with the power
+// arithmetic of the ray layout (pixel centres x + 0.5, y + 0.5); the two
+// halves of a receiver are then added in a fixed order.
+constexpr int kDeadBatch = 128;
+constexpr int kDeadWarps = 4;
+
+struct DeadSmem {  // one warp's
+  float4 e0[kDeadBatch], e1[kDeadBatch];
+  float den[2][kDeadBatch];
+  uint16_t unit[2 * kDeadBatch];  // receiver (bits 0-7) and half (bit 8) of each unit
+};
+
+// The beta sum of one receiver entry over the 16 x 8 pixels of half h of an
+// interior tile, column by column.
+__device__ __forceinline__ float dead_half(const float4 e0, const float4 e1, int h) {
+  float dy[8];
+  const float y0 = 8.f * h + 0.5f;
+#pragma unroll
+  for (int y = 0; y < 8; ++y) dy[y] = (y0 + (float)y) - e0.y;
+  float den = 0.f, fx = 0.5f;
+#pragma unroll 1
+  for (int x = 0; x < kTile; ++x) {
+    const float dx = fx - e0.x;
+    fx += 1.f;
+    const float sx = (e0.z * dx) * dx, v = e1.x * dx;
+#pragma unroll
+    for (int y = 0; y < 8; ++y) den = recv_den(fmaf(dy[y], fmaf(e0.w, dy[y], v), sx), e1.y, den);
+  }
+  return den;
+}
+
+// the same over the pixels of half h that lie inside the image (edge tiles)
+__device__ __forceinline__ float dead_half_edge(const float4 e0, const float4 e1, int h, int ncol, int nrow) {
+  float den = 0.f, fx = 0.5f;
+  const int y1 = min(8 * h + 8, nrow);
+  for (int x = 0; x < ncol; ++x, fx += 1.f) {
+    const float dx = fx - e0.x;
+    const float sx = (e0.z * dx) * dx, v = e1.x * dx;
+    float fy = 8.f * h + 0.5f;
+    for (int y = 8 * h; y < y1; ++y, fy += 1.f) {
+      const float dy = fy - e0.y;
+      den = recv_den(fmaf(dy, fmaf(e0.w, dy, v), sx), e1.y, den);
+    }
+  }
+  return den;
+}
+
+__global__ void __launch_bounds__(kDeadWarps * 32, 6) k_shadow_dead(ShadowParams p) {
+  __shared__ DeadSmem smem[kDeadWarps];
+  DeadSmem& D = smem[threadIdx.x >> 5];
+  const int lane = threadIdx.x & 31;
+  const uint32_t total = p.lvl_off[kSegLevels];
+  uint32_t w;
+  while (next_item(p.ticket + 2, total, lane, w)) {
+    int lo = 0, hi = kSegLevels;  // the item's level: largest s with lvl_off[s] <= w
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (p.lvl_off[mid] <= w) lo = mid; else hi = mid;
+    }
+    if (lo == 0) continue;  // a tile's first segment starts with every ray open
+    const uint32_t pos = w - p.lvl_off[lo];
+    if (__ldcg(p.pub_flag + p.lvl_off[lo - 1] + pos) != 2u) continue;  // not stopped: K6b's
+    const int tile = (int)p.tile_order[pos];
+    const int tx = tile % p.gx, ty = tile / p.gx;
+    const float ox = (float)(tx * kTile), oy = (float)(ty * kTile);
+    const uint32_t b = p.tile_start[tile], e = p.tile_start[tile + 1];
+    const bool last = (uint32_t)lo == seg_count(e - b) - 1;
+    const uint32_t R0 = b + (uint32_t)lo * kSegLen, R1 = last ? e : R0 + kSegLen;
+    const int ncol = min(kTile, p.W - tx * kTile), nrow = min(kTile, p.H - ty * kTile);
+    const bool interior = ncol == kTile && nrow == kTile;
+    for (uint32_t rb = R0; rb < R1; rb += kDeadBatch) {
+      const int rc = (int)min((uint32_t)kDeadBatch, R1 - rb);
+      // stage the receivers; list the units of half 0, then of half 1
+      __syncwarp();
+      int n0 = 0, n1 = 0;
+      uint32_t box[kDeadBatch / 32];
+#pragma unroll
+      for (int c = 0; c < kDeadBatch / 32; ++c) {
+        const int t = 32 * c + lane;
+        box[c] = 0u;
+        if (t < rc) {
+          float4 e0, e1;
+          make_entry(p.rrec[p.list[rb + t]], ox, oy, e0, e1);
+          box[c] = __float_as_uint(e1.w) & ellipse_halves(e0, e1);
+          D.e0[t] = e0;
+          D.e1[t] = e1;
+        }
+        n0 += __popc(__ballot_sync(0xffffffffu, (box[c] & 0x3u) != 0u));
+        n1 += __popc(__ballot_sync(0xffffffffu, (box[c] & 0xCu) != 0u));
+      }
+      int b0 = 0, b1 = n0;  // next unit slot of each half
+#pragma unroll
+      for (int c = 0; c < kDeadBatch / 32; ++c) {
+        const int t = 32 * c + lane;
+        const uint32_t m0 = __ballot_sync(0xffffffffu, (box[c] & 0x3u) != 0u);
+        const uint32_t m1 = __ballot_sync(0xffffffffu, (box[c] & 0xCu) != 0u);
+        const uint32_t below = (1u << lane) - 1u;
+        if (box[c] & 0x3u) D.unit[b0 + __popc(m0 & below)] = (uint16_t)t;
+        if (box[c] & 0xCu) D.unit[b1 + __popc(m1 & below)] = (uint16_t)(t | 0x100);
+        b0 += __popc(m0);
+        b1 += __popc(m1);
+        if (t < rc) D.den[0][t] = D.den[1][t] = 0.f;
+      }
+      __syncwarp();
+      const int nu = n0 + n1;
+      for (int u = lane; u < nu; u += 32) {
+        const int code = D.unit[u];
+        const int t = code & 0xFF, h = code >> 8;
+        const float4 e0 = D.e0[t], e1 = D.e1[t];
+        D.den[h][t] = interior ? dead_half(e0, e1, h) : dead_half_edge(e0, e1, h, ncol, nrow);
+      }
+      __syncwarp();
+      for (int t = lane; t < rc; t += 32) {
+        const uint32_t rank = p.list[rb + t];
+        const SplatRec qr = p.rrec[rank];
+        const float d0 = D.den[0][t], d1 = D.den[1][t];
+        const uint32_t slot = p.off[rank] + (uint32_t)((ty - qr.r.y) * (qr.r.z - qr.r.x + 1) + (tx - qr.r.x));
+        p.partial[slot] = make_float2(0.f, d0 + d1);
+        p.pass_mask[rb + t] = (uint8_t)((d0 > 0.f ? 0x3u : 0u) | (d1 > 0.f ? 0xCu : 0u));
+      }
+    }
+  }
+}
+
+// K6b: the receivers of every segment, with the products P = A(C_s) q, q the
+// running product of the range's occluders; A(C_s) comes from K6a.
+__global__ void __launch_bounds__(kSegWarps * 32, 5) k_shadow(ShadowParams p) {
+  __shared__ ShadowSmem smem[kSegWarps];
+  ShadowSmem& S = smem[threadIdx.x >> 5];
+  SegState st;
+  st.lane = threadIdx.x & 31;
+  const int lane = st.lane;
+  const int lxi = lane & 15, lyi = lane >> 4;
+  st.lx = lxi + 0.5f;
+  st.omin = 1.f - p.amax;
+  const uint32_t total = p.lvl_off[kSegLevels];
+  const uint32_t ain = (uint32_t)__cvta_generic_to_shared(&S.ain[lane]);
+  uint32_t w;
+  while (next_item(p.ticket + 1, total, lane, w)) {
+    const SegItem it = seg_item(p, w, lane);
+    st.s = it.s;
+    st.tx = it.tx;
+    st.ty = it.ty;
+    st.ox = (float)(it.tx * kTile);
+    st.oy = (float)(it.ty * kTile);
+    st.C1 = it.C1;
+    float ly[kPx];
+#pragma unroll
+    for (int i = 0; i < kPx; ++i) ly[i] = i < it.rows_in ? lyi + 2 * i + 0.5f : 1.0e6f;
+    // A(C_s) and A(C_s+1), as K6a published them
+    uint32_t fl_in = it.s == 0 ? 1u : __ldcg(p.pub_flag + it.wpred);
+    uint32_t fl_out = it.last ? 1u : __ldcg(p.pub_flag + w);
+    float P[kPx];
+    load_entering(p, it.s, it.wpred, fl_in, lane, it.rows_in, P);
+    const bool dead = all_stopped(P);
+    if (dead) continue;  // K6c takes it
+    // rays the publication has stop in this range (they must reach their stop)
+    bool pending = false;
+    float q[kPx];
+    __syncwarp();
+#pragma unroll
+    for (int i = 0; i < kPx; ++i) {
+      q[i] = 1.f;
+      S.ain[32 * i + lane] = P[i];
+      S.xlim[32 * i + lane] = 0u;
+      if (P[i] >= kShadowStop && !it.last) {
+        const float out = fl_out == 2u ? 0.f : __ldcg(p.pub_a + (size_t)w * 256 + 32 * i + lane);
+        pending |= out == 0.f;
+      }
+      if (!(P[i] >= kShadowStop)) P[i] = 0.f;
+    }
+    __syncwarp();
+    st.live = live_halves(P);
+    st.k = st.wb = st.we = it.C0;
+    st.pix0 = (size_t)(it.ty * kTile + lyi) * p.W + it.tx * kTile + lxi;
+    // one pseudo-receiver past the last: the rest of the range, for rays that
+    // stop in it after the last receiver
+    const bool tail = __any_sync(0xffffffffu, pending);
+    for (uint32_t rb = it.R0; rb < it.R1 || (tail && rb == it.R1); rb += kRecv) {
+      const int rc = (int)min((uint32_t)kRecv, it.R1 - min(rb, it.R1));
+      if (rc > 0) stage_receivers(p, S, st, rb, rc);
+      const int steps = rc + (tail && rb + kRecv >= it.R1 ? 1 : 0);
+      for (int jj = 0; jj < steps; ++jj) {
+        const bool real = jj < rc;
+        if (st.live) walk_to(p, S, st, real ? S.rk[jj] : st.C1, ly, ain, q, P);
+        if (!real) break;
+        const float4 r1 = S.r1[jj];
+        const uint32_t box = __float_as_uint(r1.w);
+        float den0 = 0.f, den1 = 0.f, num = 0.f;
+        if (box) {
+          const float4 r0 = S.r0[jj];
+          const float dx = st.lx - r0.x;
+          const float sx = (r0.z * dx) * dx, v = r1.x * dx;
+          if (box & 0x3u) recv_half<true, 0>(ly, P, r0.y, r0.w, v, sx, r1.y, num, den0);
+          if (box & 0xCu) recv_half<true, 1>(ly, P, r0.y, r0.w, v, sx, r1.y, num, den1);
+        }
+        finish_receiver(p, S, lane, rb, jj, rc, num, den0, den1);
+      }
+    }
+    // where each ray ended (the backward starts from it): rays that stopped in
+    // this segment, and those that ran through every segment without
+    // stopping, written by the tile's last segment
+    __syncwarp();
+#pragma unroll
+    for (int i = 0; i < kPx; ++i) {
+      const uint32_t lim = S.xlim[32 * i + lane];
+      if (lim != 0u || (it.last && i < it.rows_in && P[i] >= kShadowStop)) {
+        p.light_final[st.pix0 + (size_t)2 * i * p.W] = P[i];
+        p.light_stop[st.pix0 + (size_t)2 * i * p.W] = lim != 0u ? lim : kNoStop;
       }
     }
   }
@@ -494,43 +912,63 @@ __global__ void __launch_bounds__(256) k_camera(CamParams p) {
 // Launch order of a splat's tiles: longest list first, so that the last
 // blocks to start are the short ones and the final partial wave stays short
 // (a longest-processing-time-first schedule).  One block: a counting sort on
-// the list length in steps of 8 (1024 buckets; longer lists share the first),
-// placed by shared-memory atomics.  The order within a bucket may vary from
-// run to run; no result depends on it, since every tile writes only its own
-// outputs.
+// a key of the list length (1024 buckets, the largest first), placed by
+// shared-memory atomics.  The key is the length in steps of 8 (longer lists
+// share the top bucket), or with seg_len > 0 the tile's number of shadow
+// segments, seg_count(length); then lvl_off[s] (s = 0..1024) also receives
+// the first work item of segment level s: the number of segments of levels
+// below s, level s holding every tile with more than s segments (a prefix of
+// the order).  The order within a bucket may vary from run to run; no result
+// depends on it.
 __global__ void __launch_bounds__(1024) k_tile_order(const uint32_t* __restrict__ tile_start, int ntiles,
-                                                     uint32_t* __restrict__ order) {
+                                                     uint32_t* __restrict__ order, uint32_t seg_len,
+                                                     uint32_t* __restrict__ lvl_off) {
   constexpr int kBuckets = 1024;
   __shared__ uint32_t cnt[kBuckets];
   __shared__ uint32_t wsum[32];
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   auto bucket = [&](int i) {
     const uint32_t len = tile_start[i + 1] - tile_start[i];
-    return (uint32_t)(kBuckets - 1) - min(len >> 3, (uint32_t)(kBuckets - 1));  // longest first
+    const uint32_t key = seg_len ? seg_count(len) : min(len >> 3, (uint32_t)(kBuckets - 1));
+    return (uint32_t)(kBuckets - 1) - key;  // largest key first
+  };
+  // exclusive scan of one value per thread over the block
+  auto block_scan = [&](uint32_t c) -> uint32_t {
+    uint32_t x = c;
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+      uint32_t v = wsum[lane];
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += y;
+      }
+      wsum[lane] = v;
+    }
+    __syncthreads();
+    const uint32_t r = (warp ? wsum[warp - 1] : 0u) + x - c;
+    __syncthreads();  // wsum is free for the next scan
+    return r;
   };
   cnt[t] = 0u;
   __syncthreads();
   for (int i = t; i < ntiles; i += blockDim.x) atomicAdd(&cnt[bucket(i)], 1u);
   __syncthreads();
-  // exclusive scan of the 1024 bucket counts (thread t owns bucket t)
-  const uint32_t c = cnt[t];
-  uint32_t x = c;
-  for (int o = 1; o < 32; o <<= 1) {
-    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-    if (lane >= o) x += y;
-  }
-  if (lane == 31) wsum[warp] = x;
+  const uint32_t before = block_scan(cnt[t]);  // tiles in buckets < t: key > 1023 - t
   __syncthreads();
-  if (warp == 0) {
-    uint32_t w = wsum[lane];
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
-      if (lane >= o) w += y;
-    }
-    wsum[lane] = w;
-  }
+  cnt[t] = before;
   __syncthreads();
-  cnt[t] = (warp ? wsum[warp - 1] : 0u) + x - c;
+  if (lvl_off) {
+    // level s holds the tiles with more than s segments: cnt[1023 - s] of them
+    const uint32_t c = t < kBuckets - 1 ? cnt[kBuckets - 1 - t] : 0u;
+    const uint32_t off = block_scan(c);
+    lvl_off[t] = off;
+    if (t == kBuckets - 1) lvl_off[kBuckets] = off + c;
+  }
   __syncthreads();
   for (int i = t; i < ntiles; i += blockDim.x) order[atomicAdd(&cnt[bucket(i)], 1u)] = (uint32_t)i;
 }
@@ -540,9 +978,11 @@ __global__ void __launch_bounds__(1024) k_tile_order(const uint32_t* __restrict_
 void launch_tile_order(const FrameArgs& f, int splat, cudaStream_t s) {
   const Workspace& L = *f.L;
   uint32_t* order = at<uint32_t>(f.ws, L.tile_order[splat]);
-  k_tile_order<<<1, 1024, 0, s>>>(at<uint32_t>(f.ws, L.sp[splat].tile_start), L.ntiles, order);
+  k_tile_order<<<1, 1024, 0, s>>>(at<uint32_t>(f.ws, L.sp[splat].tile_start), L.ntiles, order, 0u, nullptr);
   count_launch();
 }
+
+size_t shadow_seg_items(int ntiles, size_t cap) { return (size_t)ntiles + cap / kSegLen + 1; }
 
 void launch_shadow_composite(const FrameArgs& f, cudaStream_t s) {
   const SplatBufs& b = f.L->sp[1];
@@ -551,18 +991,31 @@ void launch_shadow_composite(const FrameArgs& f, cudaStream_t s) {
   // the non-final tile-sort buffers are free after the sort: depth per entry, occluder bound
   float* dl = at<float>(ws, b.tk[1 - fin]);
   uint32_t* kb = at<uint32_t>(ws, b.tv[1 - fin]);
-  const uint32_t* header = at<uint32_t>(ws, f.L->header);
+  uint32_t* header = at<uint32_t>(ws, f.L->header);
+  const int nsm = device_sm_count();
   int blocks = (int)((f.L->cap + 255) / 256);
-  if (blocks > device_sm_count() * 16) blocks = device_sm_count() * 16;
+  if (blocks > nsm * 16) blocks = nsm * 16;
   // the depth sort's four passes leave the keys in rank order in sk[1]
   k_gather_depth<<<blocks, 256, 0, s>>>(at<uint32_t>(ws, b.tv[fin]), at<uint32_t>(ws, b.sk[1]), header, dl,
                                         (uint32_t)f.L->cap);
   k_occluder_bound<<<blocks, 256, 0, s>>>(at<uint32_t>(ws, b.tk[fin]), at<uint32_t>(ws, b.tile_start), dl, header,
                                           f.opts.shadow_bias, kb, (uint32_t)f.L->cap);
   count_launch(2);
-  launch_tile_order(f, 1, s);
+  // the light tiles by segment count, and the work items of each segment level
+  uint32_t* lvl = at<uint32_t>(ws, f.L->seg_lvl);
+  uint32_t* ticket = lvl + kSegLevels + 1;
+  uint32_t* flags = at<uint32_t>(ws, f.L->seg_flag);
+  cudaMemsetAsync(ticket, 0, 12, s);
+  cudaMemsetAsync(flags, 0, 4 * shadow_seg_items(f.L->ntiles, f.L->cap), s);
+  k_tile_order<<<1, 1024, 0, s>>>(at<uint32_t>(ws, b.tile_start), f.L->ntiles, at<uint32_t>(ws, f.L->tile_order[1]),
+                                  kSegLen, lvl);
+  count_launch();
   ShadowParams p;
   p.tile_order = at<uint32_t>(ws, f.L->tile_order[1]);
+  p.lvl_off = lvl;
+  p.ticket = ticket;
+  p.pub_a = at<float>(ws, f.L->seg_pub);
+  p.pub_flag = flags;
   p.list = at<uint32_t>(ws, b.tv[fin]);
   p.tile_start = at<uint32_t>(ws, b.tile_start);
   p.rrec = at<SplatRec>(ws, b.rrec);
@@ -572,15 +1025,34 @@ void launch_shadow_composite(const FrameArgs& f, cudaStream_t s) {
   p.partial = at<float2>(ws, f.L->partial);
   p.light_final = at<float>(ws, f.L->light_final);
   p.light_stop = at<uint32_t>(ws, f.L->light_stop);
+  p.status = header + H_STATUS;
   p.W = f.L->width; p.H = f.L->height; p.gx = f.L->gx;
   p.amax = f.opts.alpha_max;
   static DeviceOnce once;
+  static int per_sm[kMaxDevices][2];
   once.run([] {
-    return cudaFuncSetAttribute(k_shadow, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                (int)cudaSharedmemCarveoutMaxShared) == cudaSuccess;
+    int d = 0;
+    cudaGetDevice(&d);
+    bool ok = cudaFuncSetAttribute(k_shadow, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                   (int)cudaSharedmemCarveoutMaxShared) == cudaSuccess &&
+              cudaFuncSetAttribute(k_shadow_chain, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                   (int)cudaSharedmemCarveoutMaxShared) == cudaSuccess;
+    if (d >= 0 && d < kMaxDevices) {
+      ok = ok && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[d][0], k_shadow_chain, kSegWarps * 32, 0) ==
+                     cudaSuccess &&
+           cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[d][1], k_shadow, kSegWarps * 32, 0) == cudaSuccess;
+    }
+    return ok;
   });
-  k_shadow<<<f.L->ntiles, kShadowThreads, 0, s>>>(p);
-  count_launch();
+  int d = 0;
+  cudaGetDevice(&d);
+  const int bc = d >= 0 && d < kMaxDevices && per_sm[d][0] > 0 ? per_sm[d][0] : 1;
+  const int br = d >= 0 && d < kMaxDevices && per_sm[d][1] > 0 ? per_sm[d][1] : 1;
+  // persistent warps: every resident warp slot takes segments from a ticket
+  k_shadow_chain<<<nsm * bc, kSegWarps * 32, 0, s>>>(p);
+  k_shadow<<<nsm * br, kSegWarps * 32, 0, s>>>(p);
+  k_shadow_dead<<<nsm * 6, kDeadWarps * 32, 0, s>>>(p);
+  count_launch(3);
 }
 
 void launch_shadow_reduce(const FrameArgs& f, cudaStream_t s) {

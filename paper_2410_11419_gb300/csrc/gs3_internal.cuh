@@ -71,6 +71,9 @@ struct Workspace {
   size_t light_stop = 0;   // u32[HW] 1 + list index of the occluder that stopped the ray, or all ones
   size_t shadow_den = 0;   // float[N] sum of beta per Gaussian (by index)
   size_t tile_order[2] = {0, 0};  // u32[ntiles] per splat: tiles by decreasing list length (launch order)
+  size_t seg_lvl = 0;   // u32[1025 + 3]: shadow work items per segment level, then three ticket counters
+  size_t seg_flag = 0;  // u32[items]: shadow segment publications (0 none, 1 done, 2 done and all stopped)
+  size_t seg_pub = 0;   // float[items][256]: the products each shadow segment hands to the next
   int n = 0, width = 0, height = 0, gx = 0, gy = 0, ntiles = 0;
   size_t cap = 0;
   int nb_n = 0;    // radix blocks over N
@@ -165,6 +168,8 @@ void launch_prep(const FrameArgs& f, cudaStream_t s);
 void launch_depth_sort(const FrameArgs& f, int splat, cudaStream_t s);
 void launch_binning(const FrameArgs& f, int splat, cudaStream_t s);
 void launch_shadow_composite(const FrameArgs& f, cudaStream_t s);
+// shadow composite work items (tile segments) a frame can have at most
+size_t shadow_seg_items(int ntiles, size_t cap);
 // a splat's tiles ordered longest list first (in length steps of 8), into L.tile_order[splat]
 void launch_tile_order(const FrameArgs& f, int splat, cudaStream_t s);
 void launch_shadow_reduce(const FrameArgs& f, cudaStream_t s);
