@@ -407,7 +407,7 @@ __device__ __forceinline__ bool next_item(uint32_t* ticket, uint32_t total, int 
 // K6a: A(C_s+1) of every segment but a tile's last, chained from A(C_s).
 // Step 1 (the range's products Q) runs before the chain is known, so the
 // segments of a list run side by side and only the combination is chained.
-__global__ void __launch_bounds__(kSegWarps * 32, 5) k_shadow_chain(ShadowParams p) {
+__global__ void __launch_bounds__(kSegWarps * 32, 4) k_shadow_chain(ShadowParams p) {
   __shared__ ShadowSmem smem[kSegWarps];
   ShadowSmem& S = smem[threadIdx.x >> 5];
   const int lane = threadIdx.x & 31;
@@ -654,7 +654,7 @@ __global__ void __launch_bounds__(kDeadWarps * 32, 6) k_shadow_dead(ShadowParams
 
 // K6b: the receivers of every segment, with the products P = A(C_s) q, q the
 // running product of the range's occluders; A(C_s) comes from K6a.
-__global__ void __launch_bounds__(kSegWarps * 32, 5) k_shadow(ShadowParams p) {
+__global__ void __launch_bounds__(kSegWarps * 32, 4) k_shadow(ShadowParams p) {
   __shared__ ShadowSmem smem[kSegWarps];
   ShadowSmem& S = smem[threadIdx.x >> 5];
   SegState st;
