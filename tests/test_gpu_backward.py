@@ -4,9 +4,12 @@ differences of the C oracle in test_oracle_grad.py).
 
 Both sides get the same dL/d(image): that of L = 0.8 L1 + 0.2 (1 - SSIM)
 (Sec. 4.4) at the oracle's image.  Per parameter group the GPU gradient
-must satisfy ||g - o|| <= 2e-3 ||o|| (FP32 accumulation over thousands of
-pixels and Gaussians) and, element-wise, |g - o| <= 2e-3 max|o| + 1e-2 |o|.
-Measured relative norm errors are 1e-7 to 1e-6 per group."""
+must satisfy ||g - o|| <= 1e-4 ||o|| (FP32 accumulation over thousands of
+pixels and Gaussians) and, element-wise, |g - o| <= 1e-4 max|o| + 1e-3 |o|.
+Measured relative norm errors are recorded per group in $GS3_PARITY_STATS."""
+import json
+import os
+
 import numpy as np
 import pytest
 
@@ -14,7 +17,7 @@ from paper_2410_11419_gb300 import synth
 
 pytestmark = pytest.mark.gpu
 
-REL_NORM, REL_MAX = 2e-3, 2e-3
+REL_NORM, REL_MAX, REL_ELEM = 1e-4, 1e-4, 1e-3
 
 
 def _gpu_grads(scene, cam, light, dimg, ablate=0):
@@ -50,7 +53,7 @@ def _as_ref_layout(scene, ref):
     return lay
 
 
-def _compare(gpu, ref, skip=()):
+def _compare(gpu, ref, skip=(), case=""):
     report = {}
     for kname, o in ref.items():
         if kname in skip:
@@ -63,8 +66,12 @@ def _compare(gpu, ref, skip=()):
             assert np.abs(g).max() < 1e-12, kname
             continue
         assert err <= REL_NORM * no, f"{kname}: relative norm error {err / no:.2e}"
-        bad = np.abs(g - o) > REL_MAX * np.abs(o).max() + 1e-2 * np.abs(o)
+        bad = np.abs(g - o) > REL_MAX * np.abs(o).max() + REL_ELEM * np.abs(o)
         assert not bad.any(), f"{kname}: {bad.sum()} elements off, worst {np.abs(g - o).max():.3e}"
+    path = os.environ.get("GS3_PARITY_STATS")
+    if path:
+        with open(path, "a") as fh:
+            fh.write(json.dumps({"test": f"backward[{case}]", "rel_norm": report}) + "\n")
     return report
 
 
@@ -72,7 +79,9 @@ def _compare(gpu, ref, skip=()):
     (lambda: synth.make_scene(21, 500, 4, "ball"), 64, 21),
     (lambda: synth.tiny_scene(0), 96, 3),
     (lambda: synth.paper_mlp_scene(5, n=800, k=2), 80, 8),
-], ids=["fd500_64", "tiny_96", "paper_mlp_80"])
+    # 20k-Gaussian shell (K = 8, 3x128) at 256^2: long light lists, segments of open rays
+    (lambda: synth.object_scene(2, n=20000), 256, 7),
+], ids=["fd500_64", "tiny_96", "paper_mlp_80", "shell_20k_256"])
 def test_backward_matches_gradient_oracle(gs3, oracle, make, res, seed):
     from oracle import torch_ref as TR
     scene = make()
@@ -82,7 +91,7 @@ def test_backward_matches_gradient_oracle(gs3, oracle, make, res, seed):
     dimg, _ = TR.image_grad_of_loss(fr["img"], target)
     ref, _ = TR.grads_given_image_grad(scene, cam, light, dimg)
     gpu = _gpu_grads(scene, cam, light, dimg)
-    rep = _compare(gpu, _as_ref_layout(scene, ref))
+    rep = _compare(gpu, _as_ref_layout(scene, ref), case=f"{scene.n}_{res}")
     assert len(rep) == 14
 
 
