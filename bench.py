@@ -93,6 +93,9 @@ def parse():
     ap.add_argument("--served-frames", type=int, default=100,
                     help="frames the served arm times (at least --steps)")
     ap.add_argument("--inflight", type=int, default=4, help="server in-flight slots (served arm)")
+    ap.add_argument("--max-batch", type=int, default=1, help="requests a server slot renders together")
+    ap.add_argument("--batched-arm", default="2x4",
+                    help="slots x batch of the batched served arm timed beside the headline ('' to skip)")
     ap.add_argument("--no-serve", action="store_true", help="time single frames only")
     ap.add_argument("--no-mix", action="store_true", help="skip the mixed-scene serving measurement")
     ap.add_argument("--no-ksweep", action="store_true", help="skip the lobe-count sweep")
@@ -353,7 +356,7 @@ def serving_mix(a, dev, np, torch, N, R, synth):
     views = [synth.camera_light_pair(1000 + i, res, res) for i, (_, res) in enumerate(reqs)]
     outs = [torch.empty((res, res, 3), device=dev) for _, res in reqs]
     ds = [R.DeviceScene(sc, device=dev, mlp_dtype=N.GS3_MLP_BF16) for sc in scenes]
-    srv = R.Server(hbm_budget=96 << 30, max_inflight=a.inflight, device=dev.index or 0)
+    srv = R.Server(hbm_budget=96 << 30, max_inflight=a.inflight, device=dev.index or 0, max_batch=a.max_batch)
     ids = [srv.add_scene(d) for d in ds]
     for si in range(len(scenes)):  # learn every (scene, resolution) capacity, warm the pool
         for res in MIX_RES:
@@ -421,7 +424,7 @@ def serving_mix(a, dev, np, torch, N, R, synth):
             lat[i] = fin - arr[i]
         one[str(rate)] = {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99))}
     return {"scenes": [s.n for s in scenes], "resolutions": list(MIX_RES), "requests_per_rate": nreq,
-            "inflight_slots": a.inflight, "served_bf16": served, "one_at_a_time_fp32": one,
+            "inflight_slots": a.inflight, "max_batch": a.max_batch, "served_bf16": served, "one_at_a_time_fp32": one,
             "note": "served: host wall clock from the first arrival to the last completion; latency "
                     "submit to completion. one_at_a_time: CUDA-event service times, latency from a FIFO "
                     "recursion over the same Poisson arrivals"}
@@ -572,13 +575,14 @@ def main():
     e2e_val = replicas.whole_job_rate(K, e2e_s, world)
 
     # ---- served arm: continuous batching through the server (headline) ----
-    served = None
-    if not a.no_serve:
+    def serve(slots, batch):
+        """Frames/s of the server over RS frames (CUDA-event span), then the
+        latency of open-loop Poisson arrivals at 80 % of that rate."""
         RS = max(K, a.served_frames)
-        srv = R.Server(hbm_budget=48 << 30, max_inflight=a.inflight, device=local)
+        srv = R.Server(hbm_budget=48 << 30, max_inflight=slots, device=local, max_batch=batch)
         sid = srv.add_scene(ds)
-        outs = [torch.empty((a.res, a.res, 3), device=dev) for _ in range(a.inflight + 2)]
-        for i in range(2 * a.inflight):  # warm the capacity estimate and the memory pool
+        outs = [torch.empty((a.res, a.res, 3), device=dev) for _ in range(slots * max(1, batch) + 2)]
+        for i in range(2 * slots * max(1, batch)):  # warm the capacity estimate and the memory pool
             cam, light = pairs[i % 100]
             srv.wait(srv.submit(sid, cam, light, outs[i % len(outs)]))
         srv.reset_counters()
@@ -595,7 +599,6 @@ def main():
         st = srv.stats()
         span_ms = replicas.max_over_ranks(st.device_span_ms, dev)
         rate = RS / (span_ms / 1e3)
-        # latency under load: open-loop Poisson arrivals at 80 % of the served rate
         rng = np.random.default_rng(1234)
         lam = 0.8 * rate
         gaps = rng.exponential(1.0 / lam, RS)
@@ -608,14 +611,24 @@ def main():
             cam, light = pairs[(a.warmup + 7 * s_) % 100]
             lat_t.append(srv.submit(sid, cam, light, outs[s_ % len(outs)]))
         lats = np.array([srv.wait(t)[1] for t in lat_t])
-        served = {"value": world * rate, "frames": RS, "device_span_ms": span_ms, "wall_s": served_wall,
-                  "inflight_slots": a.inflight, "max_in_flight": int(st.max_in_flight),
-                  "retries": int(st.retries), "failed": int(sum(1 for b in bad if b != 0)),
-                  "latency_open_loop": {"rate_rps": lam, "requests": RS,
-                                        "p50_ms": float(np.percentile(lats, 50)),
-                                        "p99_ms": float(np.percentile(lats, 99)),
-                                        "clock": "host, submit to completion"}}
         srv.close()
+        return {"value": world * rate, "frames": RS, "device_span_ms": span_ms, "wall_s": served_wall,
+                "inflight_slots": slots, "max_batch": batch, "batches": int(st.batches),
+                "largest_batch": int(st.max_batch), "max_in_flight": int(st.max_in_flight),
+                "retries": int(st.retries), "failed": int(sum(1 for b in bad if b != 0)),
+                "latency_open_loop": {"rate_rps": lam, "requests": RS,
+                                      "p50_ms": float(np.percentile(lats, 50)),
+                                      "p99_ms": float(np.percentile(lats, 99)),
+                                      "clock": "host, submit to completion"}}
+
+    served = served_batched = None
+    if not a.no_serve:
+        served = serve(a.inflight, a.max_batch)
+        if a.batched_arm:
+            bs_, bb_ = (int(x) for x in a.batched_arm.split("x"))
+            served_batched = serve(bs_, bb_)
+            served_batched["note"] = ("batches of requests rendered together: per-frame stages on sub-streams, "
+                                      "the shadow and camera composites over the batch in single launches")
 
     # ---- FP32 plain comparison arm (one request at a time, FP32 MLPs) ----
     plain = None
@@ -761,6 +774,7 @@ def main():
         "alu_peak": {"ffma_tflops": ffma_tflops, "ex2_gops": ex2_gops},
         "p50_ms": p50, "p99_ms": p99,
         "served": served,
+        "served_batched": served_batched,
         "single_frame": single,
         "stages_ms": {k: round(v, 4) for k, v in stage_ms.items()},
         "pairs_per_frame": {"camera": float(np.mean(per_step_cam_P)),

@@ -311,14 +311,19 @@ gs3_status gs3_adam_step(float *param, const float *grad, float *m, float *v, si
 
 /* ---- Continuous-batching server -----------------------------------------
  * Serving form of gs3_render (no counterpart in the paper, which renders one
- * frame at a time): a worker thread admits queued (scene, camera, light)
- * requests while an in-flight slot is free and the request's workspace fits
- * in the HBM budget, and runs each admitted frame on its slot's own stream, so
- * requests that arrive while others are on the GPU overlap with them.  The
+ * frame at a time): a worker thread keeps a queue of (scene, camera, light)
+ * requests and max_inflight slots.  A free slot takes up to max_batch
+ * requests from the head of the queue whose workspaces fit in the HBM budget
+ * and renders them as one batch: each frame's shading, projections and
+ * binning on its own sub-stream, then the shadow composite's persistent
+ * segment kernels and the camera composite over every frame of the batch in
+ * single launches.  Requests that arrive while batches are on the GPU join
+ * the next free slot's batch; the slots' batches overlap on the device.  Each
+ * frame equals the same frame rendered alone by gs3_render, bit for bit.  The
  * workspace capacity is estimated per (scene, resolution) from the pair
  * counts seen so far; a request that overflows it is re-admitted once with
  * the exact count.  Latency is measured from gs3_server_submit to the
- * completion of the request's work on the GPU. */
+ * completion of the request's batch on the GPU. */
 enum { GS3_REQ_QUEUED = 0, GS3_REQ_RUNNING = 1, GS3_REQ_DONE = 2, GS3_REQ_FAILED = 3 };
 
 typedef struct {
@@ -328,13 +333,17 @@ typedef struct {
     int32_t inject_alloc_failures; /* testing: fail this many workspace allocations (0 in use) */
     float initial_pairs;           /* first-request capacity guess: pairs per Gaussian at 800x800,
                                       scaled with the pixel count (0: 64) */
+    int32_t max_batch;             /* requests rendered together by one slot, 1..8 (0: 1: every
+                                      request alone on its slot's streams) */
 } gs3_server_opts;
 
 typedef struct {
     uint64_t completed, failed, retries, queued, in_flight, max_in_flight;
     uint64_t bytes_in_use, peak_bytes_in_use;
-    double device_span_ms; /* CUDA-event time from the first admitted frame's start to the
-                              last completed frame's end since the last reset */
+    double device_span_ms; /* CUDA-event time from the first admitted batch's start to the
+                              last completed batch's end since the last reset */
+    uint64_t batches;      /* batches launched */
+    uint64_t max_batch;    /* the most requests one batch held */
 } gs3_server_counters;
 
 typedef struct gs3_server gs3_server;
@@ -437,6 +446,24 @@ gs3_status gs3_selftest_wait_timeout(uint32_t n, uint32_t *status_out);
  * and frees a small output buffer).  Errors: INVALID_ARG (null output,
  * repeats outside [1, 100]), CUDA. */
 gs3_status gs3_measure_alu_peak(int32_t repeats, double *ffma_tflops, double *ex2_gops);
+
+/* Not an operation of the paper either: a check that the shadow composite's
+ * chain of segment products gives up instead of holding the GPU when a
+ * predecessor never publishes.  Runs the frame's shading, projections and
+ * light binning (the checks and workspace of gs3_render_stages), then the
+ * chain kernel with its work tickets starting past every tile's first
+ * segment, so that the waits of every second segment can never end: each
+ * gives up after its poll bound (well under a second), records
+ * GS3_ERR_TIMEOUT and publishes its rays as stopped.
+ *   status_out: host, one uint32: the workspace's status word afterwards,
+ *               GS3_ERR_TIMEOUT when the bounded waits work (a frame whose
+ *               light tiles all hold one segment has nothing to wait for)
+ * Synchronous (synchronises the device); the context stays usable.  Errors:
+ * as gs3_render_stages, INVALID_ARG for a null status_out or a shadow-splat
+ * ablation, CUDA. */
+gs3_status gs3_selftest_shadow_wait(gs3_scene *scene, const gs3_camera *camera, const gs3_light *light,
+                                    const gs3_render_opts *opts, void *workspace, size_t workspace_bytes,
+                                    size_t key_capacity, uint32_t *status_out);
 
 /* Number of CUDA kernels this library has launched in this process (all
  * threads, all devices); a host-side counter for launch accounting. */

@@ -101,13 +101,13 @@ class gs3_server(C.Structure):
 
 class gs3_server_opts(C.Structure):
     _fields_ = [("hbm_budget", C.c_size_t), ("max_inflight", C.c_int32), ("device", C.c_int32),
-                ("inject_alloc_failures", C.c_int32), ("initial_pairs", C.c_float)]
+                ("inject_alloc_failures", C.c_int32), ("initial_pairs", C.c_float), ("max_batch", C.c_int32)]
 
 
 class gs3_server_counters(C.Structure):
     _fields_ = [(f, C.c_uint64) for f in ("completed", "failed", "retries", "queued", "in_flight",
                                           "max_in_flight", "bytes_in_use", "peak_bytes_in_use")] + [
-        ("device_span_ms", C.c_double)]
+        ("device_span_ms", C.c_double), ("batches", C.c_uint64), ("max_batch", C.c_uint64)]
 
 
 GS3_REQ_QUEUED, GS3_REQ_RUNNING, GS3_REQ_DONE, GS3_REQ_FAILED = 0, 1, 2, 3
@@ -157,6 +157,9 @@ SIGNATURES = {
     "gs3_server_destroy": (C.c_int, [_SERVER_P]),
     "gs3_depth_order_static": (C.c_int, [C.c_void_p, C.c_uint32, C.c_void_p, C.c_void_p]),
     "gs3_selftest_wait_timeout": (C.c_int, [C.c_uint32, C.POINTER(C.c_uint32)]),
+    "gs3_selftest_shadow_wait": (C.c_int, [_SCENE_P, C.POINTER(gs3_camera), C.POINTER(gs3_light),
+                                           C.POINTER(gs3_render_opts), C.c_void_p, C.c_size_t, C.c_size_t,
+                                           C.POINTER(C.c_uint32)]),
     "gs3_kernel_launches": (C.c_uint64, []),
     "gs3_measure_alu_peak": (C.c_int, [C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "gs3_last_error": (C.c_char_p, []),
@@ -294,9 +297,9 @@ def gs3_workspace_read_header(workspace, stream: int) -> gs3_ws_header:
 
 
 def gs3_server_create(hbm_budget: int, max_inflight: int, device: int = 0,
-                      inject_alloc_failures: int = 0, initial_pairs: float = 0.0):
+                      inject_alloc_failures: int = 0, initial_pairs: float = 0.0, max_batch: int = 0):
     out = _SERVER_P()
-    o = gs3_server_opts(hbm_budget, max_inflight, device, inject_alloc_failures, initial_pairs)
+    o = gs3_server_opts(hbm_budget, max_inflight, device, inject_alloc_failures, initial_pairs, max_batch)
     _check(lib().gs3_server_create(C.byref(o), C.byref(out)), "gs3_server_create")
     return out
 
@@ -358,6 +361,14 @@ def gs3_selftest_wait_timeout(n: int) -> int:
     """The status word of a look-back sort pass whose waits can never end."""
     out = C.c_uint32(0)
     _check(lib().gs3_selftest_wait_timeout(n, C.byref(out)), "gs3_selftest_wait_timeout")
+    return int(out.value)
+
+
+def gs3_selftest_shadow_wait(scene, cam, light, opts, workspace, ws_bytes: int, cap: int) -> int:
+    """The workspace status after a shadow chain whose predecessors never publish."""
+    out = C.c_uint32(0)
+    _check(lib().gs3_selftest_shadow_wait(scene, C.byref(cam), C.byref(light), C.byref(opts), _ptr(workspace),
+                                          ws_bytes, cap, C.byref(out)), "gs3_selftest_shadow_wait")
     return int(out.value)
 
 

@@ -445,6 +445,120 @@ gs3_status render_frame(gs3_scene* scene, const gs3_camera* cam, const gs3_light
   return GS3_OK;
 }
 
+bool BatchStreams::create(int n) {
+  if (cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&fork2, cudaEventDisableTiming) != cudaSuccess)
+    return false;
+  for (int r = 0; r < n; ++r) {
+    if (cudaStreamCreateWithFlags(&sub[r], cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&join[r], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&join2[r], cudaEventDisableTiming) != cudaSuccess)
+      return false;
+  }
+  return true;
+}
+
+void BatchStreams::destroy() {
+  for (int r = 0; r < 8; ++r) {
+    if (sub[r]) cudaStreamDestroy(sub[r]);
+    if (join[r]) cudaEventDestroy(join[r]);
+    if (join2[r]) cudaEventDestroy(join2[r]);
+    sub[r] = nullptr;
+    join[r] = join2[r] = nullptr;
+  }
+  if (fork) cudaEventDestroy(fork);
+  if (fork2) cudaEventDestroy(fork2);
+  fork = fork2 = nullptr;
+}
+
+// A batch of frames rendered together (the serving form; each frame has its
+// own workspace and equals the same frame rendered alone, bit for bit):
+//   1. per frame, on its own sub-stream: header reset, shading and both
+//      projections (K1), the light binning and the shadow composite's
+//      per-frame set-up (occluder bounds, segment plan), then the camera
+//      binning, which runs beside step 2;
+//   2. on `stream`: the shadow composite's three persistent segment kernels
+//      over every segment of every frame, from shared tickets;
+//   3. per frame, on its sub-stream again: the shadow reduce and the MLPs;
+//   4. on `stream`: one camera composite over every frame's tiles.
+gs3_status render_batch(const BatchFrame* frames, int n, cudaStream_t s, BatchStreams& bs,
+                        unsigned char* param_dev, unsigned char* param_host) {
+  if (n < 1 || n > kMaxBatch) return fail(GS3_ERR_INVALID_ARG, "render_batch: 1 <= n <= 8 frames");
+  Workspace L[kMaxBatch];
+  FrameArgs f[kMaxBatch];
+  for (int r = 0; r < n; ++r) {
+    const BatchFrame& b = frames[r];
+    if (!b.scene || !b.out || !b.ws || b.opts.tile != kTile || b.cam.width < 1 || b.cam.height < 1 ||
+        b.cam.width > 16384 || b.cam.height > 16384 || !(b.cam.fx > 0.f) || !(b.cam.fy > 0.f))
+      return fail(GS3_ERR_INVALID_ARG, "render_batch: bad frame");
+    if (light_problem(b.light, b.opts)) return fail(GS3_ERR_INVALID_ARG, light_problem(b.light, b.opts));
+    L[r] = plan_workspace(b.scene->dev.n, b.cam.width, b.cam.height, b.cap);
+    if (b.ws_bytes < L[r].total || reinterpret_cast<uintptr_t>(b.ws) % 256 != 0)
+      return fail(GS3_ERR_INVALID_ARG, "render_batch: workspace too small or misaligned");
+    f[r].sc = b.scene->dev;
+    f[r].cam = b.cam;
+    f[r].light = b.light;
+    f[r].opts = b.opts;
+    f[r].ws = static_cast<unsigned char*>(b.ws);
+    f[r].L = &L[r];
+  }
+  (void)cudaGetLastError();  // only this call's launches are checked below
+  // 1. per-frame stages beside one another: the light chain first (the batch's
+  //    shadow composite waits for it), then the camera binning, which runs on
+  //    beside the shadow composite
+  cudaEventRecord(bs.fork, s);
+  const FrameArgs* shadowed[kMaxBatch];
+  int ns = 0;
+  for (int r = 0; r < n; ++r) {
+    cudaStream_t sr = bs.sub[r];
+    cudaStreamWaitEvent(sr, bs.fork, 0);
+    cudaMemsetAsync(f[r].ws + L[r].header, 0, 4 * H_RESET_WORDS, sr);
+    launch_prep(f[r], sr);
+    if (!(f[r].opts.ablate & GS3_ABLATE_SHADOW_SPLAT)) {
+      launch_depth_sort(f[r], 1, sr);
+      launch_binning(f[r], 1, sr);
+      prepare_shadow_composite(f[r], sr);
+      shadowed[ns++] = &f[r];
+    }
+    cudaEventRecord(bs.join[r], sr);
+    launch_depth_sort(f[r], 0, sr);
+    launch_binning(f[r], 0, sr);
+    launch_tile_order(f[r], 0, sr);
+  }
+  for (int r = 0; r < n; ++r) cudaStreamWaitEvent(s, bs.join[r], 0);
+  // 2. the shadow composite of the whole batch
+  if (ns > 0) launch_shadow_composite_batch(shadowed, ns, param_dev, param_host, s);
+  // 3. per frame (after its camera binning): shadow average and the MLPs
+  cudaEventRecord(bs.fork2, s);
+  for (int r = 0; r < n; ++r) {
+    cudaStream_t sr = bs.sub[r];
+    cudaStreamWaitEvent(sr, bs.fork2, 0);
+    if (f[r].opts.ablate & GS3_ABLATE_SHADOW_SPLAT) launch_fill_shadow_one(f[r], sr);
+    else launch_shadow_reduce(f[r], sr);
+    const gs3_scene* sc = frames[r].scene;
+    if (sc->dev.mlp_dtype != GS3_MLP_FP32) {
+      launch_mlp(f[r], sr, /*identity_only=*/true);
+      const unsigned char* blobs[2] = {sc->tc_blob[0], sc->tc_blob[1]};
+      launch_mlp_tc(f[r], blobs, sr);
+    } else {
+      launch_mlp(f[r], sr);
+    }
+    cudaEventRecord(bs.join2[r], sr);
+  }
+  for (int r = 0; r < n; ++r) cudaStreamWaitEvent(s, bs.join2[r], 0);
+  // 4. the camera composite of the whole batch
+  const FrameArgs* all[kMaxBatch];
+  float* outs[kMaxBatch];
+  for (int r = 0; r < n; ++r) {
+    all[r] = &f[r];
+    outs[r] = frames[r].out;
+  }
+  launch_camera_composite_batch(all, outs, n, param_dev, param_host, s);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "render_batch: launch");
+  return GS3_OK;
+}
+
 }  // namespace gs3
 
 extern "C" {
@@ -524,6 +638,32 @@ gs3_status gs3_render_backward(gs3_scene* scene, const gs3_camera* cam, const gs
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "gs3_render_backward: launch");
   return GS3_OK;
+}
+
+gs3_status gs3_selftest_shadow_wait(gs3_scene* scene, const gs3_camera* cam, const gs3_light* light,
+                                    const gs3_render_opts* opts, void* workspace, size_t ws_bytes,
+                                    size_t key_capacity, uint32_t* status_out) {
+  if (!status_out) return fail(GS3_ERR_INVALID_ARG, "gs3_selftest_shadow_wait: null status_out");
+  if (opts && (opts->ablate & GS3_ABLATE_SHADOW_SPLAT))
+    return fail(GS3_ERR_INVALID_ARG, "gs3_selftest_shadow_wait: needs the shadow splat");
+  // shading, projections and the light binning, with the render's own checks
+  gs3_status st = render_frame(scene, cam, light, opts, reinterpret_cast<float*>(workspace), workspace, ws_bytes,
+                               key_capacity, GS3_STAGE_PREP | GS3_STAGE_LIGHT_BIN, 0, nullptr);
+  if (st != GS3_OK) return st;
+  Workspace L = plan_workspace(scene->dev.n, cam->width, cam->height, key_capacity);
+  FrameArgs f;
+  f.sc = scene->dev;
+  f.cam = *cam;
+  f.light = *light;
+  f.opts = *opts;
+  f.ws = static_cast<unsigned char*>(workspace);
+  f.L = &L;
+  launch_shadow_chain_selftest(f, 0);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e == cudaSuccess)
+    e = cudaMemcpy(status_out, static_cast<unsigned char*>(workspace) + L.header, 4, cudaMemcpyDeviceToHost);
+  return e == cudaSuccess ? GS3_OK : cuda_fail(e, "gs3_selftest_shadow_wait");
 }
 
 gs3_status gs3_adam_step(float* param, const float* grad, float* m, float* v, size_t n, float lr, float beta1,

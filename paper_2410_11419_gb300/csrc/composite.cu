@@ -407,18 +407,13 @@ __device__ __forceinline__ bool next_item(uint32_t* ticket, uint32_t total, int 
 // K6a: A(C_s+1) of every segment but a tile's last, chained from A(C_s).
 // Step 1 (the range's products Q) runs before the chain is known, so the
 // segments of a list run side by side and only the combination is chained.
-__global__ void __launch_bounds__(kSegWarps * 32, 4) k_shadow_chain(ShadowParams p) {
-  __shared__ ShadowSmem smem[kSegWarps];
-  ShadowSmem& S = smem[threadIdx.x >> 5];
-  const int lane = threadIdx.x & 31;
+__device__ __forceinline__ void chain_item(const ShadowParams& p, uint32_t w, ShadowSmem& S, int lane) {
   const int lxi = lane & 15, lyi = lane >> 4;
   const float lx = lxi + 0.5f, omin = 1.f - p.amax;
-  const uint32_t total = p.lvl_off[kSegLevels];
   const uint32_t ain = (uint32_t)__cvta_generic_to_shared(&S.ain[lane]);
-  uint32_t w;
-  while (next_item(p.ticket, total, lane, w)) {
+
     const SegItem it = seg_item(p, w, lane);
-    if (it.last) continue;  // nothing follows it
+    if (it.last) return;  // nothing follows it
     const float ox = (float)(it.tx * kTile), oy = (float)(it.ty * kTile);
     float ly[kPx];
 #pragma unroll
@@ -521,6 +516,42 @@ __global__ void __launch_bounds__(kSegWarps * 32, 4) k_shadow_chain(ShadowParams
     __syncwarp();
     if (lane == 0) st_release(p.pub_flag + w, any_out ? 1u : 2u);
   }
+
+// The work items of a batch of frames: the tickets run over every frame's
+// items in turn; locate() maps a ticket to its frame and the frame's item.
+__device__ __forceinline__ uint32_t batch_items(const ShadowParams* reqs, int nreq) {
+  uint32_t t = 0;
+  for (int r = 0; r < nreq; ++r) t += reqs[r].lvl_off[kSegLevels];
+  return t;
+}
+__device__ __forceinline__ int locate(const ShadowParams* reqs, int nreq, uint32_t& w) {
+  int r = 0;
+  for (; r < nreq - 1; ++r) {
+    const uint32_t t = reqs[r].lvl_off[kSegLevels];
+    if (w < t) break;
+    w -= t;
+  }
+  return r;
+}
+
+// One frame (p) or a batch of nreq frames (reqs, in device memory; p is the
+// first, whose tickets the batch shares).
+template <bool BATCH>
+__global__ void __launch_bounds__(kSegWarps * 32, 4) k_shadow_chain(const ShadowParams p, const ShadowParams* reqs,
+                                                                    int nreq) {
+  __shared__ ShadowSmem smem[kSegWarps];
+  ShadowSmem& S = smem[threadIdx.x >> 5];
+  const int lane = threadIdx.x & 31;
+  const uint32_t total = BATCH ? batch_items(reqs, nreq) : p.lvl_off[kSegLevels];
+  uint32_t w;
+  while (next_item(p.ticket, total, lane, w)) {
+    if (BATCH) {
+      const int r = locate(reqs, nreq, w);
+      chain_item(reqs[r], w, S, lane);
+    } else {
+      chain_item(p, w, S, lane);
+    }
+  }
 }
 
 // K6c: the receivers of the segments every ray of which stopped before the
@@ -575,21 +606,16 @@ __device__ __forceinline__ float dead_half_edge(const float4 e0, const float4 e1
   return den;
 }
 
-__global__ void __launch_bounds__(kDeadWarps * 32, 6) k_shadow_dead(ShadowParams p) {
-  __shared__ DeadSmem smem[kDeadWarps];
-  DeadSmem& D = smem[threadIdx.x >> 5];
-  const int lane = threadIdx.x & 31;
-  const uint32_t total = p.lvl_off[kSegLevels];
-  uint32_t w;
-  while (next_item(p.ticket + 2, total, lane, w)) {
+__device__ __forceinline__ void dead_item(const ShadowParams& p, uint32_t w, DeadSmem& D, int lane) {
+
     int lo = 0, hi = kSegLevels;  // the item's level: largest s with lvl_off[s] <= w
     while (hi - lo > 1) {
       const int mid = (lo + hi) >> 1;
       if (p.lvl_off[mid] <= w) lo = mid; else hi = mid;
     }
-    if (lo == 0) continue;  // a tile's first segment starts with every ray open
+    if (lo == 0) return;  // a tile's first segment starts with every ray open
     const uint32_t pos = w - p.lvl_off[lo];
-    if (__ldcg(p.pub_flag + p.lvl_off[lo - 1] + pos) != 2u) continue;  // not stopped: K6b's
+    if (__ldcg(p.pub_flag + p.lvl_off[lo - 1] + pos) != 2u) return;  // not stopped: K6b's
     const int tile = (int)p.tile_order[pos];
     const int tx = tile % p.gx, ty = tile / p.gx;
     const float ox = (float)(tx * kTile), oy = (float)(ty * kTile);
@@ -650,23 +676,35 @@ __global__ void __launch_bounds__(kDeadWarps * 32, 6) k_shadow_dead(ShadowParams
       }
     }
   }
+
+template <bool BATCH>
+__global__ void __launch_bounds__(kDeadWarps * 32, 6) k_shadow_dead(const ShadowParams p, const ShadowParams* reqs,
+                                                                    int nreq) {
+  __shared__ DeadSmem smem[kDeadWarps];
+  DeadSmem& D = smem[threadIdx.x >> 5];
+  const int lane = threadIdx.x & 31;
+  const uint32_t total = BATCH ? batch_items(reqs, nreq) : p.lvl_off[kSegLevels];
+  uint32_t w;
+  while (next_item(p.ticket + 2, total, lane, w)) {
+    if (BATCH) {
+      const int r = locate(reqs, nreq, w);
+      dead_item(reqs[r], w, D, lane);
+    } else {
+      dead_item(p, w, D, lane);
+    }
+  }
 }
 
 // K6b: the receivers of every segment, with the products P = A(C_s) q, q the
 // running product of the range's occluders; A(C_s) comes from K6a.
-__global__ void __launch_bounds__(kSegWarps * 32, 4) k_shadow(ShadowParams p) {
-  __shared__ ShadowSmem smem[kSegWarps];
-  ShadowSmem& S = smem[threadIdx.x >> 5];
+__device__ __forceinline__ void live_item(const ShadowParams& p, uint32_t w, ShadowSmem& S, int lane) {
   SegState st;
-  st.lane = threadIdx.x & 31;
-  const int lane = st.lane;
+  st.lane = lane;
   const int lxi = lane & 15, lyi = lane >> 4;
   st.lx = lxi + 0.5f;
   st.omin = 1.f - p.amax;
-  const uint32_t total = p.lvl_off[kSegLevels];
   const uint32_t ain = (uint32_t)__cvta_generic_to_shared(&S.ain[lane]);
-  uint32_t w;
-  while (next_item(p.ticket + 1, total, lane, w)) {
+
     const SegItem it = seg_item(p, w, lane);
     st.s = it.s;
     st.tx = it.tx;
@@ -683,7 +721,7 @@ __global__ void __launch_bounds__(kSegWarps * 32, 4) k_shadow(ShadowParams p) {
     float P[kPx];
     load_entering(p, it.s, it.wpred, fl_in, lane, it.rows_in, P);
     const bool dead = all_stopped(P);
-    if (dead) continue;  // K6c takes it
+    if (dead) return;  // K6c takes it
     // rays the publication has stop in this range (they must reach their stop)
     bool pending = false;
     float q[kPx];
@@ -738,6 +776,22 @@ __global__ void __launch_bounds__(kSegWarps * 32, 4) k_shadow(ShadowParams p) {
         p.light_final[st.pix0 + (size_t)2 * i * p.W] = P[i];
         p.light_stop[st.pix0 + (size_t)2 * i * p.W] = lim != 0u ? lim : kNoStop;
       }
+    }
+  }
+
+template <bool BATCH>
+__global__ void __launch_bounds__(kSegWarps * 32, 4) k_shadow(const ShadowParams p, const ShadowParams* reqs, int nreq) {
+  __shared__ ShadowSmem smem[kSegWarps];
+  ShadowSmem& S = smem[threadIdx.x >> 5];
+  const int lane = threadIdx.x & 31;
+  const uint32_t total = BATCH ? batch_items(reqs, nreq) : p.lvl_off[kSegLevels];
+  uint32_t w;
+  while (next_item(p.ticket + 1, total, lane, w)) {
+    if (BATCH) {
+      const int r = locate(reqs, nreq, w);
+      live_item(reqs[r], w, S, lane);
+    } else {
+      live_item(p, w, S, lane);
     }
   }
 }
@@ -833,10 +887,16 @@ struct CamParams {
   float amax, tstop;
 };
 
-__global__ void __launch_bounds__(256) k_camera(CamParams p) {
-  __shared__ float4 Ga[256], Gb[256], Gc[256], C0[256], C1[256];
-  __shared__ uint32_t Gmask[256];
-  const int tile = (int)p.tile_order[blockIdx.x];
+struct CamSmem {
+  float4 Ga[256], Gb[256], Gc[256], C0[256], C1[256];
+  uint32_t Gmask[256];
+};
+
+// Block blk of a frame: tile tile_order[blk] (longest list first).
+__device__ __forceinline__ void camera_tile(const CamParams& p, int blk, CamSmem& M) {
+  float4 *Ga = M.Ga, *Gb = M.Gb, *Gc = M.Gc, *C0 = M.C0, *C1 = M.C1;
+  uint32_t* Gmask = M.Gmask;
+  const int tile = (int)p.tile_order[blk];
   const int tx = tile % p.gx, ty = tile / p.gx;
   const int t = threadIdx.x;
   const uint32_t wbit = 1u << (t >> 5);
@@ -906,6 +966,21 @@ __global__ void __launch_bounds__(256) k_camera(CamParams p) {
     p.n_contrib[pix] = consumed;
     p.pix_aux[2 * pix] = make_float4(S0, S1, S2, Sh);
     p.pix_aux[2 * pix + 1] = make_float4(R0, R1, R2, 0.f);
+  }
+}
+
+// One frame (p), or a batch of nreq frames (reqs in device memory) whose
+// tiles follow one another: frame r owns blocks [tile_prefix[r], tile_prefix[r + 1]).
+template <bool BATCH>
+__global__ void __launch_bounds__(256) k_camera(const CamParams p, const CamParams* reqs, const uint32_t* tile_prefix,
+                                                int nreq) {
+  __shared__ CamSmem M;
+  if (BATCH) {
+    int r = 0;
+    while (r < nreq - 1 && blockIdx.x >= tile_prefix[r + 1]) ++r;
+    camera_tile(reqs[r], (int)(blockIdx.x - tile_prefix[r]), M);
+  } else {
+    camera_tile(p, (int)blockIdx.x, M);
   }
 }
 
@@ -984,7 +1059,104 @@ void launch_tile_order(const FrameArgs& f, int splat, cudaStream_t s) {
 
 size_t shadow_seg_items(int ntiles, size_t cap) { return (size_t)ntiles + cap / kSegLen + 1; }
 
-void launch_shadow_composite(const FrameArgs& f, cudaStream_t s) {
+namespace {
+
+// The shadow composite's parameters of a prepared frame.
+ShadowParams shadow_params(const FrameArgs& f) {
+  const SplatBufs& b = f.L->sp[1];
+  unsigned char* ws = f.ws;
+  const int fin = (f.L->ntiles <= 256 ? 1 : 2) & 1;
+  uint32_t* lvl = at<uint32_t>(ws, f.L->seg_lvl);
+  uint32_t* header = at<uint32_t>(ws, f.L->header);
+  ShadowParams p;
+  p.tile_order = at<uint32_t>(ws, f.L->tile_order[1]);
+  p.lvl_off = lvl;
+  p.ticket = lvl + kSegLevels + 1;
+  p.pub_a = at<float>(ws, f.L->seg_pub);
+  p.pub_flag = at<uint32_t>(ws, f.L->seg_flag);
+  p.list = at<uint32_t>(ws, b.tv[fin]);
+  p.tile_start = at<uint32_t>(ws, b.tile_start);
+  p.rrec = at<SplatRec>(ws, b.rrec);
+  p.off = at<uint32_t>(ws, b.off);
+  p.kbound = at<uint32_t>(ws, b.tv[1 - fin]);
+  p.pass_mask = at<uint8_t>(ws, b.tk[1 - fin]);  // the depths are consumed by k_occluder_bound
+  p.partial = at<float2>(ws, f.L->partial);
+  p.light_final = at<float>(ws, f.L->light_final);
+  p.light_stop = at<uint32_t>(ws, f.L->light_stop);
+  p.status = header + H_STATUS;
+  p.W = f.L->width; p.H = f.L->height; p.gx = f.L->gx;
+  p.amax = f.opts.alpha_max;
+  return p;
+}
+
+CamParams camera_params(const FrameArgs& f, float* out_rgb) {
+  const SplatBufs& b = f.L->sp[0];
+  unsigned char* ws = f.ws;
+  const int fin = (f.L->ntiles <= 256 ? 1 : 2) & 1;
+  CamParams p;
+  p.list = at<uint32_t>(ws, b.tv[fin]);
+  p.tile_start = at<uint32_t>(ws, b.tile_start);
+  p.rrec = at<SplatRec>(ws, b.rrec);
+  p.ccol = at<float4>(ws, f.L->ccol);
+  p.out = out_rgb;
+  p.final_t = at<float>(ws, f.L->final_t);
+  p.n_contrib = at<uint32_t>(ws, f.L->n_contrib);
+  p.pix_aux = at<float4>(ws, f.L->pix_aux);
+  p.W = f.L->width; p.H = f.L->height; p.gx = f.L->gx;
+  p.amax = f.opts.alpha_max; p.tstop = f.opts.t_stop;
+  p.tile_order = at<uint32_t>(ws, f.L->tile_order[0]);  // from the camera binning stage
+  return p;
+}
+
+// Blocks per SM of the persistent segment kernels (per device, looked up once).
+struct SegOccupancy {
+  int chain, live, dead;
+};
+SegOccupancy seg_occupancy() {
+  static DeviceOnce once;
+  static SegOccupancy occ[kMaxDevices];
+  once.run([] {
+    int d = 0;
+    cudaGetDevice(&d);
+    bool ok = true;
+    for (const void* k : {(const void*)k_shadow<false>, (const void*)k_shadow<true>, (const void*)k_shadow_chain<false>,
+                          (const void*)k_shadow_chain<true>})
+      ok = ok && cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                      (int)cudaSharedmemCarveoutMaxShared) == cudaSuccess;
+    if (d >= 0 && d < kMaxDevices) {
+      SegOccupancy& o = occ[d];
+      ok = ok &&
+           cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o.chain, k_shadow_chain<true>, kSegWarps * 32, 0) ==
+               cudaSuccess &&
+           cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o.live, k_shadow<true>, kSegWarps * 32, 0) == cudaSuccess &&
+           cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o.dead, k_shadow_dead<true>, kDeadWarps * 32, 0) ==
+               cudaSuccess;
+    }
+    return ok;
+  });
+  int d = 0;
+  cudaGetDevice(&d);
+  SegOccupancy o{1, 1, 1};
+  if (d >= 0 && d < kMaxDevices) o = occ[d];
+  if (o.chain < 1) o.chain = 1;
+  if (o.live < 1) o.live = 1;
+  if (o.dead < 1) o.dead = 1;
+  return o;
+}
+
+// Layout of a batch's parameter block (device, and its pinned host staging).
+struct BatchLayout {
+  static constexpr size_t shadow = 0;
+  static constexpr size_t camera = ((sizeof(ShadowParams) * kMaxBatch + 255) / 256) * 256;
+  static constexpr size_t prefix = camera + ((sizeof(CamParams) * kMaxBatch + 255) / 256) * 256;
+  static constexpr size_t total = prefix + 4 * (kMaxBatch + 1);
+};
+
+}  // namespace
+
+size_t batch_param_bytes() { return BatchLayout::total; }
+
+void prepare_shadow_composite(const FrameArgs& f, cudaStream_t s) {
   const SplatBufs& b = f.L->sp[1];
   unsigned char* ws = f.ws;
   const int fin = (f.L->ntiles <= 256 ? 1 : 2) & 1;
@@ -1003,55 +1175,54 @@ void launch_shadow_composite(const FrameArgs& f, cudaStream_t s) {
   count_launch(2);
   // the light tiles by segment count, and the work items of each segment level
   uint32_t* lvl = at<uint32_t>(ws, f.L->seg_lvl);
-  uint32_t* ticket = lvl + kSegLevels + 1;
-  uint32_t* flags = at<uint32_t>(ws, f.L->seg_flag);
-  cudaMemsetAsync(ticket, 0, 12, s);
-  cudaMemsetAsync(flags, 0, 4 * shadow_seg_items(f.L->ntiles, f.L->cap), s);
+  cudaMemsetAsync(lvl + kSegLevels + 1, 0, 12, s);  // the tickets
+  cudaMemsetAsync(at<uint32_t>(ws, f.L->seg_flag), 0, 4 * shadow_seg_items(f.L->ntiles, f.L->cap), s);
   k_tile_order<<<1, 1024, 0, s>>>(at<uint32_t>(ws, b.tile_start), f.L->ntiles, at<uint32_t>(ws, f.L->tile_order[1]),
                                   kSegLen, lvl);
   count_launch();
-  ShadowParams p;
-  p.tile_order = at<uint32_t>(ws, f.L->tile_order[1]);
-  p.lvl_off = lvl;
-  p.ticket = ticket;
-  p.pub_a = at<float>(ws, f.L->seg_pub);
-  p.pub_flag = flags;
-  p.list = at<uint32_t>(ws, b.tv[fin]);
-  p.tile_start = at<uint32_t>(ws, b.tile_start);
-  p.rrec = at<SplatRec>(ws, b.rrec);
-  p.off = at<uint32_t>(ws, b.off);
-  p.kbound = kb;
-  p.pass_mask = reinterpret_cast<uint8_t*>(dl);  // the depths are consumed by k_occluder_bound
-  p.partial = at<float2>(ws, f.L->partial);
-  p.light_final = at<float>(ws, f.L->light_final);
-  p.light_stop = at<uint32_t>(ws, f.L->light_stop);
-  p.status = header + H_STATUS;
-  p.W = f.L->width; p.H = f.L->height; p.gx = f.L->gx;
-  p.amax = f.opts.alpha_max;
-  static DeviceOnce once;
-  static int per_sm[kMaxDevices][2];
-  once.run([] {
-    int d = 0;
-    cudaGetDevice(&d);
-    bool ok = cudaFuncSetAttribute(k_shadow, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                   (int)cudaSharedmemCarveoutMaxShared) == cudaSuccess &&
-              cudaFuncSetAttribute(k_shadow_chain, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                   (int)cudaSharedmemCarveoutMaxShared) == cudaSuccess;
-    if (d >= 0 && d < kMaxDevices) {
-      ok = ok && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[d][0], k_shadow_chain, kSegWarps * 32, 0) ==
-                     cudaSuccess &&
-           cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[d][1], k_shadow, kSegWarps * 32, 0) == cudaSuccess;
-    }
-    return ok;
-  });
-  int d = 0;
-  cudaGetDevice(&d);
-  const int bc = d >= 0 && d < kMaxDevices && per_sm[d][0] > 0 ? per_sm[d][0] : 1;
-  const int br = d >= 0 && d < kMaxDevices && per_sm[d][1] > 0 ? per_sm[d][1] : 1;
+}
+
+void launch_shadow_composite(const FrameArgs& f, cudaStream_t s) {
+  prepare_shadow_composite(f, s);
+  const ShadowParams p = shadow_params(f);
+  const SegOccupancy o = seg_occupancy();
+  const int nsm = device_sm_count();
   // persistent warps: every resident warp slot takes segments from a ticket
-  k_shadow_chain<<<nsm * bc, kSegWarps * 32, 0, s>>>(p);
-  k_shadow<<<nsm * br, kSegWarps * 32, 0, s>>>(p);
-  k_shadow_dead<<<nsm * 6, kDeadWarps * 32, 0, s>>>(p);
+  k_shadow_chain<false><<<nsm * o.chain, kSegWarps * 32, 0, s>>>(p, nullptr, 1);
+  k_shadow<false><<<nsm * o.live, kSegWarps * 32, 0, s>>>(p, nullptr, 1);
+  k_shadow_dead<false><<<nsm * o.dead, kDeadWarps * 32, 0, s>>>(p, nullptr, 1);
+  count_launch(3);
+}
+
+// Self-test of the chain's bounded waits: the segment plan of a frame whose
+// light binning ran, then K6a with its ticket starting at the second segment
+// level, so that no first segment ever publishes and every second segment's
+// wait runs out (each then publishes its rays as stopped).
+__global__ void k_skip_first_level(const uint32_t* lvl_off, uint32_t* ticket) {
+  if (threadIdx.x == 0) ticket[0] = lvl_off[1];
+}
+
+void launch_shadow_chain_selftest(const FrameArgs& f, cudaStream_t s) {
+  prepare_shadow_composite(f, s);
+  const ShadowParams p = shadow_params(f);
+  k_skip_first_level<<<1, 32, 0, s>>>(p.lvl_off, p.ticket);
+  const SegOccupancy o = seg_occupancy();
+  k_shadow_chain<false><<<device_sm_count() * o.chain, kSegWarps * 32, 0, s>>>(p, nullptr, 1);
+  count_launch(2);
+}
+
+void launch_shadow_composite_batch(const FrameArgs* const* f, int n, unsigned char* dev, unsigned char* host,
+                                   cudaStream_t s) {
+  ShadowParams* hp = reinterpret_cast<ShadowParams*>(host + BatchLayout::shadow);
+  for (int r = 0; r < n; ++r) hp[r] = shadow_params(*f[r]);
+  cudaMemcpyAsync(dev + BatchLayout::shadow, hp, sizeof(ShadowParams) * n, cudaMemcpyHostToDevice, s);
+  const ShadowParams* dp = reinterpret_cast<const ShadowParams*>(dev + BatchLayout::shadow);
+  // the batch shares the first frame's tickets; every frame's flags were zeroed when it was prepared
+  const SegOccupancy o = seg_occupancy();
+  const int nsm = device_sm_count();
+  k_shadow_chain<true><<<nsm * o.chain, kSegWarps * 32, 0, s>>>(hp[0], dp, n);
+  k_shadow<true><<<nsm * o.live, kSegWarps * 32, 0, s>>>(hp[0], dp, n);
+  k_shadow_dead<true><<<nsm * o.dead, kDeadWarps * 32, 0, s>>>(hp[0], dp, n);
   count_launch(3);
 }
 
@@ -1075,22 +1246,23 @@ void launch_fill_shadow_one(const FrameArgs& f, cudaStream_t s) {
 }
 
 void launch_camera_composite(const FrameArgs& f, float* out_rgb, cudaStream_t s) {
-  const SplatBufs& b = f.L->sp[0];
-  unsigned char* ws = f.ws;
-  const int fin = (f.L->ntiles <= 256 ? 1 : 2) & 1;
-  CamParams p;
-  p.list = at<uint32_t>(ws, b.tv[fin]);
-  p.tile_start = at<uint32_t>(ws, b.tile_start);
-  p.rrec = at<SplatRec>(ws, b.rrec);
-  p.ccol = at<float4>(ws, f.L->ccol);
-  p.out = out_rgb;
-  p.final_t = at<float>(ws, f.L->final_t);
-  p.n_contrib = at<uint32_t>(ws, f.L->n_contrib);
-  p.pix_aux = at<float4>(ws, f.L->pix_aux);
-  p.W = f.L->width; p.H = f.L->height; p.gx = f.L->gx;
-  p.amax = f.opts.alpha_max; p.tstop = f.opts.t_stop;
-  p.tile_order = at<uint32_t>(ws, f.L->tile_order[0]);  // from the camera binning stage
-  k_camera<<<f.L->ntiles, 256, 0, s>>>(p);
+  k_camera<false><<<f.L->ntiles, 256, 0, s>>>(camera_params(f, out_rgb), nullptr, nullptr, 1);
+  count_launch();
+}
+
+void launch_camera_composite_batch(const FrameArgs* const* f, float* const* out, int n, unsigned char* dev,
+                                   unsigned char* host, cudaStream_t s) {
+  CamParams* hp = reinterpret_cast<CamParams*>(host + BatchLayout::camera);
+  uint32_t* pre = reinterpret_cast<uint32_t*>(host + BatchLayout::prefix);
+  pre[0] = 0;
+  for (int r = 0; r < n; ++r) {
+    hp[r] = camera_params(*f[r], out[r]);
+    pre[r + 1] = pre[r] + (uint32_t)f[r]->L->ntiles;
+  }
+  cudaMemcpyAsync(dev + BatchLayout::camera, hp, sizeof(CamParams) * n, cudaMemcpyHostToDevice, s);
+  cudaMemcpyAsync(dev + BatchLayout::prefix, pre, 4 * (n + 1), cudaMemcpyHostToDevice, s);
+  k_camera<true><<<pre[n], 256, 0, s>>>(hp[0], reinterpret_cast<const CamParams*>(dev + BatchLayout::camera),
+                                         reinterpret_cast<const uint32_t*>(dev + BatchLayout::prefix), n);
   count_launch();
 }
 

@@ -129,6 +129,28 @@ gs3_status render_frame(gs3_scene* scene, const gs3_camera* cam, const gs3_light
                         const gs3_render_opts* opts, float* out_rgb, void* workspace, size_t ws_bytes,
                         size_t key_capacity, uint32_t stages, cudaStream_t stream, SideStream* side);
 
+// One frame of a batch: its scene, view, light, options, output and workspace.
+struct BatchFrame {
+  gs3_scene* scene;
+  gs3_camera cam;
+  gs3_light light;
+  gs3_render_opts opts;
+  float* out;
+  void* ws;
+  size_t ws_bytes;
+  size_t cap;
+};
+// Streams and events of a batch: a sub-stream per frame for the per-frame stages.
+struct BatchStreams {
+  cudaStream_t sub[8] = {};
+  cudaEvent_t fork = nullptr, fork2 = nullptr, join[8] = {}, join2[8] = {};
+  bool create(int n);
+  void destroy();
+};
+// Renders n <= kMaxBatch frames together on `stream` (see render_batch in api.cu).
+gs3_status render_batch(const BatchFrame* frames, int n, cudaStream_t stream, BatchStreams& bs,
+                        unsigned char* param_dev, unsigned char* param_host);
+
 // ---- launchers (stream-ordered, no host synchronisation) ----
 struct FrameArgs {
   SceneDev sc;
@@ -168,6 +190,20 @@ void launch_prep(const FrameArgs& f, cudaStream_t s);
 void launch_depth_sort(const FrameArgs& f, int splat, cudaStream_t s);
 void launch_binning(const FrameArgs& f, int splat, cudaStream_t s);
 void launch_shadow_composite(const FrameArgs& f, cudaStream_t s);
+// Batches of frames (up to kMaxBatch, each with its own workspace): the
+// shadow composite's per-frame set-up (on each frame's stream), then its
+// segment kernels and the camera composite over every frame of the batch in
+// single launches.  dev / host: a batch parameter block, device memory and
+// pinned host staging of batch_param_bytes() each, not reused until the
+// batch's work completed.
+constexpr int kMaxBatch = 8;
+size_t batch_param_bytes();
+void prepare_shadow_composite(const FrameArgs& f, cudaStream_t s);
+void launch_shadow_chain_selftest(const FrameArgs& f, cudaStream_t s);
+void launch_shadow_composite_batch(const FrameArgs* const* f, int n, unsigned char* dev, unsigned char* host,
+                                   cudaStream_t s);
+void launch_camera_composite_batch(const FrameArgs* const* f, float* const* out, int n, unsigned char* dev,
+                                   unsigned char* host, cudaStream_t s);
 // shadow composite work items (tile segments) a frame can have at most
 size_t shadow_seg_items(int ntiles, size_t cap);
 // a splat's tiles ordered longest list first (in length steps of 8), into L.tile_order[splat]

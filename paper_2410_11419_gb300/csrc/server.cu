@@ -1,14 +1,19 @@
 // Continuous-batching render server over device-resident scenes.
 //
-// A worker thread owns a FIFO of (scene, camera, light) requests.  A request
-// is admitted when an in-flight slot is free and its workspace fits in the
-// HBM budget (bytes in use by admitted requests); it then runs the whole
-// frame on its slot's stream, so requests admitted while others are still on
-// the GPU overlap on the device.  Workspaces come from a stream-ordered
-// memory pool and go back to it when the request's completion event fires.
-// The workspace capacity (tile/Gaussian pairs) is estimated per
-// (scene, resolution) from the largest count seen so far; a request that
-// overflows is re-admitted once with the exact count its first run reported.
+// A worker thread owns a FIFO of (scene, camera, light) requests and a set
+// of in-flight slots.  A free slot takes up to max_batch requests from the
+// head of the queue, as long as their workspaces fit in the HBM budget
+// (bytes in use by admitted requests), and renders them as one batch: every
+// frame's shading, projections and binning on its own sub-stream, then the
+// shadow composite's persistent segment kernels and the camera composite
+// over all the batch's frames in single launches (render_batch).  Requests
+// that arrive while batches are on the GPU wait for the next free slot and
+// join its batch; batches in different slots overlap on the device.
+// Workspaces come from a stream-ordered memory pool and go back to it when
+// the batch's completion event fires.  The workspace capacity
+// (tile/Gaussian pairs) is estimated per (scene, resolution) from the largest
+// count seen so far; a request that overflows is re-admitted once with the
+// exact count its first run reported.
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -37,17 +42,26 @@ struct Request {
   int attempts = 0;
 };
 
-struct Slot {
-  cudaStream_t stream = nullptr;
-  SideStream side;  // the slot's own stream for its frames' light chains
-  cudaEvent_t start = nullptr;
-  cudaEvent_t done = nullptr;
+// One request of a batch and its workspace.
+struct Member {
+  Request req;
   gs3_ws_header* hdr = nullptr;  // pinned copy of the workspace header
   void* ws = nullptr;
   size_t bytes = 0;
   size_t cap = 0;
+};
+
+struct Slot {
+  cudaStream_t stream = nullptr;
+  SideStream side;     // a lone frame's light chain
+  BatchStreams batch;  // a batch's per-frame sub-streams
+  unsigned char* param_dev = nullptr;   // the batch's kernel parameters
+  unsigned char* param_host = nullptr;  // and their pinned staging
+  cudaEvent_t start = nullptr;
+  cudaEvent_t done = nullptr;
+  Member m[kMaxBatch];
+  int n = 0;  // requests in the batch
   bool busy = false;
-  Request req;
 };
 
 struct Result {
@@ -79,6 +93,9 @@ struct gs3_server {
   uint64_t next_ticket = 1;
   uint64_t completed = 0, failed = 0, retries = 0;
   int max_inflight_seen = 0;
+  int max_batch = 1;
+  int max_batch_seen = 0;
+  uint64_t batches = 0;
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
   std::thread worker;
@@ -106,20 +123,19 @@ size_t estimate_cap(gs3_server* S, const Request& r) {
   return (size_t)c;
 }
 
-void finish(gs3_server* S, Slot& sl, gs3_status st) {
-  Result& res = S->results[sl.req.ticket];
+void finish(gs3_server* S, const Request& req, gs3_status st) {
+  Result& res = S->results[req.ticket];
   res.state = st == GS3_OK ? GS3_REQ_DONE : GS3_REQ_FAILED;
   res.status = st;
-  res.latency_ms = std::chrono::duration<double, std::milli>(Clock::now() - sl.req.t_submit).count();
+  res.latency_ms = std::chrono::duration<double, std::milli>(Clock::now() - req.t_submit).count();
   if (st == GS3_OK) ++S->completed; else ++S->failed;
 }
 
-void release(gs3_server* S, Slot& sl) {
-  if (sl.ws) cudaFreeAsync(sl.ws, sl.stream);
-  sl.ws = nullptr;
-  S->in_use -= sl.bytes;
-  sl.bytes = 0;
-  sl.busy = false;
+void release(gs3_server* S, Slot& sl, Member& m) {
+  if (m.ws) cudaFreeAsync(m.ws, sl.stream);
+  m.ws = nullptr;
+  S->in_use -= m.bytes;
+  m.bytes = 0;
 }
 
 // Completions: called with the lock held.
@@ -130,44 +146,52 @@ bool poll_slots(gs3_server* S) {
     const cudaError_t q = cudaEventQuery(sl.done);
     if (q == cudaErrorNotReady) continue;
     any = true;
-    gs3_status st = GS3_OK;
-    if (q != cudaSuccess) {
-      st = GS3_ERR_CUDA;
-    } else if (sl.hdr->status == GS3_ERR_CAPACITY && sl.req.attempts < 2) {
-      // re-admit at the front with the exact pair count of this frame
-      Request r = sl.req;
-      const size_t need = sl.hdr->pairs_cam_needed > sl.hdr->pairs_light_needed ? sl.hdr->pairs_cam_needed
-                                                                                   : sl.hdr->pairs_light_needed;
-      r.forced_cap = need + need / 16 + 1024;
-      ++S->retries;
-      auto& hint = S->cap_hint[hint_key(r.scene, r.cam.width, r.cam.height)];
-      if (r.forced_cap > hint) hint = r.forced_cap;
-      release(S, sl);
-      S->results[r.ticket].state = GS3_REQ_QUEUED;
-      S->queue.push_front(r);
-      continue;
-    } else {
-      st = (gs3_status)sl.hdr->status;
-      const size_t seen = sl.hdr->pairs_cam > sl.hdr->pairs_light ? sl.hdr->pairs_cam : sl.hdr->pairs_light;
-      auto& hint = S->cap_hint[hint_key(sl.req.scene, sl.req.cam.width, sl.req.cam.height)];
-      const size_t want = seen + seen / 8 + 1024;  // 12.5 % head room over the largest count seen
-      if (want > hint) hint = want;
-    }
-    if (st == GS3_OK && S->epoch_set) {
-      float a = 0.f, b = 0.f;
-      if (cudaEventElapsedTime(&a, S->epoch, sl.start) == cudaSuccess &&
-          cudaEventElapsedTime(&b, S->epoch, sl.done) == cudaSuccess) {
-        if (a < S->span_lo) S->span_lo = a;
-        if (b > S->span_hi) S->span_hi = b;
+    bool timed = false;
+    for (int i = 0; i < sl.n; ++i) {
+      Member& m = sl.m[i];
+      gs3_status st = GS3_OK;
+      if (q != cudaSuccess) {
+        st = GS3_ERR_CUDA;
+      } else if (m.hdr->status == GS3_ERR_CAPACITY && m.req.attempts < 2) {
+        // re-admit at the front with the exact pair count of this frame
+        Request r = m.req;
+        const size_t need = m.hdr->pairs_cam_needed > m.hdr->pairs_light_needed ? m.hdr->pairs_cam_needed
+                                                                                : m.hdr->pairs_light_needed;
+        r.forced_cap = need + need / 16 + 1024;
+        ++S->retries;
+        auto& hint = S->cap_hint[hint_key(r.scene, r.cam.width, r.cam.height)];
+        if (r.forced_cap > hint) hint = r.forced_cap;
+        release(S, sl, m);
+        S->results[r.ticket].state = GS3_REQ_QUEUED;
+        S->queue.push_front(r);
+        continue;
+      } else {
+        st = (gs3_status)m.hdr->status;
+        const size_t seen = m.hdr->pairs_cam > m.hdr->pairs_light ? m.hdr->pairs_cam : m.hdr->pairs_light;
+        auto& hint = S->cap_hint[hint_key(m.req.scene, m.req.cam.width, m.req.cam.height)];
+        const size_t want = seen + seen / 8 + 1024;  // 12.5 % head room over the largest count seen
+        if (want > hint) hint = want;
       }
+      if (st == GS3_OK && S->epoch_set && !timed) {
+        float a = 0.f, b = 0.f;
+        if (cudaEventElapsedTime(&a, S->epoch, sl.start) == cudaSuccess &&
+            cudaEventElapsedTime(&b, S->epoch, sl.done) == cudaSuccess) {
+          if (a < S->span_lo) S->span_lo = a;
+          if (b > S->span_hi) S->span_hi = b;
+        }
+        timed = true;
+      }
+      finish(S, m.req, st);
+      release(S, sl, m);
     }
-    finish(S, sl, st);
-    release(S, sl);
+    sl.n = 0;
+    sl.busy = false;
   }
   return any;
 }
 
-// Admission: called with the lock held.  FIFO: the head waits for memory.
+// Admission: called with the lock held.  FIFO: the head waits for memory.  A
+// free slot takes up to max_batch requests from the head of the queue.
 bool admit(gs3_server* S) {
   bool any = false;
   while (!S->queue.empty()) {
@@ -175,58 +199,85 @@ bool admit(gs3_server* S) {
     for (Slot& sl : S->slots)
       if (!sl.busy) { free_slot = &sl; break; }
     if (!free_slot) break;
-    const Request& head = S->queue.front();
-    gs3_scene* sc = S->scenes[head.scene];
-    const size_t cap = estimate_cap(S, head);
-    const size_t bytes = gs3_workspace_size(sc->dev.n, head.cam.width, head.cam.height, cap) + 256;
-    const bool fits_ever = bytes <= S->budget;
-    if (fits_ever && S->in_use + bytes > S->budget) break;  // wait for memory
     Slot& sl = *free_slot;
-    sl.req = head;
-    sl.req.attempts += 1;
-    S->queue.pop_front();
-    any = true;
-    if (!fits_ever) {  // can never fit: fail it rather than block the queue
-      finish(S, sl, GS3_ERR_OOM);
-      continue;
+    sl.n = 0;
+    while (!S->queue.empty() && sl.n < S->max_batch) {
+      const Request& head = S->queue.front();
+      gs3_scene* sc = S->scenes[head.scene];
+      const size_t cap = estimate_cap(S, head);
+      const size_t bytes = gs3_workspace_size(sc->dev.n, head.cam.width, head.cam.height, cap) + 256;
+      const bool fits_ever = bytes <= S->budget;
+      if (fits_ever && S->in_use + bytes > S->budget) break;  // wait for memory
+      Request req = head;
+      req.attempts += 1;
+      S->queue.pop_front();
+      any = true;
+      if (!fits_ever) {  // can never fit: fail it rather than block the queue
+        finish(S, req, GS3_ERR_OOM);
+        continue;
+      }
+      void* ws = nullptr;
+      cudaError_t e = cudaSuccess;
+      if (S->inject_alloc_failures > 0) {
+        --S->inject_alloc_failures;
+        e = cudaErrorMemoryAllocation;
+      } else {
+        e = cudaMallocFromPoolAsync(&ws, bytes, S->pool, sl.stream);
+      }
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        finish(S, req, GS3_ERR_OOM);
+        continue;
+      }
+      Member& m = sl.m[sl.n++];
+      m.req = req;
+      m.ws = ws;
+      m.bytes = bytes;
+      m.cap = cap;
+      S->in_use += bytes;
+      if (S->in_use > S->peak_in_use) S->peak_in_use = S->in_use;
+      S->results[req.ticket].state = GS3_REQ_RUNNING;
     }
-    void* ws = nullptr;
-    cudaError_t e = cudaSuccess;
-    if (S->inject_alloc_failures > 0) {
-      --S->inject_alloc_failures;
-      e = cudaErrorMemoryAllocation;
-    } else {
-      e = cudaMallocFromPoolAsync(&ws, bytes, S->pool, sl.stream);
-    }
-    if (e != cudaSuccess) {
-      cudaGetLastError();
-      finish(S, sl, GS3_ERR_OOM);
-      continue;
-    }
-    sl.ws = ws;
-    sl.bytes = bytes;
-    sl.cap = cap;
+    if (sl.n == 0) break;  // the head waits for memory
     sl.busy = true;
-    S->in_use += bytes;
-    if (S->in_use > S->peak_in_use) S->peak_in_use = S->in_use;
-    S->results[sl.req.ticket].state = GS3_REQ_RUNNING;
-    void* aligned = reinterpret_cast<void*>((reinterpret_cast<uintptr_t>(ws) + 255) & ~uintptr_t(255));
     if (!S->epoch_set) {
       cudaEventRecord(S->epoch, sl.stream);
       S->epoch_set = true;
     }
     cudaEventRecord(sl.start, sl.stream);
-    gs3_status st = render_frame(sc, &sl.req.cam, &sl.req.light, &sl.req.opts, sl.req.out, aligned, bytes - 256,
-                                 cap, GS3_STAGE_ALL, sl.stream, sl.side.s ? &sl.side : nullptr);
-    if (st == GS3_OK) {
-      cudaMemcpyAsync(sl.hdr, aligned, sizeof(gs3_ws_header), cudaMemcpyDeviceToHost, sl.stream);
-      cudaEventRecord(sl.done, sl.stream);
+    gs3_status st = GS3_OK;
+    void* aligned[kMaxBatch];
+    for (int i = 0; i < sl.n; ++i)
+      aligned[i] = reinterpret_cast<void*>((reinterpret_cast<uintptr_t>(sl.m[i].ws) + 255) & ~uintptr_t(255));
+    if (sl.n == 1) {
+      Member& m = sl.m[0];
+      st = render_frame(S->scenes[m.req.scene], &m.req.cam, &m.req.light, &m.req.opts, m.req.out, aligned[0],
+                        m.bytes - 256, m.cap, GS3_STAGE_ALL, sl.stream, sl.side.s ? &sl.side : nullptr);
     } else {
-      finish(S, sl, st);
-      release(S, sl);
+      BatchFrame fr[kMaxBatch];
+      for (int i = 0; i < sl.n; ++i) {
+        const Member& m = sl.m[i];
+        fr[i] = BatchFrame{S->scenes[m.req.scene], m.req.cam, m.req.light, m.req.opts, m.req.out, aligned[i],
+                           m.bytes - 256, m.cap};
+      }
+      st = render_batch(fr, sl.n, sl.stream, sl.batch, sl.param_dev, sl.param_host);
+    }
+    if (st == GS3_OK) {
+      for (int i = 0; i < sl.n; ++i)
+        cudaMemcpyAsync(sl.m[i].hdr, aligned[i], sizeof(gs3_ws_header), cudaMemcpyDeviceToHost, sl.stream);
+      cudaEventRecord(sl.done, sl.stream);
+      ++S->batches;
+      if (sl.n > S->max_batch_seen) S->max_batch_seen = sl.n;
+    } else {
+      for (int i = 0; i < sl.n; ++i) {
+        finish(S, sl.m[i].req, st);
+        release(S, sl, sl.m[i]);
+      }
+      sl.n = 0;
+      sl.busy = false;
     }
     int inflight = 0;
-    for (Slot& s2 : S->slots) inflight += s2.busy ? 1 : 0;
+    for (Slot& s2 : S->slots) inflight += s2.busy ? s2.n : 0;
     if (inflight > S->max_inflight_seen) S->max_inflight_seen = inflight;
   }
   return any;
@@ -266,7 +317,13 @@ gs3_status gs3_server_create(const gs3_server_opts* o, gs3_server** out) {
   *out = nullptr;
   gs3_server* S = new (std::nothrow) gs3_server;
   if (!S) return GS3_ERR_OOM;
+  if (o->max_batch < 0 || o->max_batch > kMaxBatch) {
+    delete S;
+    set_last_error("gs3_server_create: max_batch must be in [0, 8]");
+    return GS3_ERR_INVALID_ARG;
+  }
   S->budget = o->hbm_budget;
+  S->max_batch = o->max_batch > 0 ? o->max_batch : 1;
   S->inject_alloc_failures = o->inject_alloc_failures;
   if (o->initial_pairs > 0.f) S->initial_pairs = o->initial_pairs;
   S->device = o->device;
@@ -287,12 +344,21 @@ gs3_status gs3_server_create(const gs3_server_opts* o, gs3_server** out) {
   uint64_t keep = (uint64_t)S->budget;  // keep freed memory in the pool up to the budget
   cudaMemPoolSetAttribute(S->pool, cudaMemPoolAttrReleaseThreshold, &keep);
   S->slots.resize(o->max_inflight);
+  bool ok = true;
   for (Slot& sl : S->slots) {
-    cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking);
-    sl.side.create();
-    cudaEventCreate(&sl.start);
-    cudaEventCreate(&sl.done);
-    cudaMallocHost(reinterpret_cast<void**>(&sl.hdr), sizeof(gs3_ws_header));
+    ok = ok && cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) == cudaSuccess;
+    ok = ok && sl.side.create() && sl.batch.create(S->max_batch);
+    ok = ok && cudaEventCreate(&sl.start) == cudaSuccess && cudaEventCreate(&sl.done) == cudaSuccess;
+    ok = ok && cudaMalloc(reinterpret_cast<void**>(&sl.param_dev), batch_param_bytes()) == cudaSuccess;
+    ok = ok && cudaMallocHost(reinterpret_cast<void**>(&sl.param_host), batch_param_bytes()) == cudaSuccess;
+    for (int i = 0; i < kMaxBatch && ok; ++i)
+      ok = cudaMallocHost(reinterpret_cast<void**>(&sl.m[i].hdr), sizeof(gs3_ws_header)) == cudaSuccess;
+  }
+  if (!ok) {
+    S->worker = std::thread();
+    gs3_server_destroy(S);
+    set_last_error("gs3_server_create: stream, event or pinned-memory creation failed");
+    return GS3_ERR_CUDA;
   }
   cudaEventCreate(&S->epoch);
   S->worker = std::thread(worker_main, S);
@@ -390,8 +456,10 @@ gs3_status gs3_server_stats(gs3_server* S, gs3_server_counters* out) {
   out->retries = S->retries;
   out->queued = S->queue.size();
   int inflight = 0;
-  for (Slot& sl : S->slots) inflight += sl.busy ? 1 : 0;
+  for (Slot& sl : S->slots) inflight += sl.busy ? sl.n : 0;
   out->in_flight = (uint64_t)inflight;
+  out->batches = S->batches;
+  out->max_batch = (uint64_t)S->max_batch_seen;
   out->max_in_flight = (uint64_t)S->max_inflight_seen;
   out->bytes_in_use = S->in_use;
   out->peak_bytes_in_use = S->peak_in_use;
@@ -404,6 +472,8 @@ gs3_status gs3_server_reset_counters(gs3_server* S) {
   std::lock_guard<std::mutex> lock(S->mu);
   S->completed = S->failed = S->retries = 0;
   S->max_inflight_seen = 0;
+  S->max_batch_seen = 0;
+  S->batches = 0;
   S->peak_in_use = S->in_use;
   S->epoch_set = false;
   S->span_lo = 1e300;
@@ -421,13 +491,18 @@ gs3_status gs3_server_destroy(gs3_server* S) {
   if (S->worker.joinable()) S->worker.join();
   for (Slot& sl : S->slots) {
     if (sl.stream) cudaStreamSynchronize(sl.stream);
-    if (sl.ws) cudaFreeAsync(sl.ws, sl.stream);
+    for (int i = 0; i < sl.n; ++i)
+      if (sl.m[i].ws) cudaFreeAsync(sl.m[i].ws, sl.stream);
     if (sl.stream) cudaStreamSynchronize(sl.stream);
     if (sl.done) cudaEventDestroy(sl.done);
     if (sl.start) cudaEventDestroy(sl.start);
     if (sl.stream) cudaStreamDestroy(sl.stream);
     sl.side.destroy();
-    if (sl.hdr) cudaFreeHost(sl.hdr);
+    sl.batch.destroy();
+    if (sl.param_dev) cudaFree(sl.param_dev);
+    if (sl.param_host) cudaFreeHost(sl.param_host);
+    for (int i = 0; i < kMaxBatch; ++i)
+      if (sl.m[i].hdr) cudaFreeHost(sl.m[i].hdr);
   }
   if (S->epoch) cudaEventDestroy(S->epoch);
   if (S->pool) cudaMemPoolDestroy(S->pool);

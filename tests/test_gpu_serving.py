@@ -1,8 +1,10 @@
 """Continuous-batching server (gs3_server_*): every result equals the same
 frame rendered alone with gs3_render, bit for bit (each request has its own
-workspace and the frame is deterministic), while requests overlap on the GPU;
-admission respects the HBM budget; capacity overflows are retried; injected
-allocation failures fail only their own requests."""
+workspace and the frame is deterministic), while requests overlap on the GPU
+and queued requests are rendered together in batches (single launches of the
+shadow and camera composites over a batch's frames); admission respects the
+HBM budget; capacity overflows are retried; injected allocation failures fail
+only their own requests; the shadow composite's chained waits are bounded."""
 import numpy as np
 import pytest
 
@@ -146,3 +148,58 @@ def test_rejects_bad_requests(scenes):
     assert srv.wait(t_big)[0] == N.GS3_ERR_OOM
     assert srv.wait(t_ok)[0] == 0
     srv.close()
+
+
+def test_batches_render_frames_together(scenes):
+    """Requests that queue while a slot is busy are rendered as one batch (the
+    shadow and camera composites of all its frames in single launches); each
+    frame still equals the same frame rendered alone, bit for bit, across
+    scenes, MLP precisions, resolutions and ablations within a batch."""
+    import torch
+    from paper_2410_11419_gb300 import _native as N, render as R
+    srv = R.Server(hbm_budget=8 << 30, max_inflight=1, max_batch=4)
+    ids = [srv.add_scene(d) for d in scenes]
+    big_cam, big_light = synth.camera_light_pair(20, 1024, 1024)
+    blocker = torch.empty((1024, 1024, 3), device="cuda")
+    mix = [(0, 256, 21, 0), (1, 128, 22, N.GS3_ABLATE_SHADOW_SPLAT), (2, 160, 23, 0), (0, 200, 24, N.GS3_ABLATE_PHI),
+           (1, 96, 25, 0), (0, 256, 26, N.GS3_ABLATE_SPECULAR), (2, 144, 27, N.GS3_ABLATE_PSI), (0, 320, 28, 0)]
+    outs = [torch.full((res, res, 3), -1.0, device="cuda") for _, res, _, _ in mix]
+    torch.cuda.synchronize()
+    tickets = [srv.submit(ids[0], big_cam, big_light, blocker)]  # keeps the only slot busy
+    for (si, res, seed, ab), out in zip(mix, outs):
+        cam, light = synth.camera_light_pair(seed, res, res)
+        tickets.append(srv.submit(ids[si], cam, light, out, R.opts_struct(ablate=ab)))
+    for t in tickets:
+        assert srv.wait(t)[0] == 0
+    st = srv.stats()
+    assert st.max_batch >= 2 and st.batches < len(tickets), (st.max_batch, st.batches)
+    for (si, res, seed, ab), out in zip(mix, outs):
+        cam, light = synth.camera_light_pair(seed, res, res)
+        rd = R.Renderer(scenes[si], res, res, 1 << 23)
+        want = rd.render(cam, light, R.opts_struct(ablate=ab)).clone()
+        torch.cuda.synchronize()
+        rd.check()
+        assert torch.equal(out, want), (si, res, seed, ab)
+    srv.close()
+
+
+def test_shadow_chain_bounded_wait_gives_up(scenes):
+    """The shadow composite's chained segment products wait for the segment
+    before them; a chain whose first segments never publish gives up after the
+    poll bound, records GS3_ERR_TIMEOUT, and the context stays usable."""
+    import time
+    import torch
+    from paper_2410_11419_gb300 import _native as N, render as R
+    scene = synth.object_scene(2, n=20000)
+    ds = R.DeviceScene(scene)
+    cam, light = synth.camera_light_pair(7, 256, 256)
+    rd = R.Renderer(ds, 256, 256, 1 << 22)
+    t0 = time.perf_counter()
+    status = N.gs3_selftest_shadow_wait(ds.handle, R.camera_struct(cam), R.light_struct(light), R.opts_struct(),
+                                        rd.ws, rd.ws.numel(), rd.cap)
+    assert status == N.GS3_ERR_TIMEOUT
+    assert time.perf_counter() - t0 < 30.0
+    img = rd.render(cam, light).clone()  # a normal frame on the same context afterwards
+    torch.cuda.synchronize()
+    assert rd.check().status == 0 and torch.isfinite(img).all()
+    ds.close()
