@@ -99,6 +99,7 @@ def parse():
     ap.add_argument("--no-serve", action="store_true", help="time single frames only")
     ap.add_argument("--no-mix", action="store_true", help="skip the mixed-scene serving measurement")
     ap.add_argument("--no-ksweep", action="store_true", help="skip the lobe-count sweep")
+    ap.add_argument("--no-env", action="store_true", help="skip the environment-light arm")
     ap.add_argument("--mix-requests", type=int, default=160,
                     help="requests per arrival rate in the mixed-scene serving measurement")
     return ap.parse_args()
@@ -340,6 +341,61 @@ def lobe_sweep(a, dev, np, torch, N, R, synth, frames=10):
         del rd
         ds.close()
     return out
+
+
+def environment_arm(a, dev, np, torch, N, R, synth, ds, lights_n=8, frames=10):
+    """An environment light (Sec. 4.5) of `lights_n` seeded directional lights
+    on the object workload (BF16 MLPs): the batched frame (gs3_render_environment)
+    against one directional frame and against the same lights rendered one
+    after another, CUDA events per frame, L2 flushed before each."""
+    views = [synth.camera_light_pair(i, a.res, a.res)[0] for i in range(frames)]
+    envs = [synth.environment_lights(100 + i, lights_n) for i in range(frames)]
+    # pair capacity for these lights (untimed): the most any light needs, plus 5 %
+    probe = R.Renderer(ds, a.res, a.res, 40_000_000 if a.n <= 300_000 else int(a.n * 140), device=dev)
+    need = 0
+    for cam, (lights, _) in zip(views, envs):
+        for L in lights:
+            probe.render_stages(cam, L, N.GS3_STAGE_PREP | N.GS3_STAGE_CAMERA_BIN | N.GS3_STAGE_LIGHT_BIN)
+            h = probe.check()
+            need = max(need, h.pairs_cam_needed, h.pairs_light_needed)
+    del probe
+    rd = R.Renderer(ds, a.res, a.res, int(need * 1.05) + 4096, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    for i in range(2):
+        rd.render_environment(views[i], *envs[i])
+        rd.render(views[i], envs[i][0][0])
+    torch.cuda.synchronize()
+
+    def timed(fn):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(frames)]
+        for i in range(frames):
+            flush.zero_()
+            ev[i][0].record()
+            fn(i)
+            ev[i][1].record()
+        torch.cuda.synchronize()
+        return np.array([e0.elapsed_time(e1) for e0, e1 in ev])
+
+    env_ms = timed(lambda i: rd.render_environment(views[i], *envs[i]))
+    h = rd.env_header()
+    assert h.status == 0, h.status
+    one_ms = timed(lambda i: rd.render(views[i], envs[i][0][0]))
+    rd.check()
+
+    def one_after_another(i):
+        for L in envs[i][0]:
+            rd.render(views[i], L)
+
+    seq_ms = timed(one_after_another)
+    rd.check()
+    del rd
+    return {"lights": lights_n, "frames": frames, "capacity": int(need * 1.05) + 4096,
+            "batched_ms": float(env_ms.mean()), "batched_frames_per_s": frames / (env_ms.sum() / 1e3),
+            "one_directional_frame_ms": float(one_ms.mean()),
+            "lights_one_after_another_ms": float(seq_ms.mean()),
+            "batched_over_one_frame": float(env_ms.mean() / one_ms.mean()),
+            "note": "object workload, BF16 MLPs, 800x800; lights from synth.environment_lights "
+                    "(uniform directions, extent 1.25); L2 flushed before each frame"}
 
 
 def serving_mix(a, dev, np, torch, N, R, synth):
@@ -793,6 +849,9 @@ def main():
         out["serving_mix"] = serving_mix(a, dev, np, torch, N, R, synth)
     if world == 1 and not a.no_ksweep:
         out["lobe_sweep"] = lobe_sweep(a, dev, np, torch, N, R, synth)
+    if world == 1 and not a.no_env:
+        env_ds = ds if a.mlp == "bf16" else R.DeviceScene(scene, device=dev, mlp_dtype=N.GS3_MLP_BF16)
+        out["environment"] = environment_arm(a, dev, np, torch, N, R, synth, env_ds)
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(a, scene, gpu_frame0)
         out["error_vs_oracle"] = out["cpu_baseline"].pop("error_vs_oracle", None)

@@ -240,16 +240,29 @@ gs3_status gs3_render_stages(gs3_scene *scene, const gs3_camera *camera, const g
                              void *stream);
 
 /* Environment light (Sec. 4.5): out_rgb = sum_l weights[l] * (the image
- * gs3_render gives for lights[l]), the lights directional (or point).
- *   lights, weights: host arrays of `count` >= 1 entries
+ * gs3_render gives for lights[l]), the lights directional (or point), all
+ * rendered as one batched frame.  The camera splat, Psi and the camera
+ * composite's weights do not depend on the light and run once; per group of
+ * up to 8 lights, the shadow composites run in single launches, Phi runs
+ * once over 8 N rows, and one camera composite adds the group's
+ * sum_l w_l (S_l Sh_l + R).  Each light's shadow values and refined shadow
+ * equal those of its own gs3_render.
+ *   lights, weights: host arrays of `count` entries, 1 <= count <= 4096
  *   out_rgb:         device float32 [height][width][3], overwritten
- *   scratch_rgb:     device float32 [height][width][3], caller-owned
- * The frames run one after another in `workspace`; the header then reports
- * the first non-OK status and the largest pair counts over the lights.
- * Asynchronous.  Errors: as gs3_render. */
+ *   workspace:       device, 256-byte aligned, at least
+ *                    gs3_environment_workspace_size(n, width, height, count,
+ *                    key_capacity) bytes, caller-owned; its header (start of
+ *                    the workspace) then holds the first non-OK status, the
+ *                    camera's pair counts and the largest light pair counts
+ * Asynchronous on `stream` (sub-streams of the scene, made on the first call,
+ * join it).  Calls on one scene from several threads are serialised while
+ * they enqueue.  Errors: as gs3_render; GS3_ERR_INVALID_ARG for count out of
+ * range or a workspace smaller than the size below. */
+size_t gs3_environment_workspace_size(int32_t n, int32_t width, int32_t height, int32_t count,
+                                      size_t key_capacity);
 gs3_status gs3_render_environment(gs3_scene *scene, const gs3_camera *camera, const gs3_light *lights,
                                   const float *weights, int32_t count, const gs3_render_opts *opts,
-                                  float *out_rgb, float *scratch_rgb, void *workspace, size_t workspace_bytes,
+                                  float *out_rgb, void *workspace, size_t workspace_bytes,
                                   size_t key_capacity, void *stream);
 
 /* Copy the workspace header to `out` (host) and synchronise `stream`. */

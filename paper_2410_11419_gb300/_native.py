@@ -136,8 +136,8 @@ SIGNATURES = {
                                 C.c_float, C.c_float, C.c_float, C.c_int32, C.c_float, C.c_void_p]),
     "gs3_render_environment": (C.c_int, [_SCENE_P, C.POINTER(gs3_camera), C.POINTER(gs3_light),
                                          C.POINTER(C.c_float), C.c_int32, C.POINTER(gs3_render_opts),
-                                         C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t, C.c_size_t,
-                                         C.c_void_p]),
+                                         C.c_void_p, C.c_void_p, C.c_size_t, C.c_size_t, C.c_void_p]),
+    "gs3_environment_workspace_size": (C.c_size_t, [C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_size_t]),
     "gs3_backward_workspace_size": (C.c_size_t, [_SCENE_P]),
     "gs3_loss_scratch_size": (C.c_size_t, [C.c_int32, C.c_int32]),
     "gs3_loss_l1_dssim": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_float, C.c_void_p,
@@ -238,14 +238,18 @@ def gs3_adam_step(param, grad, m, v, lr: float, beta1: float, beta2: float, eps:
                                lower_bound, stream), "gs3_adam_step")
 
 
+def gs3_environment_workspace_size(n: int, width: int, height: int, count: int, key_capacity: int) -> int:
+    return int(lib().gs3_environment_workspace_size(n, width, height, count, key_capacity))
+
+
 def gs3_render_environment(scene, camera: gs3_camera, lights, weights, opts: gs3_render_opts, out_rgb,
-                           scratch_rgb, workspace, key_capacity: int, stream: int) -> None:
+                           workspace, key_capacity: int, stream: int) -> None:
     n = len(lights)
-    la = (gs3_light * n)(*lights)
-    wa = (C.c_float * n)(*[float(w) for w in weights])
+    la = (gs3_light * max(n, 1))(*lights)
+    wa = (C.c_float * max(n, 1))(*[float(w) for w in weights])
     _check(lib().gs3_render_environment(scene, C.byref(camera), la, wa, n, C.byref(opts), _ptr(out_rgb),
-                                        _ptr(scratch_rgb), _ptr(workspace),
-                                        workspace.numel() * workspace.element_size(), key_capacity, stream),
+                                        _ptr(workspace), workspace.numel() * workspace.element_size(),
+                                        key_capacity, stream),
            "gs3_render_environment")
 
 

@@ -14,8 +14,8 @@ namespace gs3 {
 std::atomic<uint64_t> g_launches{0};
 
 namespace {
-
 thread_local std::string g_last_error;
+}  // namespace
 
 gs3_status fail(gs3_status st, const char* msg) {
   g_last_error = msg;
@@ -28,6 +28,23 @@ gs3_status cuda_fail(cudaError_t e, const char* where) {
   g_last_error = buf;
   return GS3_ERR_CUDA;
 }
+
+// Why a light cannot be rendered, or null.
+const char* light_problem(const gs3_light& l, const gs3_render_opts& o) {
+  if (l.type == GS3_LIGHT_POINT) {
+    const float tl[3] = {o.target[0] - l.pos[0], o.target[1] - l.pos[1], o.target[2] - l.pos[2]};
+    if (!(tl[0] * tl[0] + tl[1] * tl[1] + tl[2] * tl[2] >= 1e-12f))
+      return "gs3_render: light coincides with the light-camera target";
+    return nullptr;
+  }
+  if (l.type != GS3_LIGHT_DIRECTIONAL) return "gs3_render: light type must be GS3_LIGHT_POINT or GS3_LIGHT_DIRECTIONAL";
+  if (!(l.dir[0] * l.dir[0] + l.dir[1] * l.dir[1] + l.dir[2] * l.dir[2] >= 1e-12f))
+    return "gs3_render: directional light needs a non-zero direction";
+  if (!(l.extent > 0.f) || !(l.extent < 1e30f)) return "gs3_render: directional light needs extent > 0";
+  return nullptr;
+}
+
+namespace {
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
@@ -48,22 +65,6 @@ bool mlp_ok(const gs3_mlp_desc& m, int in_dim, int out_dim) {
   return m.w && m.b;
 }
 
-// out (+)= w * img over n floats; block 0 also folds the frame's header into
-// the environment words (first non-OK status, largest pair counts)
-__global__ void k_env_accumulate(float* out, const float* img, size_t n, float w, int first, uint32_t* header) {
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-    out[i] = first ? w * img[i] : fmaf(w, img[i], out[i]);
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    uint32_t* env = header + H_ENV;
-    if (first) env[0] = env[1] = env[2] = env[3] = env[4] = 0u;
-    if (env[0] == 0u) env[0] = header[H_STATUS];
-    for (int k = 1; k < 5; ++k) env[k] = max(env[k], header[k]);
-  }
-}
-__global__ void k_env_finish(uint32_t* header) {
-  if (threadIdx.x == 0)
-    for (int k = 0; k < 5; ++k) header[k] = header[H_ENV + k];
-}
 }  // namespace
 
 void set_last_error(const char* msg) { g_last_error = msg; }
@@ -266,6 +267,7 @@ gs3_status gs3_scene_mlp_scales(const gs3_scene* s, int32_t which, float* out, i
 
 gs3_status gs3_destroy_scene(gs3_scene* s) {
   if (!s) return GS3_OK;
+  if (s->env_ready) s->env_bs.destroy();
   for (int w = 0; w < 2; ++w)
     if (s->tc_blob[w]) cudaFree(s->tc_blob[w]);
   delete s;
@@ -300,21 +302,6 @@ gs3_status gs3_workspace_layout(int32_t n, int32_t width, int32_t height, size_t
   out->light_final = L.light_final;
   out->light_stop = L.light_stop;
   return GS3_OK;
-}
-
-// Why a light cannot be rendered, or null.
-static const char* light_problem(const gs3_light& l, const gs3_render_opts& o) {
-  if (l.type == GS3_LIGHT_POINT) {
-    const float tl[3] = {o.target[0] - l.pos[0], o.target[1] - l.pos[1], o.target[2] - l.pos[2]};
-    if (!(tl[0] * tl[0] + tl[1] * tl[1] + tl[2] * tl[2] >= 1e-12f))
-      return "gs3_render: light coincides with the light-camera target";
-    return nullptr;
-  }
-  if (l.type != GS3_LIGHT_DIRECTIONAL) return "gs3_render: light type must be GS3_LIGHT_POINT or GS3_LIGHT_DIRECTIONAL";
-  if (!(l.dir[0] * l.dir[0] + l.dir[1] * l.dir[1] + l.dir[2] * l.dir[2] >= 1e-12f))
-    return "gs3_render: directional light needs a non-zero direction";
-  if (!(l.extent > 0.f) || !(l.extent < 1e30f)) return "gs3_render: directional light needs extent > 0";
-  return nullptr;
 }
 
 gs3_status gs3_render_stages(gs3_scene* scene, const gs3_camera* cam, const gs3_light* light,
@@ -449,6 +436,7 @@ bool BatchStreams::create(int n) {
   if (cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&fork2, cudaEventDisableTiming) != cudaSuccess)
     return false;
+  if (cudaEventCreateWithFlags(&cam, cudaEventDisableTiming) != cudaSuccess) return false;
   for (int r = 0; r < n; ++r) {
     if (cudaStreamCreateWithFlags(&sub[r], cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&join[r], cudaEventDisableTiming) != cudaSuccess ||
@@ -468,7 +456,8 @@ void BatchStreams::destroy() {
   }
   if (fork) cudaEventDestroy(fork);
   if (fork2) cudaEventDestroy(fork2);
-  fork = fork2 = nullptr;
+  if (cam) cudaEventDestroy(cam);
+  fork = fork2 = cam = nullptr;
 }
 
 // A batch of frames rendered together (the serving form; each frame has its
@@ -568,35 +557,6 @@ gs3_status gs3_render(gs3_scene* scene, const gs3_camera* cam, const gs3_light* 
                       size_t key_capacity, void* stream) {
   return gs3_render_stages(scene, cam, light, opts, out_rgb, workspace, ws_bytes, key_capacity,
                            GS3_STAGE_ALL, stream);
-}
-
-gs3_status gs3_render_environment(gs3_scene* scene, const gs3_camera* cam, const gs3_light* lights,
-                                  const float* weights, int32_t count, const gs3_render_opts* opts, float* out_rgb,
-                                  float* scratch_rgb, void* workspace, size_t ws_bytes, size_t key_capacity,
-                                  void* stream) {
-  if (!lights || !weights || count < 1 || !scratch_rgb || !cam)
-    return fail(GS3_ERR_INVALID_ARG, "gs3_render_environment: bad light list or scratch");
-  const size_t n = (size_t)cam->width * cam->height * 3;
-  if (!device_range_ok(scratch_rgb, n * sizeof(float)) || !device_range_ok(out_rgb, n * sizeof(float)))
-    return fail(GS3_ERR_INVALID_ARG, "gs3_render_environment: out_rgb / scratch_rgb not width*height*3 floats");
-  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  for (int32_t l = 0; l < count; ++l) {
-    const gs3_status st = gs3_render(scene, cam, &lights[l], opts, scratch_rgb, workspace, ws_bytes, key_capacity, stream);
-    if (st != GS3_OK) return st;  // argument errors are found on the first light, before any launch
-    uint32_t* header = reinterpret_cast<uint32_t*>(static_cast<unsigned char*>(workspace) +
-                                                   plan_workspace(scene->dev.n, cam->width, cam->height,
-                                                                  key_capacity).header);
-    const size_t want = (n + 255) / 256;
-    const size_t cap_blocks = (size_t)device_sm_count() * 8;
-    const int blocks = (int)(want < cap_blocks ? want : cap_blocks);
-    k_env_accumulate<<<blocks, 256, 0, s>>>(out_rgb, scratch_rgb, n, weights[l], l == 0, header);
-    count_launch();
-  }
-  k_env_finish<<<1, 32, 0, s>>>(reinterpret_cast<uint32_t*>(
-      static_cast<unsigned char*>(workspace) + plan_workspace(scene->dev.n, cam->width, cam->height, key_capacity).header));
-  count_launch();
-  const cudaError_t e = cudaGetLastError();
-  return e == cudaSuccess ? GS3_OK : cuda_fail(e, "gs3_render_environment: launch");
 }
 
 size_t gs3_backward_workspace_size(const gs3_scene* scene) {

@@ -984,6 +984,132 @@ __global__ void __launch_bounds__(256) k_camera(const CamParams p, const CamPara
   }
 }
 
+// ---------------------------------------------------------------------------
+// K9 for an environment light (Sec. 4.5): the camera composite of nl <= 8
+// lights in one pass.  The camera splat (alphas, order, stops) does not
+// depend on the light, so every light's shading S_l and refined shadow Sh_l
+// are composited on the same weights, each into its own accumulators, in the
+// order camera_tile uses (each light's sums equal that light's own frame's);
+// the residual R, which does not see the light, is composited once.
+// out (+)= sum_l w_l (S_l Sh_l + R).
+// ---------------------------------------------------------------------------
+constexpr int kEnvRec = 128;  // records staged per batch
+
+struct EnvCamParams {
+  CamParams c;           // the first light's workspace: camera splat, residual colours, final T
+  const float4* envcol;  // [rank][nl]: (shade_l rgb, T'_l)
+  float w[kMaxBatch];
+  int nl;
+  int accumulate;  // add to out (a later group of lights)
+};
+
+struct EnvSmem {
+  float4 Ga[kEnvRec], Gb[kEnvRec], Gc[kEnvRec], R[kEnvRec];
+  float4 C[kEnvRec][kMaxBatch];
+  uint32_t Gmask[kEnvRec];
+};
+
+__global__ void __launch_bounds__(256) k_camera_env(const EnvCamParams e) {
+  __shared__ EnvSmem M;
+  const CamParams& p = e.c;
+  const int nl = e.nl;
+  const int tile = (int)p.tile_order[blockIdx.x];
+  const int tx = tile % p.gx, ty = tile / p.gx;
+  const int t = threadIdx.x;
+  const uint32_t wbit = 1u << (t >> 5);
+  const int px = tx * kTile + tile_px(t), py = ty * kTile + tile_py(t);
+  const bool inside = px < p.W && py < p.H;
+  const float fx = px + 0.5f, fy = py + 0.5f;
+  const uint32_t b = p.tile_start[tile], end = p.tile_start[tile + 1];
+  float T = 1.f, R0 = 0.f, R1 = 0.f, R2 = 0.f;
+  float S[kMaxBatch][3], Sh[kMaxBatch];
+#pragma unroll
+  for (int l = 0; l < kMaxBatch; ++l) S[l][0] = S[l][1] = S[l][2] = Sh[l] = 0.f;
+  bool done = !inside;
+  uint32_t consumed = 0;
+  for (uint32_t rb = b; rb < end; rb += kEnvRec) {
+    if (__syncthreads_count(done) == 256) break;
+    const int rc = (int)min((uint32_t)kEnvRec, end - rb);
+    if (t < rc) {
+      const uint32_t rank = p.list[rb + t];
+      const SplatRec q = p.rrec[rank];
+      M.Ga[t] = q.a;
+      M.Gb[t] = q.b;
+      M.Gc[t] = q.c;
+      M.Gmask[t] = warp_mask(q, tx, ty);
+      M.R[t] = p.ccol[2 * rank + 1];
+      const float4* src = e.envcol + (size_t)rank * nl;
+#pragma unroll
+      for (int l = 0; l < kMaxBatch; ++l)
+        if (l < nl) M.C[t][l] = src[l];
+    }
+    __syncthreads();
+    if (!done) {
+      auto alpha_of = [&](int jj, float& alpha) -> bool {
+        if (!(M.Gmask[jj] & wbit)) return false;
+        const float4 ga = M.Ga[jj], gc = M.Gc[jj];
+        const float pw = splat_power(ga, M.Gb[jj], gc.x, fx, fy);
+        if (!(pw >= gc.w)) return false;
+        alpha = fminf(p.amax, ga.z * __expf(pw));
+        return true;
+      };
+      auto take = [&](int jj, float alpha) -> bool {
+        const float Tn = T * (1.f - alpha);
+        if (Tn < p.tstop) {
+          done = true;
+          consumed = rb - b + jj;
+          return false;
+        }
+        const float w = alpha * T;
+#pragma unroll
+        for (int l = 0; l < kMaxBatch; ++l) {
+          if (l < nl) {
+            const float4 c = M.C[jj][l];
+            S[l][0] += w * c.x; S[l][1] += w * c.y; S[l][2] += w * c.z;
+            Sh[l] += w * c.w;
+          }
+        }
+        const float4 r = M.R[jj];
+        R0 += w * r.x; R1 += w * r.y; R2 += w * r.z;
+        T = Tn;
+        return true;
+      };
+      for (int jj = 0; jj < rc; jj += 2) {
+        float a0 = 0.f, a1 = 0.f;
+        const bool p0 = alpha_of(jj, a0);
+        const bool p1 = jj + 1 < rc && alpha_of(jj + 1, a1);
+        if (p0 && !take(jj, a0)) break;
+        if (p1 && !take(jj + 1, a1)) break;
+      }
+      if (!done) consumed = rb - b + rc;
+    }
+  }
+  if (inside) {
+    const size_t pix = (size_t)py * p.W + px;
+    float o0 = 0.f, o1 = 0.f, o2 = 0.f;
+#pragma unroll
+    for (int l = 0; l < kMaxBatch; ++l) {
+      if (l < nl) {
+        // the image light l's own frame gives, then its weight
+        const float i0 = S[l][0] * Sh[l] + R0, i1 = S[l][1] * Sh[l] + R1, i2 = S[l][2] * Sh[l] + R2;
+        o0 = fmaf(e.w[l], i0, o0);
+        o1 = fmaf(e.w[l], i1, o1);
+        o2 = fmaf(e.w[l], i2, o2);
+      }
+    }
+    if (e.accumulate) {
+      o0 += p.out[3 * pix + 0];
+      o1 += p.out[3 * pix + 1];
+      o2 += p.out[3 * pix + 2];
+    }
+    p.out[3 * pix + 0] = o0;
+    p.out[3 * pix + 1] = o1;
+    p.out[3 * pix + 2] = o2;
+    p.final_t[pix] = T;
+    p.n_contrib[pix] = consumed;
+  }
+}
+
 // Launch order of a splat's tiles: longest list first, so that the last
 // blocks to start are the short ones and the final partial wave stays short
 // (a longest-processing-time-first schedule).  One block: a counting sort on
@@ -1247,6 +1373,18 @@ void launch_fill_shadow_one(const FrameArgs& f, cudaStream_t s) {
 
 void launch_camera_composite(const FrameArgs& f, float* out_rgb, cudaStream_t s) {
   k_camera<false><<<f.L->ntiles, 256, 0, s>>>(camera_params(f, out_rgb), nullptr, nullptr, 1);
+  count_launch();
+}
+
+void launch_camera_env(const FrameArgs& f0, const float4* envcol, int nl, const float* w, bool accumulate,
+                       float* out_rgb, cudaStream_t s) {
+  EnvCamParams e;
+  e.c = camera_params(f0, out_rgb);
+  e.envcol = envcol;
+  e.nl = nl;
+  for (int l = 0; l < kMaxBatch; ++l) e.w[l] = l < nl ? w[l] : 0.f;
+  e.accumulate = accumulate ? 1 : 0;
+  k_camera_env<<<f0.L->ntiles, 256, 0, s>>>(e);
   count_launch();
 }
 

@@ -82,6 +82,13 @@ struct Workspace {
 
 Workspace plan_workspace(int n, int width, int height, size_t cap);
 
+// Error reporting of the C ABI: sets gs3_last_error's message, returns st /
+// GS3_ERR_CUDA.
+gs3_status fail(gs3_status st, const char* msg);
+gs3_status cuda_fail(cudaError_t e, const char* where);
+// why a light cannot be rendered with these options, or null
+const char* light_problem(const gs3_light& l, const gs3_render_opts& o);
+
 // Header word indices (u32) -- must match gs3_ws_header.
 enum { H_STATUS = 0, H_PAIRS_CAM = 1, H_PAIRS_LIGHT = 2, H_NEED_CAM = 3, H_NEED_LIGHT = 4,
        H_LIGHT_VIEW = 8, H_LIGHT_ORTHO = 20,
@@ -143,13 +150,24 @@ struct BatchFrame {
 // Streams and events of a batch: a sub-stream per frame for the per-frame stages.
 struct BatchStreams {
   cudaStream_t sub[8] = {};
-  cudaEvent_t fork = nullptr, fork2 = nullptr, join[8] = {}, join2[8] = {};
+  cudaEvent_t fork = nullptr, fork2 = nullptr, cam = nullptr, join[8] = {}, join2[8] = {};
   bool create(int n);
   void destroy();
 };
 // Renders n <= kMaxBatch frames together on `stream` (see render_batch in api.cu).
 gs3_status render_batch(const BatchFrame* frames, int n, cudaStream_t stream, BatchStreams& bs,
                         unsigned char* param_dev, unsigned char* param_host);
+
+// Workspace of an environment render: min(count, kMaxBatch) frame
+// workspaces `stride` bytes apart (one per light of a group; the first also
+// holds the camera splat), then the lights' camera colours envcol
+// (float4[N][slices]) and the batch parameter block.
+struct EnvPlan {
+  Workspace L;
+  size_t stride = 0, envcol = 0, params = 0, total = 0;
+  int slices = 0;
+};
+EnvPlan plan_environment(int n, int width, int height, int count, size_t cap);
 
 // ---- launchers (stream-ordered, no host synchronisation) ----
 struct FrameArgs {
@@ -186,7 +204,8 @@ void run_mlp_backward(const MlpArgs& a, void* scratch, float* wred, cudaStream_t
 gs3_status run_backward(const FrameArgs& f, const float* dimg, void* bws, size_t bws_bytes,
                         const gs3_grads& out, cudaStream_t s);
 
-void launch_prep(const FrameArgs& f, cudaStream_t s);
+// shading and both projections (K1); light_only: the shadow splat's projection only
+void launch_prep(const FrameArgs& f, cudaStream_t s, bool light_only = false);
 void launch_depth_sort(const FrameArgs& f, int splat, cudaStream_t s);
 void launch_binning(const FrameArgs& f, int splat, cudaStream_t s);
 void launch_shadow_composite(const FrameArgs& f, cudaStream_t s);
@@ -209,14 +228,26 @@ size_t shadow_seg_items(int ntiles, size_t cap);
 // a splat's tiles ordered longest list first (in length steps of 8), into L.tile_order[splat]
 void launch_tile_order(const FrameArgs& f, int splat, cudaStream_t s);
 void launch_shadow_reduce(const FrameArgs& f, cudaStream_t s);
-void launch_mlp(const FrameArgs& f, cudaStream_t s, bool identity_only = false);
+// Phi and Psi of one frame; which_mask bit 0 Phi, bit 1 Psi; identity_only:
+// only the networks an ablation replaces by the identity / zero
+void launch_mlp(const FrameArgs& f, cudaStream_t s, bool identity_only = false, int which_mask = 3);
+// Phi of nl <= kMaxBatch frames of one scene and camera (an environment
+// light's directional lights; the camera ranks of f[0]) in one launch over
+// nl N rows; (shade_l, T'_l) of camera rank r go to envcol[r nl + l]
+void launch_phi_lights(const FrameArgs* const* f, int nl, float4* envcol, cudaStream_t s);
+void launch_phi_lights_tc(const FrameArgs* const* f, int nl, float4* envcol, const unsigned char* blob,
+                          cudaStream_t s);
 // BF16 / FP8 tensor-core MLPs (mlp_tc.cu)
 size_t mlp_tc_blob_bytes(const MlpDev& m, int dtype);
 size_t mlp_tc_scale_offset(const MlpDev& m, int dtype);  // FP8: (sx, sw) per hidden layer
 void pack_mlp_tc(const MlpDev& m, int dtype, const SceneDev& sc, int which, unsigned char* dst, cudaStream_t s);
 bool mlp_tc_supported(const MlpDev& m, int dtype);
-void launch_mlp_tc(const FrameArgs& f, const unsigned char* const blobs[2], cudaStream_t s);
+void launch_mlp_tc(const FrameArgs& f, const unsigned char* const blobs[2], cudaStream_t s, int which_mask = 3);
 void launch_camera_composite(const FrameArgs& f, float* out_rgb, cudaStream_t s);
+// camera composite of nl <= kMaxBatch lights over f0's camera splat:
+// out (+)= sum_l w[l] (S_l Sh_l + R), (S_l, Sh_l) per camera rank from envcol
+void launch_camera_env(const FrameArgs& f0, const float4* envcol, int nl, const float* w, bool accumulate,
+                       float* out_rgb, cudaStream_t s);
 void launch_fill_shadow_one(const FrameArgs& f, cudaStream_t s);
 
 // exclusive scan of n u32 values (in place allowed: out may equal in);
@@ -283,4 +314,9 @@ __host__ __device__ inline T* at(unsigned char* ws, size_t off) {
 struct gs3_scene {
   gs3::SceneDev dev;
   unsigned char* tc_blob[2] = {nullptr, nullptr};  // tensor-core weights and FP8 scales (owned)
+  // environment renders: sub-streams made on first use; env_mu serialises the
+  // calls' launch sequences on them
+  std::mutex env_mu;
+  gs3::BatchStreams env_bs;
+  bool env_ready = false;
 };

@@ -21,20 +21,37 @@ namespace {
 constexpr int kRows = 64;
 constexpr int kHPad = kRows + 4;  // feature-major activations, padded rows
 
+// Phi runs over the Gaussians of nl lights at once (row l n + g: Gaussian g
+// under light l); Psi, which does not see the light, over one set (nl = 1).
 struct MlpParams {
   MlpDev net;
   int n;
   int which;  // 0 Phi, 1 Psi
+  int nl;     // lights of the batch (Phi), 1 for Psi
   const float4* mean_op;
   const float4* latent;
-  const float* T;
-  float light_pos[3], cam_pos[3];
-  float light_w;     // 1: point light at light_pos; 0: directional, light_pos = unit direction
-  float* out_idx;    // Phi: T' [N];   Psi: float4 residual [N] (as floats)
-  float4* ccol;      // camera colours by rank
+  const float* T[kMaxBatch];       // Phi input T per light, by index
+  float* tp[kMaxBatch];            // Phi output T' per light, by index
+  const float4* shade[kMaxBatch];  // shading per light, by index (envcol only)
+  float4 light[kMaxBatch];         // homogeneous light per light (light_h)
+  float cam_pos[3];
+  float* res_idx;    // Psi: float4 residual [N] (as floats)
+  float4* ccol;      // camera colours by rank: Phi T' into .w of [2r] (nl = 1), Psi residual into [2r + 1]
+  float4* envcol;    // non-null (Phi): (shade_l, T'_l) at [r nl + l] instead of ccol
   const uint32_t* rank_of;
   int identity;      // ablation: Phi -> T' = T, Psi -> 0
 };
+
+// Phi's output for Gaussian g under light l, camera rank r
+__device__ __forceinline__ void put_phi(const MlpParams& p, int l, int g, uint32_t r, float y) {
+  p.tp[l][g] = y;
+  if (p.envcol) {
+    const float4 c = p.shade[l][g];
+    p.envcol[(size_t)r * p.nl + l] = make_float4(c.x, c.y, c.z, y);
+  } else {
+    p.ccol[2 * r].w = y;
+  }
+}
 
 __device__ __forceinline__ void write_pe(float (*H)[kHPad], int base, int row, int q, float v0, float v1,
                                          float v2) {
@@ -59,17 +76,16 @@ __global__ void __launch_bounds__(256) k_mlp(MlpParams p) {
   float* Ws = smem + 128 * kHPad;                                  // [din][dout]
   const int t = threadIdx.x;
   const int g0 = blockIdx.x * kRows;
+  const int rows = p.n * p.nl;
 
   if (p.identity) {
-    if (t < kRows && g0 + t < p.n) {
-      const int g = g0 + t;
+    if (t < kRows && g0 + t < rows) {
+      const int l = (g0 + t) / p.n, g = g0 + t - l * p.n;
       const uint32_t r = p.rank_of[g];
       if (p.which == 0) {
-        const float v = p.T[g];
-        p.out_idx[g] = v;
-        p.ccol[2 * r].w = v;
+        put_phi(p, l, g, r, p.T[l][g]);
       } else {
-        reinterpret_cast<float4*>(p.out_idx)[g] = make_float4(0.f, 0.f, 0.f, 0.f);
+        reinterpret_cast<float4*>(p.res_idx)[g] = make_float4(0.f, 0.f, 0.f, 0.f);
         p.ccol[2 * r + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
       }
     }
@@ -79,10 +95,13 @@ __global__ void __launch_bounds__(256) k_mlp(MlpParams p) {
   // ---- prologue: inputs, 4 threads per row (thread q handles band q) ----
   {
     const int row = t >> 2, q = t & 3;
-    const int g = min(g0 + row, p.n - 1);
+    const int rc = min(g0 + row, rows - 1);
+    const int l = rc / p.n, g = rc - l * p.n;
     const float4 m = p.mean_op[g];
-    const float* src = p.which == 0 ? p.light_pos : p.cam_pos;
-    const float sw = p.which == 0 ? p.light_w : 1.f;
+    const float4 lh = p.light[l];
+    const float src[3] = {p.which == 0 ? lh.x : p.cam_pos[0], p.which == 0 ? lh.y : p.cam_pos[1],
+                          p.which == 0 ? lh.z : p.cam_pos[2]};
+    const float sw = p.which == 0 ? lh.w : 1.f;
     float dx = src[0] - sw * m.x, dy = src[1] - sw * m.y, dz = src[2] - sw * m.z;
     const float il = rsqrtf(dx * dx + dy * dy + dz * dz);
     dx *= il; dy *= il; dz *= il;
@@ -94,7 +113,7 @@ __global__ void __launch_bounds__(256) k_mlp(MlpParams p) {
       const int lb = b0 + 54;
       H[lb + 0][row] = l0.x; H[lb + 1][row] = l0.y; H[lb + 2][row] = l0.z; H[lb + 3][row] = l0.w;
       H[lb + 4][row] = l1.x; H[lb + 5][row] = l1.y;
-      if (p.which == 0) H[0][row] = p.T[g];
+      if (p.which == 0) H[0][row] = p.T[l][g];
     }
   }
 
@@ -149,18 +168,17 @@ __global__ void __launch_bounds__(256) k_mlp(MlpParams p) {
   const int dout = p.net.out_dim;
   if (t < kRows * dout) {
     const int row = t % kRows, o = t / kRows;
-    const int g = g0 + row;
     float acc = bias[o];
     const float* wr = w + (size_t)o * din;
     for (int k = 0; k < din; ++k) acc = fmaf(H[k][row], wr[k], acc);
     const float y = 1.f / (1.f + __expf(-acc));
-    if (g < p.n) {
+    if (g0 + row < rows) {
+      const int l = (g0 + row) / p.n, g = g0 + row - l * p.n;
       const uint32_t r = p.rank_of[g];
       if (p.which == 0) {
-        p.out_idx[g] = y;
-        p.ccol[2 * r].w = y;
+        put_phi(p, l, g, r, y);
       } else {
-        p.out_idx[4 * g + o] = y;
+        p.res_idx[4 * g + o] = y;
         reinterpret_cast<float*>(&p.ccol[2 * r + 1])[o] = y;
       }
     }
@@ -174,7 +192,7 @@ void launch_width(const MlpParams& p, cudaStream_t s) {
   once.run([sm] {
     return cudaFuncSetAttribute(k_mlp<WIDTH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) == cudaSuccess;
   });
-  k_mlp<WIDTH><<<(p.n + kRows - 1) / kRows, 256, sm, s>>>(p);
+  k_mlp<WIDTH><<<(p.n * p.nl + kRows - 1) / kRows, 256, sm, s>>>(p);
   count_launch();
 }
 
@@ -189,29 +207,55 @@ void launch_one(const MlpParams& p, cudaStream_t s) {
 
 }  // namespace
 
-void launch_mlp(const FrameArgs& f, cudaStream_t s, bool identity_only) {
+void launch_mlp(const FrameArgs& f, cudaStream_t s, bool identity_only, int which_mask) {
   MlpParams p;
   p.n = f.sc.n;
+  p.nl = 1;
   p.mean_op = f.sc.mean_op;
   p.latent = f.sc.latent;
-  p.T = at<float>(f.ws, f.L->T);
-  const float4 lh = light_h(f.light);
-  p.light_pos[0] = lh.x; p.light_pos[1] = lh.y; p.light_pos[2] = lh.z; p.light_w = lh.w;
+  p.T[0] = at<float>(f.ws, f.L->T);
+  p.tp[0] = at<float>(f.ws, f.L->Tp);
+  p.shade[0] = at<float4>(f.ws, f.L->shade);
+  p.light[0] = light_h(f.light);
   for (int i = 0; i < 3; ++i) p.cam_pos[i] = f.cam.pos[i];
+  p.res_idx = at<float>(f.ws, f.L->res);
   p.ccol = at<float4>(f.ws, f.L->ccol);
+  p.envcol = nullptr;
   p.rank_of = at<uint32_t>(f.ws, f.L->sp[0].rank_of);
 
   p.net = f.sc.phi;
   p.which = 0;
-  p.out_idx = at<float>(f.ws, f.L->Tp);
   p.identity = (f.opts.ablate & GS3_ABLATE_PHI) != 0;
-  if (p.identity || !identity_only) launch_one(p, s);
+  if ((which_mask & 1) && (p.identity || !identity_only)) launch_one(p, s);
 
   p.net = f.sc.psi;
   p.which = 1;
-  p.out_idx = at<float>(f.ws, f.L->res);
   p.identity = (f.opts.ablate & GS3_ABLATE_PSI) != 0;
-  if (p.identity || !identity_only) launch_one(p, s);
+  if ((which_mask & 2) && (p.identity || !identity_only)) launch_one(p, s);
+}
+
+void launch_phi_lights(const FrameArgs* const* f, int nl, float4* envcol, cudaStream_t s) {
+  MlpParams p;
+  const FrameArgs& f0 = *f[0];
+  p.net = f0.sc.phi;
+  p.n = f0.sc.n;
+  p.which = 0;
+  p.nl = nl;
+  p.mean_op = f0.sc.mean_op;
+  p.latent = f0.sc.latent;
+  for (int l = 0; l < nl; ++l) {
+    p.T[l] = at<float>(f[l]->ws, f[l]->L->T);
+    p.tp[l] = at<float>(f[l]->ws, f[l]->L->Tp);
+    p.shade[l] = at<float4>(f[l]->ws, f[l]->L->shade);
+    p.light[l] = light_h(f[l]->light);
+  }
+  for (int i = 0; i < 3; ++i) p.cam_pos[i] = f0.cam.pos[i];
+  p.res_idx = nullptr;
+  p.ccol = nullptr;
+  p.envcol = envcol;
+  p.rank_of = at<uint32_t>(f0.ws, f0.L->sp[0].rank_of);
+  p.identity = (f0.opts.ablate & GS3_ABLATE_PHI) != 0;
+  launch_one(p, s);
 }
 
 }  // namespace gs3

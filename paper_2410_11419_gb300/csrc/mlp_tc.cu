@@ -161,11 +161,14 @@ struct TcParams {
   const float* bout;  // out_dim
   const float4* mean_op;
   const float4* latent;
-  const float* T;
-  float light_pos[3], cam_pos[3];
-  float light_w;  // 1: point light at light_pos; 0: directional, light_pos = unit direction
-  float* out_idx;
-  float4* ccol;
+  int nl;                          // Phi: lights of the batch (row l n + g); Psi: 1
+  const float* T[kMaxBatch];       // Phi input T per light, by index
+  float* out[kMaxBatch];           // Phi: T' per light; Psi: float4 residual at [0]
+  const float4* shade[kMaxBatch];  // shading per light, by index (envcol only)
+  float4 light[kMaxBatch];         // homogeneous light per light (light_h)
+  float cam_pos[3];
+  float4* ccol;    // camera colours by rank (nl = 1)
+  float4* envcol;  // non-null (Phi): (shade_l, T'_l) at [r nl + l] instead of ccol
   const uint32_t* rank_of;
   uint32_t* status;
 };
@@ -260,20 +263,24 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_tc(TcParams p) {
   const uint32_t my_lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
   const bool leaky = p.act == GS3_ACT_LEAKY_RELU;
   uint32_t phase = 0;
-  const int ntiles = (p.n + kTcRows - 1) / kTcRows;
+  const int rows = p.n * p.nl;
+  const int ntiles = (rows + kTcRows - 1) / kTcRows;
   for (int tile = blockIdx.x; tile < ntiles && !fail; tile += gridDim.x) {
     const int row = tile * kTcRows + t;
-    const int g = min(row, p.n - 1);
+    const int rc = min(row, rows - 1);
+    const int li = rc / p.n, g = rc - li * p.n;
     // ---- encoded input row, BF16, K padded to 64 ----
     {
       float x[kK0];
       const float4 m = p.mean_op[g];
-      const float* src = p.which == 0 ? p.light_pos : p.cam_pos;
-      const float sw = p.which == 0 ? p.light_w : 1.f;
-      float dx = src[0] - sw * m.x, dy = src[1] - sw * m.y, dz = src[2] - sw * m.z;
+      const float4 lh = p.light[li];
+      const float sx = p.which == 0 ? lh.x : p.cam_pos[0], sy = p.which == 0 ? lh.y : p.cam_pos[1],
+                  sz = p.which == 0 ? lh.z : p.cam_pos[2];
+      const float sw = p.which == 0 ? lh.w : 1.f;
+      float dx = sx - sw * m.x, dy = sy - sw * m.y, dz = sz - sw * m.z;
       const float il = rsqrtf(dx * dx + dy * dy + dz * dz);
       const int b0 = p.which == 0 ? 1 : 0;
-      if (p.which == 0) x[0] = p.T[g];
+      if (p.which == 0) x[0] = p.T[li][g];
       pe_row(x, b0, dx * il, dy * il, dz * il);
       pe_row(x, b0 + 27, m.x, m.y, m.z);
       const float4 l0 = p.latent[g], l1 = p.latent[p.n + g];
@@ -336,19 +343,24 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_tc(TcParams p) {
       if (fail) break;
     }
     if (fail) break;
-    if (row < p.n) {
-      const uint32_t r = p.rank_of[row];
+    if (row < rows) {
+      const uint32_t r = p.rank_of[g];
       if (p.which == 0) {
         const float y = 1.f / (1.f + __expf(-(acc_out[0] + bosm[0])));
-        p.out_idx[row] = y;
-        p.ccol[2 * r].w = y;
+        p.out[li][g] = y;
+        if (p.envcol) {
+          const float4 c = p.shade[li][g];
+          p.envcol[(size_t)r * p.nl + li] = make_float4(c.x, c.y, c.z, y);
+        } else {
+          p.ccol[2 * r].w = y;
+        }
       } else {
         float4 y;
         y.x = 1.f / (1.f + __expf(-(acc_out[0] + bosm[0])));
         y.y = 1.f / (1.f + __expf(-(acc_out[1] + bosm[1])));
         y.z = 1.f / (1.f + __expf(-(acc_out[2] + bosm[2])));
         y.w = 0.f;
-        reinterpret_cast<float4*>(p.out_idx)[row] = y;
+        reinterpret_cast<float4*>(p.out[0])[g] = y;
         p.ccol[2 * r + 1] = y;
       }
     }
@@ -522,46 +534,78 @@ bool mlp_tc_supported(const MlpDev& m, int dtype) {
          tc_smem_bytes(m, eb) <= 220 * 1024;
 }
 
-void launch_mlp_tc(const FrameArgs& f, const unsigned char* const blobs[2], cudaStream_t s) {
+namespace {
+
+// parameters of one network over one frame's Gaussians (lights filled by the caller)
+TcParams tc_params(const FrameArgs& f, int which, const unsigned char* blob) {
+  const int eb = elem_bytes(f.sc.mlp_dtype);
+  const MlpDev& m = which == 0 ? f.sc.phi : f.sc.psi;
+  TcParams p;
+  p.n = f.sc.n;
+  p.which = which;
+  p.nh = m.n_hidden;
+  p.width = m.width;
+  p.out_dim = m.out_dim;
+  p.act = m.act;
+  p.wblob = blob;
+  p.wblob_bytes = (uint32_t)weight_bytes(m, eb);
+  p.scales = eb == 1 ? reinterpret_cast<const float*>(blob + scale_offset(m, eb)) : nullptr;
+  size_t hidden_w = 0;
+  for (int l = 0; l < m.n_hidden; ++l) hidden_w += (size_t)m.width * (l == 0 ? m.in_dim : m.width);
+  p.bias = m.b;
+  p.wout = m.w + hidden_w;
+  p.bout = m.b + (size_t)m.n_hidden * m.width;
+  p.mean_op = f.sc.mean_op;
+  p.latent = f.sc.latent;
+  p.nl = 1;
+  p.T[0] = at<float>(f.ws, f.L->T);
+  p.out[0] = at<float>(f.ws, which == 0 ? f.L->Tp : f.L->res);
+  p.shade[0] = at<float4>(f.ws, f.L->shade);
+  p.light[0] = light_h(f.light);
+  for (int i = 0; i < 3; ++i) p.cam_pos[i] = f.cam.pos[i];
+  p.ccol = at<float4>(f.ws, f.L->ccol);
+  p.envcol = nullptr;
+  p.rank_of = at<uint32_t>(f.ws, f.L->sp[0].rank_of);
+  p.status = at<uint32_t>(f.ws, f.L->header) + H_STATUS;
+  return p;
+}
+
+void launch_tc(const TcParams& p, const MlpDev& m, int eb, cudaStream_t s) {
+  const size_t smem = tc_smem_bytes(m, eb);
+  auto kern = eb == 2 ? k_mlp_tc<2> : k_mlp_tc<1>;
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const int nsm = device_sm_count();
+  const int ntiles = (p.n * p.nl + kTcRows - 1) / kTcRows;
+  const int grid = ntiles < nsm ? ntiles : nsm;
+  kern<<<grid, kTcThreads, smem, s>>>(p);
+  count_launch();
+}
+
+}  // namespace
+
+void launch_mlp_tc(const FrameArgs& f, const unsigned char* const blobs[2], cudaStream_t s, int which_mask) {
   const int eb = elem_bytes(f.sc.mlp_dtype);
   for (int which = 0; which < 2; ++which) {
-    const MlpDev& m = which == 0 ? f.sc.phi : f.sc.psi;
+    if (!(which_mask & (1 << which))) continue;
     const bool identity = (f.opts.ablate & (which == 0 ? GS3_ABLATE_PHI : GS3_ABLATE_PSI)) != 0;
     if (identity) continue;  // handled by the FP32 kernel's identity path
-    TcParams p;
-    p.n = f.sc.n;
-    p.which = which;
-    p.nh = m.n_hidden;
-    p.width = m.width;
-    p.out_dim = m.out_dim;
-    p.act = m.act;
-    p.wblob = blobs[which];
-    p.wblob_bytes = (uint32_t)weight_bytes(m, eb);
-    p.scales = eb == 1 ? reinterpret_cast<const float*>(blobs[which] + scale_offset(m, eb)) : nullptr;
-    size_t hidden_w = 0;
-    for (int l = 0; l < m.n_hidden; ++l) hidden_w += (size_t)m.width * (l == 0 ? m.in_dim : m.width);
-    p.bias = m.b;
-    p.wout = m.w + hidden_w;
-    p.bout = m.b + (size_t)m.n_hidden * m.width;
-    p.mean_op = f.sc.mean_op;
-    p.latent = f.sc.latent;
-    p.T = at<float>(f.ws, f.L->T);
-    const float4 lh = light_h(f.light);
-    p.light_pos[0] = lh.x; p.light_pos[1] = lh.y; p.light_pos[2] = lh.z; p.light_w = lh.w;
-    for (int i = 0; i < 3; ++i) p.cam_pos[i] = f.cam.pos[i];
-    p.out_idx = at<float>(f.ws, which == 0 ? f.L->Tp : f.L->res);
-    p.ccol = at<float4>(f.ws, f.L->ccol);
-    p.rank_of = at<uint32_t>(f.ws, f.L->sp[0].rank_of);
-    p.status = at<uint32_t>(f.ws, f.L->header) + H_STATUS;
-    const size_t smem = tc_smem_bytes(m, eb);
-    auto kern = eb == 2 ? k_mlp_tc<2> : k_mlp_tc<1>;
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    const int nsm = device_sm_count();
-    const int ntiles = (f.sc.n + kTcRows - 1) / kTcRows;
-    const int grid = ntiles < nsm ? ntiles : nsm;
-    kern<<<grid, kTcThreads, smem, s>>>(p);
-    count_launch();
+    launch_tc(tc_params(f, which, blobs[which]), which == 0 ? f.sc.phi : f.sc.psi, eb, s);
   }
+}
+
+void launch_phi_lights_tc(const FrameArgs* const* f, int nl, float4* envcol, const unsigned char* blob,
+                          cudaStream_t s) {
+  TcParams p = tc_params(*f[0], 0, blob);
+  p.nl = nl;
+  for (int l = 0; l < nl; ++l) {
+    p.T[l] = at<float>(f[l]->ws, f[l]->L->T);
+    p.out[l] = at<float>(f[l]->ws, f[l]->L->Tp);
+    p.shade[l] = at<float4>(f[l]->ws, f[l]->L->shade);
+    p.light[l] = light_h(f[l]->light);
+  }
+  p.ccol = nullptr;
+  p.envcol = envcol;
+  launch_tc(p, f[0]->sc.phi, elem_bytes(f[0]->sc.mlp_dtype), s);
 }
 
 }  // namespace gs3

@@ -297,6 +297,7 @@ struct PrepParams {
   float intensity;
   gs3_render_opts o;
   int gx, gy;
+  int sp0;  // first splat projected: 0 camera and light, 1 light only
   uint32_t* key[2];
   SplatRec* rec[2];
   int4* rect[2];
@@ -333,6 +334,7 @@ __global__ void __launch_bounds__(256) k_prep(PrepParams p) {
 
 #pragma unroll
   for (int sp = 0; sp < 2; ++sp) {
+    if (sp < p.sp0) continue;
     SplatRec rec;
     bool vis = project_rn(m, s, q, sp ? lv : p.cam, p.o, p.gx, p.gy, sp ? p.light.pos : nullptr, gamma,
                           p.nl_amin, rec);
@@ -394,8 +396,9 @@ __global__ void __launch_bounds__(256) k_prep(PrepParams p) {
 
 }  // namespace
 
-void launch_prep(const FrameArgs& f, cudaStream_t s) {
+void launch_prep(const FrameArgs& f, cudaStream_t s, bool light_only) {
   PrepParams p;
+  p.sp0 = light_only ? 1 : 0;
   p.sc = f.sc;
   for (int i = 0; i < 9; ++i) p.cam.R[i] = f.cam.R[i];
   for (int i = 0; i < 3; ++i) { p.cam.t[i] = f.cam.t[i]; p.cam_pos[i] = f.cam.pos[i]; }

@@ -107,15 +107,25 @@ class Renderer:
                      self.cap, s.cuda_stream)
         return out
 
+    def env_workspace(self, count: int):
+        """The 256-byte aligned workspace of an environment render of `count` lights."""
+        nbytes = N.gs3_environment_workspace_size(self.scene.n, self.width, self.height, max(count, 1),
+                                                  self.cap)
+        have = getattr(self, "env_ws", None)
+        if have is None or have.numel() < nbytes:
+            raw = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.ws.device)
+            pad = (-raw.data_ptr()) % 256
+            self.env_ws = raw[pad:pad + nbytes]
+        return self.env_ws
+
     def render_environment(self, cam, lights, weights, opts=None, out=None, stream=None):
-        """Sec. 4.5: sum_l weights[l] * render(lights[l]) (directional lights)."""
+        """Sec. 4.5: sum_l weights[l] * render(lights[l]) (directional lights), one batched frame."""
         opts = opts if opts is not None else opts_struct()
         out = self.image if out is None else out
-        if getattr(self, "env_scratch", None) is None:
-            self.env_scratch = torch.empty_like(self.image)
+        ws = self.env_workspace(len(lights))
         s = torch.cuda.current_stream() if stream is None else stream
         N.gs3_render_environment(self.scene.handle, camera_struct(cam), [light_struct(L) for L in lights],
-                                 weights, opts, out, self.env_scratch, self.ws, self.cap, s.cuda_stream)
+                                 weights, opts, out, ws, self.cap, s.cuda_stream)
         return out
 
     def render_stages(self, cam, light, stages: int, opts=None, out=None, stream=None):
@@ -142,6 +152,11 @@ class Renderer:
     def header(self, stream=None) -> N.gs3_ws_header:
         s = torch.cuda.current_stream() if stream is None else stream
         return N.gs3_workspace_read_header(self.ws, s.cuda_stream)
+
+    def env_header(self, stream=None) -> N.gs3_ws_header:
+        """Header of the last environment render (status, camera and largest light pair counts)."""
+        s = torch.cuda.current_stream() if stream is None else stream
+        return N.gs3_workspace_read_header(self.env_ws, s.cuda_stream)
 
     def check(self):
         h = self.header()

@@ -4,8 +4,11 @@
   view (rotation, translation, pixel scale) equal bit for bit, keys, lists and
   ranges of both splats bit-exact, and the floating-point stages within
   1e-4 relative + 1e-6 + the oracle's decision bounds.
-* gs3_render_environment equals the weighted sum of single renders, and the
-  oracle's environment image within the summed tolerances.
+* gs3_render_environment (one batched frame) equals the weighted sum of
+  single renders, and the oracle's environment image within the summed
+  tolerances: 9 lights (a group of 8 and one more), FP32 and BF16 MLPs, the
+  ablations; its header reports the camera's and the largest light pair
+  counts.
 * The backward of a directional frame against the FP64 gradient oracle.
 """
 import numpy as np
@@ -55,14 +58,19 @@ def test_environment_render(gs3, oracle):
     rd = R.Renderer(ds, 96, 96, 1 << 20)
     env = rd.render_environment(cam, lights, w).clone()
     torch.cuda.synchronize()
-    rd.check()
+    eh = rd.env_header()
+    assert eh.status == 0
     # the weighted sum of the single renders, accumulated in the same order
     acc = None
+    light_pairs = []
     for L, wl in zip(lights, w):
         img = rd.render(cam, L).clone().double()
+        h = rd.check()
+        light_pairs.append(h.pairs_light)
         acc = float(wl) * img if acc is None else acc + float(wl) * img
     torch.cuda.synchronize()
     np.testing.assert_allclose(env.double().cpu().numpy(), acc.cpu().numpy(), rtol=1e-6, atol=1e-7)
+    assert eh.pairs_cam == h.pairs_cam and eh.pairs_light == max(light_pairs)
     # against the oracle: sum of per-light tolerances
     want = np.zeros((96, 96, 3))
     tol = np.zeros((96, 96, 3))
@@ -72,6 +80,60 @@ def test_environment_render(gs3, oracle):
         tol += abs(float(wl)) * (1e-4 * np.abs(fr["img"]) + 1e-6 + fr["img_bound"])
     err = np.abs(env.double().cpu().numpy() - want)
     assert np.all(err <= tol + 1e-6), float((err - tol).max())
+    ds.close()
+
+
+ENV_VARIANTS = [
+    ("bf16_3", "bf16", 3, 0),
+    ("fp8_8", "fp8", 8, 0),
+    ("fp32_no_shadow_splat", "fp32", 5, "shadow"),
+    ("bf16_identity_phi_psi", "bf16", 4, "mlps"),
+    ("fp32_17", "fp32", 17, 0),
+]
+
+
+@pytest.mark.parametrize("name,dtype,count,ablate", ENV_VARIANTS, ids=[v[0] for v in ENV_VARIANTS])
+def test_environment_equals_single_frames(gs3, name, dtype, count, ablate):
+    """The batched environment frame against the weighted sum of the same
+    lights' single frames, for the tensor-core MLPs, the ablations and more
+    than two groups of lights; each light's shadow values T and refined T'
+    (batched Phi over the group's lights) equal its single frame's bit for bit."""
+    import torch
+    from paper_2410_11419_gb300 import _native as N, render as R
+    scene = synth.make_scene(3, 3000, 4, "ball")
+    cam, _ = synth.camera_light_pair(6, 120, 104)
+    lights, w = synth.environment_lights(11, count)
+    mlp = {"fp32": N.GS3_MLP_FP32, "bf16": N.GS3_MLP_BF16, "fp8": N.GS3_MLP_FP8_E4M3}[dtype]
+    ds = R.DeviceScene(scene, mlp_dtype=mlp)
+    rd = R.Renderer(ds, 120, 104, 1 << 20)
+    opts = R.opts_struct()
+    if ablate == "shadow":
+        opts.ablate = N.GS3_ABLATE_SHADOW_SPLAT
+    elif ablate == "mlps":
+        opts.ablate = N.GS3_ABLATE_PHI | N.GS3_ABLATE_PSI
+    env = rd.render_environment(cam, lights, w, opts=opts).clone()
+    torch.cuda.synchronize()
+    assert rd.env_header().status == 0
+    # the last group's lights keep their shadow values in the workspace's
+    # per-light frames (8 lights per group), 256-byte aligned frame sizes apart
+    n = scene.n
+    stride = (N.gs3_workspace_size(n, 120, 104, rd.cap) + 255) // 256 * 256
+    g0 = 8 * ((count - 1) // 8)
+    kept = {}
+    for li in range(g0, count):
+        base = (li - g0) * stride
+        kept[li] = {nm: rd.env_ws[base + off:base + off + 4 * n].view(torch.float32).clone()
+                    for nm, off in (("T", rd.layout.shadow), ("Tp", rd.layout.shadow_refined))}
+    acc = None
+    for li, (L, wl) in enumerate(zip(lights, w)):
+        img = rd.render(cam, L, opts=opts).clone().double()
+        rd.check()
+        if li in kept:
+            for nm in ("T", "Tp"):
+                assert torch.equal(kept[li][nm], rd.stage(nm)), (li, nm)
+        acc = float(wl) * img if acc is None else acc + float(wl) * img
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(env.double().cpu().numpy(), acc.cpu().numpy(), rtol=2e-6, atol=1e-7)
     ds.close()
 
 
