@@ -243,10 +243,10 @@ gs3_status gs3_render_stages(gs3_scene *scene, const gs3_camera *camera, const g
  * gs3_render gives for lights[l]), the lights directional (or point), all
  * rendered as one batched frame.  The camera splat, Psi and the camera
  * composite's weights do not depend on the light and run once; per group of
- * up to 8 lights, the shadow composites run in single launches, Phi runs
- * once over 8 N rows, and one camera composite adds the group's
- * sum_l w_l (S_l Sh_l + R).  Each light's shadow values and refined shadow
- * equal those of its own gs3_render.
+ * up to 8 lights, the lights' shadow splats run beside one another on
+ * sub-streams, Phi runs once over 8 N rows, and one camera composite adds the
+ * group's sum_l w_l (S_l Sh_l + R).  Each light's shadow values and refined
+ * shadow equal those of its own gs3_render.
  *   lights, weights: host arrays of `count` entries, 1 <= count <= 4096
  *   out_rgb:         device float32 [height][width][3], overwritten
  *   workspace:       device, 256-byte aligned, at least

@@ -8,20 +8,17 @@
 // composite's alphas are the same for every light.  So for lights taken in
 // groups of up to kMaxBatch:
 //   1. per light, on its own sub-stream: header reset, shading and the light
-//      projection, light binning and the shadow composite's set-up; for the
-//      first group, the first light's sub-stream then bins the camera splat
-//      and runs Psi, beside step 2;
-//   2. on `stream`: the shadow composite's segment kernels over every light
-//      of the group in single launches (the serving batch's kernels);
-//   3. per light: the shadow reduce;
-//   4. on `stream`: Phi over the group's lights in one launch over nl N rows,
+//      projection, light binning, shadow composite and shadow average (the
+//      lights' persistent composite kernels run beside one another);
+//   2. once, on `stream`, beside step 1: the camera splat's binning and tile
+//      order, then Psi;
+//   3. on `stream`: Phi over the group's lights in one launch over nl N rows,
 //      writing (S_l, T'_l) per camera rank and light;
-//   5. one camera composite of the group's lights (k_camera_env), which adds
+//   4. one camera composite of the group's lights (k_camera_env), which adds
 //      sum_l w_l (S_l Sh_l + R) into the image.
-// Each light's shadow splat and Phi outputs equal that light's single frame
+// Each light's shadow values and Phi outputs equal that light's single frame
 // bit for bit, and so do its composited S_l and Sh_l.
 #include <mutex>
-#include <vector>
 
 #include "gs3_internal.cuh"
 
@@ -64,8 +61,7 @@ EnvPlan plan_environment(int n, int width, int height, int count, size_t cap) {
   E.stride = (E.L.total + 255) & ~size_t(255);
   E.slices = count < kMaxBatch ? count : kMaxBatch;
   E.envcol = E.stride * (size_t)E.slices;
-  E.params = (E.envcol + 16ull * (size_t)n * (size_t)E.slices + 255) & ~size_t(255);
-  E.total = E.params + batch_param_bytes();
+  E.total = E.envcol + 16ull * (size_t)n * (size_t)E.slices;
   return E;
 }
 
@@ -137,54 +133,41 @@ gs3_status gs3_render_environment(gs3_scene* scene, const gs3_camera* cam, const
   const bool no_shadow = (opts->ablate & GS3_ABLATE_SHADOW_SPLAT) != 0;
   const bool tc = scene->dev.mlp_dtype != GS3_MLP_FP32;
   const unsigned char* blobs[2] = {scene->tc_blob[0], scene->tc_blob[1]};
-  // pageable staging for the batch parameters: cudaMemcpyAsync has consumed
-  // it by the time it returns
-  std::vector<unsigned char> host(batch_param_bytes());
   for (int32_t g0 = 0; g0 < count; g0 += kMaxBatch) {
     const int nl = count - g0 < kMaxBatch ? count - g0 : kMaxBatch;
     const bool first = g0 == 0;
     for (int r = 0; r < nl; ++r) f[r].light = lights[g0 + r];
-    // 1. per light: shading, light projection and binning; the camera splat
-    //    and Psi once, on the first light's stream
+    // 1. per light, on its sub-stream: shading, the light projection, binning,
+    //    shadow composite and average
     cudaEventRecord(bs.fork, s);
-    const FrameArgs* shadowed[kMaxBatch];
-    int ns = 0;
     for (int r = 0; r < nl; ++r) {
       cudaStream_t sr = bs.sub[r];
       cudaStreamWaitEvent(sr, bs.fork, 0);
       cudaMemsetAsync(f[r].ws + E.L.header, 0, 4 * H_RESET_WORDS, sr);
       launch_prep(f[r], sr, /*light_only=*/!(first && r == 0));
-      if (!no_shadow) {
+      if (first && r == 0) cudaEventRecord(bs.cam, sr);  // the camera projection is done
+      if (no_shadow) {
+        launch_fill_shadow_one(f[r], sr);
+      } else {
         launch_depth_sort(f[r], 1, sr);
         launch_binning(f[r], 1, sr);
-        prepare_shadow_composite(f[r], sr);
-        shadowed[ns++] = &f[r];
+        launch_shadow_composite(f[r], sr);
+        launch_shadow_reduce(f[r], sr);
       }
       cudaEventRecord(bs.join[r], sr);
-      if (first && r == 0) {
-        launch_depth_sort(f[0], 0, sr);
-        launch_binning(f[0], 0, sr);
-        launch_tile_order(f[0], 0, sr);
-        launch_mlp(f[0], sr, /*identity_only=*/tc, /*which_mask=*/2);
-        if (tc) launch_mlp_tc(f[0], blobs, sr, /*which_mask=*/2);
-        cudaEventRecord(bs.cam, sr);
-      }
+    }
+    if (first) {
+      // 2. once, on `stream` beside the light chains: the camera splat (after
+      //    the first light's projections) and Psi
+      cudaStreamWaitEvent(s, bs.cam, 0);
+      launch_depth_sort(f[0], 0, s);
+      launch_binning(f[0], 0, s);
+      launch_tile_order(f[0], 0, s);
+      launch_mlp(f[0], s, /*identity_only=*/tc, /*which_mask=*/2);
+      if (tc) launch_mlp_tc(f[0], blobs, s, /*which_mask=*/2);
     }
     for (int r = 0; r < nl; ++r) cudaStreamWaitEvent(s, bs.join[r], 0);
-    // 2. the group's shadow composites
-    if (ns > 0) launch_shadow_composite_batch(shadowed, ns, base + E.params, host.data(), s);
-    // 3. per light: the shadow average
-    cudaEventRecord(bs.fork2, s);
-    for (int r = 0; r < nl; ++r) {
-      cudaStream_t sr = bs.sub[r];
-      cudaStreamWaitEvent(sr, bs.fork2, 0);
-      if (no_shadow) launch_fill_shadow_one(f[r], sr);
-      else launch_shadow_reduce(f[r], sr);
-      cudaEventRecord(bs.join2[r], sr);
-    }
-    for (int r = 0; r < nl; ++r) cudaStreamWaitEvent(s, bs.join2[r], 0);
-    cudaStreamWaitEvent(s, bs.cam, 0);
-    // 4. Phi over the group's lights; 5. their camera composite
+    // 3. Phi over the group's lights; 4. their camera composite
     const FrameArgs* fl[kMaxBatch];
     for (int r = 0; r < nl; ++r) fl[r] = &f[r];
     if (tc && !(opts->ablate & GS3_ABLATE_PHI)) launch_phi_lights_tc(fl, nl, envcol, blobs[0], s);

@@ -161,10 +161,10 @@ gs3_status render_batch(const BatchFrame* frames, int n, cudaStream_t stream, Ba
 // Workspace of an environment render: min(count, kMaxBatch) frame
 // workspaces `stride` bytes apart (one per light of a group; the first also
 // holds the camera splat), then the lights' camera colours envcol
-// (float4[N][slices]) and the batch parameter block.
+// (float4[N][slices]).
 struct EnvPlan {
   Workspace L;
-  size_t stride = 0, envcol = 0, params = 0, total = 0;
+  size_t stride = 0, envcol = 0, total = 0;
   int slices = 0;
 };
 EnvPlan plan_environment(int n, int width, int height, int count, size_t cap);
