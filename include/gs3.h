@@ -54,8 +54,9 @@ enum { GS3_ACT_RELU = 0, GS3_ACT_LEAKY_RELU = 1 };         /* hidden-layer activ
  * scaled by max|W| / 448, each hidden layer's input by twice its largest
  * magnitude over a calibration pass that gs3_create_scene runs (FP32, on a
  * strided sample of up to 16384 Gaussians for 8 fixed directions); inputs
- * beyond the calibrated range saturate at 448.  FP8 needs hidden widths of
- * 32, 64 or 128. */
+ * beyond the calibrated range saturate at 448.  BF16 and FP8 need hidden
+ * widths of 32, 64 or 128 (gs3_create_scene: GS3_ERR_UNSUPPORTED otherwise).
+ * BF16 layers start their FP32 accumulators at the bias. */
 enum { GS3_MLP_FP32 = 0, GS3_MLP_BF16 = 1, GS3_MLP_FP8_E4M3 = 2 };
 /* Ablations (render modes): no shadow splat (T = 1), no Phi (T' = T), no Psi
  * (residual 0), Lambertian only (no angular-Gaussian lobes: the first stage

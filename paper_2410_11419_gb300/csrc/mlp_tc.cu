@@ -11,19 +11,26 @@
 // eight fixed directions), so inputs up to twice the calibrated range stay
 // finite; larger ones saturate.
 //
-// One persistent CTA per SM, 128 threads, thread t owns row t of a 128-row
-// tile of Gaussians:
-//   - once per CTA: the hidden layers' BF16 weights (pre-arranged at scene
+// One persistent CTA per SM with up to three warpgroups (128 threads each);
+// each warpgroup owns one 128-row tile of Gaussians at a time, thread t of
+// the group row t, so that up to three tiles are in flight and one group's
+// MMAs run while the others encode their inputs or run their epilogues:
+//   - once per CTA: the hidden layers' weights (pre-arranged at scene
 //     creation in the K-major, no-swizzle core-matrix layout the MMA reads)
-//     arrive by bulk TMA copies on an mbarrier; biases and the FP32 output
-//     layer by plain loads; the accumulator columns are allocated in TMEM;
-//   - per tile: each thread writes its row's encoded input [T, PE(w), PE(mu), l]
-//     (K padded to 64) as BF16 into shared memory; for every hidden layer one
-//     thread issues the tcgen05.mma chain (M = 128, N = width, K = 16 per
-//     instruction) and commits it to an mbarrier; after the wait every thread
-//     reads its accumulator row back with tcgen05.ld, adds the bias, applies
-//     the activation and stores BF16 as the next layer's A operand; the last
+//     arrive by bulk TMA copies on an mbarrier, shared by the groups; biases
+//     and the FP32 output layer by plain loads; each group gets its own
+//     accumulator columns in TMEM;
+//   - per tile, within a group: each thread writes its row's encoded input
+//     [T, PE(w), PE(mu), l] (K padded to 64) as BF16 into the group's
+//     activation tile; for every hidden layer one thread issues the
+//     tcgen05.mma chain (M = 128, N = width, K = 16 per instruction) and
+//     commits it to the group's mbarrier; after the wait every thread reads
+//     its accumulator row back with tcgen05.ld, adds the bias, applies the
+//     activation and stores BF16 into the same activation tile as the next
+//     layer's A operand (the MMAs that read it have completed); the last
 //     hidden layer feeds the output layer and the sigmoid in FP32 registers.
+//     A group synchronises on its own named barrier.
+// Phi can run over the Gaussians of several lights at once (rows l N + g).
 // Every wait is bounded: a timeout sets GS3_ERR_TIMEOUT in the workspace
 // header and the CTA frees its tensor memory and returns.
 #include <cuda_bf16.h>
@@ -35,9 +42,22 @@ namespace gs3 {
 namespace {
 
 constexpr int kTcRows = 128;
-constexpr int kTcThreads = 128;
+constexpr int kTcThreads = 128;   // one warpgroup: a thread per row of a tile
+constexpr int kTcMaxGroups = 4;   // tiles in flight per CTA
+
+// tensor-memory columns of a CTA: a width-W accumulator per group, rounded up
+// to a power of two >= 32 (the allocation unit)
+__host__ __device__ inline uint32_t tc_tmem_cols(int W, int groups) {
+  uint32_t c = 32;
+  while (c < (uint32_t)(W * groups)) c <<= 1;
+  return c;
+}
 constexpr int kK0 = 64;  // padded input width (61 / 60 features)
-constexpr uint32_t kWaitLimit = 1u << 22;
+// Bounded mbarrier waits: a waiting thread may sleep up to kSuspendNs per
+// poll (it wakes when the phase completes), and gives up after kWaitNs of
+// wall time on the global nanosecond timer.
+constexpr uint32_t kSuspendNs = 10000;
+constexpr uint64_t kWaitNs = 2000000000ull;
 
 // ---- PTX wrappers ----------------------------------------------------------
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -56,17 +76,25 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t phase) {
   uint32_t ok;
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
       "selp.u32 %0, 1, 0, p;\n\t}"
       : "=r"(ok)
-      : "r"(bar), "r"(phase)
+      : "r"(bar), "r"(phase), "r"(kSuspendNs)
       : "memory");
   return ok != 0;
 }
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
 __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t phase) {
-  for (uint32_t i = 0; i < kWaitLimit; ++i)
+  if (mbar_try_wait(bar, phase)) return true;
+  const uint64_t t0 = global_ns();
+  for (;;) {
     if (mbar_try_wait(bar, phase)) return true;
-  return false;
+    if (global_ns() - t0 > kWaitNs) return false;
+  }
 }
 __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
   asm volatile(
@@ -130,6 +158,27 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
 #pragma unroll
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
+
+// 32 consecutive FP32 columns of this thread's TMEM lane from registers
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const float* v) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], "
+      "{%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
+      "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};" ::"r"(taddr),
+      "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
+      "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
+      "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])), "r"(__float_as_uint(v[8])),
+      "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])),
+      "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])),
+      "r"(__float_as_uint(v[15])), "r"(__float_as_uint(v[16])), "r"(__float_as_uint(v[17])),
+      "r"(__float_as_uint(v[18])), "r"(__float_as_uint(v[19])), "r"(__float_as_uint(v[20])),
+      "r"(__float_as_uint(v[21])), "r"(__float_as_uint(v[22])), "r"(__float_as_uint(v[23])),
+      "r"(__float_as_uint(v[24])), "r"(__float_as_uint(v[25])), "r"(__float_as_uint(v[26])),
+      "r"(__float_as_uint(v[27])), "r"(__float_as_uint(v[28])), "r"(__float_as_uint(v[29])),
+      "r"(__float_as_uint(v[30])), "r"(__float_as_uint(v[31]))
+      : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
 // Shared-memory matrix descriptor: K-major, no swizzle.  Core matrices of
 // 8 rows x 16 bytes; lbo = byte step between core matrices along K, sbo =
@@ -217,20 +266,75 @@ __device__ __forceinline__ void store16(unsigned char* tile, int row, int k0, in
   *reinterpret_cast<uint4*>(tile + canon_off(row, k0 * EB, kdim * EB)) = u;
 }
 
-template <int EB>
-__global__ void __launch_bounds__(kTcThreads, 1) k_mlp_tc(TcParams p) {
-  constexpr int kChunk = 16 / EB;  // elements per 16-byte store
+// Named barrier of one warpgroup (ids 1.. ; 0 is __syncthreads)
+__device__ __forceinline__ void group_sync(int id) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(kTcThreads) : "memory");
+}
+
+// Encoded input row of Gaussian g (under light li for Phi), K padded to 64:
+// Phi [T, PE(w_i), PE(mu), l], Psi [PE(w_o), PE(mu), l]; stored as row `row`
+// of the K-major input tile.
+template <int EB, int WHICH>
+__device__ __forceinline__ void encode_row(const TcParams& p, int li, int g, unsigned char* tile, int row) {
+  constexpr int kChunk = 16 / EB;
+  float x[kK0];
+  const float4 m = p.mean_op[g];
+  float sx, sy, sz, sw;
+  if (WHICH == 0) {
+    const float4 lh = p.light[li];
+    sx = lh.x; sy = lh.y; sz = lh.z; sw = lh.w;
+  } else {
+    sx = p.cam_pos[0]; sy = p.cam_pos[1]; sz = p.cam_pos[2]; sw = 1.f;
+  }
+  float dx = sx - sw * m.x, dy = sy - sw * m.y, dz = sz - sw * m.z;
+  const float il = rsqrtf(dx * dx + dy * dy + dz * dz);
+  constexpr int b0 = WHICH == 0 ? 1 : 0;
+  if (WHICH == 0) x[0] = p.T[li][g];
+  pe_row(x, b0, dx * il, dy * il, dz * il);
+  pe_row(x, b0 + 27, m.x, m.y, m.z);
+  const float4 l0 = p.latent[g], l1 = p.latent[p.n + g];
+  x[b0 + 54] = l0.x; x[b0 + 55] = l0.y; x[b0 + 56] = l0.z; x[b0 + 57] = l0.w;
+  x[b0 + 58] = l1.x; x[b0 + 59] = l1.y;
+#pragma unroll
+  for (int k = b0 + 60; k < kK0; ++k) x[k] = 0.f;
+  const float inv0 = EB == 1 ? 1.f / p.scales[0] : 1.f;
+#pragma unroll
+  for (int k0 = 0; k0 < kK0; k0 += kChunk) store16<EB>(tile, row, k0, kK0, x + k0, inv0);
+}
+
+// BF16: a layer's bias becomes the accumulator's initial value: this
+// thread's row of the group's accumulator columns is set to b before the
+// layer's MMAs, which then all accumulate (the sum b + sum_k a_k w_k is
+// formed in FP32 by the tensor core; no per-element add in the epilogue).
+__device__ __forceinline__ void tmem_bias(uint32_t lane_addr, const float* b, int W) {
+  for (int c0 = 0; c0 < W; c0 += 32) {
+    float v[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = b[c0 + i];
+    tmem_st32(lane_addr + (uint32_t)c0, v);
+  }
+}
+
+// One CTA per SM, blockDim = 128 x groups: each warpgroup owns one 128-row
+// tile at a time, with its own activation tile in shared memory and its own
+// accumulator columns in tensor memory, so that one group's MMAs run while
+// the others encode or run their epilogues.  The weights are shared.
+template <int EB, int WHICH>
+__global__ void __launch_bounds__(kTcThreads * kTcMaxGroups, 1) k_mlp_tc(TcParams p) {
   extern __shared__ __align__(1024) unsigned char sm[];
-  __shared__ __align__(8) uint64_t bar_w, bar_mma;
+  __shared__ __align__(8) uint64_t bar_w, bar_mma[kTcMaxGroups];
   __shared__ uint32_t tmem_slot;
+  __shared__ int group_fail[kTcMaxGroups];
   const int t = threadIdx.x, warp = t >> 5;
+  const int groups = blockDim.x / kTcThreads, grp = t / kTcThreads, tg = t - grp * kTcThreads;
   const int W = p.width, nh = p.nh;
-  const uint32_t ncols = W < 32 ? 32u : (uint32_t)W;
-  // shared layout: [weights blob][X 128 x 64][H 128 x W][bias][wout][bout]
+  constexpr int kOut = WHICH == 0 ? 1 : 3;  // outputs of Phi (T') and Psi (residual rgb)
+  const uint32_t ncols = tc_tmem_cols(W, groups);
+  const int act_bytes = kTcRows * (W > kK0 ? W : kK0) * EB;
+  // shared layout: [weights blob][activation tile per group][bias][wout][bout]
   unsigned char* wsm = sm;
-  unsigned char* xsm = sm + ((p.wblob_bytes + 1023) & ~1023u);
-  unsigned char* hsm = xsm + kTcRows * kK0 * EB;
-  float* bsm = reinterpret_cast<float*>(hsm + kTcRows * W * EB);
+  unsigned char* act = sm + ((p.wblob_bytes + 1023) & ~1023u) + grp * act_bytes;
+  float* bsm = reinterpret_cast<float*>(sm + ((p.wblob_bytes + 1023) & ~1023u) + groups * act_bytes);
   float* wosm = bsm + nh * W;
   float* bosm = wosm + p.out_dim * W;
 
@@ -240,13 +344,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_tc(TcParams p) {
   }
   if (t == 0) {
     mbar_init(smem_u32(&bar_w), 1);
-    mbar_init(smem_u32(&bar_mma), 1);
+    for (int g = 0; g < groups; ++g) mbar_init(smem_u32(&bar_mma[g]), 1);
     fence_mbar_init();
   }
+  if (t < kTcMaxGroups) group_fail[t] = 0;
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  const uint32_t tmem = tmem_slot;
+  const uint32_t tmem = tmem_slot + (uint32_t)(grp * W);  // this group's accumulator columns
   if (t == 0) {
     mbar_expect_tx(smem_u32(&bar_w), p.wblob_bytes);
     for (uint32_t off = 0; off < p.wblob_bytes; off += 32768u) {
@@ -254,64 +359,52 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_tc(TcParams p) {
       bulk_g2s(smem_u32(wsm + off), p.wblob + off, nb, smem_u32(&bar_w));
     }
   }
-  for (int i = t; i < nh * W; i += kTcThreads) bsm[i] = p.bias[i];
-  for (int i = t; i < p.out_dim * W; i += kTcThreads) wosm[i] = p.wout[i];
+  for (int i = t; i < nh * W; i += blockDim.x) bsm[i] = p.bias[i];
+  for (int i = t; i < p.out_dim * W; i += blockDim.x) wosm[i] = p.wout[i];
   if (t < p.out_dim) bosm[t] = p.bout[t];
   const bool w_ok = mbar_wait_bounded(smem_u32(&bar_w), 0);
-  int fail = __syncthreads_or(!w_ok);
+  const int wfail = __syncthreads_or(!w_ok);
   const uint32_t idesc = idesc_mma(EB, kTcRows, W);
-  const uint32_t my_lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
+  const uint32_t my_lane_addr = tmem + ((uint32_t)((warp & 3) * 32) << 16);
   const bool leaky = p.act == GS3_ACT_LEAKY_RELU;
+  const uint32_t bar = smem_u32(&bar_mma[grp]);
   uint32_t phase = 0;
   const int rows = p.n * p.nl;
   const int ntiles = (rows + kTcRows - 1) / kTcRows;
-  for (int tile = blockIdx.x; tile < ntiles && !fail; tile += gridDim.x) {
-    const int row = tile * kTcRows + t;
+  bool fail = wfail != 0;
+  for (int tile = blockIdx.x * groups + grp; tile < ntiles && !fail; tile += gridDim.x * groups) {
+    const int row = tile * kTcRows + tg;
     const int rc = min(row, rows - 1);
     const int li = rc / p.n, g = rc - li * p.n;
-    // ---- encoded input row, BF16, K padded to 64 ----
-    {
-      float x[kK0];
-      const float4 m = p.mean_op[g];
-      const float4 lh = p.light[li];
-      const float sx = p.which == 0 ? lh.x : p.cam_pos[0], sy = p.which == 0 ? lh.y : p.cam_pos[1],
-                  sz = p.which == 0 ? lh.z : p.cam_pos[2];
-      const float sw = p.which == 0 ? lh.w : 1.f;
-      float dx = sx - sw * m.x, dy = sy - sw * m.y, dz = sz - sw * m.z;
-      const float il = rsqrtf(dx * dx + dy * dy + dz * dz);
-      const int b0 = p.which == 0 ? 1 : 0;
-      if (p.which == 0) x[0] = p.T[li][g];
-      pe_row(x, b0, dx * il, dy * il, dz * il);
-      pe_row(x, b0 + 27, m.x, m.y, m.z);
-      const float4 l0 = p.latent[g], l1 = p.latent[p.n + g];
-      x[b0 + 54] = l0.x; x[b0 + 55] = l0.y; x[b0 + 56] = l0.z; x[b0 + 57] = l0.w;
-      x[b0 + 58] = l1.x; x[b0 + 59] = l1.y;
-#pragma unroll
-      for (int k = b0 + 60; k < kK0; ++k) x[k] = 0.f;
-      const float inv0 = EB == 1 ? 1.f / p.scales[0] : 1.f;
-#pragma unroll
-      for (int k0 = 0; k0 < kK0; k0 += kChunk) store16<EB>(xsm, t, k0, kK0, x + k0, inv0);
+    encode_row<EB, WHICH>(p, li, g, act, tg);
+    if (EB == 2) {
+      tmem_bias(my_lane_addr, bsm, W);  // layer 0's bias; the previous tile's reads are done
+      tmem_wait_st();
     }
     fence_proxy_async();
-    __syncthreads();
+    tc_fence_before();
+    group_sync(1 + grp);
     uint32_t woff = 0;
-    float acc_out[4] = {0.f, 0.f, 0.f, 0.f};
+    float acc_out[kOut];
+#pragma unroll
+    for (int o = 0; o < kOut; ++o) acc_out[o] = 0.f;
     for (int l = 0; l < nh; ++l) {
       const int kdim = l == 0 ? kK0 : W;
-      if (t == 0) {
+      if (tg == 0) {
         tc_fence_after();
-        const uint32_t a0 = smem_u32(l == 0 ? xsm : hsm), b0 = smem_u32(wsm + woff);
+        const uint32_t a0 = smem_u32(act), b0 = smem_u32(wsm + woff);
         const uint32_t sbo = (uint32_t)(kdim * EB * 8);
         for (int s = 0; s < kdim * EB / 32; ++s) {  // 32 bytes of K per instruction
           const uint64_t da = smem_desc(a0 + s * 256, 128, sbo), db = smem_desc(b0 + s * 256, 128, sbo);
-          if (EB == 2) tc_mma(tmem, da, db, idesc, s > 0 ? 1u : 0u);
+          if (EB == 2) tc_mma(tmem, da, db, idesc, 1u);  // onto the bias
           else tc_mma_f8(tmem, da, db, idesc, s > 0 ? 1u : 0u);
         }
-        tc_commit(smem_u32(&bar_mma));
+        tc_commit(bar);
       }
       woff += (uint32_t)(W * kdim * EB);
-      const bool mma_ok = mbar_wait_bounded(smem_u32(&bar_mma), phase);
+      const bool mma_ok = mbar_wait_bounded(bar, phase);
       phase ^= 1u;
+      if (!mma_ok) group_fail[grp] = 1;
       tc_fence_after();
       const float* bl = bsm + l * W;
       const float deq = EB == 1 ? p.scales[2 * l] * p.scales[2 * l + 1] : 1.f;
@@ -321,14 +414,22 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_tc(TcParams p) {
         tmem_ld32(my_lane_addr + (uint32_t)c0, v);
 #pragma unroll
         for (int i = 0; i < 32; ++i) {
-          float h = EB == 1 ? fmaf(v[i], deq, bl[c0 + i]) : v[i] + bl[c0 + i];
-          v[i] = h > 0.f ? h : (leaky ? 0.01f * h : 0.f);
+          const float h = EB == 1 ? fmaf(v[i], deq, bl[c0 + i]) : v[i];  // BF16: the bias is in the sum
+          // leaky ReLU as max(h, 0.01 h) (slope below 1), ReLU as max(h, 0)
+          v[i] = fmaxf(h, leaky ? 0.01f * h : 0.f);
         }
         if (l + 1 < nh) {
 #pragma unroll
-          for (int i = 0; i < 32; i += kChunk) store16<EB>(hsm, t, c0 + i, W, v + i, inv_next);
+          for (int i = 0; i < 32; i += 16 / EB) store16<EB>(act, tg, c0 + i, W, v + i, inv_next);
+          if (EB == 2) {  // the next layer's bias into the columns just read
+            float bn[32];
+#pragma unroll
+            for (int i = 0; i < 32; ++i) bn[i] = bl[W + c0 + i];
+            tmem_st32(my_lane_addr + (uint32_t)c0, bn);
+          }
         } else {
-          for (int o = 0; o < p.out_dim; ++o) {
+#pragma unroll
+          for (int o = 0; o < kOut; ++o) {
             const float* wr = wosm + o * W + c0;
             float s = 0.f;
 #pragma unroll
@@ -337,15 +438,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_tc(TcParams p) {
           }
         }
       }
+      if (EB == 2 && l + 1 < nh) tmem_wait_st();
       tc_fence_before();
       fence_proxy_async();
-      fail = __syncthreads_or(!mma_ok);
+      group_sync(1 + grp);
+      fail = group_fail[grp] != 0;
       if (fail) break;
     }
     if (fail) break;
     if (row < rows) {
       const uint32_t r = p.rank_of[g];
-      if (p.which == 0) {
+      if (WHICH == 0) {
         const float y = 1.f / (1.f + __expf(-(acc_out[0] + bosm[0])));
         p.out[li][g] = y;
         if (p.envcol) {
@@ -366,12 +469,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_tc(TcParams p) {
     }
   }
   if (fail) {
-    if (t == 0) atomicCAS(p.status, 0u, (uint32_t)GS3_ERR_TIMEOUT);
+    if (tg == 0) atomicCAS(p.status, 0u, (uint32_t)GS3_ERR_TIMEOUT);
     if (!w_ok) mbar_wait_bounded(smem_u32(&bar_w), 0);  // let our own bulk copies land before leaving
   }
   tc_fence_before();
   __syncthreads();
-  if (warp == 0) tmem_dealloc(tmem, ncols);
+  if (warp == 0) tmem_dealloc(tmem_slot, ncols);
 }
 
 // FP32 (out, in) row-major weights -> canonical tile [out rows][kdim] (K
@@ -520,18 +623,29 @@ void pack_mlp_tc(const MlpDev& m, int dtype, const SceneDev& sc, int which, unsi
   }
 }
 
-static size_t tc_smem_bytes(const MlpDev& m, int eb) {
+// dynamic shared memory of a CTA with `groups` tiles in flight
+static size_t tc_smem_bytes(const MlpDev& m, int eb, int groups) {
   const size_t blob = (weight_bytes(m, eb) + 1023) & ~size_t(1023);
-  return blob + kTcRows * kK0 * eb + (size_t)kTcRows * m.width * eb +
-         4 * ((size_t)m.n_hidden * m.width + (size_t)m.out_dim * m.width + m.out_dim);
+  const size_t act = (size_t)kTcRows * (m.width > kK0 ? m.width : kK0) * eb;
+  return blob + groups * act + 4 * ((size_t)m.n_hidden * m.width + (size_t)m.out_dim * m.width + m.out_dim);
+}
+
+constexpr size_t kTcSmemCap = 220 * 1024;
+
+// Tiles in flight per CTA: as many as fit, up to kTcMaxGroups.
+static int tc_groups(const MlpDev& m, int eb) {
+  int g = kTcMaxGroups;
+  while (g > 1 && tc_smem_bytes(m, eb, g) > kTcSmemCap) --g;
+  return g;
 }
 
 bool mlp_tc_supported(const MlpDev& m, int dtype) {
   const int eb = elem_bytes(dtype);
-  // an FP8 instruction consumes K = 32: hidden widths of 16 cannot be fed
-  const bool width_ok = m.width == 32 || m.width == 64 || m.width == 128 || (m.width == 16 && eb == 2);
+  (void)eb;
+  // the epilogue moves accumulator columns 32 at a time
+  const bool width_ok = m.width == 32 || m.width == 64 || m.width == 128;
   return m.in_dim <= kK0 && m.out_dim <= 4 && m.n_hidden >= 1 && m.n_hidden <= 4 && width_ok &&
-         tc_smem_bytes(m, eb) <= 220 * 1024;
+         tc_smem_bytes(m, eb, 1) <= kTcSmemCap;
 }
 
 namespace {
@@ -571,13 +685,23 @@ TcParams tc_params(const FrameArgs& f, int which, const unsigned char* blob) {
 }
 
 void launch_tc(const TcParams& p, const MlpDev& m, int eb, cudaStream_t s) {
-  const size_t smem = tc_smem_bytes(m, eb);
-  auto kern = eb == 2 ? k_mlp_tc<2> : k_mlp_tc<1>;
+  const int groups = tc_groups(m, eb);
+  size_t smem = tc_smem_bytes(m, eb, groups);
+  // CTAs of this kernel (of any launch) that share an SM must fit in its 512
+  // tensor-memory columns, or an allocation would wait for another CTA to
+  // finish: pad the shared memory so that no more than that many fit
+  const int max_ctas = (int)(512 / tc_tmem_cols(m.width, groups));
+  const size_t per_sm = 228 * 1024, reserve = 2048;  // reserved and static shared memory per CTA
+  const size_t floor_bytes = per_sm / (size_t)(max_ctas + 1) + 1;
+  if (smem + reserve < floor_bytes) smem = floor_bytes - reserve;
+  auto kern = eb == 2 ? (p.which == 0 ? k_mlp_tc<2, 0> : k_mlp_tc<2, 1>)
+                      : (p.which == 0 ? k_mlp_tc<1, 0> : k_mlp_tc<1, 1>);
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   const int nsm = device_sm_count();
   const int ntiles = (p.n * p.nl + kTcRows - 1) / kTcRows;
-  const int grid = ntiles < nsm ? ntiles : nsm;
-  kern<<<grid, kTcThreads, smem, s>>>(p);
+  const int ctas = (ntiles + groups - 1) / groups;
+  const int grid = ctas < nsm ? ctas : nsm;
+  kern<<<grid, kTcThreads * groups, smem, s>>>(p);
   count_launch();
 }
 
