@@ -896,6 +896,7 @@ gs3_status run_backward(const FrameArgs& f, const float* dimg, void* bws, size_t
       a.color = color;
       a.dT = dT;
       a.mlp_in = mlp_in;
+      a.status = at<uint32_t>(ws, L.header) + H_STATUS;
       run_mlp_backward(a, B + bp.mlp_scratch, wred, s);
     }
     k_split_params<<<64, 256, 0, s>>>(wred, m.in_dim, m.width, m.n_hidden, m.out_dim, dw, db);

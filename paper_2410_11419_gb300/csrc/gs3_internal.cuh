@@ -198,6 +198,7 @@ struct MlpArgs {
   const float* color;  // [N][8]: dT' at 3, dres at 4..6
   float* dT;           // Phi: d/d(input T)
   float* mlp_in;       // [N][24]
+  uint32_t* status;    // device status word (GS3_ERR_TIMEOUT of a tensor-core GEMM's wait)
 };
 size_t mlp_bwd_scratch_bytes(int n, const MlpDev& m);
 void run_mlp_backward(const MlpArgs& a, void* scratch, float* wred, cudaStream_t s);

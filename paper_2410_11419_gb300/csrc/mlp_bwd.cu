@@ -1,4 +1,4 @@
-// K8b: backward of the Phi (Sec. 4.2) and Psi (Sec. 4.3) MLPs in FP32.
+// K8b: backward of the Phi (Sec. 4.2) and Psi (Sec. 4.3) MLPs of an FP32 scene.
 //
 // The network is x -> h_1 = act(W_1 x + b_1) -> ... -> h_L -> y = sigmoid(W_o h_L + b_o)
 // with x = encode(Gaussian) (the positional encoding of the direction and
@@ -10,19 +10,23 @@
 // and dx goes back through the encoding to the Gaussian's position,
 // direction and latent.
 //
-// Every product over the Gaussians is a dense FP32 GEMM with N rows and
-// 128 or fewer columns, run by one register-tiled SIMT kernel: a block
-// computes a 128 x 128 tile of C = A B, each thread 8 x 8 of it, with the
-// contraction staged through double-buffered shared memory in chunks of 16.
-// Its two uses:
-//   row GEMM (k_rowgemm):  rows = Gaussians; forward recompute h_l = act(h_{l-1} W_l^T + b_l)
-//                          and the data gradients dz_{l-1} = (dz_l W_l) * act'(h_{l-1})
-//   weight GEMM (k_wgemm): rows = output units, contraction over Gaussians split
-//                          across blocks; per-block partials are summed in block order,
-//                          so the gradients do not depend on scheduling.
+// Every product over the Gaussians is a dense GEMM with N rows and 128 or
+// fewer columns:
+//   row GEMM (k_rowgemm_tc):  rows = Gaussians; forward recompute h_l = act(h_{l-1} W_l^T + b_l)
+//                             and the data gradients dz_{l-1} = (dz_l W_l) * act'(h_{l-1})
+//   weight GEMM (k_wgemm_tc): rows = output units, contraction over Gaussians split
+//                             across blocks (the bias sums from a ones column); per-block
+//                             partials are summed in block order, so the gradients do not
+//                             depend on scheduling.
+// Both run on the tensor cores in three-pass TF32 (about 2^-21 relative per
+// product, FP32 accumulation).  The output layer's weight gradient (1 or 3
+// units) stays on a register-tiled FP32 SIMT kernel (k_wgemm): a block owns
+// a 128 x 128 tile of C = A B, each thread 8 x 8 of it, with the contraction
+// staged through double-buffered shared memory in chunks of 16.
 // The activations and data gradients of one network live in the backward
 // workspace (about (64 + 4 W) N floats), shared by Phi and Psi in turn.
 #include "gs3_internal.cuh"
+#include "tc_ptx.cuh"
 
 namespace gs3 {
 namespace {
@@ -136,40 +140,6 @@ struct RowGemm {
   int act;
 };
 
-template <int EPI>
-__global__ void __launch_bounds__(kGemmThreads, 2) k_rowgemm(RowGemm p) {
-  __shared__ __align__(16) GemmSmem S;
-  const int i0 = blockIdx.x * kTileR;
-  float acc[8][8];
-#pragma unroll
-  for (int r = 0; r < 8; ++r)
-#pragma unroll
-    for (int c = 0; c < 8; ++c) acc[r][c] = 0.f;
-  float unused = 0.f;
-  gemm_tile<false>(S, p.A, p.B, i0, 0, 0, p.kdim, acc, unused);
-  const int t = threadIdx.x, tx = t & 15, ty = t >> 4;
-  const bool leaky = p.act == GS3_ACT_LEAKY_RELU;
-#pragma unroll
-  for (int r = 0; r < 8; ++r) {
-    const int g = i0 + 8 * ty + r;
-    if (g >= p.n) break;
-#pragma unroll
-    for (int c = 0; c < 8; ++c) {
-      const int j = 8 * tx + c;
-      if (j >= p.ncols) break;
-      float v = acc[r][c];
-      if (EPI == EPI_BIAS_ACT) {
-        v += p.bias[j];
-        v = v > 0.f ? v : (leaky ? 0.01f * v : 0.f);
-      } else if (EPI == EPI_DACT) {
-        const float h = p.H[(size_t)g * p.ldh + j];
-        v = h > 0.f ? v : (leaky ? 0.01f * v : 0.f);
-      }
-      p.C[(size_t)g * p.ldc + j] = v;
-    }
-  }
-}
-
 // Block b: partial[b][j][k] = sum over its Gaussians g of dZ[g][j] H[g][k]
 // (j < nout, k < nin), and partial bias sums; written in the parameter order
 // (weights row-major, then biases).
@@ -204,6 +174,368 @@ __global__ void __launch_bounds__(kGemmThreads, 2) k_wgemm(WGemm p) {
     }
   }
   if (t < p.nout) out[(size_t)p.nout * p.nin + t] = bsum;
+}
+
+// ---- the same GEMMs on the tensor cores, three-pass TF32 --------------------
+// Every FP32 operand x is split into big = x with its low 13 mantissa bits
+// cleared (a TF32 value) and small = x - big (exact in FP32); a product is
+// formed as big*big' + big*small' + small*big' by tcgen05.mma kind::tf32
+// with FP32 accumulation in tensor memory, which drops only small*small'
+// and the bits of small below TF32: about 2^-21 |x y| per product, against
+// 2^-24 for an FP32 FMA.
+//
+// A CTA of 128 threads owns a 128 x npad output tile in TMEM (npad a
+// multiple of 32).  The contraction runs in chunks of kTcK elements: each
+// thread stages one row of the A chunk and one (or two) rows of the B chunk,
+// split, into K-major no-swizzle shared-memory tiles; thread 0 issues the
+// chunk's 4 K-steps x 3 passes and commits them to an mbarrier (a bounded,
+// sleeping wait); the next chunk is staged once they have completed.  Several
+// CTAs per SM overlap one CTA's staging with another's MMAs.
+constexpr int kTcK = 32;            // contraction elements per chunk
+constexpr int kTcRowBytes = kTcK * 4;  // bytes of a chunk row
+constexpr int kTcTile = 128;
+
+__host__ __device__ inline uint32_t tc_alloc_cols(int npad) {
+  uint32_t c = 32;
+  while (c < (uint32_t)npad) c <<= 1;
+  return c;
+}
+// dynamic shared memory of a CTA: A big/small (128 rows), B big/small (npad rows)
+__host__ __device__ inline size_t tc_gemm_smem(int npad) {
+  return 2ull * kTcTile * kTcRowBytes + 2ull * npad * kTcRowBytes;
+}
+
+__device__ __forceinline__ float tf32_big(float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
+
+// Split four values into big / small and store them as 16 bytes of row r,
+// bytes 16 c4 .. 16 c4 + 15, of the big and small chunk tiles.
+__device__ __forceinline__ void tc_put4(const float (&v)[4], int r, int c4, unsigned char* big, unsigned char* small) {
+  const float4 b4 = make_float4(tf32_big(v[0]), tf32_big(v[1]), tf32_big(v[2]), tf32_big(v[3]));
+  const float4 s4 = make_float4(v[0] - b4.x, v[1] - b4.y, v[2] - b4.z, v[3] - b4.w);
+  const uint32_t off = tc::canon_off(r, 16 * c4, kTcRowBytes);
+  *reinterpret_cast<float4*>(big + off) = b4;
+  *reinterpret_cast<float4*>(small + off) = s4;
+}
+
+// A thread's share of one operand chunk (elements kk = k0 .. k0 + 31 of
+// operand rows i0 + r, r < nrows <= 128; 0 outside the operand or past kend),
+// loaded into registers ahead of the chunk that uses it.  Both access
+// patterns keep a warp's global loads on few lines and its 16-byte shared
+// stores on distinct banks:
+//   kk_rows (operand row-major in i): lane = row r = t, consecutive lanes
+//     read consecutive i (one line per load), 32 loads per thread;
+//   otherwise (row-major in kk): a warp covers 8 rows x 4 float4 per step,
+//     lane l row l & 7 and float4 l >> 3 (16-byte loads where aligned); the
+//     stores of 8 lanes fill one 128-byte core-matrix row group.
+struct TcRegs {
+  float4 v[8];
+};
+
+__device__ __forceinline__ void tc_load(const Operand& o, int i0, int nrows, int k0, int kend, TcRegs& R) {
+  const int t = threadIdx.x;
+  const int klim = min(kend, o.nk);
+  if (o.kk_rows) {
+    const int i = i0 + t;
+    const bool row_ok = t < nrows && i < o.ni;
+#pragma unroll
+    for (int c4 = 0; c4 < kTcK / 4; ++c4) {
+      float v[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int kk = k0 + 4 * c4 + e;
+        v[e] = (row_ok && kk < klim) ? o.m[(size_t)kk * o.ld + i] : 0.f;
+      }
+      R.v[c4] = make_float4(v[0], v[1], v[2], v[3]);
+    }
+  } else {
+    const int lane = t & 31, warp = t >> 5;
+    const int steps = (nrows / 8) * 2;  // (8-row group, half of the chunk's 8 float4) pairs
+    const bool vec = (o.ld & 3) == 0 && (reinterpret_cast<uintptr_t>(o.m) & 15) == 0;
+#pragma unroll
+    for (int qq = 0; qq < 8; ++qq) {
+      const int q = warp + 4 * qq;
+      float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (q < steps) {
+        const int r = (q >> 1) * 8 + (lane & 7), c4 = (q & 1) * 4 + (lane >> 3);
+        const int i = i0 + r, kk = k0 + 4 * c4;
+        if (i < o.ni) {
+          const float* src = o.m + (size_t)i * o.ld + kk;
+          if (vec && kk + 4 <= klim) {
+            x = *reinterpret_cast<const float4*>(src);
+          } else {
+            x.x = kk < klim ? src[0] : 0.f;
+            x.y = kk + 1 < klim ? src[1] : 0.f;
+            x.z = kk + 2 < klim ? src[2] : 0.f;
+            x.w = kk + 3 < klim ? src[3] : 0.f;
+          }
+        }
+      }
+      R.v[qq] = x;
+    }
+  }
+}
+
+// Split a thread's loaded share into the big and small chunk tiles.  Rows
+// [128, nrows) (a weight GEMM's N past 128) hold no operand data: the ones
+// row (1 for kk < kend) or zeros.
+__device__ __forceinline__ void tc_store(const Operand& o, int nrows, int k0, int kend, int ones_row,
+                                         const TcRegs& R, unsigned char* big, unsigned char* small) {
+  const int t = threadIdx.x;
+  if (o.kk_rows) {
+    if (t < nrows) {
+#pragma unroll
+      for (int c4 = 0; c4 < kTcK / 4; ++c4) {
+        float v[4] = {R.v[c4].x, R.v[c4].y, R.v[c4].z, R.v[c4].w};
+        if (t == ones_row)
+#pragma unroll
+          for (int e = 0; e < 4; ++e) v[e] = k0 + 4 * c4 + e < kend ? 1.f : 0.f;
+        tc_put4(v, t, c4, big, small);
+      }
+    }
+    for (int r = t + kTcTile; r < nrows; r += kTcTile) {
+#pragma unroll
+      for (int c4 = 0; c4 < kTcK / 4; ++c4) {
+        float v[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) v[e] = (r == ones_row && k0 + 4 * c4 + e < kend) ? 1.f : 0.f;
+        tc_put4(v, r, c4, big, small);
+      }
+    }
+  } else {
+    const int lane = t & 31, warp = t >> 5;
+    const int steps = (nrows / 8) * 2;
+#pragma unroll
+    for (int qq = 0; qq < 8; ++qq) {
+      const int q = warp + 4 * qq;
+      if (q < steps) {
+        const int r = (q >> 1) * 8 + (lane & 7), c4 = (q & 1) * 4 + (lane >> 3);
+        const float v[4] = {R.v[qq].x, R.v[qq].y, R.v[qq].z, R.v[qq].w};
+        tc_put4(v, r, c4, big, small);
+      }
+    }
+  }
+}
+
+// 32 accumulator columns of this thread's row into the shared transpose
+// buffer (rows of 36 floats: 16-byte stores of 8 consecutive rows hit
+// distinct banks), for a write-out where a warp covers 4 rows x 8 float4.
+constexpr int kTcOutStride = 36;
+__device__ __forceinline__ void tc_rows_to_smem(const float (&v)[32], float* buf) {
+  float* row = buf + threadIdx.x * kTcOutStride;
+#pragma unroll
+  for (int c = 0; c < 8; ++c)
+    *reinterpret_cast<float4*>(row + 4 * c) = make_float4(v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]);
+}
+
+// One chunk's MMAs: 4 K-steps of 8 TF32 elements, three passes each
+__device__ __forceinline__ void tc_chunk_mma(uint32_t tmem, uint32_t ab, uint32_t as, uint32_t bb, uint32_t bs,
+                                             uint32_t idesc, bool first) {
+  constexpr uint32_t kSbo = 8 * kTcRowBytes;
+#pragma unroll
+  for (int st = 0; st < kTcK / 8; ++st) {
+    const uint32_t o = (uint32_t)st * 256;  // 32 bytes of K: two core matrices
+    const uint64_t dab = tc::smem_desc(ab + o, 128, kSbo), das = tc::smem_desc(as + o, 128, kSbo);
+    const uint64_t dbb = tc::smem_desc(bb + o, 128, kSbo), dbs = tc::smem_desc(bs + o, 128, kSbo);
+    tc::tc_mma_tf32(tmem, das, dbb, idesc, (first && st == 0) ? 0u : 1u);
+    tc::tc_mma_tf32(tmem, dab, dbs, idesc, 1u);
+    tc::tc_mma_tf32(tmem, dab, dbb, idesc, 1u);
+  }
+}
+
+// Shared prologue / epilogue pieces of the two tensor-core GEMM kernels
+struct TcCta {
+  unsigned char *ab, *as, *bb, *bs;
+  uint32_t tmem, ncols;
+};
+__device__ __forceinline__ TcCta tc_cta_begin(unsigned char* sm, int npad, uint64_t* bar, uint32_t* slot) {
+  TcCta c;
+  c.ab = sm;
+  c.as = sm + kTcTile * kTcRowBytes;
+  c.bb = sm + 2 * kTcTile * kTcRowBytes;
+  c.bs = c.bb + npad * kTcRowBytes;
+  c.ncols = tc_alloc_cols(npad);
+  if (threadIdx.x < 32) {
+    tc::tmem_alloc(tc::smem_u32(slot), c.ncols);
+    tc::tmem_relinquish();
+  }
+  if (threadIdx.x == 0) {
+    tc::mbar_init(tc::smem_u32(bar), 1);
+    tc::fence_mbar_init();
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  c.tmem = *slot;
+  return c;
+}
+__device__ __forceinline__ void tc_cta_end(const TcCta& c, bool ok, uint32_t* status) {
+  if (!ok && threadIdx.x == 0 && status) atomicCAS(status, 0u, (uint32_t)GS3_ERR_TIMEOUT);
+  tc::tc_fence_before();
+  __syncthreads();
+  if (threadIdx.x < 32) tc::tmem_dealloc(c.tmem, c.ncols);
+}
+// Issue a staged chunk (thread 0), run `meanwhile` (every thread), wait for
+// the chunk (every thread); false on a timeout
+template <typename F>
+__device__ __forceinline__ bool tc_run_chunk(const TcCta& c, uint32_t bar, uint32_t& phase, uint32_t idesc,
+                                             bool first, F&& meanwhile) {
+  tc::fence_proxy_async();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    tc::tc_fence_after();
+    tc_chunk_mma(c.tmem, tc::smem_u32(c.ab), tc::smem_u32(c.as), tc::smem_u32(c.bb), tc::smem_u32(c.bs), idesc,
+                 first);
+    tc::tc_commit(bar);
+  }
+  meanwhile();
+  const bool ok = tc::mbar_wait_bounded(bar, phase);
+  phase ^= 1u;
+  tc::tc_fence_after();
+  return __syncthreads_and(ok) != 0;  // also: every thread is done with the tiles
+}
+
+// C[g][j] = epi(sum_kk A[g][kk] B[kk][j]) for the 128 rows of this CTA and
+// j < ncols (npad = ncols rounded up to 32); the epilogues of k_rowgemm.
+template <int EPI>
+__global__ void __launch_bounds__(kTcTile) k_rowgemm_tc(RowGemm p, int npad, uint32_t* status) {
+  extern __shared__ __align__(1024) unsigned char sm[];
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ uint32_t slot;
+  const int t = threadIdx.x;
+  const int i0 = blockIdx.x * kTcTile;
+  const TcCta c = tc_cta_begin(sm, npad, &bar, &slot);
+  const uint32_t idesc = tc::idesc_tf32(kTcTile, npad);
+  uint32_t phase = 0;
+  bool ok = true;
+  TcRegs ra, rb;
+  tc_load(p.A, i0, kTcTile, 0, p.kdim, ra);
+  tc_load(p.B, 0, npad, 0, p.kdim, rb);
+  for (int k0 = 0; k0 < p.kdim && ok; k0 += kTcK) {
+    tc_store(p.A, kTcTile, k0, p.kdim, -1, ra, c.ab, c.as);
+    tc_store(p.B, npad, k0, p.kdim, -1, rb, c.bb, c.bs);
+    ok = tc_run_chunk(c, tc::smem_u32(&bar), phase, idesc, k0 == 0, [&] {
+      if (k0 + kTcK < p.kdim) {  // the next chunk's loads overlap this chunk's MMAs
+        tc_load(p.A, i0, kTcTile, k0 + kTcK, p.kdim, ra);
+        tc_load(p.B, 0, npad, k0 + kTcK, p.kdim, rb);
+      }
+    });
+  }
+  if (ok) {
+    // 32 columns at a time: TMEM row -> shared transpose buffer -> a warp
+    // applies the epilogue to 4 rows x 8 float4 and writes whole row segments
+    float* buf = reinterpret_cast<float*>(sm);  // the operand tiles are free now
+    const bool leaky = p.act == GS3_ACT_LEAKY_RELU;
+    const uint32_t lane_addr = c.tmem + ((uint32_t)((t >> 5) * 32) << 16);
+    const int lane = t & 31, warp = t >> 5;
+    for (int c0 = 0; c0 < npad; c0 += 32) {
+      float v[32];
+      tc::tmem_ld32(lane_addr + (uint32_t)c0, v);
+      tc_rows_to_smem(v, buf);
+      __syncthreads();
+      for (int q = warp; q < kTcTile / 4; q += kTcTile / 32) {
+        const int r = q * 4 + (lane >> 3), c4 = lane & 7;
+        const int g = i0 + r, j0 = c0 + 4 * c4;
+        if (g < p.n && j0 < p.ncols) {
+          const float4 a4 = *reinterpret_cast<const float4*>(buf + r * kTcOutStride + 4 * c4);
+          float x[4] = {a4.x, a4.y, a4.z, a4.w};
+          if (j0 + 4 <= p.ncols && (p.ldc & 3) == 0 && (EPI != EPI_DACT || (p.ldh & 3) == 0)) {
+            // whole float4: 8 lanes write one row's 128 contiguous bytes
+            float hv[4] = {1.f, 1.f, 1.f, 1.f};
+            if (EPI == EPI_DACT) {
+              const float4 h4 = *reinterpret_cast<const float4*>(p.H + (size_t)g * p.ldh + j0);
+              hv[0] = h4.x; hv[1] = h4.y; hv[2] = h4.z; hv[3] = h4.w;
+            }
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              if (EPI == EPI_BIAS_ACT) {
+                x[e] += p.bias[j0 + e];
+                x[e] = x[e] > 0.f ? x[e] : (leaky ? 0.01f * x[e] : 0.f);
+              } else if (EPI == EPI_DACT) {
+                x[e] = hv[e] > 0.f ? x[e] : (leaky ? 0.01f * x[e] : 0.f);
+              }
+            }
+            *reinterpret_cast<float4*>(p.C + (size_t)g * p.ldc + j0) = make_float4(x[0], x[1], x[2], x[3]);
+            continue;
+          }
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const int j = j0 + e;
+            if (j >= p.ncols) break;
+            if (EPI == EPI_BIAS_ACT) {
+              x[e] += p.bias[j];
+              x[e] = x[e] > 0.f ? x[e] : (leaky ? 0.01f * x[e] : 0.f);
+            } else if (EPI == EPI_DACT) {
+              const float h = p.H[(size_t)g * p.ldh + j];
+              x[e] = h > 0.f ? x[e] : (leaky ? 0.01f * x[e] : 0.f);
+            }
+            p.C[(size_t)g * p.ldc + j] = x[e];
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  tc_cta_end(c, ok, status);
+}
+
+// Block b: partial[b][j][k] = sum over its Gaussians g of dZ[g][j] H[g][k]
+// (j < nout <= 128, k < nin) and, from a ones column at k = nin, the bias
+// partial sum_g dZ[g][j]; the layout of k_wgemm's partials.
+__global__ void __launch_bounds__(kTcTile) k_wgemm_tc(WGemm p, int npad, uint32_t* status) {
+  extern __shared__ __align__(1024) unsigned char sm[];
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ uint32_t slot;
+  const int t = threadIdx.x;
+  const int kbeg = blockIdx.x * p.rows_per_block;
+  const int kend = min(p.n, kbeg + p.rows_per_block);
+  const TcCta c = tc_cta_begin(sm, npad, &bar, &slot);
+  const uint32_t idesc = tc::idesc_tf32(kTcTile, npad);
+  uint32_t phase = 0;
+  bool ok = true;
+  TcRegs ra, rb;
+  if (kbeg < kend) {
+    tc_load(p.A, 0, kTcTile, kbeg, kend, ra);
+    tc_load(p.B, 0, npad, kbeg, kend, rb);
+  }
+  for (int k0 = kbeg; k0 < kend && ok; k0 += kTcK) {
+    tc_store(p.A, kTcTile, k0, kend, -1, ra, c.ab, c.as);
+    tc_store(p.B, npad, k0, kend, p.nin, rb, c.bb, c.bs);
+    ok = tc_run_chunk(c, tc::smem_u32(&bar), phase, idesc, k0 == kbeg, [&] {
+      if (k0 + kTcK < kend) {  // the next chunk's loads overlap this chunk's MMAs
+        tc_load(p.A, 0, kTcTile, k0 + kTcK, kend, ra);
+        tc_load(p.B, 0, npad, k0 + kTcK, kend, rb);
+      }
+    });
+  }
+  const size_t np = (size_t)p.nout * p.nin + p.nout;
+  float* out = p.part + (size_t)blockIdx.x * np;
+  if (ok && kbeg >= kend) {  // no rows: zero partials
+    for (size_t i = t; i < np; i += kTcTile) out[i] = 0.f;
+  } else if (ok) {
+    float* buf = reinterpret_cast<float*>(sm);
+    const uint32_t lane_addr = c.tmem + ((uint32_t)((t >> 5) * 32) << 16);
+    const int lane = t & 31, warp = t >> 5;
+    for (int c0 = 0; c0 < npad; c0 += 32) {
+      float v[32];
+      tc::tmem_ld32(lane_addr + (uint32_t)c0, v);
+      tc_rows_to_smem(v, buf);
+      __syncthreads();
+      for (int q = warp; q < kTcTile / 4; q += kTcTile / 32) {
+        const int j = q * 4 + (lane >> 3), k0c = c0 + 4 * (lane & 7);
+        if (j < p.nout) {
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const int k = k0c + e;
+            const float x = buf[j * kTcOutStride + 4 * (lane & 7) + e];
+            if (k < p.nin) out[(size_t)j * p.nin + k] = x;
+            else if (k == p.nin) out[(size_t)p.nout * p.nin + j] = x;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  tc_cta_end(c, ok, status);
 }
 
 // ---- per-Gaussian steps ----------------------------------------------------
@@ -392,6 +724,49 @@ size_t mlp_bwd_scratch_bytes(int n, const MlpDev& m) {
          al(16ull * n) + al(4ull * wgemm_blocks(n) * layer_max);
 }
 
+namespace {
+
+int round32(int x) { return (x + 31) & ~31; }
+
+// Dynamic shared memory of a tensor-core GEMM launch: the operand tiles,
+// padded so that the CTAs that fit on an SM never need more than its 512
+// tensor-memory columns at once.
+size_t tc_launch_smem(int npad) {
+  size_t smem = tc_gemm_smem(npad);
+  const int max_ctas = (int)(512 / tc_alloc_cols(npad));
+  const size_t per_sm = 228 * 1024, reserve = 2048;
+  const size_t floor_bytes = per_sm / (size_t)(max_ctas + 1) + 1;
+  if (smem + reserve < floor_bytes) smem = floor_bytes - reserve;
+  return smem;
+}
+
+template <int EPI>
+void launch_rowgemm_tc(const RowGemm& g, int grid, uint32_t* status, cudaStream_t s) {
+  const int npad = round32(g.ncols);
+  const size_t smem = tc_launch_smem(npad);
+  static DeviceOnce once;
+  once.run([] {
+    return cudaFuncSetAttribute(k_rowgemm_tc<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) ==
+           cudaSuccess;
+  });
+  k_rowgemm_tc<EPI><<<grid, kTcTile, smem, s>>>(g, npad, status);
+  count_launch();
+}
+
+void launch_wgemm_tc(const WGemm& w, int grid, uint32_t* status, cudaStream_t s) {
+  const int npad = round32(w.nin + 1);
+  const size_t smem = tc_launch_smem(npad);
+  static DeviceOnce once;
+  once.run([] {
+    return cudaFuncSetAttribute(k_wgemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) ==
+           cudaSuccess;
+  });
+  k_wgemm_tc<<<grid, kTcTile, smem, s>>>(w, npad, status);
+  count_launch();
+}
+
+}  // namespace
+
 void run_mlp_backward(const MlpArgs& a, void* scratch, float* wred, cudaStream_t s) {
   const MlpDev& m = a.net;
   const int n = a.n, W = m.width, nh = m.n_hidden;
@@ -432,8 +807,7 @@ void run_mlp_backward(const MlpArgs& a, void* scratch, float* wred, cudaStream_t
     g.n = n; g.ncols = W; g.kdim = din;
     g.C = S.H + (size_t)l * n * W; g.ldc = W;
     g.bias = bl[l]; g.H = nullptr; g.ldh = 0; g.act = m.act;
-    k_rowgemm<EPI_BIAS_ACT><<<rows_grid, kGemmThreads, 0, s>>>(g);
-    count_launch();
+    launch_rowgemm_tc<EPI_BIAS_ACT>(g, rows_grid, a.status, s);
   }
   // output layer, then its weight gradient
   r.Hlast = S.H + (size_t)(nh - 1) * n * W;
@@ -450,10 +824,15 @@ void run_mlp_backward(const MlpArgs& a, void* scratch, float* wred, cudaStream_t
     w.B = {Hin, ldhin, nin, n, true};
     w.n = n; w.nout = nout; w.nin = nin; w.rows_per_block = rpb;
     w.part = S.part;
-    k_wgemm<<<nb, kGemmThreads, 0, s>>>(w);
+    if (nout >= 32) {
+      launch_wgemm_tc(w, nb, a.status, s);
+    } else {  // the output layer's 1 or 3 units: FP32 SIMT
+      k_wgemm<<<nb, kGemmThreads, 0, s>>>(w);
+      count_launch();
+    }
     const size_t np = (size_t)nout * nin + nout;
     k_sum_parts<<<(int)((np + 255) / 256), 256, 0, s>>>(S.part, np, nb, wred + poff[layer]);
-    count_launch(2);
+    count_launch();
   };
   wgrad(S.dzo, 4, m.out_dim, r.Hlast, W, W, nh);
   // hidden layers, last to first
@@ -472,12 +851,11 @@ void run_mlp_backward(const MlpArgs& a, void* scratch, float* wred, cudaStream_t
     g.bias = nullptr; g.act = m.act;
     if (l > 0) {
       g.H = Hin; g.ldh = W;
-      k_rowgemm<EPI_DACT><<<rows_grid, kGemmThreads, 0, s>>>(g);
+      launch_rowgemm_tc<EPI_DACT>(g, rows_grid, a.status, s);
     } else {
       g.H = nullptr; g.ldh = 0;  // columns din..63 of dx stay unwritten and unread
-      k_rowgemm<EPI_NONE><<<rows_grid, kGemmThreads, 0, s>>>(g);
+      launch_rowgemm_tc<EPI_NONE>(g, rows_grid, a.status, s);
     }
-    count_launch();
     cur ^= 1;
   }
   r.dX = S.dz[cur];
