@@ -131,6 +131,7 @@ __device__ __forceinline__ void gemm_tile(GemmSmem& S, const Operand& A, const O
 //   EPI_NONE:     .                           (dx)
 struct RowGemm {
   Operand A, B;
+  const unsigned char* bpack;  // tensor-core form: B pre-split into chunk tiles (tc_pack_b), or null
   int n, ncols, kdim;
   float* C;
   int ldc;
@@ -316,6 +317,24 @@ __device__ __forceinline__ void tc_store(const Operand& o, int nrows, int k0, in
   }
 }
 
+// A row GEMM's B operand (npad rows n x kdim elements k; element (n, k) =
+// W[n ld + k], or W[k ld + n] when transposed; 0 for n >= nvalid or
+// k >= kvalid) pre-split once into the chunk tiles the kernel reads: chunk c
+// at c * 2 npad 128 bytes, its big tile then its small tile, each in the
+// canonical K-major layout.  A CTA then copies a chunk with one bulk copy.
+__global__ void k_pack_b(const float* __restrict__ W, int ld, bool transposed, int nvalid, int kvalid, int npad,
+                         int nchunks, unsigned char* __restrict__ dst) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= npad * nchunks * kTcK) return;
+  const int n = idx % npad, k = idx / npad;
+  const float x = (n < nvalid && k < kvalid) ? (transposed ? W[(size_t)k * ld + n] : W[(size_t)n * ld + k]) : 0.f;
+  const float b = tf32_big(x);
+  unsigned char* chunk = dst + (size_t)(k / kTcK) * 2 * npad * kTcRowBytes;
+  const uint32_t off = tc::canon_off(n, 4 * (k % kTcK), kTcRowBytes);
+  *reinterpret_cast<float*>(chunk + off) = b;
+  *reinterpret_cast<float*>(chunk + (size_t)npad * kTcRowBytes + off) = x - b;
+}
+
 // 32 accumulator columns of this thread's row into the shared transpose
 // buffer (rows of 36 floats: 16-byte stores of 8 consecutive rows hit
 // distinct banks), for a write-out where a warp covers 4 rows x 8 float4.
@@ -399,26 +418,45 @@ __device__ __forceinline__ bool tc_run_chunk(const TcCta& c, uint32_t bar, uint3
 template <int EPI>
 __global__ void __launch_bounds__(kTcTile) k_rowgemm_tc(RowGemm p, int npad, uint32_t* status) {
   extern __shared__ __align__(1024) unsigned char sm[];
-  __shared__ __align__(8) uint64_t bar;
+  __shared__ __align__(8) uint64_t bar, bar_b;
   __shared__ uint32_t slot;
   const int t = threadIdx.x;
   const int i0 = blockIdx.x * kTcTile;
   const TcCta c = tc_cta_begin(sm, npad, &bar, &slot);
+  if (t == 0) {
+    tc::mbar_init(tc::smem_u32(&bar_b), 1);
+    tc::fence_mbar_init();
+  }
+  __syncthreads();
   const uint32_t idesc = tc::idesc_tf32(kTcTile, npad);
-  uint32_t phase = 0;
-  bool ok = true;
+  const uint32_t chunk_bytes = 2u * npad * kTcRowBytes;
+  uint32_t phase = 0, phase_b = 0;
+  bool ok = true, b_late = false;
   TcRegs ra, rb;
   tc_load(p.A, i0, kTcTile, 0, p.kdim, ra);
-  tc_load(p.B, 0, npad, 0, p.kdim, rb);
+  if (!p.bpack) tc_load(p.B, 0, npad, 0, p.kdim, rb);
   for (int k0 = 0; k0 < p.kdim && ok; k0 += kTcK) {
+    if (p.bpack && t == 0) {  // the chunk's B tiles (big, small) by one bulk copy
+      tc::mbar_expect_tx(tc::smem_u32(&bar_b), chunk_bytes);
+      tc::bulk_g2s(tc::smem_u32(c.bb), p.bpack + (size_t)(k0 / kTcK) * chunk_bytes, chunk_bytes,
+                   tc::smem_u32(&bar_b));
+    }
     tc_store(p.A, kTcTile, k0, p.kdim, -1, ra, c.ab, c.as);
-    tc_store(p.B, npad, k0, p.kdim, -1, rb, c.bb, c.bs);
+    if (!p.bpack) tc_store(p.B, npad, k0, p.kdim, -1, rb, c.bb, c.bs);
+    if (p.bpack) {  // every thread: the B tiles have landed (a bounded wait)
+      const bool b_ok = tc::mbar_wait_bounded(tc::smem_u32(&bar_b), phase_b);
+      if (!b_ok) {
+        ok = false;
+        b_late = true;
+      }
+      phase_b ^= 1u;
+    }
     ok = tc_run_chunk(c, tc::smem_u32(&bar), phase, idesc, k0 == 0, [&] {
       if (k0 + kTcK < p.kdim) {  // the next chunk's loads overlap this chunk's MMAs
         tc_load(p.A, i0, kTcTile, k0 + kTcK, p.kdim, ra);
-        tc_load(p.B, 0, npad, k0 + kTcK, p.kdim, rb);
+        if (!p.bpack) tc_load(p.B, 0, npad, k0 + kTcK, p.kdim, rb);
       }
-    });
+    }) && ok;
   }
   if (ok) {
     // 32 columns at a time: TMEM row -> shared transpose buffer -> a warp
@@ -475,6 +513,7 @@ __global__ void __launch_bounds__(kTcTile) k_rowgemm_tc(RowGemm p, int npad, uin
       __syncthreads();
     }
   }
+  if (b_late) tc::mbar_wait_bounded(tc::smem_u32(&bar_b), phase_b ^ 1u);  // our own copy lands before we leave
   tc_cta_end(c, ok, status);
 }
 
@@ -551,7 +590,6 @@ struct RowArgs {
   const float* color;  // [N][8]: dT' at 3, dres at 4..6
   float* X;            // [N][kXdim]
   const float* Hlast;  // [N][width]
-  float* dzo;          // [N][4]
   float* dZlast;       // [N][width]
   const float* dX;     // [N][kXdim]
   float* dT;
@@ -617,44 +655,86 @@ __global__ void k_encode(RowArgs p) {
   for (int k = 0; k < kXdim / 4; ++k) dst[k] = make_float4(x[4 * k], x[4 * k + 1], x[4 * k + 2], x[4 * k + 3]);
 }
 
-// Output layer, one warp per Gaussian (kOutRowsPerWarp Gaussians per warp in
-// turn, the weights staged once per block): y = sigmoid(W_o h_L + b_o),
-// dz_o = dL/dy y (1 - y), dz_L = (dz_o W_o) * act'(h_L).  Lane l owns the
-// columns l, l + 32, l + 64, l + 96 that exist (widths 16..128).
-constexpr int kOutRowsPerWarp = 8;
-__global__ void __launch_bounds__(256) k_out_layer(RowArgs p) {
+// Output layer and its weight gradient, one warp per Gaussian at a time:
+// y = sigmoid(W_o h_L + b_o), dz_o = dL/dy y (1 - y), dz_L = (dz_o W_o) *
+// act'(h_L); lane l owns the columns l, l + 32, l + 64, l + 96 that exist
+// (widths 16..128).  Block b takes the Gaussians [b rpb, (b + 1) rpb), warp w
+// of it every 8th from the w-th (the next one's h_L loaded ahead); each lane
+// accumulates dz_o h_L for its columns, and the block adds its warps' sums in
+// warp order into partial[b] (the weight gradient's order: W_o row-major,
+// then b_o), so the result does not depend on scheduling.
+constexpr int kOutWarps = 8;
+__global__ void __launch_bounds__(kOutWarps * 32) k_out_layer(RowArgs p, int rows_per_block, float* part) {
   __shared__ float wo[4 * 128];  // the output layer's weights (out_dim <= 3, width <= 128)
   __shared__ float bo[4];
-  const int W = p.width, nq = (W + 31) / 32, lane = threadIdx.x & 31;
-  for (int i = threadIdx.x; i < p.out_dim * W; i += blockDim.x) wo[i] = p.w_out[i];
-  if (threadIdx.x < p.out_dim) bo[threadIdx.x] = p.b_out[threadIdx.x];
+  __shared__ float red[kOutWarps][3 * 128 + 3];
+  const int W = p.width, nq = (W + 31) / 32, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nout = p.out_dim;
+  for (int i = threadIdx.x; i < nout * W; i += blockDim.x) wo[i] = p.w_out[i];
+  if (threadIdx.x < nout) bo[threadIdx.x] = p.b_out[threadIdx.x];
   __syncthreads();
   const bool leaky = p.act == GS3_ACT_LEAKY_RELU;
-  const int warp0 = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * kOutRowsPerWarp;
-  for (int g = warp0; g < min(p.n, warp0 + kOutRowsPerWarp); ++g) {
-    const float* h = p.Hlast + (size_t)g * W;
-    float hv[4] = {0.f, 0.f, 0.f, 0.f};
-    for (int q = 0; q < nq; ++q)
-      if (lane + 32 * q < W) hv[q] = h[lane + 32 * q];
-    float dzo[4] = {0.f, 0.f, 0.f, 0.f};
-    for (int o = 0; o < p.out_dim; ++o) {
+  const int kbeg = blockIdx.x * rows_per_block, kend = min(p.n, kbeg + rows_per_block);
+  float wacc[3][4], bacc[3];
+#pragma unroll
+  for (int o = 0; o < 3; ++o) {
+    bacc[o] = 0.f;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) wacc[o][q] = 0.f;
+  }
+  auto load_h = [&](int g, float (&hv)[4]) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) hv[q] = (g < kend && q < nq && lane + 32 * q < W) ? p.Hlast[(size_t)g * W + lane + 32 * q] : 0.f;
+  };
+  float hn[4];
+  load_h(kbeg + warp, hn);
+  for (int g = kbeg + warp; g < kend; g += kOutWarps) {
+    float hv[4] = {hn[0], hn[1], hn[2], hn[3]};
+    load_h(g + kOutWarps, hn);
+    float dzo[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int o = 0; o < 3; ++o) {
+      if (o >= nout) break;
       float s = 0.f;
-      for (int q = 0; q < nq; ++q)
-        if (lane + 32 * q < W) s = fmaf(hv[q], wo[o * W + lane + 32 * q], s);
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (q < nq && lane + 32 * q < W) s = fmaf(hv[q], wo[o * W + lane + 32 * q], s);
 #pragma unroll
       for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
       const float y = 1.f / (1.f + expf(-(s + bo[o])));
       const float dy = p.which == 0 ? p.color[(size_t)kColorStride * g + 3] : p.color[(size_t)kColorStride * g + 4 + o];
       dzo[o] = dy * y * (1.f - y);
+      bacc[o] += dzo[o];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) wacc[o][q] = fmaf(dzo[o], hv[q], wacc[o][q]);
     }
-    if (lane < 4) p.dzo[(size_t)4 * g + lane] = lane < p.out_dim ? dzo[lane] : 0.f;
-    for (int q = 0; q < nq; ++q) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
       const int j = lane + 32 * q;
-      if (j >= W) break;
+      if (q >= nq || j >= W) break;
       float s = 0.f;
-      for (int o = 0; o < p.out_dim; ++o) s = fmaf(dzo[o], wo[o * W + j], s);
+#pragma unroll
+      for (int o = 0; o < 3; ++o)
+        if (o < nout) s = fmaf(dzo[o], wo[o * W + j], s);
       p.dZlast[(size_t)g * W + j] = hv[q] > 0.f ? s : (leaky ? 0.01f * s : 0.f);
     }
+  }
+  // the block's partial weight gradient, its warps added in order
+#pragma unroll
+  for (int o = 0; o < 3; ++o) {
+    if (o >= nout) break;
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      if (q < nq && lane + 32 * q < W) red[warp][o * W + lane + 32 * q] = wacc[o][q];
+    if (lane == 0) red[warp][nout * W + o] = bacc[o];
+  }
+  __syncthreads();
+  const int np = nout * W + nout;
+  float* out = part + (size_t)blockIdx.x * np;
+  for (int i = threadIdx.x; i < np; i += blockDim.x) {
+    float v = 0.f;
+    for (int w = 0; w < kOutWarps; ++w) v += red[w][i];
+    out[i] = v;
   }
 }
 
@@ -684,12 +764,25 @@ __global__ void k_input_grad(RowArgs p) {
   if (p.which == 0) p.dT[g] = dx[0];
 }
 
-__global__ void k_sum_parts(const float* part, size_t np, int nblocks, float* red) {
-  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= np) return;
+// red[i] = sum over b of part[b][i], for 32 consecutive i per block: warp w
+// adds the partials b = w, w + 8, ... (lane = i, coalesced), then the eight
+// warp sums are added in warp order: a fixed order, so the result does not
+// depend on scheduling.
+constexpr int kSumWarps = 8;
+__global__ void __launch_bounds__(kSumWarps * 32) k_sum_parts(const float* part, size_t np, int nblocks, float* red) {
+  __shared__ float acc[kSumWarps][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const size_t i = (size_t)blockIdx.x * 32 + lane;
   float s = 0.f;
-  for (int b = 0; b < nblocks; ++b) s += part[(size_t)b * np + i];
-  red[i] = s;
+  if (i < np)
+    for (int b = warp; b < nblocks; b += kSumWarps) s += part[(size_t)b * np + i];
+  acc[warp][lane] = s;
+  __syncthreads();
+  if (warp == 0 && i < np) {
+    float t = 0.f;
+    for (int w = 0; w < kSumWarps; ++w) t += acc[w][lane];
+    red[i] = t;
+  }
 }
 
 int wgemm_blocks(int n) {
@@ -698,8 +791,10 @@ int wgemm_blocks(int n) {
 }
 
 struct Scratch {
-  float *X, *H, *dz[2], *dzo, *part;
+  float *X, *H, *dz[2], *part;
+  unsigned char* bpack;  // pre-split B operands: per hidden layer the forward one, then the data gradient's
 };
+constexpr size_t kPackBytes = 4ull * 2 * kTcTile * kTcRowBytes;  // a B operand of <= 128 x 128: 4 chunks
 
 Scratch carve(void* base, int n, const MlpDev& m) {
   auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
@@ -709,7 +804,7 @@ Scratch carve(void* base, int n, const MlpDev& m) {
   s.H = reinterpret_cast<float*>(c); c += al(4ull * n * m.width * m.n_hidden);
   s.dz[0] = reinterpret_cast<float*>(c); c += al(4ull * n * (m.width > kXdim ? m.width : kXdim));
   s.dz[1] = reinterpret_cast<float*>(c); c += al(4ull * n * (m.width > kXdim ? m.width : kXdim));
-  s.dzo = reinterpret_cast<float*>(c); c += al(4ull * n * 4);
+  s.bpack = c; c += 2 * kPackBytes * m.n_hidden;
   s.part = reinterpret_cast<float*>(c);
   return s;
 }
@@ -721,7 +816,7 @@ size_t mlp_bwd_scratch_bytes(int n, const MlpDev& m) {
   const size_t wide = (size_t)(m.width > kXdim ? m.width : kXdim);
   const size_t layer_max = (size_t)m.width * (m.width > m.in_dim ? m.width : m.in_dim) + m.width;
   return al(4ull * n * kXdim) + al(4ull * n * m.width * m.n_hidden) + 2 * al(4ull * n * wide) +
-         al(16ull * n) + al(4ull * wgemm_blocks(n) * layer_max);
+         2 * kPackBytes * m.n_hidden + al(4ull * wgemm_blocks(n) * layer_max);
 }
 
 namespace {
@@ -796,6 +891,19 @@ void run_mlp_backward(const MlpArgs& a, void* scratch, float* wred, cudaStream_t
   r.w_out = wl[nh]; r.b_out = bl[nh];
   r.color = a.color; r.X = S.X; r.dT = a.dT; r.mlp_in = a.mlp_in;
   const int rows_grid = (n + kTileR - 1) / kTileR;
+  // the row GEMMs' B operands, pre-split: forward W_l (n = out unit, k = in),
+  // data gradient W_l^T (n = in unit, k = out)
+  auto pack = [&](const float* w, int ld, bool tr, int nvalid, int kvalid, unsigned char* dst) {
+    const int npad = round32(nvalid), nchunks = (kvalid + kTcK - 1) / kTcK;
+    const int total = npad * nchunks * kTcK;
+    k_pack_b<<<(total + 255) / 256, 256, 0, s>>>(w, ld, tr, nvalid, kvalid, npad, nchunks, dst);
+    count_launch();
+  };
+  for (int l = 0; l < nh; ++l) {
+    const int din = l == 0 ? m.in_dim : W;
+    pack(wl[l], din, false, W, din, S.bpack + (size_t)(2 * l) * kPackBytes);
+    pack(wl[l], din, true, din, W, S.bpack + (size_t)(2 * l + 1) * kPackBytes);
+  }
   // forward recompute
   k_encode<<<(n + 127) / 128, 128, 0, s>>>(r);
   count_launch();
@@ -804,6 +912,7 @@ void run_mlp_backward(const MlpArgs& a, void* scratch, float* wred, cudaStream_t
     RowGemm g;
     g.A = {l == 0 ? S.X : S.H + (size_t)(l - 1) * n * W, l == 0 ? kXdim : W, n, din, false};
     g.B = {wl[l], din, W, din, false};  // B[kk][j] = W_l[j][kk]
+    g.bpack = S.bpack + (size_t)(2 * l) * kPackBytes;
     g.n = n; g.ncols = W; g.kdim = din;
     g.C = S.H + (size_t)l * n * W; g.ldc = W;
     g.bias = bl[l]; g.H = nullptr; g.ldh = 0; g.act = m.act;
@@ -811,13 +920,16 @@ void run_mlp_backward(const MlpArgs& a, void* scratch, float* wred, cudaStream_t
   }
   // output layer, then its weight gradient
   r.Hlast = S.H + (size_t)(nh - 1) * n * W;
-  r.dzo = S.dzo;
   r.dZlast = S.dz[0];
-  const int out_warps = (n + kOutRowsPerWarp - 1) / kOutRowsPerWarp;
-  k_out_layer<<<(out_warps * 32 + 255) / 256, 256, 0, s>>>(r);
-  count_launch();
   const int nb = wgemm_blocks(n);
   const int rpb = ((n + nb - 1) / nb + kKc - 1) / kKc * kKc;
+  // output layer with its weight gradient's block partials, then their sum
+  k_out_layer<<<nb, kOutWarps * 32, 0, s>>>(r, rpb, S.part);
+  {
+    const size_t np = (size_t)m.out_dim * W + m.out_dim;
+    k_sum_parts<<<(int)((np + 31) / 32), kSumWarps * 32, 0, s>>>(S.part, np, nb, wred + poff[nh]);
+  }
+  count_launch(2);
   auto wgrad = [&](const float* dZ, int ldz, int nout, const float* Hin, int ldhin, int nin, int layer) {
     WGemm w;
     w.A = {dZ, ldz, nout, n, true};
@@ -826,15 +938,14 @@ void run_mlp_backward(const MlpArgs& a, void* scratch, float* wred, cudaStream_t
     w.part = S.part;
     if (nout >= 32) {
       launch_wgemm_tc(w, nb, a.status, s);
-    } else {  // the output layer's 1 or 3 units: FP32 SIMT
+    } else {  // hidden widths of 16: FP32 SIMT
       k_wgemm<<<nb, kGemmThreads, 0, s>>>(w);
       count_launch();
     }
     const size_t np = (size_t)nout * nin + nout;
-    k_sum_parts<<<(int)((np + 255) / 256), 256, 0, s>>>(S.part, np, nb, wred + poff[layer]);
+    k_sum_parts<<<(int)((np + 31) / 32), kSumWarps * 32, 0, s>>>(S.part, np, nb, wred + poff[layer]);
     count_launch();
   };
-  wgrad(S.dzo, 4, m.out_dim, r.Hlast, W, W, nh);
   // hidden layers, last to first
   int cur = 0;
   for (int l = nh - 1; l >= 0; --l) {
@@ -846,6 +957,7 @@ void run_mlp_backward(const MlpArgs& a, void* scratch, float* wred, cudaStream_t
     RowGemm g;
     g.A = {S.dz[cur], W, n, W, false};
     g.B = {wl[l], din, din, W, true};  // B[kk][j] = W_l[kk][j]
+    g.bpack = S.bpack + (size_t)(2 * l + 1) * kPackBytes;
     g.n = n; g.ncols = din; g.kdim = W;
     g.C = S.dz[cur ^ 1]; g.ldc = l == 0 ? kXdim : W;
     g.bias = nullptr; g.act = m.act;
