@@ -707,31 +707,42 @@ def main():
         plain = {"mlp": "fp32" if other == N.GS3_MLP_FP32 else "bf16", "value": K / (pms.sum() / 1e3),
                  "unit": UNIT, "ms_per_step": float(pms.mean()), "p50_ms": float(np.percentile(pms, 50)),
                  "p99_ms": float(np.percentile(pms, 99))}
-        # differentiation form: forward + hand-written backward of the same frames (FP32)
-        if other == N.GS3_MLP_FP32:
-            tgt = torch.rand((a.res, a.res, 3), device=dev, generator=torch.Generator(dev).manual_seed(7))
-            dimg = torch.empty_like(tgt)
+        # differentiation form: forward + hand-written backward of the same frames
+        tgt = torch.rand((a.res, a.res, 3), device=dev, generator=torch.Generator(dev).manual_seed(7))
+        dimg = torch.empty_like(tgt)
+
+        def fwd_bwd(r_):
             for s_ in range(2):  # warm-up: the backward workspace is allocated on first use
-                img = rd2.render(*pairs[s_ % 100], opts)
+                img = r_.render(*pairs[s_ % 100], opts)
                 torch.sign(img - tgt, out=dimg)
-                rd2.backward(*pairs[s_ % 100], dimg, opts)
+                r_.backward(*pairs[s_ % 100], dimg, opts)
             torch.cuda.synchronize()
             be = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
             for s_ in range(K):
                 cam, light = pairs[(a.warmup + s_) % 100]
                 be[s_][0].record(stream)
-                img = rd2.render(cam, light, opts)
+                img = r_.render(cam, light, opts)
                 torch.sign(img - tgt, out=dimg)
                 be[s_][1].record(stream)
-                rd2.backward(cam, light, dimg, opts)
+                r_.backward(cam, light, dimg, opts)
                 be[s_][2].record(stream)
             torch.cuda.synchronize()
-            fb = np.array([x[0].elapsed_time(x[2]) for x in be])
-            bw = np.array([x[1].elapsed_time(x[2]) for x in be])
+            r_.check()
+            return (np.array([x[0].elapsed_time(x[2]) for x in be]),
+                    np.array([x[1].elapsed_time(x[2]) for x in be]))
+
+        if other == N.GS3_MLP_FP32:
+            fb, bw = fwd_bwd(rd2)
             plain["differentiation"] = {
                 "fwd_bwd_ms": float(fb.mean()), "bwd_ms": float(bw.mean()),
                 "fwd_bwd_per_s": K / (fb.sum() / 1e3),
                 "note": "gs3_render + gs3_render_backward per frame, FP32 MLPs, dL/dI = sign(I - target)"}
+            if mlp_dtype == N.GS3_MLP_BF16:
+                fb16, bw16 = fwd_bwd(rd)
+                plain["differentiation"]["bf16_forward"] = {
+                    "fwd_bwd_ms": float(fb16.mean()), "bwd_ms": float(bw16.mean()),
+                    "note": "BF16 MLP forward; the backward's MLP gradients are the FP32 networks' at the "
+                            "same inputs (three-pass TF32 tensor-core GEMMs)"}
             # one training iteration (Sec. 4.4): render, L1 + D-SSIM loss, backward, Adam on every group
             from paper_2410_11419_gb300.train import Trainer
             del rd2

@@ -293,8 +293,12 @@ size_t gs3_backward_workspace_size(const gs3_scene *scene);
  *   workspace: the workspace of a gs3_render of the same scene, camera,
  *              light and options, unchanged since (it holds the forward state)
  *   bwd_ws:    device, >= gs3_backward_workspace_size bytes, caller-owned
- * The scene must use GS3_MLP_FP32 (GS3_ERR_UNSUPPORTED otherwise).
- * Asynchronous on `stream`.  Errors: INVALID_ARG, UNSUPPORTED, CUDA. */
+ * The MLP gradients are those of the scene's FP32 networks evaluated at the
+ * forward's inputs (their GEMMs on the tensor cores in three-pass TF32,
+ * about FP32 accuracy); for a BF16 or FP8 scene the rest of the backward
+ * uses the forward's reduced-precision T' and residual, so the rounding of
+ * the MLP operands passes straight through.
+ * Asynchronous on `stream`.  Errors: INVALID_ARG, CUDA. */
 gs3_status gs3_render_backward(gs3_scene *scene, const gs3_camera *camera, const gs3_light *light,
                                const gs3_render_opts *opts, const float *dL_drgb, void *workspace,
                                size_t workspace_bytes, size_t key_capacity, void *bwd_ws,

@@ -572,8 +572,6 @@ gs3_status gs3_render_backward(gs3_scene* scene, const gs3_camera* cam, const gs
                                const gs3_grads* grads, void* stream) {
   if (!scene || !cam || !light || !opts || !dimg || !workspace || !bws || !grads)
     return fail(GS3_ERR_INVALID_ARG, "gs3_render_backward: null argument");
-  if (scene->dev.mlp_dtype != GS3_MLP_FP32)
-    return fail(GS3_ERR_UNSUPPORTED, "gs3_render_backward: needs a GS3_MLP_FP32 scene");
   if (cam->width < 1 || cam->height < 1 || opts->tile != kTile)
     return fail(GS3_ERR_INVALID_ARG, "gs3_render_backward: bad camera or options");
   if (light_problem(*light, *opts)) return fail(GS3_ERR_INVALID_ARG, "gs3_render_backward: invalid light");
