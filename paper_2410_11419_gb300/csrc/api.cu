@@ -151,6 +151,7 @@ Workspace plan_workspace(int n, int width, int height, size_t cap) {
   L.seg_lvl = P.take(4 * (1025 + 3));
   L.seg_flag = P.take(4 * items);
   L.seg_pub = P.take(4 * 256 * items);
+  L.rank_flags = P.take(2 * N);
   L.shade = P.take(16 * N);
   L.T = P.take(4 * N);
   L.Tp = P.take(4 * N);

@@ -105,6 +105,8 @@ struct ShadowParams {
   float* light_final;     // per light pixel: the product where the ray ended
   uint32_t* light_stop;   // per light pixel: 1 + index of the occluder that stopped it, or kNoStop
   uint32_t* status;
+  uint8_t* live_rank;  // per light rank: 1 if an entry of it lies in a segment with an open ray (K6b)
+  uint8_t* den_found;  // per light rank: 1 once K6c found a passing pixel of a Gaussian with no such entry
   int W, H, gx;
   float amax;
 };
@@ -304,6 +306,7 @@ __device__ __forceinline__ void stage_receivers(const ShadowParams& p, ShadowSme
     S.r1[t] = e1;
     S.rk[t] = p.kbound[rb + t];
     S.rslot[t] = p.off[rank] + (uint32_t)((st.ty - qr.r.y) * (qr.r.z - qr.r.x + 1) + (st.tx - qr.r.x));
+    p.live_rank[rank] = 1;
   }
   __syncwarp();
 }
@@ -554,6 +557,14 @@ __global__ void __launch_bounds__(kSegWarps * 32, 4) k_shadow_chain(const Shadow
   }
 }
 
+// The light tile of the pixel nearest a splat's centre (k_dead_probe's
+// pixel), or all ones off the image.
+__device__ __forceinline__ uint32_t probe_tile(const SplatRec& q, int W, int H, int gx) {
+  const float cx = q.a.x + q.b.w, cy = q.a.y + q.c.x;
+  if (!(cx >= 0.f && cy >= 0.f && cx < (float)W && cy < (float)H)) return 0xFFFFFFFFu;
+  return (uint32_t)(((int)cy / kTile) * gx + (int)cx / kTile);
+}
+
 // K6c: the receivers of the segments every ray of which stopped before the
 // segment (A(C_s) = 0 throughout, as K6a published).  The products are 0,
 // so a receiver needs only its beta sum over the tile, which depends on no
@@ -562,6 +573,16 @@ __global__ void __launch_bounds__(kSegWarps * 32, 4) k_shadow_chain(const Shadow
 // lane walks the 16 x 8 pixels of one unit at a time, with the power
 // arithmetic of the ray layout (pixel centres x + 0.5, y + 0.5); the two
 // halves of a receiver are then added in a fixed order.
+// A Gaussian none of whose entries lies in a segment with an open ray (K6b
+// marked those) has a zero numerator everywhere, so its shadow value is 0 if
+// any of its pixels passes and 1 otherwise: the beta sum only has to be
+// known to be positive.  Once that is known (den_found: k_dead_probe found
+// its pixel nearest the centre passing, or one of its units here found a
+// passing pixel), its entries are skipped (partial (0, 0), no pass halves)
+// except the one of the probe tile, which is evaluated in full, so the sum
+// stays positive.  Which other entries are skipped depends on timing; T
+// does not, and the backward takes nothing from such a Gaussian (its
+// products and T are 0).
 constexpr int kDeadBatch = 128;
 constexpr int kDeadWarps = 4;
 
@@ -635,9 +656,15 @@ __device__ __forceinline__ void dead_item(const ShadowParams& p, uint32_t w, Dea
         const int t = 32 * c + lane;
         box[c] = 0u;
         if (t < rc) {
+          const uint32_t rank = p.list[rb + t];
+          const SplatRec q = p.rrec[rank];
           float4 e0, e1;
-          make_entry(p.rrec[p.list[rb + t]], ox, oy, e0, e1);
-          box[c] = __float_as_uint(e1.w) & ellipse_halves(e0, e1);
+          make_entry(q, ox, oy, e0, e1);
+          // skipped: a Gaussian with no open-ray entry whose den is known positive,
+          // except in its probe tile (whose entry keeps den > 0 in the sum)
+          const bool skip = !p.live_rank[rank] && __ldcg(p.den_found + rank) != 0 &&
+                            probe_tile(q, p.W, p.H, p.gx) != (uint32_t)(ty * p.gx + tx);
+          box[c] = skip ? 0u : __float_as_uint(e1.w) & ellipse_halves(e0, e1);
           D.e0[t] = e0;
           D.e1[t] = e1;
         }
@@ -673,9 +700,38 @@ __device__ __forceinline__ void dead_item(const ShadowParams& p, uint32_t w, Dea
         const uint32_t slot = p.off[rank] + (uint32_t)((ty - qr.r.y) * (qr.r.z - qr.r.x + 1) + (tx - qr.r.x));
         p.partial[slot] = make_float2(0.f, d0 + d1);
         p.pass_mask[rb + t] = (uint8_t)((d0 > 0.f ? 0x3u : 0u) | (d1 > 0.f ? 0xCu : 0u));
+        if (d0 + d1 > 0.f && !p.live_rank[rank]) __stcg(p.den_found + rank, (uint8_t)1);
       }
     }
   }
+
+// Before K6c: a Gaussian none of whose entries K6b saw has its pixel nearest
+// the splat centre tested with K6c's exact arithmetic (the entry of that
+// tile, the pixel's power against the threshold); if it passes, den > 0 is
+// known and K6c can skip every entry of the Gaussian.  Only a pixel that K6c
+// itself would evaluate counts: inside the image, in a tile of the
+// Gaussian's rectangle, in a half its box and ellipse reach.
+__global__ void k_dead_probe(const ShadowParams p, int n) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n || p.live_rank[r]) return;
+  const SplatRec q = p.rrec[r];
+  if (q.r.x < 0) return;  // not in the light view
+  const float cx = q.a.x + q.b.w, cy = q.a.y + q.c.x;
+  if (!(cx >= 0.f && cy >= 0.f && cx < (float)p.W && cy < (float)p.H)) return;
+  const int px = (int)cx, py = (int)cy;
+  const int tx = px / kTile, ty = py / kTile;
+  if (tx < q.r.x || tx > q.r.z || ty < q.r.y || ty > q.r.w) return;
+  float4 e0, e1;
+  make_entry(q, (float)(tx * kTile), (float)(ty * kTile), e0, e1);
+  const int x = px - tx * kTile, y = py - ty * kTile, h = y >> 3;
+  // K6c evaluates the half only if the entry's box and ellipse reach it
+  if (!(__float_as_uint(e1.w) & ellipse_halves(e0, e1) & (3u << (2 * h)))) return;
+  const float dx = (0.5f + (float)x) - e0.x;
+  const float sx = (e0.z * dx) * dx, v = e1.x * dx;
+  const float dy = ((8.f * h + 0.5f) + (float)(y & 7)) - e0.y;
+  const float pw = fmaf(dy, fmaf(e0.w, dy, v), sx);
+  if (pw >= e1.y) p.den_found[r] = 1;
+}
 
 template <bool BATCH>
 __global__ void __launch_bounds__(kDeadWarps * 32, 6) k_shadow_dead(const ShadowParams p, const ShadowParams* reqs,
@@ -1210,6 +1266,8 @@ ShadowParams shadow_params(const FrameArgs& f) {
   p.light_final = at<float>(ws, f.L->light_final);
   p.light_stop = at<uint32_t>(ws, f.L->light_stop);
   p.status = header + H_STATUS;
+  p.live_rank = at<uint8_t>(ws, f.L->rank_flags);
+  p.den_found = p.live_rank + f.L->n;
   p.W = f.L->width; p.H = f.L->height; p.gx = f.L->gx;
   p.amax = f.opts.alpha_max;
   return p;
@@ -1303,6 +1361,7 @@ void prepare_shadow_composite(const FrameArgs& f, cudaStream_t s) {
   uint32_t* lvl = at<uint32_t>(ws, f.L->seg_lvl);
   cudaMemsetAsync(lvl + kSegLevels + 1, 0, 12, s);  // the tickets
   cudaMemsetAsync(at<uint32_t>(ws, f.L->seg_flag), 0, 4 * shadow_seg_items(f.L->ntiles, f.L->cap), s);
+  cudaMemsetAsync(ws + f.L->rank_flags, 0, 2 * (size_t)f.L->n, s);
   k_tile_order<<<1, 1024, 0, s>>>(at<uint32_t>(ws, b.tile_start), f.L->ntiles, at<uint32_t>(ws, f.L->tile_order[1]),
                                   kSegLen, lvl);
   count_launch();
@@ -1316,8 +1375,9 @@ void launch_shadow_composite(const FrameArgs& f, cudaStream_t s) {
   // persistent warps: every resident warp slot takes segments from a ticket
   k_shadow_chain<false><<<nsm * o.chain, kSegWarps * 32, 0, s>>>(p, nullptr, 1);
   k_shadow<false><<<nsm * o.live, kSegWarps * 32, 0, s>>>(p, nullptr, 1);
+  k_dead_probe<<<(f.L->n + 255) / 256, 256, 0, s>>>(p, f.L->n);
   k_shadow_dead<false><<<nsm * o.dead, kDeadWarps * 32, 0, s>>>(p, nullptr, 1);
-  count_launch(3);
+  count_launch(4);
 }
 
 // Self-test of the chain's bounded waits: the segment plan of a frame whose
@@ -1348,8 +1408,9 @@ void launch_shadow_composite_batch(const FrameArgs* const* f, int n, unsigned ch
   const int nsm = device_sm_count();
   k_shadow_chain<true><<<nsm * o.chain, kSegWarps * 32, 0, s>>>(hp[0], dp, n);
   k_shadow<true><<<nsm * o.live, kSegWarps * 32, 0, s>>>(hp[0], dp, n);
+  for (int r = 0; r < n; ++r) k_dead_probe<<<(f[r]->L->n + 255) / 256, 256, 0, s>>>(hp[r], f[r]->L->n);
   k_shadow_dead<true><<<nsm * o.dead, kDeadWarps * 32, 0, s>>>(hp[0], dp, n);
-  count_launch(3);
+  count_launch(2 + n + 1);
 }
 
 void launch_shadow_reduce(const FrameArgs& f, cudaStream_t s) {

@@ -74,6 +74,7 @@ struct Workspace {
   size_t seg_lvl = 0;   // u32[1025 + 3]: shadow work items per segment level, then three ticket counters
   size_t seg_flag = 0;  // u32[items]: shadow segment publications (0 none, 1 done, 2 done and all stopped)
   size_t seg_pub = 0;   // float[items][256]: the products each shadow segment hands to the next
+  size_t rank_flags = 0;  // u8[2N] by light rank: has an entry in a segment with an open ray; a dead unit passed
   int n = 0, width = 0, height = 0, gx = 0, gy = 0, ntiles = 0;
   size_t cap = 0;
   int nb_n = 0;    // radix blocks over N
