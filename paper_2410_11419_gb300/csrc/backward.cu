@@ -69,17 +69,20 @@ BwdPlan plan_bwd(int n, const MlpDev& phi, const MlpDev& psi) {
 
 // pixel offset, power and alpha of a splat record at a pixel centre
 struct Eval {
-  float dx, dy, power, beta, alpha;
+  float dx, dy, beta, alpha;
   bool pass, clamped;
 };
-__device__ __forceinline__ Eval eval_rec(const SplatRec& q, float fx, float fy, float amax) {
+// A camera-splat entry (make_entry, tile-relative) at the tile pixel centre
+// (lx, ly), with the forward composite's arithmetic (power2_at): pass,
+// beta = 2^power2, alpha = min(amax, gamma beta); (dx, dy) = pixel - centre.
+__device__ __forceinline__ Eval eval_entry(const float4 e0, const float4 e1, float lx, float ly, float amax) {
   Eval r;
-  r.dx = (fx - q.a.x) - q.b.w;
-  r.dy = (fy - q.a.y) - q.c.x;
-  r.power = -0.5f * (q.b.x * r.dx * r.dx + q.b.z * r.dy * r.dy) - q.b.y * r.dx * r.dy;
-  r.pass = r.power >= q.c.w;
-  r.beta = r.pass ? __expf(r.power) : 0.f;
-  const float ga = q.a.z * r.beta;
+  r.dx = lx - e0.x;
+  r.dy = ly - e0.y;
+  const float pw = power2_at(e0, e1.x, lx, ly);
+  r.pass = pw >= e1.y;
+  r.beta = r.pass ? ex2(pw) : 0.f;
+  const float ga = e1.z * r.beta;
   r.clamped = ga >= amax;
   r.alpha = fminf(amax, ga);
   return r;
@@ -137,13 +140,14 @@ __device__ __forceinline__ float warp_sum16(const float (&v)[16], int lane) {
 
 __global__ void __launch_bounds__(256) k_camera_bwd(CamBwdParams p) {
   __shared__ SplatRec R[256];
-  __shared__ float4 C0[256], C1[256];
+  __shared__ float4 E0[256], E1[256], C0[256], C1[256];
   __shared__ uint32_t G[256];
   __shared__ int s_max;
   const int tile = (int)p.tile_order[blockIdx.x], tx = tile % p.gx, ty = tile / p.gx, t = threadIdx.x;
   const int px = tx * kTile + (t & 15), py = ty * kTile + (t >> 4);
   const bool inside = px < p.W && py < p.H;
-  const float fx = px + 0.5f, fy = py + 0.5f;
+  const float ox = (float)(tx * kTile), oy = (float)(ty * kTile);
+  const float lx = (float)(t & 15) + 0.5f, ly = (float)(t >> 4) + 0.5f;
   const uint32_t b = p.tile_start[tile];
   const size_t pix = (size_t)py * p.W + px;
   uint32_t nc = 0;
@@ -170,7 +174,9 @@ __global__ void __launch_bounds__(256) k_camera_bwd(CamBwdParams p) {
     __syncthreads();
     if (t < cnt) {
       const uint32_t rank = p.list[lo + t];
-      R[t] = p.rrec[rank];
+      const SplatRec q = p.rrec[rank];
+      R[t] = q;
+      make_entry(q, ox, oy, E0[t], E1[t]);
       C0[t] = p.ccol[2 * rank];
       C1[t] = p.ccol[2 * rank + 1];
       G[t] = p.order[rank];
@@ -185,7 +191,7 @@ __global__ void __launch_bounds__(256) k_camera_bwd(CamBwdParams p) {
       bool contrib = false;
       if (active) {
         const SplatRec q = R[jj];
-        const Eval ev = eval_rec(q, fx, fy, p.amax);
+        const Eval ev = eval_entry(E0[jj], E1[jj], lx, ly, p.amax);
         if (ev.pass) {
           contrib = true;
           T = T / (1.f - ev.alpha);

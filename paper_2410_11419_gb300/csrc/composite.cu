@@ -2,43 +2,15 @@
 // (Sec. 3, Eq. 2) with the deferred per-pixel combination (Sec. 4).
 //
 // Both composites stream a 16x16 tile's depth-ordered list through shared
-// memory: the shadow composite with one warp per tile (eight rays per lane),
-// the camera composite with one 256-thread block per tile (one pixel per
-// thread, batches of 256 records).
+// memory as tile-relative entries (splat_eval.cuh): the shadow composite
+// over segments of the list with eight rays per lane, the camera composite
+// with one 128-thread block per tile (two pixels per thread, batches of 256
+// records).
 #include "gs3_internal.cuh"
 #include "splat_eval.cuh"
 
 namespace gs3 {
 namespace {
-
-// Pixel of thread t inside its 16x16 tile: warp w covers the 8x4 block at
-// (8 (w & 1), 4 (w >> 1)); lane l is pixel (l & 7, l >> 3) of that block.
-__device__ __forceinline__ int tile_px(int t) { return ((t >> 5) & 1) * 8 + (t & 7); }
-__device__ __forceinline__ int tile_py(int t) { return ((t >> 5) >> 1) * 4 + ((t & 31) >> 3); }
-
-// Bit w set when the splat's alpha >= alpha_min box can reach warp w's 8x4
-// pixel block of tile (tx, ty); a warp whose bit is clear has no passing
-// pixel and skips the splat.
-__device__ __forceinline__ uint32_t warp_mask(const SplatRec& q, int tx, int ty) {
-  const float hx = q.c.y, hy = q.c.z;
-  if (!(hx >= 0.f)) return 0u;
-  const float u = q.a.x + q.b.w, v = q.a.y + q.c.x;
-  uint32_t m = 0u;
-#pragma unroll
-  for (int w = 0; w < 8; ++w) {
-    const float x0 = tx * kTile + (w & 1) * 8 + 0.5f, y0 = ty * kTile + (w >> 1) * 4 + 0.5f;
-    const bool hit = (u + hx >= x0) && (u - hx <= x0 + 7.f) && (v + hy >= y0) && (v - hy <= y0 + 3.f);
-    m |= hit ? (1u << w) : 0u;
-  }
-  return m;
-}
-
-// power of a splat at a pixel centre; the centre is (a.x + b.w, a.y + c.x),
-// high part subtracted first so the offset keeps its precision.
-__device__ __forceinline__ float splat_power(const float4 a, const float4 b, float vlo, float fx, float fy) {
-  const float dx = (fx - a.x) - b.w, dy = (fy - a.y) - vlo;
-  return -0.5f * (b.x * dx * dx + b.z * dy * dy) - b.y * dx * dy;
-}
 
 // ---------------------------------------------------------------------------
 // K6: shadow composite.
@@ -929,6 +901,9 @@ __global__ void k_fill(float* x, int n, float v) {
 // fall below t_stop; the block leaves a batch loop once all rays stopped.
 // Output: shading * shadow + residual per pixel.
 // ---------------------------------------------------------------------------
+constexpr int kCamThreads = 128;  // two pixels per thread
+constexpr int kCamRec = 256;      // records staged per batch
+
 struct CamParams {
   const uint32_t* list;
   const uint32_t* tile_start;
@@ -944,91 +919,99 @@ struct CamParams {
 };
 
 struct CamSmem {
-  float4 Ga[256], Gb[256], Gc[256], C0[256], C1[256];
-  uint32_t Gmask[256];
+  float4 E0[kCamRec], E1[kCamRec], C0[kCamRec], C1[kCamRec];
 };
 
-// Block blk of a frame: tile tile_order[blk] (longest list first).
+// Block blk of a frame: tile tile_order[blk] (longest list first).  128
+// threads, two pixels each: warp w covers quadrant w (the 8x8 block at
+// (8 (w & 1), 8 (w >> 1))), lane l column l & 7 and rows l >> 3 and
+// (l >> 3) + 4 of it, so the two pixels share the entry's dx terms and a
+// warp skips an entry whose box and ellipse miss its quadrant.  Records are
+// staged as shadow-splat entries (centre relative to the tile, conic times
+// log2 e): the alpha is gamma 2^power2, the power's arithmetic that of the
+// backward (power2_at).
 __device__ __forceinline__ void camera_tile(const CamParams& p, int blk, CamSmem& M) {
-  float4 *Ga = M.Ga, *Gb = M.Gb, *Gc = M.Gc, *C0 = M.C0, *C1 = M.C1;
-  uint32_t* Gmask = M.Gmask;
   const int tile = (int)p.tile_order[blk];
   const int tx = tile % p.gx, ty = tile / p.gx;
-  const int t = threadIdx.x;
-  const uint32_t wbit = 1u << (t >> 5);
-  const int px = tx * kTile + tile_px(t), py = ty * kTile + tile_py(t);
-  const bool inside = px < p.W && py < p.H;
-  const float fx = px + 0.5f, fy = py + 0.5f;
+  const float ox = (float)(tx * kTile), oy = (float)(ty * kTile);
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  const uint32_t wq = 1u << w;
+  const int cx = 8 * (w & 1) + (lane & 7), cy0 = 8 * (w >> 1) + (lane >> 3);
+  const int px = tx * kTile + cx, py[2] = {ty * kTile + cy0, ty * kTile + cy0 + 4};
+  const float lx = cx + 0.5f, ly0 = cy0 + 0.5f, ly1 = cy0 + 4.5f;
   const uint32_t b = p.tile_start[tile], e = p.tile_start[tile + 1];
-  float T = 1.f, S0 = 0.f, S1 = 0.f, S2 = 0.f, Sh = 0.f, R0 = 0.f, R1 = 0.f, R2 = 0.f;
-  bool done = !inside;
-  uint32_t consumed = 0;
-  for (uint32_t rb = b; rb < e; rb += 256) {
-    if (__syncthreads_count(done) == 256) break;
-    const int rc = (int)min(256u, e - rb);
-    if (t < rc) {
-      const uint32_t rank = p.list[rb + t];
-      const SplatRec q = p.rrec[rank];
-      Ga[t] = q.a;
-      Gb[t] = q.b;
-      Gc[t] = q.c;
-      Gmask[t] = warp_mask(q, tx, ty);
-      C0[t] = p.ccol[2 * rank];
-      C1[t] = p.ccol[2 * rank + 1];
+  float T[2] = {1.f, 1.f}, acc[2][7];
+#pragma unroll
+  for (int k = 0; k < 2; ++k)
+#pragma unroll
+    for (int c = 0; c < 7; ++c) acc[k][c] = 0.f;
+  bool done[2] = {!(px < p.W && py[0] < p.H), !(px < p.W && py[1] < p.H)};
+  uint32_t consumed[2] = {0u, 0u};
+  for (uint32_t rb = b; rb < e; rb += kCamRec) {
+    if (__syncthreads_count(done[0] && done[1]) == kCamThreads) break;
+    const int rc = (int)min((uint32_t)kCamRec, e - rb);
+    for (int k = t; k < rc; k += kCamThreads) {
+      const uint32_t rank = p.list[rb + k];
+      float4 e0, e1;
+      make_entry(p.rrec[rank], ox, oy, e0, e1);
+      e1.w = __uint_as_float(__float_as_uint(e1.w) & ellipse_halves(e0, e1));
+      M.E0[k] = e0;
+      M.E1[k] = e1;
+      M.C0[k] = p.ccol[2 * rank];
+      M.C1[k] = p.ccol[2 * rank + 1];
     }
     __syncthreads();
-    if (!done) {
-      // two records' alphas are formed ahead of the serial update of T (the
-      // same arithmetic, in the same order, as one record at a time)
-      auto alpha_of = [&](int jj, float& alpha) -> bool {
-        if (!(Gmask[jj] & wbit)) return false;
-        const float4 ga = Ga[jj], gc = Gc[jj];
-        const float pw = splat_power(ga, Gb[jj], gc.x, fx, fy);
-        if (!(pw >= gc.w)) return false;
-        alpha = fminf(p.amax, ga.z * __expf(pw));
-        return true;
-      };
-      auto take = [&](int jj, float alpha) -> bool {
-        const float Tn = T * (1.f - alpha);
+    if (!(done[0] && done[1])) {
+      // one pixel's step: false once its ray stopped here
+      auto take = [&](int k, int jj, float pw, float g) {
+        const float alpha = fminf(p.amax, g * ex2(pw));
+        const float Tn = T[k] * (1.f - alpha);
         if (Tn < p.tstop) {
-          done = true;
-          consumed = rb - b + jj;
-          return false;
+          done[k] = true;
+          consumed[k] = rb - b + jj;
+          return;
         }
-        const float w = alpha * T;
-        const float4 c0 = C0[jj], c1 = C1[jj];
-        S0 += w * c0.x; S1 += w * c0.y; S2 += w * c0.z;
-        Sh += w * c0.w;
-        R0 += w * c1.x; R1 += w * c1.y; R2 += w * c1.z;
-        T = Tn;
-        return true;
+        const float wt = alpha * T[k];
+        const float4 c0 = M.C0[jj], c1 = M.C1[jj];
+        acc[k][0] += wt * c0.x; acc[k][1] += wt * c0.y; acc[k][2] += wt * c0.z;
+        acc[k][3] += wt * c0.w;
+        acc[k][4] += wt * c1.x; acc[k][5] += wt * c1.y; acc[k][6] += wt * c1.z;
+        T[k] = Tn;
       };
-      for (int jj = 0; jj < rc; jj += 2) {
-        float a0 = 0.f, a1 = 0.f;
-        const bool p0 = alpha_of(jj, a0);
-        const bool p1 = jj + 1 < rc && alpha_of(jj + 1, a1);
-        if (p0 && !take(jj, a0)) break;
-        if (p1 && !take(jj + 1, a1)) break;
+      for (int jj = 0; jj < rc; ++jj) {
+        const float4 e1 = M.E1[jj];
+        if (!(__float_as_uint(e1.w) & wq)) continue;  // warp-uniform
+        float p0, p1;
+        powers2(M.E0[jj], e1.x, lx, ly0, ly1, p0, p1);
+        if (!done[0] && p0 >= e1.y) take(0, jj, p0, e1.z);
+        if (!done[1] && p1 >= e1.y) take(1, jj, p1, e1.z);
+        if (done[0] && done[1]) break;
       }
-      if (!done) consumed = rb - b + rc;
+#pragma unroll
+      for (int k = 0; k < 2; ++k)
+        if (!done[k]) consumed[k] = rb - b + rc;
     }
   }
-  if (inside) {
-    const size_t pix = (size_t)py * p.W + px;
-    p.out[3 * pix + 0] = S0 * Sh + R0;
-    p.out[3 * pix + 1] = S1 * Sh + R1;
-    p.out[3 * pix + 2] = S2 * Sh + R2;
-    p.final_t[pix] = T;
-    p.n_contrib[pix] = consumed;
-    p.pix_aux[2 * pix] = make_float4(S0, S1, S2, Sh);
-    p.pix_aux[2 * pix + 1] = make_float4(R0, R1, R2, 0.f);
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    if (px < p.W && py[k] < p.H) {
+      const size_t pix = (size_t)py[k] * p.W + px;
+      const float* a = acc[k];
+      p.out[3 * pix + 0] = a[0] * a[3] + a[4];
+      p.out[3 * pix + 1] = a[1] * a[3] + a[5];
+      p.out[3 * pix + 2] = a[2] * a[3] + a[6];
+      p.final_t[pix] = T[k];
+      p.n_contrib[pix] = consumed[k];
+      p.pix_aux[2 * pix] = make_float4(a[0], a[1], a[2], a[3]);
+      p.pix_aux[2 * pix + 1] = make_float4(a[4], a[5], a[6], 0.f);
+    }
   }
 }
 
 // One frame (p), or a batch of nreq frames (reqs in device memory) whose
 // tiles follow one another: frame r owns blocks [tile_prefix[r], tile_prefix[r + 1]).
 template <bool BATCH>
-__global__ void __launch_bounds__(256) k_camera(const CamParams p, const CamParams* reqs, const uint32_t* tile_prefix,
+__global__ void __launch_bounds__(kCamThreads) k_camera(const CamParams p, const CamParams* reqs, const uint32_t* tile_prefix,
                                                 int nreq) {
   __shared__ CamSmem M;
   if (BATCH) {
@@ -1060,39 +1043,44 @@ struct EnvCamParams {
 };
 
 struct EnvSmem {
-  float4 Ga[kEnvRec], Gb[kEnvRec], Gc[kEnvRec], R[kEnvRec];
+  float4 E0[kEnvRec], E1[kEnvRec], R[kEnvRec];
   float4 C[kEnvRec][kMaxBatch];
-  uint32_t Gmask[kEnvRec];
 };
 
-__global__ void __launch_bounds__(256) k_camera_env(const EnvCamParams e) {
+// The thread layout and entry arithmetic of camera_tile, with 4 accumulators
+// per light and pixel plus 3 for R.
+__global__ void __launch_bounds__(kCamThreads) k_camera_env(const EnvCamParams e) {
   __shared__ EnvSmem M;
   const CamParams& p = e.c;
   const int nl = e.nl;
   const int tile = (int)p.tile_order[blockIdx.x];
   const int tx = tile % p.gx, ty = tile / p.gx;
-  const int t = threadIdx.x;
-  const uint32_t wbit = 1u << (t >> 5);
-  const int px = tx * kTile + tile_px(t), py = ty * kTile + tile_py(t);
-  const bool inside = px < p.W && py < p.H;
-  const float fx = px + 0.5f, fy = py + 0.5f;
+  const float ox = (float)(tx * kTile), oy = (float)(ty * kTile);
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  const uint32_t wq = 1u << w;
+  const int cx = 8 * (w & 1) + (lane & 7), cy0 = 8 * (w >> 1) + (lane >> 3);
+  const int px = tx * kTile + cx, py[2] = {ty * kTile + cy0, ty * kTile + cy0 + 4};
+  const float lx = cx + 0.5f, ly0 = cy0 + 0.5f, ly1 = cy0 + 4.5f;
   const uint32_t b = p.tile_start[tile], end = p.tile_start[tile + 1];
-  float T = 1.f, R0 = 0.f, R1 = 0.f, R2 = 0.f;
-  float S[kMaxBatch][3], Sh[kMaxBatch];
+  float T[2] = {1.f, 1.f}, R[2][3], S[2][kMaxBatch][3], Sh[2][kMaxBatch];
 #pragma unroll
-  for (int l = 0; l < kMaxBatch; ++l) S[l][0] = S[l][1] = S[l][2] = Sh[l] = 0.f;
-  bool done = !inside;
-  uint32_t consumed = 0;
+  for (int k = 0; k < 2; ++k) {
+    R[k][0] = R[k][1] = R[k][2] = 0.f;
+#pragma unroll
+    for (int l = 0; l < kMaxBatch; ++l) S[k][l][0] = S[k][l][1] = S[k][l][2] = Sh[k][l] = 0.f;
+  }
+  bool done[2] = {!(px < p.W && py[0] < p.H), !(px < p.W && py[1] < p.H)};
+  uint32_t consumed[2] = {0u, 0u};
   for (uint32_t rb = b; rb < end; rb += kEnvRec) {
-    if (__syncthreads_count(done) == 256) break;
+    if (__syncthreads_count(done[0] && done[1]) == kCamThreads) break;
     const int rc = (int)min((uint32_t)kEnvRec, end - rb);
     if (t < rc) {
       const uint32_t rank = p.list[rb + t];
-      const SplatRec q = p.rrec[rank];
-      M.Ga[t] = q.a;
-      M.Gb[t] = q.b;
-      M.Gc[t] = q.c;
-      M.Gmask[t] = warp_mask(q, tx, ty);
+      float4 e0, e1;
+      make_entry(p.rrec[rank], ox, oy, e0, e1);
+      e1.w = __uint_as_float(__float_as_uint(e1.w) & ellipse_halves(e0, e1));
+      M.E0[t] = e0;
+      M.E1[t] = e1;
       M.R[t] = p.ccol[2 * rank + 1];
       const float4* src = e.envcol + (size_t)rank * nl;
 #pragma unroll
@@ -1100,54 +1088,53 @@ __global__ void __launch_bounds__(256) k_camera_env(const EnvCamParams e) {
         if (l < nl) M.C[t][l] = src[l];
     }
     __syncthreads();
-    if (!done) {
-      auto alpha_of = [&](int jj, float& alpha) -> bool {
-        if (!(M.Gmask[jj] & wbit)) return false;
-        const float4 ga = M.Ga[jj], gc = M.Gc[jj];
-        const float pw = splat_power(ga, M.Gb[jj], gc.x, fx, fy);
-        if (!(pw >= gc.w)) return false;
-        alpha = fminf(p.amax, ga.z * __expf(pw));
-        return true;
-      };
-      auto take = [&](int jj, float alpha) -> bool {
-        const float Tn = T * (1.f - alpha);
+    if (!(done[0] && done[1])) {
+      auto take = [&](int k, int jj, float pw, float g) {
+        const float alpha = fminf(p.amax, g * ex2(pw));
+        const float Tn = T[k] * (1.f - alpha);
         if (Tn < p.tstop) {
-          done = true;
-          consumed = rb - b + jj;
-          return false;
+          done[k] = true;
+          consumed[k] = rb - b + jj;
+          return;
         }
-        const float w = alpha * T;
+        const float wt = alpha * T[k];
 #pragma unroll
         for (int l = 0; l < kMaxBatch; ++l) {
           if (l < nl) {
             const float4 c = M.C[jj][l];
-            S[l][0] += w * c.x; S[l][1] += w * c.y; S[l][2] += w * c.z;
-            Sh[l] += w * c.w;
+            S[k][l][0] += wt * c.x; S[k][l][1] += wt * c.y; S[k][l][2] += wt * c.z;
+            Sh[k][l] += wt * c.w;
           }
         }
         const float4 r = M.R[jj];
-        R0 += w * r.x; R1 += w * r.y; R2 += w * r.z;
-        T = Tn;
-        return true;
+        R[k][0] += wt * r.x; R[k][1] += wt * r.y; R[k][2] += wt * r.z;
+        T[k] = Tn;
       };
-      for (int jj = 0; jj < rc; jj += 2) {
-        float a0 = 0.f, a1 = 0.f;
-        const bool p0 = alpha_of(jj, a0);
-        const bool p1 = jj + 1 < rc && alpha_of(jj + 1, a1);
-        if (p0 && !take(jj, a0)) break;
-        if (p1 && !take(jj + 1, a1)) break;
+      for (int jj = 0; jj < rc; ++jj) {
+        const float4 e1 = M.E1[jj];
+        if (!(__float_as_uint(e1.w) & wq)) continue;  // warp-uniform
+        float p0, p1;
+        powers2(M.E0[jj], e1.x, lx, ly0, ly1, p0, p1);
+        if (!done[0] && p0 >= e1.y) take(0, jj, p0, e1.z);
+        if (!done[1] && p1 >= e1.y) take(1, jj, p1, e1.z);
+        if (done[0] && done[1]) break;
       }
-      if (!done) consumed = rb - b + rc;
+#pragma unroll
+      for (int k = 0; k < 2; ++k)
+        if (!done[k]) consumed[k] = rb - b + rc;
     }
   }
-  if (inside) {
-    const size_t pix = (size_t)py * p.W + px;
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    if (!(px < p.W && py[k] < p.H)) continue;
+    const size_t pix = (size_t)py[k] * p.W + px;
     float o0 = 0.f, o1 = 0.f, o2 = 0.f;
 #pragma unroll
     for (int l = 0; l < kMaxBatch; ++l) {
       if (l < nl) {
         // the image light l's own frame gives, then its weight
-        const float i0 = S[l][0] * Sh[l] + R0, i1 = S[l][1] * Sh[l] + R1, i2 = S[l][2] * Sh[l] + R2;
+        const float i0 = S[k][l][0] * Sh[k][l] + R[k][0], i1 = S[k][l][1] * Sh[k][l] + R[k][1],
+                    i2 = S[k][l][2] * Sh[k][l] + R[k][2];
         o0 = fmaf(e.w[l], i0, o0);
         o1 = fmaf(e.w[l], i1, o1);
         o2 = fmaf(e.w[l], i2, o2);
@@ -1161,8 +1148,8 @@ __global__ void __launch_bounds__(256) k_camera_env(const EnvCamParams e) {
     p.out[3 * pix + 0] = o0;
     p.out[3 * pix + 1] = o1;
     p.out[3 * pix + 2] = o2;
-    p.final_t[pix] = T;
-    p.n_contrib[pix] = consumed;
+    p.final_t[pix] = T[k];
+    p.n_contrib[pix] = consumed[k];
   }
 }
 
@@ -1433,7 +1420,7 @@ void launch_fill_shadow_one(const FrameArgs& f, cudaStream_t s) {
 }
 
 void launch_camera_composite(const FrameArgs& f, float* out_rgb, cudaStream_t s) {
-  k_camera<false><<<f.L->ntiles, 256, 0, s>>>(camera_params(f, out_rgb), nullptr, nullptr, 1);
+  k_camera<false><<<f.L->ntiles, kCamThreads, 0, s>>>(camera_params(f, out_rgb), nullptr, nullptr, 1);
   count_launch();
 }
 
@@ -1445,7 +1432,7 @@ void launch_camera_env(const FrameArgs& f0, const float4* envcol, int nl, const 
   e.nl = nl;
   for (int l = 0; l < kMaxBatch; ++l) e.w[l] = l < nl ? w[l] : 0.f;
   e.accumulate = accumulate ? 1 : 0;
-  k_camera_env<<<f0.L->ntiles, 256, 0, s>>>(e);
+  k_camera_env<<<f0.L->ntiles, kCamThreads, 0, s>>>(e);
   count_launch();
 }
 
@@ -1460,7 +1447,7 @@ void launch_camera_composite_batch(const FrameArgs* const* f, float* const* out,
   }
   cudaMemcpyAsync(dev + BatchLayout::camera, hp, sizeof(CamParams) * n, cudaMemcpyHostToDevice, s);
   cudaMemcpyAsync(dev + BatchLayout::prefix, pre, 4 * (n + 1), cudaMemcpyHostToDevice, s);
-  k_camera<true><<<pre[n], 256, 0, s>>>(hp[0], reinterpret_cast<const CamParams*>(dev + BatchLayout::camera),
+  k_camera<true><<<pre[n], kCamThreads, 0, s>>>(hp[0], reinterpret_cast<const CamParams*>(dev + BatchLayout::camera),
                                          reinterpret_cast<const uint32_t*>(dev + BatchLayout::prefix), n);
   count_launch();
 }

@@ -54,6 +54,16 @@ __device__ __forceinline__ void powers2(const float4 e0, float r, float lx, floa
   p1 = fmaf(dy1, fmaf(e0.w, dy1, v), sx);
 }
 
+// The same power2 at one pixel (lx, ly) of the tile: the camera composite
+// and its backward evaluate an entry with this arithmetic (powers2 is its
+// two-pixel form), so both take every alpha decision alike.
+__device__ __forceinline__ float power2_at(const float4 e0, float r, float lx, float ly) {
+  const float dx = lx - e0.x;
+  const float sx = (e0.z * dx) * dx, v = r * dx;
+  const float dy = ly - e0.y;
+  return fmaf(dy, fmaf(e0.w, dy, v), sx);
+}
+
 // A shadow ray stops taking occluders once its product A falls below
 // kShadowStop: the occluder that takes A below it is the last one applied,
 // and A stays frozen after it.  Every receiver behind the stop would see an
