@@ -978,13 +978,24 @@ __device__ __forceinline__ void camera_tile(const CamParams& p, int blk, CamSmem
         acc[k][4] += wt * c1.x; acc[k][5] += wt * c1.y; acc[k][6] += wt * c1.z;
         T[k] = Tn;
       };
-      for (int jj = 0; jj < rc; ++jj) {
-        const float4 e1 = M.E1[jj];
-        if (!(__float_as_uint(e1.w) & wq)) continue;  // warp-uniform
-        float p0, p1;
-        powers2(M.E0[jj], e1.x, lx, ly0, ly1, p0, p1);
-        if (!done[0] && p0 >= e1.y) take(0, jj, p0, e1.z);
-        if (!done[1] && p1 >= e1.y) take(1, jj, p1, e1.z);
+      // two records' powers are formed ahead of the updates (the same
+      // arithmetic, in the same order, as one record at a time)
+      for (int jj = 0; jj < rc; jj += 2) {
+        const float4 ea = M.E1[jj];
+        const bool two = jj + 1 < rc;
+        const float4 eb = two ? M.E1[jj + 1] : ea;
+        const bool ha = (__float_as_uint(ea.w) & wq) != 0u, hb = two && (__float_as_uint(eb.w) & wq) != 0u;
+        float pa0 = 0.f, pa1 = 0.f, pb0 = 0.f, pb1 = 0.f;
+        if (ha) powers2(M.E0[jj], ea.x, lx, ly0, ly1, pa0, pa1);
+        if (hb) powers2(M.E0[jj + 1], eb.x, lx, ly0, ly1, pb0, pb1);
+        if (ha) {
+          if (!done[0] && pa0 >= ea.y) take(0, jj, pa0, ea.z);
+          if (!done[1] && pa1 >= ea.y) take(1, jj, pa1, ea.z);
+        }
+        if (hb) {
+          if (!done[0] && pb0 >= eb.y) take(0, jj + 1, pb0, eb.z);
+          if (!done[1] && pb1 >= eb.y) take(1, jj + 1, pb1, eb.z);
+        }
         if (done[0] && done[1]) break;
       }
 #pragma unroll
