@@ -124,9 +124,16 @@ __global__ void __launch_bounds__(256) k_mlp(MlpParams p) {
   const float* bias = p.net.b;
   for (int l = 0; l < p.net.n_hidden; ++l) {
     __syncthreads();  // H complete, previous Ws no longer read
-    for (int i = t; i < din * WIDTH; i += 256) {
-      const int j = i / din, k = i - j * din;  // W row-major (out, in)
-      Ws[k * (WIDTH + 4) + j] = w[i];
+    {
+      // W row-major (out, in): thread t takes input k = t % kp of rows
+      // j = t / kp, + 256 / kp, ... (kp = din rounded up to 64 or 128), so a
+      // warp's loads are consecutive and several are in flight
+      const int kp = din <= 64 ? 64 : 128, k = t % kp;
+      const int rows = 256 / kp;
+      if (k < din) {
+#pragma unroll 4
+        for (int j = t / kp; j < WIDTH; j += rows) Ws[k * (WIDTH + 4) + j] = w[(size_t)j * din + k];
+      }
     }
     __syncthreads();
     float acc[4][CPT];
