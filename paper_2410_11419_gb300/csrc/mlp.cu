@@ -119,6 +119,10 @@ __global__ void __launch_bounds__(256) k_mlp(MlpParams p) {
 
   constexpr int CPT = WIDTH / 16;  // columns per thread
   const int tcol = t & 15, trow = t >> 4;
+  // output column c of thread column tcol: with 8 per thread two runs of 4
+  // (tcol 4 + c and 64 + tcol 4 + c - 4), so that 16 threads' 16-byte
+  // weight loads cover 256 contiguous bytes (no bank conflict)
+  auto out_col = [](int tc, int c) { return CPT == 8 ? (c >> 2) * 64 + tc * 4 + (c & 3) : tc * CPT + c; };
   int din = p.net.in_dim;
   const float* w = p.net.w;
   const float* bias = p.net.b;
@@ -139,7 +143,7 @@ __global__ void __launch_bounds__(256) k_mlp(MlpParams p) {
     float acc[4][CPT];
 #pragma unroll
     for (int c = 0; c < CPT; ++c) {
-      const float bv = bias[tcol * CPT + c];
+      const float bv = bias[out_col(tcol, c)];
 #pragma unroll
       for (int r = 0; r < 4; ++r) acc[r][c] = bv;
     }
@@ -147,7 +151,7 @@ __global__ void __launch_bounds__(256) k_mlp(MlpParams p) {
       const float4 a = *reinterpret_cast<const float4*>(&H[k][trow * 4]);
       float bv[CPT];
 #pragma unroll
-      for (int c = 0; c < CPT; ++c) bv[c] = Ws[k * (WIDTH + 4) + tcol * CPT + c];
+      for (int c = 0; c < CPT; ++c) bv[c] = Ws[k * (WIDTH + 4) + out_col(tcol, c)];
 #pragma unroll
       for (int c = 0; c < CPT; ++c) {
         acc[0][c] = fmaf(a.x, bv[c], acc[0][c]);
@@ -159,24 +163,24 @@ __global__ void __launch_bounds__(256) k_mlp(MlpParams p) {
     __syncthreads();  // all reads of H done
     const bool leaky = p.net.act == GS3_ACT_LEAKY_RELU;
 #pragma unroll
-    for (int c = 0; c < CPT; ++c)
+    for (int c = 0; c < CPT; ++c) {
+      float v[4];
 #pragma unroll
-      for (int r = 0; r < 4; ++r) {
-        float v = acc[r][c];
-        v = v > 0.f ? v : (leaky ? 0.01f * v : 0.f);
-        H[tcol * CPT + c][trow * 4 + r] = v;
-      }
+      for (int r = 0; r < 4; ++r) v[r] = acc[r][c] > 0.f ? acc[r][c] : (leaky ? 0.01f * acc[r][c] : 0.f);
+      *reinterpret_cast<float4*>(&H[out_col(tcol, c)][trow * 4]) = make_float4(v[0], v[1], v[2], v[3]);
+    }
     w += (size_t)din * WIDTH;
     bias += WIDTH;
     din = WIDTH;
   }
-  __syncthreads();
-  // ---- output layer + sigmoid ----
+  // ---- output layer + sigmoid (its weights staged where the last layer's were) ----
   const int dout = p.net.out_dim;
+  for (int i = t; i < dout * din; i += 256) Ws[i] = w[i];
+  __syncthreads();
   if (t < kRows * dout) {
     const int row = t % kRows, o = t / kRows;
     float acc = bias[o];
-    const float* wr = w + (size_t)o * din;
+    const float* wr = Ws + o * din;
     for (int k = 0; k < din; ++k) acc = fmaf(H[k][row], wr[k], acc);
     const float y = 1.f / (1.f + __expf(-acc));
     if (g0 + row < rows) {
