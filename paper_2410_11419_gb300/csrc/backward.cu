@@ -144,10 +144,15 @@ __global__ void __launch_bounds__(256) k_camera_bwd(CamBwdParams p) {
   __shared__ uint32_t G[256];
   __shared__ int s_max;
   const int tile = (int)p.tile_order[blockIdx.x], tx = tile % p.gx, ty = tile / p.gx, t = threadIdx.x;
-  const int px = tx * kTile + (t & 15), py = ty * kTile + (t >> 4);
+  // warps 2q and 2q + 1 take quadrant q of the tile (the 8x8 block at
+  // (8 (q & 1), 8 (q >> 1))), so a warp skips an entry whose alpha box misses it
+  const int q4 = t >> 6, qi = t & 63;
+  const uint32_t qbit = 1u << q4;
+  const int cx = 8 * (q4 & 1) + (qi & 7), cy = 8 * (q4 >> 1) + (qi >> 3);
+  const int px = tx * kTile + cx, py = ty * kTile + cy;
   const bool inside = px < p.W && py < p.H;
   const float ox = (float)(tx * kTile), oy = (float)(ty * kTile);
-  const float lx = (float)(t & 15) + 0.5f, ly = (float)(t >> 4) + 0.5f;
+  const float lx = (float)cx + 0.5f, ly = (float)cy + 0.5f;
   const uint32_t b = p.tile_start[tile];
   const size_t pix = (size_t)py * p.W + px;
   uint32_t nc = 0;
@@ -176,13 +181,18 @@ __global__ void __launch_bounds__(256) k_camera_bwd(CamBwdParams p) {
       const uint32_t rank = p.list[lo + t];
       const SplatRec q = p.rrec[rank];
       R[t] = q;
-      make_entry(q, ox, oy, E0[t], E1[t]);
+      float4 e0, e1;
+      make_entry(q, ox, oy, e0, e1);
+      e1.w = __uint_as_float(__float_as_uint(e1.w) & ellipse_halves(e0, e1));  // as the forward culls
+      E0[t] = e0;
+      E1[t] = e1;
       C0[t] = p.ccol[2 * rank];
       C1[t] = p.ccol[2 * rank + 1];
       G[t] = p.order[rank];
     }
     __syncthreads();
     for (int jj = cnt - 1; jj >= 0; --jj) {
+      if (!(__float_as_uint(E1[jj].w) & qbit)) continue;  // warp-uniform: the forward skipped it here too
       const uint32_t i = lo + jj;
       const bool active = inside && (i - b) < nc;
       float gv[16];

@@ -92,36 +92,6 @@ struct ShadowSmem {  // one warp's
   float2 red[kRedGroup][33];  // per receiver of the group, per lane: (num, den); padded row
 };
 
-// Halves of a tile (0x3: rows 0-7, 0xC: rows 8-15, as quadrant bits) where
-// the entry's alpha >= alpha_min ellipse can hold a pixel centre.  With
-// q = -power2 = al dx^2 + be dx dy + ga dy^2 (positive definite), a pixel
-// passes where q <= -thr.  The minimum of q over a half's rectangle of pixel
-// centres is 0 if the splat centre lies inside, else it lies on an edge: on
-// x = X the minimiser is dy = -be X / (2 ga) clamped to the edge, on y = Y
-// dx = -be Y / (2 al).  The margin, 1e-4 of a bound on the terms' size, is far
-// above the FP32 rounding of either side, so a half with a passing pixel is
-// never dropped; only the work is culled, not the result.
-__device__ __forceinline__ uint32_t ellipse_halves(const float4 e0, const float4 e1) {
-  const float al = -e0.z, ga = -e0.w, be = -e1.x, lim = -e1.y;
-  const float X0 = 0.5f - e0.x, X1 = 15.5f - e0.x;
-  const float mx = fmaxf(X0 * X0, X1 * X1);
-  auto q = [&](float dx, float dy) { return fmaf(dx, fmaf(al, dx, be * dy), ga * dy * dy); };
-  uint32_t m = 0u;
-#pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    const float Y0 = 8.f * h + 0.5f - e0.y, Y1 = 8.f * h + 7.5f - e0.y;
-    float best = 0.f;
-    if (!(X0 <= 0.f && X1 >= 0.f && Y0 <= 0.f && Y1 >= 0.f)) {
-      const float kx = -be / (2.f * ga), ky = -be / (2.f * al);
-      best = fminf(fminf(q(X0, fminf(fmaxf(kx * X0, Y0), Y1)), q(X1, fminf(fmaxf(kx * X1, Y0), Y1))),
-                   fminf(q(fminf(fmaxf(ky * Y0, X0), X1), Y0), q(fminf(fmaxf(ky * Y1, X0), X1), Y1)));
-    }
-    const float size = 2.f * (al * mx + ga * fmaxf(Y0 * Y0, Y1 * Y1));
-    if (best <= lim + 1e-4f * (1.f + size)) m |= 3u << (2 * h);
-  }
-  return m;
-}
-
 // one list entry, staged: make_entry's record plus the halves its box and
 // ellipse both reach (in e1.w)
 __device__ __forceinline__ void stage_entry(const ShadowParams& p, uint32_t idx, float ox, float oy, float4& e0,
