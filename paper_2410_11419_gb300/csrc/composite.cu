@@ -806,21 +806,67 @@ __global__ void __launch_bounds__(256) k_gather_depth(const uint32_t* __restrict
     dl[i] = __uint_as_float(rank_key[list[i]]);
 }
 
-// K(i) for every entry i of the light lists: the first index of i's tile
-// segment whose distance is >= d_i - bias (the end of i's occluder prefix).
-__global__ void __launch_bounds__(256) k_occluder_bound(const uint32_t* __restrict__ keys,
-                                                        const uint32_t* __restrict__ tile_start,
-                                                        const float* __restrict__ dl, const uint32_t* header,
-                                                        float bias, uint32_t* __restrict__ kb, uint32_t limit) {
-  const uint32_t P = min(header[H_PAIRS_LIGHT], limit);
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < P; i += gridDim.x * blockDim.x) {
-    const float thr = __fsub_rn(dl[i], bias);
-    uint32_t lo = tile_start[keys[i]], hi = i;
-    while (lo < hi) {
-      const uint32_t mid = (lo + hi) >> 1;
-      if (dl[mid] < thr) lo = mid + 1; else hi = mid;
-    }
-    kb[i] = lo;
+// K(i) of entry i of a light list: the first index of i's tile list (from b)
+// whose distance is >= d_i - bias, the end of i's occluder prefix.
+__device__ __forceinline__ uint32_t occ_bound(const float* __restrict__ dl, uint32_t b, uint32_t i, float bias) {
+  const float thr = __fsub_rn(dl[i], bias);
+  uint32_t lo = b, hi = i;
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (dl[mid] < thr) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+// The level s of work item w and the item's tile position (lvl_off holds
+// each level's first item).
+__device__ __forceinline__ int item_level(const uint32_t* lvl_off, uint32_t w) {
+  int lo = 0, hi = kSegLevels;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (lvl_off[mid] <= w) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+// K at the entries the segment plan reads (every segment's first entry and
+// every tile's last), one thread per segment, before K6a.
+__global__ void __launch_bounds__(256) k_bound_starts(const ShadowParams p, const float* __restrict__ dl,
+                                                      uint32_t* __restrict__ kb, float bias) {
+  const uint32_t w = blockIdx.x * blockDim.x + threadIdx.x;
+  if (w >= p.lvl_off[kSegLevels]) return;
+  const int s = item_level(p.lvl_off, w);
+  const int tile = (int)p.tile_order[w - p.lvl_off[s]];
+  const uint32_t b = p.tile_start[tile], e = p.tile_start[tile + 1];
+  if (e <= b) return;
+  const uint32_t r0 = b + (uint32_t)s * kSegLen;
+  kb[r0] = occ_bound(dl, b, r0, bias);
+  if ((uint32_t)s == seg_count(e - b) - 1 && e - 1 > r0) kb[e - 1] = occ_bound(dl, b, e - 1, bias);
+}
+
+// After K6a: K of every other entry of a segment with an open ray (K6b reads
+// it per receiver), one warp per segment.  In a segment every ray enters
+// stopped no kernel takes an occluder or needs the exact bound: its entries
+// get the segment's first bound C_s (<= K(j)); the backward, which reads
+// them, takes no occluder at or past a ray's stop, and every ray stopped
+// before C_s, so any bound in [C_s, K(j)] gives it the same result.
+__global__ void __launch_bounds__(256) k_bound_rest(const ShadowParams p, const float* __restrict__ dl,
+                                                    uint32_t* __restrict__ kb, float bias) {
+  const uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= p.lvl_off[kSegLevels]) return;
+  const int s = item_level(p.lvl_off, w);
+  const uint32_t pos = w - p.lvl_off[s];
+  const int tile = (int)p.tile_order[pos];
+  const uint32_t b = p.tile_start[tile], e = p.tile_start[tile + 1];
+  if (e <= b) return;
+  const bool last = (uint32_t)s == seg_count(e - b) - 1;
+  const uint32_t r0 = b + (uint32_t)s * kSegLen, r1 = last ? e : r0 + kSegLen;
+  const bool open = s == 0 || __ldcg(p.pub_flag + p.lvl_off[s - 1] + pos) != 2u;
+  const uint32_t c0 = kb[r0];
+  for (uint32_t j = r0 + 1 + lane; j < r1; j += 32) {
+    if (j == e - 1) continue;  // k_bound_starts's
+    kb[j] = open ? occ_bound(dl, b, j, bias) : c0;
   }
 }
 
@@ -1322,9 +1368,7 @@ void prepare_shadow_composite(const FrameArgs& f, cudaStream_t s) {
   // the depth sort's four passes leave the keys in rank order in sk[1]
   k_gather_depth<<<blocks, 256, 0, s>>>(at<uint32_t>(ws, b.tv[fin]), at<uint32_t>(ws, b.sk[1]), header, dl,
                                         (uint32_t)f.L->cap);
-  k_occluder_bound<<<blocks, 256, 0, s>>>(at<uint32_t>(ws, b.tk[fin]), at<uint32_t>(ws, b.tile_start), dl, header,
-                                          f.opts.shadow_bias, kb, (uint32_t)f.L->cap);
-  count_launch(2);
+  count_launch();
   // the light tiles by segment count, and the work items of each segment level
   uint32_t* lvl = at<uint32_t>(ws, f.L->seg_lvl);
   cudaMemsetAsync(lvl + kSegLevels + 1, 0, 12, s);  // the tickets
@@ -1332,6 +1376,19 @@ void prepare_shadow_composite(const FrameArgs& f, cudaStream_t s) {
   cudaMemsetAsync(ws + f.L->rank_flags, 0, 2 * (size_t)f.L->n, s);
   k_tile_order<<<1, 1024, 0, s>>>(at<uint32_t>(ws, b.tile_start), f.L->ntiles, at<uint32_t>(ws, f.L->tile_order[1]),
                                   kSegLen, lvl);
+  // the occluder bounds the segment plan reads; the rest follow K6a
+  const size_t items = shadow_seg_items(f.L->ntiles, f.L->cap);
+  k_bound_starts<<<(int)((items + 255) / 256), 256, 0, s>>>(shadow_params(f), dl, kb, f.opts.shadow_bias);
+  count_launch(2);
+}
+
+// the occluder bounds of the open segments' other entries (after K6a)
+void launch_bound_rest(const FrameArgs& f, const ShadowParams& p, cudaStream_t s) {
+  const SplatBufs& b = f.L->sp[1];
+  const int fin = (f.L->ntiles <= 256 ? 1 : 2) & 1;
+  const size_t items = shadow_seg_items(f.L->ntiles, f.L->cap);
+  k_bound_rest<<<(int)((items * 32 + 255) / 256), 256, 0, s>>>(p, at<float>(f.ws, b.tk[1 - fin]),
+                                                               at<uint32_t>(f.ws, b.tv[1 - fin]), f.opts.shadow_bias);
   count_launch();
 }
 
@@ -1342,6 +1399,7 @@ void launch_shadow_composite(const FrameArgs& f, cudaStream_t s) {
   const int nsm = device_sm_count();
   // persistent warps: every resident warp slot takes segments from a ticket
   k_shadow_chain<false><<<nsm * o.chain, kSegWarps * 32, 0, s>>>(p, nullptr, 1);
+  launch_bound_rest(f, p, s);
   k_shadow<false><<<nsm * o.live, kSegWarps * 32, 0, s>>>(p, nullptr, 1);
   k_dead_probe<<<(f.L->n + 255) / 256, 256, 0, s>>>(p, f.L->n);
   k_shadow_dead<false><<<nsm * o.dead, kDeadWarps * 32, 0, s>>>(p, nullptr, 1);
@@ -1375,6 +1433,7 @@ void launch_shadow_composite_batch(const FrameArgs* const* f, int n, unsigned ch
   const SegOccupancy o = seg_occupancy();
   const int nsm = device_sm_count();
   k_shadow_chain<true><<<nsm * o.chain, kSegWarps * 32, 0, s>>>(hp[0], dp, n);
+  for (int r = 0; r < n; ++r) launch_bound_rest(*f[r], hp[r], s);
   k_shadow<true><<<nsm * o.live, kSegWarps * 32, 0, s>>>(hp[0], dp, n);
   for (int r = 0; r < n; ++r) k_dead_probe<<<(f[r]->L->n + 255) / 256, 256, 0, s>>>(hp[r], f[r]->L->n);
   k_shadow_dead<true><<<nsm * o.dead, kDeadWarps * 32, 0, s>>>(hp[0], dp, n);
