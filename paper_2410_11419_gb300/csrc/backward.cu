@@ -279,10 +279,27 @@ struct ShadowBwdParams {
   const float* dT;   // by index
   const float* den;  // by index
   const float* T;    // by index
+  const uint32_t* lvl_off;   // the forward's segment plan: first work item of each segment level
+  const uint32_t* pub_flag;  // per item: 2 when every ray entered the next segment stopped
   float* light_geom;
   int W, H, gx;
   float amax;
 };
+
+// The first entry of the tile at launch position pos whose segment every ray
+// enters stopped (the forward's K6a published A = 0 for all rays into it),
+// or e.  Such segments form a suffix of the list.
+__device__ __forceinline__ uint32_t stopped_from(const ShadowBwdParams& p, uint32_t pos, uint32_t b, uint32_t e,
+                                                 int lane) {
+  const uint32_t nseg = seg_count(e - b);
+  for (uint32_t s0 = 1; s0 < nseg; s0 += 32) {
+    const uint32_t s = s0 + (uint32_t)lane;
+    const bool dead = s < nseg && __ldcg(p.pub_flag + p.lvl_off[s - 1] + pos) == 2u;
+    const uint32_t m = __ballot_sync(0xffffffffu, dead);
+    if (m) return b + (s0 + (uint32_t)(__ffs(m) - 1)) * kSegLen;
+  }
+  return e;
+}
 
 constexpr int kBRecv = 64;
 constexpr int kBOcc = 128;
@@ -325,8 +342,11 @@ __global__ void __launch_bounds__(kBThreads, 18) k_shadow_bwd(ShadowBwdParams p)
   const float kFar = 1.0e6f;  // off-image pixels never pass (same rule as the forward)
   const float ox = (float)(tx * kTile), oy = (float)(ty * kTile);
   const float omin = 1.f - p.amax;
-  const uint32_t b = p.tile_start[tile], e = p.tile_start[tile + 1];
-  if (b == e) return;
+  const uint32_t b = p.tile_start[tile], e_all = p.tile_start[tile + 1];
+  if (b == e_all) return;
+  // receivers from the first stopped segment on are k_shadow_bwd_stopped's;
+  // this warp sweeps the open segments back to front
+  const uint32_t e = stopped_from(p, blockIdx.x, b, e_all, lane);
   float ly[kBPx], A[kBPx], Sm[kBPx];
   uint32_t lim[kBPx];
   uint32_t lmax = 0u;
@@ -343,7 +363,9 @@ __global__ void __launch_bounds__(kBThreads, 18) k_shadow_bwd(ShadowBwdParams p)
   }
   // occluders at or past every ray's limit were taken by none
   const uint32_t wlim = __reduce_max_sync(0xffffffffu, lmax);
-  uint32_t kc = min(p.kbound[e - 1], max(wlim, b));
+  // occluders the forward walked end at K of the last entry, or, before a
+  // stopped segment, at its first bound C (every ray stopped below it)
+  uint32_t kc = min(e < e_all ? p.kbound[e] : p.kbound[e - 1], max(wlim, b));
 
   // An entry's gradient terms, per lane, go to a shared-memory row; every
   // kGradGroup entries lane 6 e + c (< 24) adds term c of entry e over the
@@ -491,6 +513,79 @@ __global__ void __launch_bounds__(kBThreads, 18) k_shadow_bwd(ShadowBwdParams p)
     for (; kc > kt; --kc) occlude_bwd((int)(kc - 1 - kt), kc - 1);
   }
   if (ng) reduce_grads();
+}
+
+
+// K6b for the receivers of the segments every ray enters stopped: the
+// forward's products there are 0 (its K6a publishes A = 0 into them), so
+// receiver j's beta at ray m carries dL/dbeta = coef_j (0 - T_j) and no
+// occluder of these segments is taken.  The receivers are independent: a
+// warp takes one such segment, its lanes one (receiver, half) unit at a time
+// (the halves the forward found passing), walk the unit's 16 x 8 pixels with
+// the forward's power arithmetic, and turn the per-column moments of
+// w = dL/dpower into the centre and conic gradients, added to the Gaussian's
+// accumulators.  A receiver with T_j = 0 (no pixel of it sees light) adds
+// nothing and is skipped.
+constexpr int kStopWarps = 4;
+__global__ void __launch_bounds__(kStopWarps * 32) k_shadow_bwd_stopped(ShadowBwdParams p) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t w = blockIdx.x * kStopWarps + (threadIdx.x >> 5);
+  if (w >= p.lvl_off[kSegLevels]) return;
+  int lo = 0, hi = kSegLevels;  // the item's level: largest s with lvl_off[s] <= w
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (p.lvl_off[mid] <= w) lo = mid; else hi = mid;
+  }
+  if (lo == 0) return;  // a tile's first segment starts with every ray open
+  const uint32_t pos = w - p.lvl_off[lo];
+  if (__ldcg(p.pub_flag + p.lvl_off[lo - 1] + pos) != 2u) return;
+  const int tile = (int)p.tile_order[pos];
+  const int tx = tile % p.gx, ty = tile / p.gx;
+  const float ox = (float)(tx * kTile), oy = (float)(ty * kTile);
+  const uint32_t b = p.tile_start[tile], e = p.tile_start[tile + 1];
+  const bool last = (uint32_t)lo == seg_count(e - b) - 1;
+  const uint32_t r0 = b + (uint32_t)lo * kSegLen, r1 = last ? e : r0 + kSegLen;
+  const int ncol = min(kTile, p.W - tx * kTile), nrow = min(kTile, p.H - ty * kTile);
+  // units (receiver, half), two per receiver, taken by the lanes in turn
+  for (uint32_t u = lane; u < 2u * (r1 - r0); u += 32) {
+    const uint32_t j = r0 + (u >> 1);
+    const int h = (int)(u & 1u);
+    const uint32_t bits = p.pass_mask[j];
+    if (!(bits & (3u << (2 * h)))) continue;
+    const uint32_t rank = p.list[j];
+    const uint32_t g = p.order[rank];
+    const float den = p.den[g], Tj = p.T[g];
+    const float coef = den > 0.f ? p.dT[g] / den : 0.f;
+    const float cw = -coef * Tj;  // w = dL/dpower = coef beta (0 - T_j)
+    if (cw == 0.f) continue;
+    float4 e0, e1;
+    make_entry(p.rrec[rank], ox, oy, e0, e1);
+    float gsum[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    const int y1 = min(8 * h + 8, nrow);
+    for (int x = 0; x < ncol; ++x) {
+      const float lx = (float)x + 0.5f;
+      const float dx = lx - e0.x;
+      const float sx = (e0.z * dx) * dx, v = e1.x * dx;
+      float m0 = 0.f, m1 = 0.f, m2 = 0.f;
+      for (int y = 8 * h; y < y1; ++y) {
+        const float dy = ((float)y + 0.5f) - e0.y;
+        const float pw = fmaf(dy, fmaf(e0.w, dy, v), sx);
+        if (pw >= e1.y) {
+          const float wv = cw * ex2(pw), wdy = wv * dy;
+          m0 += wv;
+          m1 += wdy;
+          m2 = fmaf(wdy, dy, m2);
+        }
+      }
+      float gc[8];
+      moments_to_grad(e0, e1.x, dx, m0, m1, m2, gc);
+#pragma unroll
+      for (int c = 0; c < 5; ++c) gsum[c] += gc[c];
+    }
+#pragma unroll
+    for (int c = 0; c < 5; ++c)
+      if (gsum[c] != 0.f) atomicAdd(p.light_geom + (size_t)kGeom * g + c, gsum[c]);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -933,6 +1028,8 @@ gs3_status run_backward(const FrameArgs& f, const float* dimg, void* bws, size_t
     p.dT = dT;
     p.den = at<float>(ws, L.shadow_den);
     p.T = at<float>(ws, L.T);
+    p.lvl_off = at<uint32_t>(ws, L.seg_lvl);
+    p.pub_flag = at<uint32_t>(ws, L.seg_flag);
     p.light_geom = light_geom;
     p.W = L.width; p.H = L.height; p.gx = L.gx;
     p.amax = f.opts.alpha_max;
@@ -942,7 +1039,9 @@ gs3_status run_backward(const FrameArgs& f, const float* dimg, void* bws, size_t
                                   (int)cudaSharedmemCarveoutMaxShared) == cudaSuccess;
     });
     k_shadow_bwd<<<L.ntiles, kBThreads, 0, s>>>(p);
-    count_launch();
+    const size_t items = shadow_seg_items(L.ntiles, L.cap);
+    k_shadow_bwd_stopped<<<(int)((items + kStopWarps - 1) / kStopWarps), kStopWarps * 32, 0, s>>>(p);
+    count_launch(2);
   }
   // K1b
   {

@@ -47,8 +47,6 @@ namespace {
 // q.  Thread layout as in the splat evaluation: lane l owns column l & 15,
 // rows (l >> 4) + 2 i, i = 0..7, which is ray 32 i + l of the tile.
 // ---------------------------------------------------------------------------
-constexpr uint32_t kSegLen = 256;   // receivers per segment
-constexpr int kSegLevels = 1024;    // segments per tile at most (the last takes the rest)
 constexpr int kSegWarps = 4;        // independent warps per block
 constexpr int kRecv = 32;           // receivers staged at a time
 constexpr int kOccWin = 32;         // occluder window
@@ -56,10 +54,6 @@ constexpr int kRedGroup = 16;       // receivers whose per-lane sums are reduced
 constexpr int kPx = 8;              // rays per lane
 constexpr int kSegSpin = 1 << 20;   // polls of a predecessor's publication before giving up
 
-__host__ __device__ inline uint32_t seg_count(uint32_t len) {
-  const uint32_t n = (len + kSegLen - 1) / kSegLen;
-  return n < 1 ? 1u : (n > (uint32_t)(kSegLevels - 1) ? (uint32_t)(kSegLevels - 1) : n);
-}
 
 struct ShadowParams {
   const uint32_t* list;

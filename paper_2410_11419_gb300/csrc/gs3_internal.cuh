@@ -227,6 +227,15 @@ void launch_camera_composite_batch(const FrameArgs* const* f, float* const* out,
                                    unsigned char* host, cudaStream_t s);
 // shadow composite work items (tile segments) a frame can have at most
 size_t shadow_seg_items(int ntiles, size_t cap);
+// A light tile's list is cut into segments of kSegLen entries, at most
+// kSegLevels - 1 per tile (the last takes the rest); the shadow composite and
+// its backward share the cut.
+constexpr uint32_t kSegLen = 256;
+constexpr int kSegLevels = 1024;
+__host__ __device__ inline uint32_t seg_count(uint32_t len) {
+  const uint32_t n = (len + kSegLen - 1) / kSegLen;
+  return n < 1 ? 1u : (n > (uint32_t)(kSegLevels - 1) ? (uint32_t)(kSegLevels - 1) : n);
+}
 // a splat's tiles ordered longest list first (in length steps of 8), into L.tile_order[splat]
 void launch_tile_order(const FrameArgs& f, int splat, cudaStream_t s);
 void launch_shadow_reduce(const FrameArgs& f, cudaStream_t s);
