@@ -592,7 +592,7 @@ gs3_status gs3_render_backward(gs3_scene* scene, const gs3_camera* cam, const gs
   f.ws = static_cast<unsigned char*>(workspace);
   f.L = &L;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  gs3_status st = run_backward(f, dimg, bws, bws_bytes, *grads, s);
+  gs3_status st = run_backward(f, dimg, bws, bws_bytes, *grads, s, thread_side_stream());
   if (st != GS3_OK) return fail(st, "gs3_render_backward: bad workspace");
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "gs3_render_backward: launch");

@@ -945,7 +945,7 @@ size_t backward_workspace_bytes(int n, const MlpDev& phi, const MlpDev& psi) {
 }
 
 gs3_status run_backward(const FrameArgs& f, const float* dimg, void* bws, size_t bws_bytes,
-                        const gs3_grads& out, cudaStream_t s) {
+                        const gs3_grads& out, cudaStream_t s, SideStream* side) {
   const int n = f.sc.n;
   const BwdPlan bp = plan_bwd(n, f.sc.phi, f.sc.psi);
   if (bws_bytes < bp.total) return GS3_ERR_INVALID_ARG;
@@ -979,8 +979,8 @@ gs3_status run_backward(const FrameArgs& f, const float* dimg, void* bws, size_t
     k_camera_bwd<<<L.ntiles, 256, 0, s>>>(p);
     count_launch();
   }
-  // K8b: Psi and Phi, then the weight gradients in fixed block order
-  for (int which = 1; which >= 0; --which) {
+  // K8b: one network's backward, then its weight gradients in fixed block order
+  auto mlp_bwd = [&](int which, cudaStream_t st) {
     const MlpDev& m = which == 0 ? f.sc.phi : f.sc.psi;
     float* wred = reinterpret_cast<float*>(B + bp.wred[which]);
     const bool identity = (f.opts.ablate & (which == 0 ? GS3_ABLATE_PHI : GS3_ABLATE_PSI)) != 0;
@@ -988,9 +988,9 @@ gs3_status run_backward(const FrameArgs& f, const float* dimg, void* bws, size_t
     float* db = which == 0 ? out.phi_b : out.psi_b;
     const size_t np = mlp_params(m);
     if (identity) {
-      cudaMemsetAsync(wred, 0, 4 * np, s);
+      cudaMemsetAsync(wred, 0, 4 * np, st);
       if (which == 0) {  // T' = T: the gradient passes straight through
-        k_copy_strided<<<(n + 255) / 256, 256, 0, s>>>(color, kColor, 3, dT, n);
+        k_copy_strided<<<(n + 255) / 256, 256, 0, st>>>(color, kColor, 3, dT, n);
         count_launch();
       }
     } else {
@@ -1008,10 +1008,22 @@ gs3_status run_backward(const FrameArgs& f, const float* dimg, void* bws, size_t
       a.dT = dT;
       a.mlp_in = mlp_in;
       a.status = at<uint32_t>(ws, L.header) + H_STATUS;
-      run_mlp_backward(a, B + bp.mlp_scratch, wred, s);
+      run_mlp_backward(a, B + bp.mlp_scratch, wred, st);
     }
-    k_split_params<<<64, 256, 0, s>>>(wred, m.in_dim, m.width, m.n_hidden, m.out_dim, dw, db);
+    k_split_params<<<64, 256, 0, st>>>(wred, m.in_dim, m.width, m.n_hidden, m.out_dim, dw, db);
     count_launch();
+  };
+  // Phi first: the shadow backward takes its dL/dT.  Then Psi, which the
+  // shadow backward does not need, runs on the side stream beside it (the
+  // networks share the MLP scratch, so they run in turn), with the receivers
+  // of the stopped segments; the one-warp-per-tile sweep leaves most SMs idle
+  // towards its end.
+  mlp_bwd(0, s);
+  cudaStream_t ss = s;
+  if (side) {
+    cudaEventRecord(side->fork, s);
+    cudaStreamWaitEvent(side->s, side->fork, 0);
+    ss = side->s;
   }
   // K6b
   if (!(f.opts.ablate & GS3_ABLATE_SHADOW_SPLAT)) {
@@ -1040,8 +1052,13 @@ gs3_status run_backward(const FrameArgs& f, const float* dimg, void* bws, size_t
     });
     k_shadow_bwd<<<L.ntiles, kBThreads, 0, s>>>(p);
     const size_t items = shadow_seg_items(L.ntiles, L.cap);
-    k_shadow_bwd_stopped<<<(int)((items + kStopWarps - 1) / kStopWarps), kStopWarps * 32, 0, s>>>(p);
+    k_shadow_bwd_stopped<<<(int)((items + kStopWarps - 1) / kStopWarps), kStopWarps * 32, 0, ss>>>(p);
     count_launch(2);
+  }
+  mlp_bwd(1, ss);
+  if (side) {
+    cudaEventRecord(side->join, ss);
+    cudaStreamWaitEvent(s, side->join, 0);
   }
   // K1b
   {

@@ -203,8 +203,9 @@ struct MlpArgs {
 };
 size_t mlp_bwd_scratch_bytes(int n, const MlpDev& m);
 void run_mlp_backward(const MlpArgs& a, void* scratch, float* wred, cudaStream_t s);
+// side: a second stream for the parts that can overlap (null: all on s)
 gs3_status run_backward(const FrameArgs& f, const float* dimg, void* bws, size_t bws_bytes,
-                        const gs3_grads& out, cudaStream_t s);
+                        const gs3_grads& out, cudaStream_t s, SideStream* side = nullptr);
 
 // shading and both projections (K1); light_only: the shadow splat's projection only
 void launch_prep(const FrameArgs& f, cudaStream_t s, bool light_only = false);
