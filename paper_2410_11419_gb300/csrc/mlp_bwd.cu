@@ -19,10 +19,11 @@
 //                             partials are summed in block order, so the gradients do not
 //                             depend on scheduling.
 // Both run on the tensor cores in three-pass TF32 (about 2^-21 relative per
-// product, FP32 accumulation).  The output layer's weight gradient (1 or 3
-// units) stays on a register-tiled FP32 SIMT kernel (k_wgemm): a block owns
-// a 128 x 128 tile of C = A B, each thread 8 x 8 of it, with the contraction
-// staged through double-buffered shared memory in chunks of 16.
+// product, FP32 accumulation).  The output layer (1 or 3 units) and its
+// weight gradient run on CUDA cores in k_out_layer.  Hidden widths of 16 take
+// their weight gradients from a register-tiled FP32 SIMT kernel (k_wgemm): a
+// block owns a 128 x 128 tile of C = A B, each thread 8 x 8 of it, with the
+// contraction staged through double-buffered shared memory in chunks of 16.
 // The activations and data gradients of one network live in the backward
 // workspace (about (64 + 4 W) N floats), shared by Phi and Psi in turn.
 #include "gs3_internal.cuh"
