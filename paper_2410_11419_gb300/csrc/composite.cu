@@ -525,6 +525,8 @@ constexpr int kDeadWarps = 4;
 struct DeadSmem {  // one warp's
   float4 e0[kDeadBatch], e1[kDeadBatch];
   float den[2][kDeadBatch];
+  uint32_t slot[kDeadBatch];      // the receiver's partial slot
+  uint32_t rank[kDeadBatch];      // its depth rank, bit 31 set if K6b saw it
   uint16_t unit[2 * kDeadBatch];  // receiver (bits 0-7) and half (bit 8) of each unit
 };
 
@@ -594,15 +596,18 @@ __device__ __forceinline__ void dead_item(const ShadowParams& p, uint32_t w, Dea
         if (t < rc) {
           const uint32_t rank = p.list[rb + t];
           const SplatRec q = p.rrec[rank];
+          const bool live = p.live_rank[rank] != 0;
           float4 e0, e1;
           make_entry(q, ox, oy, e0, e1);
           // skipped: a Gaussian with no open-ray entry whose den is known positive,
           // except in its probe tile (whose entry keeps den > 0 in the sum)
-          const bool skip = !p.live_rank[rank] && __ldcg(p.den_found + rank) != 0 &&
+          const bool skip = !live && __ldcg(p.den_found + rank) != 0 &&
                             probe_tile(q, p.W, p.H, p.gx) != (uint32_t)(ty * p.gx + tx);
           box[c] = skip ? 0u : __float_as_uint(e1.w) & ellipse_halves(e0, e1);
           D.e0[t] = e0;
           D.e1[t] = e1;
+          D.slot[t] = p.off[rank] + (uint32_t)((ty - q.r.y) * (q.r.z - q.r.x + 1) + (tx - q.r.x));
+          D.rank[t] = rank | (live ? 0x80000000u : 0u);
         }
         n0 += __popc(__ballot_sync(0xffffffffu, (box[c] & 0x3u) != 0u));
         n1 += __popc(__ballot_sync(0xffffffffu, (box[c] & 0xCu) != 0u));
@@ -630,13 +635,11 @@ __device__ __forceinline__ void dead_item(const ShadowParams& p, uint32_t w, Dea
       }
       __syncwarp();
       for (int t = lane; t < rc; t += 32) {
-        const uint32_t rank = p.list[rb + t];
-        const SplatRec qr = p.rrec[rank];
         const float d0 = D.den[0][t], d1 = D.den[1][t];
-        const uint32_t slot = p.off[rank] + (uint32_t)((ty - qr.r.y) * (qr.r.z - qr.r.x + 1) + (tx - qr.r.x));
-        p.partial[slot] = make_float2(0.f, d0 + d1);
+        const uint32_t rk = D.rank[t];
+        p.partial[D.slot[t]] = make_float2(0.f, d0 + d1);
         p.pass_mask[rb + t] = (uint8_t)((d0 > 0.f ? 0x3u : 0u) | (d1 > 0.f ? 0xCu : 0u));
-        if (d0 + d1 > 0.f && !p.live_rank[rank]) __stcg(p.den_found + rank, (uint8_t)1);
+        if (d0 + d1 > 0.f && !(rk >> 31)) __stcg(p.den_found + rk, (uint8_t)1);
       }
     }
   }
@@ -670,7 +673,7 @@ __global__ void k_dead_probe(const ShadowParams p, int n) {
 }
 
 template <bool BATCH>
-__global__ void __launch_bounds__(kDeadWarps * 32, 6) k_shadow_dead(const ShadowParams p, const ShadowParams* reqs,
+__global__ void __launch_bounds__(kDeadWarps * 32, 7) k_shadow_dead(const ShadowParams p, const ShadowParams* reqs,
                                                                     int nreq) {
   __shared__ DeadSmem smem[kDeadWarps];
   DeadSmem& D = smem[threadIdx.x >> 5];
