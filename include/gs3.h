@@ -220,7 +220,7 @@ gs3_status gs3_render(gs3_scene *scene, const gs3_camera *camera, const gs3_ligh
 /* Stage bits of gs3_render_stages (in pipeline order). */
 enum {
     GS3_STAGE_PREP = 1,             /* K1: shading colour, both projections, keys */
-    GS3_STAGE_CAMERA_BIN = 2,       /* camera splat: depth sort, pairs, tile sort, ranges, tile launch order */
+    GS3_STAGE_CAMERA_BIN = 2,       /* camera splat: depth sort, per-tile lists and ranges, tile launch order */
     GS3_STAGE_LIGHT_BIN = 4,        /* light splat: the same toward the light */
     GS3_STAGE_SHADOW_COMPOSITE = 8, /* shadow rays: biased transmittance, partial sums (Sec. 4.2) */
     GS3_STAGE_SHADOW_REDUCE = 16,   /* per-Gaussian beta-weighted average (Sec. 4.2) */
@@ -436,8 +436,9 @@ gs3_status gs3_depth_order_static(const uint32_t *keys, uint32_t n, uint32_t *or
 /* ---- Self-test of the bounded device waits ------------------------------
  * Not an operation of the paper: a check that a device-side wait which can
  * never end gives up instead of holding the GPU.  Runs one pass of the
- * look-back tile sort that gs3_render's binning uses (each block waits for
- * the digit counts of the blocks before it) over n zero keys in scratch it
+ * look-back radix sort that gs3_render's depth sorts use (each block waits
+ * for the digit counts of the blocks before it; here with blocks of 4096
+ * keys) over n zero keys in scratch it
  * allocates and frees, with the block tickets starting at 1, so the waits
  * reach ticket 0's words, which no block writes.  Each such wait gives up
  * after its poll bound (well under a second) and the pass records

@@ -115,8 +115,7 @@ Workspace plan_workspace(int n, int width, int height, size_t cap) {
   L.ntiles = L.gx * L.gy;
   L.cap = cap;
   L.nb_n = (int)((n + kDepthSortItems - 1) / kDepthSortItems);
-  L.nb_cap = (int)((cap + kTileSortItems - 1) / kTileSortItems);
-  if (L.nb_cap < 1) L.nb_cap = 1;
+  L.nb_rows = (int)((n + kBinBlock - 1) / kBinBlock);
   const size_t N = (size_t)n;
   const size_t scan_words = scan_scratch_words(N);  // the scan of the tile counts
   Planner P;
@@ -141,8 +140,10 @@ Workspace plan_workspace(int n, int width, int height, size_t cap) {
     b.tv[1] = P.take(4 * cap);
     b.tile_start = P.take(4 * ((size_t)L.ntiles + 1));
     b.scan_part = P.take(4 * scan_words);
-    b.look = P.take(onesweep_bytes(L.nb_cap, 2));
     b.dlook = P.take(onesweep_bytes(L.nb_n, 4));
+    b.row_cnt = P.take(4 * (size_t)L.gy * (size_t)L.nb_rows);
+    b.bin_plan = P.take(4 * (3 * (size_t)L.gy + 3));
+    b.bin_tab = P.take(4 * bin_tab_words(cap, L.gx, L.gy));
   }
   L.partial = P.take(8 * cap);
   L.tile_order[0] = P.take(4 * (size_t)L.ntiles);

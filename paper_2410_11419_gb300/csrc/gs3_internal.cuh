@@ -16,8 +16,17 @@ constexpr int kTilePix = kTile * kTile;
 constexpr int kSortThreads = 256;     // radix-sort block size
 constexpr int kSortRounds = 16;       // items per thread per block tile
 constexpr int kSortTileItems = kSortThreads * kSortRounds;  // 4096 items per block
-constexpr int kTileSortRounds = 16;   // the look-back tile sort: items per thread per block
+constexpr int kTileSortRounds = 16;   // look-back sort of the wait self-test: items per thread per block
 constexpr int kTileSortItems = kSortThreads * kTileSortRounds;
+// Tile binning by counting (tile_bin.cu)
+constexpr int kMaxTileAxis = 1024;    // tiles per image row or column (16384 pixels)
+constexpr int kBinBlock = 256;        // depth ranks per block of the row counts
+// items of a tile row's rank sequence per chunk of the column counts
+inline uint32_t bin_chunk(int gx) { return 256u * (uint32_t)((gx + 127) / 128); }
+// words of the (row, column, chunk) count table: at most cap / chunk + gy chunks
+inline size_t bin_tab_words(size_t cap, int gx, int gy) {
+  return (cap / bin_chunk(gx) + (size_t)gy + 1) * (size_t)gx;
+}
 constexpr int kDepthSortRounds = 4;   // the per-splat depth sort: 1024 keys per block
 constexpr int kDepthSortItems = kSortThreads * kDepthSortRounds;
 constexpr int kScanItems = 4096;      // items per block in the device-wide scan
@@ -47,11 +56,13 @@ struct SplatBufs {
   size_t rrec;          // SplatRec[N] by rank
   size_t cnt;           // u32[N] tiles covered, by rank
   size_t off;           // u32[N] exclusive prefix of cnt
-  size_t tk[2], tv[2];  // u32[cap] tile-sort ping-pong (key = tile, value = rank)
+  size_t tk[2], tv[2];  // u32[cap] each: tv[fin] the tile lists, tk[fin] the row sequence, the rest scratch
   size_t tile_start;    // u32[ntiles + 1]
   size_t scan_part;     // u32 partial sums of the device-wide scan
-  size_t look;          // tile sort's look-back region, onesweep_bytes(nb_cap, 2)
   size_t dlook;         // depth sort's look-back region, onesweep_bytes(nb_n, 4)
+  size_t row_cnt;       // u32[gy][nb_rows]: ranks per (tile row, block of kBinBlock ranks), then scanned
+  size_t bin_plan;      // u32[3 gy + 3]: row starts, chunk starts, pairs per row, capacity flag
+  size_t bin_tab;       // u32[bin_tab_words]: list entries per (row, column, chunk), then scanned per row
 };
 
 struct Workspace {
@@ -77,8 +88,8 @@ struct Workspace {
   size_t rank_flags = 0;  // u8[2N] by light rank: has an entry in a segment with an open ray; a dead unit passed
   int n = 0, width = 0, height = 0, gx = 0, gy = 0, ntiles = 0;
   size_t cap = 0;
-  int nb_n = 0;    // radix blocks over N
-  int nb_cap = 0;  // radix blocks over the capacity
+  int nb_n = 0;     // radix blocks over N
+  int nb_rows = 0;  // blocks of kBinBlock depth ranks
 };
 
 Workspace plan_workspace(int n, int width, int height, size_t cap);

@@ -1,18 +1,16 @@
-// K2-K5: binning of one splat (camera or light) into per-tile depth-ordered
-// lists; the paper bins the light view with the same splatting pipeline as
-// the camera view (Sec. 3, Sec. 4.2).
+// K2-K3: the depth sort of one splat (camera or light) and the records in
+// depth-rank order; the paper bins the light view with the same splatting
+// pipeline as the camera view (Sec. 3, Sec. 4.2).
 //
-// Order of operations (LSD radix on the composite (tile, depth) key, with the
-// depth digits sorted once per Gaussian before duplication):
 //   1. stable radix sort of the N FP32 depth keys (index payload, emitted in
-//      index order)  -> rank r, order[r]
-//   2. records gathered into rank order, tile counts per rank, exclusive scan
-//   3. one (tile, rank) pair per covered tile, written in rank order
-//   4. stable radix sort of the pairs on the tile bits only: digit totals
-//      counted once, then one pass per 8-bit digit with decoupled look-back
-//   5. per-tile [start, end) ranges
-// Within a tile the result is ascending (depth bits, index), identical to a
-// stable sort of 64-bit (tile << 32 | depth) keys emitted in index order.
+//      index order), one pass per 8-bit digit with decoupled look-back
+//      -> rank r, order[r]
+//   2. records gathered into rank order, tile counts per rank, and the counts
+//      per (tile row, block of ranks) that the binning by counting
+//      (tile_bin.cu) starts from
+// Ties in depth keep index order, so a tile's list is ascending (depth bits,
+// index), as a stable sort of 64-bit (tile << 32 | depth) keys emitted in
+// index order would give.
 #include "gs3_internal.cuh"
 
 namespace gs3 {
@@ -460,88 +458,52 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_onesweep(
 }
 
 // ---------------------------------------------------------------------------
-// Rank order, counts, emission, ranges
+// Rank order and counts
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_reorder(int n, const uint32_t* __restrict__ order,
-                                                 const SplatRec* __restrict__ rec, SplatRec* __restrict__ rrec,
-                                                 uint32_t* __restrict__ rank_of, uint32_t* __restrict__ cnt,
-                                                 const float4* __restrict__ shade, float4* __restrict__ ccol) {
+// Records into depth-rank order and the tile count of each rank.  Also
+// counts, for the block's kBinBlock ranks, the ranks whose rectangle covers
+// each tile row y (a difference array over the rows, then its running sum),
+// into row_cnt[y][block].
+__global__ void __launch_bounds__(kBinBlock) k_reorder(int n, const uint32_t* __restrict__ order,
+                                                       const SplatRec* __restrict__ rec, SplatRec* __restrict__ rrec,
+                                                       uint32_t* __restrict__ rank_of, uint32_t* __restrict__ cnt,
+                                                       const float4* __restrict__ shade, float4* __restrict__ ccol,
+                                                       uint32_t* __restrict__ row_cnt, int gy) {
+  __shared__ int d[kMaxTileAxis + 1];
+  for (int y = threadIdx.x; y <= gy; y += blockDim.x) d[y] = 0;
+  __syncthreads();
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= n) return;
-  const uint32_t g = order[r];
-  if (g >= (uint32_t)n) return;
-  const SplatRec q = rec[g];
-  rrec[r] = q;
-  rank_of[g] = r;
-  cnt[r] = q.r.x >= 0 ? (uint32_t)(q.r.z - q.r.x + 1) * (uint32_t)(q.r.w - q.r.y + 1) : 0u;
-  if (ccol) {
-    float4 c = shade[g];
-    ccol[2 * r] = make_float4(c.x, c.y, c.z, 0.f);
-  }
-}
-
-// One warp per kEmitRanks consecutive depth ranks: lanes 0..kEmitRanks-1 load
-// the ranks' rectangles and offsets at once; then for each rank the lanes
-// write its (tile, rank) pairs, its rectangle's tiles in row-major order, at
-// off[r] + i.  The row of pair i is floor((i + 0.5) / w) by an FP32
-// reciprocal, then moved by one where rounding left it off, so it is exact.
-constexpr int kEmitRanks = 8;
-
-__global__ void __launch_bounds__(256) k_emit(int n, uint32_t cap, const SplatRec* __restrict__ rrec,
-                                              const uint32_t* __restrict__ off, uint32_t* header, int h_need,
-                                              int h_pairs, uint32_t* __restrict__ tk, uint32_t* __restrict__ tv,
-                                              int gx) {
-  const uint32_t need = header[h_need];
-  if (need > cap) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-      header[h_pairs] = 0;
-      atomicCAS(&header[H_STATUS], 0u, (uint32_t)GS3_ERR_CAPACITY);
+  const uint32_t g = r < n ? order[r] : 0xFFFFFFFFu;
+  if (g < (uint32_t)n) {
+    const SplatRec q = rec[g];
+    rrec[r] = q;
+    rank_of[g] = r;
+    const bool in = q.r.x >= 0;
+    cnt[r] = in ? (uint32_t)(q.r.z - q.r.x + 1) * (uint32_t)(q.r.w - q.r.y + 1) : 0u;
+    if (in) {
+      atomicAdd(&d[q.r.y], 1);
+      atomicAdd(&d[q.r.w + 1], -1);
     }
-    return;
+    if (ccol) {
+      float4 c = shade[g];
+      ccol[2 * r] = make_float4(c.x, c.y, c.z, 0.f);
+    }
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) header[h_pairs] = need;
-  const int r0 = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * kEmitRanks, lane = threadIdx.x & 31;
-  if (r0 >= n) return;
-  int4 q = make_int4(-1, 0, -1, 0);  // past n: no pairs
-  uint32_t base = 0;
-  if (lane < kEmitRanks && r0 + lane < n) {
-    q = rrec[r0 + lane].r;
-    base = off[r0 + lane];
-  }
-#pragma unroll 1
-  for (int j = 0; j < kEmitRanks; ++j) {
-    const int qx = __shfl_sync(0xffffffffu, q.x, j), qy = __shfl_sync(0xffffffffu, q.y, j);
-    const int qz = __shfl_sync(0xffffffffu, q.z, j), qw = __shfl_sync(0xffffffffu, q.w, j);
-    const uint32_t b = __shfl_sync(0xffffffffu, base, j);
-    if (qx < 0) continue;  // culled: no pairs
-    const int w = qz - qx + 1;
-    const uint32_t cnt = (uint32_t)w * (uint32_t)(qw - qy + 1);
-    const float inv = 1.f / (float)w;
-    const uint32_t r = (uint32_t)(r0 + j);
-    for (uint32_t i = lane; i < cnt; i += 32) {
-      int row = (int)(((float)i + 0.5f) * inv);
-      int col = (int)i - row * w;
-      if (col < 0) {
-        --row;
-        col += w;
-      } else if (col >= w) {
-        ++row;
-        col -= w;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    int run = 0;
+    for (int y0 = 0; y0 < gy; y0 += 32) {
+      const int y = y0 + lane;
+      int v = y < gy ? d[y] : 0;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
       }
-      tk[b + i] = (uint32_t)((qy + row) * gx + qx + col);
-      tv[b + i] = r;
+      if (y < gy) row_cnt[(size_t)y * gridDim.x + blockIdx.x] = (uint32_t)(run + v);
+      run += __shfl_sync(0xffffffffu, v, 31);
     }
-  }
-}
-
-__global__ void __launch_bounds__(256) k_ranges(const uint32_t* __restrict__ keys, const uint32_t* header,
-                                                int h_pairs, uint32_t* __restrict__ start, int ntiles,
-                                                uint32_t limit) {
-  const uint32_t P = header[h_pairs];
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i <= P && i <= limit; i += gridDim.x * blockDim.x) {
-    const int prev = i == 0 ? -1 : (int)keys[i - 1];
-    const int cur = i == P ? ntiles : (int)keys[i];
-    for (int t = prev + 1; t <= cur && t <= ntiles; ++t) start[t] = i;
   }
 }
 
@@ -627,8 +589,6 @@ void device_exclusive_scan(const uint32_t* in, uint32_t* out, uint32_t n, uint32
   count_launch(3);
 }
 
-int tile_sort_passes(int ntiles) { return ntiles <= 256 ? 1 : 2; }
-
 void launch_depth_sort(const FrameArgs& f, int sp, cudaStream_t s) {
   const SplatBufs& b = f.L->sp[sp];
   unsigned char* ws = f.ws;
@@ -640,39 +600,10 @@ void launch_depth_sort(const FrameArgs& f, int sp, cudaStream_t s) {
                                      nullptr, (uint32_t)n, f.L->nb_n, 4, at<unsigned char>(ws, b.dlook),
                                      at<uint32_t>(ws, f.L->header), s);
   // 4 passes end in buffer 1: sv[1] holds the index of each depth rank
-  k_reorder<<<(n + 255) / 256, 256, 0, s>>>(
+  k_reorder<<<f.L->nb_rows, kBinBlock, 0, s>>>(
       n, at<uint32_t>(ws, b.sv[1]), at<SplatRec>(ws, b.rec), at<SplatRec>(ws, b.rrec),
       at<uint32_t>(ws, b.rank_of), at<uint32_t>(ws, b.cnt), at<float4>(ws, f.L->shade),
-      sp == 0 ? at<float4>(ws, f.L->ccol) : nullptr);
-  count_launch();
-}
-
-void launch_binning(const FrameArgs& f, int sp, cudaStream_t s) {
-  const SplatBufs& b = f.L->sp[sp];
-  unsigned char* ws = f.ws;
-  const int n = f.sc.n;
-  uint32_t* header = at<uint32_t>(ws, f.L->header);
-  const int h_need = sp ? H_NEED_LIGHT : H_NEED_CAM;
-  const int h_pairs = sp ? H_PAIRS_LIGHT : H_PAIRS_CAM;
-  device_exclusive_scan(at<uint32_t>(ws, b.cnt), at<uint32_t>(ws, b.off), (uint32_t)n, header + h_need,
-                        at<uint32_t>(ws, b.scan_part), s);
-  const size_t emit_warps = ((size_t)n + kEmitRanks - 1) / kEmitRanks;
-  k_emit<<<(int)((emit_warps * 32 + 255) / 256), 256, 0, s>>>(n, (uint32_t)f.L->cap, at<SplatRec>(ws, b.rrec),
-                                                              at<uint32_t>(ws, b.off), header, h_need, h_pairs,
-                                                              at<uint32_t>(ws, b.tk[0]), at<uint32_t>(ws, b.tv[0]),
-                                                              f.L->gx);
-  count_launch();
-  const int passes = tile_sort_passes(f.L->ntiles);
-  // sort (tile, rank) pairs on the tile bits; start from buffer 0, alternate
-  onesweep_sort<kTileSortRounds, 2>(at<uint32_t>(ws, b.tk[0]), at<uint32_t>(ws, b.tv[0]), at<uint32_t>(ws, b.tk[1]),
-                                at<uint32_t>(ws, b.tv[1]), at<uint32_t>(ws, b.tk[0]), at<uint32_t>(ws, b.tv[0]),
-                                header + h_pairs, 0, f.L->nb_cap, passes, at<unsigned char>(ws, b.look), header, s);
-  const int fin = passes & 1;  // 1 pass ends in buffer 1, 2 passes in buffer 0
-  const uint32_t* keys = at<uint32_t>(ws, b.tk[fin]);
-  int blocks = (int)((f.L->cap + 1 + 255) / 256);
-  if (blocks > device_sm_count() * 16) blocks = device_sm_count() * 16;
-  k_ranges<<<blocks, 256, 0, s>>>(keys, header, h_pairs, at<uint32_t>(ws, b.tile_start), f.L->ntiles,
-                                  (uint32_t)f.L->cap);
+      sp == 0 ? at<float4>(ws, f.L->ccol) : nullptr, at<uint32_t>(ws, b.row_cnt), f.L->gy);
   count_launch();
 }
 
