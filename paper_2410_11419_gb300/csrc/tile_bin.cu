@@ -6,21 +6,24 @@
 // A rank's (tile, rank) pairs are the tiles of its rectangle, so the lists
 // are built from the rectangles by two stable counting passes instead of
 // emitting the pairs and sorting them on the tile bits:
-//   rows     the ranks covering tile row y, for every y, in rank order: the
-//            counts per (row, block of kBinBlock ranks) come from k_reorder;
-//            k_bin_plan scans them (row-major), k_bin_rows places the ranks;
-//   columns  each row's rank sequence is cut into chunks of bin_chunk(gx)
-//            items; k_bin_count counts the items per (row, column, chunk);
+//   rows     the ranks covering tile row y, for every y, in rank order, with
+//            each rank's column span beside it: the counts per (row, block
+//            of kBinBlock ranks) come from k_reorder; k_bin_rowtot scans each
+//            row's counts, k_bin_plan the row totals; k_bin_rows places;
+//   columns  each row's sequence is cut into chunks of bin_chunk(gx) items;
+//            k_bin_count counts the items per (row, column, chunk);
 //            k_bin_rowscan scans each row's counts in (column, chunk) order,
 //            after the pairs of the rows above, which gives every tile's
 //            start and every chunk's offset in each of its tiles; k_bin_place
 //            writes the list entries.
-// Inside a block of 256 items the position of an item among the items
-// covering the same row (or column) is the count of earlier warps plus the
-// popcount of the lower lanes in a ballot, each warp sweeping the union of
-// its lanes' spans once.  Every list is therefore in rank order, the result
-// a stable sort of the pairs by tile would give, and no step depends on
-// timing or waits on another block.
+// Both placements take 256 items at a time, one per thread, in order.  A
+// warp's offset in bucket x is the bucket's running offset plus the items of
+// earlier warps covering x (per-warp difference arrays); inside a warp the
+// (item, bucket) pairs are dealt 32 per round in item order, and a pair's
+// rank among the round's pairs of the same bucket (match_any) is added to a
+// per-bucket counter.  Every list is therefore in rank order, the result a
+// stable sort of the pairs by tile would give, and no step depends on timing
+// or waits on another block.
 #include <climits>
 
 #include "gs3_internal.cuh"
@@ -30,6 +33,15 @@ namespace {
 
 constexpr int kBinThreads = 256;  // 8 warps
 constexpr int kBinWarps = kBinThreads / 32;
+
+__device__ __forceinline__ uint32_t warp_inclusive_sum(uint32_t v, int lane) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t u = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += u;
+  }
+  return v;
+}
 
 // Exclusive scan of v[0, len) in place, starting at carry, by one block of
 // NT threads (four consecutive words per thread per step); returns carry plus
@@ -46,21 +58,11 @@ __device__ uint32_t block_scan_inplace(uint32_t* v, size_t len, uint32_t carry, 
       x[j] = i < len ? v[i] : 0u;
       s += x[j];
     }
-    uint32_t inc = s;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t u = __shfl_up_sync(0xffffffffu, inc, o);
-      if (lane >= o) inc += u;
-    }
+    const uint32_t inc = warp_inclusive_sum(s, lane);
     if (lane == 31) sm[w] = inc;
     __syncthreads();
     if (w == 0) {
-      uint32_t u = lane < kWarps ? sm[lane] : 0u;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t z = __shfl_up_sync(0xffffffffu, u, o);
-        if (lane >= o) u += z;
-      }
+      const uint32_t u = warp_inclusive_sum(lane < kWarps ? sm[lane] : 0u, lane);
       if (lane < kWarps) sm[lane] = u;
     }
     __syncthreads();
@@ -77,7 +79,8 @@ __device__ uint32_t block_scan_inplace(uint32_t* v, size_t len, uint32_t carry, 
   return carry;
 }
 
-// the sum of every thread's x over a block of kBinThreads (all threads get it)
+// the sum of every thread's x over a block of NT threads (all threads get it)
+template <int NT>
 __device__ uint32_t block_sum(uint32_t x, uint32_t* sm) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
@@ -85,7 +88,7 @@ __device__ uint32_t block_sum(uint32_t x, uint32_t* sm) {
   __syncthreads();
   uint32_t s = 0;
 #pragma unroll
-  for (int k = 0; k < kBinWarps; ++k) s += sm[k];
+  for (int k = 0; k < NT / 32; ++k) s += sm[k];
   __syncthreads();
   return s;
 }
@@ -108,47 +111,129 @@ __device__ __forceinline__ int chunk_row(const uint32_t* cb, int gy, uint32_t kg
   return lo;
 }
 
-// One block of 1024 threads: scans the row counts (row-major, so that the
-// counts of row y start at the row's place in the row sequence), cuts every
-// row into chunks, and checks that the pairs fit the capacity.
-__global__ void __launch_bounds__(1024) k_bin_plan(uint32_t* __restrict__ row_cnt, int nb, int gy, uint32_t ch,
-                                                  size_t tab_words, int gx, uint32_t* __restrict__ plan,
-                                                  uint32_t* header, int h_need, int h_pairs, size_t cap) {
+// Shared memory of a span placement (about 41 KB).
+struct SpanSmem {
+  int cnt[kBinWarps][kMaxTileAxis + 1];  // per warp: difference array, counts, then offsets per bucket
+  uint32_t run[kMaxTileAxis];            // per bucket: the running offset
+  uint32_t ex[kBinWarps][32];            // per warp: exclusive prefix of the lanes' span widths
+  int lo[kBinWarps][32];                 // per warp: the lanes' first buckets
+  uint32_t v0[kBinWarps][32], v1[kBinWarps][32];  // per warp: the lanes' payloads
+};
+
+// Stable placement of 256 items, one per thread in thread order: an item with
+// a <= b covers buckets a..b, and its copy for bucket x goes to
+// out0 / out1[S.run[x] + the items of lower threads covering x].  S.run must
+// hold the buckets' offsets and is advanced past the items.  Every thread of
+// the block calls it.
+__device__ void place_spans(SpanSmem& S, int nbk, int a, int b, uint32_t v0, uint32_t v1,
+                            uint32_t* __restrict__ out0, uint32_t* __restrict__ out1, size_t cap) {
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int* c = S.cnt[w];
+  for (int x = lane; x <= nbk; x += 32) c[x] = 0;
+  __syncwarp();
+  const bool has = a <= b;
+  if (has) {
+    atomicAdd(&c[a], 1);
+    atomicAdd(&c[b + 1], -1);
+  }
+  __syncwarp();
+  uint32_t carry = 0;  // the warp's items per bucket: running sum of the difference array
+  for (int x0 = 0; x0 < nbk; x0 += 32) {
+    const int x = x0 + lane;
+    const uint32_t v = warp_inclusive_sum(x < nbk ? (uint32_t)c[x] : 0u, lane);
+    if (x < nbk) c[x] = (int)(carry + v);
+    carry += __shfl_sync(0xffffffffu, v, 31);
+  }
+  __syncthreads();
+  for (int x = threadIdx.x; x < nbk; x += kBinThreads) {  // warp k starts after warps 0..k-1
+    uint32_t base = S.run[x];
+#pragma unroll
+    for (int k = 0; k < kBinWarps; ++k) {
+      const uint32_t n = (uint32_t)S.cnt[k][x];
+      S.cnt[k][x] = (int)base;
+      base += n;
+    }
+    S.run[x] = base;
+  }
+  __syncthreads();
+  // the warp's (item, bucket) pairs in item order, 32 per round
+  const uint32_t wid = has ? (uint32_t)(b - a + 1) : 0u;
+  const uint32_t inc = warp_inclusive_sum(wid, lane);
+  const uint32_t total = __shfl_sync(0xffffffffu, inc, 31);
+  S.ex[w][lane] = inc - wid;
+  S.lo[w][lane] = a;
+  S.v0[w][lane] = v0;
+  S.v1[w][lane] = v1;
+  __syncwarp();
+  const uint32_t lt = (1u << lane) - 1u;
+  for (uint32_t p0 = 0; p0 < total; p0 += 32) {
+    const uint32_t p = p0 + lane;
+    const bool act = p < total;
+    int j = 0;  // the item of pair p: the last lane j with ex[j] <= p
+#pragma unroll
+    for (int s = 16; s > 0; s >>= 1)
+      if (S.ex[w][j + s] <= p) j += s;
+    const int x = S.lo[w][j] + (int)(p - S.ex[w][j]);
+    const uint32_t m = __match_any_sync(0xffffffffu, act ? x : -1 - lane);
+    if (act) {
+      const uint32_t pos = (uint32_t)c[x] + (uint32_t)__popc(m & lt);
+      if (pos < cap) {
+        out0[pos] = S.v0[w][j];
+        if (out1) out1[pos] = S.v1[w][j];
+      }
+    }
+    __syncwarp();  // every lane has read its bucket's counter
+    if (act && (m >> lane) == 1u) c[x] += __popc(m);
+    __syncwarp();
+  }
+  __syncthreads();  // S is rewritten by the next call
+}
+
+// Each row's block counts scanned in place (exclusive, within the row); the
+// row's total goes to rs[y] for k_bin_plan.
+__global__ void __launch_bounds__(kBinThreads) k_bin_rowtot(uint32_t* __restrict__ row_cnt, int nb, int gy,
+                                                            uint32_t* __restrict__ plan) {
   __shared__ uint32_t sm[32];
-  const uint32_t M = block_scan_inplace<1024>(row_cnt, (size_t)gy * nb, 0u, sm);
+  const int y = blockIdx.x;
+  const uint32_t t = block_scan_inplace<kBinThreads>(row_cnt + (size_t)y * nb, (size_t)nb, 0u, sm);
+  if (threadIdx.x == 0) plan[y] = t;
+}
+
+// One block of 1024 threads (gy <= 1024, one row per thread): row starts from
+// the row totals, chunks per row and their starts, and the capacity check.
+__global__ void __launch_bounds__(1024) k_bin_plan(int gy, uint32_t ch, size_t tab_words, int gx,
+                                                  uint32_t* __restrict__ plan, uint32_t* header, int h_need,
+                                                  int h_pairs, size_t cap) {
+  __shared__ uint32_t sm[32];
   BinPlan P(plan, gy);
   const int y = threadIdx.x, lane = y & 31, w = y >> 5;
-  uint32_t nch = 0;
+  const uint32_t m = y < gy ? P.rs[y] : 0u;  // the row's total
+  const uint32_t c = (uint32_t)(((uint64_t)m + ch - 1) / ch);
+  const uint32_t nch = y < gy ? (c > 1u ? c : 1u) : 0u;
+  // exclusive prefixes of (m, nch) over the rows
+  const uint32_t im = warp_inclusive_sum(m, lane), ic = warp_inclusive_sum(nch, lane);
+  if (lane == 31) sm[w] = im;
+  __syncthreads();
+  const uint32_t wm = w == 0 ? warp_inclusive_sum(sm[lane], lane) : 0u;
+  __syncthreads();
+  if (w == 0) sm[lane] = wm;
+  __syncthreads();
+  const uint32_t rs = (w ? sm[w - 1] : 0u) + im - m, M = sm[31];
+  __syncthreads();
+  if (lane == 31) sm[w] = ic;
+  __syncthreads();
+  const uint32_t wc = w == 0 ? warp_inclusive_sum(sm[lane], lane) : 0u;
+  __syncthreads();
+  if (w == 0) sm[lane] = wc;
+  __syncthreads();
+  const uint32_t cb = (w ? sm[w - 1] : 0u) + ic - nch, C = sm[31];
   if (y < gy) {
-    const uint32_t a = row_cnt[(size_t)y * nb];
-    const uint32_t e = y + 1 < gy ? row_cnt[(size_t)(y + 1) * nb] : M;
-    P.rs[y] = a;
+    P.rs[y] = rs;
+    P.cb[y] = cb;
     P.pairs[y] = 0u;
-    const uint32_t c = (uint32_t)(((uint64_t)(e - a) + ch - 1) / ch);
-    nch = c > 1u ? c : 1u;
   }
-  if (y == 0) P.rs[gy] = M;
-  uint32_t inc = nch;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const uint32_t u = __shfl_up_sync(0xffffffffu, inc, o);
-    if (lane >= o) inc += u;
-  }
-  if (lane == 31) sm[w] = inc;
-  __syncthreads();
-  if (w == 0) {
-    uint32_t u = sm[lane];
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t z = __shfl_up_sync(0xffffffffu, u, o);
-      if (lane >= o) u += z;
-    }
-    sm[lane] = u;
-  }
-  __syncthreads();
-  if (y < gy) P.cb[y] = (w ? sm[w - 1] : 0u) + inc - nch;
   if (y == 0) {
-    const uint32_t C = sm[31];
+    P.rs[gy] = M;
     P.cb[gy] = C;
     const uint32_t need = header[h_need];
     const bool ok = need <= cap && (size_t)C * (size_t)gx <= tab_words;
@@ -158,64 +243,37 @@ __global__ void __launch_bounds__(1024) k_bin_plan(uint32_t* __restrict__ row_cn
   }
 }
 
-// The row sequence: rank r goes to every row of its rectangle, at the row's
-// offset for r's block, plus the ranks of earlier warps and lower lanes of
-// the block covering that row.
+// The row sequence: the block's 256 ranks over their rows, each copy with the
+// rank's column span (x0 | x1 << 16) beside it; row y's offset for this block
+// is the row's start plus the row's counts of the blocks before.
 __global__ void __launch_bounds__(kBinThreads) k_bin_rows(int n, const SplatRec* __restrict__ rrec,
                                                           const uint32_t* __restrict__ row_cnt, int nb, int gy,
                                                           const uint32_t* __restrict__ plan,
-                                                          uint32_t* __restrict__ rowseq, size_t cap) {
-  __shared__ uint32_t wc[kBinWarps][kMaxTileAxis];
-  __shared__ int wlo[kBinWarps], whi[kBinWarps];
+                                                          uint32_t* __restrict__ rowseq, uint32_t* __restrict__ rowspan,
+                                                          size_t cap) {
+  __shared__ SpanSmem S;
   if (plan[3 * gy + 2] == 0u) return;
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int y = threadIdx.x; y < gy; y += kBinThreads) S.run[y] = plan[y] + row_cnt[(size_t)y * nb + blockIdx.x];
   const int r = blockIdx.x * kBinThreads + threadIdx.x;
-  int a = 0, b = -1;  // the rank's rows
+  int a = 0, b = -1;
+  uint32_t span = 0;
   if (r < n) {
     const int4 q = rrec[r].r;
     if (q.x >= 0) {
       a = q.y;
       b = q.w;
-    }
-  }
-  const int lo = __reduce_min_sync(0xffffffffu, a <= b ? a : INT_MAX);
-  const int hi = __reduce_max_sync(0xffffffffu, a <= b ? b : -1);
-  for (int y = lo; y <= hi; ++y) {
-    const uint32_t m = __ballot_sync(0xffffffffu, a <= y && y <= b);
-    if (lane == 0) wc[w][y] = (uint32_t)__popc(m);
-  }
-  if (lane == 0) {
-    wlo[w] = lo;
-    whi[w] = hi;
-  }
-  __syncthreads();
-  for (int y = threadIdx.x; y < gy; y += kBinThreads) {
-    uint32_t run = row_cnt[(size_t)y * nb + blockIdx.x];
-#pragma unroll
-    for (int k = 0; k < kBinWarps; ++k) {
-      const uint32_t c = (y >= wlo[k] && y <= whi[k]) ? wc[k][y] : 0u;
-      wc[k][y] = run;
-      run += c;
+      span = (uint32_t)q.x | ((uint32_t)q.z << 16);
     }
   }
   __syncthreads();
-  const uint32_t lt = (1u << lane) - 1u;
-  for (int y = lo; y <= hi; ++y) {
-    const bool cov = a <= y && y <= b;
-    const uint32_t m = __ballot_sync(0xffffffffu, cov);
-    if (cov) {
-      const uint32_t pos = wc[w][y] + (uint32_t)__popc(m & lt);
-      if (pos < cap) rowseq[pos] = (uint32_t)r;
-    }
-  }
+  place_spans(S, gy, a, b, (uint32_t)r, span, rowseq, rowspan, cap);
 }
 
 // Counts per (row, column, chunk): a difference array over the columns of
-// the chunk's rectangles, then its running sum, at tab[cb[y] gx + x nch + k]
+// the chunk's spans, then its running sum, at tab[cb[y] gx + x nch + k]
 // (row y's counts in (column, chunk) order); adds the chunk's list entries
 // to the row's pairs.
-__global__ void __launch_bounds__(kBinThreads) k_bin_count(const SplatRec* __restrict__ rrec,
-                                                           const uint32_t* __restrict__ rowseq,
+__global__ void __launch_bounds__(kBinThreads) k_bin_count(const uint32_t* __restrict__ rowspan,
                                                            uint32_t* __restrict__ plan, int gx, int gy, uint32_t ch,
                                                            uint32_t* __restrict__ tab) {
   __shared__ int d[kMaxTileAxis + 1];
@@ -231,26 +289,22 @@ __global__ void __launch_bounds__(kBinThreads) k_bin_count(const SplatRec* __res
     __syncthreads();
     uint32_t width = 0;
     for (uint32_t i = i0 + threadIdx.x; i < i1; i += kBinThreads) {
-      const int4 q = rrec[rowseq[i]].r;
-      atomicAdd(&d[q.x], 1);
-      atomicAdd(&d[q.z + 1], -1);
-      width += (uint32_t)(q.z - q.x + 1);
+      const uint32_t sp = rowspan[i];
+      const int x0 = (int)(sp & 0xFFFFu), x1 = (int)(sp >> 16);
+      atomicAdd(&d[x0], 1);
+      atomicAdd(&d[x1 + 1], -1);
+      width += (uint32_t)(x1 - x0 + 1);
     }
-    const uint32_t total = block_sum(width, sm);  // also orders the difference array's updates
+    const uint32_t total = block_sum<kBinThreads>(width, sm);  // also orders the difference array's updates
     if (threadIdx.x == 0 && total) atomicAdd(P.pairs + y, total);
     if (threadIdx.x < 32) {
       const int lane = threadIdx.x;
       uint32_t* out = tab + (size_t)c0 * gx + k;
-      int run = 0;
+      uint32_t run = 0;
       for (int x0 = 0; x0 < gx; x0 += 32) {
         const int x = x0 + lane;
-        int v = x < gx ? d[x] : 0;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const int t = __shfl_up_sync(0xffffffffu, v, o);
-          if (lane >= o) v += t;
-        }
-        if (x < gx) out[(size_t)x * nch] = (uint32_t)(run + v);
+        const uint32_t v = warp_inclusive_sum(x < gx ? (uint32_t)d[x] : 0u, lane);
+        if (x < gx) out[(size_t)x * nch] = run + v;
         run += __shfl_sync(0xffffffffu, v, 31);
       }
     }
@@ -261,95 +315,59 @@ __global__ void __launch_bounds__(kBinThreads) k_bin_count(const SplatRec* __res
 // One block per row: the row's counts scanned in (column, chunk) order after
 // the list entries of the rows above; tile (y, x) starts at the scanned count
 // of its first chunk.  The last row also writes the end of the last tile.
-__global__ void __launch_bounds__(kBinThreads) k_bin_rowscan(uint32_t* __restrict__ tab,
-                                                             const uint32_t* __restrict__ plan, int gx, int gy,
-                                                             uint32_t* __restrict__ tile_start) {
+__global__ void __launch_bounds__(1024) k_bin_rowscan(uint32_t* __restrict__ tab, const uint32_t* __restrict__ plan,
+                                                      int gx, int gy, uint32_t* __restrict__ tile_start) {
   __shared__ uint32_t sm[32];
   const int y = blockIdx.x;
   const uint32_t* cb = plan + gy + 1;
   const uint32_t* pairs = plan + 2 * gy + 2;
   uint32_t* ts = tile_start + (size_t)y * gx;
   if (plan[3 * gy + 2] == 0u) {  // over capacity: every list empty
-    for (int x = threadIdx.x; x < gx; x += kBinThreads) ts[x] = 0u;
+    for (int x = threadIdx.x; x < gx; x += blockDim.x) ts[x] = 0u;
     if (y == gy - 1 && threadIdx.x == 0) tile_start[(size_t)gx * gy] = 0u;
     return;
   }
   uint32_t above = 0;
-  for (int t = threadIdx.x; t < y; t += kBinThreads) above += pairs[t];
-  above = block_sum(above, sm);
+  for (int t = threadIdx.x; t < y; t += blockDim.x) above += pairs[t];
+  above = block_sum<1024>(above, sm);
   const uint32_t c0 = cb[y], nch = cb[y + 1] - c0;
   uint32_t* seg = tab + (size_t)c0 * gx;
-  const uint32_t end = block_scan_inplace<kBinThreads>(seg, (size_t)nch * gx, above, sm);
-  for (int x = threadIdx.x; x < gx; x += kBinThreads) ts[x] = seg[(size_t)x * nch];
+  const uint32_t end = block_scan_inplace<1024>(seg, (size_t)nch * gx, above, sm);
+  for (int x = threadIdx.x; x < gx; x += blockDim.x) ts[x] = seg[(size_t)x * nch];
   if (y == gy - 1 && threadIdx.x == 0) tile_start[(size_t)gx * gy] = end;
 }
 
-// The list entries: each chunk in sub-chunks of 256 items; column x of a
-// sub-chunk's warp k starts at the chunk's running offset in tile (y, x)
-// plus the items of warps 0..k-1 covering x, and an item at the popcount of
-// the lower lanes covering x.
-__global__ void __launch_bounds__(kBinThreads) k_bin_place(const SplatRec* __restrict__ rrec,
-                                                           const uint32_t* __restrict__ rowseq,
+// The list entries: each chunk in steps of 256 items over their columns,
+// starting at the chunk's offsets in its tiles.
+__global__ void __launch_bounds__(kBinThreads) k_bin_place(const uint32_t* __restrict__ rowseq,
+                                                           const uint32_t* __restrict__ rowspan,
                                                            const uint32_t* __restrict__ plan,
                                                            const uint32_t* __restrict__ tab, int gx, int gy,
                                                            uint32_t ch, uint32_t* __restrict__ list, size_t cap) {
-  __shared__ uint32_t wc[kBinWarps][kMaxTileAxis];
-  __shared__ uint32_t run[kMaxTileAxis];
-  __shared__ int wlo[kBinWarps], whi[kBinWarps];
+  __shared__ SpanSmem S;
   const uint32_t* rs = plan;
   const uint32_t* cb = plan + gy + 1;
   if (plan[3 * gy + 2] == 0u) return;
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const uint32_t lt = (1u << lane) - 1u;
   const uint32_t C = cb[gy];
   for (uint32_t kg = blockIdx.x; kg < C; kg += gridDim.x) {
     const int y = chunk_row(cb, gy, kg);
     const uint32_t c0 = cb[y], nch = cb[y + 1] - c0, k = kg - c0;
     const uint32_t i0 = rs[y] + k * ch, i1 = min(rs[y + 1], i0 + ch);
-    // each thread reads back only the columns it wrote
-    for (int x = threadIdx.x; x < gx; x += kBinThreads) run[x] = tab[(size_t)c0 * gx + (size_t)x * nch + k];
+    for (int x = threadIdx.x; x < gx; x += kBinThreads) S.run[x] = tab[(size_t)c0 * gx + (size_t)x * nch + k];
+    __syncthreads();
     for (uint32_t sub = i0; sub < i1; sub += kBinThreads) {
       const uint32_t i = sub + threadIdx.x;
-      int a = 0, b = -1;  // the item's columns
+      int a = 0, b = -1;
       uint32_t r = 0;
       if (i < i1) {
         r = rowseq[i];
-        const int4 q = rrec[r].r;
-        a = q.x;
-        b = q.z;
+        const uint32_t sp = rowspan[i];
+        a = (int)(sp & 0xFFFFu);
+        b = (int)(sp >> 16);
       }
-      const int lo = __reduce_min_sync(0xffffffffu, a <= b ? a : INT_MAX);
-      const int hi = __reduce_max_sync(0xffffffffu, a <= b ? b : -1);
-      for (int x = lo; x <= hi; ++x) {
-        const uint32_t m = __ballot_sync(0xffffffffu, a <= x && x <= b);
-        if (lane == 0) wc[w][x] = (uint32_t)__popc(m);
-      }
-      if (lane == 0) {
-        wlo[w] = lo;
-        whi[w] = hi;
-      }
-      __syncthreads();
-      for (int x = threadIdx.x; x < gx; x += kBinThreads) {
-        uint32_t base = run[x];
-#pragma unroll
-        for (int kk = 0; kk < kBinWarps; ++kk) {
-          const uint32_t c = (x >= wlo[kk] && x <= whi[kk]) ? wc[kk][x] : 0u;
-          wc[kk][x] = base;
-          base += c;
-        }
-        run[x] = base;
-      }
-      __syncthreads();
-      for (int x = lo; x <= hi; ++x) {
-        const bool cov = a <= x && x <= b;
-        const uint32_t m = __ballot_sync(0xffffffffu, cov);
-        if (cov) {
-          const uint32_t pos = wc[w][x] + (uint32_t)__popc(m & lt);
-          if (pos < cap) list[pos] = r;
-        }
-      }
-      __syncthreads();  // wc, wlo and whi are rewritten by the next sub-chunk
+      place_spans(S, gx, a, b, r, 0u, list, nullptr, cap);
     }
+    __syncthreads();  // S.run is rewritten for the next chunk
   }
 }
 
@@ -367,25 +385,26 @@ void launch_binning(const FrameArgs& f, int sp, cudaStream_t s) {
   // every rank's first list slot in rank order (the shadow partials' slots) and the total
   device_exclusive_scan(at<uint32_t>(ws, b.cnt), at<uint32_t>(ws, b.off), (uint32_t)n, header + h_need,
                         at<uint32_t>(ws, b.scan_part), s);
-  // the lists go where the composites and the backward read them
+  // the lists go where the composites and the backward read them; the row
+  // sequence and spans use buffers that are free until the shadow composite
   const int fin = (f.L->ntiles <= 256 ? 1 : 2) & 1;
-  uint32_t* rowseq = at<uint32_t>(ws, b.tk[fin]);
   uint32_t* list = at<uint32_t>(ws, b.tv[fin]);
+  uint32_t* rowseq = at<uint32_t>(ws, b.tk[fin]);
+  uint32_t* rowspan = at<uint32_t>(ws, b.tk[1 - fin]);
   uint32_t* row_cnt = at<uint32_t>(ws, b.row_cnt);
   uint32_t* plan = at<uint32_t>(ws, b.bin_plan);
   uint32_t* tab = at<uint32_t>(ws, b.bin_tab);
-  const SplatRec* rrec = at<SplatRec>(ws, b.rrec);
   const uint32_t ch = bin_chunk(gx);
-  k_bin_plan<<<1, 1024, 0, s>>>(row_cnt, nb, gy, ch, bin_tab_words(cap, gx, gy), gx, plan, header, h_need, h_pairs,
-                                cap);
-  k_bin_rows<<<nb, kBinThreads, 0, s>>>(n, rrec, row_cnt, nb, gy, plan, rowseq, cap);
+  k_bin_rowtot<<<gy, kBinThreads, 0, s>>>(row_cnt, nb, gy, plan);
+  k_bin_plan<<<1, 1024, 0, s>>>(gy, ch, bin_tab_words(cap, gx, gy), gx, plan, header, h_need, h_pairs, cap);
+  k_bin_rows<<<nb, kBinThreads, 0, s>>>(n, at<SplatRec>(ws, b.rrec), row_cnt, nb, gy, plan, rowseq, rowspan, cap);
   const size_t chunks = cap / ch + (size_t)gy + 1;
-  int grid = device_sm_count() * 6;
+  int grid = device_sm_count() * 5;
   if ((size_t)grid > chunks) grid = (int)chunks;
-  k_bin_count<<<grid, kBinThreads, 0, s>>>(rrec, rowseq, plan, gx, gy, ch, tab);
-  k_bin_rowscan<<<gy, kBinThreads, 0, s>>>(tab, plan, gx, gy, at<uint32_t>(ws, b.tile_start));
-  k_bin_place<<<grid, kBinThreads, 0, s>>>(rrec, rowseq, plan, tab, gx, gy, ch, list, cap);
-  count_launch(5);
+  k_bin_count<<<grid, kBinThreads, 0, s>>>(rowspan, plan, gx, gy, ch, tab);
+  k_bin_rowscan<<<gy, 1024, 0, s>>>(tab, plan, gx, gy, at<uint32_t>(ws, b.tile_start));
+  k_bin_place<<<grid, kBinThreads, 0, s>>>(rowseq, rowspan, plan, tab, gx, gy, ch, list, cap);
+  count_launch(6);
 }
 
 }  // namespace gs3
