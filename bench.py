@@ -39,7 +39,7 @@ sys.path.insert(0, ROOT)
 # one ncu capture of the kernel, valid only while its sources are unchanged:
 # kernel -> (bytes, SHA-256 of the concatenated sources, the summary file).
 PROFILED_TRAFFIC = {
-    "k_shadow": (552.4e6, "e983e324fb65304b4adcc37165fc4ac888a25b569714887f87725af1c7be6fd1",
+    "k_shadow": (483.0e6, "554efd2e55a5587be4b0fa92ca88152f9c75daadb6035ca817332d132e3ced08",
                  "profiles/k_shadow_object_300k_800.md"),
 }
 TRAFFIC_SOURCES = {
