@@ -18,7 +18,8 @@ namespace {
 // alpha test, T_m(j) = prod (1 - alpha_k,m) over passing k with
 // d_k < d_j - bias.  The list is ordered by distance, so the occluders of j
 // form a prefix of the tile's list; its end K(j) is precomputed per entry
-// (k_occluder_bound) and is non-decreasing in j.
+// (k_bound_starts, k_bound_rest, from the distances the binning writes beside
+// the list) and is non-decreasing in j.
 //
 // Work is split into segments of a tile's list: segment s holds receivers
 // [R_s, R_s+1) (kSegLen entries; the last takes the rest) and needs the
@@ -92,11 +93,6 @@ __device__ __forceinline__ void stage_entry(const ShadowParams& p, uint32_t idx,
                                             float4& e1) {
   make_entry(p.rrec[p.list[idx]], ox, oy, e0, e1);
   e1.w = __uint_as_float(__float_as_uint(e1.w) & ellipse_halves(e0, e1));
-}
-
-// 1 - alpha of an occluder entry at a pixel where it passes (power2 >= threshold)
-__device__ __forceinline__ float occ_factor(const float4 o1, float pw, float omin) {
-  return fmaxf(omin, fmaf(-o1.z, ex2(pw), 1.f));
 }
 
 __device__ __forceinline__ uint32_t ld_acquire(const uint32_t* a) {
@@ -791,18 +787,6 @@ __global__ void __launch_bounds__(kSegWarps * 32, 4) k_shadow(const ShadowParams
   }
 }
 
-// The distance of every list entry, from the depth sort's keys: the key of
-// depth rank r is the FP32 bit pattern of rank r's light distance (the
-// record's a.w), so this reads 4 bytes per entry instead of a record.
-__global__ void __launch_bounds__(256) k_gather_depth(const uint32_t* __restrict__ list,
-                                                      const uint32_t* __restrict__ rank_key,
-                                                      const uint32_t* header, float* __restrict__ dl,
-                                                      uint32_t limit) {
-  const uint32_t P = min(header[H_PAIRS_LIGHT], limit);
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < P; i += gridDim.x * blockDim.x)
-    dl[i] = __uint_as_float(rank_key[list[i]]);
-}
-
 // K(i) of entry i of a light list: the first index of i's tile list (from b)
 // whose distance is >= d_i - bias, the end of i's occluder prefix.
 __device__ __forceinline__ uint32_t occ_bound(const float* __restrict__ dl, uint32_t b, uint32_t i, float bias) {
@@ -1272,7 +1256,7 @@ ShadowParams shadow_params(const FrameArgs& f) {
   p.rrec = at<SplatRec>(ws, b.rrec);
   p.off = at<uint32_t>(ws, b.off);
   p.kbound = at<uint32_t>(ws, b.tv[1 - fin]);
-  p.pass_mask = at<uint8_t>(ws, b.tk[1 - fin]);  // the depths are consumed by k_occluder_bound
+  p.pass_mask = at<uint8_t>(ws, b.tk[1 - fin]);  // over the distances, once the occluder bounds are done
   p.partial = at<float2>(ws, f.L->partial);
   p.light_final = at<float>(ws, f.L->light_final);
   p.light_stop = at<uint32_t>(ws, f.L->light_stop);
@@ -1355,17 +1339,9 @@ void prepare_shadow_composite(const FrameArgs& f, cudaStream_t s) {
   const SplatBufs& b = f.L->sp[1];
   unsigned char* ws = f.ws;
   const int fin = (f.L->ntiles <= 256 ? 1 : 2) & 1;
-  // the non-final tile-sort buffers are free after the sort: depth per entry, occluder bound
+  // the distance of every list entry (written by the binning) and the occluder bounds
   float* dl = at<float>(ws, b.tk[1 - fin]);
   uint32_t* kb = at<uint32_t>(ws, b.tv[1 - fin]);
-  uint32_t* header = at<uint32_t>(ws, f.L->header);
-  const int nsm = device_sm_count();
-  int blocks = (int)((f.L->cap + 255) / 256);
-  if (blocks > nsm * 16) blocks = nsm * 16;
-  // the depth sort's four passes leave the keys in rank order in sk[1]
-  k_gather_depth<<<blocks, 256, 0, s>>>(at<uint32_t>(ws, b.tv[fin]), at<uint32_t>(ws, b.sk[1]), header, dl,
-                                        (uint32_t)f.L->cap);
-  count_launch();
   // the light tiles by segment count, and the work items of each segment level
   uint32_t* lvl = at<uint32_t>(ws, f.L->seg_lvl);
   cudaMemsetAsync(lvl + kSegLevels + 1, 0, 12, s);  // the tickets

@@ -338,12 +338,16 @@ __global__ void __launch_bounds__(1024) k_bin_rowscan(uint32_t* __restrict__ tab
 }
 
 // The list entries: each chunk in steps of 256 items over their columns,
-// starting at the chunk's offsets in its tiles.
+// starting at the chunk's offsets in its tiles.  With dist (the light
+// splat), each entry's distance goes beside it: the depth sort's key of rank
+// r is the FP32 bit pattern of r's light distance.
 __global__ void __launch_bounds__(kBinThreads) k_bin_place(const uint32_t* __restrict__ rowseq,
                                                            const uint32_t* __restrict__ rowspan,
                                                            const uint32_t* __restrict__ plan,
                                                            const uint32_t* __restrict__ tab, int gx, int gy,
-                                                           uint32_t ch, uint32_t* __restrict__ list, size_t cap) {
+                                                           uint32_t ch, const uint32_t* __restrict__ rank_key,
+                                                           uint32_t* __restrict__ list, uint32_t* __restrict__ dist,
+                                                           size_t cap) {
   __shared__ SpanSmem S;
   const uint32_t* rs = plan;
   const uint32_t* cb = plan + gy + 1;
@@ -358,14 +362,15 @@ __global__ void __launch_bounds__(kBinThreads) k_bin_place(const uint32_t* __res
     for (uint32_t sub = i0; sub < i1; sub += kBinThreads) {
       const uint32_t i = sub + threadIdx.x;
       int a = 0, b = -1;
-      uint32_t r = 0;
+      uint32_t r = 0, key = 0;
       if (i < i1) {
         r = rowseq[i];
         const uint32_t sp = rowspan[i];
         a = (int)(sp & 0xFFFFu);
         b = (int)(sp >> 16);
+        if (dist) key = rank_key[r];
       }
-      place_spans(S, gx, a, b, r, 0u, list, nullptr, cap);
+      place_spans(S, gx, a, b, r, key, list, dist, cap);
     }
     __syncthreads();  // S.run is rewritten for the next chunk
   }
@@ -385,12 +390,14 @@ void launch_binning(const FrameArgs& f, int sp, cudaStream_t s) {
   // every rank's first list slot in rank order (the shadow partials' slots) and the total
   device_exclusive_scan(at<uint32_t>(ws, b.cnt), at<uint32_t>(ws, b.off), (uint32_t)n, header + h_need,
                         at<uint32_t>(ws, b.scan_part), s);
-  // the lists go where the composites and the backward read them; the row
-  // sequence and spans use buffers that are free until the shadow composite
+  // the lists go where the composites and the backward read them, and for
+  // the light splat each entry's distance where the occluder bounds read it;
+  // the row sequence and spans use buffers that are free until then
   const int fin = (f.L->ntiles <= 256 ? 1 : 2) & 1;
   uint32_t* list = at<uint32_t>(ws, b.tv[fin]);
+  uint32_t* dist = sp ? at<uint32_t>(ws, b.tk[1 - fin]) : nullptr;
   uint32_t* rowseq = at<uint32_t>(ws, b.tk[fin]);
-  uint32_t* rowspan = at<uint32_t>(ws, b.tk[1 - fin]);
+  uint32_t* rowspan = at<uint32_t>(ws, b.tv[1 - fin]);
   uint32_t* row_cnt = at<uint32_t>(ws, b.row_cnt);
   uint32_t* plan = at<uint32_t>(ws, b.bin_plan);
   uint32_t* tab = at<uint32_t>(ws, b.bin_tab);
@@ -403,7 +410,8 @@ void launch_binning(const FrameArgs& f, int sp, cudaStream_t s) {
   if ((size_t)grid > chunks) grid = (int)chunks;
   k_bin_count<<<grid, kBinThreads, 0, s>>>(rowspan, plan, gx, gy, ch, tab);
   k_bin_rowscan<<<gy, 1024, 0, s>>>(tab, plan, gx, gy, at<uint32_t>(ws, b.tile_start));
-  k_bin_place<<<grid, kBinThreads, 0, s>>>(rowseq, rowspan, plan, tab, gx, gy, ch, list, cap);
+  k_bin_place<<<grid, kBinThreads, 0, s>>>(rowseq, rowspan, plan, tab, gx, gy, ch, at<uint32_t>(ws, b.sk[1]), list,
+                                           dist, cap);
   count_launch(6);
 }
 
