@@ -166,25 +166,37 @@ __device__ void place_spans(SpanSmem& S, int nbk, int a, int b, uint32_t v0, uin
   S.v1[w][lane] = v1;
   __syncwarp();
   const uint32_t lt = (1u << lane) - 1u;
-  for (uint32_t p0 = 0; p0 < total; p0 += 32) {
-    const uint32_t p = p0 + lane;
-    const bool act = p < total;
-    int j = 0;  // the item of pair p: the last lane j with ex[j] <= p
+  // four rounds at a time: their item searches are independent, so they run
+  // side by side; the counters are then read and advanced round by round
+  for (uint32_t p0 = 0; p0 < total; p0 += 128) {
+    int jq[4], xq[4];
 #pragma unroll
-    for (int s = 16; s > 0; s >>= 1)
-      if (S.ex[w][j + s] <= p) j += s;
-    const int x = S.lo[w][j] + (int)(p - S.ex[w][j]);
-    const uint32_t m = __match_any_sync(0xffffffffu, act ? x : -1 - lane);
-    if (act) {
-      const uint32_t pos = (uint32_t)c[x] + (uint32_t)__popc(m & lt);
-      if (pos < cap) {
-        out0[pos] = S.v0[w][j];
-        if (out1) out1[pos] = S.v1[w][j];
-      }
+    for (int q = 0; q < 4; ++q) {
+      const uint32_t p = p0 + 32 * q + lane;
+      int j = 0;  // the item of pair p: the last lane j with ex[j] <= p
+#pragma unroll
+      for (int s = 16; s > 0; s >>= 1)
+        if (S.ex[w][j + s] <= p) j += s;
+      jq[q] = j;
+      xq[q] = S.lo[w][j] + (int)(p - S.ex[w][j]);
     }
-    __syncwarp();  // every lane has read its bucket's counter
-    if (act && (m >> lane) == 1u) c[x] += __popc(m);
-    __syncwarp();
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      if (p0 + 32 * q >= total) break;  // the same for every lane
+      const bool act = p0 + 32 * q + lane < total;
+      const int j = jq[q], x = xq[q];
+      const uint32_t m = __match_any_sync(0xffffffffu, act ? x : -1 - lane);
+      if (act) {
+        const uint32_t pos = (uint32_t)c[x] + (uint32_t)__popc(m & lt);
+        if (pos < cap) {
+          out0[pos] = S.v0[w][j];
+          if (out1) out1[pos] = S.v1[w][j];
+        }
+      }
+      __syncwarp();  // every lane has read its bucket's counter
+      if (act && (m >> lane) == 1u) c[x] += __popc(m);
+      __syncwarp();
+    }
   }
   __syncthreads();  // S is rewritten by the next call
 }
