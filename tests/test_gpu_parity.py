@@ -107,10 +107,13 @@ CASES = [
     ("ball_3k_k8", lambda: synth.make_scene(5, 3000, 8, "ball"), 5, 200, 152),
     ("shell_20k", lambda: synth.object_scene(2, n=20000), 7, 256, 256),
     ("paper_mlp", lambda: synth.paper_mlp_scene(1, n=2000), 11, 160, 144),
-    # 1444 tiles: counting-sort binning, lists in the second buffer pair
+    # 1444 tiles: lists in the second buffer pair
     ("ball_3k_608", lambda: synth.make_scene(6, 3000, 4, "ball"), 13, 608, 608),
-    # 16641 tiles: above the counting sort's shared-memory counters, radix binning
+    # 16641 tiles, 129 columns: binning chunks of 512 row items (two steps of 256)
     ("tiny_2064", lambda: synth.tiny_scene(0), 17, 2064, 2064),
+    # one tile row of 129 columns, and one tile column of 65 rows
+    ("strip_wide", lambda: synth.tiny_scene(0), 19, 2064, 16),
+    ("strip_tall", lambda: synth.tiny_scene(0), 23, 16, 1040),
 ]
 
 
