@@ -630,6 +630,35 @@ def main():
     e2e_s = replicas.max_over_ranks(time.perf_counter() - e0, dev)
     e2e_val = replicas.whole_job_rate(K, e2e_s, world)
 
+    # ---- a moving camera under a fixed light ----
+    # The shadow values depend on the scene, the light and the image size only,
+    # so after one full frame the camera-side stages (projections and shading,
+    # camera binning, both MLPs, the camera composite) render every further
+    # view on the same workspace; the result equals a full frame of that view
+    # bit for bit (tests/test_gpu_parity.py).
+    cam_side = N.GS3_STAGE_PREP | N.GS3_STAGE_CAMERA_BIN | N.GS3_STAGE_MLP | N.GS3_STAGE_CAMERA
+    fixed_light = pairs[0][1]
+    rd.render(pairs[0][0], fixed_light, opts)
+    for s in range(3):
+        rd.render_stages(pairs[s + 1][0], fixed_light, cam_side, opts)
+    MK = max(K, 100)
+    mev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(MK)]
+    torch.cuda.synchronize()
+    for s in range(MK):
+        mev[s][0].record(stream)
+        rd.render_stages(pairs[s % len(pairs)][0], fixed_light, cam_side, opts)
+        mev[s][1].record(stream)
+    torch.cuda.synchronize()
+    rd.check()
+    mv_ms = np.array([e0.elapsed_time(e1) for e0, e1 in mev])
+    mv_total = replicas.max_over_ranks(float(mv_ms.sum()), dev)
+    moving = {"value": replicas.whole_job_rate(MK, mv_total / 1e3, world), "unit": UNIT,
+              "ms_per_frame": mv_total / MK, "frames": MK,
+              "p50_ms": float(np.percentile(mv_ms, 50)), "p99_ms": float(np.percentile(mv_ms, 99)),
+              "note": "the light of pair 0 for every frame, the cameras of the 100 pairs: one full frame, "
+                      "then only the camera-side stages per view (gs3_render_stages), CUDA events per "
+                      "frame; not the headline workload, whose every frame has its own light"}
+
     # ---- served arm: continuous batching through the server (headline) ----
     def serve(slots, batch):
         """Frames/s of the server over RS frames (CUDA-event span), then the
@@ -855,6 +884,7 @@ def main():
                 "d2h_bytes_per_step": a.res * a.res * 3 * 4,
                 "note": "gs3_render through the C ABI, camera/light host structs in, image copied "
                         "to pinned host memory and synchronised every step"},
+        "moving_camera_fixed_light": moving,
     }
     if world == 1 and not a.no_mix:
         out["serving_mix"] = serving_mix(a, dev, np, torch, N, R, synth)

@@ -234,7 +234,14 @@ enum {
  * workspace, so a frame split into several calls (same scene, camera, light,
  * options and workspace, stages in order, header reset by the call that
  * includes GS3_STAGE_PREP) equals one gs3_render.  Used to time stages with
- * events recorded on `stream` between the calls.  Errors as gs3_render. */
+ * events recorded on `stream` between the calls.
+ * A moving camera under a fixed light: the shadow values T (Sec. 4.2) depend
+ * on the scene, the light, the image size and the options, not on the
+ * camera.  After one full frame on a workspace, GS3_STAGE_PREP |
+ * GS3_STAGE_CAMERA_BIN | GS3_STAGE_MLP | GS3_STAGE_CAMERA with another camera
+ * (same scene, light, size, options and workspace) equals gs3_render of that
+ * view bit for bit, without the light splat.  The header's light pair counts
+ * then read 0.  Errors as gs3_render. */
 gs3_status gs3_render_stages(gs3_scene *scene, const gs3_camera *camera, const gs3_light *light,
                              const gs3_render_opts *opts, float *out_rgb, void *workspace,
                              size_t workspace_bytes, size_t key_capacity, uint32_t stages,

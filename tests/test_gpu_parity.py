@@ -187,6 +187,32 @@ def test_capacity_overflow_reported(gs3):
     rd2.check()
 
 
+@pytest.mark.parametrize("mlp_dtype", [0, 1], ids=["fp32", "bf16"])
+def test_moving_camera_fixed_light(gs3, mlp_dtype):
+    """The shadow values depend on the scene, the light and the image size,
+    not on the camera: after a full frame, the camera-side stages alone render
+    another view under the same light bit for bit as its full frame."""
+    import torch
+    from paper_2410_11419_gb300 import render as R, _native as N
+    scene = synth.make_scene(5, 3000, 8, "ball")
+    cam_a, light = synth.camera_light_pair(5, 200, 152)
+    views = [synth.camera_light_pair(s, 200, 152)[0] for s in (8, 9)]
+    ds = R.DeviceScene(scene, mlp_dtype=mlp_dtype)
+    moving = R.Renderer(ds, 200, 152, 1 << 20)
+    full = R.Renderer(ds, 200, 152, 1 << 20)
+    moving.render(cam_a, light)
+    cam_side = N.GS3_STAGE_PREP | N.GS3_STAGE_CAMERA_BIN | N.GS3_STAGE_MLP | N.GS3_STAGE_CAMERA
+    for cam in views:
+        got = moving.render_stages(cam, light, cam_side).clone()
+        want = full.render(cam, light).clone()
+        torch.cuda.synchronize()
+        moving.check()
+        full.check()
+        assert torch.equal(got, want)
+        assert torch.equal(moving.stage("Tp"), full.stage("Tp"))
+    ds.close()
+
+
 def test_bounded_wait_gives_up(gs3):
     """A look-back wait that can never end (its predecessor's words are never
     written) gives up, records GS3_ERR_TIMEOUT, and the context still renders."""
