@@ -360,6 +360,13 @@ typedef struct {
                                       scaled with the pixel count (0: 64) */
     int32_t max_batch;             /* requests rendered together by one slot, 1..8 (0: 1: every
                                       request alone on its slot's streams) */
+    int32_t light_cache;           /* 0..4096: shadow values kept for this many (scene, light,
+                                      image size, options) keys (0: none).  A request alone on its
+                                      slot whose key is kept copies them into its workspace and runs
+                                      only the camera-side stages (gs3_render_stages); its image
+                                      still equals its gs3_render bit for bit.  Each key holds
+                                      4 n bytes of device memory outside the budget until the
+                                      server is destroyed. */
 } gs3_server_opts;
 
 typedef struct {
@@ -369,6 +376,7 @@ typedef struct {
                               last completed batch's end since the last reset */
     uint64_t batches;      /* batches launched */
     uint64_t max_batch;    /* the most requests one batch held */
+    uint64_t light_reuse;  /* requests rendered from kept shadow values (light_cache) */
 } gs3_server_counters;
 
 typedef struct gs3_server gs3_server;

@@ -101,13 +101,15 @@ class gs3_server(C.Structure):
 
 class gs3_server_opts(C.Structure):
     _fields_ = [("hbm_budget", C.c_size_t), ("max_inflight", C.c_int32), ("device", C.c_int32),
-                ("inject_alloc_failures", C.c_int32), ("initial_pairs", C.c_float), ("max_batch", C.c_int32)]
+                ("inject_alloc_failures", C.c_int32), ("initial_pairs", C.c_float), ("max_batch", C.c_int32),
+                ("light_cache", C.c_int32)]
 
 
 class gs3_server_counters(C.Structure):
     _fields_ = [(f, C.c_uint64) for f in ("completed", "failed", "retries", "queued", "in_flight",
                                           "max_in_flight", "bytes_in_use", "peak_bytes_in_use")] + [
-        ("device_span_ms", C.c_double), ("batches", C.c_uint64), ("max_batch", C.c_uint64)]
+        ("device_span_ms", C.c_double), ("batches", C.c_uint64), ("max_batch", C.c_uint64),
+        ("light_reuse", C.c_uint64)]
 
 
 GS3_REQ_QUEUED, GS3_REQ_RUNNING, GS3_REQ_DONE, GS3_REQ_FAILED = 0, 1, 2, 3
@@ -301,9 +303,11 @@ def gs3_workspace_read_header(workspace, stream: int) -> gs3_ws_header:
 
 
 def gs3_server_create(hbm_budget: int, max_inflight: int, device: int = 0,
-                      inject_alloc_failures: int = 0, initial_pairs: float = 0.0, max_batch: int = 0):
+                      inject_alloc_failures: int = 0, initial_pairs: float = 0.0, max_batch: int = 0,
+                      light_cache: int = 0):
     out = _SERVER_P()
-    o = gs3_server_opts(hbm_budget, max_inflight, device, inject_alloc_failures, initial_pairs, max_batch)
+    o = gs3_server_opts(hbm_budget, max_inflight, device, inject_alloc_failures, initial_pairs, max_batch,
+                        light_cache)
     _check(lib().gs3_server_create(C.byref(o), C.byref(out)), "gs3_server_create")
     return out
 

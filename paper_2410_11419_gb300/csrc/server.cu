@@ -14,8 +14,14 @@
 // (tile/Gaussian pairs) is estimated per (scene, resolution) from the largest
 // count seen so far; a request that overflows is re-admitted once with the
 // exact count its first run reported.
+// With a light cache, the shadow values T of a completed frame are kept per
+// (scene, light, image size, options): they depend on nothing else (not on
+// the camera), so a later request alone on its slot with the same key copies
+// them into its workspace and runs only the camera-side stages.  A kept entry
+// becomes usable when the frame that filled it has completed without error.
 #include <chrono>
 #include <condition_variable>
+#include <cstring>
 #include <deque>
 #include <mutex>
 #include <string>
@@ -49,7 +55,18 @@ struct Member {
   void* ws = nullptr;
   size_t bytes = 0;
   size_t cap = 0;
+  std::string fill;  // the light-cache key this frame's shadow values fill, or empty
 };
+
+// Shadow values T (n floats) of one light-cache key.
+struct LightEntry {
+  float* T = nullptr;
+  size_t n = 0;
+  bool ready = false;  // the frame that filled it completed without error
+};
+
+// the stages that depend on the camera (gs3_render_stages)
+constexpr uint32_t kCameraSide = GS3_STAGE_PREP | GS3_STAGE_CAMERA_BIN | GS3_STAGE_MLP | GS3_STAGE_CAMERA;
 
 struct Slot {
   cudaStream_t stream = nullptr;
@@ -96,6 +113,9 @@ struct gs3_server {
   int max_batch = 1;
   int max_batch_seen = 0;
   uint64_t batches = 0;
+  int light_cache_max = 0;
+  std::unordered_map<std::string, LightEntry> light_cache;
+  uint64_t light_reuse = 0;
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
   std::thread worker;
@@ -108,6 +128,34 @@ namespace {
 
 uint64_t hint_key(int scene, int w, int h) {
   return ((uint64_t)scene << 40) ^ ((uint64_t)w << 20) ^ (uint64_t)h;
+}
+
+// The light-cache key: scene, image size, light and options, byte for byte
+// (padding bytes that differ can only cause a miss).
+std::string light_key(const Request& r) {
+  const int32_t v[3] = {r.scene, r.cam.width, r.cam.height};
+  std::string k(sizeof v + sizeof(gs3_light) + sizeof(gs3_render_opts), '\0');
+  std::memcpy(&k[0], v, sizeof v);
+  std::memcpy(&k[sizeof v], &r.light, sizeof(gs3_light));
+  std::memcpy(&k[sizeof v + sizeof(gs3_light)], &r.opts, sizeof(gs3_render_opts));
+  return k;
+}
+
+// A frame that was to fill a light-cache entry has finished: the entry becomes
+// usable if the frame succeeded, else it is dropped (its memory returned in
+// stream order after the frame's copy).
+void settle_fill(gs3_server* S, Slot& sl, Member& m, bool ok) {
+  if (m.fill.empty()) return;
+  auto it = S->light_cache.find(m.fill);
+  if (it != S->light_cache.end()) {
+    if (ok) {
+      it->second.ready = true;
+    } else {
+      cudaFreeAsync(it->second.T, sl.stream);
+      S->light_cache.erase(it);
+    }
+  }
+  m.fill.clear();
 }
 
 size_t estimate_cap(gs3_server* S, const Request& r) {
@@ -161,6 +209,7 @@ bool poll_slots(gs3_server* S) {
         ++S->retries;
         auto& hint = S->cap_hint[hint_key(r.scene, r.cam.width, r.cam.height)];
         if (r.forced_cap > hint) hint = r.forced_cap;
+        settle_fill(S, sl, m, false);
         release(S, sl, m);
         S->results[r.ticket].state = GS3_REQ_QUEUED;
         S->queue.push_front(r);
@@ -181,6 +230,7 @@ bool poll_slots(gs3_server* S) {
         }
         timed = true;
       }
+      settle_fill(S, sl, m, st == GS3_OK);
       finish(S, m.req, st);
       release(S, sl, m);
     }
@@ -234,6 +284,7 @@ bool admit(gs3_server* S) {
       m.ws = ws;
       m.bytes = bytes;
       m.cap = cap;
+      m.fill.clear();
       S->in_use += bytes;
       if (S->in_use > S->peak_in_use) S->peak_in_use = S->in_use;
       S->results[req.ticket].state = GS3_REQ_RUNNING;
@@ -251,8 +302,39 @@ bool admit(gs3_server* S) {
       aligned[i] = reinterpret_cast<void*>((reinterpret_cast<uintptr_t>(sl.m[i].ws) + 255) & ~uintptr_t(255));
     if (sl.n == 1) {
       Member& m = sl.m[0];
-      st = render_frame(S->scenes[m.req.scene], &m.req.cam, &m.req.light, &m.req.opts, m.req.out, aligned[0],
-                        m.bytes - 256, m.cap, GS3_STAGE_ALL, sl.stream, sl.side.s ? &sl.side : nullptr);
+      gs3_scene* sc = S->scenes[m.req.scene];
+      const size_t n = (size_t)sc->dev.n;
+      const LightEntry* kept = nullptr;
+      if (S->light_cache_max > 0) {
+        const std::string key = light_key(m.req);
+        auto it = S->light_cache.find(key);
+        if (it != S->light_cache.end()) {
+          if (it->second.ready) kept = &it->second;  // else its frame is still in flight: render in full
+        } else if ((int)S->light_cache.size() < S->light_cache_max) {
+          void* T = nullptr;
+          if (cudaMallocFromPoolAsync(&T, 4 * n, S->pool, sl.stream) == cudaSuccess) {
+            S->light_cache.emplace(key, LightEntry{static_cast<float*>(T), n, false});
+            m.fill = key;
+          } else {
+            cudaGetLastError();
+          }
+        }
+      }
+      // the shadow values' place in this request's workspace
+      unsigned char* Tws = static_cast<unsigned char*>(aligned[0]) +
+                           plan_workspace(sc->dev.n, m.req.cam.width, m.req.cam.height, m.cap).T;
+      if (kept) {
+        cudaMemcpyAsync(Tws, kept->T, 4 * n, cudaMemcpyDeviceToDevice, sl.stream);
+        st = render_frame(sc, &m.req.cam, &m.req.light, &m.req.opts, m.req.out, aligned[0], m.bytes - 256, m.cap,
+                          kCameraSide, sl.stream, nullptr);
+        if (st == GS3_OK) ++S->light_reuse;
+      } else {
+        st = render_frame(sc, &m.req.cam, &m.req.light, &m.req.opts, m.req.out, aligned[0], m.bytes - 256, m.cap,
+                          GS3_STAGE_ALL, sl.stream, sl.side.s ? &sl.side : nullptr);
+        if (st == GS3_OK && !m.fill.empty())
+          cudaMemcpyAsync(S->light_cache[m.fill].T, Tws, 4 * n, cudaMemcpyDeviceToDevice, sl.stream);
+      }
+      if (st != GS3_OK) settle_fill(S, sl, m, false);
     } else {
       BatchFrame fr[kMaxBatch];
       for (int i = 0; i < sl.n; ++i) {
@@ -322,8 +404,14 @@ gs3_status gs3_server_create(const gs3_server_opts* o, gs3_server** out) {
     set_last_error("gs3_server_create: max_batch must be in [0, 8]");
     return GS3_ERR_INVALID_ARG;
   }
+  if (o->light_cache < 0 || o->light_cache > 4096) {
+    delete S;
+    set_last_error("gs3_server_create: light_cache must be in [0, 4096]");
+    return GS3_ERR_INVALID_ARG;
+  }
   S->budget = o->hbm_budget;
   S->max_batch = o->max_batch > 0 ? o->max_batch : 1;
+  S->light_cache_max = o->light_cache;
   S->inject_alloc_failures = o->inject_alloc_failures;
   if (o->initial_pairs > 0.f) S->initial_pairs = o->initial_pairs;
   S->device = o->device;
@@ -460,6 +548,7 @@ gs3_status gs3_server_stats(gs3_server* S, gs3_server_counters* out) {
   out->in_flight = (uint64_t)inflight;
   out->batches = S->batches;
   out->max_batch = (uint64_t)S->max_batch_seen;
+  out->light_reuse = S->light_reuse;
   out->max_in_flight = (uint64_t)S->max_inflight_seen;
   out->bytes_in_use = S->in_use;
   out->peak_bytes_in_use = S->peak_in_use;
@@ -474,6 +563,7 @@ gs3_status gs3_server_reset_counters(gs3_server* S) {
   S->max_inflight_seen = 0;
   S->max_batch_seen = 0;
   S->batches = 0;
+  S->light_reuse = 0;
   S->peak_in_use = S->in_use;
   S->epoch_set = false;
   S->span_lo = 1e300;
@@ -489,6 +579,11 @@ gs3_status gs3_server_destroy(gs3_server* S) {
   }
   S->cv_work.notify_all();
   if (S->worker.joinable()) S->worker.join();
+  for (Slot& sl : S->slots)
+    if (sl.stream) cudaStreamSynchronize(sl.stream);
+  if (!S->slots.empty() && S->slots[0].stream)  // the kept shadow values, once every copy is done
+    for (auto& kv : S->light_cache) cudaFreeAsync(kv.second.T, S->slots[0].stream);
+  S->light_cache.clear();
   for (Slot& sl : S->slots) {
     if (sl.stream) cudaStreamSynchronize(sl.stream);
     for (int i = 0; i < sl.n; ++i)

@@ -206,11 +206,13 @@ class Server:
     """Continuous-batching server (gs3_server_*) over device-resident scenes."""
 
     def __init__(self, hbm_budget: int, max_inflight: int = 4, device: int = 0,
-                 inject_alloc_failures: int = 0, initial_pairs: float = 0.0, max_batch: int = 0):
+                 inject_alloc_failures: int = 0, initial_pairs: float = 0.0, max_batch: int = 0,
+                 light_cache: int = 0):
         """max_inflight slots, each rendering up to max_batch requests together
-        (0 or 1: every request alone on its slot's streams)."""
+        (0 or 1: every request alone on its slot's streams); light_cache: shadow
+        values kept for that many (scene, light, size, options) keys."""
         self.handle = N.gs3_server_create(hbm_budget, max_inflight, device, inject_alloc_failures,
-                                          initial_pairs, max_batch)
+                                          initial_pairs, max_batch, light_cache)
         self.scenes = []
 
     def add_scene(self, dscene: DeviceScene) -> int:

@@ -44,6 +44,8 @@ def test_struct_sizes_match_header_layout(libgs3):
     assert ctypes.sizeof(N.gs3_render_opts) == 4 * (7 + 3 + 3)
     assert ctypes.sizeof(N.gs3_ws_header) == 4 * (8 + 12 + 1)
     assert ctypes.sizeof(N.gs3_ws_layout) == 8 * (2 + 5 * 2 + 8)
+    assert ctypes.sizeof(N.gs3_server_opts) == 8 + 4 * 6      # budget, 5 int32/float fields, light_cache
+    assert ctypes.sizeof(N.gs3_server_counters) == 8 * 12     # 8 counters, span, batches, max_batch, reuse
 
 
 def test_host_only_entry_points(libgs3):

@@ -210,6 +210,17 @@ def test_moving_camera_fixed_light(gs3, mlp_dtype):
         full.check()
         assert torch.equal(got, want)
         assert torch.equal(moving.stage("Tp"), full.stage("Tp"))
+    # only T carries over: a workspace whose other light-side buffers hold
+    # another light's frame gives the same image once T is the right one
+    other = R.Renderer(ds, 200, 152, 1 << 20)
+    other.render(cam_a, synth.camera_light_pair(6, 200, 152)[1])
+    full.render(cam_a, light)
+    other.stage("T").copy_(full.stage("T"))
+    got = other.render_stages(views[0], light, cam_side).clone()
+    want = full.render(views[0], light).clone()
+    torch.cuda.synchronize()
+    other.check()
+    assert torch.equal(got, want)
     ds.close()
 
 

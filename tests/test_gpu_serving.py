@@ -67,6 +67,35 @@ def test_mixed_requests_equal_alone(scenes):
     srv.close()
 
 
+def test_light_cache_reuses_shadow_values(scenes):
+    """With a light cache, requests sharing (scene, light, size, options) with
+    a completed frame copy its shadow values and run only the camera-side
+    stages; every image still equals its frame rendered alone."""
+    import torch
+    from paper_2410_11419_gb300 import render as R
+    srv = R.Server(hbm_budget=8 << 30, max_inflight=2, light_cache=4)
+    sid = srv.add_scene(scenes[0])
+    light = synth.camera_light_pair(21, 256, 256)[1]
+    light2 = synth.camera_light_pair(22, 256, 256)[1]
+    cams = [synth.camera_light_pair(s, 256, 256)[0] for s in range(30, 36)]
+    first = torch.empty((256, 256, 3), device="cuda")
+    torch.cuda.synchronize()
+    assert srv.wait(srv.submit(sid, cams[0], light, first))[0] == 0  # fills the cache
+    reqs = [(cams[1], light2)] + [(c, light) for c in cams[1:]]
+    outs = [torch.full((256, 256, 3), -1.0, device="cuda") for _ in reqs]
+    torch.cuda.synchronize()
+    ts = [srv.submit(sid, c, l, o) for (c, l), o in zip(reqs, outs)]
+    for t in ts:
+        assert srv.wait(t)[0] == 0
+    st = srv.stats()
+    assert st.completed == len(reqs) + 1 and st.failed == 0
+    assert st.light_reuse == len(cams) - 1  # every later view of the first light
+    assert torch.equal(first, alone(scenes[0], cams[0], light))
+    for (c, l), o in zip(reqs, outs):
+        assert torch.equal(o, alone(scenes[0], c, l))
+    srv.close()
+
+
 def test_admission_respects_budget(scenes):
     import torch
     from paper_2410_11419_gb300 import _native as N, render as R
