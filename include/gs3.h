@@ -364,9 +364,10 @@ typedef struct {
                                       image size, options) keys (0: none).  A request alone on its
                                       slot whose key is kept copies them into its workspace and runs
                                       only the camera-side stages (gs3_render_stages); its image
-                                      still equals its gs3_render bit for bit.  Each key holds
-                                      4 n bytes of device memory outside the budget until the
-                                      server is destroyed. */
+                                      still equals its gs3_render bit for bit.  When all keys are
+                                      taken, the least recently used one that no admitted request
+                                      reads is dropped.  Each key holds 4 n bytes of device memory
+                                      outside the budget. */
 } gs3_server_opts;
 
 typedef struct {

@@ -18,7 +18,9 @@
 // (scene, light, image size, options): they depend on nothing else (not on
 // the camera), so a later request alone on its slot with the same key copies
 // them into its workspace and runs only the camera-side stages.  A kept entry
-// becomes usable when the frame that filled it has completed without error.
+// becomes usable when the frame that filled it has completed without error;
+// when the cache is full, the least recently used entry that no admitted
+// frame reads makes room.
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -55,7 +57,8 @@ struct Member {
   void* ws = nullptr;
   size_t bytes = 0;
   size_t cap = 0;
-  std::string fill;  // the light-cache key this frame's shadow values fill, or empty
+  std::string fill;   // the light-cache key this frame's shadow values fill, or empty
+  std::string reuse;  // the light-cache key this frame copies its shadow values from, or empty
 };
 
 // Shadow values T (n floats) of one light-cache key.
@@ -63,6 +66,8 @@ struct LightEntry {
   float* T = nullptr;
   size_t n = 0;
   bool ready = false;  // the frame that filled it completed without error
+  int users = 0;       // admitted frames copying from it that have not completed
+  uint64_t last_use = 0;
 };
 
 // the stages that depend on the camera (gs3_render_stages)
@@ -116,6 +121,7 @@ struct gs3_server {
   int light_cache_max = 0;
   std::unordered_map<std::string, LightEntry> light_cache;
   uint64_t light_reuse = 0;
+  uint64_t light_clock = 0;  // orders the entries' last uses
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
   std::thread worker;
@@ -156,6 +162,30 @@ void settle_fill(gs3_server* S, Slot& sl, Member& m, bool ok) {
     }
   }
   m.fill.clear();
+}
+
+// A frame that copied kept shadow values has finished (or was not launched).
+void settle_reuse(gs3_server* S, Member& m) {
+  if (m.reuse.empty()) return;
+  auto it = S->light_cache.find(m.reuse);
+  if (it != S->light_cache.end() && it->second.users > 0) --it->second.users;
+  m.reuse.clear();
+}
+
+// Room for one more light-cache entry: below the limit, or after freeing the
+// least recently used entry that is ready and that no admitted frame reads
+// (its copies have completed, so its memory is idle).  False if none can go.
+bool light_cache_room(gs3_server* S, cudaStream_t s) {
+  if ((int)S->light_cache.size() < S->light_cache_max) return true;
+  auto victim = S->light_cache.end();
+  for (auto it = S->light_cache.begin(); it != S->light_cache.end(); ++it)
+    if (it->second.ready && it->second.users == 0 &&
+        (victim == S->light_cache.end() || it->second.last_use < victim->second.last_use))
+      victim = it;
+  if (victim == S->light_cache.end()) return false;
+  cudaFreeAsync(victim->second.T, s);
+  S->light_cache.erase(victim);
+  return true;
 }
 
 size_t estimate_cap(gs3_server* S, const Request& r) {
@@ -210,6 +240,7 @@ bool poll_slots(gs3_server* S) {
         auto& hint = S->cap_hint[hint_key(r.scene, r.cam.width, r.cam.height)];
         if (r.forced_cap > hint) hint = r.forced_cap;
         settle_fill(S, sl, m, false);
+        settle_reuse(S, m);
         release(S, sl, m);
         S->results[r.ticket].state = GS3_REQ_QUEUED;
         S->queue.push_front(r);
@@ -231,6 +262,7 @@ bool poll_slots(gs3_server* S) {
         timed = true;
       }
       settle_fill(S, sl, m, st == GS3_OK);
+      settle_reuse(S, m);
       finish(S, m.req, st);
       release(S, sl, m);
     }
@@ -285,6 +317,7 @@ bool admit(gs3_server* S) {
       m.bytes = bytes;
       m.cap = cap;
       m.fill.clear();
+      m.reuse.clear();
       S->in_use += bytes;
       if (S->in_use > S->peak_in_use) S->peak_in_use = S->in_use;
       S->results[req.ticket].state = GS3_REQ_RUNNING;
@@ -309,11 +342,20 @@ bool admit(gs3_server* S) {
         const std::string key = light_key(m.req);
         auto it = S->light_cache.find(key);
         if (it != S->light_cache.end()) {
-          if (it->second.ready) kept = &it->second;  // else its frame is still in flight: render in full
-        } else if ((int)S->light_cache.size() < S->light_cache_max) {
+          if (it->second.ready) {  // else its frame is still in flight: render in full
+            kept = &it->second;
+            ++it->second.users;
+            it->second.last_use = ++S->light_clock;
+            m.reuse = key;
+          }
+        } else if (light_cache_room(S, sl.stream)) {
           void* T = nullptr;
           if (cudaMallocFromPoolAsync(&T, 4 * n, S->pool, sl.stream) == cudaSuccess) {
-            S->light_cache.emplace(key, LightEntry{static_cast<float*>(T), n, false});
+            LightEntry e;
+            e.T = static_cast<float*>(T);
+            e.n = n;
+            e.last_use = ++S->light_clock;
+            S->light_cache.emplace(key, e);
             m.fill = key;
           } else {
             cudaGetLastError();
@@ -334,7 +376,10 @@ bool admit(gs3_server* S) {
         if (st == GS3_OK && !m.fill.empty())
           cudaMemcpyAsync(S->light_cache[m.fill].T, Tws, 4 * n, cudaMemcpyDeviceToDevice, sl.stream);
       }
-      if (st != GS3_OK) settle_fill(S, sl, m, false);
+      if (st != GS3_OK) {
+        settle_fill(S, sl, m, false);
+        settle_reuse(S, m);
+      }
     } else {
       BatchFrame fr[kMaxBatch];
       for (int i = 0; i < sl.n; ++i) {

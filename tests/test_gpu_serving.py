@@ -96,6 +96,29 @@ def test_light_cache_reuses_shadow_values(scenes):
     srv.close()
 
 
+def test_light_cache_evicts_least_recently_used(scenes):
+    """A full light cache drops its least recently used entry for a new light;
+    one request at a time, so which lights are kept is fixed: with room for
+    two, A B A C B C A reuses only the third (A) and the sixth (C)."""
+    import torch
+    from paper_2410_11419_gb300 import render as R
+    srv = R.Server(hbm_budget=8 << 30, max_inflight=2, light_cache=2)
+    sid = srv.add_scene(scenes[1])
+    lights = {k: synth.camera_light_pair(40 + i, 128, 128)[1] for i, k in enumerate("ABC")}
+    order = "ABACBCA"
+    reused = []
+    for i, k in enumerate(order):
+        cam = synth.camera_light_pair(50 + i, 128, 128)[0]
+        out = torch.full((128, 128, 3), -1.0, device="cuda")
+        torch.cuda.synchronize()
+        before = srv.stats().light_reuse
+        assert srv.wait(srv.submit(sid, cam, lights[k], out))[0] == 0
+        reused.append(srv.stats().light_reuse - before)
+        assert torch.equal(out, alone(scenes[1], cam, lights[k])), (i, k)
+    assert reused == [0, 0, 1, 0, 0, 1, 0]
+    srv.close()
+
+
 def test_admission_respects_budget(scenes):
     import torch
     from paper_2410_11419_gb300 import _native as N, render as R
