@@ -127,6 +127,21 @@ def test_frame_parity(gs3, oracle, name, make, seed, w, h):
     check_float_stages(g, fr)
 
 
+@pytest.mark.parametrize("seed,w,h", [(30, 16384, 16), (34, 16, 16384)], ids=["wide_16384", "tall_16384"])
+def test_maximum_image_sides(gs3, oracle, seed, w, h):
+    """The largest image side (16384 pixels, 1024 tiles): one tile row of
+    1024 columns (the binning's widest placement and 2048-item chunks), and
+    one tile column of 1024 rows (the row pass's widest placement, a plan
+    block with every thread a row); 90 degrees along the long side."""
+    import math
+    fov = 90.0 if h > w else math.degrees(2 * math.atan(h / w))
+    cam, light = synth.camera_light_pair(seed, w, h, fov_y_deg=fov)
+    g, fr = run_both(gs3, oracle, synth.tiny_scene(0), cam, light)
+    assert g["hdr"].pairs_cam == fr["cam_P"] > 0 and g["hdr"].pairs_light == fr["light_P"] > 0
+    check_integer_stages(g, fr)
+    check_float_stages(g, fr)
+
+
 @pytest.mark.parametrize("ablate", [1, 2, 4, 7, 8])
 def test_ablations(gs3, oracle, ablate):
     scene = synth.tiny_scene(0)
